@@ -1,0 +1,289 @@
+"""Plain FP64 CPU oracle of the CTU-MHD patch step (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA path never does, and nothing
+here imports the CUDA path: the two share no code.  The arithmetic lives in
+``ctu_oracle.c`` (the scheme of Mignone et al., Sections 3-4) and
+``exact_euler.c`` (the exact Euler Riemann solution used to pin it); this
+module only compiles them with ``gcc -O2 -ffp-contract=off`` and marshals
+numpy arrays through ctypes.
+
+Array convention: a patch is a C-contiguous float64 array of shape
+``(9, NZ, NY, NX)`` with ``N = n + 2*g`` per dimension, ``g = 4`` for active
+dimensions and 0 for inactive ones (``n = 1`` there).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+LIB_PATH = HERE / "liboracle.so"
+SOURCES = ["ctu_oracle.c", "exact_euler.c", "srmhd_oracle.c"]
+NG = 4
+NVAR = 9
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle into ``oracle/liboracle.so``."""
+    srcs = [HERE / s for s in SOURCES if (HERE / s).exists()]
+    if LIB_PATH.exists() and not force:
+        newest = max(p.stat().st_mtime for p in srcs)
+        if LIB_PATH.stat().st_mtime >= newest:
+            return LIB_PATH
+    tmp = LIB_PATH.with_suffix(f".{os.getpid()}.tmp.so")
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99",
+           "-fPIC", "-shared", "-o", str(tmp)] + [str(s) for s in srcs] + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(str(LIB_PATH))
+        D, I, P = ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+        L.or_mhd_step.restype = I
+        L.or_mhd_step.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, I, I,
+                                  ctypes.POINTER(ctypes.c_long), P, I, P]
+        L.or_mhd_max_speed.restype = D
+        L.or_mhd_max_speed.argtypes = [P, I, I, I, I, D, D, D, D]
+        L.or_mhd_eigen.restype = None
+        L.or_mhd_eigen.argtypes = [P, D, D, P, P, P]
+        L.or_mhd_riemann.restype = I
+        L.or_mhd_riemann.argtypes = [P, P, D, D, P]
+        L.or_mhd_char_predict.restype = None
+        L.or_mhd_char_predict.argtypes = [P, D, D, D, I, I, P, P]
+        L.or_mhd_prim2cons.restype = None
+        L.or_mhd_prim2cons.argtypes = [P, D, P]
+        L.or_mhd_cons2prim.restype = I
+        L.or_mhd_cons2prim.argtypes = [P, D, P]
+        L.or_mhd_cfast.restype = D
+        L.or_mhd_cfast.argtypes = [P, D]
+        L.or_euler_sample.restype = I
+        L.or_euler_sample.argtypes = [D, D, D, D, D, D, D, D, P]
+        if hasattr(L, "or_srmhd_step"):
+            L.or_srmhd_step.restype = I
+            L.or_srmhd_step.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, P, D]
+            L.or_srmhd_max_speed.restype = D
+            L.or_srmhd_max_speed.argtypes = [P, I, I, I, I, D, D, D, D]
+            L.or_srmhd_prim2cons.restype = None
+            L.or_srmhd_prim2cons.argtypes = [P, D, P]
+            L.or_srmhd_cons2prim.restype = I
+            L.or_srmhd_cons2prim.argtypes = [P, D, P]
+            L.or_srmhd_fast_speeds.restype = None
+            L.or_srmhd_fast_speeds.argtypes = [P, D, P, P]
+            L.or_srmhd_riemann.restype = I
+            L.or_srmhd_riemann.argtypes = [P, P, D, D, P]
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- geometry
+
+def ghosts(ndim: int):
+    return [NG if d < ndim else 0 for d in range(3)]
+
+
+def shape(n, ndim):
+    """Ghosted array shape (9, NZ, NY, NX) of a patch with interior n=(nx,ny,nz)."""
+    g = ghosts(ndim)
+    return (NVAR, n[2] + 2 * g[2], n[1] + 2 * g[1], n[0] + 2 * g[0])
+
+
+def interior(A, n, ndim):
+    g = ghosts(ndim)
+    return A[..., g[2]:g[2] + n[2], g[1]:g[1] + n[1], g[0]:g[0] + n[0]]
+
+
+def fill_periodic(U, n, ndim):
+    """Fill the ghost cells of U in place with periodic copies."""
+    g = ghosts(ndim)
+    for d in range(ndim):
+        ax = 3 - d
+        nd, gd = n[d], g[d]
+        sl = [slice(None)] * 4
+        src = [slice(None)] * 4
+        sl[ax] = slice(0, gd)
+        src[ax] = slice(nd, nd + gd)
+        U[tuple(sl)] = U[tuple(src)]
+        sl[ax] = slice(nd + gd, nd + 2 * gd)
+        src[ax] = slice(gd, 2 * gd)
+        U[tuple(sl)] = U[tuple(src)]
+    return U
+
+
+def fill_outflow(U, n, ndim):
+    """Zero-gradient ghost cells (copy of the nearest interior layer)."""
+    g = ghosts(ndim)
+    for d in range(ndim):
+        ax = 3 - d
+        nd, gd = n[d], g[d]
+        for k in range(gd):
+            sl = [slice(None)] * 4
+            src = [slice(None)] * 4
+            sl[ax] = k
+            src[ax] = gd
+            U[tuple(sl)] = U[tuple(src)]
+            sl[ax] = nd + gd + k
+            src[ax] = nd + gd - 1
+            U[tuple(sl)] = U[tuple(src)]
+    return U
+
+
+# ---------------------------------------------------------------- MHD step
+
+def mhd_step(U, n, ndim, dx, dt, ch, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
+             windows=None, reg=None, upwind=0):
+    """One CTU step of a ghost-filled patch; returns (Unew, n_bad_states).
+
+    windows: optional list of (d, f, a0, a1, b0, b1, dst, weight) flux-register
+    windows accumulated into the float64 array `reg` (see or_mhd_step)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    assert U.shape == shape(n, ndim), (U.shape, shape(n, ndim))
+    Un = np.empty_like(U)
+    dx = list(dx) + [1.0] * (3 - len(dx))
+    nwin = 0 if windows is None else len(windows)
+    win = np.zeros(max(1, 7 * nwin), dtype=np.int64)
+    wgt = np.zeros(max(1, nwin))
+    for i, w in enumerate(windows or []):
+        win[7 * i:7 * i + 7] = w[:7]
+        wgt[i] = w[7]
+    regp = None
+    if nwin:
+        assert reg.dtype == np.float64 and reg.flags.c_contiguous
+        regp = _dp(reg)
+    bad = lib().or_mhd_step(_dp(U), _dp(Un), int(n[0]), int(n[1]), int(n[2]), int(ndim),
+                            float(dx[0]), float(dx[1]), float(dx[2]), float(dt), float(ch),
+                            float(gamma), float(glm_alpha), int(recon), int(upwind),
+                            win.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(wgt),
+                            nwin, regp)
+    return Un, bad
+
+
+def boundary_windows(n, ndim, weight=1.0, base=0):
+    """Windows covering the 2*ndim boundary faces of a patch, stored one after
+    another from offset `base` in the order x-, x+, y-, y+, z-, z+."""
+    out = []
+    off = base
+    for d in range(ndim):
+        a, b = [e for e in range(3) if e != d]
+        for f in (0, n[d]):
+            out.append((d, f, 0, n[a], 0, n[b], off, weight))
+            off += NVAR * n[a] * n[b]
+    return out, off - base
+
+
+def mhd_max_speed(U, n, ndim, dx, gamma=5.0 / 3.0):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    dx = list(dx) + [1.0] * (3 - len(dx))
+    return lib().or_mhd_max_speed(_dp(U), int(n[0]), int(n[1]), int(n[2]), int(ndim),
+                                  float(dx[0]), float(dx[1]), float(dx[2]), float(gamma))
+
+
+def dt_ch(max_speed, dx, ndim, cfl):
+    """dt = C_a / max_d(lambda_d/dx_d) (Eq. Ca) and c_h = C_a min(dx) / dt."""
+    dt = cfl / max_speed
+    ch = cfl * min(dx[:ndim]) / dt
+    return dt, ch
+
+
+def mhd_eigen(V, gamma, ch):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    lam = np.zeros(NVAR)
+    L = np.zeros((NVAR, NVAR))
+    R = np.zeros((NVAR, NVAR))
+    lib().or_mhd_eigen(_dp(V), float(gamma), float(ch), _dp(lam), _dp(L), _dp(R))
+    return lam, L, R
+
+
+def mhd_riemann(VL, VR, gamma, ch):
+    VL = np.ascontiguousarray(VL, dtype=np.float64)
+    VR = np.ascontiguousarray(VR, dtype=np.float64)
+    F = np.zeros(NVAR)
+    lib().or_mhd_riemann(_dp(VL), _dp(VR), float(gamma), float(ch), _dp(F))
+    return F
+
+
+def mhd_char_predict(vs, gamma, ch, dtdx, recon, upwind=0):
+    vs = np.ascontiguousarray(vs, dtype=np.float64).reshape(5, NVAR)
+    Vp = np.zeros(NVAR)
+    Vm = np.zeros(NVAR)
+    lib().or_mhd_char_predict(_dp(vs), float(gamma), float(ch), float(dtdx), int(recon),
+                              int(upwind), _dp(Vp), _dp(Vm))
+    return Vp, Vm
+
+
+def mhd_prim2cons(V, gamma):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    U = np.zeros(NVAR)
+    lib().or_mhd_prim2cons(_dp(V), float(gamma), _dp(U))
+    return U
+
+
+def mhd_cons2prim(U, gamma):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    V = np.zeros(NVAR)
+    bad = lib().or_mhd_cons2prim(_dp(U), float(gamma), _dp(V))
+    return V, bad
+
+
+def mhd_cfast(Vloc, gamma):
+    Vloc = np.ascontiguousarray(Vloc, dtype=np.float64)
+    return lib().or_mhd_cfast(_dp(Vloc), float(gamma))
+
+
+def euler_sample(left, right, gamma, xi):
+    """Exact Euler Riemann solution (rho, u, p) at xi = x/t; xi may be an array."""
+    xi = np.atleast_1d(np.asarray(xi, dtype=np.float64))
+    out = np.zeros((xi.size, 3))
+    o = np.zeros(3)
+    for i, x in enumerate(xi):
+        it = lib().or_euler_sample(float(left[0]), float(left[1]), float(left[2]),
+                                   float(right[0]), float(right[1]), float(right[2]),
+                                   float(gamma), float(x), _dp(o))
+        if it < 0:
+            raise ValueError("vacuum generated")
+        out[i] = o
+    return out
+
+
+def mhd_run(U, n, ndim, dx, steps, cfl, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
+            bc="periodic", t_end=None, upwind=0):
+    """Advance a patch `steps` CTU steps (or up to t_end), filling ghosts each
+    step; returns (U, t, dts)."""
+    U = np.array(U, dtype=np.float64, copy=True)
+    fill = fill_periodic if bc == "periodic" else fill_outflow
+    t = 0.0
+    dts = []
+    k = 0
+    while True:
+        if t_end is None and k >= steps:
+            break
+        if t_end is not None and t >= t_end * (1 - 1e-14):
+            break
+        fill(U, n, ndim)
+        m = mhd_max_speed(U, n, ndim, dx, gamma)
+        dt, ch = dt_ch(m, list(dx), ndim, cfl)
+        if t_end is not None and t + dt > t_end:
+            dt = t_end - t
+        U, bad = mhd_step(U, n, ndim, dx, dt, ch, gamma, glm_alpha, recon, upwind=upwind)
+        if bad:
+            raise FloatingPointError(f"oracle met {bad} unphysical states at step {k}")
+        t += dt
+        dts.append((dt, ch))
+        k += 1
+    fill(U, n, ndim)
+    return U, t, dts

@@ -1,0 +1,815 @@
+/*
+ * ctu_oracle.c -- plain, slow, single-threaded FP64 CPU oracle of the
+ * unsplit CTU patch step for ideal MHD with GLM divergence cleaning.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the package smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or helper with the CUDA path.  Build with
+ *     gcc -O2 -ffp-contract=off -fPIC -shared
+ * so that every expression is rounded exactly as written.
+ *
+ * What it follows (Mignone et al., "The PLUTO code for adaptive mesh
+ * computations in astrophysical fluid dynamics"):
+ *   - ideal MHD equations and ideal-gas energy: Section 2.1, Eq. (1)-(2)
+ *   - GLM cleaning: Section 3, Eq. (glm2x2); psi source operator-split
+ *   - unsplit update:             Section 3.1, Eq. (update), (incrementop_hyp)
+ *   - n+1/2 face Riemann problems: Section 3.1, Eq. (ctu_flux)
+ *   - corner-coupled states with first-order transverse fluxes:
+ *                                  Section 3.1, Eq. (transv) with Pi = 0
+ *   - CFL time step:               Section 3.1, Eq. (Ca)
+ *   - characteristic projection:   Section 3.2, Eq. (char_var)
+ *   - upwind characteristic tracing with w_ref = w_(+/-):
+ *                                  Section 3.2, Eq. (wnorm_predp), (wnorm_predm)
+ *   - right-eigenvector recombination with the S_Bx and S_psi sources:
+ *                                  Section 3.2 (V*_{i,+/-} expansion)
+ *   - PPM, MC limiter, MinMod, parabolic limiter:
+ *                                  Section 3.2, Eq. (ppm1), (MClim), (minmod),
+ *                                  (ppm_parabolic_lim)
+ *   - linear reconstruction:       Section 3.2, Eq. (Linear)
+ *   - flux-register contribution:  Section 4.2, Eq. (fluxcorr)
+ * The paper gives neither the primitive eigenvectors nor the Riemann solver
+ * formulas; they are written here from the mathematics: the eigenvectors are
+ * derived from the primitive Jacobian of Eq. (1) (Roe-Balsara normalisation),
+ * the solver is HLLD (Miyoshi & Kusano 2005) with the exact linear (B_n, psi)
+ * face solve of Dedner et al. (2002).
+ *
+ * Variable order.  Primitive V = (rho, vx, vy, vz, p, Bx, By, Bz, psi),
+ * conservative U = (rho, mx, my, mz, E, Bx, By, Bz, psi).  Arrays are SoA:
+ * U[var * ncell + cell], cell = (k * NY + j) * NX + i over the ghosted patch,
+ * x fastest.  Active dimensions carry 4 ghost cells per side, inactive ones
+ * (ndim < 3) carry none and have n = 1.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NVAR 9
+#define NGHOST 4
+
+/* Local 1-D frame for a sweep along d: local component q reads global
+ * component PERM[d][q].  Local order: (rho, v_n, v_t1, v_t2, p, B_n, B_t1,
+ * B_t2, psi) with (t1, t2) = (y, z), (x, z), (x, y) for d = x, y, z. */
+static const int PERM[3][NVAR] = {
+    {0, 1, 2, 3, 4, 5, 6, 7, 8},
+    {0, 2, 1, 3, 4, 6, 5, 7, 8},
+    {0, 3, 1, 2, 4, 7, 5, 6, 8},
+};
+
+/* ------------------------------------------------------------------ */
+/* Equation of state and variable maps, Section 2.1                    */
+/* ------------------------------------------------------------------ */
+
+/* U(V): E = p/(Gamma-1) + rho v^2/2 + B^2/2 (ideal gas, Section 2.1). */
+void or_mhd_prim2cons(const double *V, double gam, double *U)
+{
+    double rho = V[0];
+    double v2 = V[1] * V[1] + V[2] * V[2] + V[3] * V[3];
+    double B2 = V[5] * V[5] + V[6] * V[6] + V[7] * V[7];
+    U[0] = rho;
+    U[1] = rho * V[1];
+    U[2] = rho * V[2];
+    U[3] = rho * V[3];
+    U[4] = V[4] / (gam - 1.0) + 0.5 * rho * v2 + 0.5 * B2;
+    U[5] = V[5];
+    U[6] = V[6];
+    U[7] = V[7];
+    U[8] = V[8];
+}
+
+/* V(U): p = (Gamma-1)(E - m^2/(2 rho) - B^2/2).  Returns 1 when rho <= 0 or
+ * p <= 0 (or NaN), 0 otherwise. */
+int or_mhd_cons2prim(const double *U, double gam, double *V)
+{
+    double rho = U[0];
+    double m2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
+    double B2 = U[5] * U[5] + U[6] * U[6] + U[7] * U[7];
+    V[0] = rho;
+    V[1] = U[1] / rho;
+    V[2] = U[2] / rho;
+    V[3] = U[3] / rho;
+    V[4] = (gam - 1.0) * (U[4] - 0.5 * m2 / rho - 0.5 * B2);
+    V[5] = U[5];
+    V[6] = U[6];
+    V[7] = U[7];
+    V[8] = U[8];
+    return (rho > 0.0 && V[4] > 0.0) ? 0 : 1;
+}
+
+/* Fast magnetosonic speed along the local normal:
+ * c_f^2 = ( a^2 + b^2 + sqrt((a^2 - b^2)^2 + 4 a^2 b_t^2) ) / 2,
+ * the larger root of c^4 - (a^2 + b^2) c^2 + a^2 b_n^2 = 0 written with a
+ * non-negative discriminant. */
+double or_mhd_cfast(const double *Vloc, double gam)
+{
+    double rho = Vloc[0];
+    double a2 = gam * Vloc[4] / rho;
+    double bn2 = Vloc[5] * Vloc[5] / rho;
+    double bt2 = (Vloc[6] * Vloc[6] + Vloc[7] * Vloc[7]) / rho;
+    double b2 = bn2 + bt2;
+    double disc = sqrt((a2 - b2) * (a2 - b2) + 4.0 * a2 * bt2);
+    return sqrt(0.5 * (a2 + b2 + disc));
+}
+
+/* Physical MHD flux along the local normal, Eq. (1).  F[5] (B_n) and F[8]
+ * (psi) are left at zero: the GLM face solve supplies them. */
+static void mhd_flux(const double *V, const double *U, double *F)
+{
+    double rho = V[0], u = V[1], v = V[2], w = V[3], p = V[4];
+    double Bn = V[5], B1 = V[6], B2 = V[7];
+    double Bsq = Bn * Bn + B1 * B1 + B2 * B2;
+    double pt = p + 0.5 * Bsq;
+    double vB = u * Bn + v * B1 + w * B2;
+    F[0] = rho * u;
+    F[1] = rho * u * u + pt - Bn * Bn;
+    F[2] = rho * u * v - Bn * B1;
+    F[3] = rho * u * w - Bn * B2;
+    F[4] = (U[4] + pt) * u - Bn * vB;
+    F[5] = 0.0;
+    F[6] = u * B1 - Bn * v;
+    F[7] = u * B2 - Bn * w;
+    F[8] = 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Eigen-structure of the primitive system along the local normal.     */
+/* ------------------------------------------------------------------ */
+/*
+ * The 7-wave block acts on (rho, v_n, v_t1, v_t2, p, B_t1, B_t2) with B_n a
+ * parameter; the 2-wave GLM block acts on (B_n, psi) with matrix
+ * [[0, 1], [c_h^2, 0]].  Waves, in order of speed:
+ *   0: v-c_f  1: v-c_a  2: v-c_s  3: v  4: v+c_s  5: v+c_a  6: v+c_f
+ *   7: -c_h   8: +c_h
+ * R[k][q] is component q of right eigenvector k, L[k][q] of left eigenvector
+ * k, in the local order; L R = I.  The coupling of the 7-wave block to
+ * d(B_n)/dn and d(psi)/dn is not part of this block: the step adds it as the
+ * S_Bx, S_psi source of Section 3.2.
+ */
+void or_mhd_eigen(const double *V, double gam, double ch,
+                  double *lam, double *L, double *R)
+{
+    int k, q;
+    double rho = V[0], u = V[1], p = V[4];
+    double Bn = V[5], B1 = V[6], B2 = V[7];
+    double a2 = gam * p / rho;
+    double a = sqrt(a2);
+    double srho = sqrt(rho);
+    double bn2 = Bn * Bn / rho;
+    double bt2 = (B1 * B1 + B2 * B2) / rho;
+    double b2 = bn2 + bt2;
+    double disc = sqrt((a2 - b2) * (a2 - b2) + 4.0 * a2 * bt2); /* c_f^2 - c_s^2 */
+    double cf2 = 0.5 * (a2 + b2 + disc);
+    double cs2 = a2 * bn2 / cf2; /* c_f^2 c_s^2 = a^2 b_n^2 */
+    double cf = sqrt(cf2), cs = sqrt(cs2), ca = sqrt(bn2);
+    double af, as, b1, b2n, S, bt;
+    double fa, sa; /* a^2 - c_s^2 and c_f^2 - a^2, each without cancellation */
+
+    if (a2 >= b2) {
+        fa = 0.5 * (a2 - b2 + disc);
+        sa = (disc + (a2 - b2) > 0.0) ? 2.0 * a2 * bt2 / (disc + (a2 - b2)) : 0.0;
+    } else {
+        sa = 0.5 * (b2 - a2 + disc);
+        fa = 2.0 * a2 * bt2 / (disc + (b2 - a2));
+    }
+    if (disc > 0.0) {
+        af = sqrt(fa / disc);
+        as = sqrt(sa / disc);
+    } else { /* triple umbilic point: a = |b_n|, b_t = 0 */
+        af = 1.0;
+        as = 0.0;
+    }
+    bt = sqrt(B1 * B1 + B2 * B2);
+    if (bt2 > 1.0e-24 * a2) {
+        b1 = B1 / bt;
+        b2n = B2 / bt;
+    } else {
+        b1 = 1.0 / sqrt(2.0);
+        b2n = 1.0 / sqrt(2.0);
+    }
+    S = copysign(1.0, Bn);
+
+    for (k = 0; k < NVAR * NVAR; k++) {
+        L[k] = 0.0;
+        R[k] = 0.0;
+    }
+#define RR(k, q) R[(k) * NVAR + (q)]
+#define LL(k, q) L[(k) * NVAR + (q)]
+    lam[0] = u - cf;
+    lam[1] = u - ca;
+    lam[2] = u - cs;
+    lam[3] = u;
+    lam[4] = u + cs;
+    lam[5] = u + ca;
+    lam[6] = u + cf;
+    lam[7] = -ch;
+    lam[8] = ch;
+
+    /* fast waves, s = -1 (k = 0) and s = +1 (k = 6) */
+    for (q = 0; q < 2; q++) {
+        double s = q == 0 ? -1.0 : 1.0;
+        k = q == 0 ? 0 : 6;
+        RR(k, 0) = rho * af;
+        RR(k, 1) = s * af * cf;
+        RR(k, 2) = -s * as * cs * S * b1;
+        RR(k, 3) = -s * as * cs * S * b2n;
+        RR(k, 4) = rho * af * a2;
+        RR(k, 6) = as * srho * a * b1;
+        RR(k, 7) = as * srho * a * b2n;
+        LL(k, 1) = s * af * cf / (2.0 * a2);
+        LL(k, 2) = -s * as * cs * S * b1 / (2.0 * a2);
+        LL(k, 3) = -s * as * cs * S * b2n / (2.0 * a2);
+        LL(k, 4) = af / (2.0 * rho * a2);
+        LL(k, 6) = as * b1 / (2.0 * srho * a);
+        LL(k, 7) = as * b2n / (2.0 * srho * a);
+    }
+    /* Alfven waves, k = 1 (s = -1) and k = 5 (s = +1) */
+    for (q = 0; q < 2; q++) {
+        double s = q == 0 ? -1.0 : 1.0;
+        k = q == 0 ? 1 : 5;
+        RR(k, 2) = -b2n;
+        RR(k, 3) = b1;
+        RR(k, 6) = s * S * srho * b2n;
+        RR(k, 7) = -s * S * srho * b1;
+        LL(k, 2) = -0.5 * b2n;
+        LL(k, 3) = 0.5 * b1;
+        LL(k, 6) = s * S * b2n / (2.0 * srho);
+        LL(k, 7) = -s * S * b1 / (2.0 * srho);
+    }
+    /* slow waves, k = 2 (s = -1) and k = 4 (s = +1) */
+    for (q = 0; q < 2; q++) {
+        double s = q == 0 ? -1.0 : 1.0;
+        k = q == 0 ? 2 : 4;
+        RR(k, 0) = rho * as;
+        RR(k, 1) = s * as * cs;
+        RR(k, 2) = s * af * cf * S * b1;
+        RR(k, 3) = s * af * cf * S * b2n;
+        RR(k, 4) = rho * as * a2;
+        RR(k, 6) = -af * srho * a * b1;
+        RR(k, 7) = -af * srho * a * b2n;
+        LL(k, 1) = s * as * cs / (2.0 * a2);
+        LL(k, 2) = s * af * cf * S * b1 / (2.0 * a2);
+        LL(k, 3) = s * af * cf * S * b2n / (2.0 * a2);
+        LL(k, 4) = as / (2.0 * rho * a2);
+        LL(k, 6) = -af * b1 / (2.0 * srho * a);
+        LL(k, 7) = -af * b2n / (2.0 * srho * a);
+    }
+    /* entropy wave */
+    RR(3, 0) = 1.0;
+    LL(3, 0) = 1.0;
+    LL(3, 4) = -1.0 / a2;
+    /* GLM waves on (B_n, psi) */
+    RR(7, 5) = 1.0;
+    RR(7, 8) = -ch;
+    RR(8, 5) = 1.0;
+    RR(8, 8) = ch;
+    LL(7, 5) = 0.5;
+    LL(7, 8) = -0.5 / ch;
+    LL(8, 5) = 0.5;
+    LL(8, 8) = 0.5 / ch;
+#undef RR
+#undef LL
+}
+
+/* ------------------------------------------------------------------ */
+/* Riemann solver: GLM (B_n, psi) face solve + HLLD                    */
+/* ------------------------------------------------------------------ */
+/*
+ * Numerical flux R(V_L, V_R) along the local normal.  The linear 2x2 GLM
+ * system of Eq. (glm2x2) is solved exactly at the face (Dedner et al. 2002):
+ *   B_m   = (B_nL + B_nR)/2 - (psi_R - psi_L)/(2 c_h)
+ *   psi_m = (psi_L + psi_R)/2 - c_h (B_nR - B_nL)/2
+ * with fluxes F(B_n) = psi_m, F(psi) = c_h^2 B_m; both states then carry
+ * B_n = B_m (pressure kept) into the HLLD solver of Miyoshi & Kusano (2005).
+ * Returns 1 if an input state has rho <= 0 or p <= 0.
+ */
+int or_mhd_riemann(const double *VL0, const double *VR0, double gam, double ch,
+                   double *F)
+{
+    double VL[NVAR], VR[NVAR], UL[NVAR], UR[NVAR], FL[NVAR], FR[NVAR];
+    double Bm, pm, Bn, cfL, cfR, cmax, SL, SR;
+    double sdL, sdR, den, SM, pts;
+    double rsL, rsR, vsL, vsR, wsL, wsR, B1sL, B1sR, B2sL, B2sR, EsL, EsR;
+    double UsL[NVAR], UsR[NVAR];
+    int q, bad;
+
+    for (q = 0; q < NVAR; q++) {
+        VL[q] = VL0[q];
+        VR[q] = VR0[q];
+    }
+    bad = !(VL[0] > 0.0 && VL[4] > 0.0 && VR[0] > 0.0 && VR[4] > 0.0);
+
+    Bm = 0.5 * (VL[5] + VR[5]) - 0.5 * (VR[8] - VL[8]) / ch;
+    pm = 0.5 * (VL[8] + VR[8]) - 0.5 * ch * (VR[5] - VL[5]);
+    VL[5] = Bm;
+    VR[5] = Bm;
+    Bn = Bm;
+
+    or_mhd_prim2cons(VL, gam, UL);
+    or_mhd_prim2cons(VR, gam, UR);
+    mhd_flux(VL, UL, FL);
+    mhd_flux(VR, UR, FR);
+
+    cfL = or_mhd_cfast(VL, gam);
+    cfR = or_mhd_cfast(VR, gam);
+    cmax = fmax(cfL, cfR);
+    SL = fmin(VL[1], VR[1]) - cmax;
+    SR = fmax(VL[1], VR[1]) + cmax;
+
+    if (SL >= 0.0) {
+        for (q = 0; q < NVAR; q++)
+            F[q] = FL[q];
+    } else if (SR <= 0.0) {
+        for (q = 0; q < NVAR; q++)
+            F[q] = FR[q];
+    } else {
+        double ptL = VL[4] + 0.5 * (Bn * Bn + VL[6] * VL[6] + VL[7] * VL[7]);
+        double ptR = VR[4] + 0.5 * (Bn * Bn + VR[6] * VR[6] + VR[7] * VR[7]);
+        double dL, dR, sqL, sqR, SLs, SRs;
+
+        sdL = SL - VL[1];
+        sdR = SR - VR[1];
+        den = sdR * VR[0] - sdL * VL[0];
+        SM = (sdR * VR[0] * VR[1] - sdL * VL[0] * VL[1] - ptR + ptL) / den;
+        pts = (sdR * VR[0] * ptL - sdL * VL[0] * ptR +
+               VL[0] * VR[0] * sdR * sdL * (VR[1] - VL[1])) / den;
+
+        /* single-star states (MK05 Eq. 43-48) */
+        rsL = VL[0] * sdL / (SL - SM);
+        rsR = VR[0] * sdR / (SR - SM);
+        dL = VL[0] * sdL * (SL - SM) - Bn * Bn;
+        dR = VR[0] * sdR * (SR - SM) - Bn * Bn;
+        if (fabs(dL) <= 1.0e-12 * (VL[0] * sdL * sdL + Bn * Bn)) {
+            vsL = VL[2];
+            wsL = VL[3];
+            B1sL = VL[6];
+            B2sL = VL[7];
+        } else {
+            double f = (VL[0] * sdL * sdL - Bn * Bn) / dL;
+            vsL = VL[2] - Bn * VL[6] * (SM - VL[1]) / dL;
+            wsL = VL[3] - Bn * VL[7] * (SM - VL[1]) / dL;
+            B1sL = VL[6] * f;
+            B2sL = VL[7] * f;
+        }
+        if (fabs(dR) <= 1.0e-12 * (VR[0] * sdR * sdR + Bn * Bn)) {
+            vsR = VR[2];
+            wsR = VR[3];
+            B1sR = VR[6];
+            B2sR = VR[7];
+        } else {
+            double f = (VR[0] * sdR * sdR - Bn * Bn) / dR;
+            vsR = VR[2] - Bn * VR[6] * (SM - VR[1]) / dR;
+            wsR = VR[3] - Bn * VR[7] * (SM - VR[1]) / dR;
+            B1sR = VR[6] * f;
+            B2sR = VR[7] * f;
+        }
+        {
+            double vBL = VL[1] * Bn + VL[2] * VL[6] + VL[3] * VL[7];
+            double vBR = VR[1] * Bn + VR[2] * VR[6] + VR[3] * VR[7];
+            double vBsL = SM * Bn + vsL * B1sL + wsL * B2sL;
+            double vBsR = SM * Bn + vsR * B1sR + wsR * B2sR;
+            EsL = (sdL * UL[4] - ptL * VL[1] + pts * SM + Bn * (vBL - vBsL)) / (SL - SM);
+            EsR = (sdR * UR[4] - ptR * VR[1] + pts * SM + Bn * (vBR - vBsR)) / (SR - SM);
+        }
+        UsL[0] = rsL; UsL[1] = rsL * SM; UsL[2] = rsL * vsL; UsL[3] = rsL * wsL;
+        UsL[4] = EsL; UsL[5] = Bn; UsL[6] = B1sL; UsL[7] = B2sL; UsL[8] = 0.0;
+        UsR[0] = rsR; UsR[1] = rsR * SM; UsR[2] = rsR * vsR; UsR[3] = rsR * wsR;
+        UsR[4] = EsR; UsR[5] = Bn; UsR[6] = B1sR; UsR[7] = B2sR; UsR[8] = 0.0;
+
+        sqL = sqrt(rsL);
+        sqR = sqrt(rsR);
+        SLs = SM - fabs(Bn) / sqL;
+        SRs = SM + fabs(Bn) / sqR;
+
+        if (SLs >= 0.0) {
+            for (q = 0; q < NVAR; q++)
+                F[q] = FL[q] + SL * (UsL[q] - UL[q]);
+        } else if (SRs <= 0.0) {
+            for (q = 0; q < NVAR; q++)
+                F[q] = FR[q] + SR * (UsR[q] - UR[q]);
+        } else {
+            /* double-star states (MK05 Eq. 59-63) */
+            double sB = copysign(1.0, Bn);
+            double isq = 1.0 / (sqL + sqR);
+            double vss = (sqL * vsL + sqR * vsR + (B1sR - B1sL) * sB) * isq;
+            double wss = (sqL * wsL + sqR * wsR + (B2sR - B2sL) * sB) * isq;
+            double B1ss = (sqL * B1sR + sqR * B1sL + sqL * sqR * (vsR - vsL) * sB) * isq;
+            double B2ss = (sqL * B2sR + sqR * B2sL + sqL * sqR * (wsR - wsL) * sB) * isq;
+            double vBss = SM * Bn + vss * B1ss + wss * B2ss;
+            double Uss[NVAR];
+            if (SM >= 0.0) {
+                double vBsL = SM * Bn + vsL * B1sL + wsL * B2sL;
+                Uss[0] = rsL; Uss[1] = rsL * SM; Uss[2] = rsL * vss; Uss[3] = rsL * wss;
+                Uss[4] = EsL - sqL * (vBsL - vBss) * sB;
+                Uss[5] = Bn; Uss[6] = B1ss; Uss[7] = B2ss; Uss[8] = 0.0;
+                for (q = 0; q < NVAR; q++)
+                    F[q] = FL[q] + SL * (UsL[q] - UL[q]) + SLs * (Uss[q] - UsL[q]);
+            } else {
+                double vBsR = SM * Bn + vsR * B1sR + wsR * B2sR;
+                Uss[0] = rsR; Uss[1] = rsR * SM; Uss[2] = rsR * vss; Uss[3] = rsR * wss;
+                Uss[4] = EsR + sqR * (vBsR - vBss) * sB;
+                Uss[5] = Bn; Uss[6] = B1ss; Uss[7] = B2ss; Uss[8] = 0.0;
+                for (q = 0; q < NVAR; q++)
+                    F[q] = FR[q] + SR * (UsR[q] - UR[q]) + SRs * (Uss[q] - UsR[q]);
+            }
+        }
+    }
+    F[5] = pm;
+    F[8] = ch * ch * Bm;
+    return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* Reconstruction, Section 3.2                                         */
+/* ------------------------------------------------------------------ */
+
+/* mm(a,b) = (sign a + sign b)/2 min(|a|,|b|), Eq. (minmod) */
+static double minmod(double a, double b)
+{
+    if (a > 0.0 && b > 0.0)
+        return fmin(a, b);
+    if (a < 0.0 && b < 0.0)
+        return fmax(a, b);
+    return 0.0;
+}
+
+/* MC-limited slope from the backward and forward undivided differences,
+ * Eq. (MClim). */
+static double mc_slope(double dm, double dp)
+{
+    return minmod(0.5 * (dp + dm), 2.0 * minmod(dm, dp));
+}
+
+/* Interface values w_(i,+) and w_(i,-) of one characteristic field from the
+ * stencil w[0..4] = w_(i,-2) .. w_(i,+2).  recon = 1: PPM, Eq. (ppm1) with
+ * the parabolic limiter of Eq. (ppm_parabolic_lim); recon = 0: linear,
+ * Eq. (Linear) with the MC limiter. */
+static void reconstruct(const double *w, int recon, double *wp, double *wm)
+{
+    double w0 = w[2];
+    double s0 = mc_slope(w[2] - w[1], w[3] - w[2]);
+    if (recon == 0) {
+        *wp = w0 + 0.5 * s0;
+        *wm = w0 - 0.5 * s0;
+    } else {
+        double sm = mc_slope(w[1] - w[0], w[2] - w[1]);
+        double sp = mc_slope(w[3] - w[2], w[4] - w[3]);
+        double p = 0.5 * (w0 + w[3]) - (sp - s0) / 6.0;
+        double m = 0.5 * (w0 + w[1]) + (sm - s0) / 6.0;
+        double dp = p - w0, dm = m - w0;
+        double ndp, ndm;
+        if (dp * dm > 0.0) {
+            ndp = 0.0;
+            ndm = 0.0;
+        } else {
+            ndp = (fabs(dp) >= 2.0 * fabs(dm)) ? -2.0 * dm : dp;
+            ndm = (fabs(dm) >= 2.0 * fabs(dp)) ? -2.0 * dp : dm;
+        }
+        *wp = w0 + ndp;
+        *wm = w0 + ndm;
+    }
+}
+
+/* Characteristic tracing of one field to t^(n+1/2), Eq. (wnorm_predp) and
+ * (wnorm_predm) with w_ref = w_(+/-).
+ * upwind = 0 (default): no reference state, every field is traced to both
+ *   interfaces (beta_+ = beta_- = 1), the choice Section 3.2 recommends for
+ *   smooth flows so that waves not reaching an edge still enter its value.
+ * upwind = 1: the literal selection beta_+ = [nu > 0], beta_- = [nu < 0]. */
+static void trace(double wp, double w0, double wm, double nu, int upwind,
+                  double *tp, double *tm)
+{
+    double dw = wp - wm;
+    double d2w = wp - 2.0 * w0 + wm;
+    *tp = wp;
+    *tm = wm;
+    if (!upwind || nu > 0.0)
+        *tp = wp - 0.5 * nu * (dw + d2w * (3.0 - 2.0 * nu));
+    if (!upwind || nu < 0.0)
+        *tm = wm - 0.5 * nu * (dw - d2w * (3.0 + 2.0 * nu));
+}
+
+/*
+ * Normal predictor in characteristic variables for one cell (Section 3.2).
+ * vs[l*NVAR + q], l = 0..4: primitive stencil V_(i-2) .. V_(i+2) in the local
+ * order.  Outputs the time-centred interface primitives V*_(i,+), V*_(i,-)
+ * (local order), including the S_Bx dBn/dx and S_psi dpsi/dx sources.
+ */
+void or_mhd_char_predict(const double *vs, double gam, double ch, double dtdx,
+                         int recon, int upwind, double *Vp, double *Vm)
+{
+    double lam[NVAR], L[NVAR * NVAR], R[NVAR * NVAR];
+    double tp[NVAR], tm[NVAR], rp[NVAR], rm[NVAR];
+    const double *V0 = vs + 2 * NVAR;
+    double dBn, dpsi, src[NVAR];
+    double vB;
+    int k, l, q;
+
+    or_mhd_eigen(V0, gam, ch, lam, L, R);
+    for (k = 0; k < NVAR; k++) {
+        double w[5];
+        for (l = 0; l < 5; l++) {
+            double s = 0.0;
+            for (q = 0; q < NVAR; q++)
+                s += L[k * NVAR + q] * vs[l * NVAR + q];
+            w[l] = s;
+        }
+        reconstruct(w, recon, &rp[k], &rm[k]);
+        trace(rp[k], w[2], rm[k], lam[k] * dtdx, upwind, &tp[k], &tm[k]);
+    }
+    for (q = 0; q < NVAR; q++) {
+        double sp = 0.0, sm = 0.0;
+        for (k = 0; k < NVAR; k++) {
+            sp += tp[k] * R[k * NVAR + q];
+            sm += tm[k] * R[k * NVAR + q];
+        }
+        Vp[q] = sp;
+        Vm[q] = sm;
+    }
+    /* undivided jumps of B_n and psi across the cell, from the (untraced)
+     * reconstruction of the two GLM fields */
+    dBn = (rp[7] - rm[7]) * R[7 * NVAR + 5] + (rp[8] - rm[8]) * R[8 * NVAR + 5];
+    dpsi = (rp[7] - rm[7]) * R[7 * NVAR + 8] + (rp[8] - rm[8]) * R[8 * NVAR + 8];
+    /* S_Bx and S_psi: minus the columns of the primitive Jacobian that couple
+     * the 7-wave block to d(B_n)/dn and d(psi)/dn */
+    vB = V0[1] * V0[5] + V0[2] * V0[6] + V0[3] * V0[7];
+    for (q = 0; q < NVAR; q++)
+        src[q] = 0.0;
+    src[1] = V0[5] / V0[0] * dBn;
+    src[2] = V0[6] / V0[0] * dBn;
+    src[3] = V0[7] / V0[0] * dBn;
+    src[4] = -(gam - 1.0) * vB * dBn + (gam - 1.0) * V0[5] * dpsi;
+    src[6] = V0[2] * dBn;
+    src[7] = V0[3] * dBn;
+    for (q = 0; q < NVAR; q++) {
+        Vp[q] += 0.5 * dtdx * src[q];
+        Vm[q] += 0.5 * dtdx * src[q];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Patch geometry                                                      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int n[3], g[3], N[3];
+    long ncell;
+    int ndim;
+} grid_t;
+
+static void grid_init(grid_t *G, int nx, int ny, int nz, int ndim)
+{
+    int d;
+    G->n[0] = nx;
+    G->n[1] = ny;
+    G->n[2] = nz;
+    G->ndim = ndim;
+    for (d = 0; d < 3; d++) {
+        G->g[d] = d < ndim ? NGHOST : 0;
+        G->N[d] = G->n[d] + 2 * G->g[d];
+    }
+    G->ncell = (long)G->N[0] * G->N[1] * G->N[2];
+}
+
+static long cidx(const grid_t *G, const int *c)
+{
+    return ((long)(c[2] + G->g[2]) * G->N[1] + (c[1] + G->g[1])) * G->N[0] + (c[0] + G->g[0]);
+}
+
+static long dstride(const grid_t *G, int d)
+{
+    return d == 0 ? 1 : (d == 1 ? G->N[0] : (long)G->N[0] * G->N[1]);
+}
+
+/* ------------------------------------------------------------------ */
+/* CFL, Eq. (Ca)                                                       */
+/* ------------------------------------------------------------------ */
+
+/* max over interior cells of max_d (|v_d| + c_f,d)/dx_d.  The caller sets
+ * dt = C_a / max and c_h = max * min_d dx_d. */
+double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
+                        double dx, double dy, double dz, double gam)
+{
+    grid_t G;
+    double h[3] = {dx, dy, dz}, m = 0.0;
+    int c[3], d, q;
+    grid_init(&G, nx, ny, nz, ndim);
+    for (c[2] = 0; c[2] < G.n[2]; c[2]++)
+        for (c[1] = 0; c[1] < G.n[1]; c[1]++)
+            for (c[0] = 0; c[0] < G.n[0]; c[0]++) {
+                long id = cidx(&G, c);
+                double Uc[NVAR], V[NVAR], Vl[NVAR];
+                for (q = 0; q < NVAR; q++)
+                    Uc[q] = U[q * G.ncell + id];
+                or_mhd_cons2prim(Uc, gam, V);
+                for (d = 0; d < ndim; d++) {
+                    double s;
+                    for (q = 0; q < NVAR; q++)
+                        Vl[q] = V[PERM[d][q]];
+                    s = (fabs(Vl[1]) + or_mhd_cfast(Vl, gam)) / h[d];
+                    if (s > m)
+                        m = s;
+                }
+            }
+    return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* One CTU step on one ghost-filled patch                              */
+/* ------------------------------------------------------------------ */
+/*
+ * Unew receives U with the interior advanced by dt; ghosts are copied.
+ *
+ * Flux registers, Eq. (fluxcorr): nwin face windows, window w described by
+ * win[7*w .. 7*w+6] = (d, f, a0, a1, b0, b1, dst).  It covers the faces
+ * normal to d on plane f (0 <= f <= n_d; plane f separates cells f-1 and f)
+ * with the two other coordinates a in [a0, a1), b in [b0, b1) ((a, b) the
+ * two other dimensions in increasing order).  For every such face
+ *     reg[dst + (q * nb + (b - b0)) * na + (a - a0)] += wgt[w] * dt * A * F_q
+ * with na = a1 - a0, nb = b1 - b0, A the face area (product of the two
+ * transverse cell widths) and F the n+1/2 flux through the face in +d.
+ * Returns the number of states met with rho <= 0 or p <= 0.
+ */
+int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
+                double dx, double dy, double dz, double dt, double ch,
+                double gam, double glm_alpha, int recon, int upwind,
+                const long *win, const double *wgt, int nwin, double *reg)
+{
+    grid_t G;
+    double h[3] = {dx, dy, dz};
+    double *V, *F1[3] = {0, 0, 0}, *Up[3] = {0, 0, 0}, *Um[3] = {0, 0, 0}, *F[3] = {0, 0, 0};
+    int c[3], d, q, bad = 0;
+    long nc;
+
+    grid_init(&G, nx, ny, nz, ndim);
+    nc = G.ncell;
+    V = (double *)malloc(sizeof(double) * NVAR * nc);
+
+    /* 1. V = V(U) everywhere, ghosts included */
+    for (long id = 0; id < nc; id++) {
+        double Uc[NVAR], Vc[NVAR];
+        for (q = 0; q < NVAR; q++)
+            Uc[q] = U[q * nc + id];
+        bad += or_mhd_cons2prim(Uc, gam, Vc);
+        for (q = 0; q < NVAR; q++)
+            V[q * nc + id] = Vc[q];
+    }
+
+    /* 2. first-order Godunov fluxes F^n_d = R(U_c, U_(c+e_d)) on the faces the
+     *    transverse increments need; F1[d] at cell c is its upper face. */
+    for (d = 0; d < ndim; d++) {
+        long st = dstride(&G, d);
+        int lo[3], hi[3], e;
+        F1[d] = (double *)calloc((size_t)NVAR * nc, sizeof(double));
+        for (e = 0; e < 3; e++) {
+            if (e >= ndim) {
+                lo[e] = 0;
+                hi[e] = 0;
+            } else if (e == d) {
+                lo[e] = -1;
+                hi[e] = G.n[e] - 1;
+            } else {
+                lo[e] = -1;
+                hi[e] = G.n[e];
+            }
+        }
+        for (c[2] = lo[2]; c[2] <= hi[2]; c[2]++)
+            for (c[1] = lo[1]; c[1] <= hi[1]; c[1]++)
+                for (c[0] = lo[0]; c[0] <= hi[0]; c[0]++) {
+                    long id = cidx(&G, c);
+                    double VL[NVAR], VR[NVAR], Fl[NVAR];
+                    for (q = 0; q < NVAR; q++) {
+                        VL[q] = V[PERM[d][q] * nc + id];
+                        VR[q] = V[PERM[d][q] * nc + id + st];
+                    }
+                    or_mhd_riemann(VL, VR, gam, ch, Fl);
+                    for (q = 0; q < NVAR; q++)
+                        F1[d][PERM[d][q] * nc + id] = Fl[q];
+                }
+    }
+
+    /* 3. normal predictors + transverse correction, Eq. (transv) */
+    for (d = 0; d < ndim; d++) {
+        long st = dstride(&G, d);
+        int lo[3], hi[3], e, tr[2], ntr = 0;
+        for (e = 0; e < ndim; e++)
+            if (e != d)
+                tr[ntr++] = e;
+        Up[d] = (double *)calloc((size_t)NVAR * nc, sizeof(double));
+        Um[d] = (double *)calloc((size_t)NVAR * nc, sizeof(double));
+        for (e = 0; e < 3; e++) {
+            lo[e] = 0;
+            hi[e] = e < ndim ? G.n[e] - 1 : 0;
+        }
+        lo[d] = -1;
+        hi[d] = G.n[d];
+        for (c[2] = lo[2]; c[2] <= hi[2]; c[2]++)
+            for (c[1] = lo[1]; c[1] <= hi[1]; c[1]++)
+                for (c[0] = lo[0]; c[0] <= hi[0]; c[0]++) {
+                    long id = cidx(&G, c);
+                    double vs[5 * NVAR], Vp[NVAR], Vm[NVAR], Ul[NVAR], Ug[NVAR], T[NVAR];
+                    int l, t;
+                    for (l = 0; l < 5; l++)
+                        for (q = 0; q < NVAR; q++)
+                            vs[l * NVAR + q] = V[PERM[d][q] * nc + id + (l - 2) * st];
+                    or_mhd_char_predict(vs, gam, ch, dt / h[d], recon, upwind, Vp, Vm);
+                    /* transverse increments L^n_d' = -(F_(d',+) - F_(d',-))/dx_d' */
+                    for (q = 0; q < NVAR; q++)
+                        T[q] = 0.0;
+                    for (t = 0; t < ntr; t++) {
+                        int e2 = tr[t];
+                        long st2 = dstride(&G, e2);
+                        for (q = 0; q < NVAR; q++)
+                            T[q] += (F1[e2][q * nc + id - st2] - F1[e2][q * nc + id]) / h[e2];
+                    }
+                    or_mhd_prim2cons(Vp, gam, Ul);
+                    for (q = 0; q < NVAR; q++)
+                        Ug[PERM[d][q]] = Ul[q];
+                    for (q = 0; q < NVAR; q++)
+                        Up[d][q * nc + id] = Ug[q] + 0.5 * dt * T[q];
+                    or_mhd_prim2cons(Vm, gam, Ul);
+                    for (q = 0; q < NVAR; q++)
+                        Ug[PERM[d][q]] = Ul[q];
+                    for (q = 0; q < NVAR; q++)
+                        Um[d][q * nc + id] = Ug[q] + 0.5 * dt * T[q];
+                }
+    }
+
+    /* 4. n+1/2 Riemann problems, Eq. (ctu_flux); F[d] at c is its upper face */
+    for (d = 0; d < ndim; d++) {
+        long st = dstride(&G, d);
+        int lo[3], hi[3], e;
+        F[d] = (double *)calloc((size_t)NVAR * nc, sizeof(double));
+        for (e = 0; e < 3; e++) {
+            lo[e] = 0;
+            hi[e] = e < ndim ? G.n[e] - 1 : 0;
+        }
+        lo[d] = -1;
+        for (c[2] = lo[2]; c[2] <= hi[2]; c[2]++)
+            for (c[1] = lo[1]; c[1] <= hi[1]; c[1]++)
+                for (c[0] = lo[0]; c[0] <= hi[0]; c[0]++) {
+                    long id = cidx(&G, c);
+                    double UL[NVAR], UR[NVAR], VLg[NVAR], VRg[NVAR], VL[NVAR], VR[NVAR], Fl[NVAR];
+                    for (q = 0; q < NVAR; q++) {
+                        UL[q] = Up[d][q * nc + id];
+                        UR[q] = Um[d][q * nc + id + st];
+                    }
+                    bad += or_mhd_cons2prim(UL, gam, VLg);
+                    bad += or_mhd_cons2prim(UR, gam, VRg);
+                    for (q = 0; q < NVAR; q++) {
+                        VL[q] = VLg[PERM[d][q]];
+                        VR[q] = VRg[PERM[d][q]];
+                    }
+                    or_mhd_riemann(VL, VR, gam, ch, Fl);
+                    for (q = 0; q < NVAR; q++)
+                        F[d][PERM[d][q] * nc + id] = Fl[q];
+                }
+    }
+
+    /* 5. conservative update, Eq. (update): U + dt * (L_x + L_y + L_z) */
+    memcpy(Unew, U, sizeof(double) * NVAR * nc);
+    {
+        double hmin = h[0], damp;
+        for (d = 1; d < ndim; d++)
+            hmin = fmin(hmin, h[d]);
+        /* psi source -(c_h^2/c_p^2) psi integrated exactly over dt (operator
+         * split, Section 3.1), with c_h^2/c_p^2 = glm_alpha c_h / min dx */
+        damp = exp(-glm_alpha * ch * dt / hmin);
+        for (c[2] = 0; c[2] < G.n[2]; c[2]++)
+            for (c[1] = 0; c[1] < G.n[1]; c[1]++)
+                for (c[0] = 0; c[0] < G.n[0]; c[0]++) {
+                    long id = cidx(&G, c);
+                    for (q = 0; q < NVAR; q++) {
+                        double s = 0.0;
+                        for (d = 0; d < ndim; d++)
+                            s += (F[d][q * nc + id - dstride(&G, d)] - F[d][q * nc + id]) / h[d];
+                        Unew[q * nc + id] = U[q * nc + id] + dt * s;
+                    }
+                    Unew[8 * nc + id] *= damp;
+                }
+    }
+
+    /* 6. flux-register contributions, Eq. (fluxcorr) */
+    for (int w = 0; w < nwin; w++) {
+        const long *W = win + 7 * w;
+        int wd = (int)W[0], a = wd == 0 ? 1 : 0, b = wd == 2 ? 1 : 2;
+        long na = W[3] - W[2], nb = W[5] - W[4];
+        double area = h[a] * h[b];
+        for (q = 0; q < NVAR; q++)
+            for (long jb = 0; jb < nb; jb++)
+                for (long ja = 0; ja < na; ja++) {
+                    c[wd] = (int)W[1] - 1; /* F[d] at cell c is its upper face */
+                    c[a] = (int)(W[2] + ja);
+                    c[b] = (int)(W[4] + jb);
+                    reg[W[6] + (q * nb + jb) * na + ja] +=
+                        wgt[w] * dt * area * F[wd][q * nc + cidx(&G, c)];
+                }
+    }
+
+    free(V);
+    for (d = 0; d < 3; d++) {
+        free(F1[d]);
+        free(Up[d]);
+        free(Um[d]);
+        free(F[d]);
+    }
+    return bad;
+}

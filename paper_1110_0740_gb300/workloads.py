@@ -1,0 +1,168 @@
+"""Seeded synthetic inputs for the CTU-MHD step (shared by tests and bench).
+
+This module only builds initial data: smooth random fields from Fourier
+modes, a vector-potential magnetic field, a pressure sphere, and the
+periodic ghost frame.  It holds none of the scheme's arithmetic; the only
+physics it writes out is the definition of the initial conserved state from
+the primitive one (ideal-gas total energy, Section 2.1 of the paper), which
+defines the test problem.  Both the CUDA path and the CPU oracle receive the
+same float64 arrays from here.
+
+Layout: ``(9, NZ, NY, NX)`` float64, conservative variables
+(rho, mx, my, mz, E, Bx, By, Bz, psi), 4 ghost cells per side in each active
+dimension, x fastest.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+NG = 4
+NVAR = 9
+
+
+def ghosted(n, ndim):
+    g = [NG if d < ndim else 0 for d in range(3)]
+    return (NVAR, n[2] + 2 * g[2], n[1] + 2 * g[1], n[0] + 2 * g[0])
+
+
+def pad_periodic(F, ndim):
+    """Wrap-pad the last `ndim` spatial axes of F (shape (..., nz, ny, nx))."""
+    pad = [(0, 0)] * (F.ndim - 3)
+    for ax in range(3):  # z, y, x
+        d = 2 - ax
+        pad.append((NG, NG) if d < ndim else (0, 0))
+    return np.pad(F, pad, mode="wrap")
+
+
+def ideal_cons(V, gamma):
+    """Conserved state of an ideal-gas MHD initial condition from primitives."""
+    rho, vx, vy, vz, p, bx, by, bz, psi = V
+    E = p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz) \
+        + 0.5 * (bx * bx + by * by + bz * bz)
+    return np.stack([rho, rho * vx, rho * vy, rho * vz, E, bx, by, bz, psi])
+
+
+def _modes_2d(rng, kmax):
+    ks = [(kx, ky) for kx in range(-kmax, kmax + 1) for ky in range(0, kmax + 1)
+          if 0 < kx * kx + ky * ky <= kmax * kmax and (ky > 0 or kx > 0)]
+    ph = rng.uniform(0.0, 2.0 * np.pi, size=len(ks))
+    return ks, ph
+
+
+def _field_2d(rng, n, kmax):
+    """sum_k cos(2 pi k.x + phi_k) over 0 < |k| <= kmax, scaled to max |f| = 1;
+    also returns the pieces needed for an exact spectral curl."""
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x, indexing="xy")  # shape (ny, nx)
+    ks, ph = _modes_2d(rng, kmax)
+    f = np.zeros((n, n))
+    fx = np.zeros((n, n))
+    fy = np.zeros((n, n))
+    for (kx, ky), p in zip(ks, ph):
+        arg = 2.0 * np.pi * (kx * X + ky * Y) + p
+        f += np.cos(arg)
+        fx += -2.0 * np.pi * kx * np.sin(arg)
+        fy += -2.0 * np.pi * ky * np.sin(arg)
+    s = np.abs(f).max()
+    return f / s, fx / s, fy / s
+
+
+def mhd_turb_2d(n=128, seed=0, gamma=5.0 / 3.0):
+    """2-D periodic ideal-MHD turbulence-like state on [0,1]^2 (interior n x n).
+
+    rho = 1 + 0.2 f1, p = 1 + 0.1 f2, (vx, vy) = 0.5 (f3, f4), B = curl(A_z z)
+    with A_z = 0.1 f5, where each f is a seeded random-phase sum of the modes
+    0 < |k| <= 4 normalised to max|f| = 1; psi = 0.  Returns U with ghosts."""
+    rng = np.random.default_rng(seed)
+    f1, _, _ = _field_2d(rng, n, 4)
+    f2, _, _ = _field_2d(rng, n, 4)
+    f3, _, _ = _field_2d(rng, n, 4)
+    f4, _, _ = _field_2d(rng, n, 4)
+    a, ax, ay = _field_2d(rng, n, 4)
+    rho = 1.0 + 0.2 * f1
+    p = 1.0 + 0.1 * f2
+    vx, vy = 0.5 * f3, 0.5 * f4
+    bx, by = 0.1 * ay, -0.1 * ax
+    z = np.zeros_like(rho)
+    V = np.stack([rho, vx, vy, z, p, bx, by, z, z])[:, None, :, :]
+    return pad_periodic(ideal_cons(V, gamma), 2)
+
+
+def _field_3d(rng, n, kmax, deriv=False):
+    """Real random-phase field with all modes 0 < |k| <= kmax, via inverse FFT.
+    Returns f (max |f| = 1) and, if deriv, the spectral gradient of the same
+    (unnormalised) field with the same scale factor."""
+    k1 = np.fft.fftfreq(n, d=1.0 / n)
+    kz = k1[:, None, None]
+    ky = k1[None, :, None]
+    kx = np.fft.rfftfreq(n, d=1.0 / n)[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    mask = (k2 > 0) & (k2 <= kmax * kmax)
+    spec = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+    idx = np.nonzero(mask)
+    ph = rng.uniform(0.0, 2.0 * np.pi, size=idx[0].size)
+    spec[idx] = np.exp(1j * ph)
+    f = np.fft.irfftn(spec, s=(n, n, n), axes=(0, 1, 2))
+    s = np.abs(f).max()
+    if not deriv:
+        return f / s
+    grads = []
+    for kk in (kx, ky, kz):
+        grads.append(np.fft.irfftn(spec * (2j * np.pi * kk), s=(n, n, n), axes=(0, 1, 2)) / s)
+    return f / s, grads
+
+
+def mhd_blast_3d(n=256, seed=0, gamma=5.0 / 3.0, kmax=8):
+    """3-D periodic ideal-MHD state on [0,1]^3 with a pressure sphere.
+
+    rho = 1 + 0.2 f_rho, v = 0.5 (f_x, f_y, f_z), B = curl A with A a seeded
+    random vector potential (modes 0 < |k| <= kmax) scaled to max |B| = 1,
+    p = 1 outside and 100 inside a sphere of radius 0.1 at a seeded centre
+    (periodic distance), psi = 0.  Returns U with ghosts, shape (9, n+8, n+8, n+8)."""
+    rng = np.random.default_rng(seed)
+    frho = _field_3d(rng, n, kmax)
+    vx = 0.5 * _field_3d(rng, n, kmax)
+    vy = 0.5 * _field_3d(rng, n, kmax)
+    vz = 0.5 * _field_3d(rng, n, kmax)
+    _, gax = _field_3d(rng, n, kmax, deriv=True)
+    _, gay = _field_3d(rng, n, kmax, deriv=True)
+    _, gaz = _field_3d(rng, n, kmax, deriv=True)
+    # B = curl A: (dAz/dy - dAy/dz, dAx/dz - dAz/dx, dAy/dx - dAx/dy)
+    bx = gaz[1] - gay[2]
+    by = gax[2] - gaz[0]
+    bz = gay[0] - gax[1]
+    del gax, gay, gaz
+    bmax = np.sqrt(bx * bx + by * by + bz * bz).max()
+    bx /= bmax
+    by /= bmax
+    bz /= bmax
+    c = rng.uniform(0.0, 1.0, size=3)
+    x = (np.arange(n) + 0.5) / n
+    dxs = [np.minimum(np.abs(x - c[d]), 1.0 - np.abs(x - c[d])) for d in range(3)]
+    r2 = dxs[2][:, None, None] ** 2 + dxs[1][None, :, None] ** 2 + dxs[0][None, None, :] ** 2
+    p = np.where(r2 < 0.01, 100.0, 1.0)
+    rho = 1.0 + 0.2 * frho
+    z = np.zeros_like(rho)
+    U = ideal_cons([rho, vx, vy, vz, p, bx, by, bz, z], gamma)
+    del rho, vx, vy, vz, p, bx, by, bz, z, frho
+    return pad_periodic(U, 3)
+
+
+def mhd_lowbeta_3d(n=256, seed=0, gamma=5.0 / 3.0, kmax=8, beta=0.01, mach=10.0):
+    """Low-beta, high-Mach variant: rho = 1 + 0.2 f, p = 1, uniform
+    B0 = sqrt(2 p / beta) along a seeded unit direction, and a seeded velocity
+    field scaled to an rms Mach number `mach` (v_rms = mach sqrt(gamma p/rho0))."""
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + 0.2 * _field_3d(rng, n, kmax)
+    v = [_field_3d(rng, n, kmax) for _ in range(3)]
+    vrms = np.sqrt(np.mean(v[0] ** 2 + v[1] ** 2 + v[2] ** 2))
+    scale = mach * np.sqrt(gamma * 1.0 / 1.0) / vrms
+    v = [c * scale for c in v]
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    b0 = np.sqrt(2.0 / beta)
+    p = np.ones_like(rho)
+    z = np.zeros_like(rho)
+    U = ideal_cons([rho, v[0], v[1], v[2], p, z + b0 * d[0], z + b0 * d[1], z + b0 * d[2], z],
+                   gamma)
+    return pad_periodic(U, 3)
