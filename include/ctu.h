@@ -1,0 +1,168 @@
+/*
+ * ctu.h -- C ABI of the GB300 CTU-MHD patch integrator (libctu.so).
+ *
+ * The library advances batches of ghost-filled patches of an ideal-MHD
+ * (GLM-cleaned) state by one dimensionally unsplit Corner Transport Upwind
+ * step, following Mignone et al., "The PLUTO code for adaptive mesh
+ * computations in astrophysical fluid dynamics" (ApJS 198, 7, 2012):
+ *   - equations: Section 2.1, Eq. (1)-(2) (ideal MHD, ideal gas) and
+ *     Section 3, Eq. (glm2x2) (GLM divergence cleaning, psi source split);
+ *   - time step: Section 3.1, Eq. (Ca);
+ *   - step:      Section 3.1, Eq. (update), (incrementop_hyp), (ctu_flux),
+ *                (transv) with Pi = 0; Section 3.2 (characteristic
+ *                normal predictor, PPM / MC-linear reconstruction);
+ *   - flux registers: Section 4.2, Eq. (fluxcorr).
+ *
+ * Data layout (all arrays are caller-owned device memory unless stated):
+ *   A "pool" holds 9 conservative variables in structure-of-arrays form,
+ *   U[q * stride + cell], q = 0..8 = (rho, m_x, m_y, m_z, E, B_x, B_y, B_z,
+ *   psi), float64.  A patch occupies cells base .. base + NX*NY*NZ - 1 of the
+ *   pool, x fastest: cell = base + (k * NY + j) * NX + i, with
+ *   N_d = n_d + 2 * 4 for active dimensions (d < ndim) and N_d = n_d = 1 for
+ *   inactive ones.  Ghost cells must be filled by the caller before a call.
+ *   stride >= base + NX*NY*NZ for every patch; patches must not overlap.
+ *
+ * Streams: every call that takes `stream` (a cudaStream_t passed as void*)
+ * only enqueues work on it, except where "synchronises" is stated.
+ *
+ * Errors: host-side validation errors are returned at once.  Device-side
+ * conditions (a state with rho <= 0 or p <= 0, a NaN) set sticky bits in a
+ * device status word that ctu_status_sync() returns and clears.  The library
+ * never traps, asserts or exits.
+ */
+#ifndef CTU_H
+#define CTU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CTU_OK = 0,
+    CTU_EINVAL = 1,        /* bad argument (null pointer, size, config value) */
+    CTU_ENOMEM = 2,        /* device or pinned-host allocation failed */
+    CTU_ECUDA = 3,         /* a CUDA runtime call failed */
+    CTU_EUNSUPPORTED = 4,  /* valid but not implemented combination */
+    CTU_ENEGATIVE = 5,     /* device: a state with rho <= 0 or p <= 0 was met */
+    CTU_ENAN = 6,          /* device: a NaN/Inf was met */
+    CTU_ERECOVERY = 7,     /* device: primitive recovery did not converge */
+    CTU_ESUPERLUMINAL = 8, /* device: |v| >= 1 in relativistic MHD */
+    CTU_ETIMEOUT = 9       /* device: a bounded wait gave up */
+} ctu_status;
+
+enum { CTU_MHD = 0, CTU_SRMHD = 1 };
+enum { CTU_EOS_IDEAL = 0, CTU_EOS_TM = 1 };
+enum { CTU_LINEAR_MC = 0, CTU_PPM = 1 };
+enum { CTU_CHAR_TRACE = 0, CTU_MUSCL_HANCOCK = 1 };
+enum { CTU_HLLD = 0, CTU_HLL = 1 };
+enum { CTU_FP64 = 0, CTU_MIXED = 1 };
+/* trace_mode: Section 3.2 normal predictor with w_ref = w_(+/-).
+ *   CTU_TRACE_ALL    every characteristic field is traced to both
+ *                    interfaces (no reference state); second order for
+ *                    smooth flows with HLLD, the default.
+ *   CTU_TRACE_UPWIND the literal upwind selection beta_+ = [nu > 0],
+ *                    beta_- = [nu < 0]. */
+enum { CTU_TRACE_ALL = 0, CTU_TRACE_UPWIND = 1 };
+
+typedef struct {
+    int physics;      /* CTU_MHD (CTU_SRMHD: CTU_EUNSUPPORTED in this build) */
+    int eos;          /* CTU_EOS_IDEAL */
+    double gamma;     /* ratio of specific heats, > 1 */
+    int ndim;         /* 1, 2 or 3 active dimensions; v_z, B_z always carried */
+    int recon;        /* CTU_LINEAR_MC or CTU_PPM (Section 3.2) */
+    int predictor;    /* CTU_CHAR_TRACE */
+    int riemann;      /* CTU_HLLD */
+    int precision;    /* CTU_FP64: all arithmetic in float64.  CTU_MIXED:
+                         tracing, projections and Riemann fluxes in float32;
+                         pressure recovery, interface conservative states and
+                         the update accumulation in float64. */
+    double cfl;       /* C_a of Eq. (Ca): <= 1 in 2D, <= 1/2 in 3D */
+    double glm_alpha; /* c_h^2/c_p^2 = glm_alpha * c_h / min(dx): psi decays by
+                         exp(-glm_alpha c_h dt / min dx) per step */
+    int nghost;       /* must be 4 */
+    int trace_mode;   /* CTU_TRACE_ALL or CTU_TRACE_UPWIND */
+} ctu_config;
+
+typedef struct {
+    int32_t n[3];     /* interior cells per dimension (1 for inactive ones) */
+    double dx[3];     /* cell widths; face areas and volumes are Cartesian */
+    int64_t base;     /* pool offset of the first (ghost) cell */
+    int32_t level;    /* AMR level, informational */
+    int32_t flags;    /* reserved, 0 */
+} ctu_patch;
+
+/* A flux-register window, Eq. (fluxcorr): faces normal to `dir` on plane
+ * `plane` of patch `patch` (0 <= plane <= n_dir; plane p separates interior
+ * cells p-1 and p), transverse ranges a in [a0, a1), b in [b0, b1) where
+ * (a, b) are the two other dimensions in increasing order.  During every
+ * ctu_step that advances this patch, for each such face and variable q:
+ *   reg[dst + (q * nb + (b - b0)) * na + (a - a0)] += weight * dt * A * F_q
+ * with na = a1 - a0, nb = b1 - b0, A the face area (product of the two
+ * transverse cell widths) and F the time-centred flux through the face in
+ * the +dir direction. */
+typedef struct {
+    int32_t patch;    /* index into the ctu_patch array of the ctu_step call */
+    int32_t dir;      /* 0, 1, 2 */
+    int32_t plane;
+    int32_t a0, a1, b0, b1;
+    int32_t pad;
+    double weight;
+    int64_t dst;      /* offset in doubles into the bound register array */
+} ctu_flux_window;
+
+typedef struct ctu_ctx ctu_ctx;
+
+/* Validate `cfg`, create a context on the current CUDA device.  *out is
+ * library-owned; release it with ctu_destroy. */
+ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out);
+
+/* CFL time step, Eq. (Ca): M = max over the interior cells of all patches of
+ * max_d (|v_d| + c_f,d) / dx_d; then dt = cfl / M and c_h = M * min dx (the
+ * GLM speed, equal to cfl * min dx / dt).  Writes {dt, c_h} to the device
+ * array d_dt_ch[2]; if h_dt_ch is non-null it also copies them there and
+ * synchronises the stream.  U: device pool; patches: host array. */
+ctu_status ctu_dt(ctu_ctx *ctx, const double *U, int64_t stride,
+                  const ctu_patch *patches, int npatch,
+                  double *d_dt_ch, double *h_dt_ch, void *stream);
+
+/* One CTU step of every patch: interior cells of U_out receive U_in advanced
+ * by dt, with {dt, c_h} read from the device array d_dt_ch[2].  Ghost cells
+ * of U_out are not written.  U_in and U_out must not alias.  Bound flux
+ * windows whose patch index is < npatch accumulate into the bound register
+ * array.  The first call with a new patch list uploads the list and may
+ * allocate scratch; make that call before any stream capture. */
+ctu_status ctu_step(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t stride,
+                    const ctu_patch *patches, int npatch, const double *d_dt_ch,
+                    void *stream);
+
+/* Bind (or, with reg == NULL or nwin == 0, unbind) flux-register windows.
+ * `win` is a host array copied at call time; `reg` is a device float64 array
+ * the caller owns and zeroes.  Windows must not overlap in reg. */
+ctu_status ctu_flux_registers(ctu_ctx *ctx, double *reg, const ctu_flux_window *win,
+                              int nwin);
+
+/* Fill the ghost cells of every patch with periodic copies of its own
+ * interior (helper for periodic boxes; not part of the step). */
+ctu_status ctu_fill_periodic(ctu_ctx *ctx, double *U, int64_t stride,
+                             const ctu_patch *patches, int npatch, void *stream);
+
+/* Synchronise the stream and return (and clear) the sticky device status:
+ * CTU_OK or the first device error met since the last call. */
+ctu_status ctu_status_sync(ctu_ctx *ctx, void *stream);
+
+/* Static description of a status code. */
+const char *ctu_strerror(ctu_status s);
+
+/* Release a context (synchronises the device). */
+void ctu_destroy(ctu_ctx *ctx);
+
+/* Number of kernel launches the last ctu_step enqueued (for accounting). */
+int ctu_last_launch_count(const ctu_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTU_H */

@@ -1,0 +1,64 @@
+"""Build libctu.so for sm_103a with nvcc (translation units in parallel)."""
+from __future__ import annotations
+
+import os
+import subprocess
+from pathlib import Path
+
+PKG = Path(__file__).resolve().parent
+ROOT = PKG.parent
+CSRC = PKG / "csrc"
+OUT_DIR = PKG / "_lib"
+LIB = OUT_DIR / "libctu.so"
+SOURCES = ["ctu_api.cu", "ctu_f64.cu", "ctu_f32.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def flags(extra=()):
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                   "-I", str(ROOT / "include"), "-I", str(CSRC)] + list(extra)
+
+
+def build(force: bool = False, verbose: bool = False, extra=()) -> Path:
+    OUT_DIR.mkdir(exist_ok=True)
+    deps = [CSRC / s for s in SOURCES] + list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) \
+        + list((ROOT / "include").glob("*.h"))
+    if LIB.exists() and not force and not extra:
+        if LIB.stat().st_mtime >= max(p.stat().st_mtime for p in deps):
+            return LIB
+    objs = []
+    procs = []
+    for s in SOURCES:
+        o = OUT_DIR / (Path(s).stem + ".o")
+        cmd = [nvcc(), "-c", str(CSRC / s), "-o", str(o)] + flags(extra)
+        if verbose:
+            cmd += ["-Xptxas", "-v"]
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        objs.append(o)
+    failed = []
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        if verbose or p.returncode:
+            print(out.decode(errors="replace"))
+        if p.returncode:
+            failed.append(" ".join(cmd))
+    if failed:
+        raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
+    tmp = OUT_DIR / f"libctu.{os.getpid()}.so"
+    subprocess.run([nvcc(), "-shared", "-o", str(tmp)] + [str(o) for o in objs] + ARCH + ["-lcudart"],
+                   check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    import sys
+    build(force=True, verbose="-v" in sys.argv)
+    print(LIB)

@@ -1,0 +1,26 @@
+// ctu_launch.h -- host-side launchers of the CTU kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ctu_kernels.cuh"
+
+namespace ctu {
+
+// Scratch elements of type R needed per unit of scratch stride.
+constexpr int SCRATCH_ARRAYS = 9 /*V*/ + 27 /*F1*/ + 18 /*Vp,Vm*/ + 27 /*F*/;
+
+struct LaunchInfo {
+    long long max_cells;   // largest ghosted patch
+    int recon;             // 0 linear, 1 PPM
+    const DevWindow *win;  // device windows (may be null)
+    int nwin;
+    double *reg;
+    void *scratch;         // SCRATCH_ARRAYS * sstride elements of R
+};
+
+template <class R> int launch_step(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
+template <class R> int launch_maxspeed(const StepArgs &a, long long max_cells, unsigned long long *out,
+                                       cudaStream_t s);
+
+} // namespace ctu

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libctu.so (the C ABI in include/ctu.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device arrays are passed as torch CUDA tensors (or raw
+integer device addresses); torch provides device memory and streams.  If the
+library is missing this module raises at load time -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+from . import _build
+
+# ---------------------------------------------------------------- ABI structs
+
+CTU_MHD, CTU_SRMHD = 0, 1
+CTU_EOS_IDEAL, CTU_EOS_TM = 0, 1
+CTU_LINEAR_MC, CTU_PPM = 0, 1
+CTU_CHAR_TRACE, CTU_MUSCL_HANCOCK = 0, 1
+CTU_HLLD, CTU_HLL = 0, 1
+CTU_FP64, CTU_MIXED = 0, 1
+CTU_TRACE_ALL, CTU_TRACE_UPWIND = 0, 1
+
+STATUS = ["CTU_OK", "CTU_EINVAL", "CTU_ENOMEM", "CTU_ECUDA", "CTU_EUNSUPPORTED", "CTU_ENEGATIVE",
+          "CTU_ENAN", "CTU_ERECOVERY", "CTU_ESUPERLUMINAL", "CTU_ETIMEOUT"]
+
+
+class ctu_config(ctypes.Structure):
+    _fields_ = [("physics", ctypes.c_int), ("eos", ctypes.c_int), ("gamma", ctypes.c_double),
+                ("ndim", ctypes.c_int), ("recon", ctypes.c_int), ("predictor", ctypes.c_int),
+                ("riemann", ctypes.c_int), ("precision", ctypes.c_int), ("cfl", ctypes.c_double),
+                ("glm_alpha", ctypes.c_double), ("nghost", ctypes.c_int),
+                ("trace_mode", ctypes.c_int)]
+
+
+class ctu_patch(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("dx", ctypes.c_double * 3), ("base", ctypes.c_int64),
+                ("level", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class ctu_flux_window(ctypes.Structure):
+    _fields_ = [("patch", ctypes.c_int32), ("dir", ctypes.c_int32), ("plane", ctypes.c_int32),
+                ("a0", ctypes.c_int32), ("a1", ctypes.c_int32), ("b0", ctypes.c_int32),
+                ("b1", ctypes.c_int32), ("pad", ctypes.c_int32), ("weight", ctypes.c_double),
+                ("dst", ctypes.c_int64)]
+
+
+class CtuError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        name = STATUS[code] if 0 <= code < len(STATUS) else str(code)
+        super().__init__(f"{where}: {name} ({_lib().ctu_strerror(code).decode()})")
+
+
+_L = None
+
+
+def lib_path() -> Path:
+    return _build.LIB
+
+
+def _lib():
+    global _L
+    if _L is None:
+        p = _build.LIB
+        if not p.exists():
+            raise RuntimeError(f"libctu.so not built at {p}: run __graft_entry__.build()")
+        L = ctypes.CDLL(str(p))
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        L.ctu_init.argtypes = [ctypes.POINTER(ctu_config), ctypes.POINTER(vp)]
+        L.ctu_dt.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp, vp, vp]
+        L.ctu_step.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp, vp]
+        L.ctu_flux_registers.argtypes = [vp, vp, ctypes.POINTER(ctu_flux_window), i32]
+        L.ctu_fill_periodic.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp]
+        L.ctu_status_sync.argtypes = [vp, vp]
+        L.ctu_destroy.argtypes = [vp]
+        L.ctu_destroy.restype = None
+        L.ctu_strerror.argtypes = [i32]
+        L.ctu_strerror.restype = ctypes.c_char_p
+        L.ctu_last_launch_count.argtypes = [vp]
+        for f in ("ctu_init", "ctu_dt", "ctu_step", "ctu_flux_registers", "ctu_fill_periodic",
+                  "ctu_status_sync", "ctu_last_launch_count"):
+            getattr(L, f).restype = i32
+        _L = L
+    return _L
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _check(code, where):
+    if code != 0:
+        raise CtuError(code, where)
+
+
+def make_config(ndim=3, gamma=5.0 / 3.0, recon=CTU_PPM, precision=CTU_FP64, cfl=0.3,
+                glm_alpha=0.1, trace_mode=CTU_TRACE_ALL, physics=CTU_MHD, riemann=CTU_HLLD,
+                predictor=CTU_CHAR_TRACE, eos=CTU_EOS_IDEAL):
+    return ctu_config(physics=physics, eos=eos, gamma=gamma, ndim=ndim, recon=recon,
+                      predictor=predictor, riemann=riemann, precision=precision, cfl=cfl,
+                      glm_alpha=glm_alpha, nghost=4, trace_mode=trace_mode)
+
+
+def make_patches(specs):
+    """specs: iterable of (n(3), dx(3), base[, level])."""
+    specs = list(specs)
+    arr = (ctu_patch * len(specs))()
+    for i, s in enumerate(specs):
+        n, dx, base = s[0], s[1], s[2]
+        arr[i].n[:] = [int(v) for v in n]
+        arr[i].dx[:] = [float(v) for v in dx]
+        arr[i].base = int(base)
+        arr[i].level = int(s[3]) if len(s) > 3 else 0
+        arr[i].flags = 0
+    return arr
+
+
+# ---------------------------------------------------------------- C-ABI mirrors
+
+def ctu_init(cfg: ctu_config):
+    h = ctypes.c_void_p()
+    _check(_lib().ctu_init(ctypes.byref(cfg), ctypes.byref(h)), "ctu_init")
+    return h
+
+
+def ctu_destroy(ctx):
+    _lib().ctu_destroy(ctx)
+
+
+def ctu_dt(ctx, U, stride, patches, d_dt_ch, h_dt_ch=None, stream=None):
+    _check(_lib().ctu_dt(ctx, _ptr(U), int(stride), patches, len(patches), _ptr(d_dt_ch),
+                         h_dt_ch, _stream(stream)), "ctu_dt")
+
+
+def ctu_step(ctx, U_in, U_out, stride, patches, d_dt_ch, stream=None):
+    _check(_lib().ctu_step(ctx, _ptr(U_in), _ptr(U_out), int(stride), patches, len(patches),
+                           _ptr(d_dt_ch), _stream(stream)), "ctu_step")
+
+
+def ctu_flux_registers(ctx, reg, windows):
+    if reg is None or not windows:
+        _check(_lib().ctu_flux_registers(ctx, None, None, 0), "ctu_flux_registers")
+        return
+    arr = (ctu_flux_window * len(windows))()
+    for i, w in enumerate(windows):
+        (arr[i].patch, arr[i].dir, arr[i].plane, arr[i].a0, arr[i].a1, arr[i].b0, arr[i].b1) = \
+            [int(v) for v in w[:7]]
+        arr[i].weight = float(w[7])
+        arr[i].dst = int(w[8])
+    _check(_lib().ctu_flux_registers(ctx, _ptr(reg), arr, len(windows)), "ctu_flux_registers")
+
+
+def ctu_fill_periodic(ctx, U, stride, patches, stream=None):
+    _check(_lib().ctu_fill_periodic(ctx, _ptr(U), int(stride), patches, len(patches),
+                                    _stream(stream)), "ctu_fill_periodic")
+
+
+def ctu_status_sync(ctx, stream=None):
+    return _lib().ctu_status_sync(ctx, _stream(stream))
+
+
+def ctu_last_launch_count(ctx):
+    return _lib().ctu_last_launch_count(ctx)
+
+
+def ctu_strerror(code):
+    return _lib().ctu_strerror(code).decode()
+
+
+class Ctx:
+    """Owning wrapper of a ctu_ctx with the same calls as methods."""
+
+    def __init__(self, cfg: ctu_config):
+        self.cfg = cfg
+        self.h = ctu_init(cfg)
+
+    def close(self):
+        if self.h:
+            ctu_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dt(self, U, stride, patches, d_dt_ch, h_dt_ch=None, stream=None):
+        ctu_dt(self.h, U, stride, patches, d_dt_ch, h_dt_ch, stream)
+
+    def step(self, U_in, U_out, stride, patches, d_dt_ch, stream=None):
+        ctu_step(self.h, U_in, U_out, stride, patches, d_dt_ch, stream)
+
+    def flux_registers(self, reg, windows):
+        ctu_flux_registers(self.h, reg, windows)
+
+    def fill_periodic(self, U, stride, patches, stream=None):
+        ctu_fill_periodic(self.h, U, stride, patches, stream)
+
+    def status_sync(self, stream=None):
+        return ctu_status_sync(self.h, stream)
+
+    def launches(self):
+        return ctu_last_launch_count(self.h)
