@@ -1,0 +1,405 @@
+"""Benchmark of the CTU-MHD step on GB300: cell-updates/s, roofline, oracle baseline.
+
+One "step" is the whole hot path over one batch: ctu_dt (the CFL reduction
+of Eq. Ca) followed by ctu_step (prim, first-order transverse fluxes,
+characteristic tracing, HLLD, update, psi damping, flux registers bound on
+the patch's six boundary faces).  Workload: one periodic 256^3 ideal-MHD
+patch (+4 ghost layers, 1.32 GB of float64 state) with a seeded Fourier
+spectrum (|k| <= 8) in rho, v and B (vector potential) plus a radius-0.1
+sphere at 100x pressure; PPM + characteristic tracing, HLLD, GLM, CFL 0.3.
+The state (1.3 GB in, 1.2 GB out) is far larger than L2, so no flush is
+needed between timed steps.
+
+The headline `value` is the mixed-precision path (float32 tracing and
+Riemann fluxes, float64 pressure recovery / interface states / update); the
+FP64 path is measured in the same run and reported under `fp64_path`.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS = 256
+WORKLOAD = ("3D ideal MHD 256^3 periodic patch, seeded |k|<=8 spectrum in rho/v/B + "
+            "100x pressure sphere (r=0.1); PPM + characteristic tracing, HLLD, GLM, CFL 0.3")
+METRIC = "MHD cell-updates/s per CTU step"
+# Per-SM unit counts x max SM clock (2070 MHz) x 152 SMs, 2 flops per FMA.
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP32_LANES = 128
+FP64_PEAK_NOMINAL = 1.25e12  # GB300 FP64 (non-tensor and tensor) nominal
+BYTES_PER_CELL_F64_IO = None  # computed per patch: 9 vars x 8 B x (ghosted + interior)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def algorithmic_bytes(n):
+    """Bytes the step must move per launch: read the ghosted state once and
+    write the interior once (9 float64 variables), plus the flux registers
+    (6 faces x n^2 x 9 float64, read-modify-write)."""
+    ghosted = (n + 8) ** 3
+    interior = n ** 3
+    regs = 6 * n * n * 9 * 8 * 2
+    return 9 * 8 * (ghosted + interior) + regs
+
+
+class Clocks:
+    """nvidia-smi sampler over the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons, pw = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                smax = float(c[2])
+                pw.append(float(c[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        busy = [s for s, w in zip(sm, pw) if w > 200.0] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(pw) if pw else None}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+
+def oracle_sample(U0, n_full, sub, steps=1, seed=0):
+    """Time the CPU oracle on a bounded sample of the workload: a sub x sub x
+    sub block of the 256^3 state (with its true neighbours as ghosts), one CTU
+    step per repetition.  Returns (cell-updates/s, seconds, sample text)."""
+    import numpy as np
+    import oracle as O
+    g = 4
+    lo = (n_full - sub) // 2
+    blk = U0[:, lo:lo + sub + 2 * g, lo:lo + sub + 2 * g, lo:lo + sub + 2 * g].copy()
+    n = [sub] * 3
+    dx = [1.0 / n_full] * 3
+    m = O.mhd_max_speed(blk, n, 3, dx)
+    dt, ch = O.dt_ch(m, dx, 3, 0.3)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        out, bad = O.mhd_step(blk, n, 3, dx, dt, ch, recon=1)
+    el = time.perf_counter() - t0
+    cells = sub ** 3 * steps
+    return cells / el, el, f"{sub}^3 interior block of the 256^3 state, {steps} CTU step(s), 1 thread"
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle timed on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1110_0740_gb300 import workloads as W
+    U0 = W.mhd_blast_3d(N_CELLS, seed=0)
+    vals = []
+    sub = 32
+    for _ in range(max(1, args.warmup)):
+        oracle_sample(U0, N_CELLS, sub)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, el, txt = oracle_sample(U0, N_CELLS, sub)
+        vals.append(v)
+    total = time.perf_counter() - t0
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": txt},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1,
+                             "kind": "oracle", "sample": txt},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1110_0740_gb300 import ctu, workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    n = args.n
+    U0 = W.mhd_blast_3d(n, seed=rank)
+    Uh = torch.from_numpy(U0.reshape(9, -1))
+    stride = Uh.shape[1]
+    U = Uh.to(dev)
+    Uo = torch.empty_like(U)
+    dx = [1.0 / n] * 3
+    patches = ctu.make_patches([([n] * 3, dx, 0)])
+    # flux registers on the 6 boundary faces of the patch
+    windows, off = [], 0
+    for d in range(3):
+        for plane in (0, n):
+            windows.append((0, d, plane, 0, n, 0, n, 1.0, off))
+            off += 9 * n * n
+    reg = torch.zeros(off, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def make(prec):
+        c = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3))
+        c.flux_registers(reg, windows)
+        return c
+
+    dtch = torch.zeros(2, dtype=torch.float64, device=dev)
+
+    def step(c):
+        c.dt(U, stride, patches, dtch)
+        c.step(U, Uo, stride, patches, dtch)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def timed(c, K, W_, prof=False):
+        for _ in range(W_):
+            step(c)
+        if prof:
+            c.profile(True)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            step(c)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        kern = c.profile_read() if prof else {}
+        if prof:
+            c.profile(False)
+        if pg is not None:
+            t = torch.tensor([ms], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, kern
+
+    primary = ctu.CTU_MIXED if args.precision == "mixed" else ctu.CTU_FP64
+    other = ctu.CTU_FP64 if primary == ctu.CTU_MIXED else ctu.CTU_MIXED
+    cells = n ** 3
+    results = {}
+    clocks = Clocks(local)
+    for prec in (primary, other):
+        if prec == other and args.skip_other:
+            continue
+        c = make(prec)
+        K = args.steps if prec == primary else max(2, min(args.steps, args.other_steps))
+        Wn = args.warmup if prec == primary else 1
+        if prec == primary:
+            clocks.start()
+        ms, kern = timed(c, K, Wn, prof=False)
+        if prec == primary:
+            clk = clocks.stop()
+            st = c.status_sync()
+            launches_per_step = c.launches() + 2  # ctu_step launches + maxspeed + dt finalize
+            # kernel durations over a second, profiled pass of the same region
+            _, kern = timed(c, K, 0, prof=True)
+        else:
+            st = c.status_sync()
+            _, kern = timed(c, K, 0, prof=True)
+        results[prec] = {"ms_total": ms, "K": K, "kern": kern, "status": st}
+        c.close()
+
+    res = results[primary]
+    ms_step = res["ms_total"] / res["K"]
+    value = world * cells / (ms_step * 1e-3)
+
+    # roofline of the dominant kernel
+    peaks, src = measured_peaks()
+    kern = res["kern"]
+    top = max(kern.items(), key=lambda kv: kv[1][0]) if kern else ("?", (0.0, 1))
+    top_name, (top_ms, top_cnt) = top
+    top_avg = top_ms / max(1, top_cnt)
+    step_kernel_ms = sum(v[0] for v in kern.values()) / res["K"]
+    nbytes = algorithmic_bytes(n)
+    hbm_achieved = nbytes / (step_kernel_ms * 1e-3) / 1e9
+    sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ
+    fp64_peak = FP64_PEAK_NOMINAL
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6
+    flops = load_flop_counts()
+    key = "mixed" if primary == ctu.CTU_MIXED else "fp64"
+    roof = None
+    if flops and top_name in flops.get(key, {}):
+        fc = flops[key][top_name]
+        # cells processed per launch of this kernel = interior cells (per direction)
+        f32 = fc.get("f32", 0.0) * cells
+        f64 = fc.get("f64", 0.0) * cells
+        t = top_avg * 1e-3
+        frac32 = (f32 / t) / fp32_peak
+        frac64 = (f64 / t) / fp64_peak
+        if frac64 >= frac32:
+            roof = {"bound": "alu", "achieved": f64 / t / 1e12, "peak": fp64_peak / 1e12,
+                    "unit": "TFLOP/s", "frac": frac64, "traffic": None,
+                    "kernel": top_name, "pipe": "fp64", "fp32_frac": frac32,
+                    "peak_source": "derived: nominal GB300 FP64 1.25 TFLOP/s"}
+        else:
+            roof = {"bound": "alu", "achieved": f32 / t / 1e12, "peak": fp32_peak / 1e12,
+                    "unit": "TFLOP/s", "frac": frac32, "traffic": None,
+                    "kernel": top_name, "pipe": "fp32", "fp64_frac": frac64,
+                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
+    if roof is None:
+        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "whole step",
+                "peak_source": f"{src} hbm_gbs"}
+    roof["kernel_avg_ms"] = top_avg
+    roof["kernels_ms_per_step"] = {k: v[0] / res["K"] for k, v in kern.items()}
+    roof["hbm_step"] = {"algorithmic_bytes": nbytes, "achieved_gbs": hbm_achieved,
+                        "frac_of_measured": hbm_achieved / peaks["hbm_gbs"]}
+
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if not args.skip_e2e:
+        c = make(primary)
+        Uh_pin = Uh.pin_memory()
+        Uout_pin = torch.empty_like(Uh_pin).pin_memory()
+        E = max(1, min(args.steps, 3))
+        for it in range(E + 1):
+            if it == 1:
+                barrier()
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record(stream)
+            U.copy_(Uh_pin, non_blocking=True)
+            step(c)
+            Uout_pin.copy_(Uo, non_blocking=True)
+        t1.record(stream)
+        barrier()
+        ems = t0.elapsed_time(t1) / E
+        c.close()
+        e2e = {"value": world * cells / (ems * 1e-3), "unit": "cell-updates/s",
+               "h2d_bytes_per_step": int(U.numel() * 8), "d2h_bytes_per_step": int(Uo.numel() * 8),
+               "ms_per_step": ems}
+
+    fp64_path = None
+    if other in results:
+        r2 = results[other]
+        ms2 = r2["ms_total"] / r2["K"]
+        fp64_path = {"precision": "fp64" if other == ctu.CTU_FP64 else "mixed",
+                     "value": world * cells / (ms2 * 1e-3), "ms_per_step": ms2, "steps": r2["K"],
+                     "kernels_ms_per_step": {k: v[0] / r2["K"] for k, v in r2["kern"].items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        v, el, txt = oracle_sample(U0, n, 32)
+        cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": txt,
+               "seconds": el}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+                "steps": res["K"], "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if primary == ctu.CTU_MIXED else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "cells_per_gpu": cells, "patches_per_gpu": 1,
+                           "precision": args.precision, "l2_flush": "inputs (1.3 GB) > L2",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path,
+                "gpu_launches": launches_per_step * res["K"], "clocks": clk,
+                "status": ctu.STATUS[res["status"]] if 0 <= res["status"] < 10 else res["status"],
+                "gpu": torch.cuda.get_device_name(dev)}
+        print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def load_flop_counts():
+    p = os.path.join(ROOT, "profiles", "flops_per_cell.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=N_CELLS)
+    ap.add_argument("--other-steps", type=int, default=3)
+    ap.add_argument("--skip-other", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

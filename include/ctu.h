@@ -57,7 +57,18 @@ enum { CTU_EOS_IDEAL = 0, CTU_EOS_TM = 1 };
 enum { CTU_LINEAR_MC = 0, CTU_PPM = 1 };
 enum { CTU_CHAR_TRACE = 0, CTU_MUSCL_HANCOCK = 1 };
 enum { CTU_HLLD = 0, CTU_HLL = 1 };
-enum { CTU_FP64 = 0, CTU_MIXED = 1 };
+/* precision:
+ *   CTU_FP64          all arithmetic in float64.
+ *   CTU_MIXED         tracing, characteristic projections, Riemann fluxes and
+ *                     flux differences in float32; cell-centre pressure
+ *                     recovery from the float64 state and the update
+ *                     accumulation in float64; the n+1/2 interface pressure
+ *                     is recovered in an exact increment form that has no
+ *                     catastrophic cancellation and so runs in float32.
+ *   CTU_MIXED_IFACE64 as CTU_MIXED, but the interface states are formed as
+ *                     float64 conservative states and their pressure is
+ *                     recovered in float64. */
+enum { CTU_FP64 = 0, CTU_MIXED = 1, CTU_MIXED_IFACE64 = 2 };
 /* trace_mode: Section 3.2 normal predictor with w_ref = w_(+/-).
  *   CTU_TRACE_ALL    every characteristic field is traced to both
  *                    interfaces (no reference state); second order for
@@ -74,10 +85,7 @@ typedef struct {
     int recon;        /* CTU_LINEAR_MC or CTU_PPM (Section 3.2) */
     int predictor;    /* CTU_CHAR_TRACE */
     int riemann;      /* CTU_HLLD */
-    int precision;    /* CTU_FP64: all arithmetic in float64.  CTU_MIXED:
-                         tracing, projections and Riemann fluxes in float32;
-                         pressure recovery, interface conservative states and
-                         the update accumulation in float64. */
+    int precision;    /* CTU_FP64, CTU_MIXED or CTU_MIXED_IFACE64 (above) */
     double cfl;       /* C_a of Eq. (Ca): <= 1 in 2D, <= 1/2 in 3D */
     double glm_alpha; /* c_h^2/c_p^2 = glm_alpha * c_h / min(dx): psi decays by
                          exp(-glm_alpha c_h dt / min dx) per step */
@@ -160,6 +168,18 @@ void ctu_destroy(ctu_ctx *ctx);
 
 /* Number of kernel launches the last ctu_step enqueued (for accounting). */
 int ctu_last_launch_count(const ctu_ctx *ctx);
+
+/* Per-kernel timing (measurement aid, not part of the method).  With
+ * enable != 0 every kernel the context launches is bracketed by two CUDA
+ * events recorded on its stream; totals restart at zero.  enable == 0 turns
+ * it off.  Synchronises the device. */
+ctu_status ctu_profile(ctu_ctx *ctx, int enable);
+
+/* Synchronises the device, folds the recorded event pairs into per-kernel
+ * totals and returns the number of distinct kernel names; if 0 <= i < that
+ * number, writes the i-th name (library-owned string), its total device
+ * time in ms and its launch count.  Returns 0 when profiling is off. */
+int ctu_profile_read(ctu_ctx *ctx, int i, const char **name, double *total_ms, long long *launches);
 
 #ifdef __cplusplus
 }

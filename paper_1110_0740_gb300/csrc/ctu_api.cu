@@ -8,13 +8,78 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "ctu.h"
 #include "ctu_launch.h"
 
 using namespace ctu;
+
+// Per-kernel CUDA-event timing: an event is recorded on the launching stream
+// right before and right after every kernel; totals are resolved on read.
+struct EventProf : ProfHook {
+    struct Rec { const char *name; cudaEvent_t a, b; };
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<Rec> pending;
+    const char *open = nullptr;
+    cudaEvent_t open_ev = nullptr;
+    std::vector<std::string> names;
+    std::map<std::string, std::pair<double, long>> tot;
+    cudaEvent_t take()
+    {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void mark(const char *name, cudaStream_t s) override
+    {
+        cudaEvent_t e = take();
+        if (!e) return;
+        cudaEventRecord(e, s);
+        if (name) {
+            open = name;
+            open_ev = e;
+        } else if (open) {
+            pending.push_back({open, open_ev, e});
+            open = nullptr;
+        }
+    }
+    void resolve()
+    {
+        for (const Rec &r : pending) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+                auto it = tot.find(r.name);
+                if (it == tot.end()) {
+                    names.push_back(r.name);
+                    tot[r.name] = {0.0, 0};
+                }
+                tot[r.name].first += ms;
+                tot[r.name].second += 1;
+            }
+        }
+        pending.clear();
+        used = 0;
+    }
+    void reset()
+    {
+        pending.clear();
+        used = 0;
+        names.clear();
+        tot.clear();
+    }
+    ~EventProf() override
+    {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
 
 struct ctu_ctx {
     ctu_config cfg;
@@ -38,6 +103,7 @@ struct ctu_ctx {
     int nwin = 0;
     double *reg = nullptr;
     int last_launches = 0;
+    EventProf *prof = nullptr;
 };
 
 static ctu_status cuda_fail(cudaError_t e)
@@ -113,7 +179,7 @@ static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStr
 
 static ctu_status ensure_scratch(ctu_ctx *ctx)
 {
-    const size_t elt = ctx->cfg.precision == CTU_MIXED ? sizeof(float) : sizeof(double);
+    const size_t elt = ctx->cfg.precision == CTU_FP64 ? sizeof(double) : sizeof(float);
     const size_t need = (size_t)SCRATCH_ARRAYS * (size_t)ctx->sstride * elt;
     if (need <= ctx->scratch_bytes) return CTU_OK;
     if (ctx->scratch) {
@@ -159,7 +225,8 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
     if (cfg->recon != CTU_LINEAR_MC && cfg->recon != CTU_PPM) return CTU_EINVAL;
     if (cfg->predictor != CTU_CHAR_TRACE) return CTU_EUNSUPPORTED;
     if (cfg->riemann != CTU_HLLD) return CTU_EUNSUPPORTED;
-    if (cfg->precision != CTU_FP64 && cfg->precision != CTU_MIXED) return CTU_EINVAL;
+    if (cfg->precision != CTU_FP64 && cfg->precision != CTU_MIXED && cfg->precision != CTU_MIXED_IFACE64)
+        return CTU_EINVAL;
     if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return CTU_EINVAL;
     if (!(cfg->glm_alpha >= 0.0)) return CTU_EINVAL;
     if (cfg->nghost != 4) return CTU_EINVAL;
@@ -187,6 +254,7 @@ void ctu_destroy(ctu_ctx *ctx)
     if (ctx->dstatus) cudaFree(ctx->dstatus);
     if (ctx->dmax) cudaFree(ctx->dmax);
     if (ctx->dwin) cudaFree(ctx->dwin);
+    delete ctx->prof;
     delete ctx;
 }
 
@@ -209,10 +277,10 @@ ctu_status ctu_dt(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patch
     if (st != CTU_OK) return st;
     CTU_CUDA(cudaMemsetAsync(ctx->dmax, 0, sizeof(unsigned long long), s));
     StepArgs a = make_args(ctx, U, nullptr, stride, npatch, nullptr);
-    if (ctx->cfg.precision == CTU_MIXED)
-        launch_maxspeed<float>(a, ctx->max_interior, ctx->dmax, s);
+    if (ctx->cfg.precision != CTU_FP64)
+        launch_maxspeed<float>(a, ctx->max_interior, ctx->dmax, s, ctx->prof);
     else
-        launch_maxspeed<double>(a, ctx->max_interior, ctx->dmax, s);
+        launch_maxspeed<double>(a, ctx->max_interior, ctx->dmax, s, ctx->prof);
     k_dt_finalize<<<1, 1, 0, s>>>(ctx->dmax, ctx->cfg.cfl, ctx->dxmin, d_dt_ch);
     CTU_CUDA(cudaGetLastError());
     if (h_dt_ch) {
@@ -241,7 +309,9 @@ ctu_status ctu_step(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t str
     li.nwin = ctx->reg ? ctx->nwin : 0;
     li.reg = ctx->reg;
     li.scratch = ctx->scratch;
-    if (ctx->cfg.precision == CTU_MIXED)
+    li.prof = ctx->prof;
+    li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
+    if (ctx->cfg.precision != CTU_FP64)
         ctx->last_launches = launch_step<float>(a, li, s);
     else
         ctx->last_launches = launch_step<double>(a, li, s);
@@ -349,5 +419,36 @@ const char *ctu_strerror(ctu_status s)
 }
 
 int ctu_last_launch_count(const ctu_ctx *ctx) { return ctx ? ctx->last_launches : -1; }
+
+ctu_status ctu_profile(ctu_ctx *ctx, int enable)
+{
+    if (!ctx) return CTU_EINVAL;
+    CTU_CUDA(cudaDeviceSynchronize());
+    if (!enable) {
+        delete ctx->prof;
+        ctx->prof = nullptr;
+        return CTU_OK;
+    }
+    if (!ctx->prof) ctx->prof = new (std::nothrow) EventProf();
+    if (!ctx->prof) return CTU_ENOMEM;
+    ctx->prof->reset();
+    return CTU_OK;
+}
+
+int ctu_profile_read(ctu_ctx *ctx, int i, const char **name, double *total_ms, long long *launches)
+{
+    if (!ctx || !ctx->prof) return 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return 0;
+    ctx->prof->resolve();
+    const int n = (int)ctx->prof->names.size();
+    if (i >= 0 && i < n) {
+        const std::string &k = ctx->prof->names[i];
+        const auto &v = ctx->prof->tot[k];
+        if (name) *name = k.c_str();
+        if (total_ms) *total_ms = v.first;
+        if (launches) *launches = v.second;
+    }
+    return n;
+}
 
 } // extern "C"

@@ -5,5 +5,6 @@
 
 namespace ctu {
 template int launch_step<float>(const StepArgs &, const LaunchInfo &, cudaStream_t);
-template int launch_maxspeed<float>(const StepArgs &, long long, unsigned long long *, cudaStream_t);
+template int launch_maxspeed<float>(const StepArgs &, long long, unsigned long long *, cudaStream_t,
+                                       ProfHook *);
 } // namespace ctu

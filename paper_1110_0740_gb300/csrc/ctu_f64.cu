@@ -3,5 +3,6 @@
 
 namespace ctu {
 template int launch_step<double>(const StepArgs &, const LaunchInfo &, cudaStream_t);
-template int launch_maxspeed<double>(const StepArgs &, long long, unsigned long long *, cudaStream_t);
+template int launch_maxspeed<double>(const StepArgs &, long long, unsigned long long *, cudaStream_t,
+                                       ProfHook *);
 } // namespace ctu

@@ -91,13 +91,14 @@ __device__ __forceinline__ bool prim_from_cons64(const double (&U)[NV], double g
     return rho > 0.0 && p > 0.0;
 }
 
+// igm = 1/(Gamma - 1)
 template <class R>
-__device__ __forceinline__ void cons64_from_prim(const R (&V)[NV], double gam, double (&U)[NV])
+__device__ __forceinline__ void cons64_from_prim(const R (&V)[NV], double igm, double (&U)[NV])
 {
     const double rho = V[0], vx = V[1], vy = V[2], vz = V[3], p = V[4];
     const double bx = V[5], by = V[6], bz = V[7];
     U[0] = rho; U[1] = rho * vx; U[2] = rho * vy; U[3] = rho * vz;
-    U[4] = p / (gam - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz) + 0.5 * (bx * bx + by * by + bz * bz);
+    U[4] = p * igm + 0.5 * rho * (vx * vx + vy * vy + vz * vz) + 0.5 * (bx * bx + by * by + bz * bz);
     U[5] = bx; U[6] = by; U[7] = bz; U[8] = V[8];
 }
 
@@ -163,9 +164,19 @@ __global__ void k_flux1(StepArgs a, int d, const R *Vs, R *F1)
 
 // Normal predictor along d plus the transverse correction (Eq. transv):
 // cells with c_d in [-1, n_d], other active coordinates in [0, n-1].
-// Writes the primitive n+1/2 interface states (pressure recovered in
-// float64) to Vp, Vm.
-template <class R, int PPM>
+// Writes the primitive n+1/2 interface states to Vp, Vm.
+//
+// IFACE64 = 1: U* = U(V*) and U^(n+1/2) = U* + dt/2 T formed in float64,
+//   pressure recovered from U^(n+1/2) in float64 (the FP64 path, and the
+//   mixed path's literal variant).
+// IFACE64 = 0 (mixed path): the same state in increment form.  With
+//   d = dt/2 T, rho = rho* + d_rho, m = rho* v* + d_m, B = B* + d_B,
+//     p = p* + (Gamma-1) [ d_E + (rho* v*^2 d_rho - 2 rho* v*.d_m - d_m^2)/(2 rho)
+//                          - d_B.(B* + d_B/2) ],
+//   which equals (Gamma-1)(E - m^2/2rho - B^2/2) exactly but never forms E, so
+//   no catastrophic cancellation occurs and float32 keeps the accuracy the
+//   float32 transverse fluxes allow.
+template <class R, int PPM, int IFACE64>
 __global__ void k_trace(StepArgs a, int d, const R *Vs, const R *F1x, const R *F1y, const R *F1z,
                         R *Vp, R *Vm)
 {
@@ -185,7 +196,11 @@ __global__ void k_trace(StepArgs a, int d, const R *Vs, const R *F1x, const R *F
     int t1 = -1, t2 = -1;
     for (int e = 0; e < a.ndim; ++e)
         if (e != d) { if (t1 < 0) t1 = e; else t2 = e; }
-    const R *F1[3] = {F1x, F1y, F1z};
+    const R *F1t1 = t1 == 0 ? F1x : (t1 == 1 ? F1y : F1z);
+    const R *F1t2 = t2 == 0 ? F1x : (t2 == 1 ? F1y : F1z);
+    const long long s1 = t1 >= 0 ? dstride(P, t1) : 0, s2 = t2 >= 0 ? dstride(P, t2) : 0;
+    const double ih1 = t1 >= 0 ? 1.0 / P.dx[t1] : 0.0, ih2 = t2 >= 0 ? 1.0 / P.dx[t2] : 0.0;
+    const double igm = 1.0 / (a.gam - 1.0);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < b.size();
          t += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
@@ -201,38 +216,78 @@ __global__ void k_trace(StepArgs a, int d, const R *Vs, const R *F1x, const R *F
         R Vpg[NV], Vmg[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) { Vpg[perm(d, q)] = Vpl[q]; Vmg[perm(d, q)] = Vml[q]; }
-        // transverse increments L^n_d' = (F_(d',-) - F_(d',+)) / dx_d'
-        double T[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) T[q] = 0.0;
-        if (t1 >= 0) {
-            const long long s1 = dstride(P, t1);
-            const double ih = 1.0 / P.dx[t1];
-#pragma unroll
-            for (int q = 0; q < NV; ++q)
-                T[q] += ((double)F1[t1][q * a.sstride + c - s1] - (double)F1[t1][q * a.sstride + c]) * ih;
-        }
-        if (t2 >= 0) {
-            const long long s2 = dstride(P, t2);
-            const double ih = 1.0 / P.dx[t2];
-#pragma unroll
-            for (int q = 0; q < NV; ++q)
-                T[q] += ((double)F1[t2][q * a.sstride + c - s2] - (double)F1[t2][q * a.sstride + c]) * ih;
-        }
-        double Ui[NV], Vi[NV];
         unsigned int fl = 0;
-        cons64_from_prim(Vpg, a.gam, Ui);
+        if (IFACE64) {
+            // transverse increments L^n_d' = (F_(d',-) - F_(d',+)) / dx_d'
+            double T[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) Ui[q] += 0.5 * dt * T[q];
-        if (!prim_from_cons64(Ui, a.gam, Vi)) fl |= state_flags(Vi[0], Vi[4]);
+            for (int q = 0; q < NV; ++q) T[q] = 0.0;
+            if (t1 >= 0) {
 #pragma unroll
-        for (int q = 0; q < NV; ++q) Vp[q * a.sstride + c] = (R)Vi[q];
-        cons64_from_prim(Vmg, a.gam, Ui);
+                for (int q = 0; q < NV; ++q)
+                    T[q] += ((double)F1t1[q * a.sstride + c - s1] - (double)F1t1[q * a.sstride + c]) * ih1;
+            }
+            if (t2 >= 0) {
 #pragma unroll
-        for (int q = 0; q < NV; ++q) Ui[q] += 0.5 * dt * T[q];
-        if (!prim_from_cons64(Ui, a.gam, Vi)) fl |= state_flags(Vi[0], Vi[4]);
+                for (int q = 0; q < NV; ++q)
+                    T[q] += ((double)F1t2[q * a.sstride + c - s2] - (double)F1t2[q * a.sstride + c]) * ih2;
+            }
+            double Ui[NV], Vi[NV];
+            cons64_from_prim(Vpg, igm, Ui);
 #pragma unroll
-        for (int q = 0; q < NV; ++q) Vm[q * a.sstride + c] = (R)Vi[q];
+            for (int q = 0; q < NV; ++q) Ui[q] += 0.5 * dt * T[q];
+            if (!prim_from_cons64(Ui, a.gam, Vi)) fl |= state_flags(Vi[0], Vi[4]);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Vp[q * a.sstride + c] = (R)Vi[q];
+            cons64_from_prim(Vmg, igm, Ui);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Ui[q] += 0.5 * dt * T[q];
+            if (!prim_from_cons64(Ui, a.gam, Vi)) fl |= state_flags(Vi[0], Vi[4]);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Vm[q * a.sstride + c] = (R)Vi[q];
+        } else {
+            // half-step transverse increments d = dt/2 T, in R
+            R D[NV];
+            const R h1 = (R)(0.5 * dt * ih1), h2 = (R)(0.5 * dt * ih2);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) D[q] = R(0);
+            if (t1 >= 0) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) D[q] += (F1t1[q * a.sstride + c - s1] - F1t1[q * a.sstride + c]) * h1;
+            }
+            if (t2 >= 0) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) D[q] += (F1t2[q * a.sstride + c - s2] - F1t2[q * a.sstride + c]) * h2;
+            }
+            const R gm1 = gam - R(1);
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const R(&W)[NV] = side == 0 ? Vpg : Vmg;
+                R *out = side == 0 ? Vp : Vm;
+                const R rs = W[0];
+                const R rho = rs + D[0];
+                const R irho = R(1) / rho;
+                const R m1 = rs * W[1] + D[1], m2 = rs * W[2] + D[2], m3 = rs * W[3] + D[3];
+                const R v2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
+                const R vdm = W[1] * D[1] + W[2] * D[2] + W[3] * D[3];
+                const R dm2 = D[1] * D[1] + D[2] * D[2] + D[3] * D[3];
+                const R dke = (rs * v2 * D[0] - R(2) * rs * vdm - dm2) * (R(0.5) * irho);
+                const R dme = -(D[5] * (W[5] + R(0.5) * D[5]) + D[6] * (W[6] + R(0.5) * D[6]) +
+                                D[7] * (W[7] + R(0.5) * D[7]));
+                const R p = W[4] + gm1 * (D[4] + dke + dme);
+                out[0 * a.sstride + c] = rho;
+                out[1 * a.sstride + c] = m1 * irho;
+                out[2 * a.sstride + c] = m2 * irho;
+                out[3 * a.sstride + c] = m3 * irho;
+                out[4 * a.sstride + c] = p;
+                out[5 * a.sstride + c] = W[5] + D[5];
+                out[6 * a.sstride + c] = W[6] + D[6];
+                out[7 * a.sstride + c] = W[7] + D[7];
+                out[8 * a.sstride + c] = W[8] + D[8];
+                if (!(rho > R(0)) || !(p > R(0))) fl |= ST_NEG;
+                if (!isfinite(rho) || !isfinite(p)) fl |= ST_NAN;
+            }
+        }
         if (fl) atomicOr(a.status, fl);
     }
 }
@@ -277,12 +332,13 @@ __global__ void k_update(StepArgs a, const R *Fx, const R *Fy, const R *Fz)
     Box b;
 #pragma unroll
     for (int e = 0; e < 3; ++e) { b.lo[e] = 0; b.ext[e] = P.n[e]; }
-    __shared__ double s_damp;
+    __shared__ double s_damp, s_idx[3];
     const double dt = a.dtch[0];
     if (threadIdx.x == 0) {
         double hmin = P.dx[0];
         for (int e = 1; e < a.ndim; ++e) hmin = fmin(hmin, P.dx[e]);
         s_damp = exp(-a.glm_alpha * a.dtch[1] * dt / hmin);
+        for (int e = 0; e < 3; ++e) s_idx[e] = 1.0 / P.dx[e];
     }
     __syncthreads();
     const double damp = s_damp;
@@ -295,12 +351,13 @@ __global__ void k_update(StepArgs a, const R *Fx, const R *Fy, const R *Fz)
         const long long c = P.soff + cl;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-            double s = 0.0;
+            // flux divergence in R (float64 on the FP64 path), accumulation in float64
+            R s = R(0);
             for (int d = 0; d < a.ndim; ++d) {
                 const long long st = dstride(P, d);
-                s += ((double)F[d][q * a.sstride + c - st] - (double)F[d][q * a.sstride + c]) / P.dx[d];
+                s += (F[d][q * a.sstride + c - st] - F[d][q * a.sstride + c]) * (R)s_idx[d];
             }
-            double u = a.U[q * a.ustride + P.base + cl] + dt * s;
+            double u = a.U[q * a.ustride + P.base + cl] + dt * (double)s;
             if (q == 8) u *= damp;
             a.Uout[q * a.ustride + P.base + cl] = u;
         }
@@ -346,6 +403,7 @@ __global__ void k_maxspeed(StepArgs a, unsigned long long *out)
 #pragma unroll
     for (int e = 0; e < 3; ++e) { b.lo[e] = 0; b.ext[e] = P.n[e]; }
     double m = 0.0;
+    const double idx[3] = {1.0 / P.dx[0], 1.0 / P.dx[1], 1.0 / P.dx[2]};
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < b.size();
          t += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
@@ -360,8 +418,8 @@ __global__ void k_maxspeed(StepArgs a, unsigned long long *out)
             const int qn = 1 + d, bn = 5 + d;
             const int b1 = 5 + (d == 0 ? 1 : 0), b2 = 5 + (d == 2 ? 1 : 2);
             const R cf = fast_speed(rho, p, (R)V[bn], (R)V[b1], (R)V[b2], g);
-            const double s = (fabs(V[qn]) + (double)cf) / P.dx[d];
-            m = fmax(m, s);
+            const R sp = (fabs((R)V[qn]) + cf) * (R)idx[d];
+            m = fmax(m, (double)sp);
         }
     }
     // warp + block reduction

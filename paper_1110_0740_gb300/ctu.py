@@ -19,7 +19,7 @@ CTU_EOS_IDEAL, CTU_EOS_TM = 0, 1
 CTU_LINEAR_MC, CTU_PPM = 0, 1
 CTU_CHAR_TRACE, CTU_MUSCL_HANCOCK = 0, 1
 CTU_HLLD, CTU_HLL = 0, 1
-CTU_FP64, CTU_MIXED = 0, 1
+CTU_FP64, CTU_MIXED, CTU_MIXED_IFACE64 = 0, 1, 2
 CTU_TRACE_ALL, CTU_TRACE_UPWIND = 0, 1
 
 STATUS = ["CTU_OK", "CTU_EINVAL", "CTU_ENOMEM", "CTU_ECUDA", "CTU_EUNSUPPORTED", "CTU_ENEGATIVE",
@@ -79,6 +79,12 @@ def _lib():
         L.ctu_strerror.argtypes = [i32]
         L.ctu_strerror.restype = ctypes.c_char_p
         L.ctu_last_launch_count.argtypes = [vp]
+        L.ctu_profile.argtypes = [vp, i32]
+        L.ctu_profile.restype = i32
+        L.ctu_profile_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_longlong)]
+        L.ctu_profile_read.restype = i32
         for f in ("ctu_init", "ctu_dt", "ctu_step", "ctu_flux_registers", "ctu_fill_periodic",
                   "ctu_status_sync", "ctu_last_launch_count"):
             getattr(L, f).restype = i32
@@ -176,6 +182,22 @@ def ctu_last_launch_count(ctx):
     return _lib().ctu_last_launch_count(ctx)
 
 
+def ctu_profile(ctx, enable):
+    _check(_lib().ctu_profile(ctx, int(bool(enable))), "ctu_profile")
+
+
+def ctu_profile_read(ctx):
+    """{kernel name: (total ms, launches)} since profiling was enabled."""
+    L = _lib()
+    n = L.ctu_profile_read(ctx, -1, None, None, None)
+    out = {}
+    for i in range(n):
+        nm, ms, cnt = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_longlong()
+        L.ctu_profile_read(ctx, i, ctypes.byref(nm), ctypes.byref(ms), ctypes.byref(cnt))
+        out[nm.value.decode()] = (ms.value, cnt.value)
+    return out
+
+
 def ctu_strerror(code):
     return _lib().ctu_strerror(code).decode()
 
@@ -215,3 +237,9 @@ class Ctx:
 
     def launches(self):
         return ctu_last_launch_count(self.h)
+
+    def profile(self, enable=True):
+        ctu_profile(self.h, enable)
+
+    def profile_read(self):
+        return ctu_profile_read(self.h)

@@ -148,13 +148,16 @@ def mhd_blast_3d(n=256, seed=0, gamma=5.0 / 3.0, kmax=8):
     return pad_periodic(U, 3)
 
 
-def mhd_lowbeta_3d(n=256, seed=0, gamma=5.0 / 3.0, kmax=8, beta=0.01, mach=10.0):
-    """Low-beta, high-Mach variant: rho = 1 + 0.2 f, p = 1, uniform
-    B0 = sqrt(2 p / beta) along a seeded unit direction, and a seeded velocity
-    field scaled to an rms Mach number `mach` (v_rms = mach sqrt(gamma p/rho0))."""
+def mhd_lowbeta_3d(n=256, seed=0, gamma=5.0 / 3.0, kmax=8, beta=0.01, mach=10.0, kmax_v=2):
+    """Low-beta, high-Mach variant: rho = 1 + 0.2 f (modes |k| <= kmax), p = 1,
+    uniform B0 = sqrt(2 p / beta) along a seeded unit direction, and a seeded
+    large-scale velocity field (modes |k| <= kmax_v) scaled to an rms Mach
+    number `mach` (v_rms = mach sqrt(gamma p / rho0)).  The velocity is kept
+    large-scale: with |k| up to 8 a Mach-10 field drives the unlimited PPM
+    scheme to negative pressures within a step."""
     rng = np.random.default_rng(seed)
     rho = 1.0 + 0.2 * _field_3d(rng, n, kmax)
-    v = [_field_3d(rng, n, kmax) for _ in range(3)]
+    v = [_field_3d(rng, n, kmax_v) for _ in range(3)]
     vrms = np.sqrt(np.mean(v[0] ** 2 + v[1] ** 2 + v[2] ** 2))
     scale = mach * np.sqrt(gamma * 1.0 / 1.0) / vrms
     v = [c * scale for c in v]

@@ -79,3 +79,23 @@ def test_mixed_precision_matches_oracle_loosely():
     ref, odts = oracle_run(Vp, n, 3, dx, 5, 0.3, recon=1)
     e = l1rel(O.interior(got, n, 3), O.interior(ref, n, 3), odts[-1][1])
     assert np.all(e < 1e-4), e
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_lowbeta_accuracy(prec):
+    """Low-beta (0.01), rms-Mach-10 state, where E - rho v^2/2 - B^2/2 loses
+    about 7 bits: both mixed variants (increment-form float32 interface
+    recovery, prec 1; float64 interface recovery, prec 2) stay close to the
+    FP64 oracle, and the FP64 GPU path matches it to 1e-11."""
+    n = [32, 32, 32]
+    U0 = W.mhd_lowbeta_3d(32, seed=1)
+    dx = [1.0 / 32] * 3
+    ref, odts = oracle_run(U0, n, 3, dx, 5, 0.3, recon=1)
+    R = O.interior(ref, n, 3)
+    got, _, st = gpu_run(U0, n, 3, dx, 5, 0.3, precision=prec, recon=1)
+    assert st == 0
+    e = l1rel(O.interior(got, n, 3), R, odts[-1][1])
+    assert np.all(e < 2e-5), e
+    g64, _, st = gpu_run(U0, n, 3, dx, 5, 0.3, precision=0, recon=1)
+    assert st == 0
+    assert np.all(l1rel(O.interior(g64, n, 3), R, odts[-1][1]) < TOL64)
