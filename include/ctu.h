@@ -49,7 +49,8 @@ typedef enum {
     CTU_ENAN = 6,          /* device: a NaN/Inf was met */
     CTU_ERECOVERY = 7,     /* device: primitive recovery did not converge */
     CTU_ESUPERLUMINAL = 8, /* device: |v| >= 1 in relativistic MHD */
-    CTU_ETIMEOUT = 9       /* device: a bounded wait gave up */
+    CTU_ETIMEOUT = 9,      /* device: a bounded wait gave up */
+    CTU_ETOOLARGE = 10     /* ctu_step_noalloc: batch exceeds its fixed scratch */
 } ctu_status;
 
 enum { CTU_MHD = 0, CTU_SRMHD = 1 };
@@ -180,6 +181,40 @@ ctu_status ctu_profile(ctu_ctx *ctx, int enable);
  * number, writes the i-th name (library-owned string), its total device
  * time in ms and its launch count.  Returns 0 when profiling is off. */
 int ctu_profile_read(ctu_ctx *ctx, int i, const char **name, double *total_ms, long long *launches);
+
+/* ---- Allocation-free step ------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory, such as a host framework whose caching
+ * allocator owns all device memory, a real-time loop that cannot take
+ * cudaMalloc's implicit synchronisation, or a plug-in that only receives
+ * pre-allocated buffers.  ctu_step_noalloc advances the batch exactly as
+ * ctu_step does (same kernels, same arithmetic), without flux registers and
+ * without a context: its scratch, status word and patch table live in one
+ * fixed device array inside libctu.so of CTU_NOALLOC_SCRATCH_BYTES (+ a few
+ * KB), held on every GPU that loads the library until the process exits.
+ *
+ * Limits: npatch <= CTU_NOALLOC_MAX_PATCHES and the scratch the batch needs
+ * -- 81 words per ghosted cell (each patch rounded up to 32 cells), 8 bytes
+ * for CTU_FP64, 4 for the mixed modes -- must fit in
+ * CTU_NOALLOC_SCRATCH_BYTES (one 32^3 patch in FP64, one 40^3 patch mixed);
+ * otherwise the call returns CTU_ETOOLARGE and launches nothing.
+ *
+ * The call allocates nothing (no cudaMalloc/cudaFree, no heap).  Its first
+ * call on a device looks up the array's device address (set-up), so make
+ * that first call before any stream capture.  All calls share the one array
+ * and it keeps the last call's contents (the status word is cleared at the
+ * start of every call): calls that overlap on the GPU -- on different
+ * streams, or from different threads -- race and corrupt each other.
+ *
+ * cfg: as for ctu_init.  U_in, U_out, stride, patches, npatch, d_dt_ch: as
+ * for ctu_step.  wait_status != 0: synchronise the stream and return the
+ * device status of this call (CTU_OK, CTU_ENEGATIVE or CTU_ENAN);
+ * wait_status == 0: return after enqueueing. */
+#define CTU_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
+#define CTU_NOALLOC_MAX_PATCHES 64
+ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in, double *U_out,
+                            int64_t stride, const ctu_patch *patches, int npatch,
+                            const double *d_dt_ch, int wait_status, void *stream);
 
 #ifdef __cplusplus
 }

@@ -414,6 +414,7 @@ const char *ctu_strerror(ctu_status s)
     case CTU_ERECOVERY: return "primitive recovery did not converge";
     case CTU_ESUPERLUMINAL: return "superluminal velocity met";
     case CTU_ETIMEOUT: return "bounded wait timed out";
+    case CTU_ETOOLARGE: return "batch exceeds the fixed scratch of ctu_step_noalloc";
     }
     return "unknown status";
 }

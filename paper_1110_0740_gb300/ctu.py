@@ -23,7 +23,7 @@ CTU_FP64, CTU_MIXED, CTU_MIXED_IFACE64 = 0, 1, 2
 CTU_TRACE_ALL, CTU_TRACE_UPWIND = 0, 1
 
 STATUS = ["CTU_OK", "CTU_EINVAL", "CTU_ENOMEM", "CTU_ECUDA", "CTU_EUNSUPPORTED", "CTU_ENEGATIVE",
-          "CTU_ENAN", "CTU_ERECOVERY", "CTU_ESUPERLUMINAL", "CTU_ETIMEOUT"]
+          "CTU_ENAN", "CTU_ERECOVERY", "CTU_ESUPERLUMINAL", "CTU_ETIMEOUT", "CTU_ETOOLARGE"]
 
 
 class ctu_config(ctypes.Structure):
@@ -85,6 +85,9 @@ def _lib():
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_longlong)]
         L.ctu_profile_read.restype = i32
+        L.ctu_step_noalloc.argtypes = [ctypes.POINTER(ctu_config), vp, vp, i64,
+                                       ctypes.POINTER(ctu_patch), i32, vp, i32, vp]
+        L.ctu_step_noalloc.restype = i32
         for f in ("ctu_init", "ctu_dt", "ctu_step", "ctu_flux_registers", "ctu_fill_periodic",
                   "ctu_status_sync", "ctu_last_launch_count"):
             getattr(L, f).restype = i32
@@ -140,6 +143,14 @@ def ctu_init(cfg: ctu_config):
     h = ctypes.c_void_p()
     _check(_lib().ctu_init(ctypes.byref(cfg), ctypes.byref(h)), "ctu_init")
     return h
+
+
+def ctu_step_noalloc(cfg, U_in, U_out, stride, patches, d_dt_ch, wait_status=True, stream=None):
+    """Allocation-free step (see include/ctu.h); returns the status code
+    instead of raising, so callers can see CTU_ETOOLARGE."""
+    return _lib().ctu_step_noalloc(ctypes.byref(cfg), _ptr(U_in), _ptr(U_out), int(stride), patches,
+                                   len(patches), _ptr(d_dt_ch), int(bool(wait_status)),
+                                   _stream(stream))
 
 
 def ctu_destroy(ctx):
