@@ -1,0 +1,151 @@
+"""Batched patches, flux registers, full-size sampled parity and status
+flags of the CUDA path, against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1110_0740_gb300 import workloads as W
+from tests.gpu_util import l1rel
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-11
+
+
+def _dev():
+    import torch
+    return torch.device("cuda:0")
+
+
+def test_batch_of_uneven_patches_and_registers():
+    """Five patches of different shapes (one with a single interior cell
+    along y, one with a different dx) in one ctu_step call, flux-register
+    windows on every boundary face plus an interior plane; each patch and
+    each register matches the oracle run patch by patch."""
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    shapes = [(16, 16, 16), (8, 8, 8), (11, 1, 7), (24, 9, 5), (3, 3, 3)]
+    dxs = [(1 / 16,) * 3, (1 / 8,) * 3, (0.05, 0.07, 0.06), (1 / 24, 1 / 24, 1 / 24), (0.1,) * 3]
+    src = W.mhd_blast_3d(40, seed=21, kmax=3)
+    arrays, bases, base = [], [], 0
+    for i, n in enumerate(shapes):
+        A = np.zeros(O.shape(list(n), 3))
+        g = src[:, 2 * i:2 * i + n[2] + 8, i:i + n[1] + 8, 3 * i:3 * i + n[0] + 8]
+        A[:] = g
+        arrays.append(A)
+        bases.append(base)
+        base += A[0].size + 17  # ragged gaps between patches
+    stride = base
+    pool = np.zeros((9, stride))
+    for A, b in zip(arrays, bases):
+        pool[:, b:b + A[0].size] = A.reshape(9, -1)
+    windows, off = [], 0
+    per_patch = []
+    for p, n in enumerate(shapes):
+        ws = []
+        for d in range(3):
+            a_, b_ = [e for e in range(3) if e != d]
+            for plane in sorted({0, n[d] // 2, n[d]}):
+                windows.append((p, d, plane, 0, n[a_], 0, n[b_], 0.5 + p, off))
+                ws.append((d, plane, 0, n[a_], 0, n[b_], off, 0.5 + p))
+                off += 9 * n[a_] * n[b_]
+        per_patch.append(ws)
+    dev = _dev()
+    U = torch.from_numpy(pool).to(dev)
+    Uo = torch.zeros_like(U)
+    reg = torch.zeros(off, dtype=torch.float64, device=dev)
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_FP64, cfl=0.3))
+    patches = ctu.make_patches([(n, dx, b) for n, dx, b in zip(shapes, dxs, bases)])
+    ctx.flux_registers(reg, windows)
+    dtch = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.dt(U, stride, patches, dtch)
+    ctx.step(U, Uo, stride, patches, dtch)
+    ctx.step(U, Uo, stride, patches, dtch)  # registers accumulate over calls
+    assert ctx.status_sync() == 0
+    dt, ch = dtch.cpu().tolist()
+    # dt over the whole batch
+    m = max(O.mhd_max_speed(A, list(n), 3, list(dx)) for A, n, dx in zip(arrays, shapes, dxs))
+    dt_ref, ch_ref = O.dt_ch(m, [min(min(d) for d in dxs)] * 3, 3, 0.3)
+    assert abs(dt - dt_ref) <= 1e-14 * dt_ref and abs(ch - ch_ref) <= 1e-14 * ch_ref
+    out = Uo.cpu().numpy()
+    regs = reg.cpu().numpy()
+    ref_reg = np.zeros(off)
+    for A, n, dx, b, ws in zip(arrays, shapes, dxs, bases, per_patch):
+        R, bad = O.mhd_step(A, list(n), 3, list(dx), dt, ch, recon=1, windows=ws, reg=ref_reg)
+        O.mhd_step(A, list(n), 3, list(dx), dt, ch, recon=1, windows=ws, reg=ref_reg)
+        G = out[:, b:b + A[0].size].reshape(A.shape)
+        e = l1rel(O.interior(G, list(n), 3), O.interior(R, list(n), 3), ch)
+        assert np.all(e <= TOL64), (n, e)
+    scale = np.abs(ref_reg).max()
+    assert np.abs(regs - ref_reg).max() <= 1e-12 * scale
+
+
+def test_full_size_sampled_parity_256():
+    """The bench workload (256^3, PPM, mixed and FP64, the bench's launch
+    configuration): one GPU step, then 6 sampled 6^3 blocks recomputed by the
+    oracle from their own ghosted neighbourhood of the same input."""
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    n = 256
+    U0 = W.mhd_blast_3d(n, seed=0)
+    dev = _dev()
+    U = torch.from_numpy(U0.reshape(9, -1)).to(dev)
+    Uo = torch.zeros_like(U)
+    stride = U.shape[1]
+    patches = ctu.make_patches([([n] * 3, [1.0 / n] * 3, 0)])
+    rng = np.random.default_rng(5)
+    corners = [rng.integers(0, n - 6, size=3) for _ in range(5)] + [np.array([0, 0, n - 6])]
+    for prec, tol in ((ctu.CTU_FP64, TOL64), (ctu.CTU_MIXED, 2e-5)):
+        ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3))
+        dtch = torch.zeros(2, dtype=torch.float64, device=dev)
+        ctx.dt(U, stride, patches, dtch)
+        ctx.step(U, Uo, stride, patches, dtch)
+        assert ctx.status_sync() == 0
+        dt, ch = dtch.cpu().tolist()
+        G = Uo.view(9, n + 8, n + 8, n + 8)
+        for c in corners:
+            k, j, i = int(c[2]), int(c[1]), int(c[0])
+            blk = U0[:, k:k + 14, j:j + 14, i:i + 14].copy()
+            R, bad = O.mhd_step(blk, [6, 6, 6], 3, [1.0 / n] * 3, dt, ch, recon=1)
+            assert bad == 0
+            got = G[:, k + 4:k + 10, j + 4:j + 10, i + 4:i + 10].cpu().numpy()
+            e = l1rel(got, O.interior(R, [6, 6, 6], 3), ch)
+            assert np.all(e <= tol), (prec, c, e)
+        ctx.close()
+
+
+def test_negative_density_sets_status_flag():
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    n = [8, 8, 8]
+    U0 = W.mhd_blast_3d(8, seed=1, kmax=2)
+    U0[0, 6, 6, 6] = -1.0
+    dev = _dev()
+    U = torch.from_numpy(U0.reshape(9, -1).copy()).to(dev)
+    Uo = torch.zeros_like(U)
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, precision=ctu.CTU_FP64))
+    patches = ctu.make_patches([(n, [1 / 8] * 3, 0)])
+    dtch = torch.tensor([1e-3, 1.0], dtype=torch.float64, device=dev)
+    ctx.step(U, Uo, U.shape[1], patches, dtch)
+    assert ctu.STATUS[ctx.status_sync()] in ("CTU_ENEGATIVE", "CTU_ENAN")
+    assert ctx.status_sync() == 0  # sticky bits are cleared by the read
+
+
+def test_invalid_arguments_rejected_on_host():
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    dev = _dev()
+    U = torch.zeros(9 * 1000, dtype=torch.float64, device=dev)
+    ctx = ctu.Ctx(ctu.make_config(ndim=3))
+    dtch = torch.zeros(2, dtype=torch.float64, device=dev)
+    p = ctu.make_patches([([2, 2, 2], [1.0] * 3, 0)])
+    with pytest.raises(ctu.CtuError):  # aliasing in/out
+        ctx.step(U, U, 1000, p, dtch)
+    with pytest.raises(ctu.CtuError):  # patch beyond the stride
+        ctx.step(U, torch.zeros_like(U), 999, p, dtch)
+    bad = ctu.make_patches([([2, 2, 2], [0.0, 1.0, 1.0], 0)])
+    with pytest.raises(ctu.CtuError):
+        ctx.step(U, torch.zeros_like(U), 1000, bad, dtch)
+    with pytest.raises(ctu.CtuError):
+        ctu.Ctx(ctu.make_config(ndim=4))
+    with pytest.raises(ctu.CtuError):
+        ctu.Ctx(ctu.make_config(cfl=1.5))
