@@ -146,6 +146,15 @@ ctu_status ctu_step(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t str
                     const ctu_patch *patches, int npatch, const double *d_dt_ch,
                     void *stream);
 
+/* ctu_step, and in the same pass the CFL time step of the result: writes
+ * {dt, c_h} of U_out's interior cells (as ctu_dt would compute them, in the
+ * context's precision) to the device array d_dt_ch_next[2], which must not
+ * alias d_dt_ch.  This is the step's fused epilogue of Eq. (Ca), so a time
+ * loop needs ctu_dt only before its first step. */
+ctu_status ctu_step_next_dt(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t stride,
+                            const ctu_patch *patches, int npatch, const double *d_dt_ch,
+                            double *d_dt_ch_next, void *stream);
+
 /* Bind (or, with reg == NULL or nwin == 0, unbind) flux-register windows.
  * `win` is a host array copied at call time; `reg` is a device float64 array
  * the caller owns and zeroes.  Windows must not overlap in reg. */
@@ -194,9 +203,9 @@ int ctu_profile_read(ctu_ctx *ctx, int i, const char **name, double *total_ms, l
  * KB), held on every GPU that loads the library until the process exits.
  *
  * Limits: npatch <= CTU_NOALLOC_MAX_PATCHES and the scratch the batch needs
- * -- 81 words per ghosted cell (each patch rounded up to 32 cells), 8 bytes
+ * -- 45 words per ghosted cell (each patch rounded up to 32 cells), 8 bytes
  * for CTU_FP64, 4 for the mixed modes -- must fit in
- * CTU_NOALLOC_SCRATCH_BYTES (one 32^3 patch in FP64, one 40^3 patch mixed);
+ * CTU_NOALLOC_SCRATCH_BYTES (one 40^3 patch in FP64, one 56^3 patch mixed);
  * otherwise the call returns CTU_ETOOLARGE and launches nothing.
  *
  * The call allocates nothing (no cudaMalloc/cudaFree, no heap).  Its first

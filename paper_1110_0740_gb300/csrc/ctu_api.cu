@@ -1,10 +1,13 @@
 // ctu_api.cu -- C ABI of libctu.so (declared in include/ctu.h).
 //
 // Host side of the CTU-MHD integrator: argument validation, patch-list
-// upload, scratch management, the CFL reduction of Eq. (Ca), the step
-// launch sequence, flux-register binding and the sticky device status.
+// binding (patches grouped by shape so that every kernel launch covers a
+// group of identical patches with no idle blocks), scratch management, the
+// CFL reduction of Eq. (Ca), the step launch sequence, flux-register
+// binding, the sticky device status and the optional per-kernel timers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -19,7 +22,7 @@
 using namespace ctu;
 
 // Per-kernel CUDA-event timing: an event is recorded on the launching stream
-// right before and right after every kernel; totals are resolved on read.
+// right before and right after every kernel group; totals are resolved on read.
 struct EventProf : ProfHook {
     struct Rec { const char *name; cudaEvent_t a, b; };
     std::vector<cudaEvent_t> pool;
@@ -28,7 +31,7 @@ struct EventProf : ProfHook {
     const char *open = nullptr;
     cudaEvent_t open_ev = nullptr;
     std::vector<std::string> names;
-    std::map<std::string, std::pair<double, long>> tot;
+    std::map<std::string, std::pair<double, long long>> tot;
     cudaEvent_t take()
     {
         if (used == pool.size()) {
@@ -56,8 +59,7 @@ struct EventProf : ProfHook {
         for (const Rec &r : pending) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
-                auto it = tot.find(r.name);
-                if (it == tot.end()) {
+                if (tot.find(r.name) == tot.end()) {
                     names.push_back(r.name);
                     tot[r.name] = {0.0, 0};
                 }
@@ -84,24 +86,28 @@ struct EventProf : ProfHook {
 struct ctu_ctx {
     ctu_config cfg;
     int device = 0;
-    // patch list cache
+    // patch list cache (caller order) and its device table (grouped order)
     std::vector<ctu_patch> hpatch;
+    std::vector<int> sorted_of;  // caller index -> device-table index
+    std::vector<Group> groups;
     DevPatch *dpatch = nullptr;
     int dpatch_cap = 0;
     long long sstride = 0;
-    long long max_cells = 0;
-    long long max_interior = 0;
     double dxmin = 0.0;
     // scratch
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
-    // status, reduction word
+    // status, reduction word, per-step parameters
     unsigned int *dstatus = nullptr;
     unsigned long long *dmax = nullptr;
+    StepParams *dsp = nullptr;
     // flux registers
-    DevWindow *dwin = nullptr;
-    int nwin = 0;
+    std::vector<ctu_flux_window> hwin;
     double *reg = nullptr;
+    DevWindow *dwin = nullptr;
+    int *dwstart = nullptr;  // npatch * 3 starts then npatch * 3 counts
+    int dwin_cap = 0, dws_cap = 0;
+    bool win_dirty = false;
     int last_launches = 0;
     EventProf *prof = nullptr;
 };
@@ -111,10 +117,10 @@ static ctu_status cuda_fail(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? CTU_ENOMEM : CTU_ECUDA;
 }
 
-#define CTU_CUDA(call)                                    \
-    do {                                                  \
-        cudaError_t e_ = (call);                          \
-        if (e_ != cudaSuccess) return cuda_fail(e_);      \
+#define CTU_CUDA(call)                               \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
     } while (0)
 
 static int active_ghost(const ctu_ctx *ctx, int d) { return d < ctx->cfg.ndim ? 4 : 0; }
@@ -125,42 +131,123 @@ static ctu_status validate_patches(const ctu_ctx *ctx, int64_t stride, const ctu
     for (int i = 0; i < np; ++i) {
         long long cells = 1;
         for (int d = 0; d < 3; ++d) {
-            if (p[i].n[d] < 1) return CTU_EINVAL;
+            if (p[i].n[d] < 1 || p[i].n[d] > 4096) return CTU_EINVAL;
             if (d >= ctx->cfg.ndim && p[i].n[d] != 1) return CTU_EINVAL;
             if (!(p[i].dx[d] > 0.0)) return CTU_EINVAL;
             cells *= (long long)p[i].n[d] + 2 * active_ghost(ctx, d);
         }
+        if (cells > (1LL << 30)) return CTU_EINVAL;  // local cell indices are 32-bit
         if (p[i].base < 0 || p[i].base + cells > stride) return CTU_EINVAL;
     }
     return CTU_OK;
 }
 
-// Upload the patch list if it differs from the cached one; sizes scratch.
+// Device table of flux windows, sorted by (device patch index, dir), with
+// per (patch, dir) start/count arrays.
+static ctu_status upload_windows(ctu_ctx *ctx, cudaStream_t s)
+{
+    const int np = (int)ctx->hpatch.size();
+    if (!ctx->reg || ctx->hwin.empty() || np == 0) {
+        ctx->win_dirty = false;
+        return CTU_OK;
+    }
+    struct W { int key; DevWindow w; };
+    std::vector<W> v;
+    for (const ctu_flux_window &x : ctx->hwin) {
+        if (x.patch >= np) continue;
+        DevWindow w;
+        w.patch = ctx->sorted_of[x.patch];
+        w.dir = x.dir; w.plane = x.plane; w.a0 = x.a0; w.a1 = x.a1; w.b0 = x.b0; w.b1 = x.b1; w.pad = 0;
+        w.weight = x.weight;
+        w.dst = x.dst;
+        v.push_back({w.patch * 3 + w.dir, w});
+    }
+    std::stable_sort(v.begin(), v.end(), [](const W &a, const W &b) { return a.key < b.key; });
+    std::vector<DevWindow> dw(v.size() ? v.size() : 1);
+    std::vector<int> sc(2 * 3 * np, 0);
+    for (size_t i = 0; i < v.size(); ++i) {
+        dw[i] = v[i].w;
+        if (sc[3 * np + v[i].key] == 0) sc[v[i].key] = (int)i;
+        sc[3 * np + v[i].key] += 1;
+    }
+    if ((int)dw.size() > ctx->dwin_cap) {
+        if (ctx->dwin) cudaFree(ctx->dwin);
+        ctx->dwin = nullptr;
+        CTU_CUDA(cudaMalloc(&ctx->dwin, sizeof(DevWindow) * dw.size()));
+        ctx->dwin_cap = (int)dw.size();
+    }
+    if ((int)sc.size() > ctx->dws_cap) {
+        if (ctx->dwstart) cudaFree(ctx->dwstart);
+        ctx->dwstart = nullptr;
+        CTU_CUDA(cudaMalloc(&ctx->dwstart, sizeof(int) * sc.size()));
+        ctx->dws_cap = (int)sc.size();
+    }
+    CTU_CUDA(cudaMemcpyAsync(ctx->dwin, dw.data(), sizeof(DevWindow) * dw.size(), cudaMemcpyHostToDevice, s));
+    CTU_CUDA(cudaMemcpyAsync(ctx->dwstart, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice, s));
+    CTU_CUDA(cudaStreamSynchronize(s));
+    ctx->win_dirty = false;
+    return CTU_OK;
+}
+
+// Upload the patch list (grouped by shape) if it differs from the cached one.
 static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStream_t s)
 {
-    if ((int)ctx->hpatch.size() == np && std::memcmp(ctx->hpatch.data(), p, sizeof(ctu_patch) * np) == 0)
+    if ((int)ctx->hpatch.size() == np && std::memcmp(ctx->hpatch.data(), p, sizeof(ctu_patch) * np) == 0) {
+        if (ctx->win_dirty) return upload_windows(ctx, s);
         return CTU_OK;
+    }
+    std::vector<int> order(np);
+    for (int i = 0; i < np; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        for (int d = 0; d < 3; ++d)
+            if (p[a].n[d] != p[b].n[d]) return p[a].n[d] < p[b].n[d];
+        return false;
+    });
     std::vector<DevPatch> dp(np);
-    long long off = 0, maxc = 0, maxi = 0;
+    std::vector<int> sorted_of(np);
+    std::vector<Group> groups;
+    long long off = 0;
     double dxmin = 1e300;
-    for (int i = 0; i < np; ++i) {
-        DevPatch &q = dp[i];
-        long long cells = 1, inner = 1;
+    for (int r = 0; r < np; ++r) {
+        const ctu_patch &src = p[order[r]];
+        sorted_of[order[r]] = r;
+        DevPatch &q = dp[r];
+        long long cells = 1;
+        q.hmin = 1e300;
         for (int d = 0; d < 3; ++d) {
-            q.n[d] = p[i].n[d];
+            q.n[d] = src.n[d];
             q.g[d] = active_ghost(ctx, d);
             q.N[d] = q.n[d] + 2 * q.g[d];
-            q.dx[d] = p[i].dx[d];
+            q.dx[d] = src.dx[d];
+            q.idx[d] = 1.0 / src.dx[d];
+            q.idxf[d] = (float)q.idx[d];
             cells *= q.N[d];
-            inner *= q.n[d];
-            if (d < ctx->cfg.ndim && q.dx[d] < dxmin) dxmin = q.dx[d];
+            if (d < ctx->cfg.ndim) {
+                q.hmin = std::min(q.hmin, q.dx[d]);
+                dxmin = std::min(dxmin, q.dx[d]);
+            }
         }
-        q.base = p[i].base;
+        q.base = src.base;
         q.soff = off;
         off += (cells + 31) / 32 * 32;
-        if (cells > maxc) maxc = cells;
-        if (inner > maxi) maxi = inner;
+        if (groups.empty() || std::memcmp(groups.back().n, q.n, sizeof(q.n)) != 0) {
+            Group G;
+            G.first = r;
+            G.count = 0;
+            for (int d = 0; d < 3; ++d) { G.n[d] = q.n[d]; G.N[d] = q.N[d]; }
+            groups.push_back(G);
+        }
+        groups.back().count += 1;
     }
+    // split groups into <= 65535 patches (grid y limit)
+    std::vector<Group> g2;
+    for (const Group &G : groups)
+        for (int f = 0; f < G.count; f += 65535) {
+            Group H = G;
+            H.first = G.first + f;
+            H.count = std::min(65535, G.count - f);
+            g2.push_back(H);
+        }
     if (np > ctx->dpatch_cap) {
         if (ctx->dpatch) cudaFree(ctx->dpatch);
         ctx->dpatch = nullptr;
@@ -170,11 +257,11 @@ static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStr
     CTU_CUDA(cudaMemcpyAsync(ctx->dpatch, dp.data(), sizeof(DevPatch) * np, cudaMemcpyHostToDevice, s));
     CTU_CUDA(cudaStreamSynchronize(s));
     ctx->hpatch.assign(p, p + np);
+    ctx->sorted_of = sorted_of;
+    ctx->groups = g2;
     ctx->sstride = off;
-    ctx->max_cells = maxc;
-    ctx->max_interior = maxi;
     ctx->dxmin = dxmin;
-    return CTU_OK;
+    return upload_windows(ctx, s);
 }
 
 static ctu_status ensure_scratch(ctu_ctx *ctx)
@@ -197,10 +284,14 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
                           const double *dtch)
 {
     StepArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.patches = ctx->dpatch;
     a.npatch = np;
     a.ndim = ctx->cfg.ndim;
     a.gam = ctx->cfg.gamma;
+    a.igm = 1.0 / (ctx->cfg.gamma - 1.0);
+    a.gamf = (float)ctx->cfg.gamma;
+    a.gm1f = (float)(ctx->cfg.gamma - 1.0);
     a.glm_alpha = ctx->cfg.glm_alpha;
     a.upwind = ctx->cfg.trace_mode == CTU_TRACE_UPWIND;
     a.U = Uin;
@@ -208,8 +299,47 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.ustride = stride;
     a.sstride = ctx->sstride;
     a.dtch = dtch;
+    a.sp = ctx->dsp;
     a.status = ctx->dstatus;
+    const bool regs = ctx->reg && !ctx->hwin.empty();
+    a.win = regs ? ctx->dwin : nullptr;
+    a.wstart = regs ? ctx->dwstart : nullptr;
+    a.wcount = regs ? ctx->dwstart + 3 * (int)ctx->hpatch.size() : nullptr;
+    a.reg = regs ? ctx->reg : nullptr;
+    a.nextmax = nullptr;
     return a;
+}
+
+static LaunchInfo make_info(const ctu_ctx *ctx)
+{
+    LaunchInfo li;
+    li.groups = ctx->groups.data();
+    li.ngroups = (int)ctx->groups.size();
+    li.recon = ctx->cfg.recon == CTU_PPM;
+    li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
+    li.scratch = ctx->scratch;
+    li.sp = ctx->dsp;
+    li.prof = ctx->prof;
+    return li;
+}
+
+namespace ctu {
+template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
+{
+    return launch_step_impl<double, 1>(a, li, s);
+}
+template <> int launch_step<float>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
+{
+    return li.iface64 ? launch_step_impl<float, 1>(a, li, s) : launch_step_impl<float, 0>(a, li, s);
+}
+} // namespace ctu
+
+__global__ void k_dt_finalize(const unsigned long long *m, double cfl, double dxmin, double *dtch)
+{
+    const double M = __longlong_as_double((long long)*m);
+    const double dt = cfl / M;
+    dtch[0] = dt;
+    dtch[1] = cfl * dxmin / dt;
 }
 
 extern "C" {
@@ -237,6 +367,7 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
     if (cudaGetDevice(&ctx->device) != cudaSuccess ||
         cudaMalloc(&ctx->dstatus, sizeof(unsigned int)) != cudaSuccess ||
         cudaMalloc(&ctx->dmax, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&ctx->dsp, sizeof(StepParams)) != cudaSuccess ||
         cudaMemset(ctx->dstatus, 0, sizeof(unsigned int)) != cudaSuccess) {
         ctu_destroy(ctx);
         return CTU_ECUDA;
@@ -253,17 +384,11 @@ void ctu_destroy(ctu_ctx *ctx)
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->dstatus) cudaFree(ctx->dstatus);
     if (ctx->dmax) cudaFree(ctx->dmax);
+    if (ctx->dsp) cudaFree(ctx->dsp);
     if (ctx->dwin) cudaFree(ctx->dwin);
+    if (ctx->dwstart) cudaFree(ctx->dwstart);
     delete ctx->prof;
     delete ctx;
-}
-
-__global__ void k_dt_finalize(const unsigned long long *m, double cfl, double dxmin, double *dtch)
-{
-    const double M = __longlong_as_double((long long)*m);
-    const double dt = cfl / M;
-    dtch[0] = dt;
-    dtch[1] = cfl * dxmin / dt;
 }
 
 ctu_status ctu_dt(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patch *patches, int npatch,
@@ -277,10 +402,11 @@ ctu_status ctu_dt(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patch
     if (st != CTU_OK) return st;
     CTU_CUDA(cudaMemsetAsync(ctx->dmax, 0, sizeof(unsigned long long), s));
     StepArgs a = make_args(ctx, U, nullptr, stride, npatch, nullptr);
+    LaunchInfo li = make_info(ctx);
     if (ctx->cfg.precision != CTU_FP64)
-        launch_maxspeed<float>(a, ctx->max_interior, ctx->dmax, s, ctx->prof);
+        launch_maxspeed<float>(a, li, ctx->dmax, s);
     else
-        launch_maxspeed<double>(a, ctx->max_interior, ctx->dmax, s, ctx->prof);
+        launch_maxspeed<double>(a, li, ctx->dmax, s);
     k_dt_finalize<<<1, 1, 0, s>>>(ctx->dmax, ctx->cfg.cfl, ctx->dxmin, d_dt_ch);
     CTU_CUDA(cudaGetLastError());
     if (h_dt_ch) {
@@ -290,8 +416,9 @@ ctu_status ctu_dt(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patch
     return CTU_OK;
 }
 
-ctu_status ctu_step(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t stride,
-                    const ctu_patch *patches, int npatch, const double *d_dt_ch, void *stream)
+static ctu_status step_common(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t stride,
+                              const ctu_patch *patches, int npatch, const double *d_dt_ch, double *d_next,
+                              void *stream)
 {
     if (!ctx || !U_in || !U_out || !d_dt_ch || U_in == U_out) return CTU_EINVAL;
     ctu_status st = validate_patches(ctx, stride, patches, npatch);
@@ -302,21 +429,37 @@ ctu_status ctu_step(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t str
     st = ensure_scratch(ctx);
     if (st != CTU_OK) return st;
     StepArgs a = make_args(ctx, U_in, U_out, stride, npatch, d_dt_ch);
-    LaunchInfo li;
-    li.max_cells = ctx->max_cells;
-    li.recon = ctx->cfg.recon == CTU_PPM;
-    li.win = ctx->dwin;
-    li.nwin = ctx->reg ? ctx->nwin : 0;
-    li.reg = ctx->reg;
-    li.scratch = ctx->scratch;
-    li.prof = ctx->prof;
-    li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
+    LaunchInfo li = make_info(ctx);
+    int n = 0;
+    if (d_next) {
+        CTU_CUDA(cudaMemsetAsync(ctx->dmax, 0, sizeof(unsigned long long), s));
+        a.nextmax = ctx->dmax;
+    }
     if (ctx->cfg.precision != CTU_FP64)
-        ctx->last_launches = launch_step<float>(a, li, s);
+        n = launch_step<float>(a, li, s);
     else
-        ctx->last_launches = launch_step<double>(a, li, s);
+        n = launch_step<double>(a, li, s);
+    if (d_next) {
+        k_dt_finalize<<<1, 1, 0, s>>>(ctx->dmax, ctx->cfg.cfl, ctx->dxmin, d_next);
+        ++n;
+    }
+    ctx->last_launches = n;
     CTU_CUDA(cudaGetLastError());
     return CTU_OK;
+}
+
+ctu_status ctu_step(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t stride,
+                    const ctu_patch *patches, int npatch, const double *d_dt_ch, void *stream)
+{
+    return step_common(ctx, U_in, U_out, stride, patches, npatch, d_dt_ch, nullptr, stream);
+}
+
+ctu_status ctu_step_next_dt(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t stride,
+                            const ctu_patch *patches, int npatch, const double *d_dt_ch,
+                            double *d_dt_ch_next, void *stream)
+{
+    if (!d_dt_ch_next || d_dt_ch_next == d_dt_ch) return CTU_EINVAL;
+    return step_common(ctx, U_in, U_out, stride, patches, npatch, d_dt_ch, d_dt_ch_next, stream);
 }
 
 ctu_status ctu_flux_registers(ctu_ctx *ctx, double *reg, const ctu_flux_window *win, int nwin)
@@ -324,26 +467,22 @@ ctu_status ctu_flux_registers(ctu_ctx *ctx, double *reg, const ctu_flux_window *
     if (!ctx || nwin < 0) return CTU_EINVAL;
     if (!reg || nwin == 0) {
         ctx->reg = nullptr;
-        ctx->nwin = 0;
+        ctx->hwin.clear();
+        ctx->win_dirty = false;
         return CTU_OK;
     }
-    if (!win || nwin > 65535) return CTU_EINVAL;
-    std::vector<DevWindow> w(nwin);
+    if (!win) return CTU_EINVAL;
     for (int i = 0; i < nwin; ++i) {
         const ctu_flux_window &x = win[i];
-        if (x.patch < 0 || x.dir < 0 || x.dir >= ctx->cfg.ndim || x.a1 < x.a0 || x.b1 < x.b0 || x.dst < 0)
+        if (x.patch < 0 || x.dir < 0 || x.dir >= ctx->cfg.ndim || x.a1 < x.a0 || x.b1 < x.b0 || x.a0 < 0 ||
+            x.b0 < 0 || x.dst < 0 || x.plane < 0)
             return CTU_EINVAL;
-        w[i].patch = x.patch; w[i].dir = x.dir; w[i].plane = x.plane;
-        w[i].a0 = x.a0; w[i].a1 = x.a1; w[i].b0 = x.b0; w[i].b1 = x.b1; w[i].pad = 0;
-        w[i].weight = x.weight; w[i].dst = x.dst;
     }
     CTU_CUDA(cudaDeviceSynchronize());
-    if (ctx->dwin) cudaFree(ctx->dwin);
-    ctx->dwin = nullptr;
-    CTU_CUDA(cudaMalloc(&ctx->dwin, sizeof(DevWindow) * nwin));
-    CTU_CUDA(cudaMemcpy(ctx->dwin, w.data(), sizeof(DevWindow) * nwin, cudaMemcpyHostToDevice));
-    ctx->nwin = nwin;
+    ctx->hwin.assign(win, win + nwin);
     ctx->reg = reg;
+    ctx->win_dirty = true;
+    if (!ctx->hpatch.empty()) return upload_windows(ctx, 0);
     return CTU_OK;
 }
 
@@ -381,7 +520,9 @@ ctu_status ctu_fill_periodic(ctu_ctx *ctx, double *U, int64_t stride, const ctu_
     cudaStream_t s = (cudaStream_t)stream;
     st = bind_patches(ctx, patches, npatch, s);
     if (st != CTU_OK) return st;
-    long long bx = (ctx->max_cells + 255) / 256;
+    long long maxc = 0;
+    for (const Group &G : ctx->groups) maxc = std::max(maxc, (long long)G.N[0] * G.N[1] * G.N[2]);
+    long long bx = (maxc + 255) / 256;
     if (bx > (1LL << 20)) bx = 1LL << 20;
     k_fill_periodic<<<dim3((unsigned)bx, (unsigned)npatch, 1), 256, 0, s>>>(ctx->dpatch, ctx->cfg.ndim, U, stride);
     CTU_CUDA(cudaGetLastError());

@@ -1,10 +1,13 @@
-// Mixed-precision instantiation: tracing, projections and Riemann fluxes in
-// float32; pressure recovery, interface conservative states and the update
-// accumulation stay in float64 inside the kernels.
+// Mixed path (CTU_MIXED): float32 tracing, projections, Riemann fluxes and
+// interface states; float64 state, double-float pressure recovery at cell
+// centres, float64 update accumulation.
 #include "ctu_launch.cuh"
 
 namespace ctu {
-template int launch_step<float>(const StepArgs &, const LaunchInfo &, cudaStream_t);
-template int launch_maxspeed<float>(const StepArgs &, long long, unsigned long long *, cudaStream_t,
-                                       ProfHook *);
+template int launch_step_impl<float, 0>(const StepArgs &, const LaunchInfo &, cudaStream_t);
+template <> int launch_maxspeed<float>(const StepArgs &a, const LaunchInfo &li, unsigned long long *out,
+                                       cudaStream_t s)
+{
+    return launch_maxspeed_impl<float>(a, li, out, s);
+}
 } // namespace ctu

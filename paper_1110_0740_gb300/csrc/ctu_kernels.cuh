@@ -1,31 +1,45 @@
 // ctu_kernels.cuh -- kernels of the CTU step, templated on the working
-// precision R of the tracing / Riemann stages.  Instantiated once for
-// R = double (FP64 path) and once for R = float (mixed path) by
-// ctu_f64.cu and ctu_f32.cu.
+// precision R of the tracing / Riemann stages (double: FP64 path; float:
+// mixed path) and on the sweep direction D.
 //
 // One step (Section 3.1 of Mignone et al. 2012, Eq. update / ctu_flux /
 // transv with Pi = 0) is the kernel sequence
-//   k_prim       V = V(U) on every cell (pressure recovery in float64)
-//   k_flux1<d>   first-order Godunov fluxes F^n_d = R(U_c, U_c+e_d)
-//   k_trace<d>   normal predictor + transverse correction -> V^(n+1/2)_(+/-)
-//   k_riemann<d> F^(n+1/2)_d = R(V_(c,+), V_(c+e_d,-))
-//   k_update     U^(n+1) = U^n + dt sum_d (F_(d,-) - F_(d,+))/dx_d, psi damping
-//   k_registers  flux-register windows, Eq. (fluxcorr)
-// Intermediate arrays live in a library-owned scratch buffer with the same
-// ghosted-patch layout as the pool (one region per patch).
+//   k_setup        {dt, c_h} -> per-step parameters (float copies)
+//   k_prim         V = V(U) on every ghosted cell
+//   k_flux1<D>     first-order Godunov fluxes F^n_D = R(U_c, U_c+e_D)
+//   k_sweep_x      direction x: normal predictor + transverse correction,
+//                  n+1/2 Riemann problems and L_x, one thread per traced cell,
+//                  interface states exchanged through shared memory
+//   k_sweep_m<D>   directions y, z: the same, one thread per pencil segment
+//                  marching along D with the 5-cell stencil in registers
+// The last sweep of the step adds U^n + dt (L_x + L_y + L_z), applies the
+// psi source and, on request, reduces the next step's CFL speed; every sweep
+// accumulates the flux-register windows of its faces (Eq. fluxcorr).
+//
+// Scratch (library-owned, per-patch regions with the ghosted layout): V (9
+// words per cell), F^n (3 x 9), and the running sum A = L_x (+ L_y) (9), all
+// in R.  Interface states and n+1/2 fluxes never leave the chip.
+//
+// Mixed path and the FP64 pipe: besides the float64 update accumulation
+// (one DFMA per variable and cell) the mixed kernels issue no FP64
+// instruction on the common path -- float64 inputs are split and widened
+// with integer operations and the cell-centre pressure is recovered in
+// double-float arithmetic (df.cuh); per-step parameters arrive as floats.
 #pragma once
 
+#include "df.cuh"
 #include "mhd_device.cuh"
 
 namespace ctu {
 
-constexpr int NG = 4;
-
 struct DevPatch {
-    int n[3];      // interior cells
-    int N[3];      // ghosted extent
-    int g[3];      // ghosts per side
+    int n[3];        // interior cells
+    int N[3];        // ghosted extent
+    int g[3];        // ghosts per side (4 active, 0 inactive)
+    float idxf[3];   // 1/dx in float
     double dx[3];
+    double idx[3];   // 1/dx
+    double hmin;     // min dx over active dimensions
     long long base;  // pool offset of the first ghosted cell
     long long soff;  // scratch offset of the first ghosted cell
 };
@@ -36,11 +50,18 @@ struct DevWindow {
     long long dst;
 };
 
+struct StepParams {
+    double dt, ch;
+    float dtf, chf;
+};
+
 struct StepArgs {
     const DevPatch *patches;
     int npatch;
     int ndim;
     double gam;
+    double igm;            // 1/(Gamma-1)
+    float gamf, gm1f;      // Gamma, Gamma-1 in float
     double glm_alpha;
     int upwind;
     const double *U;       // pool in
@@ -48,58 +69,50 @@ struct StepArgs {
     long long ustride;     // pool variable stride
     long long sstride;     // scratch variable stride
     const double *dtch;    // device {dt, c_h}
+    const StepParams *sp;  // device per-step parameters (written by k_setup)
     unsigned int *status;  // sticky status bits
+    // flux registers: windows sorted by (patch, dir); wstart/wcount per patch*3+dir
+    const DevWindow *win;
+    const int *wstart;
+    const int *wcount;
+    double *reg;
+    unsigned long long *nextmax;  // nullable: max CFL speed of U^(n+1)
 };
 
 enum : unsigned int { ST_NEG = 1u, ST_NAN = 2u };
 
-__device__ __forceinline__ long long cell_of(const DevPatch &P, int i, int j, int k)
+constexpr int BLOCK = 128;
+constexpr int SEG = 32;  // cells per marching segment
+
+// Local component q of a sweep along D reads global component gperm<D>(q).
+template <int D> __host__ __device__ constexpr int gperm(int q)
 {
-    return ((long long)(k + P.g[2]) * P.N[1] + (j + P.g[1])) * P.N[0] + (i + P.g[0]);
+    return D == 0 ? q
+                  : (D == 1 ? (q == 1 ? 2 : q == 2 ? 1 : q == 5 ? 6 : q == 6 ? 5 : q)
+                            : (q == 1 ? 3 : q == 2 ? 1 : q == 3 ? 2 : q == 5 ? 7 : q == 6 ? 5 : q == 7 ? 6 : q));
 }
 
-__device__ __forceinline__ long long dstride(const DevPatch &P, int d)
+__device__ __forceinline__ int lcell(const DevPatch &P, int i, int j, int k)
 {
-    return d == 0 ? 1LL : (d == 1 ? (long long)P.N[0] : (long long)P.N[0] * P.N[1]);
+    return ((k + P.g[2]) * P.N[1] + (j + P.g[1])) * P.N[0] + (i + P.g[0]);
 }
 
-// Box [lo, lo + ext) of cell coordinates; thread t -> (i, j, k), x fastest.
-struct Box {
-    int lo[3], ext[3];
-    __device__ __forceinline__ long long size() const { return (long long)ext[0] * ext[1] * ext[2]; }
-    __device__ __forceinline__ void coords(long long t, int &i, int &j, int &k) const
-    {
-        i = lo[0] + (int)(t % ext[0]);
-        long long r = t / ext[0];
-        j = lo[1] + (int)(r % ext[1]);
-        k = lo[2] + (int)(r / ext[1]);
-    }
-};
-
-// ---------------------------------------------------------------- conversions
-
-__device__ __forceinline__ bool prim_from_cons64(const double (&U)[NV], double gam, double (&V)[NV])
+__device__ __forceinline__ int dstr(const DevPatch &P, int d)
 {
-    const double rho = U[0];
-    const double ir = 1.0 / rho;
-    const double vx = U[1] * ir, vy = U[2] * ir, vz = U[3] * ir;
-    const double ke = 0.5 * (U[1] * vx + U[2] * vy + U[3] * vz);
-    const double me = 0.5 * (U[5] * U[5] + U[6] * U[6] + U[7] * U[7]);
-    const double p = (gam - 1.0) * (U[4] - ke - me);
-    V[0] = rho; V[1] = vx; V[2] = vy; V[3] = vz; V[4] = p;
-    V[5] = U[5]; V[6] = U[6]; V[7] = U[7]; V[8] = U[8];
-    return rho > 0.0 && p > 0.0;
+    return d == 0 ? 1 : (d == 1 ? P.N[0] : P.N[0] * P.N[1]);
 }
 
-// igm = 1/(Gamma - 1)
-template <class R>
-__device__ __forceinline__ void cons64_from_prim(const R (&V)[NV], double igm, double (&U)[NV])
+// x-width of a block's thread tile for a patch: 8, 16 or 32 lanes along x.
+__host__ __device__ __forceinline__ int tile_xw(int nx)
 {
-    const double rho = V[0], vx = V[1], vy = V[2], vz = V[3], p = V[4];
-    const double bx = V[5], by = V[6], bz = V[7];
-    U[0] = rho; U[1] = rho * vx; U[2] = rho * vy; U[3] = rho * vz;
-    U[4] = p * igm + 0.5 * rho * (vx * vx + vy * vy + vz * vz) + 0.5 * (bx * bx + by * by + bz * bz);
-    U[5] = bx; U[6] = by; U[7] = bz; U[8] = V[8];
+    return nx >= 24 ? 32 : (nx >= 12 ? 16 : 8);
+}
+
+// Bring the cache line holding *p into L1 ahead of its use (no register is
+// held while the load is in flight).
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ unsigned int state_flags(double rho, double p)
@@ -110,331 +123,579 @@ __device__ __forceinline__ unsigned int state_flags(double rho, double p)
     return f;
 }
 
-// ---------------------------------------------------------------- kernels
+// ---------------------------------------------------------------- parameters in R
 
-// V = V(U) on every ghosted cell of every patch; stores V in precision R.
-template <class R>
-__global__ void k_prim(StepArgs a, R *Vs)
+template <class R> __device__ __forceinline__ R pgam(const StepArgs &a);
+template <> __device__ __forceinline__ double pgam<double>(const StepArgs &a) { return a.gam; }
+template <> __device__ __forceinline__ float pgam<float>(const StepArgs &a) { return a.gamf; }
+template <class R> __device__ __forceinline__ R pgm1(const StepArgs &a);
+template <> __device__ __forceinline__ double pgm1<double>(const StepArgs &a) { return a.gam - 1.0; }
+template <> __device__ __forceinline__ float pgm1<float>(const StepArgs &a) { return a.gm1f; }
+template <class R> __device__ __forceinline__ R pdt(const StepParams *sp);
+template <> __device__ __forceinline__ double pdt<double>(const StepParams *sp) { return sp->dt; }
+template <> __device__ __forceinline__ float pdt<float>(const StepParams *sp) { return sp->dtf; }
+template <class R> __device__ __forceinline__ R pch(const StepParams *sp);
+template <> __device__ __forceinline__ double pch<double>(const StepParams *sp) { return sp->ch; }
+template <> __device__ __forceinline__ float pch<float>(const StepParams *sp) { return sp->chf; }
+template <class R> __device__ __forceinline__ R pidx(const DevPatch &P, int d);
+template <> __device__ __forceinline__ double pidx<double>(const DevPatch &P, int d) { return P.idx[d]; }
+template <> __device__ __forceinline__ float pidx<float>(const DevPatch &P, int d) { return P.idxf[d]; }
+
+// ---------------------------------------------------------------- conversions
+
+__device__ __forceinline__ bool prim_from_cons64(const double (&U)[NV], double gm1, double (&V)[NV])
 {
-    const DevPatch P = a.patches[blockIdx.y];
-    const long long ncell = (long long)P.N[0] * P.N[1] * P.N[2];
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
-         c += (long long)gridDim.x * blockDim.x) {
+    const double rho = U[0];
+    const double ir = 1.0 / rho;
+    const double vx = U[1] * ir, vy = U[2] * ir, vz = U[3] * ir;
+    const double ke = 0.5 * (U[1] * vx + U[2] * vy + U[3] * vz);
+    const double me = 0.5 * (U[5] * U[5] + U[6] * U[6] + U[7] * U[7]);
+    const double p = gm1 * (U[4] - ke - me);
+    V[0] = rho; V[1] = vx; V[2] = vy; V[3] = vz; V[4] = p;
+    V[5] = U[5]; V[6] = U[6]; V[7] = U[7]; V[8] = U[8];
+    return rho > 0.0 && p > 0.0;
+}
+
+// V(U) of a float64 state in precision R.  R = double: plain float64.
+// R = float: every field rounded by integer splitting, p in double-float,
+// v = m / rho in float32.  Returns status flags.
+template <class R> __device__ __forceinline__ unsigned int prim_of(const double (&U)[NV], const StepArgs &a, R (&V)[NV]);
+
+template <>
+__device__ __forceinline__ unsigned int prim_of<double>(const double (&U)[NV], const StepArgs &a, double (&V)[NV])
+{
+    return prim_from_cons64(U, a.gam - 1.0, V) ? 0u : state_flags(V[0], V[4]);
+}
+
+template <>
+__device__ __forceinline__ unsigned int prim_of<float>(const double (&U)[NV], const StepArgs &a, float (&V)[NV])
+{
+    float r[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const df s = df_split(U[q]);
+        r[q] = s.hi + s.lo;
+    }
+    const float p = df_pressure(U, a.gm1f);
+    const float ir = 1.0f / r[0];
+    V[0] = r[0]; V[1] = r[1] * ir; V[2] = r[2] * ir; V[3] = r[3] * ir; V[4] = p;
+    V[5] = r[5]; V[6] = r[6]; V[7] = r[7]; V[8] = r[8];
+    unsigned int f = 0;
+    if (!(r[0] > 0.0f) || !(p > 0.0f)) f |= ST_NEG;
+    if (!isfinite(r[0]) || !isfinite(p)) f |= ST_NAN;
+    return f;
+}
+
+// R -> float64 for the update accumulation (integer widening for float).
+template <class R> __device__ __forceinline__ double widen(R x);
+template <> __device__ __forceinline__ double widen<double>(double x) { return x; }
+template <> __device__ __forceinline__ double widen<float>(float x) { return f2d_int(x); }
+
+// ---------------------------------------------------------------- per-cell pieces
+
+// Half-step transverse increments dt/2 sum_{d' != D} L^n_d' at cell c (global
+// order) from the first-order fluxes (F1 at a cell = its upper face).
+template <class R, int D>
+__device__ __forceinline__ void transverse(const StepArgs &a, const DevPatch &P, const R *F1, long long c, R hdt,
+                                           R (&T)[NV])
+{
+#pragma unroll
+    for (int q = 0; q < NV; ++q) T[q] = R(0);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        if (e == D || e >= a.ndim) continue;
+        const R *Fe = F1 + (long long)e * NV * a.sstride;
+        const int st = dstr(P, e);
+        const R h = hdt * pidx<R>(P, e);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) T[q] += (Fe[q * a.sstride + c - st] - Fe[q * a.sstride + c]) * h;
+    }
+}
+
+// Interface primitive state at n+1/2 from V* (global order) and the
+// half-step transverse increments T (Eq. transv).  IFACE64: U* = U(V*) and
+// U* + T in float64, pressure recovered in float64.  Otherwise the exact
+// increment form p = p* + (Gamma-1)[dE + (rho* v*^2 d_rho - 2 rho* v*.d_m -
+// d_m^2)/(2 rho) - d_B.(B* + d_B/2)] in precision R.
+template <class R, int IFACE64>
+__device__ __forceinline__ unsigned int interface_state(const R (&W)[NV], const R (&T)[NV], const StepArgs &a,
+                                                        R (&out)[NV])
+{
+    if (IFACE64) {
+        const double rho = W[0], vx = W[1], vy = W[2], vz = W[3], p = W[4];
+        const double bx = W[5], by = W[6], bz = W[7];
         double U[NV], V[NV];
+        U[0] = rho + (double)T[0];
+        U[1] = rho * vx + (double)T[1];
+        U[2] = rho * vy + (double)T[2];
+        U[3] = rho * vz + (double)T[3];
+        U[4] = p * a.igm + 0.5 * rho * (vx * vx + vy * vy + vz * vz) + 0.5 * (bx * bx + by * by + bz * bz) +
+               (double)T[4];
+        U[5] = bx + (double)T[5];
+        U[6] = by + (double)T[6];
+        U[7] = bz + (double)T[7];
+        U[8] = (double)W[8] + (double)T[8];
+        const bool ok = prim_from_cons64(U, a.gam - 1.0, V);
 #pragma unroll
-        for (int q = 0; q < NV; ++q) U[q] = a.U[q * a.ustride + P.base + c];
-        bool ok = prim_from_cons64(U, a.gam, V);
-        if (!ok) atomicOr(a.status, state_flags(V[0], V[4]));
-#pragma unroll
-        for (int q = 0; q < NV; ++q) Vs[q * a.sstride + P.soff + c] = (R)V[q];
+        for (int q = 0; q < NV; ++q) out[q] = (R)V[q];
+        return ok ? 0u : state_flags(V[0], V[4]);
+    } else {
+        const R gm1 = pgm1<R>(a);
+        const R rs = W[0];
+        const R rho = rs + T[0];
+        const R irho = R(1) / rho;
+        const R v2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
+        const R vdm = W[1] * T[1] + W[2] * T[2] + W[3] * T[3];
+        const R dm2 = T[1] * T[1] + T[2] * T[2] + T[3] * T[3];
+        const R dke = (rs * v2 * T[0] - R(2) * rs * vdm - dm2) * (R(0.5) * irho);
+        const R dme = -(T[5] * (W[5] + R(0.5) * T[5]) + T[6] * (W[6] + R(0.5) * T[6]) + T[7] * (W[7] + R(0.5) * T[7]));
+        const R p = W[4] + gm1 * (T[4] + dke + dme);
+        out[0] = rho;
+        out[1] = (rs * W[1] + T[1]) * irho;
+        out[2] = (rs * W[2] + T[2]) * irho;
+        out[3] = (rs * W[3] + T[3]) * irho;
+        out[4] = p;
+        out[5] = W[5] + T[5];
+        out[6] = W[6] + T[6];
+        out[7] = W[7] + T[7];
+        out[8] = W[8] + T[8];
+        unsigned int f = 0;
+        if (!(rho > R(0)) || !(p > R(0))) f |= ST_NEG;
+        if (!isfinite(rho) || !isfinite(p)) f |= ST_NAN;
+        return f;
     }
 }
 
-// First-order Godunov fluxes through the upper d-face of cells with
-// c_d in [-1, n_d - 1] and the other active coordinates in [-1, n].
+// Trace one cell along D: stencil (local order) -> interface states (global).
+template <class R, int PPM, int IFACE64, int D>
+__device__ __forceinline__ unsigned int trace_cell(const StepArgs &a, const DevPatch &P, const R (&vs)[5][NV],
+                                                   const R *F1, long long c, R ch, R dtdx, R hdt, R (&Vp)[NV],
+                                                   R (&Vm)[NV])
+{
+    R pl[NV], ml[NV], pg[NV], mg[NV], T[NV];
+    char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind != 0, pl, ml);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        pg[gperm<D>(q)] = pl[q];
+        mg[gperm<D>(q)] = ml[q];
+    }
+    transverse<R, D>(a, P, F1, c, hdt, T);
+    unsigned int f = interface_state<R, IFACE64>(pg, T, a, Vp);
+    f |= interface_state<R, IFACE64>(mg, T, a, Vm);
+    return f;
+}
+
+// n+1/2 flux through a D-face from the left cell's + state and the right
+// cell's - state (both global order); flux returned in global order.
+template <class R, int D>
+__device__ __forceinline__ void face_flux(const R (&Lg)[NV], const R (&Rg)[NV], R gam, R ch, R (&Fg)[NV])
+{
+    R L[NV], Rr[NV], F[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        L[q] = Lg[gperm<D>(q)];
+        Rr[q] = Rg[gperm<D>(q)];
+    }
+    riemann_hlld(L, Rr, gam, ch, F);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Fg[gperm<D>(q)] = F[q];
+}
+
+// Flux-register windows of one face (plane pl normal to D, transverse
+// coordinates ca, cb in increasing dimension order), Eq. (fluxcorr).
+template <class R, int D>
+__device__ __forceinline__ void register_face(const StepArgs &a, int patch, const DevPatch &P, int pl, int ca, int cb,
+                                              const R (&Fg)[NV])
+{
+    const int ws = a.wstart[patch * 3 + D], wc = a.wcount[patch * 3 + D];
+    for (int w = 0; w < wc; ++w) {
+        const DevWindow W = a.win[ws + w];
+        if (W.plane != pl || ca < W.a0 || ca >= W.a1 || cb < W.b0 || cb >= W.b1) continue;
+        constexpr int ea = D == 0 ? 1 : 0, eb = D == 2 ? 1 : 2;
+        const double f = W.weight * a.sp->dt * P.dx[ea] * P.dx[eb];
+        const long long na = W.a1 - W.a0, nb = W.b1 - W.b0;
+        const long long o = W.dst + (long long)(cb - W.b0) * na + (ca - W.a0);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) a.reg[o + q * nb * na] += f * widen<R>(Fg[q]);
+    }
+}
+
+// Final update of one interior cell: U^(n+1) = U^n + dt s, psi source, and
+// the CFL speed of U^(n+1) if requested (returned in R; 0 otherwise).
 template <class R>
-__global__ void k_flux1(StepArgs a, int d, const R *Vs, R *F1)
+__device__ __forceinline__ R finish_cell(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
+                                         double damp, unsigned int &fl)
 {
-    const DevPatch P = a.patches[blockIdx.y];
-    Box b;
+    const double dt = a.sp->dt;
+    double u[NV];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        if (e >= a.ndim) { b.lo[e] = 0; b.ext[e] = 1; }
-        else if (e == d) { b.lo[e] = -1; b.ext[e] = P.n[e] + 1; }
-        else { b.lo[e] = -1; b.ext[e] = P.n[e] + 2; }
+    for (int q = 0; q < NV; ++q) u[q] = fma(dt, widen<R>(s[q]), a.U[q * a.ustride + P.base + cl]);
+    u[8] *= damp;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) a.Uout[q * a.ustride + P.base + cl] = u[q];
+    if (!a.nextmax) return R(0);
+    R V[NV];
+    fl |= prim_of<R>(u, a, V);
+    const R g = pgam<R>(a);
+    R m = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= a.ndim) continue;
+        const int b1 = 5 + (d == 0 ? 1 : 0), b2 = 5 + (d == 2 ? 1 : 2);
+        const R cf = fast_speed(V[0], V[4], V[5 + d], V[b1], V[b2], g);
+        m = fmax(m, (fabs(V[1 + d]) + cf) * pidx<R>(P, d));
     }
-    const R gam = (R)a.gam, ch = (R)a.dtch[1];
-    const long long st = dstride(P, d);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < b.size();
-         t += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        b.coords(t, i, j, k);
-        const long long c = P.soff + cell_of(P, i, j, k);
-        R L[NV], Rr[NV], F[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            L[q] = Vs[perm(d, q) * a.sstride + c];
-            Rr[q] = Vs[perm(d, q) * a.sstride + c + st];
-        }
-        riemann_hlld(L, Rr, gam, ch, F);
-#pragma unroll
-        for (int q = 0; q < NV; ++q) F1[perm(d, q) * a.sstride + c] = F[q];
-    }
+    return m;
 }
 
-// Normal predictor along d plus the transverse correction (Eq. transv):
-// cells with c_d in [-1, n_d], other active coordinates in [0, n-1].
-// Writes the primitive n+1/2 interface states to Vp, Vm.
-//
-// IFACE64 = 1: U* = U(V*) and U^(n+1/2) = U* + dt/2 T formed in float64,
-//   pressure recovered from U^(n+1/2) in float64 (the FP64 path, and the
-//   mixed path's literal variant).
-// IFACE64 = 0 (mixed path): the same state in increment form.  With
-//   d = dt/2 T, rho = rho* + d_rho, m = rho* v* + d_m, B = B* + d_B,
-//     p = p* + (Gamma-1) [ d_E + (rho* v*^2 d_rho - 2 rho* v*.d_m - d_m^2)/(2 rho)
-//                          - d_B.(B* + d_B/2) ],
-//   which equals (Gamma-1)(E - m^2/2rho - B^2/2) exactly but never forms E, so
-//   no catastrophic cancellation occurs and float32 keeps the accuracy the
-//   float32 transverse fluxes allow.
-template <class R, int PPM, int IFACE64>
-__global__ void k_trace(StepArgs a, int d, const R *Vs, const R *F1x, const R *F1y, const R *F1z,
-                        R *Vp, R *Vm)
+// Block maximum of a non-negative value, folded into *out as the bits of a
+// float64 (monotone in the value for non-negative doubles).
+template <class R> __device__ __forceinline__ void block_max_to(R m, unsigned long long *out)
 {
-    const DevPatch P = a.patches[blockIdx.y];
-    Box b;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        if (e >= a.ndim) { b.lo[e] = 0; b.ext[e] = 1; }
-        else if (e == d) { b.lo[e] = -1; b.ext[e] = P.n[e] + 2; }
-        else { b.lo[e] = 0; b.ext[e] = P.n[e]; }
-    }
-    const double dt = a.dtch[0];
-    const R gam = (R)a.gam, ch = (R)a.dtch[1];
-    const R dtdx = (R)(dt / P.dx[d]);
-    const long long st = dstride(P, d);
-    // transverse directions in fixed order
-    int t1 = -1, t2 = -1;
-    for (int e = 0; e < a.ndim; ++e)
-        if (e != d) { if (t1 < 0) t1 = e; else t2 = e; }
-    const R *F1t1 = t1 == 0 ? F1x : (t1 == 1 ? F1y : F1z);
-    const R *F1t2 = t2 == 0 ? F1x : (t2 == 1 ? F1y : F1z);
-    const long long s1 = t1 >= 0 ? dstride(P, t1) : 0, s2 = t2 >= 0 ? dstride(P, t2) : 0;
-    const double ih1 = t1 >= 0 ? 1.0 / P.dx[t1] : 0.0, ih2 = t2 >= 0 ? 1.0 / P.dx[t2] : 0.0;
-    const double igm = 1.0 / (a.gam - 1.0);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < b.size();
-         t += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        b.coords(t, i, j, k);
-        const long long c = P.soff + cell_of(P, i, j, k);
-        R vs[5][NV];
-#pragma unroll
-        for (int m = 0; m < 5; ++m)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) vs[m][q] = Vs[perm(d, q) * a.sstride + c + (m - 2) * st];
-        R Vpl[NV], Vml[NV];
-        char_predict<R, PPM>(vs, gam, ch, dtdx, a.upwind != 0, Vpl, Vml);
-        R Vpg[NV], Vmg[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) { Vpg[perm(d, q)] = Vpl[q]; Vmg[perm(d, q)] = Vml[q]; }
-        unsigned int fl = 0;
-        if (IFACE64) {
-            // transverse increments L^n_d' = (F_(d',-) - F_(d',+)) / dx_d'
-            double T[NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) T[q] = 0.0;
-            if (t1 >= 0) {
-#pragma unroll
-                for (int q = 0; q < NV; ++q)
-                    T[q] += ((double)F1t1[q * a.sstride + c - s1] - (double)F1t1[q * a.sstride + c]) * ih1;
-            }
-            if (t2 >= 0) {
-#pragma unroll
-                for (int q = 0; q < NV; ++q)
-                    T[q] += ((double)F1t2[q * a.sstride + c - s2] - (double)F1t2[q * a.sstride + c]) * ih2;
-            }
-            double Ui[NV], Vi[NV];
-            cons64_from_prim(Vpg, igm, Ui);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) Ui[q] += 0.5 * dt * T[q];
-            if (!prim_from_cons64(Ui, a.gam, Vi)) fl |= state_flags(Vi[0], Vi[4]);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) Vp[q * a.sstride + c] = (R)Vi[q];
-            cons64_from_prim(Vmg, igm, Ui);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) Ui[q] += 0.5 * dt * T[q];
-            if (!prim_from_cons64(Ui, a.gam, Vi)) fl |= state_flags(Vi[0], Vi[4]);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) Vm[q * a.sstride + c] = (R)Vi[q];
-        } else {
-            // half-step transverse increments d = dt/2 T, in R
-            R D[NV];
-            const R h1 = (R)(0.5 * dt * ih1), h2 = (R)(0.5 * dt * ih2);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) D[q] = R(0);
-            if (t1 >= 0) {
-#pragma unroll
-                for (int q = 0; q < NV; ++q) D[q] += (F1t1[q * a.sstride + c - s1] - F1t1[q * a.sstride + c]) * h1;
-            }
-            if (t2 >= 0) {
-#pragma unroll
-                for (int q = 0; q < NV; ++q) D[q] += (F1t2[q * a.sstride + c - s2] - F1t2[q * a.sstride + c]) * h2;
-            }
-            const R gm1 = gam - R(1);
-#pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const R(&W)[NV] = side == 0 ? Vpg : Vmg;
-                R *out = side == 0 ? Vp : Vm;
-                const R rs = W[0];
-                const R rho = rs + D[0];
-                const R irho = R(1) / rho;
-                const R m1 = rs * W[1] + D[1], m2 = rs * W[2] + D[2], m3 = rs * W[3] + D[3];
-                const R v2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
-                const R vdm = W[1] * D[1] + W[2] * D[2] + W[3] * D[3];
-                const R dm2 = D[1] * D[1] + D[2] * D[2] + D[3] * D[3];
-                const R dke = (rs * v2 * D[0] - R(2) * rs * vdm - dm2) * (R(0.5) * irho);
-                const R dme = -(D[5] * (W[5] + R(0.5) * D[5]) + D[6] * (W[6] + R(0.5) * D[6]) +
-                                D[7] * (W[7] + R(0.5) * D[7]));
-                const R p = W[4] + gm1 * (D[4] + dke + dme);
-                out[0 * a.sstride + c] = rho;
-                out[1 * a.sstride + c] = m1 * irho;
-                out[2 * a.sstride + c] = m2 * irho;
-                out[3 * a.sstride + c] = m3 * irho;
-                out[4 * a.sstride + c] = p;
-                out[5 * a.sstride + c] = W[5] + D[5];
-                out[6 * a.sstride + c] = W[6] + D[6];
-                out[7 * a.sstride + c] = W[7] + D[7];
-                out[8 * a.sstride + c] = W[8] + D[8];
-                if (!(rho > R(0)) || !(p > R(0))) fl |= ST_NEG;
-                if (!isfinite(rho) || !isfinite(p)) fl |= ST_NAN;
-            }
-        }
-        if (fl) atomicOr(a.status, fl);
-    }
-}
-
-// n+1/2 fluxes through the upper d-face of cells c_d in [-1, n_d - 1].
-template <class R>
-__global__ void k_riemann(StepArgs a, int d, const R *Vp, const R *Vm, R *Fd)
-{
-    const DevPatch P = a.patches[blockIdx.y];
-    Box b;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        if (e >= a.ndim) { b.lo[e] = 0; b.ext[e] = 1; }
-        else if (e == d) { b.lo[e] = -1; b.ext[e] = P.n[e] + 1; }
-        else { b.lo[e] = 0; b.ext[e] = P.n[e]; }
-    }
-    const R gam = (R)a.gam, ch = (R)a.dtch[1];
-    const long long st = dstride(P, d);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < b.size();
-         t += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        b.coords(t, i, j, k);
-        const long long c = P.soff + cell_of(P, i, j, k);
-        R L[NV], Rr[NV], F[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            L[q] = Vp[perm(d, q) * a.sstride + c];
-            Rr[q] = Vm[perm(d, q) * a.sstride + c + st];
-        }
-        riemann_hlld(L, Rr, gam, ch, F);
-#pragma unroll
-        for (int q = 0; q < NV; ++q) Fd[perm(d, q) * a.sstride + c] = F[q];
-    }
-}
-
-// U^(n+1) = U^n + dt (L_x + L_y + L_z) on interior cells, then the psi
-// source -(c_h^2/c_p^2) psi integrated exactly (operator split).
-template <class R>
-__global__ void k_update(StepArgs a, const R *Fx, const R *Fy, const R *Fz)
-{
-    const DevPatch P = a.patches[blockIdx.y];
-    Box b;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) { b.lo[e] = 0; b.ext[e] = P.n[e]; }
-    __shared__ double s_damp, s_idx[3];
-    const double dt = a.dtch[0];
-    if (threadIdx.x == 0) {
-        double hmin = P.dx[0];
-        for (int e = 1; e < a.ndim; ++e) hmin = fmin(hmin, P.dx[e]);
-        s_damp = exp(-a.glm_alpha * a.dtch[1] * dt / hmin);
-        for (int e = 0; e < 3; ++e) s_idx[e] = 1.0 / P.dx[e];
-    }
-    __syncthreads();
-    const double damp = s_damp;
-    const R *F[3] = {Fx, Fy, Fz};
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < b.size();
-         t += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        b.coords(t, i, j, k);
-        const long long cl = cell_of(P, i, j, k);
-        const long long c = P.soff + cl;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            // flux divergence in R (float64 on the FP64 path), accumulation in float64
-            R s = R(0);
-            for (int d = 0; d < a.ndim; ++d) {
-                const long long st = dstride(P, d);
-                s += (F[d][q * a.sstride + c - st] - F[d][q * a.sstride + c]) * (R)s_idx[d];
-            }
-            double u = a.U[q * a.ustride + P.base + cl] + dt * (double)s;
-            if (q == 8) u *= damp;
-            a.Uout[q * a.ustride + P.base + cl] = u;
-        }
-    }
-}
-
-// Flux-register windows, Eq. (fluxcorr): one thread per (window face, var).
-template <class R>
-__global__ void k_registers(StepArgs a, const DevWindow *win, int nwin, const R *Fx, const R *Fy,
-                            const R *Fz, double *reg)
-{
-    const int w = blockIdx.y;
-    if (w >= nwin) return;
-    const DevWindow W = win[w];
-    if (W.patch >= a.npatch) return;
-    const DevPatch P = a.patches[W.patch];
-    const int d = W.dir;
-    const int ea = d == 0 ? 1 : 0, eb = d == 2 ? 1 : 2;
-    const long long na = W.a1 - W.a0, nb = W.b1 - W.b0;
-    const double area = P.dx[ea] * P.dx[eb];
-    const double f = W.weight * a.dtch[0] * area;
-    const R *F = d == 0 ? Fx : (d == 1 ? Fy : Fz);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < NV * na * nb;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(t / (na * nb));
-        const long long r = t % (na * nb);
-        int c3[3];
-        c3[d] = W.plane - 1;
-        c3[ea] = W.a0 + (int)(r % na);
-        c3[eb] = W.b0 + (int)(r / na);
-        const long long c = P.soff + cell_of(P, c3[0], c3[1], c3[2]);
-        reg[W.dst + t] += f * (double)F[q * a.sstride + c];
-    }
-}
-
-// Max over interior cells of max_d (|v_d| + c_f,d)/dx_d, as the bits of a
-// positive double (monotone in the value) -> atomicMax.
-template <class R>
-__global__ void k_maxspeed(StepArgs a, unsigned long long *out)
-{
-    const DevPatch P = a.patches[blockIdx.y];
-    Box b;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) { b.lo[e] = 0; b.ext[e] = P.n[e]; }
-    double m = 0.0;
-    const double idx[3] = {1.0 / P.dx[0], 1.0 / P.dx[1], 1.0 / P.dx[2]};
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < b.size();
-         t += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        b.coords(t, i, j, k);
-        const long long cl = cell_of(P, i, j, k);
-        double U[NV], V[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) U[q] = a.U[q * a.ustride + P.base + cl];
-        if (!prim_from_cons64(U, a.gam, V)) atomicOr(a.status, state_flags(V[0], V[4]));
-        const R rho = (R)V[0], p = (R)V[4], g = (R)a.gam;
-        for (int d = 0; d < a.ndim; ++d) {
-            const int qn = 1 + d, bn = 5 + d;
-            const int b1 = 5 + (d == 0 ? 1 : 0), b2 = 5 + (d == 2 ? 1 : 2);
-            const R cf = fast_speed(rho, p, (R)V[bn], (R)V[b1], (R)V[b2], g);
-            const R sp = (fabs((R)V[qn]) + cf) * (R)idx[d];
-            m = fmax(m, (double)sp);
-        }
-    }
-    // warp + block reduction
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    __shared__ double sm[32];
+    __shared__ R sm[BLOCK / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) sm[wid] = m;
     __syncthreads();
     if (wid == 0) {
-        m = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0.0;
+        m = lane < BLOCK / 32 ? sm[lane] : R(0);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+        if (lane == 0 && m > R(0)) atomicMax(out, (unsigned long long)__double_as_longlong(widen<R>(m)));
     }
+}
+
+__device__ __forceinline__ double patch_damp(const StepArgs &a, const DevPatch &P)
+{
+    __shared__ double s_damp;
+    if (threadIdx.x == 0) s_damp = exp(-a.glm_alpha * a.sp->ch * a.sp->dt / P.hmin);
+    __syncthreads();
+    return s_damp;
+}
+
+// Thread tile of a block: BLOCK threads as xw lanes along x times BLOCK/xw rows.
+struct Tile {
+    int xw, rows;
+    __device__ __forceinline__ explicit Tile(int nx)
+    {
+        xw = tile_xw(nx);
+        rows = BLOCK / xw;
+    }
+    __device__ __forceinline__ int tx() const { return threadIdx.x % xw; }
+    __device__ __forceinline__ int ty() const { return threadIdx.x / xw; }
+};
+
+// Host mirror of the kernels' block counts per patch (same tiling).
+struct Tiles {
+    static int xw(int nx) { return tile_xw(nx); }
+    static long long prim(const int *n, const int *N)
+    {
+        const int w = xw(n[0]), r = BLOCK / w;
+        return (long long)((N[0] + w - 1) / w) * ((N[1] + r - 1) / r) * N[2];
+    }
+    static long long flux1(const int *n, int ndim, int D)
+    {
+        int ext[3];
+        for (int e = 0; e < 3; ++e) ext[e] = e >= ndim ? 1 : (e == D ? n[e] + 1 : n[e] + 2);
+        const int w = xw(n[0]), r = BLOCK / w;
+        return (long long)((ext[0] + w - 1) / w) * ((ext[1] + r - 1) / r) * ext[2];
+    }
+    static long long sweep_x(const int *n)
+    {
+        const int w = xw(n[0]), r = BLOCK / w;
+        return (long long)((n[0] + w - 3) / (w - 2)) * ((n[1] + r - 1) / r) * n[2];
+    }
+    static long long sweep_m(const int *n, int D)
+    {
+        const int O = D == 1 ? 2 : 1;
+        const int w = xw(n[0]), r = BLOCK / w;
+        const long long nseg = (n[D] + SEG - 1) / SEG;
+        return (long long)((n[0] + w - 1) / w) * ((n[O] * nseg + r - 1) / r);
+    }
+    static long long interior(const int *n)
+    {
+        const int w = xw(n[0]), r = BLOCK / w;
+        return (long long)((n[0] + w - 1) / w) * ((n[1] + r - 1) / r) * n[2];
+    }
+};
+
+// ---------------------------------------------------------------- kernels
+
+static __global__ void k_setup(const double *dtch, StepParams *sp)
+{
+    const double dt = dtch[0], ch = dtch[1];
+    sp->dt = dt;
+    sp->ch = ch;
+    sp->dtf = (float)dt;
+    sp->chf = (float)ch;
+}
+
+// V = V(U) on every ghosted cell; blockIdx.y = patch (within the group).
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, int first, R *Vs)
+{
+    const DevPatch P = a.patches[first + blockIdx.y];
+    const Tile t(P.n[0]);
+    const int T0 = (P.N[0] + t.xw - 1) / t.xw, T1 = (P.N[1] + t.rows - 1) / t.rows;
+    const int b = blockIdx.x;
+    const int gi = (b % T0) * t.xw + t.tx();
+    const int gj = ((b / T0) % T1) * t.rows + t.ty();
+    const int gk = b / (T0 * T1);
+    if (gi >= P.N[0] || gj >= P.N[1] || gk >= P.N[2]) return;
+    const int c = (gk * P.N[1] + gj) * P.N[0] + gi;
+    double U[NV];
+    R V[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) U[q] = a.U[q * a.ustride + P.base + c];
+    const unsigned int f = prim_of<R>(U, a, V);
+    if (f) atomicOr(a.status, f);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Vs[q * a.sstride + P.soff + c] = V[q];
+}
+
+// First-order fluxes through the upper D-face of cells with c_D in
+// [-1, n_D - 1] and the other active coordinates in [-1, n].
+template <class R, int D>
+__global__ void __launch_bounds__(BLOCK) k_flux1(StepArgs a, int first, const R *Vs, R *F1)
+{
+    const DevPatch P = a.patches[first + blockIdx.y];
+    int lo[3], ext[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        if (e >= a.ndim) { lo[e] = 0; ext[e] = 1; }
+        else if (e == D) { lo[e] = -1; ext[e] = P.n[e] + 1; }
+        else { lo[e] = -1; ext[e] = P.n[e] + 2; }
+    }
+    const Tile t(P.n[0]);
+    const int T0 = (ext[0] + t.xw - 1) / t.xw, T1 = (ext[1] + t.rows - 1) / t.rows;
+    const int b = blockIdx.x;
+    const int i = (b % T0) * t.xw + t.tx(), j = ((b / T0) % T1) * t.rows + t.ty(), k = b / (T0 * T1);
+    if (i >= ext[0] || j >= ext[1] || k >= ext[2]) return;
+    const long long c = P.soff + lcell(P, lo[0] + i, lo[1] + j, lo[2] + k);
+    const int st = dstr(P, D);
+    R L[NV], Rr[NV], F[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        L[q] = Vs[gperm<D>(q) * a.sstride + c];
+        Rr[q] = Vs[gperm<D>(q) * a.sstride + c + st];
+    }
+    riemann_hlld(L, Rr, pgam<R>(a), pch<R>(a.sp), F);
+    R *Fd = F1 + (long long)D * NV * a.sstride;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Fd[gperm<D>(q) * a.sstride + c] = F[q];
+}
+
+// Sweep along x, one thread per traced cell.  A tile covers xw traced cells
+// (xw - 2 updated cells) along x times BLOCK/xw rows along y.
+template <class R, int PPM, int IFACE64, int LAST>
+__global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const R *Vs, const R *F1, R *A)
+{
+    const int patch = first + blockIdx.y;
+    const DevPatch P = a.patches[patch];
+    const Tile t(P.n[0]);
+    const int out_x = t.xw - 2;
+    const int T0 = (P.n[0] + out_x - 1) / out_x, T1 = (P.n[1] + t.rows - 1) / t.rows;
+    const int b = blockIdx.x;
+    const int tx = t.tx(), ty = t.ty();
+    const int i = (b % T0) * out_x - 1 + tx;  // traced cell, >= -1
+    const int j = ((b / T0) % T1) * t.rows + ty;
+    const int k = b / (T0 * T1);
+    const bool traced = j < P.n[1] && k < P.n[2] && i <= P.n[0];
+    __shared__ R sP[BLOCK][NV], sM[BLOCK][NV], sF[BLOCK][NV];
+    const int me = threadIdx.x;
+    const R gam = pgam<R>(a), ch = pch<R>(a.sp);
+    const R dtdx = pdt<R>(a.sp) * pidx<R>(P, 0);
+    const R hdt = R(0.5) * pdt<R>(a.sp);
+    unsigned int fl = 0;
+    const long long c = traced ? P.soff + lcell(P, i, j, k) : 0;
+    if (traced) {
+        R vs[5][NV];
+#pragma unroll
+        for (int m = 0; m < 5; ++m)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) vs[m][q] = Vs[q * a.sstride + c + (m - 2)];
+        R Vp[NV], Vm[NV];
+        fl |= trace_cell<R, PPM, IFACE64, 0>(a, P, vs, F1, c, ch, dtdx, hdt, Vp, Vm);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { sP[me][q] = Vp[q]; sM[me][q] = Vm[q]; }
+    }
+    __syncthreads();
+    if (traced && tx < t.xw - 1 && i <= P.n[0] - 1) {
+        R L[NV], Rr[NV], F[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { L[q] = sP[me][q]; Rr[q] = sM[me + 1][q]; }
+        face_flux<R, 0>(L, Rr, gam, ch, F);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sF[me][q] = F[q];
+        // faces on plane i+1; the tile's last face belongs to the next tile
+        if (a.reg && (tx < t.xw - 2 || i + 1 == P.n[0])) register_face<R, 0>(a, patch, P, i + 1, j, k, F);
+    }
+    const bool out = traced && tx >= 1 && tx <= t.xw - 2 && i >= 0 && i < P.n[0];
+    if (LAST) {
+        const double damp = patch_damp(a, P);  // includes a block barrier
+        R m = R(0);
+        if (out) {
+            const R ix = pidx<R>(P, 0);
+            R s[NV];
+            const int cl = lcell(P, i, j, k);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) s[q] = (sF[me - 1][q] - sF[me][q]) * ix;
+            m = finish_cell<R>(a, P, cl, s, damp, fl);
+        }
+        if (a.nextmax) block_max_to<R>(m, a.nextmax);
+    } else {
+        __syncthreads();
+        if (out) {
+            const R ix = pidx<R>(P, 0);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) A[q * a.sstride + c] = (sF[me - 1][q] - sF[me][q]) * ix;
+        }
+    }
+    if (fl) atomicOr(a.status, fl);
+}
+
+// Sweep along D = 1 (y) or 2 (z): each thread marches one segment of SEG
+// cells along D; the 5-cell stencil, the previous cell's + state and the
+// previous face flux stay in registers.  A tile: xw lanes along x times
+// BLOCK/xw (other-dimension, segment) pairs.
+template <class R, int PPM, int IFACE64, int D, int LAST>
+__global__ void __launch_bounds__(BLOCK) k_sweep_m(StepArgs a, int first, const R *Vs, const R *F1, R *A)
+{
+    constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
+    const int patch = first + blockIdx.y;
+    const DevPatch P = a.patches[patch];
+    const Tile t(P.n[0]);
+    const int nD = P.n[D], nO = P.n[O];
+    const int nseg = (nD + SEG - 1) / SEG;
+    const int T0 = (P.n[0] + t.xw - 1) / t.xw;
+    const int b = blockIdx.x;
+    const int x = (b % T0) * t.xw + t.tx();
+    const int comb = (b / T0) * t.rows + t.ty();
+    const int o = comb / nseg, seg = comb % nseg;
+    const bool ok = x < P.n[0] && o < nO;
+    const R gam = pgam<R>(a), ch = pch<R>(a.sp);
+    const R dtdx = pdt<R>(a.sp) * pidx<R>(P, D);
+    const R hdt = R(0.5) * pdt<R>(a.sp);
+    const R iD = pidx<R>(P, D);
+    double damp = 1.0;
+    if (LAST) damp = patch_damp(a, P);
+    unsigned int fl = 0;
+    R mx = R(0);
+    if (ok) {
+        const int j0 = seg * SEG, j1 = min(j0 + SEG, nD);
+        const int st = dstr(P, D);
+        int cc[3];
+        cc[0] = x;
+        cc[O] = o;
+        cc[D] = j0 - 1;
+        long long c = P.soff + lcell(P, cc[0], cc[1], cc[2]);  // traced cell j0 - 1
+        R win[5][NV];
+#pragma unroll
+        for (int m = 0; m < 5; ++m)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) win[m][q] = Vs[gperm<D>(q) * a.sstride + c + (m - 2) * st];
+        R Pprev[NV], Fprev[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { Pprev[q] = R(0); Fprev[q] = R(0); }
+        for (int j = j0 - 1; j <= j1; ++j, c += st) {
+            // prefetch what the next iteration reads: V(j+3), the transverse
+            // first-order fluxes of cell j+1, the running sum (and the state)
+            // of cell j
+            if (j < j1) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) prefetch_l1(Vs + gperm<D>(q) * a.sstride + c + 3 * st);
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    if (e == D || e >= a.ndim) continue;
+                    const R *Fe = F1 + (long long)e * NV * a.sstride + c + st;
+                    const int se = dstr(P, e);
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        prefetch_l1(Fe + q * a.sstride);
+                        prefetch_l1(Fe + q * a.sstride - se);
+                    }
+                }
+                if (j >= j0) {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) prefetch_l1(A + q * a.sstride + c);
+                    if (LAST) {
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) prefetch_l1(a.U + q * a.ustride + P.base + (c - P.soff));
+                    }
+                }
+            }
+            if (j > j0 - 1) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) win[m][q] = win[m + 1][q];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) win[4][q] = Vs[gperm<D>(q) * a.sstride + c + 2 * st];
+            }
+            R Vp[NV], Vm[NV];
+            fl |= trace_cell<R, PPM, IFACE64, D>(a, P, win, F1, c, ch, dtdx, hdt, Vp, Vm);
+            if (j >= j0) {
+                R F[NV];
+                face_flux<R, D>(Pprev, Vm, gam, ch, F);
+                // plane j; (a, b) = (x, o) are the two non-D dimensions in
+                // increasing order; a segment's last face belongs to the next
+                if (a.reg && (j < j1 || j1 == nD)) register_face<R, D>(a, patch, P, j, x, o, F);
+                if (j >= j0 + 1) {
+                    const long long cp = c - st;  // cell j - 1
+                    R s[NV];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) s[q] = (Fprev[q] - F[q]) * iD;
+                    if (LAST) {
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) s[q] = A[q * a.sstride + cp] + s[q];
+                        mx = fmax(mx, finish_cell<R>(a, P, (int)(cp - P.soff), s, damp, fl));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) A[q * a.sstride + cp] += s[q];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < NV; ++q) Fprev[q] = F[q];
+            }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Pprev[q] = Vp[q];
+        }
+    }
+    if (LAST && a.nextmax) block_max_to<R>(mx, a.nextmax);
+    if (fl) atomicOr(a.status, fl);
+}
+
+// ctu_dt: max over interior cells of max_d (|v_d| + c_f,d)/dx_d.
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, int first, unsigned long long *out)
+{
+    const DevPatch P = a.patches[first + blockIdx.y];
+    const Tile t(P.n[0]);
+    const int T0 = (P.n[0] + t.xw - 1) / t.xw, T1 = (P.n[1] + t.rows - 1) / t.rows;
+    const int b = blockIdx.x;
+    const int i = (b % T0) * t.xw + t.tx(), j = ((b / T0) % T1) * t.rows + t.ty(), k = b / (T0 * T1);
+    R m = R(0);
+    if (i < P.n[0] && j < P.n[1] && k < P.n[2]) {
+        const int cl = lcell(P, i, j, k);
+        double U[NV];
+        R V[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) U[q] = a.U[q * a.ustride + P.base + cl];
+        const unsigned int f = prim_of<R>(U, a, V);
+        if (f) atomicOr(a.status, f);
+        const R g = pgam<R>(a);
+        R mm = R(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= a.ndim) continue;
+            const int b1 = 5 + (d == 0 ? 1 : 0), b2 = 5 + (d == 2 ? 1 : 2);
+            const R cf = fast_speed(V[0], V[4], V[5 + d], V[b1], V[b2], g);
+            mm = fmax(mm, (fabs(V[1 + d]) + cf) * pidx<R>(P, d));
+        }
+        m = mm;
+    }
+    block_max_to<R>(m, out);
 }
 
 } // namespace ctu

@@ -1,84 +1,104 @@
-// ctu_launch.cuh -- launcher templates, instantiated per precision.
+// ctu_launch.cuh -- launcher templates, instantiated per precision and
+// interface mode by ctu_f64.cu, ctu_f32.cu and ctu_f32i.cu.
 #pragma once
 
 #include "ctu_launch.h"
 
 namespace ctu {
 
-static inline dim3 grid_for(long long cells, int npatch, int block)
-{
-    long long bx = (cells + block - 1) / block;
-    if (bx > (1LL << 20)) bx = 1LL << 20;
-    if (bx < 1) bx = 1;
-    return dim3((unsigned)bx, (unsigned)npatch, 1);
-}
+#define CTU_MARK(nm) \
+    if (li.prof) li.prof->mark(nm, s)
 
-template <class R> int launch_step(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
+template <class R, int PPM, int IF64>
+static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     const long long S = a.sstride;
     R *base = (R *)li.scratch;
     R *Vs = base;
-    R *F1[3] = {base + 9 * S, base + 18 * S, base + 27 * S};
-    R *Vp = base + 36 * S;
-    R *Vm = base + 45 * S;
-    R *F[3] = {base + 54 * S, base + 63 * S, base + 72 * S};
-    const int B = 128;
-    const dim3 g = grid_for(li.max_cells, a.npatch, B);
-    ProfHook *P = li.prof;
-#define MARK(nm) \
-    if (P) P->mark(nm, s)
+    R *F1 = base + 9 * S;
+    R *A = base + 36 * S;
     int n = 0;
-    MARK("prim");
-    k_prim<R><<<g, B, 0, s>>>(a, Vs);
-    MARK(nullptr);
+    CTU_MARK("setup");
+    k_setup<<<1, 1, 0, s>>>(a.dtch, li.sp);
+    CTU_MARK(nullptr);
     ++n;
-    for (int d = 0; d < a.ndim; ++d) {
-        MARK("flux1");
-        k_flux1<R><<<g, B, 0, s>>>(a, d, Vs, F1[d]);
-        MARK(nullptr);
+    CTU_MARK("prim");
+    for (int g = 0; g < li.ngroups; ++g) {
+        const Group &G = li.groups[g];
+        k_prim<R><<<dim3((unsigned)Tiles::prim(G.n, G.N), (unsigned)G.count), BLOCK, 0, s>>>(a, G.first, Vs);
         ++n;
     }
-    for (int d = 0; d < a.ndim; ++d) {
-        MARK("trace");
-        constexpr bool is64 = sizeof(R) == 8;
-        if (li.recon && (is64 || li.iface64))
-            k_trace<R, 1, 1><<<g, B, 0, s>>>(a, d, Vs, F1[0], F1[1], F1[2], Vp, Vm);
-        else if (li.recon)
-            k_trace<R, 1, is64 ? 1 : 0><<<g, B, 0, s>>>(a, d, Vs, F1[0], F1[1], F1[2], Vp, Vm);
-        else if (is64 || li.iface64)
-            k_trace<R, 0, 1><<<g, B, 0, s>>>(a, d, Vs, F1[0], F1[1], F1[2], Vp, Vm);
+    CTU_MARK(nullptr);
+    CTU_MARK("flux1");
+    for (int g = 0; g < li.ngroups; ++g) {
+        const Group &G = li.groups[g];
+        const unsigned c = (unsigned)G.count;
+        k_flux1<R, 0><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 0), c), BLOCK, 0, s>>>(a, G.first, Vs, F1);
+        ++n;
+        if (a.ndim > 1) {
+            k_flux1<R, 1><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 1), c), BLOCK, 0, s>>>(a, G.first, Vs, F1);
+            ++n;
+        }
+        if (a.ndim > 2) {
+            k_flux1<R, 2><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 2), c), BLOCK, 0, s>>>(a, G.first, Vs, F1);
+            ++n;
+        }
+    }
+    CTU_MARK(nullptr);
+    CTU_MARK("sweep_x");
+    for (int g = 0; g < li.ngroups; ++g) {
+        const Group &G = li.groups[g];
+        const dim3 grid((unsigned)Tiles::sweep_x(G.n), (unsigned)G.count);
+        if (a.ndim == 1)
+            k_sweep_x<R, PPM, IF64, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
         else
-            k_trace<R, 0, is64 ? 1 : 0><<<g, B, 0, s>>>(a, d, Vs, F1[0], F1[1], F1[2], Vp, Vm);
-        MARK(nullptr);
-        MARK("riemann");
-        k_riemann<R><<<g, B, 0, s>>>(a, d, Vp, Vm, F[d]);
-        MARK(nullptr);
-        n += 2;
-    }
-    MARK("update");
-    k_update<R><<<g, B, 0, s>>>(a, F[0], F[1], F[2]);
-    MARK(nullptr);
-    ++n;
-    if (li.nwin > 0 && li.reg) {
-        MARK("registers");
-        k_registers<R><<<dim3(8, (unsigned)li.nwin, 1), 256, 0, s>>>(a, li.win, li.nwin, F[0], F[1], F[2],
-                                                                     li.reg);
-        MARK(nullptr);
+            k_sweep_x<R, PPM, IF64, 0><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
         ++n;
     }
-#undef MARK
+    CTU_MARK(nullptr);
+    if (a.ndim > 1) {
+        CTU_MARK("sweep_y");
+        for (int g = 0; g < li.ngroups; ++g) {
+            const Group &G = li.groups[g];
+            const dim3 grid((unsigned)Tiles::sweep_m(G.n, 1), (unsigned)G.count);
+            if (a.ndim == 2)
+                k_sweep_m<R, PPM, IF64, 1, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+            else
+                k_sweep_m<R, PPM, IF64, 1, 0><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+            ++n;
+        }
+        CTU_MARK(nullptr);
+    }
+    if (a.ndim > 2) {
+        CTU_MARK("sweep_z");
+        for (int g = 0; g < li.ngroups; ++g) {
+            const Group &G = li.groups[g];
+            const dim3 grid((unsigned)Tiles::sweep_m(G.n, 2), (unsigned)G.count);
+            k_sweep_m<R, PPM, IF64, 2, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+            ++n;
+        }
+        CTU_MARK(nullptr);
+    }
     return n;
 }
 
-template <class R>
-int launch_maxspeed(const StepArgs &a, long long max_cells, unsigned long long *out, cudaStream_t s,
-                    ProfHook *prof)
+template <class R, int IF64> int launch_step_impl(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
-    const int B = 256;
-    if (prof) prof->mark("maxspeed", s);
-    k_maxspeed<R><<<grid_for(max_cells, a.npatch, B), B, 0, s>>>(a, out);
-    if (prof) prof->mark(nullptr, s);
-    return 1;
+    return li.recon ? launch_step_t<R, 1, IF64>(a, li, s) : launch_step_t<R, 0, IF64>(a, li, s);
 }
+
+template <class R>
+int launch_maxspeed_impl(const StepArgs &a, const LaunchInfo &li, unsigned long long *out, cudaStream_t s)
+{
+    CTU_MARK("maxspeed");
+    for (int g = 0; g < li.ngroups; ++g) {
+        const Group &G = li.groups[g];
+        k_maxspeed<R><<<dim3((unsigned)Tiles::interior(G.n), (unsigned)G.count), BLOCK, 0, s>>>(a, G.first, out);
+    }
+    CTU_MARK(nullptr);
+    return li.ngroups;
+}
+
+#undef CTU_MARK
 
 } // namespace ctu

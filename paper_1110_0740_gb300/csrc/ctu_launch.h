@@ -7,8 +7,9 @@
 
 namespace ctu {
 
-// Scratch elements of type R needed per unit of scratch stride.
-constexpr int SCRATCH_ARRAYS = 9 /*V*/ + 27 /*F1*/ + 18 /*Vp,Vm*/ + 27 /*F*/;
+// Scratch words (of the working precision) per unit of scratch stride:
+// V (9), first-order fluxes F^n (3 x 9), running sum A = L_x (+ L_y) (9).
+constexpr int SCRATCH_ARRAYS = 9 + 27 + 9;
 
 // Optional per-kernel timing hook: mark(name) is called right before a
 // launch and mark(nullptr) right after it, on the same stream.
@@ -17,19 +18,30 @@ struct ProfHook {
     virtual ~ProfHook() {}
 };
 
-struct LaunchInfo {
-    long long max_cells;   // largest ghosted patch
-    int recon;             // 0 linear, 1 PPM
-    const DevWindow *win;  // device windows (may be null)
-    int nwin;
-    double *reg;
-    void *scratch;         // SCRATCH_ARRAYS * sstride elements of R
-    ProfHook *prof;        // may be null
-    int iface64;           // mixed path: 1 = float64 interface-state recovery
+// Patches of identical shape, contiguous in the device patch table: each
+// kernel is launched once per group with blockIdx.y = patch in the group.
+struct Group {
+    int first, count;
+    int n[3], N[3];
 };
 
+struct LaunchInfo {
+    const Group *groups;   // host array
+    int ngroups;
+    int recon;             // 0 linear, 1 PPM
+    int iface64;           // mixed path: 1 = float64 interface-state recovery
+    void *scratch;         // SCRATCH_ARRAYS * sstride elements of R
+    StepParams *sp;        // device per-step parameters
+    ProfHook *prof;        // may be null
+};
+
+// Enqueue one CTU step; returns the number of kernel launches.
 template <class R> int launch_step(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
-template <class R> int launch_maxspeed(const StepArgs &a, long long max_cells, unsigned long long *out,
-                                       cudaStream_t s, ProfHook *prof);
+// Enqueue the CFL reduction of ctu_dt into *out.
+template <class R> int launch_maxspeed(const StepArgs &a, const LaunchInfo &li, unsigned long long *out,
+                                       cudaStream_t s);
+
+// Per-(precision, interface-mode) instantiations, one translation unit each.
+template <class R, int IF64> int launch_step_impl(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
 
 } // namespace ctu

@@ -13,8 +13,8 @@
 //
 // Limits: at most CTU_NOALLOC_MAX_PATCHES patches and CTU_NOALLOC_SCRATCH_BYTES
 // of scratch (the sum over patches of the ghosted cell count, each rounded
-// up to 32 cells, times 81 words of 8 bytes for CTU_FP64 or 4 bytes for the
-// mixed modes: one 32^3 patch in FP64, or one 40^3 patch in mixed precision).
+// up to 32 cells, times 45 words of 8 bytes for CTU_FP64 or 4 bytes for the
+// mixed modes: one 40^3 patch in FP64, or one 56^3 patch in mixed precision).
 // The array occupies CTU_NOALLOC_SCRATCH_BYTES (plus a few KB) on every GPU
 // that loads the library, until the process exits.
 #include <cuda_runtime.h>
@@ -29,7 +29,7 @@ using namespace ctu;
 
 namespace {
 
-constexpr size_t kHeadBytes = 256;  // status word, padded
+constexpr size_t kHeadBytes = 256;  // status word at 0, per-step parameters at 64
 constexpr size_t kTableBytes = (sizeof(DevPatch) * CTU_NOALLOC_MAX_PATCHES + 255) / 256 * 256;
 constexpr size_t kScratchBytes = (size_t)CTU_NOALLOC_SCRATCH_BYTES;
 constexpr size_t kTotalBytes = kHeadBytes + kTableBytes + kScratchBytes;
@@ -78,27 +78,39 @@ extern "C" ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in
     if (npatch <= 0) return CTU_EINVAL;
     if (npatch > CTU_NOALLOC_MAX_PATCHES) return CTU_ETOOLARGE;
 
-    // Patch table on the stack (no heap use) and the scratch it needs.
+    // Patch table and launch groups on the stack (no heap use), and the
+    // scratch they need.  Each patch is its own launch group.
     DevPatch table[CTU_NOALLOC_MAX_PATCHES];
-    long long off = 0, maxc = 0;
+    Group groups[CTU_NOALLOC_MAX_PATCHES];
+    long long off = 0;
     for (int i = 0; i < npatch; ++i) {
         DevPatch &q = table[i];
         long long cells = 1;
+        q.hmin = 1e300;
         for (int d = 0; d < 3; ++d) {
             const int g = d < cfg->ndim ? 4 : 0;
-            if (patches[i].n[d] < 1 || (d >= cfg->ndim && patches[i].n[d] != 1) || !(patches[i].dx[d] > 0.0))
+            if (patches[i].n[d] < 1 || patches[i].n[d] > 4096 || (d >= cfg->ndim && patches[i].n[d] != 1) ||
+                !(patches[i].dx[d] > 0.0))
                 return CTU_EINVAL;
             q.n[d] = patches[i].n[d];
             q.g[d] = g;
             q.N[d] = q.n[d] + 2 * g;
             q.dx[d] = patches[i].dx[d];
+            q.idx[d] = 1.0 / q.dx[d];
+            q.idxf[d] = (float)q.idx[d];
+            if (d < cfg->ndim && q.dx[d] < q.hmin) q.hmin = q.dx[d];
             cells *= q.N[d];
         }
         if (patches[i].base < 0 || patches[i].base + cells > stride) return CTU_EINVAL;
         q.base = patches[i].base;
         q.soff = off;
         off += (cells + 31) / 32 * 32;
-        if (cells > maxc) maxc = cells;
+        groups[i].first = i;
+        groups[i].count = 1;
+        for (int d = 0; d < 3; ++d) {
+            groups[i].n[d] = q.n[d];
+            groups[i].N[d] = q.N[d];
+        }
     }
     const size_t elt = cfg->precision == CTU_FP64 ? sizeof(double) : sizeof(float);
     if ((size_t)off * SCRATCH_ARRAYS * elt > kScratchBytes) return CTU_ETOOLARGE;
@@ -108,21 +120,26 @@ extern "C" ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in
     if (st != CTU_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned int *status = (unsigned int *)base;
+    StepParams *sp = (StepParams *)(base + 64);
     DevPatch *dtab = (DevPatch *)(base + kHeadBytes);
     void *scratch = base + kHeadBytes + kTableBytes;
 
     // The array keeps the previous call's contents: the status word must start
-    // at zero; every scratch word the kernels read is written earlier in the
-    // same call, so the scratch needs no clearing.
+    // at zero; the per-step parameters and every scratch word the kernels read
+    // are written earlier in the same call, so they need no clearing.
     if (cudaMemsetAsync(status, 0, sizeof(unsigned int), s) != cudaSuccess) return CTU_ECUDA;
     if (cudaMemcpyAsync(dtab, table, sizeof(DevPatch) * npatch, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return CTU_ECUDA;
 
     StepArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.patches = dtab;
     a.npatch = npatch;
     a.ndim = cfg->ndim;
     a.gam = cfg->gamma;
+    a.igm = 1.0 / (cfg->gamma - 1.0);
+    a.gamf = (float)cfg->gamma;
+    a.gm1f = (float)(cfg->gamma - 1.0);
     a.glm_alpha = cfg->glm_alpha;
     a.upwind = cfg->trace_mode == CTU_TRACE_UPWIND;
     a.U = U_in;
@@ -130,16 +147,16 @@ extern "C" ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in
     a.ustride = stride;
     a.sstride = off;
     a.dtch = d_dt_ch;
+    a.sp = sp;
     a.status = status;
     LaunchInfo li;
-    li.max_cells = maxc;
+    li.groups = groups;
+    li.ngroups = npatch;
     li.recon = cfg->recon == CTU_PPM;
-    li.win = nullptr;
-    li.nwin = 0;
-    li.reg = nullptr;
-    li.scratch = scratch;
-    li.prof = nullptr;
     li.iface64 = cfg->precision == CTU_MIXED_IFACE64;
+    li.scratch = scratch;
+    li.sp = sp;
+    li.prof = nullptr;
     if (cfg->precision == CTU_FP64)
         launch_step<double>(a, li, s);
     else

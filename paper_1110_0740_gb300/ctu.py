@@ -71,6 +71,8 @@ def _lib():
         L.ctu_init.argtypes = [ctypes.POINTER(ctu_config), ctypes.POINTER(vp)]
         L.ctu_dt.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp, vp, vp]
         L.ctu_step.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp, vp]
+        L.ctu_step_next_dt.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp, vp, vp]
+        L.ctu_step_next_dt.restype = i32
         L.ctu_flux_registers.argtypes = [vp, vp, ctypes.POINTER(ctu_flux_window), i32]
         L.ctu_fill_periodic.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp]
         L.ctu_status_sync.argtypes = [vp, vp]
@@ -167,6 +169,12 @@ def ctu_step(ctx, U_in, U_out, stride, patches, d_dt_ch, stream=None):
                            _ptr(d_dt_ch), _stream(stream)), "ctu_step")
 
 
+def ctu_step_next_dt(ctx, U_in, U_out, stride, patches, d_dt_ch, d_dt_ch_next, stream=None):
+    _check(_lib().ctu_step_next_dt(ctx, _ptr(U_in), _ptr(U_out), int(stride), patches,
+                                   len(patches), _ptr(d_dt_ch), _ptr(d_dt_ch_next),
+                                   _stream(stream)), "ctu_step_next_dt")
+
+
 def ctu_flux_registers(ctx, reg, windows):
     if reg is None or not windows:
         _check(_lib().ctu_flux_registers(ctx, None, None, 0), "ctu_flux_registers")
@@ -236,6 +244,9 @@ class Ctx:
 
     def step(self, U_in, U_out, stride, patches, d_dt_ch, stream=None):
         ctu_step(self.h, U_in, U_out, stride, patches, d_dt_ch, stream)
+
+    def step_next_dt(self, U_in, U_out, stride, patches, d_dt_ch, d_dt_ch_next, stream=None):
+        ctu_step_next_dt(self.h, U_in, U_out, stride, patches, d_dt_ch, d_dt_ch_next, stream)
 
     def flux_registers(self, reg, windows):
         ctu_flux_registers(self.h, reg, windows)

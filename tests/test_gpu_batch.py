@@ -149,3 +149,29 @@ def test_invalid_arguments_rejected_on_host():
         ctu.Ctx(ctu.make_config(ndim=4))
     with pytest.raises(ctu.CtuError):
         ctu.Ctx(ctu.make_config(cfl=1.5))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_step_next_dt_matches_ctu_dt_of_result(prec):
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    n = [20, 12, 16]
+    U0 = np.zeros(O.shape(n, 3))
+    O.interior(U0, n, 3)[:] = O.interior(W.mhd_blast_3d(20, seed=4, kmax=3), [20] * 3, 3)[:, :16, :12, :]
+    O.fill_periodic(U0, n, 3)
+    dev = _dev()
+    U = torch.from_numpy(U0.reshape(9, -1).copy()).to(dev)
+    Ua, Ub = torch.zeros_like(U), torch.zeros_like(U)
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3))
+    p = ctu.make_patches([(n, [1 / 20, 1 / 12, 1 / 16], 0)])
+    d0 = torch.zeros(2, dtype=torch.float64, device=dev)
+    d1 = torch.zeros_like(d0)
+    d2 = torch.zeros_like(d0)
+    ctx.dt(U, U.shape[1], p, d0)
+    ctx.step(U, Ua, U.shape[1], p, d0)
+    ctx.step_next_dt(U, Ub, U.shape[1], p, d0, d1)
+    ctx.dt(Ub, U.shape[1], p, d2)
+    assert ctx.status_sync() == 0
+    assert torch.equal(Ua, Ub) or prec == 0 and torch.allclose(Ua, Ub, rtol=0, atol=0)
+    a, b = d1.cpu().numpy(), d2.cpu().numpy()
+    assert np.allclose(a, b, rtol=1e-13 if prec == 0 else 1e-6, atol=0), (a, b)
