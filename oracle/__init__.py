@@ -76,7 +76,8 @@ def lib():
         L.or_euler_sample.argtypes = [D, D, D, D, D, D, D, D, P]
         if hasattr(L, "or_srmhd_step"):
             L.or_srmhd_step.restype = I
-            L.or_srmhd_step.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, P, D]
+            L.or_srmhd_step.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D,
+                                        ctypes.POINTER(ctypes.c_long), P, I, P]
             L.or_srmhd_max_speed.restype = D
             L.or_srmhd_max_speed.argtypes = [P, I, I, I, I, D, D, D, D]
             L.or_srmhd_prim2cons.restype = None
@@ -87,6 +88,8 @@ def lib():
             L.or_srmhd_fast_speeds.argtypes = [P, D, P, P]
             L.or_srmhd_riemann.restype = I
             L.or_srmhd_riemann.argtypes = [P, P, D, D, P]
+            L.or_srmhd_mh_predict.restype = I
+            L.or_srmhd_mh_predict.argtypes = [P, P, D, D, D, P, P]
         _lib = L
     return _lib
 
@@ -280,6 +283,97 @@ def mhd_run(U, n, ndim, dx, steps, cfl, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
         if t_end is not None and t + dt > t_end:
             dt = t_end - t
         U, bad = mhd_step(U, n, ndim, dx, dt, ch, gamma, glm_alpha, recon, upwind=upwind)
+        if bad:
+            raise FloatingPointError(f"oracle met {bad} unphysical states at step {k}")
+        t += dt
+        dts.append((dt, ch))
+        k += 1
+    fill(U, n, ndim)
+    return U, t, dts
+
+
+# ---------------------------------------------------------------- SRMHD
+
+def _windows(windows):
+    nwin = 0 if windows is None else len(windows)
+    win = np.zeros(max(1, 7 * nwin), dtype=np.int64)
+    wgt = np.zeros(max(1, nwin))
+    for i, w in enumerate(windows or []):
+        win[7 * i:7 * i + 7] = w[:7]
+        wgt[i] = w[7]
+    return nwin, win, wgt
+
+
+def srmhd_step(U, n, ndim, dx, dt, ch, gamma=4.0 / 3.0, glm_alpha=0.1, windows=None, reg=None):
+    """One SRMHD CTU step (MUSCL-Hancock, HLL, GLM); returns (Unew, n_bad)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    assert U.shape == shape(n, ndim)
+    Un = np.empty_like(U)
+    dx = list(dx) + [1.0] * (3 - len(dx))
+    nwin, win, wgt = _windows(windows)
+    regp = _dp(reg) if nwin else None
+    bad = lib().or_srmhd_step(_dp(U), _dp(Un), int(n[0]), int(n[1]), int(n[2]), int(ndim),
+                              float(dx[0]), float(dx[1]), float(dx[2]), float(dt), float(ch),
+                              float(gamma), float(glm_alpha),
+                              win.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(wgt),
+                              nwin, regp)
+    return Un, bad
+
+
+def srmhd_max_speed(U, n, ndim, dx, gamma=4.0 / 3.0):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    dx = list(dx) + [1.0] * (3 - len(dx))
+    return lib().or_srmhd_max_speed(_dp(U), int(n[0]), int(n[1]), int(n[2]), int(ndim),
+                                    float(dx[0]), float(dx[1]), float(dx[2]), float(gamma))
+
+
+def srmhd_prim2cons(V, gamma):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    U = np.zeros(NVAR)
+    lib().or_srmhd_prim2cons(_dp(V), float(gamma), _dp(U))
+    return U
+
+
+def srmhd_cons2prim(U, gamma):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    V = np.zeros(NVAR)
+    st = lib().or_srmhd_cons2prim(_dp(U), float(gamma), _dp(V))
+    return V, st
+
+
+def srmhd_fast_speeds(Vloc, gamma):
+    Vloc = np.ascontiguousarray(Vloc, dtype=np.float64)
+    lm, lp = ctypes.c_double(), ctypes.c_double()
+    lib().or_srmhd_fast_speeds(_dp(Vloc), float(gamma), ctypes.byref(lm), ctypes.byref(lp))
+    return lm.value, lp.value
+
+
+def srmhd_riemann(VL, VR, gamma, ch):
+    VL = np.ascontiguousarray(VL, dtype=np.float64)
+    VR = np.ascontiguousarray(VR, dtype=np.float64)
+    F = np.zeros(NVAR)
+    lib().or_srmhd_riemann(_dp(VL), _dp(VR), float(gamma), float(ch), _dp(F))
+    return F
+
+
+def srmhd_run(U, n, ndim, dx, steps, cfl, gamma=4.0 / 3.0, glm_alpha=0.1, bc="periodic",
+              t_end=None):
+    U = np.array(U, dtype=np.float64, copy=True)
+    fill = fill_periodic if bc == "periodic" else fill_outflow
+    t, k, dts = 0.0, 0, []
+    while True:
+        if t_end is None and k >= steps:
+            break
+        if t_end is not None and t >= t_end * (1 - 1e-14):
+            break
+        fill(U, n, ndim)
+        m = srmhd_max_speed(U, n, ndim, dx, gamma)
+        if m < 0:
+            raise FloatingPointError("oracle recovery failed")
+        dt, ch = dt_ch(m, list(dx), ndim, cfl)
+        if t_end is not None and t + dt > t_end:
+            dt = t_end - t
+        U, bad = srmhd_step(U, n, ndim, dx, dt, ch, gamma, glm_alpha)
         if bad:
             raise FloatingPointError(f"oracle met {bad} unphysical states at step {k}")
         t += dt

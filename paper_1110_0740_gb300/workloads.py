@@ -169,3 +169,51 @@ def mhd_lowbeta_3d(n=256, seed=0, gamma=5.0 / 3.0, kmax=8, beta=0.01, mach=10.0,
     U = ideal_cons([rho, v[0], v[1], v[2], p, z + b0 * d[0], z + b0 * d[1], z + b0 * d[2], z],
                    gamma)
     return pad_periodic(U, 3)
+
+
+def srmhd_cons(V, gamma):
+    """Conserved state (D, m, E - D... see below) of an ideal-gas special
+    relativistic MHD initial condition from primitives (rho, v, p, B, psi):
+    D = rho gamma, m = (W + B^2) v - (v.B) B, E = W - p + (B^2 + E_el^2)/2 - D
+    with W = (rho + Gamma p/(Gamma-1)) gamma^2 and E_el = -v x B."""
+    rho, vx, vy, vz, p, bx, by, bz, psi = V
+    v2 = vx * vx + vy * vy + vz * vz
+    lor2 = 1.0 / (1.0 - v2)
+    W = (rho + gamma / (gamma - 1.0) * p) * lor2
+    B2 = bx * bx + by * by + bz * bz
+    vB = vx * bx + vy * by + vz * bz
+    E2 = B2 * v2 - vB * vB
+    D = rho * np.sqrt(lor2)
+    return np.stack([D, (W + B2) * vx - vB * bx, (W + B2) * vy - vB * by, (W + B2) * vz - vB * bz,
+                     W - p + 0.5 * (B2 + E2) - D, bx, by, bz, psi])
+
+
+def srmhd_jet_3d(n=256, seed=0, gamma=4.0 / 3.0, lorentz=10.0, rho_ratio=0.01, sigma=0.1,
+                 p0=0.01, radius=0.1, pert=0.01):
+    """Relativistic magnetised beam: a cylinder along z of radius 0.1 around a
+    seeded axis position, rho = 1 and Lorentz factor up to `lorentz` inside
+    (smooth tanh edge over ~2 cells), ambient rho = rho_ratio at rest, uniform
+    p = p0, uniform B_z set so that sigma = B^2/(rho h gamma^2) = `sigma` on
+    the beam axis, and seeded 1 % perturbations of rho and of the transverse
+    velocity.  Periodic unit cube; returns U with ghosts."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(n) + 0.5) / n
+    c = rng.uniform(0.3, 0.7, size=2)
+    dxc = np.minimum(np.abs(x - c[0]), 1.0 - np.abs(x - c[0]))
+    dyc = np.minimum(np.abs(x - c[1]), 1.0 - np.abs(x - c[1]))
+    r = np.sqrt(dyc[:, None] ** 2 + dxc[None, :] ** 2)  # (ny, nx)
+    prof = 0.5 * (1.0 - np.tanh((r - radius) / (2.0 / n)))
+    prof3 = np.broadcast_to(prof[None, :, :], (n, n, n))
+    lor = 1.0 + (lorentz - 1.0) * prof3
+    vz = np.sqrt(1.0 - 1.0 / lor ** 2)
+    rho = rho_ratio + (1.0 - rho_ratio) * prof3
+    rho = rho * (1.0 + pert * (2.0 * rng.random((n, n, n)) - 1.0))
+    vx = pert * (2.0 * rng.random((n, n, n)) - 1.0) * prof3
+    vy = pert * (2.0 * rng.random((n, n, n)) - 1.0) * prof3
+    vz = vz * np.sqrt(np.maximum(1.0 - (vx ** 2 + vy ** 2) / np.maximum(vz ** 2, 1e-300), 0.0))
+    p = np.full((n, n, n), p0)
+    h_axis = 1.0 + gamma / (gamma - 1.0) * p0 / 1.0
+    bz0 = np.sqrt(sigma * 1.0 * h_axis * lorentz ** 2)
+    z = np.zeros((n, n, n))
+    U = srmhd_cons([rho, vx, vy, vz, p, z, z, z + bz0, z], gamma)
+    return pad_periodic(U, 3)
