@@ -26,7 +26,8 @@
  * only enqueues work on it, except where "synchronises" is stated.
  *
  * Errors: host-side validation errors are returned at once.  Device-side
- * conditions (a state with rho <= 0 or p <= 0, a NaN) set sticky bits in a
+ * conditions (a state with rho <= 0 or p <= 0, a NaN, a relativistic
+ * recovery that did not converge or gave |v| >= 1) set sticky bits in a
  * device status word that ctu_status_sync() returns and clears.  The library
  * never traps, asserts or exits.
  */
@@ -79,13 +80,20 @@ enum { CTU_FP64 = 0, CTU_MIXED = 1, CTU_MIXED_IFACE64 = 2 };
 enum { CTU_TRACE_ALL = 0, CTU_TRACE_UPWIND = 1 };
 
 typedef struct {
-    int physics;      /* CTU_MHD (CTU_SRMHD: CTU_EUNSUPPORTED in this build) */
+    int physics;      /* CTU_MHD: ideal MHD (Section 2.1), requires
+                         predictor CTU_CHAR_TRACE and riemann CTU_HLLD.
+                         CTU_SRMHD: special-relativistic MHD (Section 2.2),
+                         requires predictor CTU_MUSCL_HANCOCK (Section 3.3),
+                         riemann CTU_HLL and recon CTU_LINEAR_MC; its
+                         primitive recovery (Newton-Raphson) is float64 in
+                         both precisions.  Other combinations return
+                         CTU_EUNSUPPORTED. */
     int eos;          /* CTU_EOS_IDEAL */
     double gamma;     /* ratio of specific heats, > 1 */
     int ndim;         /* 1, 2 or 3 active dimensions; v_z, B_z always carried */
     int recon;        /* CTU_LINEAR_MC or CTU_PPM (Section 3.2) */
-    int predictor;    /* CTU_CHAR_TRACE */
-    int riemann;      /* CTU_HLLD */
+    int predictor;    /* CTU_CHAR_TRACE (MHD) or CTU_MUSCL_HANCOCK (SRMHD) */
+    int riemann;      /* CTU_HLLD (MHD) or CTU_HLL (SRMHD) */
     int precision;    /* CTU_FP64, CTU_MIXED or CTU_MIXED_IFACE64 (above) */
     double cfl;       /* C_a of Eq. (Ca): <= 1 in 2D, <= 1/2 in 3D */
     double glm_alpha; /* c_h^2/c_p^2 = glm_alpha * c_h / min(dx): psi decays by

@@ -10,7 +10,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "libctu.so"
-SOURCES = ["ctu_api.cu", "ctu_f64.cu", "ctu_f32.cu", "ctu_f32i.cu", "ctu_noalloc.cu"]
+SOURCES = ["ctu_api.cu", "ctu_f64.cu", "ctu_f32.cu", "ctu_f32i.cu", "ctu_sr32.cu", "ctu_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -317,6 +317,7 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
     li.ngroups = (int)ctx->groups.size();
     li.recon = ctx->cfg.recon == CTU_PPM;
     li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
+    li.physics = ctx->cfg.physics == CTU_SRMHD ? PH_SR : PH_MHD;
     li.scratch = ctx->scratch;
     li.sp = ctx->dsp;
     li.prof = ctx->prof;
@@ -326,10 +327,11 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
 namespace ctu {
 template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
-    return launch_step_impl<double, 1>(a, li, s);
+    return li.physics == PH_SR ? launch_step_sr<double>(a, li, s) : launch_step_impl<double, 1>(a, li, s);
 }
 template <> int launch_step<float>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
+    if (li.physics == PH_SR) return launch_step_sr<float>(a, li, s);
     return li.iface64 ? launch_step_impl<float, 1>(a, li, s) : launch_step_impl<float, 0>(a, li, s);
 }
 } // namespace ctu
@@ -348,13 +350,21 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
 {
     if (!cfg || !out) return CTU_EINVAL;
     *out = nullptr;
-    if (cfg->physics != CTU_MHD) return cfg->physics == CTU_SRMHD ? CTU_EUNSUPPORTED : CTU_EINVAL;
+    if (cfg->physics != CTU_MHD && cfg->physics != CTU_SRMHD) return CTU_EINVAL;
     if (cfg->eos != CTU_EOS_IDEAL) return CTU_EUNSUPPORTED;
     if (!(cfg->gamma > 1.0)) return CTU_EINVAL;
     if (cfg->ndim < 1 || cfg->ndim > 3) return CTU_EINVAL;
     if (cfg->recon != CTU_LINEAR_MC && cfg->recon != CTU_PPM) return CTU_EINVAL;
-    if (cfg->predictor != CTU_CHAR_TRACE) return CTU_EUNSUPPORTED;
-    if (cfg->riemann != CTU_HLLD) return CTU_EUNSUPPORTED;
+    if (cfg->predictor != CTU_CHAR_TRACE && cfg->predictor != CTU_MUSCL_HANCOCK) return CTU_EINVAL;
+    if (cfg->riemann != CTU_HLLD && cfg->riemann != CTU_HLL) return CTU_EINVAL;
+    // implemented combinations: MHD with characteristic tracing + HLLD;
+    // SRMHD with MUSCL-Hancock (MC-linear primitive slopes) + HLL
+    if (cfg->physics == CTU_MHD && (cfg->predictor != CTU_CHAR_TRACE || cfg->riemann != CTU_HLLD))
+        return CTU_EUNSUPPORTED;
+    if (cfg->physics == CTU_SRMHD &&
+        (cfg->predictor != CTU_MUSCL_HANCOCK || cfg->riemann != CTU_HLL || cfg->recon != CTU_LINEAR_MC ||
+         cfg->precision == CTU_MIXED_IFACE64))
+        return CTU_EUNSUPPORTED;
     if (cfg->precision != CTU_FP64 && cfg->precision != CTU_MIXED && cfg->precision != CTU_MIXED_IFACE64)
         return CTU_EINVAL;
     if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return CTU_EINVAL;
@@ -538,6 +548,8 @@ ctu_status ctu_status_sync(ctu_ctx *ctx, void *stream)
     CTU_CUDA(cudaMemcpy(&h, ctx->dstatus, sizeof(h), cudaMemcpyDeviceToHost));
     CTU_CUDA(cudaMemset(ctx->dstatus, 0, sizeof(unsigned int)));
     if (h & ST_NAN) return CTU_ENAN;
+    if (h & ST_REC) return CTU_ERECOVERY;
+    if (h & ST_SUPER) return CTU_ESUPERLUMINAL;
     if (h & ST_NEG) return CTU_ENEGATIVE;
     return CTU_OK;
 }

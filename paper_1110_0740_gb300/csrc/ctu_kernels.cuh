@@ -29,8 +29,13 @@
 
 #include "df.cuh"
 #include "mhd_device.cuh"
+#include "srmhd_device.cuh"
 
 namespace ctu {
+
+// Physics of a kernel instance: ideal MHD (characteristic tracing, HLLD) or
+// special-relativistic MHD (MUSCL-Hancock, HLL, float64 Newton recovery).
+enum { PH_MHD = 0, PH_SR = 1 };
 
 struct DevPatch {
     int n[3];        // interior cells
@@ -191,6 +196,43 @@ template <class R> __device__ __forceinline__ double widen(R x);
 template <> __device__ __forceinline__ double widen<double>(double x) { return x; }
 template <> __device__ __forceinline__ double widen<float>(float x) { return f2d_int(x); }
 
+// V(U) for either physics (SRMHD: float64 Newton recovery).
+template <int PHYS, class R>
+__device__ __forceinline__ unsigned int prim_any(const double (&U)[NV], const StepArgs &a, R (&V)[NV])
+{
+    if (PHYS == PH_MHD) return prim_of<R>(U, a, V);
+    double Vd[NV];
+    const unsigned int st = sr_prim64(U, a.gam, Vd);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) V[q] = (R)Vd[q];
+    return st;
+}
+
+// CFL speed of one cell: max_d (largest |signal speed| along d) / dx_d.
+template <int PHYS, class R>
+__device__ __forceinline__ R cell_speed(const R (&V)[NV], const StepArgs &a, const DevPatch &P)
+{
+    const R g = pgam<R>(a);
+    R m = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= a.ndim) continue;
+        R s;
+        if (PHYS == PH_MHD) {
+            const int b1 = 5 + (d == 0 ? 1 : 0), b2 = 5 + (d == 2 ? 1 : 2);
+            s = fabs(V[1 + d]) + fast_speed(V[0], V[4], V[5 + d], V[b1], V[b2], g);
+        } else {
+            R Vl[NV], lm, lp;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Vl[q] = V[perm(d, q)];
+            sr_speeds(Vl, g, lm, lp);
+            s = fmax(fabs(lm), fabs(lp));
+        }
+        m = fmax(m, s * pidx<R>(P, d));
+    }
+    return m;
+}
+
 // ---------------------------------------------------------------- per-cell pieces
 
 // Half-step transverse increments dt/2 sum_{d' != D} L^n_d' at cell c (global
@@ -266,28 +308,74 @@ __device__ __forceinline__ unsigned int interface_state(const R (&W)[NV], const 
     }
 }
 
+// SRMHD interface state at n+1/2: U(V*) + T formed in float64, recovered by
+// the float64 Newton iteration (Eq. transv).
+template <class R>
+__device__ __forceinline__ unsigned int sr_interface(const R (&W)[NV], const R (&T)[NV], const StepArgs &a,
+                                                     R (&out)[NV])
+{
+    double U[NV], V[NV];
+    sr_cons<double, R>(W, a.gam, U);
+    // Newton starts from the W of the predicted state V* (the transverse
+    // correction T is an O(dt) change)
+    const double v2 = (double)W[1] * W[1] + (double)W[2] * W[2] + (double)W[3] * W[3];
+    const double W0 = ((double)W[0] + a.gam * a.igm * (double)W[4]) * rcp64(1.0 - v2);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) U[q] += (double)T[q];
+    const unsigned int st = sr_prim64(U, a.gam, V, W0);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = (R)V[q];
+    return st;
+}
+
 // Trace one cell along D: stencil (local order) -> interface states (global).
-template <class R, int PPM, int IFACE64, int D>
+// MHD: characteristic tracing (Section 3.2).  SRMHD: MUSCL-Hancock in
+// primitive variables (Section 3.3) from V_(i-1..i+1) and U_i^n.
+template <int PHYS, class R, int PPM, int IFACE64, int D>
 __device__ __forceinline__ unsigned int trace_cell(const StepArgs &a, const DevPatch &P, const R (&vs)[5][NV],
                                                    const R *F1, long long c, R ch, R dtdx, R hdt, R (&Vp)[NV],
                                                    R (&Vm)[NV])
 {
     R pl[NV], ml[NV], pg[NV], mg[NV], T[NV];
-    char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind != 0, pl, ml);
+    unsigned int f = 0;
+    if (PHYS == PH_MHD) {
+        char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind != 0, pl, ml);
+    } else {
+        double U0[NV];
+        const long long gi = P.base + (c - P.soff);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) U0[q] = a.U[gperm<D>(q) * a.ustride + gi];
+        f |= sr_mh_predict<R>(vs[1], vs[2], vs[3], U0, pgam<R>(a), ch, dtdx, a.gam, pl, ml);
+    }
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         pg[gperm<D>(q)] = pl[q];
         mg[gperm<D>(q)] = ml[q];
     }
     transverse<R, D>(a, P, F1, c, hdt, T);
-    unsigned int f = interface_state<R, IFACE64>(pg, T, a, Vp);
-    f |= interface_state<R, IFACE64>(mg, T, a, Vm);
+    if (PHYS == PH_MHD) {
+        f |= interface_state<R, IFACE64>(pg, T, a, Vp);
+        f |= interface_state<R, IFACE64>(mg, T, a, Vm);
+    } else {
+        f |= sr_interface<R>(pg, T, a, Vp);
+        f |= sr_interface<R>(mg, T, a, Vm);
+    }
     return f;
+}
+
+// Numerical flux along the local normal for either physics.
+template <int PHYS, class R>
+__device__ __forceinline__ void riemann_any(const R (&L)[NV], const R (&Rr)[NV], R gam, R ch, R (&F)[NV])
+{
+    if (PHYS == PH_MHD)
+        riemann_hlld(L, Rr, gam, ch, F);
+    else
+        riemann_hll_sr(L, Rr, gam, ch, F);
 }
 
 // n+1/2 flux through a D-face from the left cell's + state and the right
 // cell's - state (both global order); flux returned in global order.
-template <class R, int D>
+template <int PHYS, class R, int D>
 __device__ __forceinline__ void face_flux(const R (&Lg)[NV], const R (&Rg)[NV], R gam, R ch, R (&Fg)[NV])
 {
     R L[NV], Rr[NV], F[NV];
@@ -296,7 +384,7 @@ __device__ __forceinline__ void face_flux(const R (&Lg)[NV], const R (&Rg)[NV], 
         L[q] = Lg[gperm<D>(q)];
         Rr[q] = Rg[gperm<D>(q)];
     }
-    riemann_hlld(L, Rr, gam, ch, F);
+    riemann_any<PHYS, R>(L, Rr, gam, ch, F);
 #pragma unroll
     for (int q = 0; q < NV; ++q) Fg[gperm<D>(q)] = F[q];
 }
@@ -322,7 +410,7 @@ __device__ __forceinline__ void register_face(const StepArgs &a, int patch, cons
 
 // Final update of one interior cell: U^(n+1) = U^n + dt s, psi source, and
 // the CFL speed of U^(n+1) if requested (returned in R; 0 otherwise).
-template <class R>
+template <int PHYS, class R>
 __device__ __forceinline__ R finish_cell(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
                                          double damp, unsigned int &fl)
 {
@@ -335,17 +423,8 @@ __device__ __forceinline__ R finish_cell(const StepArgs &a, const DevPatch &P, i
     for (int q = 0; q < NV; ++q) a.Uout[q * a.ustride + P.base + cl] = u[q];
     if (!a.nextmax) return R(0);
     R V[NV];
-    fl |= prim_of<R>(u, a, V);
-    const R g = pgam<R>(a);
-    R m = R(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (d >= a.ndim) continue;
-        const int b1 = 5 + (d == 0 ? 1 : 0), b2 = 5 + (d == 2 ? 1 : 2);
-        const R cf = fast_speed(V[0], V[4], V[5 + d], V[b1], V[b2], g);
-        m = fmax(m, (fabs(V[1 + d]) + cf) * pidx<R>(P, d));
-    }
-    return m;
+    fl |= prim_any<PHYS, R>(u, a, V);
+    return cell_speed<PHYS, R>(V, a, P);
 }
 
 // Block maximum of a non-negative value, folded into *out as the bits of a
@@ -432,7 +511,7 @@ static __global__ void k_setup(const double *dtch, StepParams *sp)
 }
 
 // V = V(U) on every ghosted cell; blockIdx.y = patch (within the group).
-template <class R>
+template <int PHYS, class R>
 __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, int first, R *Vs)
 {
     const DevPatch P = a.patches[first + blockIdx.y];
@@ -448,7 +527,7 @@ __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, int first, R *Vs)
     R V[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) U[q] = a.U[q * a.ustride + P.base + c];
-    const unsigned int f = prim_of<R>(U, a, V);
+    const unsigned int f = prim_any<PHYS, R>(U, a, V);
     if (f) atomicOr(a.status, f);
 #pragma unroll
     for (int q = 0; q < NV; ++q) Vs[q * a.sstride + P.soff + c] = V[q];
@@ -456,7 +535,7 @@ __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, int first, R *Vs)
 
 // First-order fluxes through the upper D-face of cells with c_D in
 // [-1, n_D - 1] and the other active coordinates in [-1, n].
-template <class R, int D>
+template <int PHYS, class R, int D>
 __global__ void __launch_bounds__(BLOCK) k_flux1(StepArgs a, int first, const R *Vs, R *F1)
 {
     const DevPatch P = a.patches[first + blockIdx.y];
@@ -480,7 +559,7 @@ __global__ void __launch_bounds__(BLOCK) k_flux1(StepArgs a, int first, const R 
         L[q] = Vs[gperm<D>(q) * a.sstride + c];
         Rr[q] = Vs[gperm<D>(q) * a.sstride + c + st];
     }
-    riemann_hlld(L, Rr, pgam<R>(a), pch<R>(a.sp), F);
+    riemann_any<PHYS, R>(L, Rr, pgam<R>(a), pch<R>(a.sp), F);
     R *Fd = F1 + (long long)D * NV * a.sstride;
 #pragma unroll
     for (int q = 0; q < NV; ++q) Fd[gperm<D>(q) * a.sstride + c] = F[q];
@@ -488,7 +567,7 @@ __global__ void __launch_bounds__(BLOCK) k_flux1(StepArgs a, int first, const R 
 
 // Sweep along x, one thread per traced cell.  A tile covers xw traced cells
 // (xw - 2 updated cells) along x times BLOCK/xw rows along y.
-template <class R, int PPM, int IFACE64, int LAST>
+template <int PHYS, class R, int PPM, int IFACE64, int LAST>
 __global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const R *Vs, const R *F1, R *A)
 {
     const int patch = first + blockIdx.y;
@@ -516,7 +595,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const 
 #pragma unroll
             for (int q = 0; q < NV; ++q) vs[m][q] = Vs[q * a.sstride + c + (m - 2)];
         R Vp[NV], Vm[NV];
-        fl |= trace_cell<R, PPM, IFACE64, 0>(a, P, vs, F1, c, ch, dtdx, hdt, Vp, Vm);
+        fl |= trace_cell<PHYS, R, PPM, IFACE64, 0>(a, P, vs, F1, c, ch, dtdx, hdt, Vp, Vm);
 #pragma unroll
         for (int q = 0; q < NV; ++q) { sP[me][q] = Vp[q]; sM[me][q] = Vm[q]; }
     }
@@ -525,7 +604,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const 
         R L[NV], Rr[NV], F[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) { L[q] = sP[me][q]; Rr[q] = sM[me + 1][q]; }
-        face_flux<R, 0>(L, Rr, gam, ch, F);
+        face_flux<PHYS, R, 0>(L, Rr, gam, ch, F);
 #pragma unroll
         for (int q = 0; q < NV; ++q) sF[me][q] = F[q];
         // faces on plane i+1; the tile's last face belongs to the next tile
@@ -541,7 +620,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const 
             const int cl = lcell(P, i, j, k);
 #pragma unroll
             for (int q = 0; q < NV; ++q) s[q] = (sF[me - 1][q] - sF[me][q]) * ix;
-            m = finish_cell<R>(a, P, cl, s, damp, fl);
+            m = finish_cell<PHYS, R>(a, P, cl, s, damp, fl);
         }
         if (a.nextmax) block_max_to<R>(m, a.nextmax);
     } else {
@@ -559,7 +638,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const 
 // cells along D; the 5-cell stencil, the previous cell's + state and the
 // previous face flux stay in registers.  A tile: xw lanes along x times
 // BLOCK/xw (other-dimension, segment) pairs.
-template <class R, int PPM, int IFACE64, int D, int LAST>
+template <int PHYS, class R, int PPM, int IFACE64, int D, int LAST>
 __global__ void __launch_bounds__(BLOCK) k_sweep_m(StepArgs a, int first, const R *Vs, const R *F1, R *A)
 {
     constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
@@ -634,10 +713,10 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_m(StepArgs a, int first, const 
                 for (int q = 0; q < NV; ++q) win[4][q] = Vs[gperm<D>(q) * a.sstride + c + 2 * st];
             }
             R Vp[NV], Vm[NV];
-            fl |= trace_cell<R, PPM, IFACE64, D>(a, P, win, F1, c, ch, dtdx, hdt, Vp, Vm);
+            fl |= trace_cell<PHYS, R, PPM, IFACE64, D>(a, P, win, F1, c, ch, dtdx, hdt, Vp, Vm);
             if (j >= j0) {
                 R F[NV];
-                face_flux<R, D>(Pprev, Vm, gam, ch, F);
+                face_flux<PHYS, R, D>(Pprev, Vm, gam, ch, F);
                 // plane j; (a, b) = (x, o) are the two non-D dimensions in
                 // increasing order; a segment's last face belongs to the next
                 if (a.reg && (j < j1 || j1 == nD)) register_face<R, D>(a, patch, P, j, x, o, F);
@@ -649,7 +728,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_m(StepArgs a, int first, const 
                     if (LAST) {
 #pragma unroll
                         for (int q = 0; q < NV; ++q) s[q] = A[q * a.sstride + cp] + s[q];
-                        mx = fmax(mx, finish_cell<R>(a, P, (int)(cp - P.soff), s, damp, fl));
+                        mx = fmax(mx, finish_cell<PHYS, R>(a, P, (int)(cp - P.soff), s, damp, fl));
                     } else {
 #pragma unroll
                         for (int q = 0; q < NV; ++q) A[q * a.sstride + cp] += s[q];
@@ -667,7 +746,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_m(StepArgs a, int first, const 
 }
 
 // ctu_dt: max over interior cells of max_d (|v_d| + c_f,d)/dx_d.
-template <class R>
+template <int PHYS, class R>
 __global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, int first, unsigned long long *out)
 {
     const DevPatch P = a.patches[first + blockIdx.y];
@@ -682,18 +761,9 @@ __global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, int first, unsig
         R V[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) U[q] = a.U[q * a.ustride + P.base + cl];
-        const unsigned int f = prim_of<R>(U, a, V);
+        const unsigned int f = prim_any<PHYS, R>(U, a, V);
         if (f) atomicOr(a.status, f);
-        const R g = pgam<R>(a);
-        R mm = R(0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (d >= a.ndim) continue;
-            const int b1 = 5 + (d == 0 ? 1 : 0), b2 = 5 + (d == 2 ? 1 : 2);
-            const R cf = fast_speed(V[0], V[4], V[5 + d], V[b1], V[b2], g);
-            mm = fmax(mm, (fabs(V[1 + d]) + cf) * pidx<R>(P, d));
-        }
-        m = mm;
+        m = cell_speed<PHYS, R>(V, a, P);
     }
     block_max_to<R>(m, out);
 }

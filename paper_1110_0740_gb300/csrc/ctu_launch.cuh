@@ -1,5 +1,5 @@
-// ctu_launch.cuh -- launcher templates, instantiated per precision and
-// interface mode by ctu_f64.cu, ctu_f32.cu and ctu_f32i.cu.
+// ctu_launch.cuh -- launcher templates, instantiated per precision, physics
+// and interface mode by ctu_f64.cu, ctu_f32.cu, ctu_f32i.cu and ctu_sr32.cu.
 #pragma once
 
 #include "ctu_launch.h"
@@ -9,7 +9,7 @@ namespace ctu {
 #define CTU_MARK(nm) \
     if (li.prof) li.prof->mark(nm, s)
 
-template <class R, int PPM, int IF64>
+template <int PHYS, class R, int PPM, int IF64>
 static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     const long long S = a.sstride;
@@ -25,7 +25,7 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     CTU_MARK("prim");
     for (int g = 0; g < li.ngroups; ++g) {
         const Group &G = li.groups[g];
-        k_prim<R><<<dim3((unsigned)Tiles::prim(G.n, G.N), (unsigned)G.count), BLOCK, 0, s>>>(a, G.first, Vs);
+        k_prim<PHYS, R><<<dim3((unsigned)Tiles::prim(G.n, G.N), (unsigned)G.count), BLOCK, 0, s>>>(a, G.first, Vs);
         ++n;
     }
     CTU_MARK(nullptr);
@@ -33,14 +33,16 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     for (int g = 0; g < li.ngroups; ++g) {
         const Group &G = li.groups[g];
         const unsigned c = (unsigned)G.count;
-        k_flux1<R, 0><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 0), c), BLOCK, 0, s>>>(a, G.first, Vs, F1);
+        k_flux1<PHYS, R, 0><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 0), c), BLOCK, 0, s>>>(a, G.first, Vs, F1);
         ++n;
         if (a.ndim > 1) {
-            k_flux1<R, 1><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 1), c), BLOCK, 0, s>>>(a, G.first, Vs, F1);
+            k_flux1<PHYS, R, 1><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 1), c), BLOCK, 0, s>>>(a, G.first, Vs,
+                                                                                                  F1);
             ++n;
         }
         if (a.ndim > 2) {
-            k_flux1<R, 2><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 2), c), BLOCK, 0, s>>>(a, G.first, Vs, F1);
+            k_flux1<PHYS, R, 2><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 2), c), BLOCK, 0, s>>>(a, G.first, Vs,
+                                                                                                  F1);
             ++n;
         }
     }
@@ -50,9 +52,9 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         const Group &G = li.groups[g];
         const dim3 grid((unsigned)Tiles::sweep_x(G.n), (unsigned)G.count);
         if (a.ndim == 1)
-            k_sweep_x<R, PPM, IF64, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+            k_sweep_x<PHYS, R, PPM, IF64, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
         else
-            k_sweep_x<R, PPM, IF64, 0><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+            k_sweep_x<PHYS, R, PPM, IF64, 0><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
         ++n;
     }
     CTU_MARK(nullptr);
@@ -62,9 +64,9 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
             const Group &G = li.groups[g];
             const dim3 grid((unsigned)Tiles::sweep_m(G.n, 1), (unsigned)G.count);
             if (a.ndim == 2)
-                k_sweep_m<R, PPM, IF64, 1, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+                k_sweep_m<PHYS, R, PPM, IF64, 1, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
             else
-                k_sweep_m<R, PPM, IF64, 1, 0><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+                k_sweep_m<PHYS, R, PPM, IF64, 1, 0><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
             ++n;
         }
         CTU_MARK(nullptr);
@@ -74,7 +76,7 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         for (int g = 0; g < li.ngroups; ++g) {
             const Group &G = li.groups[g];
             const dim3 grid((unsigned)Tiles::sweep_m(G.n, 2), (unsigned)G.count);
-            k_sweep_m<R, PPM, IF64, 2, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+            k_sweep_m<PHYS, R, PPM, IF64, 2, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
             ++n;
         }
         CTU_MARK(nullptr);
@@ -82,18 +84,26 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     return n;
 }
 
+// MHD: PPM or MC-linear characteristic tracing.
 template <class R, int IF64> int launch_step_impl(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
-    return li.recon ? launch_step_t<R, 1, IF64>(a, li, s) : launch_step_t<R, 0, IF64>(a, li, s);
+    return li.recon ? launch_step_t<PH_MHD, R, 1, IF64>(a, li, s) : launch_step_t<PH_MHD, R, 0, IF64>(a, li, s);
 }
 
-template <class R>
+// SRMHD: MUSCL-Hancock with MC-linear primitive slopes.
+template <class R> int launch_step_sr(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
+{
+    return launch_step_t<PH_SR, R, 0, 1>(a, li, s);
+}
+
+template <int PHYS, class R>
 int launch_maxspeed_impl(const StepArgs &a, const LaunchInfo &li, unsigned long long *out, cudaStream_t s)
 {
     CTU_MARK("maxspeed");
     for (int g = 0; g < li.ngroups; ++g) {
         const Group &G = li.groups[g];
-        k_maxspeed<R><<<dim3((unsigned)Tiles::interior(G.n), (unsigned)G.count), BLOCK, 0, s>>>(a, G.first, out);
+        k_maxspeed<PHYS, R><<<dim3((unsigned)Tiles::interior(G.n), (unsigned)G.count), BLOCK, 0, s>>>(a, G.first,
+                                                                                                      out);
     }
     CTU_MARK(nullptr);
     return li.ngroups;

@@ -30,6 +30,7 @@ struct LaunchInfo {
     int ngroups;
     int recon;             // 0 linear, 1 PPM
     int iface64;           // mixed path: 1 = float64 interface-state recovery
+    int physics;           // PH_MHD or PH_SR
     void *scratch;         // SCRATCH_ARRAYS * sstride elements of R
     StepParams *sp;        // device per-step parameters
     ProfHook *prof;        // may be null
@@ -41,7 +42,9 @@ template <class R> int launch_step(const StepArgs &a, const LaunchInfo &li, cuda
 template <class R> int launch_maxspeed(const StepArgs &a, const LaunchInfo &li, unsigned long long *out,
                                        cudaStream_t s);
 
-// Per-(precision, interface-mode) instantiations, one translation unit each.
+// Per-(precision, physics, interface-mode) instantiations, one translation
+// unit each.
 template <class R, int IF64> int launch_step_impl(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
+template <class R> int launch_step_sr(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
 
 } // namespace ctu

@@ -154,6 +154,7 @@ extern "C" ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in
     li.ngroups = npatch;
     li.recon = cfg->recon == CTU_PPM;
     li.iface64 = cfg->precision == CTU_MIXED_IFACE64;
+    li.physics = PH_MHD;
     li.scratch = scratch;
     li.sp = sp;
     li.prof = nullptr;

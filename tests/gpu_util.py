@@ -9,9 +9,12 @@ def torch_cuda():
     return torch
 
 
-def l1rel(got, ref, ch=None):
+def l1rel(got, ref, ch=None, group_floor=False):
     """Per-variable relative L1: sum|got - ref| / sum|ref|; for psi the
-    denominator is c_h sum |B| (psi carries the units of c_h B)."""
+    denominator is c_h sum |B| (psi carries the units of c_h B).
+    group_floor: a vector component is measured against at least the size of
+    its whole vector (momentum also against D, i.e. rho gamma c with c = 1),
+    for regions where one component of the reference is nearly zero."""
     out = []
     for q in range(9):
         num = np.abs(got[q] - ref[q]).sum()
@@ -19,12 +22,16 @@ def l1rel(got, ref, ch=None):
             den = (ch if ch else 1.0) * np.abs(ref[5:8]).sum()
         else:
             den = np.abs(ref[q]).sum()
+            if group_floor and q in (1, 2, 3):
+                den = max(den, np.abs(ref[1:4]).sum(), np.abs(ref[0]).sum())
+            if group_floor and q in (5, 6, 7):
+                den = max(den, np.abs(ref[5:8]).sum())
         out.append(num / den if den > 0 else (0.0 if num == 0 else np.inf))
     return np.array(out)
 
 
 def gpu_run(U0, n, ndim, dx, steps, cfl, precision=0, recon=1, trace_mode=0, glm_alpha=0.1,
-            gamma=5.0 / 3.0):
+            gamma=5.0 / 3.0, physics=0):
     """Advance one periodic patch `steps` steps on the GPU; returns
     (U ghosted numpy, list of (dt, ch), status)."""
     import torch
@@ -33,8 +40,13 @@ def gpu_run(U0, n, ndim, dx, steps, cfl, precision=0, recon=1, trace_mode=0, glm
     U = torch.from_numpy(np.ascontiguousarray(U0).reshape(9, -1)).to(dev)
     Ub = torch.zeros_like(U)
     stride = U.shape[1]
-    cfg = ctu.make_config(ndim=ndim, gamma=gamma, recon=recon, precision=precision, cfl=cfl,
-                          glm_alpha=glm_alpha, trace_mode=trace_mode)
+    if physics == ctu.CTU_SRMHD:
+        cfg = ctu.make_config(ndim=ndim, gamma=gamma, recon=ctu.CTU_LINEAR_MC, precision=precision,
+                              cfl=cfl, glm_alpha=glm_alpha, physics=ctu.CTU_SRMHD,
+                              predictor=ctu.CTU_MUSCL_HANCOCK, riemann=ctu.CTU_HLL)
+    else:
+        cfg = ctu.make_config(ndim=ndim, gamma=gamma, recon=recon, precision=precision, cfl=cfl,
+                              glm_alpha=glm_alpha, trace_mode=trace_mode)
     ctx = ctu.Ctx(cfg)
     dx3 = list(dx) + [1.0] * (3 - len(dx))
     patches = ctu.make_patches([(n, dx3, 0)])
