@@ -375,6 +375,183 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def run_amr(args):
+    """Batched AMR level advance: the seeded 3-level hierarchy (refinement
+    ratio 2, base 128^3, ~560 patches of 8^3..64^3) around an expanding
+    spherical shock; one coarse step = level 0 once, level 1 twice, level 2
+    four times (dt_l = dt_0 / 2^l, common c_h), all seven batched ctu_step
+    calls captured in one CUDA graph; flux-register windows on both sides of
+    every coarse-fine interface.  dt_0 is fixed before timing from ctu_dt on
+    every level (dt_0 = min_l 2^l dt_l)."""
+    import torch
+    from paper_1110_0740_gb300 import ctu, workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H = W.amr_hierarchy(seed=rank)
+    L = H["levels"]
+    prec = ctu.CTU_MIXED if args.precision == "mixed" else ctu.CTU_FP64
+    # flux-register windows, per level context
+    wins = [[] for _ in L]
+    off = 0
+    for lev in range(1, len(L)):
+        for pi, (n, dx, base, _) in enumerate(L[lev]["patches"]):
+            for d in range(3):
+                a_, b_ = [e for e in range(3) if e != d]
+                for plane in (0, n[d]):
+                    wins[lev].append((pi, d, plane, 0, n[a_], 0, n[b_], 1.0, off))
+                    off += 9 * n[a_] * n[b_]
+        for (parent, o_zyx, sz) in L[lev]["footprints"]:
+            o = [o_zyx[2], o_zyx[1], o_zyx[0]]
+            for d in range(3):
+                a_, b_ = [e for e in range(3) if e != d]
+                for plane in (o[d], o[d] + sz):
+                    wins[lev - 1].append((parent, d, plane, o[a_], o[a_] + sz, o[b_], o[b_] + sz, -1.0, off))
+                    off += 9 * sz * sz
+    reg = torch.zeros(max(off, 1), dtype=torch.float64, device=dev)
+    ctxs, A, B, P, D = [], [], [], [], []
+    for lev, lv in enumerate(L):
+        c = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3))
+        pool = torch.from_numpy(lv["pool"]).to(dev)
+        A.append(pool)
+        B.append(pool.clone())
+        P.append(ctu.make_patches([(n, dx, b) for (n, dx, b, _) in lv["patches"]]))
+        c.flux_registers(reg, wins[lev])
+        ctxs.append(c)
+    h = []
+    for lev, c in enumerate(ctxs):
+        hd = torch.zeros(2, dtype=torch.float64, device=dev)
+        c.dt(A[lev], A[lev].shape[1], P[lev], hd)
+        h.append(hd.cpu().tolist())
+    dt0 = min(v[0] * 2 ** lev for lev, v in enumerate(h))
+    dx0 = L[0]["patches"][0][1][0]
+    ch = 0.3 * dx0 / dt0
+    for lev in range(len(L)):
+        D.append(torch.tensor([dt0 / 2 ** lev, ch], dtype=torch.float64, device=dev))
+    stream = torch.cuda.Stream(device=dev)
+
+    def coarse_step():
+        # recursive subcycling: l0, then for each l1 substep its two l2 substeps
+        ctxs[0].step(A[0], B[0], A[0].shape[1], P[0], D[0], stream=stream)
+        for k in range(2):
+            src, dst = (A[1], B[1]) if k == 0 else (B[1], A[1])
+            ctxs[1].step(src, dst, A[1].shape[1], P[1], D[1], stream=stream)
+            for m in range(2):
+                s2, d2 = (A[2], B[2]) if m == 0 else (B[2], A[2])
+                ctxs[2].step(s2, d2, A[2].shape[1], P[2], D[2], stream=stream)
+
+    with torch.cuda.stream(stream):
+        coarse_step()  # binds patch lists, sizes scratch (before capture)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        coarse_step()
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = [c.status_sync() for c in ctxs]
+    cells = [sum(n[0] * n[1] * n[2] for (n, _, _, _) in lv["patches"]) for lv in L]
+    upd = cells[0] + 2 * cells[1] + 4 * cells[2]
+    from collections import Counter
+    hist = {lev: dict(sorted(Counter(n[0] for (n, _, _, _) in lv["patches"]).items()))
+            for lev, lv in enumerate(L)}
+    # per-kernel times of one (non-graph) coarse step
+    for c in ctxs:
+        c.profile(True)
+    with torch.cuda.stream(stream):
+        coarse_step()
+    kern = {}
+    for lev, c in enumerate(ctxs):
+        for k_, (t_, n_) in c.profile_read().items():
+            kern[f"l{lev}_{k_}"] = t_
+        c.profile(False)
+    launches = sum(c.launches() for c in ctxs[:1]) + 2 * ctxs[1].launches() + 4 * ctxs[2].launches()
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * upd / (ms * 1e-3), "unit": "cell-updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if prec == ctu.CTU_MIXED else "f64", "data": "synthetic",
+                "config": {"workload": "batched AMR level advance: 3-level hierarchy, ratio 2, base "
+                                       "128^3, PPM+HLLD+GLM, subcycled 1/2/4 in one CUDA graph, "
+                                       "coarse-fine flux registers",
+                           "patches_per_level": [len(lv["patches"]) for lv in L],
+                           "patch_sizes_per_level": hist, "cells_per_level": cells,
+                           "cell_updates_per_coarse_step": upd, "windows": sum(len(w) for w in wins),
+                           "l2_flush": "inputs larger than L2"},
+                "gpu_launches": launches * args.steps, "clocks": clk,
+                "kernels_ms_per_coarse_step": kern,
+                "status": [ctu.STATUS[x] for x in st], "gpu": torch.cuda.get_device_name(dev)}
+        print(json.dumps(line))
+
+
+def run_srmhd(args):
+    """Special-relativistic jet (config: 256^3, Gamma 4/3, beam gamma 10,
+    density ratio 0.01, sigma 0.1, 1% noise; MUSCL-Hancock, HLL, GLM, float64
+    Newton recovery): one ctu_step_next_dt per step on one patch."""
+    import torch
+    from paper_1110_0740_gb300 import ctu, workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    U0 = W.srmhd_jet_3d(n, seed=rank)
+    U = torch.from_numpy(U0.reshape(9, -1)).to(dev)
+    Uo = torch.empty_like(U)
+    stride = U.shape[1]
+    patches = ctu.make_patches([([n] * 3, [1.0 / n] * 3, 0)])
+    res = {}
+    for prec in ((ctu.CTU_MIXED, ctu.CTU_FP64) if not args.skip_other else (ctu.CTU_MIXED,)):
+        c = ctu.Ctx(ctu.make_config(ndim=3, gamma=4.0 / 3.0, recon=ctu.CTU_LINEAR_MC, precision=prec,
+                                    cfl=0.3, physics=ctu.CTU_SRMHD, predictor=ctu.CTU_MUSCL_HANCOCK,
+                                    riemann=ctu.CTU_HLL))
+        d0 = torch.zeros(2, dtype=torch.float64, device=dev)
+        d1 = torch.zeros_like(d0)
+        c.dt(U, stride, patches, d0)
+        K = args.steps if prec == ctu.CTU_MIXED else max(2, min(args.steps, 3))
+        for _ in range(args.warmup if prec == ctu.CTU_MIXED else 1):
+            c.step_next_dt(U, Uo, stride, patches, d0, d1)
+        torch.cuda.synchronize()
+        c.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            c.step_next_dt(U, Uo, stride, patches, d0, d1)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        res[prec] = (ms, {k: v[0] / K for k, v in c.profile_read().items()}, c.status_sync(),
+                     c.launches())
+        c.close()
+    ms, kern, st, nl = res[ctu.CTU_MIXED]
+    line = {"metric": METRIC, "value": world * n ** 3 / (ms * 1e-3), "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "3D SRMHD 256^3 jet, Gamma 4/3, gamma 10 beam, density ratio 0.01,"
+                                   " sigma 0.1; MUSCL-Hancock, HLL, GLM, float64 Newton recovery"},
+            "kernels_ms_per_step": kern, "gpu_launches": nl * args.steps,
+            "status": ctu.STATUS[st], "gpu": torch.cuda.get_device_name(dev)}
+    if ctu.CTU_FP64 in res:
+        ms2, kern2, st2, _ = res[ctu.CTU_FP64]
+        line["fp64_path"] = {"value": world * n ** 3 / (ms2 * 1e-3), "ms_per_step": ms2,
+                             "kernels_ms_per_step": kern2, "status": ctu.STATUS[st2]}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def load_flop_counts():
     p = os.path.join(ROOT, "profiles", "flops_per_cell.json")
     try:
@@ -396,11 +573,18 @@ def main():
     ap.add_argument("--skip-other", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--config", default="blast", choices=["blast", "amr", "srmhd"],
+                    help="blast: the 256^3 headline workload; amr: batched AMR level advance; "
+                         "srmhd: relativistic jet")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "amr":
+        run_amr(args)
+    elif args.config == "srmhd":
+        run_srmhd(args)
     else:
         run_ours(args)
 

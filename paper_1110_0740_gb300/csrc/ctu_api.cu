@@ -105,7 +105,7 @@ struct ctu_ctx {
     std::vector<ctu_flux_window> hwin;
     double *reg = nullptr;
     DevWindow *dwin = nullptr;
-    int *dwstart = nullptr;  // npatch * 3 starts then npatch * 3 counts
+    int *dwstart = nullptr;  // npatch * 3 CSR bases, then the plane positions
     int dwin_cap = 0, dws_cap = 0;
     bool win_dirty = false;
     int last_launches = 0;
@@ -142,8 +142,10 @@ static ctu_status validate_patches(const ctu_ctx *ctx, int64_t stride, const ctu
     return CTU_OK;
 }
 
-// Device table of flux windows, sorted by (device patch index, dir), with
-// per (patch, dir) start/count arrays.
+// Device table of flux windows, sorted by (device patch index, dir, plane),
+// with a per-(patch, dir) CSR index over planes (see StepArgs::wbase).
+// Windows of patches beyond the bound list, or with a plane outside
+// [0, n_dir], are ignored.
 static ctu_status upload_windows(ctu_ctx *ctx, cudaStream_t s)
 {
     const int np = (int)ctx->hpatch.size();
@@ -151,24 +153,36 @@ static ctu_status upload_windows(ctu_ctx *ctx, cudaStream_t s)
         ctx->win_dirty = false;
         return CTU_OK;
     }
-    struct W { int key; DevWindow w; };
+    struct W { long long key; int n_d; DevWindow w; };
     std::vector<W> v;
     for (const ctu_flux_window &x : ctx->hwin) {
         if (x.patch >= np) continue;
+        if (x.plane > ctx->hpatch[x.patch].n[x.dir]) continue;
         DevWindow w;
         w.patch = ctx->sorted_of[x.patch];
         w.dir = x.dir; w.plane = x.plane; w.a0 = x.a0; w.a1 = x.a1; w.b0 = x.b0; w.b1 = x.b1; w.pad = 0;
         w.weight = x.weight;
         w.dst = x.dst;
-        v.push_back({w.patch * 3 + w.dir, w});
+        v.push_back({((long long)(w.patch * 3 + w.dir) << 20) + w.plane, ctx->hpatch[x.patch].n[x.dir], w});
     }
     std::stable_sort(v.begin(), v.end(), [](const W &a, const W &b) { return a.key < b.key; });
     std::vector<DevWindow> dw(v.size() ? v.size() : 1);
-    std::vector<int> sc(2 * 3 * np, 0);
-    for (size_t i = 0; i < v.size(); ++i) {
-        dw[i] = v[i].w;
-        if (sc[3 * np + v[i].key] == 0) sc[v[i].key] = (int)i;
-        sc[3 * np + v[i].key] += 1;
+    for (size_t i = 0; i < v.size(); ++i) dw[i] = v[i].w;
+    // CSR: wbase (3 np entries) followed by the plane positions
+    std::vector<int> sc(3 * np, -1);
+    size_t i = 0;
+    while (i < v.size()) {
+        const int pd = (int)(v[i].key >> 20);
+        const int n_d = v[i].n_d;
+        const int base = (int)sc.size();
+        sc[pd] = base - 3 * np;
+        sc.resize(sc.size() + n_d + 2, 0);
+        size_t j = i;
+        for (int pl = 0; pl <= n_d + 1; ++pl) {
+            while (j < v.size() && (int)(v[j].key >> 20) == pd && v[j].w.plane < pl) ++j;
+            sc[base + pl] = (int)j;
+        }
+        while (i < v.size() && (int)(v[i].key >> 20) == pd) ++i;
     }
     if ((int)dw.size() > ctx->dwin_cap) {
         if (ctx->dwin) cudaFree(ctx->dwin);
@@ -303,8 +317,8 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.status = ctx->dstatus;
     const bool regs = ctx->reg && !ctx->hwin.empty();
     a.win = regs ? ctx->dwin : nullptr;
-    a.wstart = regs ? ctx->dwstart : nullptr;
-    a.wcount = regs ? ctx->dwstart + 3 * (int)ctx->hpatch.size() : nullptr;
+    a.wbase = regs ? ctx->dwstart : nullptr;
+    a.wpos = regs ? ctx->dwstart + 3 * (int)ctx->hpatch.size() : nullptr;
     a.reg = regs ? ctx->reg : nullptr;
     a.nextmax = nullptr;
     return a;

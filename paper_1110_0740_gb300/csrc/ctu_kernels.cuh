@@ -76,10 +76,12 @@ struct StepArgs {
     const double *dtch;    // device {dt, c_h}
     const StepParams *sp;  // device per-step parameters (written by k_setup)
     unsigned int *status;  // sticky status bits
-    // flux registers: windows sorted by (patch, dir); wstart/wcount per patch*3+dir
+    // flux registers: windows sorted by (patch, dir, plane); for patch*3+dir,
+    // wbase[] is -1 or an offset B into wpos[] such that the windows on plane
+    // pl are win[wpos[B + pl] .. wpos[B + pl + 1])
     const DevWindow *win;
-    const int *wstart;
-    const int *wcount;
+    const int *wbase;
+    const int *wpos;
     double *reg;
     unsigned long long *nextmax;  // nullable: max CFL speed of U^(n+1)
 };
@@ -395,10 +397,12 @@ template <class R, int D>
 __device__ __forceinline__ void register_face(const StepArgs &a, int patch, const DevPatch &P, int pl, int ca, int cb,
                                               const R (&Fg)[NV])
 {
-    const int ws = a.wstart[patch * 3 + D], wc = a.wcount[patch * 3 + D];
-    for (int w = 0; w < wc; ++w) {
-        const DevWindow W = a.win[ws + w];
-        if (W.plane != pl || ca < W.a0 || ca >= W.a1 || cb < W.b0 || cb >= W.b1) continue;
+    const int B = a.wbase[patch * 3 + D];
+    if (B < 0) return;
+    const int w0 = a.wpos[B + pl], w1 = a.wpos[B + pl + 1];
+    for (int w = w0; w < w1; ++w) {
+        const DevWindow W = a.win[w];
+        if (ca < W.a0 || ca >= W.a1 || cb < W.b0 || cb >= W.b1) continue;
         constexpr int ea = D == 0 ? 1 : 0, eb = D == 2 ? 1 : 2;
         const double f = W.weight * a.sp->dt * P.dx[ea] * P.dx[eb];
         const long long na = W.a1 - W.a0, nb = W.b1 - W.b0;

@@ -217,3 +217,112 @@ def srmhd_jet_3d(n=256, seed=0, gamma=4.0 / 3.0, lorentz=10.0, rho_ratio=0.01, s
     z = np.zeros((n, n, n))
     U = srmhd_cons([rho, vx, vy, vz, p, z, z, z + bz0, z], gamma)
     return pad_periodic(U, 3)
+
+
+# ------------------------------------------------------------------ AMR hierarchy
+
+def _cover(tags, sizes=(64, 32, 16, 8), fill=0.15):
+    """Cover the True cells of a boolean 3-D array with aligned cubes, largest
+    first: an aligned cube of size s is taken when it holds uncovered tags
+    that fill more than `fill` of it (any tag for the smallest size).
+    Returns [(origin(z,y,x), s)]."""
+    left = tags.copy()
+    out = []
+    nz, ny, nx = tags.shape
+    for s in sizes:
+        if nz % s or ny % s or nx % s:
+            continue
+        blk = left.reshape(nz // s, s, ny // s, s, nx // s, s)
+        frac = blk.mean(axis=(1, 3, 5))
+        take = frac > (fill if s > sizes[-1] else 0.0)
+        for (k, j, i) in zip(*np.nonzero(take)):
+            out.append(((k * s, j * s, i * s), s))
+        mask = np.repeat(np.repeat(np.repeat(take, s, 0), s, 1), s, 2)
+        left &= ~mask
+    return out
+
+
+def _shock_prim(xc, yc, zc, c, r0, gamma):
+    """Analytic state of an expanding spherical shock at cell centres: a
+    shell of width 0.02 at radius r0 around c with 4x density, 20x pressure
+    and radial outflow 1.5 behind it, uniform B = (0.6, 0.8, 0) / 2, psi = 0."""
+    dx_, dy_, dz_ = xc - c[0], yc - c[1], zc - c[2]
+    r = np.sqrt(dx_ * dx_ + dy_ * dy_ + dz_ * dz_) + 1e-12
+    inside = 0.5 * (1.0 - np.tanh((r - r0) / 0.01))
+    shell = np.exp(-((r - r0) / 0.02) ** 2)
+    rho = 1.0 + 3.0 * shell
+    p = 1.0 + 19.0 * inside
+    vr = 1.5 * shell
+    z = np.zeros_like(r)
+    return [rho, vr * dx_ / r, vr * dy_ / r, vr * dz_ / r, p, z + 0.3, z + 0.4, z, z]
+
+
+def amr_hierarchy(seed=0, base=128, target=600, gamma=5.0 / 3.0):
+    """Seeded 3-level hierarchy (refinement ratio 2, base `base`^3 cells on the
+    unit cube as 8 patches of (base/2)^3) around an expanding spherical shock.
+    Level l+1 tags the cells of level l within a shell around the shock
+    radius and covers them with aligned cubes from {64, 32, 16, 8} (in level
+    l+1 cells), largest first, each inside one level-l patch (proper
+    nesting).  The shell width is tuned by bisection so that the hierarchy
+    has about `target` patches.  Returns a dict with, per level, the patch
+    list [(n(3), dx(3), base offset)], the float64 pool (9, stride) with
+    ghosts filled from the analytic state, and the footprints of every
+    level-(l+1) patch in its parent (parent index, origin in parent cells,
+    size in parent cells)."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0.4, 0.6, size=3)
+    r0 = rng.uniform(0.18, 0.25)
+
+    def build(width):
+        levels = [[((k, j, i), base // 2) for k in (0, base // 2) for j in (0, base // 2)
+                   for i in (0, base // 2)]]
+        parents = [[]]
+        for lev in (1, 2):
+            h = 1.0 / (base * 2 ** lev)
+            plist, par = [], []
+            for pi, (o, s) in enumerate(levels[-1]):
+                # children cells of parent patch pi, in level-lev index space
+                n = 2 * s
+                oz, oy, ox = (2 * v for v in o)
+                x = (np.arange(n) + ox + 0.5) * h
+                y = (np.arange(n) + oy + 0.5) * h
+                z = (np.arange(n) + oz + 0.5) * h
+                rr = np.sqrt((z[:, None, None] - c[2]) ** 2 + (y[None, :, None] - c[1]) ** 2
+                             + (x[None, None, :] - c[0]) ** 2)
+                tags = np.abs(rr - r0) < width / lev
+                for (lo, sz) in _cover(tags):
+                    plist.append(((lo[0] + oz, lo[1] + oy, lo[2] + ox), sz))
+                    par.append(pi)
+            levels.append(plist)
+            parents.append(par)
+        return levels, parents
+
+    best = None
+    for width in np.geomspace(0.004, 0.12, 16):
+        levels, parents = build(width)
+        tot = sum(len(L) for L in levels)
+        if best is None or abs(tot - target) < abs(best[0] - target):
+            best = (tot, levels, parents)
+    tot, levels, parents = best
+    out = {"levels": [], "center": c, "radius": r0}
+    for lev, plist in enumerate(levels):
+        h = 1.0 / (base * 2 ** lev)
+        specs, off, chunks = [], 0, []
+        for (o, s) in plist:
+            g = np.arange(-4, s + 4) + 0.5
+            xc = (o[2] + g) * h
+            yc = (o[1] + g) * h
+            zc = (o[0] + g) * h
+            Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+            U = ideal_cons(_shock_prim(X, Y, Z, c, r0, gamma), gamma)
+            specs.append(([s, s, s], [h, h, h], off, lev))
+            chunks.append(U.reshape(9, -1))
+            off += U[0].size
+        pool = np.concatenate(chunks, axis=1)
+        foot = []
+        if lev > 0:
+            for (o, s), pi in zip(plist, parents[lev]):
+                po, ps = levels[lev - 1][pi]
+                foot.append((pi, tuple((o[d] // 2 - po[d]) for d in range(3)), s // 2))
+        out["levels"].append({"patches": specs, "pool": pool, "origins": plist, "footprints": foot})
+    return out

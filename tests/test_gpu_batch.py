@@ -175,3 +175,30 @@ def test_step_next_dt_matches_ctu_dt_of_result(prec):
     assert torch.equal(Ua, Ub) or prec == 0 and torch.allclose(Ua, Ub, rtol=0, atol=0)
     a, b = d1.cpu().numpy(), d2.cpu().numpy()
     assert np.allclose(a, b, rtol=1e-13 if prec == 0 else 1e-6, atol=0), (a, b)
+
+
+def test_cuda_graph_replay_matches_direct_step():
+    """A level step captured in a CUDA graph and replayed gives bitwise the
+    same result as the direct call (patch list bound before capture)."""
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    H = W.amr_hierarchy(seed=2, base=32, target=40)
+    lv = H["levels"][1]
+    dev = _dev()
+    U = torch.from_numpy(lv["pool"]).to(dev)
+    A, B = torch.zeros_like(U), torch.zeros_like(U)
+    P = ctu.make_patches([(n, dx, b) for (n, dx, b, _) in lv["patches"]])
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_MIXED))
+    d = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.dt(U, U.shape[1], P, d)
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        ctx.step(U, A, U.shape[1], P, d, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.step(U, B, U.shape[1], P, d, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert ctx.status_sync() == 0
+    assert torch.equal(A, B)
