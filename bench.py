@@ -39,8 +39,8 @@ METRIC = "MHD cell-updates/s per CTU step"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP32_LANES = 128
-FP64_PEAK_NOMINAL = 1.25e12  # GB300 FP64 (non-tensor and tensor) nominal
-BYTES_PER_CELL_F64_IO = None  # computed per patch: 9 vars x 8 B x (ghosted + interior)
+FP32_PEAK = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6   # 80.5 TFLOP/s
+FP64_PEAK = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6            # 1.26 TFLOP/s (2 DFMA/SM/clk)
 
 
 def measured_peaks():
@@ -278,47 +278,33 @@ def run_ours(args):
     ms_step = res["ms_total"] / res["K"]
     value = world * cells / (ms_step * 1e-3)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (ALU-bound: FP32 pipe for the mixed
+    # path, FP64 pipe for the FP64 path), algorithmic flops per cell from the
+    # oracle count in profiles/flops_per_cell.txt
     peaks, src = measured_peaks()
     kern = res["kern"]
-    top = max(kern.items(), key=lambda kv: kv[1][0]) if kern else ("?", (0.0, 1))
-    top_name, (top_ms, top_cnt) = top
+    top_name, (top_ms, top_cnt) = max(kern.items(), key=lambda kv: kv[1][0])
     top_avg = top_ms / max(1, top_cnt)
-    step_kernel_ms = sum(v[0] for v in kern.values()) / res["K"]
+    fl = kernel_flops(n)
+    mixed = primary == ctu.CTU_MIXED
+    peak_tf = (FP32_PEAK if mixed else FP64_PEAK) / 1e12
+    f_top = fl.get(top_name, 0.0)
+    achieved = f_top / (top_avg * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+            "frac": achieved / peak_tf, "traffic": kernel_traffic(top_name, n), "kernel": top_name,
+            "pipe": "fp32" if mixed else "fp64",
+            "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if mixed else
+                            "derived: 152 SMs x 2 FP64 lanes x 2 x 2070 MHz (GB300 nominal 1.25 TF)"),
+            "flops_per_launch": f_top, "kernel_avg_ms": top_avg,
+            "kernels_ms_per_step": {k: v[0] / res["K"] for k, v in kern.items()}}
+    step_ms = sum(v[0] for v in kern.values()) / res["K"]
+    roof["step"] = {"flops": sum(fl.values()), "achieved_tflops": sum(fl.values()) / (step_ms * 1e-3) / 1e12,
+                    "frac": sum(fl.values()) / (step_ms * 1e-3) / 1e12 / peak_tf}
     nbytes = algorithmic_bytes(n)
-    hbm_achieved = nbytes / (step_kernel_ms * 1e-3) / 1e9
-    sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ
-    fp64_peak = FP64_PEAK_NOMINAL
-    fp32_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6
-    flops = load_flop_counts()
-    key = "mixed" if primary == ctu.CTU_MIXED else "fp64"
-    roof = None
-    if flops and top_name in flops.get(key, {}):
-        fc = flops[key][top_name]
-        # cells processed per launch of this kernel = interior cells (per direction)
-        f32 = fc.get("f32", 0.0) * cells
-        f64 = fc.get("f64", 0.0) * cells
-        t = top_avg * 1e-3
-        frac32 = (f32 / t) / fp32_peak
-        frac64 = (f64 / t) / fp64_peak
-        if frac64 >= frac32:
-            roof = {"bound": "alu", "achieved": f64 / t / 1e12, "peak": fp64_peak / 1e12,
-                    "unit": "TFLOP/s", "frac": frac64, "traffic": None,
-                    "kernel": top_name, "pipe": "fp64", "fp32_frac": frac32,
-                    "peak_source": "derived: nominal GB300 FP64 1.25 TFLOP/s"}
-        else:
-            roof = {"bound": "alu", "achieved": f32 / t / 1e12, "peak": fp32_peak / 1e12,
-                    "unit": "TFLOP/s", "frac": frac32, "traffic": None,
-                    "kernel": top_name, "pipe": "fp32", "fp64_frac": frac64,
-                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
-    if roof is None:
-        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": hbm_achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "whole step",
-                "peak_source": f"{src} hbm_gbs"}
-    roof["kernel_avg_ms"] = top_avg
-    roof["kernels_ms_per_step"] = {k: v[0] / res["K"] for k, v in kern.items()}
+    hbm_achieved = nbytes / (step_ms * 1e-3) / 1e9
     roof["hbm_step"] = {"algorithmic_bytes": nbytes, "achieved_gbs": hbm_achieved,
-                        "frac_of_measured": hbm_achieved / peaks["hbm_gbs"]}
+                        "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
+                        "peak_source": f"{src} hbm_gbs"}
 
     # end-to-end through the public API with host buffers
     e2e = None
@@ -552,13 +538,48 @@ def run_srmhd(args):
         print(json.dumps(line))
 
 
-def load_flop_counts():
-    p = os.path.join(ROOT, "profiles", "flops_per_cell.json")
+def _profile_numbers(name):
+    vals = {}
     try:
-        with open(p) as f:
-            return json.load(f)
-    except Exception:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            for line in f:
+                if line.strip() and not line.startswith("#"):
+                    k, v = line.split()[:2]
+                    vals[k] = v
+    except OSError:
+        pass
+    return vals
+
+
+def kernel_flops(n):
+    """Algorithmic flops per launch of each kernel group of one 3-D PPM step
+    on an n^3 patch: the oracle's operation counts per interior cell
+    (profiles/flops_per_cell.txt, exact-zero operands not counted) times n^3."""
+    c = {k: float(v) for k, v in _profile_numbers("flops_per_cell.txt").items()}
+    cells = float(n) ** 3
+    sweep = c.get("sweep_per_direction_ppm", 0.0)
+    return {"prim": c.get("prim", 0.0) * cells, "flux1": 3 * c.get("flux1_per_direction", 0.0) * cells,
+            "sweep_x": sweep * cells, "sweep_y": sweep * cells,
+            "sweep_z": (sweep + c.get("update", 0.0) + c.get("next_dt", 0.0)) * cells}
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1110_0740_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1110_0740_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic(name, n):
+    """DRAM bytes (read + write) per launch of `name` on an n^3 patch, scaled
+    by cells from the ncu capture recorded in profiles/dram_traffic.txt; None
+    if there is no record or the kernel sources changed since it was taken."""
+    t = _profile_numbers("dram_traffic.txt")
+    if t.get("source_hash") != kernel_source_hash() or f"{name}_bytes_per_cell" not in t:
         return None
+    return float(t[f"{name}_bytes_per_cell"]) * float(n) ** 3
 
 
 def main():

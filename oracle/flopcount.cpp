@@ -1,0 +1,108 @@
+// flopcount.cpp -- count the floating-point operations of the CPU oracle's
+// building blocks (test infrastructure; run by oracle/flopcount.py).
+//
+// The oracle source is compiled as C++ with `double` replaced by a counting
+// number type: every +, -, *, / and sqrt on it increments a counter, except
+// a +, - or * with an exact-zero operand (fabs, fmin, fmax, copysign and
+// comparisons are not counted as flops; exp is counted on its own).  The driver reads states (local 1-D order) from
+// stdin and prints the average counts per call of or_mhd_riemann,
+// or_mhd_char_predict (linear and PPM), or_mhd_prim2cons and
+// or_mhd_cons2prim.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+namespace fc {
+struct Counts {
+    unsigned long long add = 0, mul = 0, div = 0, sqrt = 0, exp = 0;
+};
+static Counts g;
+
+struct Flop {
+    double v;
+    Flop() = default;
+    Flop(double x) : v(x) {}
+};
+// an operation with an exact-zero operand (the oracle's dense eigenvector
+// matrices hold structural zeros) is not counted
+inline Flop operator+(Flop a, Flop b) { if (a.v != 0.0 && b.v != 0.0) ++g.add; return Flop(a.v + b.v); }
+inline Flop operator-(Flop a, Flop b) { if (a.v != 0.0 && b.v != 0.0) ++g.add; return Flop(a.v - b.v); }
+inline Flop operator*(Flop a, Flop b) { if (a.v != 0.0 && b.v != 0.0) ++g.mul; return Flop(a.v * b.v); }
+inline Flop operator/(Flop a, Flop b) { ++g.div; return Flop(a.v / b.v); }
+inline Flop operator-(Flop a) { return Flop(-a.v); }
+inline Flop &operator+=(Flop &a, Flop b) { a = a + b; return a; }
+inline Flop &operator-=(Flop &a, Flop b) { a = a - b; return a; }
+inline Flop &operator*=(Flop &a, Flop b) { a = a * b; return a; }
+inline Flop &operator/=(Flop &a, Flop b) { a = a / b; return a; }
+inline bool operator<(Flop a, Flop b) { return a.v < b.v; }
+inline bool operator>(Flop a, Flop b) { return a.v > b.v; }
+inline bool operator<=(Flop a, Flop b) { return a.v <= b.v; }
+inline bool operator>=(Flop a, Flop b) { return a.v >= b.v; }
+inline bool operator==(Flop a, Flop b) { return a.v == b.v; }
+inline bool operator!=(Flop a, Flop b) { return a.v != b.v; }
+inline Flop sqrt(Flop a) { ++g.sqrt; return Flop(std::sqrt(a.v)); }
+inline Flop fabs(Flop a) { return Flop(std::fabs(a.v)); }
+inline Flop fmin(Flop a, Flop b) { return Flop(std::fmin(a.v, b.v)); }
+inline Flop fmax(Flop a, Flop b) { return Flop(std::fmax(a.v, b.v)); }
+inline Flop copysign(Flop a, Flop b) { return Flop(std::copysign(a.v, b.v)); }
+inline Flop exp(Flop a) { ++g.exp; return Flop(std::exp(a.v)); }
+} // namespace fc
+
+using fc::Flop;
+using fc::sqrt;
+using fc::fabs;
+using fc::fmin;
+using fc::fmax;
+using fc::copysign;
+using fc::exp;
+
+#define double Flop
+#include "ctu_oracle.c"
+#undef double
+
+static double total(const fc::Counts &c)
+{
+    return (double)(c.add + c.mul + c.div + c.sqrt);
+}
+
+int main()
+{
+    // input: count K, gamma, ch, dtdx, then K stencils of 5 x 9 values (local order)
+    int K;
+    double gam, ch, dtdx;
+    if (scanf("%d %lf %lf %lf", &K, &gam, &ch, &dtdx) != 4) return 1;
+    double *S = (double *)malloc(sizeof(double) * 45 * K);
+    for (int i = 0; i < 45 * K; ++i)
+        if (scanf("%lf", &S[i]) != 1) return 1;
+    double r_riem = 0, r_pred0 = 0, r_pred1 = 0, r_p2c = 0, r_c2p = 0, r_cf = 0;
+    for (int k = 0; k < K; ++k) {
+        Flop vs[45], VL[9], VR[9], F[9], Vp[9], Vm[9], U[9], V[9];
+        for (int i = 0; i < 45; ++i) vs[i] = Flop(S[45 * k + i]);
+        for (int q = 0; q < 9; ++q) {
+            VL[q] = vs[18 + q];
+            VR[q] = vs[27 + q];
+        }
+        fc::g = fc::Counts();
+        or_mhd_riemann(VL, VR, Flop(gam), Flop(ch), F);
+        r_riem += total(fc::g);
+        fc::g = fc::Counts();
+        or_mhd_char_predict(vs, Flop(gam), Flop(ch), Flop(dtdx), 0, 0, Vp, Vm);
+        r_pred0 += total(fc::g);
+        fc::g = fc::Counts();
+        or_mhd_char_predict(vs, Flop(gam), Flop(ch), Flop(dtdx), 1, 0, Vp, Vm);
+        r_pred1 += total(fc::g);
+        fc::g = fc::Counts();
+        or_mhd_prim2cons(VL, Flop(gam), U);
+        r_p2c += total(fc::g);
+        fc::g = fc::Counts();
+        or_mhd_cons2prim(U, Flop(gam), V);
+        r_c2p += total(fc::g);
+        fc::g = fc::Counts();
+        or_mhd_cfast(VL, Flop(gam));
+        r_cf += total(fc::g);
+    }
+    printf("riemann %.2f\npredict_linear %.2f\npredict_ppm %.2f\nprim2cons %.2f\ncons2prim %.2f\ncfast %.2f\n",
+           r_riem / K, r_pred0 / K, r_pred1 / K, r_p2c / K, r_c2p / K, r_cf / K);
+    return 0;
+}

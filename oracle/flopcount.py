@@ -1,0 +1,97 @@
+"""Algorithmic flop counts per cell update of the CTU-MHD step, counted in the
+CPU oracle (test infrastructure).
+
+Builds oracle/flopcount.cpp (the oracle compiled with a counting number
+type that skips operations on exact zeros, i.e. the structural zeros of the
+eigenvector matrices), feeds it stencils sampled from the blast workload
+(advanced two steps) and prints
+the per-building-block averages and the per-cell totals of each stage of
+the step, in the large-patch limit:
+
+  prim        1 x cons2prim
+  flux1 (d)   1 x riemann
+  sweep (d)   predict + 2 prim2cons + 2 cons2prim + riemann
+              + 18 (half-step transverse increments of two directions,
+                    9 x (sub, mul) each) + 18 (U* + dt/2 T) + 18 (flux
+                    difference x 1/dx)
+  update      9 x 2 (dt x sum + U) + 2 (sum of three directions) x 9 + 1 (psi)
+  next dt     cons2prim + ndim x (cfast + 2)
+
+    python oracle/flopcount.py [--out profiles/flops_per_cell.txt]
+"""
+import argparse
+import os
+import subprocess
+import sys
+import tempfile
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+sys.path.insert(0, str(HERE.parent))
+
+
+def build():
+    exe = Path(tempfile.gettempdir()) / "ctu_flopcount"
+    subprocess.run(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-I", str(HERE),
+                    str(HERE / "flopcount.cpp"), "-o", str(exe)], check=True)
+    return exe
+
+
+def stencils(n=48, samples=2000, seed=0):
+    """Stencils along x from the blast workload after two oracle steps (so that
+    psi and every field is generic, not an exact zero)."""
+    import oracle as O
+    from paper_1110_0740_gb300 import workloads as W
+    U = W.mhd_blast_3d(n, seed=seed)
+    U, _, _ = O.mhd_run(U, [n] * 3, 3, [1.0 / n] * 3, 2, 0.3, recon=1)
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(samples):
+        k, j, i = (int(v) for v in rng.integers(4, n + 4, size=3))
+        vs = []
+        for m in range(-2, 3):
+            V, bad = O.mhd_cons2prim(U[:, k, j, i + m], 5.0 / 3.0)
+            vs.append(V)
+        out.append(np.array(vs))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    exe = build()
+    st = stencils()
+    txt = f"{len(st)} {5.0 / 3.0!r} 3.0 0.1\n" + "\n".join(" ".join(repr(float(x)) for x in s.ravel())
+                                                           for s in st)
+    res = subprocess.run([str(exe)], input=txt.encode(), capture_output=True, check=True)
+    c = {}
+    for line in res.stdout.decode().splitlines():
+        k, v = line.split()
+        c[k] = float(v)
+    prim = c["cons2prim"]
+    flux1 = c["riemann"]
+    sweep = {r: c[f"predict_{r}"] + 2 * c["prim2cons"] + 2 * c["cons2prim"] + c["riemann"] + 54
+             for r in ("ppm", "linear")}
+    update = 9 * 2 + 9 * 2 + 1
+    nextdt = c["cons2prim"] + 3 * (c["cfast"] + 2)
+    lines = ["# oracle flops per call, exact-zero operands not counted (averages over %d stencils"
+             " of the blast workload after two steps)" % len(st),
+             "# produced by: python oracle/flopcount.py --out profiles/flops_per_cell.txt"]
+    lines += [f"{k} {v:.1f}" for k, v in c.items()]
+    lines += ["# per interior cell update, large-patch limit, 3-D",
+              f"prim {prim:.1f}", f"flux1_per_direction {flux1:.1f}",
+              f"sweep_per_direction_ppm {sweep['ppm']:.1f}",
+              f"sweep_per_direction_linear {sweep['linear']:.1f}",
+              f"update {update:.1f}", f"next_dt {nextdt:.1f}",
+              f"step_total_ppm {prim + 3 * flux1 + 3 * sweep['ppm'] + update + nextdt:.1f}"]
+    text = "\n".join(lines) + "\n"
+    print(text)
+    if args.out:
+        Path(args.out).write_text(text)
+
+
+if __name__ == "__main__":
+    main()
