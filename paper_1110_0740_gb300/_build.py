@@ -22,8 +22,9 @@ def nvcc():
 
 
 def flags(extra=()):
+    env = os.environ.get("CTU_NVCC_EXTRA", "").split()
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-I", str(ROOT / "include"), "-I", str(CSRC)] + list(extra)
+                   "-I", str(ROOT / "include"), "-I", str(CSRC)] + env + list(extra)
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> Path:

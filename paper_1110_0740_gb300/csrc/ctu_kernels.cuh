@@ -89,7 +89,15 @@ struct StepArgs {
 enum : unsigned int { ST_NEG = 1u, ST_NAN = 2u };
 
 constexpr int BLOCK = 128;
-constexpr int SEG = 32;  // cells per marching segment
+#ifndef CTU_SEG
+#define CTU_SEG 16
+#endif
+#ifndef CTU_MARCH_MINB
+#define CTU_MARCH_MINB 3
+#endif
+constexpr int SEG = CTU_SEG;  // cells per marching segment
+// The marching sweeps are latency bound: they are compiled for at least
+// CTU_MARCH_MINB resident blocks per SM (register cap 65536 / (BLOCK * MINB)).
 
 // Local component q of a sweep along D reads global component gperm<D>(q).
 template <int D> __host__ __device__ constexpr int gperm(int q)
@@ -643,7 +651,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const 
 // previous face flux stay in registers.  A tile: xw lanes along x times
 // BLOCK/xw (other-dimension, segment) pairs.
 template <int PHYS, class R, int PPM, int IFACE64, int D, int LAST>
-__global__ void __launch_bounds__(BLOCK) k_sweep_m(StepArgs a, int first, const R *Vs, const R *F1, R *A)
+__global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, int first, const R *Vs, const R *F1, R *A)
 {
     constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
     const int patch = first + blockIdx.y;
