@@ -123,10 +123,12 @@ def dist_env():
 
 # ------------------------------------------------------------------ oracle (CPU)
 
-def oracle_sample(U0, n_full, sub, steps=1, seed=0):
+def oracle_sample(U0, n_full, sub, steps=1, min_seconds=0.0, max_steps=64):
     """Time the CPU oracle on a bounded sample of the workload: a sub x sub x
     sub block of the 256^3 state (with its true neighbours as ghosts), one CTU
-    step per repetition.  Returns (cell-updates/s, seconds, sample text)."""
+    step per repetition, `steps` repetitions or more until min_seconds have
+    passed (at most max_steps).  Returns (cell-updates/s, seconds, sample
+    text)."""
     import numpy as np
     import oracle as O
     g = 4
@@ -137,9 +139,12 @@ def oracle_sample(U0, n_full, sub, steps=1, seed=0):
     m = O.mhd_max_speed(blk, n, 3, dx)
     dt, ch = O.dt_ch(m, dx, 3, 0.3)
     t0 = time.perf_counter()
-    for _ in range(steps):
+    done = 0
+    while done < steps or (time.perf_counter() - t0 < min_seconds and done < max_steps):
         out, bad = O.mhd_step(blk, n, 3, dx, dt, ch, recon=1)
+        done += 1
     el = time.perf_counter() - t0
+    steps = done
     cells = sub ** 3 * steps
     return cells / el, el, f"{sub}^3 interior block of the 256^3 state, {steps} CTU step(s), 1 thread"
 
@@ -152,7 +157,7 @@ def run_reference(args):
     from paper_1110_0740_gb300 import workloads as W
     U0 = W.mhd_blast_3d(N_CELLS, seed=0)
     vals = []
-    sub = 32
+    sub = 64
     for _ in range(max(1, args.warmup)):
         oracle_sample(U0, N_CELLS, sub)
     t0 = time.perf_counter()
@@ -340,7 +345,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
-        v, el, txt = oracle_sample(U0, n, 32)
+        v, el, txt = oracle_sample(U0, n, min(64, n), min_seconds=10.0)
         cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": txt,
                "seconds": el}
 

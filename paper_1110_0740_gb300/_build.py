@@ -11,6 +11,11 @@ CSRC = PKG / "csrc"
 OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "libctu.so"
 SOURCES = ["ctu_api.cu", "ctu_f64.cu", "ctu_f32.cu", "ctu_f32i.cu", "ctu_sr32.cu", "ctu_noalloc.cu"]
+# The float32 stages of the mixed paths divide and take square roots with the
+# approximate hardware forms (<= 2 ulp) and flush float32 denormals; float64
+# arithmetic is unaffected by these flags.
+FLOAT_FAST = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+SOURCE_FLAGS = {"ctu_f32.cu": FLOAT_FAST, "ctu_f32i.cu": FLOAT_FAST, "ctu_sr32.cu": FLOAT_FAST}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,7 +43,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> Path:
     procs = []
     for s in SOURCES:
         o = OUT_DIR / (Path(s).stem + ".o")
-        cmd = [nvcc(), "-c", str(CSRC / s), "-o", str(o)] + flags(extra)
+        cmd = [nvcc(), "-c", str(CSRC / s), "-o", str(o)] + SOURCE_FLAGS.get(s, []) + flags(extra)
         if verbose:
             cmd += ["-Xptxas", "-v"]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -95,9 +95,13 @@ constexpr int BLOCK = 128;
 #ifndef CTU_MARCH_MINB
 #define CTU_MARCH_MINB 3
 #endif
+#ifndef CTU_SWEEPX_MINB
+#define CTU_SWEEPX_MINB 5
+#endif
 constexpr int SEG = CTU_SEG;  // cells per marching segment
 // The marching sweeps are latency bound: they are compiled for at least
-// CTU_MARCH_MINB resident blocks per SM (register cap 65536 / (BLOCK * MINB)).
+// CTU_MARCH_MINB resident blocks per SM (register cap 65536 / (BLOCK * MINB)),
+// the float x sweep for CTU_SWEEPX_MINB.
 
 // Local component q of a sweep along D reads global component gperm<D>(q).
 template <int D> __host__ __device__ constexpr int gperm(int q)
@@ -129,6 +133,24 @@ __device__ __forceinline__ void prefetch_l1(const void *p)
 {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
+
+// Asynchronous global -> shared copies (cp.async, per thread): the data land
+// in shared memory without occupying registers while in flight.
+__device__ __forceinline__ void cp_async(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async(double *dst, const double *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most one committed group of this thread is still in flight
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned int state_flags(double rho, double p)
 {
@@ -195,10 +217,7 @@ __device__ __forceinline__ unsigned int prim_of<float>(const double (&U)[NV], co
     const float ir = 1.0f / r[0];
     V[0] = r[0]; V[1] = r[1] * ir; V[2] = r[2] * ir; V[3] = r[3] * ir; V[4] = p;
     V[5] = r[5]; V[6] = r[6]; V[7] = r[7]; V[8] = r[8];
-    unsigned int f = 0;
-    if (!(r[0] > 0.0f) || !(p > 0.0f)) f |= ST_NEG;
-    if (!isfinite(r[0]) || !isfinite(p)) f |= ST_NAN;
-    return f;
+    return ((!(r[0] > 0.0f) | !(p > 0.0f)) ? ST_NEG : 0u) | ((!isfinite(r[0]) | !isfinite(p)) ? ST_NAN : 0u);
 }
 
 // R -> float64 for the update accumulation (integer widening for float).
@@ -311,10 +330,7 @@ __device__ __forceinline__ unsigned int interface_state(const R (&W)[NV], const 
         out[6] = W[6] + T[6];
         out[7] = W[7] + T[7];
         out[8] = W[8] + T[8];
-        unsigned int f = 0;
-        if (!(rho > R(0)) || !(p > R(0))) f |= ST_NEG;
-        if (!isfinite(rho) || !isfinite(p)) f |= ST_NAN;
-        return f;
+        return ((!(rho > R(0)) | !(p > R(0))) ? ST_NEG : 0u) | ((!isfinite(rho) | !isfinite(p)) ? ST_NAN : 0u);
     }
 }
 
@@ -341,12 +357,13 @@ __device__ __forceinline__ unsigned int sr_interface(const R (&W)[NV], const R (
 // Trace one cell along D: stencil (local order) -> interface states (global).
 // MHD: characteristic tracing (Section 3.2).  SRMHD: MUSCL-Hancock in
 // primitive variables (Section 3.3) from V_(i-1..i+1) and U_i^n.
+// T: the half-step transverse increments of the cell (see transverse()).
 template <int PHYS, class R, int PPM, int IFACE64, int D>
-__device__ __forceinline__ unsigned int trace_cell(const StepArgs &a, const DevPatch &P, const R (&vs)[5][NV],
-                                                   const R *F1, long long c, R ch, R dtdx, R hdt, R (&Vp)[NV],
-                                                   R (&Vm)[NV])
+__device__ __forceinline__ unsigned int trace_cell_t(const StepArgs &a, const DevPatch &P, const R (&vs)[5][NV],
+                                                     const R (&T)[NV], long long c, R ch, R dtdx, R (&Vp)[NV],
+                                                     R (&Vm)[NV])
 {
-    R pl[NV], ml[NV], pg[NV], mg[NV], T[NV];
+    R pl[NV], ml[NV], pg[NV], mg[NV];
     unsigned int f = 0;
     if (PHYS == PH_MHD) {
         char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind != 0, pl, ml);
@@ -362,7 +379,6 @@ __device__ __forceinline__ unsigned int trace_cell(const StepArgs &a, const DevP
         pg[gperm<D>(q)] = pl[q];
         mg[gperm<D>(q)] = ml[q];
     }
-    transverse<R, D>(a, P, F1, c, hdt, T);
     if (PHYS == PH_MHD) {
         f |= interface_state<R, IFACE64>(pg, T, a, Vp);
         f |= interface_state<R, IFACE64>(mg, T, a, Vm);
@@ -371,6 +387,16 @@ __device__ __forceinline__ unsigned int trace_cell(const StepArgs &a, const DevP
         f |= sr_interface<R>(mg, T, a, Vm);
     }
     return f;
+}
+
+template <int PHYS, class R, int PPM, int IFACE64, int D>
+__device__ __forceinline__ unsigned int trace_cell(const StepArgs &a, const DevPatch &P, const R (&vs)[5][NV],
+                                                   const R *F1, long long c, R ch, R dtdx, R hdt, R (&Vp)[NV],
+                                                   R (&Vm)[NV])
+{
+    R T[NV];
+    transverse<R, D>(a, P, F1, c, hdt, T);
+    return trace_cell_t<PHYS, R, PPM, IFACE64, D>(a, P, vs, T, c, ch, dtdx, Vp, Vm);
 }
 
 // Numerical flux along the local normal for either physics.
@@ -403,7 +429,7 @@ __device__ __forceinline__ void face_flux(const R (&Lg)[NV], const R (&Rg)[NV], 
 // coordinates ca, cb in increasing dimension order), Eq. (fluxcorr).
 template <class R, int D>
 __device__ __forceinline__ void register_face(const StepArgs &a, int patch, const DevPatch &P, int pl, int ca, int cb,
-                                              const R (&Fg)[NV])
+                                              const R (&Fg)[NV], double dt)
 {
     const int B = a.wbase[patch * 3 + D];
     if (B < 0) return;
@@ -412,7 +438,7 @@ __device__ __forceinline__ void register_face(const StepArgs &a, int patch, cons
         const DevWindow W = a.win[w];
         if (ca < W.a0 || ca >= W.a1 || cb < W.b0 || cb >= W.b1) continue;
         constexpr int ea = D == 0 ? 1 : 0, eb = D == 2 ? 1 : 2;
-        const double f = W.weight * a.sp->dt * P.dx[ea] * P.dx[eb];
+        const double f = W.weight * dt * P.dx[ea] * P.dx[eb];
         const long long na = W.a1 - W.a0, nb = W.b1 - W.b0;
         const long long o = W.dst + (long long)(cb - W.b0) * na + (ca - W.a0);
 #pragma unroll
@@ -422,14 +448,14 @@ __device__ __forceinline__ void register_face(const StepArgs &a, int patch, cons
 
 // Final update of one interior cell: U^(n+1) = U^n + dt s, psi source, and
 // the CFL speed of U^(n+1) if requested (returned in R; 0 otherwise).
+// u0: U^n of the cell.
 template <int PHYS, class R>
-__device__ __forceinline__ R finish_cell(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
-                                         double damp, unsigned int &fl)
+__device__ __forceinline__ R finish_cell_u(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
+                                           const double (&u0)[NV], double dt, double damp, unsigned int &fl)
 {
-    const double dt = a.sp->dt;
     double u[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) u[q] = fma(dt, widen<R>(s[q]), a.U[q * a.ustride + P.base + cl]);
+    for (int q = 0; q < NV; ++q) u[q] = fma(dt, widen<R>(s[q]), u0[q]);
     u[8] *= damp;
 #pragma unroll
     for (int q = 0; q < NV; ++q) a.Uout[q * a.ustride + P.base + cl] = u[q];
@@ -437,6 +463,39 @@ __device__ __forceinline__ R finish_cell(const StepArgs &a, const DevPatch &P, i
     R V[NV];
     fl |= prim_any<PHYS, R>(u, a, V);
     return cell_speed<PHYS, R>(V, a, P);
+}
+
+// Ideal MHD in float: as finish_cell_u, but the CFL speed of U^(n+1) comes
+// from the primitive state V^n of the cell (global order) and the increment
+// dt s through the exact increment form of the pressure (interface_state),
+// so that U^(n+1) itself is never split or recovered in double-float.
+template <class R>
+__device__ __forceinline__ R finish_cell_inc(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
+                                             const double (&u0)[NV], const R (&Vn)[NV], double dt, R dtr,
+                                             double damp, unsigned int &fl)
+{
+    double u[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) u[q] = fma(dt, widen<R>(s[q]), u0[q]);
+    u[8] *= damp;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) a.Uout[q * a.ustride + P.base + cl] = u[q];
+    if (!a.nextmax) return R(0);
+    R d[NV], V[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) d[q] = dtr * s[q];
+    fl |= interface_state<R, 0>(Vn, d, a, V);
+    return cell_speed<PH_MHD, R>(V, a, P);
+}
+
+template <int PHYS, class R>
+__device__ __forceinline__ R finish_cell(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
+                                         double dt, double damp, unsigned int &fl)
+{
+    double u0[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) u0[q] = a.U[q * a.ustride + P.base + cl];
+    return finish_cell_u<PHYS, R>(a, P, cl, s, u0, dt, damp, fl);
 }
 
 // Block maximum of a non-negative value, folded into *out as the bits of a
@@ -482,8 +541,8 @@ struct Tiles {
     static int xw(int nx) { return tile_xw(nx); }
     static long long prim(const int *n, const int *N)
     {
-        const int w = xw(n[0]), r = BLOCK / w;
-        return (long long)((N[0] + w - 1) / w) * ((N[1] + r - 1) / r) * N[2];
+        (void)n;
+        return ((long long)N[0] * N[1] * N[2] + BLOCK - 1) / BLOCK;
     }
     static long long flux1(const int *n, int ndim, int D)
     {
@@ -522,19 +581,14 @@ static __global__ void k_setup(const double *dtch, StepParams *sp)
     sp->chf = (float)ch;
 }
 
-// V = V(U) on every ghosted cell; blockIdx.y = patch (within the group).
+// V = V(U) on every ghosted cell (a flat range of the patch region);
+// blockIdx.y = patch (within the group).
 template <int PHYS, class R>
 __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, int first, R *Vs)
 {
     const DevPatch P = a.patches[first + blockIdx.y];
-    const Tile t(P.n[0]);
-    const int T0 = (P.N[0] + t.xw - 1) / t.xw, T1 = (P.N[1] + t.rows - 1) / t.rows;
-    const int b = blockIdx.x;
-    const int gi = (b % T0) * t.xw + t.tx();
-    const int gj = ((b / T0) % T1) * t.rows + t.ty();
-    const int gk = b / (T0 * T1);
-    if (gi >= P.N[0] || gj >= P.N[1] || gk >= P.N[2]) return;
-    const int c = (gk * P.N[1] + gj) * P.N[0] + gi;
+    const int c = blockIdx.x * BLOCK + threadIdx.x;
+    if (c >= P.N[0] * P.N[1] * P.N[2]) return;
     double U[NV];
     R V[NV];
 #pragma unroll
@@ -580,7 +634,7 @@ __global__ void __launch_bounds__(BLOCK) k_flux1(StepArgs a, int first, const R 
 // Sweep along x, one thread per traced cell.  A tile covers xw traced cells
 // (xw - 2 updated cells) along x times BLOCK/xw rows along y.
 template <int PHYS, class R, int PPM, int IFACE64, int LAST>
-__global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const R *Vs, const R *F1, R *A)
+__global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k_sweep_x(StepArgs a, int first, const R *Vs, const R *F1, R *A)
 {
     const int patch = first + blockIdx.y;
     const DevPatch P = a.patches[patch];
@@ -596,8 +650,10 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const 
     __shared__ R sP[BLOCK][NV], sM[BLOCK][NV], sF[BLOCK][NV];
     const int me = threadIdx.x;
     const R gam = pgam<R>(a), ch = pch<R>(a.sp);
-    const R dtdx = pdt<R>(a.sp) * pidx<R>(P, 0);
-    const R hdt = R(0.5) * pdt<R>(a.sp);
+    const R dtr = pdt<R>(a.sp);
+    const double dtd = a.sp->dt;
+    const R dtdx = dtr * pidx<R>(P, 0);
+    const R hdt = R(0.5) * dtr;
     unsigned int fl = 0;
     const long long c = traced ? P.soff + lcell(P, i, j, k) : 0;
     if (traced) {
@@ -620,7 +676,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const 
 #pragma unroll
         for (int q = 0; q < NV; ++q) sF[me][q] = F[q];
         // faces on plane i+1; the tile's last face belongs to the next tile
-        if (a.reg && (tx < t.xw - 2 || i + 1 == P.n[0])) register_face<R, 0>(a, patch, P, i + 1, j, k, F);
+        if (a.reg && (tx < t.xw - 2 || i + 1 == P.n[0])) register_face<R, 0>(a, patch, P, i + 1, j, k, F, dtd);
     }
     const bool out = traced && tx >= 1 && tx <= t.xw - 2 && i >= 0 && i < P.n[0];
     if (LAST) {
@@ -632,7 +688,7 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const 
             const int cl = lcell(P, i, j, k);
 #pragma unroll
             for (int q = 0; q < NV; ++q) s[q] = (sF[me - 1][q] - sF[me][q]) * ix;
-            m = finish_cell<PHYS, R>(a, P, cl, s, damp, fl);
+            m = finish_cell<PHYS, R>(a, P, cl, s, dtd, damp, fl);
         }
         if (a.nextmax) block_max_to<R>(m, a.nextmax);
     } else {
@@ -646,14 +702,32 @@ __global__ void __launch_bounds__(BLOCK) k_sweep_x(StepArgs a, int first, const 
     if (fl) atomicOr(a.status, fl);
 }
 
+// Shared-memory staging of the marching sweeps in float working precision.
+// Per thread and stage: V of the cell entering the stencil (9 words), the
+// transverse first-order fluxes of the traced cell (2 dimensions x 2 faces x
+// 9), and the running sum of the cell being updated (9); in the last sweep
+// also that cell's float64 state U^n (9 doubles).  Two stages: the copies
+// for the next cell are in flight while the current one is traced.  Slot k of
+// thread t lies at [k * BLOCK + t], so a warp's accesses to one slot fall on
+// consecutive banks.
+constexpr int STG_V = 0, STG_F = 9, STG_A = 45, STG_N = 54;
+
+template <class R, int LAST> __host__ __device__ constexpr int sweep_m_smem()
+{
+    return sizeof(R) == 4 ? 2 * STG_N * BLOCK * 4 + (LAST ? 2 * NV * BLOCK * 8 : 0) : 0;
+}
+
 // Sweep along D = 1 (y) or 2 (z): each thread marches one segment of SEG
 // cells along D; the 5-cell stencil, the previous cell's + state and the
 // previous face flux stay in registers.  A tile: xw lanes along x times
-// BLOCK/xw (other-dimension, segment) pairs.
+// BLOCK/xw (other-dimension, segment) pairs.  Float: the next cell's inputs
+// are staged in shared memory by cp.async (sweep_m_smem bytes per block);
+// double: they are prefetched into L1.
 template <int PHYS, class R, int PPM, int IFACE64, int D, int LAST>
 __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, int first, const R *Vs, const R *F1, R *A)
 {
     constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
+    constexpr bool STAGED = sizeof(R) == 4;
     const int patch = first + blockIdx.y;
     const DevPatch P = a.patches[patch];
     const Tile t(P.n[0]);
@@ -666,8 +740,10 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
     const int o = comb / nseg, seg = comb % nseg;
     const bool ok = x < P.n[0] && o < nO;
     const R gam = pgam<R>(a), ch = pch<R>(a.sp);
-    const R dtdx = pdt<R>(a.sp) * pidx<R>(P, D);
-    const R hdt = R(0.5) * pdt<R>(a.sp);
+    const R dtr = pdt<R>(a.sp);
+    const double dtd = a.sp->dt;
+    const R dtdx = dtr * pidx<R>(P, D);
+    const R hdt = R(0.5) * dtr;
     const R iD = pidx<R>(P, D);
     double damp = 1.0;
     if (LAST) damp = patch_damp(a, P);
@@ -689,68 +765,159 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
         R Pprev[NV], Fprev[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) { Pprev[q] = R(0); Fprev[q] = R(0); }
-        for (int j = j0 - 1; j <= j1; ++j, c += st) {
-            // prefetch what the next iteration reads: V(j+3), the transverse
-            // first-order fluxes of cell j+1, the running sum (and the state)
-            // of cell j
-            if (j < j1) {
+        // face flux of plane j from Pprev (cell j - 1) and Vm (cell j); update
+        // of cell j - 1 from the previous face flux, with its running sum A at
+        // Ap[q * as] and (last sweep) its state U^n at Up[q * us]
+        auto faces = [&](int j, long long cj, const R (&Vm)[NV], const R *Ap, long long as, const double *Up,
+                         long long us) {
+            R F[NV];
+            face_flux<PHYS, R, D>(Pprev, Vm, gam, ch, F);
+            // plane j; (a, b) = (x, o) are the two non-D dimensions in
+            // increasing order; a segment's last face belongs to the next
+            if (a.reg && (j < j1 || j1 == nD)) register_face<R, D>(a, patch, P, j, x, o, F, dtd);
+            if (j >= j0 + 1) {
+                const long long cp = cj - st;  // cell j - 1
+                R s[NV];
 #pragma unroll
-                for (int q = 0; q < NV; ++q) prefetch_l1(Vs + gperm<D>(q) * a.sstride + c + 3 * st);
+                for (int q = 0; q < NV; ++q) s[q] = (Fprev[q] - F[q]) * iD;
+                if (LAST) {
+                    double u[NV];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        s[q] = Ap[q * as] + s[q];
+                        u[q] = Up[q * us];
+                    }
+                    if constexpr (PHYS == PH_MHD && sizeof(R) == 4) {
+                        R Vn[NV];  // V^n of cell j - 1, global order
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) Vn[gperm<D>(q)] = win[1][q];
+                        mx = fmax(mx, finish_cell_inc<R>(a, P, (int)(cp - P.soff), s, u, Vn, dtd, dtr, damp, fl));
+                    } else {
+                        mx = fmax(mx, finish_cell_u<PHYS, R>(a, P, (int)(cp - P.soff), s, u, dtd, damp, fl));
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) A[q * a.sstride + cp] = Ap[q * as] + s[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Fprev[q] = F[q];
+        };
+        if constexpr (STAGED) {
+            extern __shared__ __align__(16) unsigned char sm_raw[];
+            float *sf = reinterpret_cast<float *>(sm_raw) + threadIdx.x;
+            double *sd = reinterpret_cast<double *>(sm_raw + 2 * STG_N * BLOCK * 4) + threadIdx.x;
+            // copies for traced cell jn (scratch index cn) into stage sg
+            auto issue = [&](int jn, long long cn, int sg) {
+                float *bf = sf + sg * STG_N * BLOCK;
+                if (jn > j0 - 1) {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q)
+                        cp_async(bf + (STG_V + q) * BLOCK, Vs + gperm<D>(q) * a.sstride + cn + 2 * st);
+                }
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
                     if (e == D || e >= a.ndim) continue;
-                    const R *Fe = F1 + (long long)e * NV * a.sstride + c + st;
+                    const int es = e < D ? e : e - 1;
+                    const R *Fe = F1 + (long long)e * NV * a.sstride + cn;
                     const int se = dstr(P, e);
 #pragma unroll
                     for (int q = 0; q < NV; ++q) {
-                        prefetch_l1(Fe + q * a.sstride);
-                        prefetch_l1(Fe + q * a.sstride - se);
+                        cp_async(bf + (STG_F + es * 18 + q) * BLOCK, Fe + q * a.sstride);
+                        cp_async(bf + (STG_F + es * 18 + 9 + q) * BLOCK, Fe + q * a.sstride - se);
                     }
                 }
-                if (j >= j0) {
+                if (jn >= j0 + 1) {
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) prefetch_l1(A + q * a.sstride + c);
+                    for (int q = 0; q < NV; ++q) cp_async(bf + (STG_A + q) * BLOCK, A + q * a.sstride + cn - st);
                     if (LAST) {
+                        double *bd = sd + sg * NV * BLOCK;
+                        const long long gi = P.base + (cn - st - P.soff);
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) prefetch_l1(a.U + q * a.ustride + P.base + (c - P.soff));
+                        for (int q = 0; q < NV; ++q) cp_async(bd + q * BLOCK, a.U + q * a.ustride + gi);
                     }
                 }
+                cp_async_commit();
+            };
+            issue(j0 - 1, c, (j0 - 1) & 1);
+            for (int j = j0 - 1; j <= j1; ++j, c += st) {
+                const int sg = j & 1;
+                // the stage written here was last read in iteration j - 1
+                if (j < j1)
+                    issue(j + 1, c + st, (j + 1) & 1);
+                else
+                    cp_async_commit();
+                cp_async_wait_prev();
+                const float *bf = sf + sg * STG_N * BLOCK;
+                if (j > j0 - 1) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) win[m][q] = win[m + 1][q];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) win[4][q] = bf[(STG_V + q) * BLOCK];
+                }
+                // half-step transverse increments, as in transverse()
+                R T[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) T[q] = R(0);
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    if (e == D || e >= a.ndim) continue;
+                    const int es = e < D ? e : e - 1;
+                    const R h = hdt * pidx<R>(P, e);
+#pragma unroll
+                    for (int q = 0; q < NV; ++q)
+                        T[q] += (bf[(STG_F + es * 18 + 9 + q) * BLOCK] - bf[(STG_F + es * 18 + q) * BLOCK]) * h;
+                }
+                R Vp[NV], Vm[NV];
+                fl |= trace_cell_t<PHYS, R, PPM, IFACE64, D>(a, P, win, T, c, ch, dtdx, Vp, Vm);
+                if (j >= j0) faces(j, c, Vm, bf + STG_A * BLOCK, BLOCK, sd + sg * NV * BLOCK, BLOCK);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) Pprev[q] = Vp[q];
             }
-            if (j > j0 - 1) {
+        } else {
+            for (int j = j0 - 1; j <= j1; ++j, c += st) {
+                // prefetch what the next iteration reads: V(j+3), the transverse
+                // first-order fluxes of cell j+1, the running sum (and the state)
+                // of cell j
+                if (j < j1) {
 #pragma unroll
-                for (int m = 0; m < 4; ++m)
+                    for (int q = 0; q < NV; ++q) prefetch_l1(Vs + gperm<D>(q) * a.sstride + c + 3 * st);
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) win[m][q] = win[m + 1][q];
+                    for (int e = 0; e < 3; ++e) {
+                        if (e == D || e >= a.ndim) continue;
+                        const R *Fe = F1 + (long long)e * NV * a.sstride + c + st;
+                        const int se = dstr(P, e);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) win[4][q] = Vs[gperm<D>(q) * a.sstride + c + 2 * st];
-            }
-            R Vp[NV], Vm[NV];
-            fl |= trace_cell<PHYS, R, PPM, IFACE64, D>(a, P, win, F1, c, ch, dtdx, hdt, Vp, Vm);
-            if (j >= j0) {
-                R F[NV];
-                face_flux<PHYS, R, D>(Pprev, Vm, gam, ch, F);
-                // plane j; (a, b) = (x, o) are the two non-D dimensions in
-                // increasing order; a segment's last face belongs to the next
-                if (a.reg && (j < j1 || j1 == nD)) register_face<R, D>(a, patch, P, j, x, o, F);
-                if (j >= j0 + 1) {
-                    const long long cp = c - st;  // cell j - 1
-                    R s[NV];
+                        for (int q = 0; q < NV; ++q) {
+                            prefetch_l1(Fe + q * a.sstride);
+                            prefetch_l1(Fe + q * a.sstride - se);
+                        }
+                    }
+                    if (j >= j0) {
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) s[q] = (Fprev[q] - F[q]) * iD;
-                    if (LAST) {
+                        for (int q = 0; q < NV; ++q) prefetch_l1(A + q * a.sstride + c);
+                        if (LAST) {
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) s[q] = A[q * a.sstride + cp] + s[q];
-                        mx = fmax(mx, finish_cell<PHYS, R>(a, P, (int)(cp - P.soff), s, damp, fl));
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < NV; ++q) A[q * a.sstride + cp] += s[q];
+                            for (int q = 0; q < NV; ++q) prefetch_l1(a.U + q * a.ustride + P.base + (c - P.soff));
+                        }
                     }
                 }
+                if (j > j0 - 1) {
 #pragma unroll
-                for (int q = 0; q < NV; ++q) Fprev[q] = F[q];
+                    for (int m = 0; m < 4; ++m)
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) win[m][q] = win[m + 1][q];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) win[4][q] = Vs[gperm<D>(q) * a.sstride + c + 2 * st];
+                }
+                R Vp[NV], Vm[NV];
+                fl |= trace_cell<PHYS, R, PPM, IFACE64, D>(a, P, win, F1, c, ch, dtdx, hdt, Vp, Vm);
+                if (j >= j0) faces(j, c, Vm, A + (c - st), a.sstride, a.U + P.base + (c - st - P.soff), a.ustride);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) Pprev[q] = Vp[q];
             }
-#pragma unroll
-            for (int q = 0; q < NV; ++q) Pprev[q] = Vp[q];
         }
     }
     if (LAST && a.nextmax) block_max_to<R>(mx, a.nextmax);

@@ -2,12 +2,39 @@
 // and interface mode by ctu_f64.cu, ctu_f32.cu, ctu_f32i.cu and ctu_sr32.cu.
 #pragma once
 
+#include <atomic>
+
 #include "ctu_launch.h"
 
 namespace ctu {
 
 #define CTU_MARK(nm) \
     if (li.prof) li.prof->mark(nm, s)
+
+// Launch one marching sweep over a patch group.  Kernels that stage through
+// more than the default 48 KB of dynamic shared memory are opted in once per
+// device (the carveout set to its maximum, so that the register-limited
+// number of blocks still fits).
+template <int PHYS, class R, int PPM, int IF64, int D, int LAST>
+static void launch_sweep_m(const StepArgs &a, const Group &G, const R *Vs, const R *F1, R *A, cudaStream_t s)
+{
+    constexpr int smem = sweep_m_smem<R, LAST>();
+    if (smem > 48 * 1024) {
+        static std::atomic<unsigned long long> done{0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+        if (!(done.load() & bit) || !bit) {
+            cudaFuncSetAttribute(k_sweep_m<PHYS, R, PPM, IF64, D, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+            cudaFuncSetAttribute(k_sweep_m<PHYS, R, PPM, IF64, D, LAST>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            done.fetch_or(bit);
+        }
+    }
+    const dim3 grid((unsigned)Tiles::sweep_m(G.n, D), (unsigned)G.count);
+    k_sweep_m<PHYS, R, PPM, IF64, D, LAST><<<grid, BLOCK, smem, s>>>(a, G.first, Vs, F1, A);
+}
 
 template <int PHYS, class R, int PPM, int IF64>
 static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
@@ -61,12 +88,10 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     if (a.ndim > 1) {
         CTU_MARK("sweep_y");
         for (int g = 0; g < li.ngroups; ++g) {
-            const Group &G = li.groups[g];
-            const dim3 grid((unsigned)Tiles::sweep_m(G.n, 1), (unsigned)G.count);
             if (a.ndim == 2)
-                k_sweep_m<PHYS, R, PPM, IF64, 1, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+                launch_sweep_m<PHYS, R, PPM, IF64, 1, 1>(a, li.groups[g], Vs, F1, A, s);
             else
-                k_sweep_m<PHYS, R, PPM, IF64, 1, 0><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+                launch_sweep_m<PHYS, R, PPM, IF64, 1, 0>(a, li.groups[g], Vs, F1, A, s);
             ++n;
         }
         CTU_MARK(nullptr);
@@ -74,9 +99,7 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     if (a.ndim > 2) {
         CTU_MARK("sweep_z");
         for (int g = 0; g < li.ngroups; ++g) {
-            const Group &G = li.groups[g];
-            const dim3 grid((unsigned)Tiles::sweep_m(G.n, 2), (unsigned)G.count);
-            k_sweep_m<PHYS, R, PPM, IF64, 2, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+            launch_sweep_m<PHYS, R, PPM, IF64, 2, 1>(a, li.groups[g], Vs, F1, A, s);
             ++n;
         }
         CTU_MARK(nullptr);

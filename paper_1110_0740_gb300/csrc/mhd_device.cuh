@@ -56,10 +56,14 @@ template <class R> __device__ __forceinline__ R minmod(R a, R b)
     return R(0);
 }
 
-// Monotonised-central slope, Eq. (MClim)
+// Monotonised-central slope, Eq. (MClim): minmod((dm + dp)/2, 2 minmod(dm,
+// dp)), i.e. for dm, dp of one sign that sign times min(|dm + dp|/2, 2|dm|,
+// 2|dp|), else 0 (written without branches; a product dm dp below the
+// normal range counts as zero).
 template <class R> __device__ __forceinline__ R mc_slope(R dm, R dp)
 {
-    return minmod(R(0.5) * (dp + dm), R(2) * minmod(dm, dp));
+    const R m = fmin(R(0.5) * fabs(dm + dp), R(2) * fmin(fabs(dm), fabs(dp)));
+    return dm * dp > R(0) ? copysign(m, dm) : R(0);
 }
 
 // Interface values w_(i,+/-) of one characteristic field from w_(i-2..i+2):
@@ -79,16 +83,13 @@ __device__ __forceinline__ void reconstruct(R w0m2, R w0m1, R w0, R w0p1, R w0p2
     R p = R(0.5) * (w0 + w0p1) - (sp - s0) * R(1.0 / 6.0);
     R m = R(0.5) * (w0 + w0m1) + (sm - s0) * R(1.0 / 6.0);
     R dp = p - w0, dm = m - w0;
-    R ndp, ndm;
-    if (dp * dm > R(0)) {
-        ndp = R(0);
-        ndm = R(0);
-    } else {
-        ndp = (fabs(dp) >= R(2) * fabs(dm)) ? R(-2) * dm : dp;
-        ndm = (fabs(dm) >= R(2) * fabs(dp)) ? R(-2) * dp : dm;
-    }
-    wp = w0 + ndp;
-    wm = w0 + ndm;
+    // a local extremum flattens the cell; otherwise the overshooting side is
+    // pulled back so that the parabola stays monotone
+    const bool extremum = dp * dm > R(0);
+    const R ndp = (fabs(dp) >= R(2) * fabs(dm)) ? R(-2) * dm : dp;
+    const R ndm = (fabs(dm) >= R(2) * fabs(dp)) ? R(-2) * dp : dm;
+    wp = w0 + (extremum ? R(0) : ndp);
+    wm = w0 + (extremum ? R(0) : ndm);
 }
 
 // Tracing of one characteristic field to t^(n+1/2), Eq. (wnorm_predp) and
@@ -100,10 +101,10 @@ __device__ __forceinline__ void trace(R wp, R w0, R wm, R nu, bool upwind, R &tp
 {
     R dw = wp - wm;
     R d2w = wp - R(2) * w0 + wm;
-    tp = wp;
-    tm = wm;
-    if (!upwind || nu > R(0)) tp = wp - R(0.5) * nu * (dw + d2w * (R(3) - R(2) * nu));
-    if (!upwind || nu < R(0)) tm = wm - R(0.5) * nu * (dw - d2w * (R(3) + R(2) * nu));
+    const R up = wp - R(0.5) * nu * (dw + d2w * (R(3) - R(2) * nu));
+    const R um = wm - R(0.5) * nu * (dw - d2w * (R(3) + R(2) * nu));
+    tp = (!upwind | (nu > R(0))) ? up : wp;
+    tm = (!upwind | (nu < R(0))) ? um : wm;
 }
 
 // ---------------------------------------------------------------- normal predictor
