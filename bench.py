@@ -373,32 +373,51 @@ def run_amr(args):
     four times (dt_l = dt_0 / 2^l, common c_h), all seven batched ctu_step
     calls captured in one CUDA graph; flux-register windows on both sides of
     every coarse-fine interface.  dt_0 is fixed before timing from ctu_dt on
-    every level (dt_0 = min_l 2^l dt_l)."""
+    every level (dt_0 = min_l 2^l dt_l).  With N > 1 ranks every rank builds
+    the same hierarchy and advances its shard of each level (patches split by
+    cell count, Section 4); the ranks agree on dt_0 (one scalar reduction) and
+    the step time is the slowest rank's (strong scaling)."""
     import torch
-    from paper_1110_0740_gb300 import ctu, workloads as W
+    from paper_1110_0740_gb300 import ctu, shard, workloads as W
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    H = W.amr_hierarchy(seed=rank)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    H = W.amr_hierarchy(seed=0)
     L = H["levels"]
     prec = ctu.CTU_MIXED if args.precision == "mixed" else ctu.CTU_FP64
-    # flux-register windows, per level context
+    # this rank's patches per level (indices into the level's patch list)
+    mine = []
+    for lv in L:
+        cells_l = [n[0] * n[1] * n[2] for (n, _, _, _) in lv["patches"]]
+        mine.append(shard.partition(cells_l, world)[rank])
+    loc = [{g: i for i, g in enumerate(m)} for m in mine]
+    # flux-register windows, per level context (local patch indices); a
+    # coarse window is kept by the rank that owns its parent patch
     wins = [[] for _ in L]
     off = 0
     for lev in range(1, len(L)):
-        for pi, (n, dx, base, _) in enumerate(L[lev]["patches"]):
+        for gi in mine[lev]:
+            n = L[lev]["patches"][gi][0]
             for d in range(3):
                 a_, b_ = [e for e in range(3) if e != d]
                 for plane in (0, n[d]):
-                    wins[lev].append((pi, d, plane, 0, n[a_], 0, n[b_], 1.0, off))
+                    wins[lev].append((loc[lev][gi], d, plane, 0, n[a_], 0, n[b_], 1.0, off))
                     off += 9 * n[a_] * n[b_]
         for (parent, o_zyx, sz) in L[lev]["footprints"]:
+            if parent not in loc[lev - 1]:
+                continue
             o = [o_zyx[2], o_zyx[1], o_zyx[0]]
             for d in range(3):
                 a_, b_ = [e for e in range(3) if e != d]
                 for plane in (o[d], o[d] + sz):
-                    wins[lev - 1].append((parent, d, plane, o[a_], o[a_] + sz, o[b_], o[b_] + sz, -1.0, off))
+                    wins[lev - 1].append((loc[lev - 1][parent], d, plane, o[a_], o[a_] + sz, o[b_],
+                                          o[b_] + sz, -1.0, off))
                     off += 9 * sz * sz
     reg = torch.zeros(max(off, 1), dtype=torch.float64, device=dev)
     ctxs, A, B, P, D = [], [], [], [], []
@@ -407,30 +426,40 @@ def run_amr(args):
         pool = torch.from_numpy(lv["pool"]).to(dev)
         A.append(pool)
         B.append(pool.clone())
-        P.append(ctu.make_patches([(n, dx, b) for (n, dx, b, _) in lv["patches"]]))
-        c.flux_registers(reg, wins[lev])
+        P.append(ctu.make_patches([lv["patches"][gi][:3] for gi in mine[lev]]) if mine[lev] else None)
+        if wins[lev]:
+            c.flux_registers(reg, wins[lev])
         ctxs.append(c)
     h = []
     for lev, c in enumerate(ctxs):
+        if P[lev] is None:
+            continue
         hd = torch.zeros(2, dtype=torch.float64, device=dev)
         c.dt(A[lev], A[lev].shape[1], P[lev], hd)
-        h.append(hd.cpu().tolist())
-    dt0 = min(v[0] * 2 ** lev for lev, v in enumerate(h))
+        h.append(hd.cpu().tolist()[0] * 2 ** lev)
     dx0 = L[0]["patches"][0][1][0]
-    ch = 0.3 * dx0 / dt0
+    dt0, ch = shard.agree_dt((min(h) if h else float("inf"), 0.0), 0.3, dx0,
+                             group=None if pg is None else pg.group.WORLD)
     for lev in range(len(L)):
         D.append(torch.tensor([dt0 / 2 ** lev, ch], dtype=torch.float64, device=dev))
     stream = torch.cuda.Stream(device=dev)
 
+    def lstep(lev, src, dst):
+        if P[lev] is not None:
+            ctxs[lev].step(src, dst, src.shape[1], P[lev], D[lev], stream=stream)
+
     def coarse_step():
         # recursive subcycling: l0, then for each l1 substep its two l2 substeps
-        ctxs[0].step(A[0], B[0], A[0].shape[1], P[0], D[0], stream=stream)
+        lstep(0, A[0], B[0])
         for k in range(2):
-            src, dst = (A[1], B[1]) if k == 0 else (B[1], A[1])
-            ctxs[1].step(src, dst, A[1].shape[1], P[1], D[1], stream=stream)
+            lstep(1, *((A[1], B[1]) if k == 0 else (B[1], A[1])))
             for m in range(2):
-                s2, d2 = (A[2], B[2]) if m == 0 else (B[2], A[2])
-                ctxs[2].step(s2, d2, A[2].shape[1], P[2], D[2], stream=stream)
+                lstep(2, *((A[2], B[2]) if m == 0 else (B[2], A[2])))
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
 
     with torch.cuda.stream(stream):
         coarse_step()  # binds patch lists, sizes scratch (before capture)
@@ -440,7 +469,7 @@ def run_amr(args):
         coarse_step()
     for _ in range(args.warmup):
         g.replay()
-    torch.cuda.synchronize()
+    barrier()
     clocks = Clocks(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -449,12 +478,14 @@ def run_amr(args):
         for _ in range(args.steps):
             g.replay()
         e1.record(stream)
-    torch.cuda.synchronize()
+    barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = shard.slowest(e0.elapsed_time(e1) / args.steps,
+                       group=None if pg is None else pg.group.WORLD)
     st = [c.status_sync() for c in ctxs]
     cells = [sum(n[0] * n[1] * n[2] for (n, _, _, _) in lv["patches"]) for lv in L]
     upd = cells[0] + 2 * cells[1] + 4 * cells[2]
+    my_upd = sum(2 ** lev * sum(L[lev]["patches"][gi][0][0] ** 3 for gi in mine[lev]) for lev in range(len(L)))
     from collections import Counter
     hist = {lev: dict(sorted(Counter(n[0] for (n, _, _, _) in lv["patches"]).items()))
             for lev, lv in enumerate(L)}
@@ -470,21 +501,25 @@ def run_amr(args):
         c.profile(False)
     launches = sum(c.launches() for c in ctxs[:1]) + 2 * ctxs[1].launches() + 4 * ctxs[2].launches()
     if rank == 0:
-        line = {"metric": METRIC, "value": world * upd / (ms * 1e-3), "unit": "cell-updates/s",
+        line = {"metric": METRIC, "value": upd / (ms * 1e-3), "unit": "cell-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
                 "dtype": "f32+f64" if prec == ctu.CTU_MIXED else "f64", "data": "synthetic",
                 "config": {"workload": "batched AMR level advance: 3-level hierarchy, ratio 2, base "
                                        "128^3, PPM+HLLD+GLM, subcycled 1/2/4 in one CUDA graph, "
                                        "coarse-fine flux registers",
                            "patches_per_level": [len(lv["patches"]) for lv in L],
                            "patch_sizes_per_level": hist, "cells_per_level": cells,
-                           "cell_updates_per_coarse_step": upd, "windows": sum(len(w) for w in wins),
+                           "cell_updates_per_coarse_step": upd, "windows_rank0": sum(len(w) for w in wins),
+                           "rank0_share_of_updates": my_upd / upd,
+                           "parallelism": f"patch shards x{world}" if world > 1 else "single GPU",
                            "l2_flush": "inputs larger than L2"},
                 "gpu_launches": launches * args.steps, "clocks": clk,
                 "kernels_ms_per_coarse_step": kern,
                 "status": [ctu.STATUS[x] for x in st], "gpu": torch.cuda.get_device_name(dev)}
         print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
 
 
 def run_srmhd(args):

@@ -6,7 +6,8 @@
 // transv with Pi = 0) is the kernel sequence
 //   k_setup        {dt, c_h} -> per-step parameters (float copies)
 //   k_prim         V = V(U) on every ghosted cell
-//   k_flux1<D>     first-order Godunov fluxes F^n_D = R(U_c, U_c+e_D)
+//   k_div1<D>      first-order Godunov fluxes F^n_D = R(U_c, U_c+e_D) and
+//                  their divergences L1_D (the transverse terms)
 //   k_sweep_x      direction x: normal predictor + transverse correction,
 //                  n+1/2 Riemann problems and L_x, one thread per traced cell,
 //                  interface states exchanged through shared memory
@@ -17,8 +18,8 @@
 // accumulates the flux-register windows of its faces (Eq. fluxcorr).
 //
 // Scratch (library-owned, per-patch regions with the ghosted layout): V (9
-// words per cell), F^n (3 x 9), and the running sum A = L_x (+ L_y) (9), all
-// in R.  Interface states and n+1/2 fluxes never leave the chip.
+// words per cell), the first-order divergences L1 (3 x 9), and the running
+// sum A = L_x (+ L_y) (9), all in R.  Interface states and n+1/2 fluxes never leave the chip.
 //
 // Mixed path and the FP64 pipe: besides the float64 update accumulation
 // (one DFMA per variable and cell) the mixed kernels issue no FP64
@@ -265,21 +266,18 @@ __device__ __forceinline__ R cell_speed(const R (&V)[NV], const StepArgs &a, con
 // ---------------------------------------------------------------- per-cell pieces
 
 // Half-step transverse increments dt/2 sum_{d' != D} L^n_d' at cell c (global
-// order) from the first-order fluxes (F1 at a cell = its upper face).
+// order) from the first-order flux divergences L1 (Eq. transv).
 template <class R, int D>
-__device__ __forceinline__ void transverse(const StepArgs &a, const DevPatch &P, const R *F1, long long c, R hdt,
-                                           R (&T)[NV])
+__device__ __forceinline__ void transverse(const StepArgs &a, const R *L1, long long c, R hdt, R (&T)[NV])
 {
 #pragma unroll
     for (int q = 0; q < NV; ++q) T[q] = R(0);
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         if (e == D || e >= a.ndim) continue;
-        const R *Fe = F1 + (long long)e * NV * a.sstride;
-        const int st = dstr(P, e);
-        const R h = hdt * pidx<R>(P, e);
+        const R *Le = L1 + (long long)e * NV * a.sstride;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) T[q] += (Fe[q * a.sstride + c - st] - Fe[q * a.sstride + c]) * h;
+        for (int q = 0; q < NV; ++q) T[q] += Le[q * a.sstride + c] * hdt;
     }
 }
 
@@ -391,11 +389,11 @@ __device__ __forceinline__ unsigned int trace_cell_t(const StepArgs &a, const De
 
 template <int PHYS, class R, int PPM, int IFACE64, int D>
 __device__ __forceinline__ unsigned int trace_cell(const StepArgs &a, const DevPatch &P, const R (&vs)[5][NV],
-                                                   const R *F1, long long c, R ch, R dtdx, R hdt, R (&Vp)[NV],
+                                                   const R *L1, long long c, R ch, R dtdx, R hdt, R (&Vp)[NV],
                                                    R (&Vm)[NV])
 {
     R T[NV];
-    transverse<R, D>(a, P, F1, c, hdt, T);
+    transverse<R, D>(a, L1, c, hdt, T);
     return trace_cell_t<PHYS, R, PPM, IFACE64, D>(a, P, vs, T, c, ch, dtdx, Vp, Vm);
 }
 
@@ -544,12 +542,17 @@ struct Tiles {
         (void)n;
         return ((long long)N[0] * N[1] * N[2] + BLOCK - 1) / BLOCK;
     }
-    static long long flux1(const int *n, int ndim, int D)
+    static long long div1(const int *n, int ndim, int D)
     {
-        int ext[3];
-        for (int e = 0; e < 3; ++e) ext[e] = e >= ndim ? 1 : (e == D ? n[e] + 1 : n[e] + 2);
         const int w = xw(n[0]), r = BLOCK / w;
-        return (long long)((ext[0] + w - 1) / w) * ((ext[1] + r - 1) / r) * ext[2];
+        if (D == 0) {
+            const int e1 = ndim > 1 ? n[1] + 2 : 1, e2 = ndim > 2 ? n[2] + 2 : 1;
+            return (long long)((n[0] + w - 2) / (w - 1)) * ((e1 + r - 1) / r) * e2;
+        }
+        const int O = D == 1 ? 2 : 1;
+        const int eO = ndim > O ? n[O] + 2 : 1;
+        const long long nseg = (n[D] + SEG - 1) / SEG;
+        return (long long)((n[0] + 2 + w - 1) / w) * ((eO * nseg + r - 1) / r);
     }
     static long long sweep_x(const int *n)
     {
@@ -599,42 +602,106 @@ __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, int first, R *Vs)
     for (int q = 0; q < NV; ++q) Vs[q * a.sstride + P.soff + c] = V[q];
 }
 
-// First-order fluxes through the upper D-face of cells with c_D in
-// [-1, n_D - 1] and the other active coordinates in [-1, n].
+// First-order flux divergences L1_D = (F^n_(c - e_D/2) - F^n_(c + e_D/2)) / dx_D
+// (Eq. transv; F^n from the cell-centred states) on the cells that the
+// sweeps of the other directions trace: c_D in [0, n_D), the other active
+// coordinates in [-1, n].
+//   D = x: one thread per face; a tile of xw lanes along x yields xw - 1
+//          cells, the lower face of a cell arriving from the previous lane.
+//   D = y, z: one thread per segment of SEG cells marching along D with the
+//          previous face flux and cell state in registers.
 template <int PHYS, class R, int D>
-__global__ void __launch_bounds__(BLOCK) k_flux1(StepArgs a, int first, const R *Vs, R *F1)
+__global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, int first, const R *Vs, R *L1)
 {
     const DevPatch P = a.patches[first + blockIdx.y];
-    int lo[3], ext[3];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        if (e >= a.ndim) { lo[e] = 0; ext[e] = 1; }
-        else if (e == D) { lo[e] = -1; ext[e] = P.n[e] + 1; }
-        else { lo[e] = -1; ext[e] = P.n[e] + 2; }
-    }
     const Tile t(P.n[0]);
-    const int T0 = (ext[0] + t.xw - 1) / t.xw, T1 = (ext[1] + t.rows - 1) / t.rows;
+    const R gam = pgam<R>(a), ch = pch<R>(a.sp);
+    const R iD = pidx<R>(P, D);
+    R *Ld = L1 + (long long)D * NV * a.sstride;
     const int b = blockIdx.x;
-    const int i = (b % T0) * t.xw + t.tx(), j = ((b / T0) % T1) * t.rows + t.ty(), k = b / (T0 * T1);
-    if (i >= ext[0] || j >= ext[1] || k >= ext[2]) return;
-    const long long c = P.soff + lcell(P, lo[0] + i, lo[1] + j, lo[2] + k);
-    const int st = dstr(P, D);
-    R L[NV], Rr[NV], F[NV];
+    if constexpr (D == 0) {
+        const int out = t.xw - 1;
+        const int e1 = a.ndim > 1 ? P.n[1] + 2 : 1, e2 = a.ndim > 2 ? P.n[2] + 2 : 1;
+        const int lo1 = a.ndim > 1 ? -1 : 0, lo2 = a.ndim > 2 ? -1 : 0;
+        const int T0 = (P.n[0] + out - 1) / out, T1 = (e1 + t.rows - 1) / t.rows;
+        const int tx = t.tx();
+        const int i = (b % T0) * out + tx;  // this lane's face lies between cells i - 1 and i
+        const int j = ((b / T0) % T1) * t.rows + t.ty();
+        const int k = b / (T0 * T1);
+        const bool face = j < e1 && k < e2 && i <= P.n[0];
+        const long long c = face ? P.soff + lcell(P, i, lo1 + j, lo2 + k) : 0;  // cell i
+        R F[NV];
+        if (face) {
+            R L[NV], Rr[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        L[q] = Vs[gperm<D>(q) * a.sstride + c];
-        Rr[q] = Vs[gperm<D>(q) * a.sstride + c + st];
+            for (int q = 0; q < NV; ++q) {
+                L[q] = Vs[q * a.sstride + c - 1];
+                Rr[q] = Vs[q * a.sstride + c];
+            }
+            riemann_any<PHYS, R>(L, Rr, gam, ch, F);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) F[q] = R(0);
+        }
+        // every lane of the warp takes part in the exchange
+        R Fm[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) Fm[q] = __shfl_up_sync(0xffffffffu, F[q], 1, t.xw);
+        if (face && tx >= 1) {  // cell i - 1: lower face from lane tx - 1, upper face F
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Ld[q * a.sstride + c - 1] = (Fm[q] - F[q]) * iD;
+        }
+    } else {
+        constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
+        const int nD = P.n[D];
+        const int eO = a.ndim > O ? P.n[O] + 2 : 1, loO = a.ndim > O ? -1 : 0;
+        const int nseg = (nD + SEG - 1) / SEG;
+        const int T0 = (P.n[0] + 2 + t.xw - 1) / t.xw;
+        const int x = (b % T0) * t.xw + t.tx() - 1;
+        const int comb = (b / T0) * t.rows + t.ty();
+        const int o = comb / nseg, seg = comb % nseg;
+        if (x > P.n[0] || o >= eO) return;
+        const int j0 = seg * SEG, j1 = min(j0 + SEG, nD);
+        const int st = dstr(P, D);
+        int cc[3];
+        cc[0] = x;
+        cc[O] = loO + o;
+        cc[D] = j0 - 1;
+        long long c = P.soff + lcell(P, cc[0], cc[1], cc[2]);  // cell j0 - 1
+        R Vl[NV], Vr[NV], Fp[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            Vl[q] = Vs[gperm<D>(q) * a.sstride + c];
+            Vr[q] = Vs[gperm<D>(q) * a.sstride + c + st];
+            Fp[q] = R(0);
+        }
+        for (int j = j0; j <= j1; ++j) {
+            c += st;  // cell j; the face below it separates j - 1 and j
+            R Vn[NV];
+            if (j < j1) {  // next cell, loaded ahead of the solve
+#pragma unroll
+                for (int q = 0; q < NV; ++q) Vn[q] = Vs[gperm<D>(q) * a.sstride + c + st];
+            }
+            R F[NV];
+            riemann_any<PHYS, R>(Vl, Vr, gam, ch, F);
+            if (j > j0) {  // cell j - 1
+#pragma unroll
+                for (int q = 0; q < NV; ++q) Ld[gperm<D>(q) * a.sstride + c - st] = (Fp[q] - F[q]) * iD;
+            }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                Fp[q] = F[q];
+                Vl[q] = Vr[q];
+                Vr[q] = Vn[q];
+            }
+        }
     }
-    riemann_any<PHYS, R>(L, Rr, pgam<R>(a), pch<R>(a.sp), F);
-    R *Fd = F1 + (long long)D * NV * a.sstride;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) Fd[gperm<D>(q) * a.sstride + c] = F[q];
 }
 
 // Sweep along x, one thread per traced cell.  A tile covers xw traced cells
 // (xw - 2 updated cells) along x times BLOCK/xw rows along y.
 template <int PHYS, class R, int PPM, int IFACE64, int LAST>
-__global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k_sweep_x(StepArgs a, int first, const R *Vs, const R *F1, R *A)
+__global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k_sweep_x(StepArgs a, int first, const R *Vs, const R *L1, R *A)
 {
     const int patch = first + blockIdx.y;
     const DevPatch P = a.patches[patch];
@@ -663,7 +730,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
 #pragma unroll
             for (int q = 0; q < NV; ++q) vs[m][q] = Vs[q * a.sstride + c + (m - 2)];
         R Vp[NV], Vm[NV];
-        fl |= trace_cell<PHYS, R, PPM, IFACE64, 0>(a, P, vs, F1, c, ch, dtdx, hdt, Vp, Vm);
+        fl |= trace_cell<PHYS, R, PPM, IFACE64, 0>(a, P, vs, L1, c, ch, dtdx, hdt, Vp, Vm);
 #pragma unroll
         for (int q = 0; q < NV; ++q) { sP[me][q] = Vp[q]; sM[me][q] = Vm[q]; }
     }
@@ -704,13 +771,13 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
 
 // Shared-memory staging of the marching sweeps in float working precision.
 // Per thread and stage: V of the cell entering the stencil (9 words), the
-// transverse first-order fluxes of the traced cell (2 dimensions x 2 faces x
-// 9), and the running sum of the cell being updated (9); in the last sweep
-// also that cell's float64 state U^n (9 doubles).  Two stages: the copies
-// for the next cell are in flight while the current one is traced.  Slot k of
-// thread t lies at [k * BLOCK + t], so a warp's accesses to one slot fall on
+// transverse first-order divergences of the traced cell (2 dimensions x 9),
+// and the running sum of the cell being updated (9); in the last sweep also
+// that cell's float64 state U^n (9 doubles).  Two stages: the copies for the
+// next cell are in flight while the current one is traced.  Slot k of thread
+// t lies at [k * BLOCK + t], so a warp's accesses to one slot fall on
 // consecutive banks.
-constexpr int STG_V = 0, STG_F = 9, STG_A = 45, STG_N = 54;
+constexpr int STG_V = 0, STG_F = 9, STG_A = 27, STG_N = 36;
 
 template <class R, int LAST> __host__ __device__ constexpr int sweep_m_smem()
 {
@@ -724,7 +791,7 @@ template <class R, int LAST> __host__ __device__ constexpr int sweep_m_smem()
 // are staged in shared memory by cp.async (sweep_m_smem bytes per block);
 // double: they are prefetched into L1.
 template <int PHYS, class R, int PPM, int IFACE64, int D, int LAST>
-__global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, int first, const R *Vs, const R *F1, R *A)
+__global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, int first, const R *Vs, const R *L1, R *A)
 {
     constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
     constexpr bool STAGED = sizeof(R) == 4;
@@ -819,13 +886,9 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
                 for (int e = 0; e < 3; ++e) {
                     if (e == D || e >= a.ndim) continue;
                     const int es = e < D ? e : e - 1;
-                    const R *Fe = F1 + (long long)e * NV * a.sstride + cn;
-                    const int se = dstr(P, e);
+                    const R *Le = L1 + (long long)e * NV * a.sstride + cn;
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) {
-                        cp_async(bf + (STG_F + es * 18 + q) * BLOCK, Fe + q * a.sstride);
-                        cp_async(bf + (STG_F + es * 18 + 9 + q) * BLOCK, Fe + q * a.sstride - se);
-                    }
+                    for (int q = 0; q < NV; ++q) cp_async(bf + (STG_F + es * 9 + q) * BLOCK, Le + q * a.sstride);
                 }
                 if (jn >= j0 + 1) {
 #pragma unroll
@@ -865,10 +928,8 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
                 for (int e = 0; e < 3; ++e) {
                     if (e == D || e >= a.ndim) continue;
                     const int es = e < D ? e : e - 1;
-                    const R h = hdt * pidx<R>(P, e);
 #pragma unroll
-                    for (int q = 0; q < NV; ++q)
-                        T[q] += (bf[(STG_F + es * 18 + 9 + q) * BLOCK] - bf[(STG_F + es * 18 + q) * BLOCK]) * h;
+                    for (int q = 0; q < NV; ++q) T[q] += bf[(STG_F + es * 9 + q) * BLOCK] * hdt;
                 }
                 R Vp[NV], Vm[NV];
                 fl |= trace_cell_t<PHYS, R, PPM, IFACE64, D>(a, P, win, T, c, ch, dtdx, Vp, Vm);
@@ -887,13 +948,9 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
                         if (e == D || e >= a.ndim) continue;
-                        const R *Fe = F1 + (long long)e * NV * a.sstride + c + st;
-                        const int se = dstr(P, e);
+                        const R *Le = L1 + (long long)e * NV * a.sstride + c + st;
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) {
-                            prefetch_l1(Fe + q * a.sstride);
-                            prefetch_l1(Fe + q * a.sstride - se);
-                        }
+                        for (int q = 0; q < NV; ++q) prefetch_l1(Le + q * a.sstride);
                     }
                     if (j >= j0) {
 #pragma unroll
@@ -913,7 +970,7 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
                     for (int q = 0; q < NV; ++q) win[4][q] = Vs[gperm<D>(q) * a.sstride + c + 2 * st];
                 }
                 R Vp[NV], Vm[NV];
-                fl |= trace_cell<PHYS, R, PPM, IFACE64, D>(a, P, win, F1, c, ch, dtdx, hdt, Vp, Vm);
+                fl |= trace_cell<PHYS, R, PPM, IFACE64, D>(a, P, win, L1, c, ch, dtdx, hdt, Vp, Vm);
                 if (j >= j0) faces(j, c, Vm, A + (c - st), a.sstride, a.U + P.base + (c - st - P.soff), a.ustride);
 #pragma unroll
                 for (int q = 0; q < NV; ++q) Pprev[q] = Vp[q];

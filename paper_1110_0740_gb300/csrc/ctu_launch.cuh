@@ -16,7 +16,7 @@ namespace ctu {
 // device (the carveout set to its maximum, so that the register-limited
 // number of blocks still fits).
 template <int PHYS, class R, int PPM, int IF64, int D, int LAST>
-static void launch_sweep_m(const StepArgs &a, const Group &G, const R *Vs, const R *F1, R *A, cudaStream_t s)
+static void launch_sweep_m(const StepArgs &a, const Group &G, const R *Vs, const R *L1, R *A, cudaStream_t s)
 {
     constexpr int smem = sweep_m_smem<R, LAST>();
     if (smem > 48 * 1024) {
@@ -33,7 +33,7 @@ static void launch_sweep_m(const StepArgs &a, const Group &G, const R *Vs, const
         }
     }
     const dim3 grid((unsigned)Tiles::sweep_m(G.n, D), (unsigned)G.count);
-    k_sweep_m<PHYS, R, PPM, IF64, D, LAST><<<grid, BLOCK, smem, s>>>(a, G.first, Vs, F1, A);
+    k_sweep_m<PHYS, R, PPM, IF64, D, LAST><<<grid, BLOCK, smem, s>>>(a, G.first, Vs, L1, A);
 }
 
 template <int PHYS, class R, int PPM, int IF64>
@@ -42,7 +42,7 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     const long long S = a.sstride;
     R *base = (R *)li.scratch;
     R *Vs = base;
-    R *F1 = base + 9 * S;
+    R *L1 = base + 9 * S;
     R *A = base + 36 * S;
     int n = 0;
     CTU_MARK("setup");
@@ -56,32 +56,30 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         ++n;
     }
     CTU_MARK(nullptr);
-    CTU_MARK("flux1");
-    for (int g = 0; g < li.ngroups; ++g) {
-        const Group &G = li.groups[g];
-        const unsigned c = (unsigned)G.count;
-        k_flux1<PHYS, R, 0><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 0), c), BLOCK, 0, s>>>(a, G.first, Vs, F1);
-        ++n;
-        if (a.ndim > 1) {
-            k_flux1<PHYS, R, 1><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 1), c), BLOCK, 0, s>>>(a, G.first, Vs,
-                                                                                                  F1);
-            ++n;
+    if (a.ndim > 1) {  // first-order stage: the transverse terms of the sweeps
+        CTU_MARK("flux1");
+        for (int g = 0; g < li.ngroups; ++g) {
+            const Group &G = li.groups[g];
+            const unsigned c = (unsigned)G.count;
+            k_div1<PHYS, R, 0><<<dim3((unsigned)Tiles::div1(G.n, a.ndim, 0), c), BLOCK, 0, s>>>(a, G.first, Vs, L1);
+            k_div1<PHYS, R, 1><<<dim3((unsigned)Tiles::div1(G.n, a.ndim, 1), c), BLOCK, 0, s>>>(a, G.first, Vs, L1);
+            n += 2;
+            if (a.ndim > 2) {
+                k_div1<PHYS, R, 2><<<dim3((unsigned)Tiles::div1(G.n, a.ndim, 2), c), BLOCK, 0, s>>>(a, G.first, Vs,
+                                                                                                 L1);
+                ++n;
+            }
         }
-        if (a.ndim > 2) {
-            k_flux1<PHYS, R, 2><<<dim3((unsigned)Tiles::flux1(G.n, a.ndim, 2), c), BLOCK, 0, s>>>(a, G.first, Vs,
-                                                                                                  F1);
-            ++n;
-        }
+        CTU_MARK(nullptr);
     }
-    CTU_MARK(nullptr);
     CTU_MARK("sweep_x");
     for (int g = 0; g < li.ngroups; ++g) {
         const Group &G = li.groups[g];
         const dim3 grid((unsigned)Tiles::sweep_x(G.n), (unsigned)G.count);
         if (a.ndim == 1)
-            k_sweep_x<PHYS, R, PPM, IF64, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+            k_sweep_x<PHYS, R, PPM, IF64, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, L1, A);
         else
-            k_sweep_x<PHYS, R, PPM, IF64, 0><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, F1, A);
+            k_sweep_x<PHYS, R, PPM, IF64, 0><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, L1, A);
         ++n;
     }
     CTU_MARK(nullptr);
@@ -89,9 +87,9 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         CTU_MARK("sweep_y");
         for (int g = 0; g < li.ngroups; ++g) {
             if (a.ndim == 2)
-                launch_sweep_m<PHYS, R, PPM, IF64, 1, 1>(a, li.groups[g], Vs, F1, A, s);
+                launch_sweep_m<PHYS, R, PPM, IF64, 1, 1>(a, li.groups[g], Vs, L1, A, s);
             else
-                launch_sweep_m<PHYS, R, PPM, IF64, 1, 0>(a, li.groups[g], Vs, F1, A, s);
+                launch_sweep_m<PHYS, R, PPM, IF64, 1, 0>(a, li.groups[g], Vs, L1, A, s);
             ++n;
         }
         CTU_MARK(nullptr);
@@ -99,7 +97,7 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     if (a.ndim > 2) {
         CTU_MARK("sweep_z");
         for (int g = 0; g < li.ngroups; ++g) {
-            launch_sweep_m<PHYS, R, PPM, IF64, 2, 1>(a, li.groups[g], Vs, F1, A, s);
+            launch_sweep_m<PHYS, R, PPM, IF64, 2, 1>(a, li.groups[g], Vs, L1, A, s);
             ++n;
         }
         CTU_MARK(nullptr);
