@@ -598,9 +598,10 @@ def kernel_flops(n):
     c = {k: float(v) for k, v in _profile_numbers("flops_per_cell.txt").items()}
     cells = float(n) ** 3
     sweep = c.get("sweep_per_direction_ppm", 0.0)
+    # sweeps run z, y, x; the x sweep finishes the update and the next dt
     return {"prim": c.get("prim", 0.0) * cells, "flux1": 3 * c.get("flux1_per_direction", 0.0) * cells,
-            "sweep_x": sweep * cells, "sweep_y": sweep * cells,
-            "sweep_z": (sweep + c.get("update", 0.0) + c.get("next_dt", 0.0)) * cells}
+            "sweep_z": sweep * cells, "sweep_y": sweep * cells,
+            "sweep_x": (sweep + c.get("update", 0.0) + c.get("next_dt", 0.0)) * cells}
 
 
 def kernel_source_hash():

@@ -699,7 +699,9 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, int first, const R *
 }
 
 // Sweep along x, one thread per traced cell.  A tile covers xw traced cells
-// (xw - 2 updated cells) along x times BLOCK/xw rows along y.
+// (xw - 2 updated cells) along x times BLOCK/xw rows along y.  The last sweep
+// of the step: U^(n+1) from U^n, dt (A + L_x) and the psi source, and the
+// next step's CFL speed.
 template <int PHYS, class R, int PPM, int IFACE64, int LAST>
 __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k_sweep_x(StepArgs a, int first, const R *Vs, const R *L1, R *A)
 {
@@ -755,7 +757,22 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
             const int cl = lcell(P, i, j, k);
 #pragma unroll
             for (int q = 0; q < NV; ++q) s[q] = (sF[me - 1][q] - sF[me][q]) * ix;
-            m = finish_cell<PHYS, R>(a, P, cl, s, dtd, damp, fl);
+            if (a.ndim > 1) {  // A = the other directions' L, from the earlier sweeps
+#pragma unroll
+                for (int q = 0; q < NV; ++q) s[q] = A[q * a.sstride + c] + s[q];
+            }
+            if constexpr (PHYS == PH_MHD && sizeof(R) == 4) {
+                double u0[NV];
+                R Vn[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    u0[q] = a.U[q * a.ustride + P.base + cl];
+                    Vn[q] = Vs[q * a.sstride + c];
+                }
+                m = finish_cell_inc<R>(a, P, cl, s, u0, Vn, dtd, dtr, damp, fl);
+            } else {
+                m = finish_cell<PHYS, R>(a, P, cl, s, dtd, damp, fl);
+            }
         }
         if (a.nextmax) block_max_to<R>(m, a.nextmax);
     } else {
@@ -779,9 +796,14 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
 // consecutive banks.
 constexpr int STG_V = 0, STG_F = 9, STG_A = 27, STG_N = 36;
 
-template <class R, int LAST> __host__ __device__ constexpr int sweep_m_smem()
+// Role of a marching sweep in the step: the first writes A = L_D, a middle
+// one adds L_D to A, the last one updates U (only when x is not swept, i.e.
+// never in the standard order z, y, x).
+enum { SW_MID = 0, SW_LAST = 1, SW_FIRST = 2 };
+
+template <class R, int MODE> __host__ __device__ constexpr int sweep_m_smem()
 {
-    return sizeof(R) == 4 ? 2 * STG_N * BLOCK * 4 + (LAST ? 2 * NV * BLOCK * 8 : 0) : 0;
+    return sizeof(R) == 4 ? 2 * STG_N * BLOCK * 4 + (MODE == SW_LAST ? 2 * NV * BLOCK * 8 : 0) : 0;
 }
 
 // Sweep along D = 1 (y) or 2 (z): each thread marches one segment of SEG
@@ -790,11 +812,12 @@ template <class R, int LAST> __host__ __device__ constexpr int sweep_m_smem()
 // BLOCK/xw (other-dimension, segment) pairs.  Float: the next cell's inputs
 // are staged in shared memory by cp.async (sweep_m_smem bytes per block);
 // double: they are prefetched into L1.
-template <int PHYS, class R, int PPM, int IFACE64, int D, int LAST>
+template <int PHYS, class R, int PPM, int IFACE64, int D, int MODE>
 __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, int first, const R *Vs, const R *L1, R *A)
 {
     constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
     constexpr bool STAGED = sizeof(R) == 4;
+    constexpr bool LAST = MODE == SW_LAST, FIRST = MODE == SW_FIRST;
     const int patch = first + blockIdx.y;
     const DevPatch P = a.patches[patch];
     const Tile t(P.n[0]);
@@ -862,6 +885,9 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
                     } else {
                         mx = fmax(mx, finish_cell_u<PHYS, R>(a, P, (int)(cp - P.soff), s, u, dtd, damp, fl));
                     }
+                } else if constexpr (FIRST) {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) A[q * a.sstride + cp] = s[q];
                 } else {
 #pragma unroll
                     for (int q = 0; q < NV; ++q) A[q * a.sstride + cp] = Ap[q * as] + s[q];
@@ -891,8 +917,10 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
                     for (int q = 0; q < NV; ++q) cp_async(bf + (STG_F + es * 9 + q) * BLOCK, Le + q * a.sstride);
                 }
                 if (jn >= j0 + 1) {
+                    if (!FIRST) {
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) cp_async(bf + (STG_A + q) * BLOCK, A + q * a.sstride + cn - st);
+                        for (int q = 0; q < NV; ++q) cp_async(bf + (STG_A + q) * BLOCK, A + q * a.sstride + cn - st);
+                    }
                     if (LAST) {
                         double *bd = sd + sg * NV * BLOCK;
                         const long long gi = P.base + (cn - st - P.soff);

@@ -15,25 +15,25 @@ namespace ctu {
 // more than the default 48 KB of dynamic shared memory are opted in once per
 // device (the carveout set to its maximum, so that the register-limited
 // number of blocks still fits).
-template <int PHYS, class R, int PPM, int IF64, int D, int LAST>
+template <int PHYS, class R, int PPM, int IF64, int D, int MODE>
 static void launch_sweep_m(const StepArgs &a, const Group &G, const R *Vs, const R *L1, R *A, cudaStream_t s)
 {
-    constexpr int smem = sweep_m_smem<R, LAST>();
+    constexpr int smem = sweep_m_smem<R, MODE>();
     if (smem > 48 * 1024) {
         static std::atomic<unsigned long long> done{0};
         int dev = 0;
         cudaGetDevice(&dev);
         const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
         if (!(done.load() & bit) || !bit) {
-            cudaFuncSetAttribute(k_sweep_m<PHYS, R, PPM, IF64, D, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_sweep_m<PHYS, R, PPM, IF64, D, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem);
-            cudaFuncSetAttribute(k_sweep_m<PHYS, R, PPM, IF64, D, LAST>,
+            cudaFuncSetAttribute(k_sweep_m<PHYS, R, PPM, IF64, D, MODE>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             done.fetch_or(bit);
         }
     }
     const dim3 grid((unsigned)Tiles::sweep_m(G.n, D), (unsigned)G.count);
-    k_sweep_m<PHYS, R, PPM, IF64, D, LAST><<<grid, BLOCK, smem, s>>>(a, G.first, Vs, L1, A);
+    k_sweep_m<PHYS, R, PPM, IF64, D, MODE><<<grid, BLOCK, smem, s>>>(a, G.first, Vs, L1, A);
 }
 
 template <int PHYS, class R, int PPM, int IF64>
@@ -72,36 +72,35 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         }
         CTU_MARK(nullptr);
     }
-    CTU_MARK("sweep_x");
-    for (int g = 0; g < li.ngroups; ++g) {
-        const Group &G = li.groups[g];
-        const dim3 grid((unsigned)Tiles::sweep_x(G.n), (unsigned)G.count);
-        if (a.ndim == 1)
-            k_sweep_x<PHYS, R, PPM, IF64, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, L1, A);
-        else
-            k_sweep_x<PHYS, R, PPM, IF64, 0><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, L1, A);
-        ++n;
+    // sweeps in the order z, y, x: the first writes A = L_D, the middle one
+    // adds to it, and the x sweep (thread per cell) finishes the update
+    if (a.ndim > 2) {
+        CTU_MARK("sweep_z");
+        for (int g = 0; g < li.ngroups; ++g) {
+            launch_sweep_m<PHYS, R, PPM, IF64, 2, SW_FIRST>(a, li.groups[g], Vs, L1, A, s);
+            ++n;
+        }
+        CTU_MARK(nullptr);
     }
-    CTU_MARK(nullptr);
     if (a.ndim > 1) {
         CTU_MARK("sweep_y");
         for (int g = 0; g < li.ngroups; ++g) {
             if (a.ndim == 2)
-                launch_sweep_m<PHYS, R, PPM, IF64, 1, 1>(a, li.groups[g], Vs, L1, A, s);
+                launch_sweep_m<PHYS, R, PPM, IF64, 1, SW_FIRST>(a, li.groups[g], Vs, L1, A, s);
             else
-                launch_sweep_m<PHYS, R, PPM, IF64, 1, 0>(a, li.groups[g], Vs, L1, A, s);
+                launch_sweep_m<PHYS, R, PPM, IF64, 1, SW_MID>(a, li.groups[g], Vs, L1, A, s);
             ++n;
         }
         CTU_MARK(nullptr);
     }
-    if (a.ndim > 2) {
-        CTU_MARK("sweep_z");
-        for (int g = 0; g < li.ngroups; ++g) {
-            launch_sweep_m<PHYS, R, PPM, IF64, 2, 1>(a, li.groups[g], Vs, L1, A, s);
-            ++n;
-        }
-        CTU_MARK(nullptr);
+    CTU_MARK("sweep_x");
+    for (int g = 0; g < li.ngroups; ++g) {
+        const Group &G = li.groups[g];
+        const dim3 grid((unsigned)Tiles::sweep_x(G.n), (unsigned)G.count);
+        k_sweep_x<PHYS, R, PPM, IF64, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, L1, A);
+        ++n;
     }
+    CTU_MARK(nullptr);
     return n;
 }
 
