@@ -152,6 +152,8 @@ __device__ __forceinline__ void cp_async(double *dst, const double *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // wait until at most one committed group of this thread is still in flight
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// wait until every committed group of this thread has landed
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned int state_flags(double rho, double p)
 {
@@ -423,15 +425,24 @@ __device__ __forceinline__ void face_flux(const R (&Lg)[NV], const R (&Rg)[NV], 
     for (int q = 0; q < NV; ++q) Fg[gperm<D>(q)] = F[q];
 }
 
-// Flux-register windows of one face (plane pl normal to D, transverse
+// First flux-register window of plane pl normal to D of a patch (windows of
+// the plane: [window_first(pl), window_first(pl + 1))); 0 when the patch has
+// none in direction D.  Kernels read these ahead of the face solves.
+__device__ __forceinline__ int window_base(const StepArgs &a, int patch, int D)
+{
+    return a.reg ? a.wbase[patch * 3 + D] : -1;
+}
+__device__ __forceinline__ int window_first(const StepArgs &a, int B, int pl)
+{
+    return B >= 0 ? a.wpos[B + pl] : 0;
+}
+
+// Flux-register windows [w0, w1) of one face (normal to D, transverse
 // coordinates ca, cb in increasing dimension order), Eq. (fluxcorr).
 template <class R, int D>
-__device__ __forceinline__ void register_face(const StepArgs &a, int patch, const DevPatch &P, int pl, int ca, int cb,
+__device__ __forceinline__ void register_face(const StepArgs &a, const DevPatch &P, int w0, int w1, int ca, int cb,
                                               const R (&Fg)[NV], double dt)
 {
-    const int B = a.wbase[patch * 3 + D];
-    if (B < 0) return;
-    const int w0 = a.wpos[B + pl], w1 = a.wpos[B + pl + 1];
     for (int w = w0; w < w1; ++w) {
         const DevWindow W = a.win[w];
         if (ca < W.a0 || ca >= W.a1 || cb < W.b0 || cb >= W.b1) continue;
@@ -441,6 +452,22 @@ __device__ __forceinline__ void register_face(const StepArgs &a, int patch, cons
         const long long o = W.dst + (long long)(cb - W.b0) * na + (ca - W.a0);
 #pragma unroll
         for (int q = 0; q < NV; ++q) a.reg[o + q * nb * na] += f * widen<R>(Fg[q]);
+    }
+}
+
+// One variable q of register_face.
+template <class R, int D>
+__device__ __forceinline__ void register_face_var(const StepArgs &a, const DevPatch &P, int w0, int w1, int ca, int cb,
+                                                  int q, R Fq, double dt)
+{
+    for (int w = w0; w < w1; ++w) {
+        const DevWindow W = a.win[w];
+        if (ca < W.a0 || ca >= W.a1 || cb < W.b0 || cb >= W.b1) continue;
+        constexpr int ea = D == 0 ? 1 : 0, eb = D == 2 ? 1 : 2;
+        const double f = W.weight * dt * P.dx[ea] * P.dx[eb];
+        const long long na = W.a1 - W.a0, nb = W.b1 - W.b0;
+        const long long o = W.dst + (long long)(cb - W.b0) * na + (ca - W.a0);
+        a.reg[o + q * nb * na] += f * widen<R>(Fq);
     }
 }
 
@@ -717,7 +744,10 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
     const int k = b / (T0 * T1);
     const bool traced = j < P.n[1] && k < P.n[2] && i <= P.n[0];
     __shared__ R sP[BLOCK][NV], sM[BLOCK][NV], sF[BLOCK][NV];
+    // faces of the block with flux-register windows: lane, first and end window
+    __shared__ int s_nreg, s_reg[BLOCK][3];
     const int me = threadIdx.x;
+    if (me == 0) s_nreg = 0;
     const R gam = pgam<R>(a), ch = pch<R>(a.sp);
     const R dtr = pdt<R>(a.sp);
     const double dtd = a.sp->dt;
@@ -725,6 +755,14 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
     const R hdt = R(0.5) * dtr;
     unsigned int fl = 0;
     const long long c = traced ? P.soff + lcell(P, i, j, k) : 0;
+    const bool out = traced && tx >= 1 && tx <= t.xw - 2 && i >= 0 && i < P.n[0];
+    // windows of this lane's face (plane i + 1), read ahead of the solves
+    int w0 = 0, w1 = 0;
+    if (traced && tx < t.xw - 1 && i <= P.n[0] - 1) {
+        const int B = window_base(a, patch, 0);
+        w0 = window_first(a, B, i + 1);
+        w1 = window_first(a, B, i + 2);
+    }
     if (traced) {
         R vs[5][NV];
 #pragma unroll
@@ -745,11 +783,28 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
 #pragma unroll
         for (int q = 0; q < NV; ++q) sF[me][q] = F[q];
         // faces on plane i+1; the tile's last face belongs to the next tile
-        if (a.reg && (tx < t.xw - 2 || i + 1 == P.n[0])) register_face<R, 0>(a, patch, P, i + 1, j, k, F, dtd);
+        if (w1 > w0 && (tx < t.xw - 2 || i + 1 == P.n[0])) {
+            const int slot = atomicAdd(&s_nreg, 1);
+            s_reg[slot][0] = me;
+            s_reg[slot][1] = w0;
+            s_reg[slot][2] = w1;
+        }
     }
-    const bool out = traced && tx >= 1 && tx <= t.xw - 2 && i >= 0 && i < P.n[0];
+    // after a block barrier: the listed faces' register sums, one thread per
+    // (face, variable), so that the float64 accumulation of a face is spread
+    // over lanes instead of running on one lane of its warp
+    auto registers = [&]() {
+        const int nr = s_nreg;
+        for (int it = me; it < nr * NV; it += BLOCK) {
+            const int f = it / NV, q = it - f * NV;
+            const int l = s_reg[f][0];
+            const int jl = ((b / T0) % T1) * t.rows + l / t.xw;  // row of lane l; k is the block's
+            register_face_var<R, 0>(a, P, s_reg[f][1], s_reg[f][2], jl, k, q, sF[l][q], dtd);
+        }
+    };
     if (LAST) {
         const double damp = patch_damp(a, P);  // includes a block barrier
+        registers();
         R m = R(0);
         if (out) {
             const R ix = pidx<R>(P, 0);
@@ -777,6 +832,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
         if (a.nextmax) block_max_to<R>(m, a.nextmax);
     } else {
         __syncthreads();
+        registers();
         if (out) {
             const R ix = pidx<R>(P, 0);
 #pragma unroll
@@ -855,6 +911,7 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
         R Pprev[NV], Fprev[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) { Pprev[q] = R(0); Fprev[q] = R(0); }
+        const int wb = window_base(a, patch, D);
         // face flux of plane j from Pprev (cell j - 1) and Vm (cell j); update
         // of cell j - 1 from the previous face flux, with its running sum A at
         // Ap[q * as] and (last sweep) its state U^n at Up[q * us]
@@ -864,7 +921,10 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
             face_flux<PHYS, R, D>(Pprev, Vm, gam, ch, F);
             // plane j; (a, b) = (x, o) are the two non-D dimensions in
             // increasing order; a segment's last face belongs to the next
-            if (a.reg && (j < j1 || j1 == nD)) register_face<R, D>(a, patch, P, j, x, o, F, dtd);
+            if (wb >= 0 && (j < j1 || j1 == nD)) {
+                const int w0 = window_first(a, wb, j), w1 = window_first(a, wb, j + 1);
+                register_face<R, D>(a, P, w0, w1, x, o, F, dtd);
+            }
             if (j >= j0 + 1) {
                 const long long cp = cj - st;  // cell j - 1
                 R s[NV];
