@@ -216,10 +216,14 @@ def run_ours(args):
         c = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3))
         c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
+        if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
+            c.autotune(U, Uo, stride, patches, dtch)
+            tiles["xw_seg"] = list(c.tile_params([n] * 3))
         return c
 
     dtch = torch.zeros(2, dtype=torch.float64, device=dev)
     dtn = torch.zeros(2, dtype=torch.float64, device=dev)
+    tiles = {}
 
     def step(c):
         # the step with its fused next-step CFL epilogue (Eq. Ca on U^(n+1));
@@ -356,7 +360,7 @@ def run_ours(args):
                 "dtype": "f32+f64" if primary == ctu.CTU_MIXED else "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "cells_per_gpu": cells, "patches_per_gpu": 1,
                            "precision": args.precision, "l2_flush": "inputs (1.3 GB) > L2",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}", "tiles_xw_seg": tiles.get("xw_seg")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path,
                 "gpu_launches": launches_per_step * res["K"], "clocks": clk,
                 "status": ctu.STATUS[res["status"]] if 0 <= res["status"] < 10 else res["status"],
@@ -443,6 +447,14 @@ def run_amr(args):
     for lev in range(len(L)):
         D.append(torch.tensor([dt0 / 2 ** lev, ch], dtype=torch.float64, device=dev))
     stream = torch.cuda.Stream(device=dev)
+    # tile width and marching segment per patch shape of each level
+    tiles = {}
+    for lev in range(len(L)):
+        if P[lev] is not None:
+            ctxs[lev].autotune(A[lev], B[lev], A[lev].shape[1], P[lev], D[lev], stream=stream)
+            for n in sorted({tuple(L[lev]["patches"][gi][0]) for gi in mine[lev]}):
+                tiles[f"l{lev}_{n[0]}^3"] = list(ctxs[lev].tile_params(n))
+    torch.cuda.synchronize()
 
     def lstep(lev, src, dst):
         if P[lev] is not None:
@@ -513,6 +525,7 @@ def run_amr(args):
                            "cell_updates_per_coarse_step": upd, "windows_rank0": sum(len(w) for w in wins),
                            "rank0_share_of_updates": my_upd / upd,
                            "parallelism": f"patch shards x{world}" if world > 1 else "single GPU",
+                           "tiles_xw_seg": tiles,
                            "l2_flush": "inputs larger than L2"},
                 "gpu_launches": launches * args.steps, "clocks": clk,
                 "kernels_ms_per_coarse_step": kern,

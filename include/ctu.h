@@ -169,6 +169,28 @@ ctu_status ctu_step_next_dt(ctu_ctx *ctx, const double *U_in, double *U_out, int
 ctu_status ctu_flux_registers(ctu_ctx *ctx, double *reg, const ctu_flux_window *win,
                               int nwin);
 
+/* Tile autotuner (launch configuration only; the paper has no counterpart).
+ * A launch covers every patch shape of the batch; per shape, the kernels use
+ * a thread-tile width along x (8, 16 or 32 lanes) and a marching segment
+ * length along y and z (4 to 64 cells).  ctu_autotune times ctu_step on the
+ * caller's batch for each candidate pair of every shape in turn (largest
+ * shapes first, the others held fixed), keeps the fastest, and stores the
+ * choice per shape in the context for every later call.  The choice changes
+ * only how cells map to threads: each cell's arithmetic, and so the result,
+ * is the same for every choice.  U_out is overwritten (U_in is read only);
+ * the bound flux registers are left untouched; d_dt_ch is read as in
+ * ctu_step.  Synchronises the stream; make the call before any capture.
+ * Errors: as ctu_step. */
+ctu_status ctu_autotune(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t stride,
+                        const ctu_patch *patches, int npatch, const double *d_dt_ch,
+                        void *stream);
+
+/* The tile width *xw and segment length *seg the context uses for patches of
+ * interior shape n[3] (autotuned if ctu_autotune saw that shape, else the
+ * default rule: 32 lanes for n[0] >= 24, 16 for n[0] >= 12, else 8; 16
+ * cells). */
+ctu_status ctu_tile_params(ctu_ctx *ctx, const int n[3], int *xw, int *seg);
+
 /* Fill the ghost cells of every patch with periodic copies of its own
  * interior (helper for periodic boxes; not part of the step). */
 ctu_status ctu_fill_periodic(ctu_ctx *ctx, double *U, int64_t stride,

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -83,8 +84,32 @@ struct EventProf : ProfHook {
     }
 };
 
+// Key of a patch shape in the autotune cache.
+static std::array<int, 3> shape_key(const int *n) { return {n[0], n[1], n[2]}; }
+
+// Every kernel's block count over a batch fits one launch (grid x < 2^31).
+static bool grid_fits(const std::vector<Group> &gs, int ndim)
+{
+    long long tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (const Group &G : gs) {
+        const long long c = G.count;
+        tot[0] += c * Tiles::prim(G.N);
+        for (int D = 0; D < 3; ++D) {
+            tot[1 + D] += c * Tiles::div1(G.n, ndim, D, G.xw, G.seg);
+            tot[4 + D] += c * (D == 0 ? Tiles::sweep_x(G.n, G.xw) : Tiles::sweep_m(G.n, D, G.xw, G.seg));
+        }
+        tot[7] += c * Tiles::interior(G.n, G.xw);
+    }
+    for (long long t : tot)
+        if (t >= (1LL << 31)) return false;
+    return true;
+}
+
 struct ctu_ctx {
     ctu_config cfg;
+    // autotuned thread-tile width along x and marching segment per shape
+    std::map<std::array<int, 3>, std::array<int, 2>> tune;
+    bool tuning = false;  // steps of ctu_autotune leave the flux registers alone
     int device = 0;
     // patch list cache (caller order) and its device table (grouped order)
     std::vector<ctu_patch> hpatch;
@@ -253,15 +278,15 @@ static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStr
         }
         groups.back().count += 1;
     }
-    // split groups into <= 65535 patches (grid y limit)
-    std::vector<Group> g2;
-    for (const Group &G : groups)
-        for (int f = 0; f < G.count; f += 65535) {
-            Group H = G;
-            H.first = G.first + f;
-            H.count = std::min(65535, G.count - f);
-            g2.push_back(H);
-        }
+    // tile parameters per shape (autotuned, else the default rule), and the
+    // launch order: largest patches first
+    std::vector<Group> g2(groups.rbegin(), groups.rend());
+    for (Group &G : g2) {
+        const auto it = ctx->tune.find(shape_key(G.n));
+        G.xw = it != ctx->tune.end() ? it->second[0] : Tiles::xw(G.n[0]);
+        G.seg = it != ctx->tune.end() ? it->second[1] : SEG;
+    }
+    if (!grid_fits(g2, ctx->cfg.ndim)) return CTU_EINVAL;
     if (np > ctx->dpatch_cap) {
         if (ctx->dpatch) cudaFree(ctx->dpatch);
         ctx->dpatch = nullptr;
@@ -315,7 +340,7 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.dtch = dtch;
     a.sp = ctx->dsp;
     a.status = ctx->dstatus;
-    const bool regs = ctx->reg && !ctx->hwin.empty();
+    const bool regs = ctx->reg && !ctx->hwin.empty() && !ctx->tuning;
     a.win = regs ? ctx->dwin : nullptr;
     a.wbase = regs ? ctx->dwstart : nullptr;
     a.wpos = regs ? ctx->dwstart + 3 * (int)ctx->hpatch.size() : nullptr;
@@ -484,6 +509,84 @@ ctu_status ctu_step_next_dt(ctu_ctx *ctx, const double *U_in, double *U_out, int
 {
     if (!d_dt_ch_next || d_dt_ch_next == d_dt_ch) return CTU_EINVAL;
     return step_common(ctx, U_in, U_out, stride, patches, npatch, d_dt_ch, d_dt_ch_next, stream);
+}
+
+ctu_status ctu_autotune(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t stride, const ctu_patch *patches,
+                        int npatch, const double *d_dt_ch, void *stream)
+{
+    if (!ctx || !U_in || !U_out || !d_dt_ch || U_in == U_out) return CTU_EINVAL;
+    ctu_status st = validate_patches(ctx, stride, patches, npatch);
+    if (st != CTU_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = bind_patches(ctx, patches, npatch, s);
+    if (st != CTU_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CTU_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return CTU_ECUDA;
+    }
+    ctx->tuning = true;
+    auto timed = [&](float &ms) -> ctu_status {
+        ctu_status r = step_common(ctx, U_in, U_out, stride, patches, npatch, d_dt_ch, nullptr, stream);
+        if (r != CTU_OK) return r;
+        float best = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) return CTU_ECUDA;
+            r = step_common(ctx, U_in, U_out, stride, patches, npatch, d_dt_ch, nullptr, stream);
+            if (r != CTU_OK) return r;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return CTU_ECUDA;
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return CTU_ECUDA;
+            best = std::min(best, t);
+        }
+        ms = best;
+        return CTU_OK;
+    };
+    // coordinate descent over the shapes, largest first: for each, every
+    // (tile width, segment) candidate with the other shapes fixed
+    static const int kXw[] = {8, 16, 32};
+    static const int kSeg[] = {4, 8, 16, 32, 64};
+    for (size_t g = 0; g < ctx->groups.size() && st == CTU_OK; ++g) {
+        Group &G = ctx->groups[g];
+        int bx = G.xw, bs = G.seg;
+        float bt = 1e30f;
+        const int nmax = std::max(G.n[0], std::max(G.n[1], G.n[2]));
+        for (int xw : kXw) {
+            if (xw > 8 && xw / 2 >= G.n[0] + 2) continue;  // wider than the patch
+            for (int sg : kSeg) {
+                if (sg > 4 && sg / 2 >= nmax) continue;    // longer than any pencil
+                G.xw = xw;
+                G.seg = sg;
+                if (!grid_fits(ctx->groups, ctx->cfg.ndim)) continue;
+                float t = 0.0f;
+                st = timed(t);
+                if (st != CTU_OK) break;
+                if (t < bt) {
+                    bt = t;
+                    bx = xw;
+                    bs = sg;
+                }
+            }
+            if (st != CTU_OK) break;
+        }
+        G.xw = bx;
+        G.seg = bs;
+        ctx->tune[shape_key(G.n)] = {bx, bs};
+    }
+    ctx->tuning = false;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+ctu_status ctu_tile_params(ctu_ctx *ctx, const int n[3], int *xw, int *seg)
+{
+    if (!ctx || !n || !xw || !seg) return CTU_EINVAL;
+    const auto it = ctx->tune.find(shape_key(n));
+    *xw = it != ctx->tune.end() ? it->second[0] : Tiles::xw(n[0]);
+    *seg = it != ctx->tune.end() ? it->second[1] : SEG;
+    return CTU_OK;
 }
 
 ctu_status ctu_flux_registers(ctu_ctx *ctx, double *reg, const ctu_flux_window *win, int nwin)

@@ -99,7 +99,67 @@ constexpr int BLOCK = 128;
 #ifndef CTU_SWEEPX_MINB
 #define CTU_SWEEPX_MINB 5
 #endif
-constexpr int SEG = CTU_SEG;  // cells per marching segment
+constexpr int SEG = CTU_SEG;  // default cells per marching segment
+
+// One launch covers every patch group of a batch (up to MAXG groups): block
+// blockIdx.x belongs to the group g with start[g] <= blockIdx.x < start[g+1]
+// and to its patch first[g] + (blockIdx.x - start[g]) / bpp[g].  Each group
+// carries its own thread-tile width along x and marching segment length
+// (chosen per patch shape, e.g. by the autotuner).  The table travels in the
+// kernel parameters (constant bank); the block scheduler drains the blocks,
+// largest patches first.
+constexpr int MAXG = 16;
+struct GroupTable {
+    int n;
+    int start[MAXG + 1];
+    int first[MAXG];
+    int bpp[MAXG];
+    unsigned bm[MAXG];       // division by bpp: multiplier and shifts (divmagic)
+    unsigned char bs1[MAXG], bs2[MAXG];
+    int xw[MAXG];
+    int seg[MAXG];
+};
+
+// Division of 0 <= x < 2^32 by an invariant divisor d >= 1 with one high
+// multiply, two shifts and two adds (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, Fig. 4.1):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, s1 = min(l, 1),
+// s2 = max(l - 1, 0); x / d = (t + ((x - t) >> s1)) >> s2 with t = mulhi(m, x).
+struct DivMagic {
+    unsigned m;
+    unsigned char s1, s2;
+};
+inline DivMagic divmagic(unsigned d)
+{
+    int l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    DivMagic r;
+    r.m = (unsigned)((((1ull << l) - d) << 32) / d + 1);
+    r.s1 = (unsigned char)(l < 1 ? l : 1);
+    r.s2 = (unsigned char)(l > 1 ? l - 1 : 0);
+    return r;
+}
+
+struct Where {
+    int patch, b, xw, seg;
+};
+
+__device__ __forceinline__ Where locate(const GroupTable &gt)
+{
+    const int bx = (int)blockIdx.x;
+    int g = 0;
+#pragma unroll 1
+    while (g + 1 < gt.n && bx >= gt.start[g + 1]) ++g;
+    const unsigned rel = (unsigned)(bx - gt.start[g]);
+    const unsigned t = __umulhi(gt.bm[g], rel);
+    const int q = (int)((t + ((rel - t) >> gt.bs1[g])) >> gt.bs2[g]);  // rel / bpp
+    Where w;
+    w.patch = gt.first[g] + q;
+    w.b = (int)rel - q * gt.bpp[g];
+    w.xw = gt.xw[g];
+    w.seg = gt.seg[g];
+    return w;
+}
 // The marching sweeps are latency bound: they are compiled for at least
 // CTU_MARCH_MINB resident blocks per SM (register cap 65536 / (BLOCK * MINB)),
 // the float x sweep for CTU_SWEEPX_MINB.
@@ -552,50 +612,50 @@ __device__ __forceinline__ double patch_damp(const StepArgs &a, const DevPatch &
 // Thread tile of a block: BLOCK threads as xw lanes along x times BLOCK/xw rows.
 struct Tile {
     int xw, rows;
-    __device__ __forceinline__ explicit Tile(int nx)
+    __device__ __forceinline__ explicit Tile(int w)
     {
-        xw = tile_xw(nx);
+        xw = w;
         rows = BLOCK / xw;
     }
     __device__ __forceinline__ int tx() const { return threadIdx.x % xw; }
     __device__ __forceinline__ int ty() const { return threadIdx.x / xw; }
 };
 
-// Host mirror of the kernels' block counts per patch (same tiling).
+// Host mirror of the kernels' block counts per patch (same tiling), for an
+// x tile width w (8, 16 or 32 lanes) and a marching segment of seg cells.
 struct Tiles {
     static int xw(int nx) { return tile_xw(nx); }
-    static long long prim(const int *n, const int *N)
+    static long long prim(const int *N)
     {
-        (void)n;
         return ((long long)N[0] * N[1] * N[2] + BLOCK - 1) / BLOCK;
     }
-    static long long div1(const int *n, int ndim, int D)
+    static long long div1(const int *n, int ndim, int D, int w, int seg)
     {
-        const int w = xw(n[0]), r = BLOCK / w;
+        const int r = BLOCK / w;
         if (D == 0) {
             const int e1 = ndim > 1 ? n[1] + 2 : 1, e2 = ndim > 2 ? n[2] + 2 : 1;
             return (long long)((n[0] + w - 2) / (w - 1)) * ((e1 + r - 1) / r) * e2;
         }
         const int O = D == 1 ? 2 : 1;
         const int eO = ndim > O ? n[O] + 2 : 1;
-        const long long nseg = (n[D] + SEG - 1) / SEG;
+        const long long nseg = (n[D] + seg - 1) / seg;
         return (long long)((n[0] + 2 + w - 1) / w) * ((eO * nseg + r - 1) / r);
     }
-    static long long sweep_x(const int *n)
+    static long long sweep_x(const int *n, int w)
     {
-        const int w = xw(n[0]), r = BLOCK / w;
+        const int r = BLOCK / w;
         return (long long)((n[0] + w - 3) / (w - 2)) * ((n[1] + r - 1) / r) * n[2];
     }
-    static long long sweep_m(const int *n, int D)
+    static long long sweep_m(const int *n, int D, int w, int seg)
     {
         const int O = D == 1 ? 2 : 1;
-        const int w = xw(n[0]), r = BLOCK / w;
-        const long long nseg = (n[D] + SEG - 1) / SEG;
+        const int r = BLOCK / w;
+        const long long nseg = (n[D] + seg - 1) / seg;
         return (long long)((n[0] + w - 1) / w) * ((n[O] * nseg + r - 1) / r);
     }
-    static long long interior(const int *n)
+    static long long interior(const int *n, int w)
     {
-        const int w = xw(n[0]), r = BLOCK / w;
+        const int r = BLOCK / w;
         return (long long)((n[0] + w - 1) / w) * ((n[1] + r - 1) / r) * n[2];
     }
 };
@@ -612,12 +672,13 @@ static __global__ void k_setup(const double *dtch, StepParams *sp)
 }
 
 // V = V(U) on every ghosted cell (a flat range of the patch region);
-// blockIdx.y = patch (within the group).
+// one block per BLOCK cells of a patch.
 template <int PHYS, class R>
-__global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, int first, R *Vs)
+__global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, GroupTable gt, R *Vs)
 {
-    const DevPatch P = a.patches[first + blockIdx.y];
-    const int c = blockIdx.x * BLOCK + threadIdx.x;
+    const Where w = locate(gt);
+    const DevPatch P = a.patches[w.patch];
+    const int c = w.b * BLOCK + threadIdx.x;
     if (c >= P.N[0] * P.N[1] * P.N[2]) return;
     double U[NV];
     R V[NV];
@@ -638,14 +699,16 @@ __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, int first, R *Vs)
 //   D = y, z: one thread per segment of SEG cells marching along D with the
 //          previous face flux and cell state in registers.
 template <int PHYS, class R, int D>
-__global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, int first, const R *Vs, R *L1)
+__global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const R *Vs, R *L1)
 {
-    const DevPatch P = a.patches[first + blockIdx.y];
-    const Tile t(P.n[0]);
+    const Where wh = locate(gt);
+    const DevPatch P = a.patches[wh.patch];
+    const Tile t(wh.xw);
+    const int SEGL = wh.seg;
     const R gam = pgam<R>(a), ch = pch<R>(a.sp);
     const R iD = pidx<R>(P, D);
     R *Ld = L1 + (long long)D * NV * a.sstride;
-    const int b = blockIdx.x;
+    const int b = wh.b;
     if constexpr (D == 0) {
         const int out = t.xw - 1;
         const int e1 = a.ndim > 1 ? P.n[1] + 2 : 1, e2 = a.ndim > 2 ? P.n[2] + 2 : 1;
@@ -682,13 +745,13 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, int first, const R *
         constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
         const int nD = P.n[D];
         const int eO = a.ndim > O ? P.n[O] + 2 : 1, loO = a.ndim > O ? -1 : 0;
-        const int nseg = (nD + SEG - 1) / SEG;
+        const int nseg = (nD + SEGL - 1) / SEGL;
         const int T0 = (P.n[0] + 2 + t.xw - 1) / t.xw;
         const int x = (b % T0) * t.xw + t.tx() - 1;
         const int comb = (b / T0) * t.rows + t.ty();
         const int o = comb / nseg, seg = comb % nseg;
         if (x > P.n[0] || o >= eO) return;
-        const int j0 = seg * SEG, j1 = min(j0 + SEG, nD);
+        const int j0 = seg * SEGL, j1 = min(j0 + SEGL, nD);
         const int st = dstr(P, D);
         int cc[3];
         cc[0] = x;
@@ -730,14 +793,15 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, int first, const R *
 // of the step: U^(n+1) from U^n, dt (A + L_x) and the psi source, and the
 // next step's CFL speed.
 template <int PHYS, class R, int PPM, int IFACE64, int LAST>
-__global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k_sweep_x(StepArgs a, int first, const R *Vs, const R *L1, R *A)
+__global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k_sweep_x(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *A)
 {
-    const int patch = first + blockIdx.y;
+    const Where wh = locate(gt);
+    const int patch = wh.patch;
     const DevPatch P = a.patches[patch];
-    const Tile t(P.n[0]);
+    const Tile t(wh.xw);
     const int out_x = t.xw - 2;
     const int T0 = (P.n[0] + out_x - 1) / out_x, T1 = (P.n[1] + t.rows - 1) / t.rows;
-    const int b = blockIdx.x;
+    const int b = wh.b;
     const int tx = t.tx(), ty = t.ty();
     const int i = (b % T0) * out_x - 1 + tx;  // traced cell, >= -1
     const int j = ((b / T0) % T1) * t.rows + ty;
@@ -869,18 +933,20 @@ template <class R, int MODE> __host__ __device__ constexpr int sweep_m_smem()
 // are staged in shared memory by cp.async (sweep_m_smem bytes per block);
 // double: they are prefetched into L1.
 template <int PHYS, class R, int PPM, int IFACE64, int D, int MODE>
-__global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, int first, const R *Vs, const R *L1, R *A)
+__global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *A)
 {
     constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
     constexpr bool STAGED = sizeof(R) == 4;
     constexpr bool LAST = MODE == SW_LAST, FIRST = MODE == SW_FIRST;
-    const int patch = first + blockIdx.y;
+    const Where wh = locate(gt);
+    const int patch = wh.patch;
     const DevPatch P = a.patches[patch];
-    const Tile t(P.n[0]);
+    const Tile t(wh.xw);
+    const int SEGL = wh.seg;
     const int nD = P.n[D], nO = P.n[O];
-    const int nseg = (nD + SEG - 1) / SEG;
+    const int nseg = (nD + SEGL - 1) / SEGL;
     const int T0 = (P.n[0] + t.xw - 1) / t.xw;
-    const int b = blockIdx.x;
+    const int b = wh.b;
     const int x = (b % T0) * t.xw + t.tx();
     const int comb = (b / T0) * t.rows + t.ty();
     const int o = comb / nseg, seg = comb % nseg;
@@ -896,7 +962,7 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
     unsigned int fl = 0;
     R mx = R(0);
     if (ok) {
-        const int j0 = seg * SEG, j1 = min(j0 + SEG, nD);
+        const int j0 = seg * SEGL, j1 = min(j0 + SEGL, nD);
         const int st = dstr(P, D);
         int cc[3];
         cc[0] = x;
@@ -1071,12 +1137,13 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, i
 
 // ctu_dt: max over interior cells of max_d (|v_d| + c_f,d)/dx_d.
 template <int PHYS, class R>
-__global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, int first, unsigned long long *out)
+__global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, GroupTable gt, unsigned long long *out)
 {
-    const DevPatch P = a.patches[first + blockIdx.y];
-    const Tile t(P.n[0]);
+    const Where wh = locate(gt);
+    const DevPatch P = a.patches[wh.patch];
+    const Tile t(wh.xw);
     const int T0 = (P.n[0] + t.xw - 1) / t.xw, T1 = (P.n[1] + t.rows - 1) / t.rows;
-    const int b = blockIdx.x;
+    const int b = wh.b;
     const int i = (b % T0) * t.xw + t.tx(), j = ((b / T0) % T1) * t.rows + t.ty(), k = b / (T0 * T1);
     R m = R(0);
     if (i < P.n[0] && j < P.n[1] && k < P.n[2]) {

@@ -11,12 +11,45 @@ namespace ctu {
 #define CTU_MARK(nm) \
     if (li.prof) li.prof->mark(nm, s)
 
-// Launch one marching sweep over a patch group.  Kernels that stage through
-// more than the default 48 KB of dynamic shared memory are opted in once per
-// device (the carveout set to its maximum, so that the register-limited
-// number of blocks still fits).
+// Launch a kernel once over every patch group of the batch (MAXG groups per
+// launch), in the order of li.groups (largest patches first).  bpp(G): blocks
+// per patch of group G; go(table, blocks) launches.  Returns the number of
+// launches.
+template <class BPP, class GO>
+static int over_groups(const LaunchInfo &li, BPP bpp, GO go)
+{
+    int launches = 0;
+    for (int c0 = 0; c0 < li.ngroups; c0 += MAXG) {
+        GroupTable gt;
+        gt.n = li.ngroups - c0 < MAXG ? li.ngroups - c0 : MAXG;
+        long long tot = 0;
+        for (int k = 0; k < gt.n; ++k) {
+            const Group &G = li.groups[c0 + k];
+            gt.start[k] = (int)tot;
+            gt.first[k] = G.first;
+            gt.bpp[k] = (int)bpp(G);
+            const DivMagic dm = divmagic((unsigned)(gt.bpp[k] > 0 ? gt.bpp[k] : 1));
+            gt.bm[k] = dm.m;
+            gt.bs1[k] = dm.s1;
+            gt.bs2[k] = dm.s2;
+            gt.xw[k] = G.xw;
+            gt.seg[k] = G.seg;
+            tot += (long long)G.count * gt.bpp[k];
+        }
+        gt.start[gt.n] = (int)tot;
+        if (tot > 0) {
+            go(gt, (unsigned)tot);
+            ++launches;
+        }
+    }
+    return launches;
+}
+
+// Kernels that stage through more than the default 48 KB of dynamic shared
+// memory are opted in once per device (the carveout set to its maximum, so
+// that the register-limited number of blocks still fits).
 template <int PHYS, class R, int PPM, int IF64, int D, int MODE>
-static void launch_sweep_m(const StepArgs &a, const Group &G, const R *Vs, const R *L1, R *A, cudaStream_t s)
+static int launch_sweep_m(const StepArgs &a, const LaunchInfo &li, const R *Vs, const R *L1, R *A, cudaStream_t s)
 {
     constexpr int smem = sweep_m_smem<R, MODE>();
     if (smem > 48 * 1024) {
@@ -32,8 +65,11 @@ static void launch_sweep_m(const StepArgs &a, const Group &G, const R *Vs, const
             done.fetch_or(bit);
         }
     }
-    const dim3 grid((unsigned)Tiles::sweep_m(G.n, D), (unsigned)G.count);
-    k_sweep_m<PHYS, R, PPM, IF64, D, MODE><<<grid, BLOCK, smem, s>>>(a, G.first, Vs, L1, A);
+    return over_groups(
+        li, [&](const Group &G) { return Tiles::sweep_m(G.n, D, G.xw, G.seg); },
+        [&](const GroupTable &gt, unsigned nb) {
+            k_sweep_m<PHYS, R, PPM, IF64, D, MODE><<<nb, BLOCK, smem, s>>>(a, gt, Vs, L1, A);
+        });
 }
 
 template <int PHYS, class R, int PPM, int IF64>
@@ -50,56 +86,45 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     CTU_MARK(nullptr);
     ++n;
     CTU_MARK("prim");
-    for (int g = 0; g < li.ngroups; ++g) {
-        const Group &G = li.groups[g];
-        k_prim<PHYS, R><<<dim3((unsigned)Tiles::prim(G.n, G.N), (unsigned)G.count), BLOCK, 0, s>>>(a, G.first, Vs);
-        ++n;
-    }
+    n += over_groups(
+        li, [&](const Group &G) { return Tiles::prim(G.N); },
+        [&](const GroupTable &gt, unsigned nb) { k_prim<PHYS, R><<<nb, BLOCK, 0, s>>>(a, gt, Vs); });
     CTU_MARK(nullptr);
     if (a.ndim > 1) {  // first-order stage: the transverse terms of the sweeps
         CTU_MARK("flux1");
-        for (int g = 0; g < li.ngroups; ++g) {
-            const Group &G = li.groups[g];
-            const unsigned c = (unsigned)G.count;
-            k_div1<PHYS, R, 0><<<dim3((unsigned)Tiles::div1(G.n, a.ndim, 0), c), BLOCK, 0, s>>>(a, G.first, Vs, L1);
-            k_div1<PHYS, R, 1><<<dim3((unsigned)Tiles::div1(G.n, a.ndim, 1), c), BLOCK, 0, s>>>(a, G.first, Vs, L1);
-            n += 2;
-            if (a.ndim > 2) {
-                k_div1<PHYS, R, 2><<<dim3((unsigned)Tiles::div1(G.n, a.ndim, 2), c), BLOCK, 0, s>>>(a, G.first, Vs,
-                                                                                                 L1);
-                ++n;
-            }
-        }
+        n += over_groups(
+            li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 0, G.xw, G.seg); },
+            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 0><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+        n += over_groups(
+            li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 1, G.xw, G.seg); },
+            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 1><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+        if (a.ndim > 2)
+            n += over_groups(
+                li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 2, G.xw, G.seg); },
+                [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 2><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
         CTU_MARK(nullptr);
     }
     // sweeps in the order z, y, x: the first writes A = L_D, the middle one
     // adds to it, and the x sweep (thread per cell) finishes the update
     if (a.ndim > 2) {
         CTU_MARK("sweep_z");
-        for (int g = 0; g < li.ngroups; ++g) {
-            launch_sweep_m<PHYS, R, PPM, IF64, 2, SW_FIRST>(a, li.groups[g], Vs, L1, A, s);
-            ++n;
-        }
+        n += launch_sweep_m<PHYS, R, PPM, IF64, 2, SW_FIRST>(a, li, Vs, L1, A, s);
         CTU_MARK(nullptr);
     }
     if (a.ndim > 1) {
         CTU_MARK("sweep_y");
-        for (int g = 0; g < li.ngroups; ++g) {
-            if (a.ndim == 2)
-                launch_sweep_m<PHYS, R, PPM, IF64, 1, SW_FIRST>(a, li.groups[g], Vs, L1, A, s);
-            else
-                launch_sweep_m<PHYS, R, PPM, IF64, 1, SW_MID>(a, li.groups[g], Vs, L1, A, s);
-            ++n;
-        }
+        if (a.ndim == 2)
+            n += launch_sweep_m<PHYS, R, PPM, IF64, 1, SW_FIRST>(a, li, Vs, L1, A, s);
+        else
+            n += launch_sweep_m<PHYS, R, PPM, IF64, 1, SW_MID>(a, li, Vs, L1, A, s);
         CTU_MARK(nullptr);
     }
     CTU_MARK("sweep_x");
-    for (int g = 0; g < li.ngroups; ++g) {
-        const Group &G = li.groups[g];
-        const dim3 grid((unsigned)Tiles::sweep_x(G.n), (unsigned)G.count);
-        k_sweep_x<PHYS, R, PPM, IF64, 1><<<grid, BLOCK, 0, s>>>(a, G.first, Vs, L1, A);
-        ++n;
-    }
+    n += over_groups(
+        li, [&](const Group &G) { return Tiles::sweep_x(G.n, G.xw); },
+        [&](const GroupTable &gt, unsigned nb) {
+            k_sweep_x<PHYS, R, PPM, IF64, 1><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, A);
+        });
     CTU_MARK(nullptr);
     return n;
 }
@@ -120,13 +145,11 @@ template <int PHYS, class R>
 int launch_maxspeed_impl(const StepArgs &a, const LaunchInfo &li, unsigned long long *out, cudaStream_t s)
 {
     CTU_MARK("maxspeed");
-    for (int g = 0; g < li.ngroups; ++g) {
-        const Group &G = li.groups[g];
-        k_maxspeed<PHYS, R><<<dim3((unsigned)Tiles::interior(G.n), (unsigned)G.count), BLOCK, 0, s>>>(a, G.first,
-                                                                                                      out);
-    }
+    const int n = over_groups(
+        li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
+        [&](const GroupTable &gt, unsigned nb) { k_maxspeed<PHYS, R><<<nb, BLOCK, 0, s>>>(a, gt, out); });
     CTU_MARK(nullptr);
-    return li.ngroups;
+    return n;
 }
 
 #undef CTU_MARK

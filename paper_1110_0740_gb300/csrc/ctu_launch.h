@@ -18,15 +18,17 @@ struct ProfHook {
     virtual ~ProfHook() {}
 };
 
-// Patches of identical shape, contiguous in the device patch table: each
-// kernel is launched once per group with blockIdx.y = patch in the group.
+// Patches of identical shape, contiguous in the device patch table, with the
+// thread-tile width along x (8, 16 or 32) and the marching segment length
+// their kernels use.  A launch covers up to MAXG groups (GroupTable).
 struct Group {
     int first, count;
     int n[3], N[3];
+    int xw, seg;
 };
 
 struct LaunchInfo {
-    const Group *groups;   // host array
+    const Group *groups;   // host array, largest patches first
     int ngroups;
     int recon;             // 0 linear, 1 PPM
     int iface64;           // mixed path: 1 = float64 interface-state recovery

@@ -111,6 +111,8 @@ extern "C" ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in
             groups[i].n[d] = q.n[d];
             groups[i].N[d] = q.N[d];
         }
+        groups[i].xw = Tiles::xw(q.n[0]);
+        groups[i].seg = SEG;
     }
     const size_t elt = cfg->precision == CTU_FP64 ? sizeof(double) : sizeof(float);
     if ((size_t)off * SCRATCH_ARRAYS * elt > kScratchBytes) return CTU_ETOOLARGE;

@@ -90,6 +90,11 @@ def _lib():
         L.ctu_step_noalloc.argtypes = [ctypes.POINTER(ctu_config), vp, vp, i64,
                                        ctypes.POINTER(ctu_patch), i32, vp, i32, vp]
         L.ctu_step_noalloc.restype = i32
+        L.ctu_autotune.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp, vp]
+        L.ctu_autotune.restype = i32
+        L.ctu_tile_params.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]
+        L.ctu_tile_params.restype = i32
         for f in ("ctu_init", "ctu_dt", "ctu_step", "ctu_flux_registers", "ctu_fill_periodic",
                   "ctu_status_sync", "ctu_last_launch_count"):
             getattr(L, f).restype = i32
@@ -175,6 +180,19 @@ def ctu_step_next_dt(ctx, U_in, U_out, stride, patches, d_dt_ch, d_dt_ch_next, s
                                    _stream(stream)), "ctu_step_next_dt")
 
 
+def ctu_autotune(ctx, U_in, U_out, stride, patches, d_dt_ch, stream=None):
+    _check(_lib().ctu_autotune(ctx, _ptr(U_in), _ptr(U_out), int(stride), patches, len(patches),
+                               _ptr(d_dt_ch), _stream(stream)), "ctu_autotune")
+
+
+def ctu_tile_params(ctx, n):
+    """(tile width along x, marching segment) used for interior shape n."""
+    arr = (ctypes.c_int * 3)(*[int(v) for v in n])
+    xw, seg = ctypes.c_int(), ctypes.c_int()
+    _check(_lib().ctu_tile_params(ctx, arr, ctypes.byref(xw), ctypes.byref(seg)), "ctu_tile_params")
+    return xw.value, seg.value
+
+
 def ctu_flux_registers(ctx, reg, windows):
     if reg is None or not windows:
         _check(_lib().ctu_flux_registers(ctx, None, None, 0), "ctu_flux_registers")
@@ -250,6 +268,12 @@ class Ctx:
 
     def flux_registers(self, reg, windows):
         ctu_flux_registers(self.h, reg, windows)
+
+    def autotune(self, U_in, U_out, stride, patches, d_dt_ch, stream=None):
+        ctu_autotune(self.h, U_in, U_out, stride, patches, d_dt_ch, stream)
+
+    def tile_params(self, n):
+        return ctu_tile_params(self.h, n)
 
     def fill_periodic(self, U, stride, patches, stream=None):
         ctu_fill_periodic(self.h, U, stride, patches, stream)

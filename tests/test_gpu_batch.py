@@ -202,3 +202,39 @@ def test_cuda_graph_replay_matches_direct_step():
     torch.cuda.synchronize()
     assert ctx.status_sync() == 0
     assert torch.equal(A, B)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotune_changes_only_the_launch_shape(prec):
+    """ctu_autotune picks a tile width and a segment length per patch shape of
+    an uneven batch; a step with the tuned tiles gives bitwise the result of
+    a context with the default tiles, the tuning steps leave the bound flux
+    registers untouched, and every choice is a valid one."""
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    H = W.amr_hierarchy(seed=4, base=32, target=50)
+    lv = H["levels"][2]
+    dev = _dev()
+    U = torch.from_numpy(lv["pool"]).to(dev)
+    stride = U.shape[1]
+    P = ctu.make_patches([(n, dx, b) for (n, dx, b, _) in lv["patches"]])
+    precision = ctu.CTU_FP64 if prec == 0 else ctu.CTU_MIXED
+    cfg = ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=precision, cfl=0.3)
+    ref, tuned = ctu.Ctx(cfg), ctu.Ctx(cfg)
+    d = torch.zeros(2, dtype=torch.float64, device=dev)
+    ref.dt(U, stride, P, d)
+    A, B, S = torch.zeros_like(U), torch.zeros_like(U), torch.zeros_like(U)
+    n0 = lv["patches"][0][0]
+    reg = torch.zeros(9 * n0[1] * n0[2], dtype=torch.float64, device=dev)
+    tuned.flux_registers(reg, [(0, 0, 0, 0, n0[1], 0, n0[2], 1.0, 0)])
+    tuned.autotune(U, S, stride, P, d)
+    assert torch.count_nonzero(reg) == 0
+    ref.step(U, A, stride, P, d)
+    tuned.step(U, B, stride, P, d)
+    assert ref.status_sync() == 0 and tuned.status_sync() == 0
+    assert torch.equal(A, B)
+    assert torch.count_nonzero(reg) > 0
+    for n in {tuple(p[0]) for p in lv["patches"]}:
+        xw, seg = tuned.tile_params(n)
+        assert xw in (8, 16, 32) and seg in (4, 8, 16, 32, 64)
+        assert ref.tile_params(n) == (32 if n[0] >= 24 else 16 if n[0] >= 12 else 8, 16)
