@@ -294,7 +294,7 @@ __device__ __forceinline__ unsigned int prim_any(const double (&U)[NV], const St
 {
     if (PHYS == PH_MHD) return prim_of<R>(U, a, V);
     double Vd[NV];
-    const unsigned int st = sr_prim64(U, a.gam, Vd);
+    const unsigned int st = sr_prim<R>(U, a.gam, Vd);
 #pragma unroll
     for (int q = 0; q < NV; ++q) V[q] = (R)Vd[q];
     return st;
@@ -408,7 +408,7 @@ __device__ __forceinline__ unsigned int sr_interface(const R (&W)[NV], const R (
     const double W0 = ((double)W[0] + a.gam * a.igm * (double)W[4]) * rcp64(1.0 - v2);
 #pragma unroll
     for (int q = 0; q < NV; ++q) U[q] += (double)T[q];
-    const unsigned int st = sr_prim64(U, a.gam, V, W0);
+    const unsigned int st = sr_prim<R>(U, a.gam, V, W0);
 #pragma unroll
     for (int q = 0; q < NV; ++q) out[q] = (R)V[q];
     return st;

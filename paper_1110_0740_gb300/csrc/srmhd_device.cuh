@@ -11,11 +11,46 @@
 // B, psi), sweeps use the same local frame as the MHD path.
 #pragma once
 
+#include "df.cuh"
 #include "mhd_device.cuh"
 
 namespace ctu {
 
 enum : unsigned int { ST_REC = 4u, ST_SUPER = 8u };
+
+// 1/x and 1/sqrt(x) in float64 for positive normal x inside the float
+// exponent range: a float32 seed refined by two Newton-Raphson steps
+// (r <- r (2 - x r); y <- y (3 - x y^2)/2), each doubling the number of
+// correct bits (2^-22 -> 2^-44 -> beyond double precision), so the result is
+// within about one ulp; far cheaper on GB300's FP64 pipe than the IEEE
+// float64 divide and square root.  The seed moves between float64 and
+// float32 by integer operations (df.cuh), not on the FP64 pipe.
+__device__ __forceinline__ double rcp64(double x)
+{
+    double r = f2d_int(1.0f / df_split(x).hi);
+    r = r * fma(-x, r, 2.0);
+    r = r * fma(-x, r, 2.0);
+    return r;
+}
+
+__device__ __forceinline__ double rsqrt64(double x)
+{
+    double y = f2d_int(rsqrtf(df_split(x).hi));
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    return y;
+}
+
+// 1/x, 1/sqrt(x) and sqrt(x) (x >= 0) of the working precision: hardware
+// float32 forms, or the float64 refinements above.
+template <class T> __device__ __forceinline__ T rcp_t(T x);
+template <> __device__ __forceinline__ float rcp_t<float>(float x) { return 1.0f / x; }
+template <> __device__ __forceinline__ double rcp_t<double>(double x) { return rcp64(x); }
+template <class T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt64(x); }
+template <class T> __device__ __forceinline__ T sqrt_t(T x) { return x > T(0) ? x * rsqrt_t<T>(x) : T(0); }
+template <> __device__ __forceinline__ float sqrt_t<float>(float x) { return sqrtf(x); }
 
 // U(V) in precision T (T = double for states that feed a recovery).
 template <class T, class R>
@@ -24,12 +59,12 @@ __device__ __forceinline__ void sr_cons(const R (&V)[NV], T gam, T (&U)[NV])
     const T rho = V[0], vx = V[1], vy = V[2], vz = V[3], p = V[4];
     const T bx = V[5], by = V[6], bz = V[7];
     const T v2 = vx * vx + vy * vy + vz * vz;
-    const T lor2 = T(1) / (T(1) - v2);
-    const T W = (rho + gam / (gam - T(1)) * p) * lor2;
+    const T lor2 = rcp_t<T>(T(1) - v2);
+    const T W = (rho + gam * rcp_t<T>(gam - T(1)) * p) * lor2;
     const T B2 = bx * bx + by * by + bz * bz;
     const T vB = vx * bx + vy * by + vz * bz;
     const T E2 = B2 * v2 - vB * vB;
-    U[0] = rho * sqrt(lor2);
+    U[0] = rho * rsqrt_t<T>(T(1) - v2);
     U[1] = (W + B2) * vx - vB * bx;
     U[2] = (W + B2) * vy - vB * by;
     U[3] = (W + B2) * vz - vB * bz;
@@ -40,34 +75,14 @@ __device__ __forceinline__ void sr_cons(const R (&V)[NV], T gam, T (&U)[NV])
     U[8] = V[8];
 }
 
-// 1/x and 1/sqrt(x) in float64 for positive normal x inside the float
-// exponent range: a float32 seed refined by two Newton-Raphson steps
-// (r <- r (2 - x r); y <- y (3 - x y^2)/2), each doubling the number of
-// correct bits (2^-23 -> 2^-46 -> beyond double precision), so the result is
-// within about one ulp; far cheaper on GB300's FP64 pipe than the IEEE
-// float64 divide and square root.
-__device__ __forceinline__ double rcp64(double x)
-{
-    double r = (double)(1.0f / (float)x);
-    r = r * fma(-x, r, 2.0);
-    r = r * fma(-x, r, 2.0);
-    return r;
-}
-
-__device__ __forceinline__ double rsqrt64(double x)
-{
-    double y = (double)rsqrtf((float)x);
-    y = y * fma(-0.5 * x, y * y, 1.5);
-    y = y * fma(-0.5 * x, y * y, 1.5);
-    return y;
-}
-
 // f(W) and f'(W) of the energy equation at fixed D, |m|^2, S = m.B, B^2,
 // tau = E + D: f = W - p + B^2 (1 + v^2)/2 - S^2/(2 W^2) - tau with
 // v^2(W) = (m^2 W^2 + S^2 (2W + B^2)) / (W^2 (W + B^2)^2),
 // p = (Gamma-1)/Gamma (W (1 - v^2) - D sqrt(1 - v^2)).  false if v^2 >= 1.
-__device__ __forceinline__ bool sr_energy(double W, double D, double m2, double S2, double B2, double tau,
-                                          double g1, double &f, double &df, double &v2, double &p)
+// The same with dv^2/dW and dp/dW.
+__device__ __forceinline__ bool sr_energy_d(double W, double D, double m2, double S2, double B2, double tau,
+                                            double g1, double &f, double &df, double &v2, double &p, double &dv2,
+                                            double &dp)
 {
     const double Wb = W + B2;
     const double N = m2 * W * W + S2 * (2.0 * W + B2);
@@ -77,15 +92,68 @@ __device__ __forceinline__ bool sr_energy(double W, double D, double m2, double 
     if (!(v2 < 1.0)) return false;
     const double dN = 2.0 * m2 * W + 2.0 * S2;
     const double dDn = 2.0 * W * Wb * (2.0 * W + B2);
-    const double dv2 = (dN * Dn - N * dDn) * iDn * iDn;
+    dv2 = (dN * Dn - N * dDn) * iDn * iDn;
     const double is = rsqrt64(1.0 - v2);  // gamma
     const double s = (1.0 - v2) * is;
     p = g1 * (W * (1.0 - v2) - D * s);
-    const double dp = g1 * ((1.0 - v2) + dv2 * (0.5 * D * is - W));
+    dp = g1 * ((1.0 - v2) + dv2 * (0.5 * D * is - W));
     const double iW = rcp64(W);
     f = W - p + 0.5 * B2 * (1.0 + v2) - 0.5 * S2 * iW * iW - tau;
     df = 1.0 - dp + 0.5 * B2 * dv2 + S2 * iW * iW * iW;
     return true;
+}
+
+
+__device__ __forceinline__ bool sr_energy(double W, double D, double m2, double S2, double B2, double tau,
+                                          double g1, double &f, double &df, double &v2, double &p)
+{
+    double dv2, dp;
+    return sr_energy_d(W, D, m2, S2, B2, tau, g1, f, df, v2, p, dv2, dp);
+}
+
+// f(W) and f'(W) in float32: the first stage of the mixed-path recovery.
+__device__ __forceinline__ bool sr_energy_f(float W, float D, float m2, float S2, float B2, float tau, float g1,
+                                            float &f, float &df)
+{
+    const float Wb = W + B2;
+    const float N = m2 * W * W + S2 * (2.0f * W + B2);
+    const float Dn = W * W * Wb * Wb;
+    const float iDn = 1.0f / Dn;
+    const float v2 = N * iDn;
+    if (!(v2 < 1.0f)) return false;
+    const float dN = 2.0f * m2 * W + 2.0f * S2;
+    const float dDn = 2.0f * W * Wb * (2.0f * W + B2);
+    const float dv2 = (dN * Dn - N * dDn) * iDn * iDn;
+    const float is = rsqrtf(1.0f - v2);
+    const float sq = (1.0f - v2) * is;
+    const float p = g1 * (W * (1.0f - v2) - D * sq);
+    const float dp = g1 * ((1.0f - v2) + dv2 * (0.5f * D * is - W));
+    const float iW = 1.0f / W;
+    f = W - p + 0.5f * B2 * (1.0f + v2) - 0.5f * S2 * iW * iW - tau;
+    df = 1.0f - dp + 0.5f * B2 * dv2 + S2 * iW * iW * iW;
+    return true;
+}
+
+// V from the converged W (with v^2 and p at W): v = (m + (S/W) B)/(W + B^2),
+// rho = D sqrt(1 - v^2), B and psi as in U.  Returns the status bits.
+__device__ __forceinline__ unsigned int sr_prim_tail(const double (&U)[NV], double W, double v2, double p, double S,
+                                                     double B2, double D, bool conv, bool phys, double (&V)[NV])
+{
+    V[5] = U[5];
+    V[6] = U[6];
+    V[7] = U[7];
+    V[8] = U[8];
+    const double iWB = rcp64(W + B2), SW = S * rcp64(W);
+    V[1] = (U[1] + SW * U[5]) * iWB;
+    V[2] = (U[2] + SW * U[6]) * iWB;
+    V[3] = (U[3] + SW * U[7]) * iWB;
+    V[0] = phys ? D * ((1.0 - v2) * rsqrt64(1.0 - v2)) : D;
+    V[4] = p;
+    unsigned int st = 0;
+    if (!conv) st |= ST_REC;
+    if (!phys) st |= ST_SUPER;
+    if (!(V[0] > 0.0) || !(p > 0.0)) st |= 1u;
+    return st;
 }
 
 // V(U) in float64.  With a guess W0 > 0 (the W of a nearby state) plain
@@ -103,7 +171,7 @@ __device__ __forceinline__ unsigned int sr_prim64(const double (&U)[NV], double 
     const double B2 = U[5] * U[5] + U[6] * U[6] + U[7] * U[7];
     const double S = U[1] * U[5] + U[2] * U[6] + U[3] * U[7];
     const double S2 = S * S;
-    const double g1 = (gam - 1.0) / gam;
+    const double g1 = (gam - 1.0) * rcp64(gam);
     V[5] = U[5]; V[6] = U[6]; V[7] = U[7]; V[8] = U[8];
     if (!(D > 0.0) || !(tau > 0.0)) {
         V[0] = D; V[1] = V[2] = V[3] = 0.0; V[4] = 0.0;
@@ -154,17 +222,73 @@ __device__ __forceinline__ unsigned int sr_prim64(const double (&U)[NV], double 
         W = Wn;
     }
     const bool phys = sr_energy(W, D, m2, S2, B2, tau, g1, f, df, v2, p);
-    const double iWB = rcp64(W + B2), SW = S * rcp64(W);
-    V[1] = (U[1] + SW * U[5]) * iWB;
-    V[2] = (U[2] + SW * U[6]) * iWB;
-    V[3] = (U[3] + SW * U[7]) * iWB;
-    V[0] = phys ? D * ((1.0 - v2) * rsqrt64(1.0 - v2)) : D;
-    V[4] = p;
-    unsigned int st = 0;
-    if (!conv) st |= ST_REC;
-    if (!phys) st |= ST_SUPER;
-    if (!(V[0] > 0.0) || !(p > 0.0)) st |= 1u;
-    return st;
+    return sr_prim_tail(U, W, v2, p, S, B2, D, conv, phys, V);
+}
+
+// V(U) for the mixed path.  Newton steps in float32 from the guess W0 (else
+// tau - B^2/2) bring W near float accuracy on the FP32 pipe; then float64
+// Newton steps on the float64 energy equation follow (at most three), each
+// squaring the relative error: once a step moves W by at most 1e-5 W the
+// error left is of order 1e-10 relative, below the float32 rounding of the
+// mixed path's fluxes.  v^2 and p are carried from that evaluation to the
+// final W by their first-order Taylor terms (remainder of the order of the
+// step squared).  A non-physical iterate, or no acceptance within the three
+// steps, hands over to the bracketed float64 iteration of sr_prim64.  Float64
+// inputs are rounded to float by integer operations (df_split).
+__device__ __forceinline__ unsigned int sr_prim_mixed(const double (&U)[NV], double gam, double (&V)[NV],
+                                                      double W0 = 0.0)
+{
+    const double D = U[0], tau = U[4] + U[0];
+    const double m2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
+    const double B2 = U[5] * U[5] + U[6] * U[6] + U[7] * U[7];
+    const double S = U[1] * U[5] + U[2] * U[6] + U[3] * U[7];
+    const double S2 = S * S;
+    const double g1 = (gam - 1.0) * rcp64(gam);
+    if (!(D > 0.0) || !(tau > 0.0)) return sr_prim64(U, gam, V, W0);
+    auto tof = [](double x) {
+        const df h = df_split(x);
+        return h.hi + h.lo;
+    };
+    const float Df = tof(D), tauf = tof(tau), m2f = tof(m2), B2f = tof(B2), S2f = tof(S2), g1f = tof(g1);
+    if (!(W0 > 0.0)) W0 = tau - 0.5 * B2;
+    if (!(W0 > 0.0)) return sr_prim64(U, gam, V, 0.0);
+    float Wf = tof(W0);
+    for (int it = 0; it < 12; ++it) {
+        float f, dfw;
+        if (!sr_energy_f(Wf, Df, m2f, S2f, B2f, tauf, g1f, f, dfw)) return sr_prim64(U, gam, V, W0);
+        const float Wn = Wf - f / dfw;
+        if (!(Wn > 0.0f)) return sr_prim64(U, gam, V, W0);
+        const bool done = fabsf(Wn - Wf) <= 2.0e-6f * Wf;
+        Wf = Wn;
+        if (done) break;
+    }
+    double W = f2d_int(Wf);
+    for (int it = 0; it < 3; ++it) {
+        double f, dfw, v2, p, dv2, dp;
+        if (!sr_energy_d(W, D, m2, S2, B2, tau, g1, f, dfw, v2, p, dv2, dp)) break;
+        const double dW = -f * rcp64(dfw);
+        const double Wn = W + dW;
+        if (!(Wn > 0.0)) break;
+        if (fabs(dW) <= 1.0e-5 * W) {
+            v2 += dv2 * dW;
+            p += dp * dW;
+            if (!(v2 < 1.0)) break;
+            return sr_prim_tail(U, Wn, v2, p, S, B2, D, true, true, V);
+        }
+        W = Wn;
+    }
+    return sr_prim64(U, gam, V, W);
+}
+
+// The recovery of the working precision: float64 throughout for R = double,
+// the mixed recovery for R = float.
+template <class R> __device__ __forceinline__ unsigned int sr_prim(const double (&U)[NV], double gam, double (&V)[NV],
+                                                                   double W0 = 0.0)
+{
+    if constexpr (sizeof(R) == 4)
+        return sr_prim_mixed(U, gam, V, W0);
+    else
+        return sr_prim64(U, gam, V, W0);
 }
 
 // Lower / upper signal speeds along the local normal (V[1] = v_n).
@@ -175,16 +299,16 @@ __device__ __forceinline__ void sr_speeds(const R (&V)[NV], R gam, R &lm, R &lp)
     const R v2 = V[1] * V[1] + V[2] * V[2] + V[3] * V[3];
     const R B2 = V[5] * V[5] + V[6] * V[6] + V[7] * V[7];
     const R vB = V[1] * V[5] + V[2] * V[6] + V[3] * V[7];
-    const R rh = V[0] + gam / (gam - R(1)) * V[4];
+    const R rh = V[0] + gam * rcp_t<R>(gam - R(1)) * V[4];
     const R cs2 = gam * V[4] / rh;
     const R b2 = B2 * (R(1) - v2) + vB * vB;
-    const R ca2 = b2 / (rh + b2);
+    const R ca2 = b2 * rcp_t<R>(rh + b2);
     const R a2 = cs2 + ca2 - cs2 * ca2;
     const R den = R(1) - v2 * a2;
     R disc = a2 * (R(1) - v2) * (R(1) - v2 * a2 - vn * vn * (R(1) - a2));
     disc = fmax(disc, R(0));
-    const R sq = sqrt(disc);
-    const R id = R(1) / den;
+    const R sq = sqrt_t<R>(disc);
+    const R id = rcp_t<R>(den);
     lm = (vn * (R(1) - a2) - sq) * id;
     lp = (vn * (R(1) - a2) + sq) * id;
 }
@@ -197,7 +321,7 @@ __device__ __forceinline__ void sr_flux(const R (&V)[NV], const R (&U)[NV], R ga
     const R vx = V[1], vy = V[2], vz = V[3], p = V[4];
     const R bx = V[5], by = V[6], bz = V[7];
     const R v2 = vx * vx + vy * vy + vz * vz;
-    const R W = (V[0] + gam / (gam - R(1)) * p) / (R(1) - v2);
+    const R W = (V[0] + gam * rcp_t<R>(gam - R(1)) * p) * rcp_t<R>(R(1) - v2);
     const R ex = -(vy * bz - vz * by), ey = -(vz * bx - vx * bz), ez = -(vx * by - vy * bx);
     const R pt = p + R(0.5) * (bx * bx + by * by + bz * bz + ex * ex + ey * ey + ez * ez);
     F[0] = U[0] * vx;
@@ -218,7 +342,7 @@ __device__ __forceinline__ void riemann_hll_sr(const R (&L0)[NV], const R (&R0)[
     R L[NV], Rt[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) { L[q] = L0[q]; Rt[q] = R0[q]; }
-    const R Bm = R(0.5) * (L[5] + Rt[5]) - R(0.5) * (Rt[8] - L[8]) / ch;
+    const R Bm = R(0.5) * (L[5] + Rt[5]) - R(0.5) * (Rt[8] - L[8]) * rcp_t<R>(ch);
     const R pm = R(0.5) * (L[8] + Rt[8]) - R(0.5) * ch * (Rt[5] - L[5]);
     L[5] = Bm;
     Rt[5] = Bm;
@@ -238,7 +362,7 @@ __device__ __forceinline__ void riemann_hll_sr(const R (&L0)[NV], const R (&R0)[
 #pragma unroll
         for (int q = 0; q < NV; ++q) F[q] = FR[q];
     } else {
-        const R is = R(1) / (SR - SL);
+        const R is = rcp_t<R>(SR - SL);
 #pragma unroll
         for (int q = 0; q < NV; ++q) F[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) * is;
     }
@@ -273,8 +397,8 @@ __device__ __forceinline__ unsigned int sr_mh_predict(const R (&vm1)[NV], const 
     for (int q = 0; q < NV; ++q) Us[q] = U0[q] - (double)(h * (Fp[q] - Fm[q]));
     // Newton starts from the cell-centre W = w gamma^2 (U* is an O(dt) update of U_i)
     const double v2c = (double)v0[1] * v0[1] + (double)v0[2] * v0[2] + (double)v0[3] * v0[3];
-    const double Wc = ((double)v0[0] + gamd / (gamd - 1.0) * (double)v0[4]) * rcp64(1.0 - v2c);
-    const unsigned int st = sr_prim64(Us, gamd, Vs, Wc);
+    const double Wc = ((double)v0[0] + gamd * rcp64(gamd - 1.0) * (double)v0[4]) * rcp64(1.0 - v2c);
+    const unsigned int st = sr_prim<R>(Us, gamd, Vs, Wc);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         Vp[q] = (R)Vs[q] + R(0.5) * dV[q];
