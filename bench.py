@@ -314,6 +314,8 @@ def run_ours(args):
     roof["hbm_step"] = {"algorithmic_bytes": nbytes, "achieved_gbs": hbm_achieved,
                         "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
                         "peak_source": f"{src} hbm_gbs"}
+    if mixed:
+        roof["precision_split"] = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
 
     # end-to-end through the public API with host buffers
     e2e = None
@@ -615,6 +617,31 @@ def kernel_flops(n):
     return {"prim": c.get("prim", 0.0) * cells, "flux1": 3 * c.get("flux1_per_direction", 0.0) * cells,
             "sweep_z": sweep * cells, "sweep_y": sweep * cells,
             "sweep_x": (sweep + c.get("update", 0.0) + c.get("next_dt", 0.0)) * cells}
+
+
+def precision_split_roofline(n, cells_per_s, hbm_gbs):
+    """Whole-step roofline of the mixed path with the method's work split by
+    the precision it is designated: the float64 work is the pressure
+    recoveries (cell centres, six interface states, the next-step speed),
+    the six interface prim->cons conversions and the update; the rest is
+    float32 (oracle counts, profiles/flops_per_cell.txt).  The bound is the
+    slowest of FP32 flops / FP32 peak, FP64 flops / FP64 peak and the
+    algorithmic bytes / measured HBM bandwidth, in cell updates per second.
+    This implementation runs the float64-designated recoveries in
+    double-float arithmetic on the FP32 pipe, so it is not held to the FP64
+    term; the fraction is reported beside the kernel roofline."""
+    c = {k: float(v) for k, v in _profile_numbers("flops_per_cell.txt").items()}
+    total = c.get("step_total_ppm", 0.0)
+    f64 = (8 * c.get("cons2prim", 0.0) + 6 * c.get("prim2cons", 0.0) + c.get("update", 0.0))
+    f32 = total - f64
+    bpc = algorithmic_bytes(n) / float(n) ** 3
+    bounds = {"fp32": FP32_PEAK / f32 if f32 > 0 else float("inf"),
+              "fp64": FP64_PEAK / f64 if f64 > 0 else float("inf"),
+              "hbm": hbm_gbs * 1e9 / bpc}
+    binding = min(bounds, key=bounds.get)
+    return {"fp32_flops_per_cell": f32, "fp64_flops_per_cell": f64, "bytes_per_cell": bpc,
+            "bounds_cells_per_s": bounds, "binding": binding, "achieved_cells_per_s": cells_per_s,
+            "frac": cells_per_s / bounds[binding]}
 
 
 def kernel_source_hash():
