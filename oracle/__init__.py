@@ -3,7 +3,9 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The CUDA path never does, and nothing
 here imports the CUDA path: the two share no code.  The arithmetic lives in
-``ctu_oracle.c`` (the scheme of Mignone et al., Sections 3-4) and
+``ctu_oracle.c`` (the scheme of Mignone et al., Sections 3-4),
+``srmhd_oracle.c`` (its relativistic counterpart), ``amr_oracle.c`` (the
+level operators of Section 4: prolongation, restriction, reflux) and
 ``exact_euler.c`` (the exact Euler Riemann solution used to pin it); this
 module only compiles them with ``gcc -O2 -ffp-contract=off`` and marshals
 numpy arrays through ctypes.
@@ -23,7 +25,7 @@ import numpy as np
 
 HERE = Path(__file__).resolve().parent
 LIB_PATH = HERE / "liboracle.so"
-SOURCES = ["ctu_oracle.c", "exact_euler.c", "srmhd_oracle.c"]
+SOURCES = ["ctu_oracle.c", "exact_euler.c", "srmhd_oracle.c", "amr_oracle.c"]
 NG = 4
 NVAR = 9
 
@@ -90,8 +92,58 @@ def lib():
             L.or_srmhd_riemann.argtypes = [P, P, D, D, P]
             L.or_srmhd_mh_predict.restype = I
             L.or_srmhd_mh_predict.argtypes = [P, P, D, D, D, P, P]
+        I3 = ctypes.POINTER(ctypes.c_int)
+        L.or_prolong.restype = None
+        L.or_prolong.argtypes = [P, P, I3, D, P, I3, I3, I3, I3, I, I]
+        L.or_restrict.restype = None
+        L.or_restrict.argtypes = [P, I3, P, I3, I3, I3, I3, I, I]
+        L.or_reflux.restype = None
+        L.or_reflux.argtypes = [P, I3, P, P, I, I, I, I, I, I, I, ctypes.c_long, ctypes.c_long,
+                                I, I, I, I, I, I]
         _lib = L
     return _lib
+
+
+def _i3(v):
+    return (ctypes.c_int * 3)(*[int(x) for x in v])
+
+
+# ---------------------------------------------------------------- level operators
+
+def prolong(Uc_old, Uc_new, nc, alpha, Uf, nf, lo, hi, origin, ratio, ndim):
+    """Eq. (prolong) + (intalpha): fill the fine cells [lo, hi) of Uf (in place)
+    from the coarse patch at U* = (1 - alpha) Uc_old + alpha Uc_new; fine cell
+    x lies in coarse cell origin + floor(x / ratio)."""
+    Uco = np.ascontiguousarray(Uc_old, dtype=np.float64)
+    Ucn = np.ascontiguousarray(Uc_new, dtype=np.float64)
+    assert Uco.shape == shape(nc, ndim) and Ucn.shape == Uco.shape and Uf.shape == shape(nf, ndim)
+    assert Uf.flags.c_contiguous and Uf.dtype == np.float64
+    lib().or_prolong(_dp(Uco), _dp(Ucn), _i3(nc), float(alpha), _dp(Uf), _i3(nf), _i3(lo), _i3(hi),
+                     _i3(origin), int(ratio), int(ndim))
+    return Uf
+
+
+def restrict(Uc, nc, Uf, nf, lo, hi, origin, ratio, ndim):
+    """Eq. (avgdown): coarse cells [lo, hi) of Uc (in place) become the mean of
+    their ratio^ndim fine cells (c - origin) * ratio + k."""
+    Ufc = np.ascontiguousarray(Uf, dtype=np.float64)
+    assert Uc.shape == shape(nc, ndim) and Ufc.shape == shape(nf, ndim)
+    assert Uc.flags.c_contiguous and Uc.dtype == np.float64
+    lib().or_restrict(_dp(Uc), _i3(nc), _dp(Ufc), _i3(nf), _i3(lo), _i3(hi), _i3(origin), int(ratio),
+                      int(ndim))
+    return Uc
+
+
+def reflux(Uc, nc, dxc, reg, dir, plane, side, a0, a1, b0, b1, creg, freg, fa0, fb0, fna, fnb, ratio, ndim):
+    """Eq. (fluxcorr) + (addreflux) on the coarse faces [a0, a1) x [b0, b1) of
+    plane `plane` normal to `dir` (in place); see amr_oracle.c."""
+    regc = np.ascontiguousarray(reg, dtype=np.float64)
+    assert Uc.shape == shape(nc, ndim) and Uc.flags.c_contiguous
+    dx = list(dxc) + [1.0] * (3 - len(dxc))
+    lib().or_reflux(_dp(Uc), _i3(nc), (ctypes.c_double * 3)(*dx), _dp(regc), int(dir), int(plane), int(side),
+                    int(a0), int(a1), int(b0), int(b1), int(creg), int(freg), int(fa0), int(fb0), int(fna),
+                    int(fnb), int(ratio), int(ndim))
+    return Uc
 
 
 # ---------------------------------------------------------------- geometry

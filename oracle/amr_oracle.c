@@ -1,0 +1,157 @@
+/* amr_oracle.c -- plain FP64 CPU oracle of the level operators around the
+ * CTU step (test infrastructure): coarse-to-fine prolongation with time
+ * interpolation, Eq. (prolong) and Eq. (intalpha); restriction, Eq.
+ * (avgdown); reflux, Eq. (fluxcorr) and Eq. (addreflux) of Mignone et al.
+ * (2012), Section 4.  Cartesian geometry: the volume coordinate of a
+ * direction is the coordinate itself and a cell's volume the product of its
+ * widths.
+ *
+ * Arrays: one patch is float64 [9][N2][N1][N0] with N = n + 2 g, g = 4 on
+ * active dimensions (d < ndim) and 0 otherwise; "interior" coordinates run
+ * over [0, n) and may reach -g .. n + g - 1 in the ghosts.
+ */
+#include <math.h>
+#include <stddef.h>
+
+#define NV 9
+#define NG 4
+
+static long cell(const int n[3], int ndim, int x, int y, int z)
+{
+    const int g0 = NG, g1 = ndim > 1 ? NG : 0, g2 = ndim > 2 ? NG : 0;
+    const long N0 = n[0] + 2 * g0, N1 = n[1] + 2 * g1;
+    return ((long)(z + g2) * N1 + (y + g1)) * N0 + (x + g0);
+}
+
+static long cells(const int n[3], int ndim)
+{
+    long c = 1;
+    for (int d = 0; d < 3; ++d) c *= n[d] + (d < ndim ? 2 * NG : 0);
+    return c;
+}
+
+/* MinMod and the monotonised-central slope, Eq. (minmod) and Eq. (MClim). */
+static double minmod(double a, double b)
+{
+    if (a > 0.0 && b > 0.0) return a < b ? a : b;
+    if (a < 0.0 && b < 0.0) return a > b ? a : b;
+    return 0.0;
+}
+
+static double mc(double dm, double dp) { return minmod(0.5 * (dm + dp), 2.0 * minmod(dm, dp)); }
+
+/* floor(a / b) for b > 0 */
+static int fdiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+/* Eq. (prolong) with Eq. (intalpha): every fine cell x in the box [lo, hi)
+ * of the fine patch takes U* of its coarse cell c = origin + floor(x / r)
+ * plus, along each active dimension, (xi_fine - xi_coarse) / (xi_+ - xi_-)
+ * times the MC-limited central difference of U* there, with
+ * U* = (1 - alpha) Uold + alpha Unew.  For a Cartesian cell of width h the
+ * weight is ((x mod r) + 1/2) / r - 1/2. */
+void or_prolong(const double *Uco, const double *Ucn, const int nc[3], double alpha, double *Uf, const int nf[3],
+                const int lo[3], const int hi[3], const int origin[3], int r, int ndim)
+{
+    const long Sc = cells(nc, ndim), Sf = cells(nf, ndim);
+    for (int z = lo[2]; z < hi[2]; ++z)
+        for (int y = lo[1]; y < hi[1]; ++y)
+            for (int x = lo[0]; x < hi[0]; ++x) {
+                const int xf[3] = {x, y, z};
+                int c[3];
+                double w[3];
+                for (int d = 0; d < 3; ++d) {
+                    if (d < ndim) {
+                        c[d] = origin[d] + fdiv(xf[d], r);
+                        const int m = xf[d] - r * fdiv(xf[d], r);
+                        w[d] = (m + 0.5) / r - 0.5;
+                    } else {
+                        c[d] = 0;
+                        w[d] = 0.0;
+                    }
+                }
+                const long fi = cell(nf, ndim, x, y, z);
+                for (int q = 0; q < NV; ++q) {
+                    const long c0 = cell(nc, ndim, c[0], c[1], c[2]);
+                    const double u0 = (1.0 - alpha) * Uco[q * Sc + c0] + alpha * Ucn[q * Sc + c0];
+                    double u = u0;
+                    for (int d = 0; d < ndim; ++d) {
+                        int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
+                        cm[d] -= 1;
+                        cp[d] += 1;
+                        const long im = cell(nc, ndim, cm[0], cm[1], cm[2]);
+                        const long ip = cell(nc, ndim, cp[0], cp[1], cp[2]);
+                        const double um = (1.0 - alpha) * Uco[q * Sc + im] + alpha * Ucn[q * Sc + im];
+                        const double up = (1.0 - alpha) * Uco[q * Sc + ip] + alpha * Ucn[q * Sc + ip];
+                        u += w[d] * mc(u0 - um, up - u0);
+                    }
+                    Uf[q * Sf + fi] = u;
+                }
+            }
+}
+
+/* Eq. (avgdown): every coarse cell c in the box [lo, hi) becomes the volume
+ * average of its r^ndim fine cells f = (c - origin) r + k, 0 <= k < r. */
+void or_restrict(double *Uc, const int nc[3], const double *Uf, const int nf[3], const int lo[3], const int hi[3],
+                 const int origin[3], int r, int ndim)
+{
+    const long Sc = cells(nc, ndim), Sf = cells(nf, ndim);
+    const int k1 = ndim > 1 ? r : 1, k2 = ndim > 2 ? r : 1;
+    double nk = r;
+    if (ndim > 1) nk *= r;
+    if (ndim > 2) nk *= r;
+    for (int z = lo[2]; z < hi[2]; ++z)
+        for (int y = lo[1]; y < hi[1]; ++y)
+            for (int x = lo[0]; x < hi[0]; ++x) {
+                const long ci = cell(nc, ndim, x, y, z);
+                for (int q = 0; q < NV; ++q) {
+                    double s = 0.0;
+                    for (int c2 = 0; c2 < k2; ++c2)
+                        for (int c1 = 0; c1 < k1; ++c1)
+                            for (int c0 = 0; c0 < r; ++c0) {
+                                const int fx = (x - origin[0]) * r + c0;
+                                const int fy = ndim > 1 ? (y - origin[1]) * r + c1 : 0;
+                                const int fz = ndim > 2 ? (z - origin[2]) * r + c2 : 0;
+                                s += Uf[q * Sf + cell(nf, ndim, fx, fy, fz)];
+                            }
+                    Uc[q * Sc + ci] = s / nk;
+                }
+            }
+}
+
+/* Eq. (fluxcorr) and Eq. (addreflux) for the coarse faces [a0, a1) x [b0, b1)
+ * of plane `plane` normal to `dir` (a, b: the two other dimensions in
+ * increasing order).  reg holds, per window [q][b][a], the sums a CTU step
+ * accumulates: the coarse window with weight -1 (-dt A F_coarse), the fine
+ * window with weight +1 (sum over substeps of dt_q A F_fine); the fine faces
+ * of coarse face (a, b) are a' = fa0 + (a - a0) r + i, b' = fb0 + (b - b0) r
+ * + j in a fine window of fna x fnb faces.  The coarse cell on the coarse
+ * side of the interface (cell `plane` for side = +1, whose lower face it is;
+ * cell `plane - 1` for side = -1) gains side x (coarse + fine sums) / volume. */
+void or_reflux(double *Uc, const int nc[3], const double dxc[3], const double *reg, int dir, int plane, int side,
+               int a0, int a1, int b0, int b1, long creg, long freg, int fa0, int fb0, int fna, int fnb, int r,
+               int ndim)
+{
+    const long Sc = cells(nc, ndim);
+    const int ea = dir == 0 ? 1 : 0, eb = dir == 2 ? 1 : 2;
+    const int rb = eb < ndim ? r : 1, ra = ea < ndim ? r : 1;
+    double vol = 1.0;
+    for (int d = 0; d < ndim; ++d) vol *= dxc[d];
+    const long na = a1 - a0, nb = b1 - b0;
+    for (int b = b0; b < b1; ++b)
+        for (int a = a0; a < a1; ++a) {
+            int c[3];
+            c[dir] = side > 0 ? plane : plane - 1;
+            c[ea] = a;
+            c[eb] = b;
+            const long ci = cell(nc, ndim, c[0], c[1], c[2]);
+            for (int q = 0; q < NV; ++q) {
+                double t = reg[creg + q * na * nb + (long)(b - b0) * na + (a - a0)];
+                for (int j = 0; j < rb; ++j)
+                    for (int i = 0; i < ra; ++i) {
+                        const long fa = fa0 + (long)(a - a0) * ra + i, fb = fb0 + (long)(b - b0) * rb + j;
+                        t += reg[freg + q * (long)fna * fnb + fb * fna + fa];
+                    }
+                Uc[q * Sc + ci] += side * t / vol;
+            }
+        }
+}
