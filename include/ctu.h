@@ -191,6 +191,74 @@ ctu_status ctu_autotune(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t
  * cells). */
 ctu_status ctu_tile_params(ctu_ctx *ctx, const int n[3], int *xw, int *seg);
 
+/* ---- Level operators (Section 4 of Mignone et al. 2012; Cartesian) ------
+ * The data-parallel operators that produce ctu_step's inputs on a finer
+ * level and consume its flux registers: prolongation of a coarse level into
+ * fine cells (ghost zones, or new patches), with the coarse solution
+ * interpolated in time between two coarse states (Eq. prolong, Eq. intalpha);
+ * restriction of a fine level onto the coarse cells it covers (Eq. avgdown);
+ * and the flux correction of coarse cells beside coarse-fine interfaces
+ * from the flux registers (Eq. fluxcorr, Eq. addreflux).  All arrays are the
+ * callers' float64 pools (same layout as ctu_step: [q * stride + cell], 4
+ * ghost cells per side on active dimensions, x fastest); the descriptor
+ * arrays are host arrays, copied to the device on the first call with new
+ * contents (that call synchronises the stream: make it before any capture;
+ * later calls with identical descriptors enqueue kernels only).  Returns
+ * CTU_EINVAL, on the host, for a descriptor that would reach outside a
+ * patch's ghosted region. */
+typedef struct {
+    int fn[3];        /* interior cells of the fine patch (1 on inactive dimensions) */
+    int cn[3];        /* interior cells of the coarse patch */
+    int64_t fbase;    /* pool offset of the fine patch's first ghosted cell */
+    int64_t cbase;    /* pool offset of the coarse patch's first ghosted cell */
+    int lo[3], hi[3]; /* box of cells, interior coordinates (ghosts: -4..-1, n..n+3):
+                         fine cells for ctu_prolong, coarse cells for ctu_restrict */
+    int origin[3];    /* coarse cell holding the fine patch's cell 0: fine cell x lies in
+                         coarse cell origin + floor(x / ratio) on every active dimension */
+    int ratio;        /* refinement ratio >= 1 */
+} ctu_level_box;
+
+/* Eq. (prolong) + Eq. (intalpha): every fine cell x of each box takes
+ * U* = (1 - alpha) Uc_old + alpha Uc_new of its coarse cell c, plus, along
+ * every active dimension d, (((x_d mod r) + 1/2) / r - 1/2) times the
+ * monotonised-central (Eq. MClim) central difference of U* at c.  The coarse
+ * cell and its neighbours along each active dimension must lie in the
+ * coarse patch's ghosted region.  Uc_old and Uc_new may be the same array. */
+ctu_status ctu_prolong(ctu_ctx *ctx, const double *Uc_old, const double *Uc_new, int64_t cstride,
+                       double alpha, double *Uf, int64_t fstride, const ctu_level_box *boxes,
+                       int nbox, void *stream);
+
+/* Eq. (avgdown): every coarse cell c of each box becomes the mean of its
+ * ratio^ndim fine cells (c - origin) * ratio + k, 0 <= k < ratio. */
+ctu_status ctu_restrict(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *Uf,
+                        int64_t fstride, const ctu_level_box *boxes, int nbox, void *stream);
+
+typedef struct {
+    int cn[3];            /* interior cells of the coarse patch */
+    int dir, plane, side; /* interface: plane `plane` normal to `dir`; side +1: the corrected
+                             coarse cell is `plane` (the interface is its lower face); side -1:
+                             the cell is plane - 1 (its upper face) */
+    int64_t cbase;        /* pool offset of the coarse patch's first ghosted cell */
+    double dx[3];         /* coarse cell widths (the cell volume is their product) */
+    int a0, a1, b0, b1;   /* coarse faces [a0, a1) x [b0, b1) in the two other dimensions,
+                             increasing order */
+    int64_t creg;         /* coarse window in reg, [q][b - b0][a - a0], bound with weight -1 */
+    int64_t freg;         /* fine window in reg, [q][fb][fa] of fna x fnb faces, weight +1 */
+    int fa0, fb0;         /* fine face of the set's first coarse face */
+    int fna, fnb;         /* extents of the fine window */
+    int ratio, pad;       /* refinement ratio; pad = 0 */
+} ctu_reflux_set;
+
+/* Eq. (fluxcorr) + Eq. (addreflux): after the steps of both levels, each
+ * coarse face of each set totals its coarse register sum and the sums of its
+ * ratio^(ndim-1) fine faces, and the coarse cell beside it gains side x
+ * total / volume.  With the registers bound as stated (coarse -1, fine +1)
+ * the total is dt (the space-time average fine flux minus the coarse flux)
+ * times the face area.  A cell beside several interfaces gets every
+ * correction (atomic float64 adds, so their order is not fixed). */
+ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *reg,
+                      const ctu_reflux_set *sets, int nset, void *stream);
+
 /* Fill the ghost cells of every patch with periodic copies of its own
  * interior (helper for periodic boxes; not part of the step). */
 ctu_status ctu_fill_periodic(ctu_ctx *ctx, double *U, int64_t stride,

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "ctu.h"
+#include "amr_ops.cuh"
 #include "ctu_launch.h"
 
 using namespace ctu;
@@ -110,6 +111,11 @@ struct ctu_ctx {
     // autotuned thread-tile width along x and marching segment per shape
     std::map<std::array<int, 3>, std::array<int, 2>> tune;
     bool tuning = false;  // steps of ctu_autotune leave the flux registers alone
+    // device copies of the level-operator descriptors (prolong, restrict,
+    // reflux), re-uploaded when a call brings different contents
+    std::vector<char> opcache[3];
+    void *optab[3] = {nullptr, nullptr, nullptr};
+    size_t opcap[3] = {0, 0, 0};
     int device = 0;
     // patch list cache (caller order) and its device table (grouped order)
     std::vector<ctu_patch> hpatch;
@@ -436,6 +442,8 @@ void ctu_destroy(ctu_ctx *ctx)
     if (ctx->dsp) cudaFree(ctx->dsp);
     if (ctx->dwin) cudaFree(ctx->dwin);
     if (ctx->dwstart) cudaFree(ctx->dwstart);
+    for (void *p : ctx->optab)
+        if (p) cudaFree(p);
     delete ctx->prof;
     delete ctx;
 }
@@ -578,6 +586,173 @@ ctu_status ctu_autotune(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+}
+
+// ---------------------------------------------------------------- level operators
+
+// Device copy of a descriptor array (kind 0 prolong, 1 restrict, 2 reflux),
+// uploaded only when its contents change.
+static ctu_status op_table(ctu_ctx *ctx, int kind, const void *h, size_t bytes, cudaStream_t s, const void **out)
+{
+    std::vector<char> &c = ctx->opcache[kind];
+    if (c.size() != bytes || std::memcmp(c.data(), h, bytes) != 0) {
+        if (bytes > ctx->opcap[kind]) {
+            CTU_CUDA(cudaStreamSynchronize(s));
+            if (ctx->optab[kind]) cudaFree(ctx->optab[kind]);
+            ctx->optab[kind] = nullptr;
+            ctx->opcap[kind] = 0;
+            CTU_CUDA(cudaMalloc(&ctx->optab[kind], bytes));
+            ctx->opcap[kind] = bytes;
+        }
+        CTU_CUDA(cudaMemcpyAsync(ctx->optab[kind], h, bytes, cudaMemcpyHostToDevice, s));
+        CTU_CUDA(cudaStreamSynchronize(s));
+        c.assign((const char *)h, (const char *)h + bytes);
+    }
+    *out = ctx->optab[kind];
+    return CTU_OK;
+}
+
+// Ghosted extent of a patch with n interior cells; false if n is invalid.
+static bool patch_extent(const ctu_ctx *ctx, const int n[3], long long *cells)
+{
+    long long c = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (d < ctx->cfg.ndim) {
+            if (n[d] < 1 || n[d] > (1 << 20)) return false;
+            c *= n[d] + 2 * AMR_NG;
+        } else if (n[d] != 1) {
+            return false;
+        }
+    }
+    *cells = c;
+    return true;
+}
+
+static int floordiv_h(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// A level box is valid: both patches inside their pools, the box inside the
+// output patch's ghosted region, and every cell it reads inside the input
+// patch's ghosted region (prolongation: the coarse cell and its neighbours
+// along active dimensions; restriction: all fine children).
+static bool box_ok(const ctu_ctx *ctx, const ctu_level_box &B, int64_t cstride, int64_t fstride, bool prolong,
+                   long long *cells)
+{
+    long long cc = 0, fc = 0;
+    if (!patch_extent(ctx, B.cn, &cc) || !patch_extent(ctx, B.fn, &fc) || B.ratio < 1) return false;
+    if (B.cbase < 0 || B.cbase + cc > cstride || B.fbase < 0 || B.fbase + fc > fstride) return false;
+    const int *out_n = prolong ? B.fn : B.cn;
+    long long cnt = 1;
+    for (int d = 0; d < 3; ++d) {
+        const bool act = d < ctx->cfg.ndim;
+        const int g = act ? AMR_NG : 0;
+        if (B.hi[d] < B.lo[d]) return false;
+        cnt *= B.hi[d] - B.lo[d];
+        if (B.hi[d] == B.lo[d]) continue;
+        if (!act) {
+            if (B.lo[d] != 0 || B.hi[d] != 1) return false;
+            continue;
+        }
+        if (B.lo[d] < -g || B.hi[d] > out_n[d] + g) return false;
+        if (prolong) {  // coarse cells origin + floor(x / r) and their neighbours
+            const int cmin = B.origin[d] + floordiv_h(B.lo[d], B.ratio) - 1;
+            const int cmax = B.origin[d] + floordiv_h(B.hi[d] - 1, B.ratio) + 1;
+            if (cmin < -g || cmax >= B.cn[d] + g) return false;
+        } else {  // fine children (c - origin) r + k
+            const long long fmin = (long long)(B.lo[d] - B.origin[d]) * B.ratio;
+            const long long fmax = (long long)(B.hi[d] - 1 - B.origin[d]) * B.ratio + B.ratio - 1;
+            if (fmin < -g || fmax >= B.fn[d] + g) return false;
+        }
+    }
+    *cells = cnt;
+    return true;
+}
+
+static unsigned amr_grid_x(long long maxcells)
+{
+    long long b = (maxcells + AMR_BLOCK - 1) / AMR_BLOCK;
+    if (b < 1) b = 1;
+    if (b > 4096) b = 4096;
+    return (unsigned)b;
+}
+
+ctu_status ctu_prolong(ctu_ctx *ctx, const double *Uc_old, const double *Uc_new, int64_t cstride, double alpha,
+                       double *Uf, int64_t fstride, const ctu_level_box *boxes, int nbox, void *stream)
+{
+    if (!ctx || !Uc_old || !Uc_new || !Uf || !boxes || nbox <= 0 || nbox > 65535 || !(alpha == alpha))
+        return CTU_EINVAL;
+    if (Uf == Uc_old || Uf == Uc_new) return CTU_EINVAL;
+    long long maxc = 0;
+    for (int i = 0; i < nbox; ++i) {
+        long long c = 0;
+        if (!box_ok(ctx, boxes[i], cstride, fstride, true, &c)) return CTU_EINVAL;
+        maxc = std::max(maxc, c);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *d = nullptr;
+    ctu_status st = op_table(ctx, 0, boxes, sizeof(ctu_level_box) * nbox, s, &d);
+    if (st != CTU_OK) return st;
+    if (maxc == 0) return CTU_OK;
+    k_prolong<<<dim3(amr_grid_x(maxc), (unsigned)nbox), AMR_BLOCK, 0, s>>>(
+        (const ctu_level_box *)d, ctx->cfg.ndim, Uc_old, Uc_new, cstride, alpha, Uf, fstride);
+    CTU_CUDA(cudaGetLastError());
+    return CTU_OK;
+}
+
+ctu_status ctu_restrict(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *Uf, int64_t fstride,
+                        const ctu_level_box *boxes, int nbox, void *stream)
+{
+    if (!ctx || !Uc || !Uf || !boxes || nbox <= 0 || nbox > 65535 || Uc == Uf) return CTU_EINVAL;
+    long long maxc = 0;
+    for (int i = 0; i < nbox; ++i) {
+        long long c = 0;
+        if (!box_ok(ctx, boxes[i], cstride, fstride, false, &c)) return CTU_EINVAL;
+        maxc = std::max(maxc, c);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *d = nullptr;
+    ctu_status st = op_table(ctx, 1, boxes, sizeof(ctu_level_box) * nbox, s, &d);
+    if (st != CTU_OK) return st;
+    if (maxc == 0) return CTU_OK;
+    k_restrict<<<dim3(amr_grid_x(maxc), (unsigned)nbox), AMR_BLOCK, 0, s>>>((const ctu_level_box *)d,
+                                                                             ctx->cfg.ndim, Uc, cstride, Uf,
+                                                                             fstride);
+    CTU_CUDA(cudaGetLastError());
+    return CTU_OK;
+}
+
+ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *reg, const ctu_reflux_set *sets,
+                      int nset, void *stream)
+{
+    if (!ctx || !Uc || !reg || !sets || nset <= 0 || nset > 65535) return CTU_EINVAL;
+    const int ndim = ctx->cfg.ndim;
+    long long maxc = 0;
+    for (int i = 0; i < nset; ++i) {
+        const ctu_reflux_set &S = sets[i];
+        long long cc = 0;
+        if (!patch_extent(ctx, S.cn, &cc) || S.cbase < 0 || S.cbase + cc > cstride) return CTU_EINVAL;
+        if (S.dir < 0 || S.dir >= ndim || (S.side != 1 && S.side != -1) || S.ratio < 1) return CTU_EINVAL;
+        const int cell = S.side > 0 ? S.plane : S.plane - 1;
+        if (cell < 0 || cell >= S.cn[S.dir]) return CTU_EINVAL;
+        const int ea = S.dir == 0 ? 1 : 0, eb = S.dir == 2 ? 1 : 2;
+        if (S.a0 < 0 || S.a1 < S.a0 || S.a1 > S.cn[ea] || S.b0 < 0 || S.b1 < S.b0 || S.b1 > S.cn[eb]) return CTU_EINVAL;
+        if (S.creg < 0 || S.freg < 0 || S.fa0 < 0 || S.fb0 < 0 || S.fna < 0 || S.fnb < 0) return CTU_EINVAL;
+        const long long ra = ea < ndim ? S.ratio : 1, rb = eb < ndim ? S.ratio : 1;
+        if (S.a1 > S.a0 && S.b1 > S.b0 &&
+            (S.fa0 + (S.a1 - S.a0) * ra > S.fna || S.fb0 + (S.b1 - S.b0) * rb > S.fnb))
+            return CTU_EINVAL;
+        for (int d = 0; d < ndim; ++d)
+            if (!(S.dx[d] > 0.0)) return CTU_EINVAL;
+        maxc = std::max(maxc, (long long)(S.a1 - S.a0) * (S.b1 - S.b0));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *d = nullptr;
+    ctu_status st = op_table(ctx, 2, sets, sizeof(ctu_reflux_set) * nset, s, &d);
+    if (st != CTU_OK) return st;
+    if (maxc == 0) return CTU_OK;
+    k_reflux<<<dim3(amr_grid_x(maxc), (unsigned)nset), AMR_BLOCK, 0, s>>>((const ctu_reflux_set *)d, ndim, Uc,
+                                                                           cstride, reg);
+    CTU_CUDA(cudaGetLastError());
+    return CTU_OK;
 }
 
 ctu_status ctu_tile_params(ctu_ctx *ctx, const int n[3], int *xw, int *seg)

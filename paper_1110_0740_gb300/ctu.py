@@ -46,6 +46,45 @@ class ctu_flux_window(ctypes.Structure):
                 ("dst", ctypes.c_int64)]
 
 
+class ctu_level_box(ctypes.Structure):
+    _fields_ = [("fn", ctypes.c_int32 * 3), ("cn", ctypes.c_int32 * 3), ("fbase", ctypes.c_int64),
+                ("cbase", ctypes.c_int64), ("lo", ctypes.c_int32 * 3), ("hi", ctypes.c_int32 * 3),
+                ("origin", ctypes.c_int32 * 3), ("ratio", ctypes.c_int32)]
+
+
+class ctu_reflux_set(ctypes.Structure):
+    _fields_ = [("cn", ctypes.c_int32 * 3), ("dir", ctypes.c_int32), ("plane", ctypes.c_int32),
+                ("side", ctypes.c_int32), ("cbase", ctypes.c_int64), ("dx", ctypes.c_double * 3),
+                ("a0", ctypes.c_int32), ("a1", ctypes.c_int32), ("b0", ctypes.c_int32),
+                ("b1", ctypes.c_int32), ("creg", ctypes.c_int64), ("freg", ctypes.c_int64),
+                ("fa0", ctypes.c_int32), ("fb0", ctypes.c_int32), ("fna", ctypes.c_int32),
+                ("fnb", ctypes.c_int32), ("ratio", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def make_level_boxes(boxes):
+    """boxes: iterables of dicts with keys fn, cn, fbase, cbase, lo, hi, origin, ratio."""
+    arr = (ctu_level_box * len(boxes))()
+    for i, b in enumerate(boxes):
+        for k in ("fn", "cn", "lo", "hi", "origin"):
+            getattr(arr[i], k)[:] = [int(v) for v in b[k]]
+        arr[i].fbase, arr[i].cbase, arr[i].ratio = int(b["fbase"]), int(b["cbase"]), int(b["ratio"])
+    return arr
+
+
+def make_reflux_sets(sets):
+    """sets: dicts with keys cn, dir, plane, side, cbase, dx, a0, a1, b0, b1, creg, freg, fa0, fb0,
+    fna, fnb, ratio."""
+    arr = (ctu_reflux_set * len(sets))()
+    for i, d in enumerate(sets):
+        arr[i].cn[:] = [int(v) for v in d["cn"]]
+        arr[i].dx[:] = [float(v) for v in (list(d["dx"]) + [1.0] * (3 - len(d["dx"])))]
+        for k in ("dir", "plane", "side", "cbase", "a0", "a1", "b0", "b1", "creg", "freg", "fa0", "fb0",
+                  "fna", "fnb", "ratio"):
+            setattr(arr[i], k, int(d[k]))
+        arr[i].pad = 0
+    return arr
+
+
 class CtuError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -95,6 +134,12 @@ def _lib():
         L.ctu_tile_params.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]
         L.ctu_tile_params.restype = i32
+        L.ctu_prolong.argtypes = [vp, vp, vp, i64, dbl, vp, i64, ctypes.POINTER(ctu_level_box), i32, vp]
+        L.ctu_prolong.restype = i32
+        L.ctu_restrict.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctu_level_box), i32, vp]
+        L.ctu_restrict.restype = i32
+        L.ctu_reflux.argtypes = [vp, vp, i64, vp, ctypes.POINTER(ctu_reflux_set), i32, vp]
+        L.ctu_reflux.restype = i32
         for f in ("ctu_init", "ctu_dt", "ctu_step", "ctu_flux_registers", "ctu_fill_periodic",
                   "ctu_status_sync", "ctu_last_launch_count"):
             getattr(L, f).restype = i32
@@ -193,6 +238,21 @@ def ctu_tile_params(ctx, n):
     return xw.value, seg.value
 
 
+def ctu_prolong(ctx, Uc_old, Uc_new, cstride, alpha, Uf, fstride, boxes, stream=None):
+    _check(_lib().ctu_prolong(ctx, _ptr(Uc_old), _ptr(Uc_new), int(cstride), float(alpha), _ptr(Uf),
+                              int(fstride), boxes, len(boxes), _stream(stream)), "ctu_prolong")
+
+
+def ctu_restrict(ctx, Uc, cstride, Uf, fstride, boxes, stream=None):
+    _check(_lib().ctu_restrict(ctx, _ptr(Uc), int(cstride), _ptr(Uf), int(fstride), boxes, len(boxes),
+                               _stream(stream)), "ctu_restrict")
+
+
+def ctu_reflux(ctx, Uc, cstride, reg, sets, stream=None):
+    _check(_lib().ctu_reflux(ctx, _ptr(Uc), int(cstride), _ptr(reg), sets, len(sets), _stream(stream)),
+           "ctu_reflux")
+
+
 def ctu_flux_registers(ctx, reg, windows):
     if reg is None or not windows:
         _check(_lib().ctu_flux_registers(ctx, None, None, 0), "ctu_flux_registers")
@@ -274,6 +334,15 @@ class Ctx:
 
     def tile_params(self, n):
         return ctu_tile_params(self.h, n)
+
+    def prolong(self, Uc_old, Uc_new, cstride, alpha, Uf, fstride, boxes, stream=None):
+        ctu_prolong(self.h, Uc_old, Uc_new, cstride, alpha, Uf, fstride, boxes, stream)
+
+    def restrict(self, Uc, cstride, Uf, fstride, boxes, stream=None):
+        ctu_restrict(self.h, Uc, cstride, Uf, fstride, boxes, stream)
+
+    def reflux(self, Uc, cstride, reg, sets, stream=None):
+        ctu_reflux(self.h, Uc, cstride, reg, sets, stream)
 
     def fill_periodic(self, U, stride, patches, stream=None):
         ctu_fill_periodic(self.h, U, stride, patches, stream)
