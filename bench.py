@@ -407,24 +407,31 @@ def run_amr(args):
     # coarse window is kept by the rank that owns its parent patch
     wins = [[] for _ in L]
     off = 0
+    fine_dst = [dict() for _ in L]      # (patch, dir, plane) -> register offset of a fine window
+    coarse_dst = [dict() for _ in L]    # (fine patch, dir, side) -> offset of its coarse window
+    reg_range = [None for _ in L]       # registers of the interface (lev - 1, lev)
     for lev in range(1, len(L)):
+        r0 = off
         for gi in mine[lev]:
             n = L[lev]["patches"][gi][0]
             for d in range(3):
                 a_, b_ = [e for e in range(3) if e != d]
                 for plane in (0, n[d]):
                     wins[lev].append((loc[lev][gi], d, plane, 0, n[a_], 0, n[b_], 1.0, off))
+                    fine_dst[lev][(gi, d, plane)] = off
                     off += 9 * n[a_] * n[b_]
-        for (parent, o_zyx, sz) in L[lev]["footprints"]:
+        for fi, (parent, o_zyx, sz) in enumerate(L[lev]["footprints"]):
             if parent not in loc[lev - 1]:
                 continue
             o = [o_zyx[2], o_zyx[1], o_zyx[0]]
             for d in range(3):
                 a_, b_ = [e for e in range(3) if e != d]
-                for plane in (o[d], o[d] + sz):
+                for side, plane in ((-1, o[d]), (+1, o[d] + sz)):
                     wins[lev - 1].append((loc[lev - 1][parent], d, plane, o[a_], o[a_] + sz, o[b_],
                                           o[b_] + sz, -1.0, off))
+                    coarse_dst[lev][(fi, d, side)] = off
                     off += 9 * sz * sz
+        reg_range[lev] = (r0, off)
     reg = torch.zeros(max(off, 1), dtype=torch.float64, device=dev)
     ctxs, A, B, P, D = [], [], [], [], []
     for lev, lv in enumerate(L):
@@ -462,13 +469,79 @@ def run_amr(args):
         if P[lev] is not None:
             ctxs[lev].step(src, dst, src.shape[1], P[lev], D[lev], stream=stream)
 
+    # level operators (Section 4), single rank: ghosts of every fine patch
+    # prolonged from its parent (time-interpolated) before each fine substep;
+    # at each synchronisation the parent level is refluxed, then restricted
+    # (reflux first, so that a correction landing on a covered coarse cell is
+    # overwritten by the restriction), and the interface registers zeroed
+    ops = None
+    if world == 1 and not args.no_level_ops:
+        ops = {}
+        for lev in range(1, len(L)):
+            pb, rb, fs = [], [], []
+            for fi, (n, dx, base, _) in enumerate(L[lev]["patches"]):
+                parent, o_zyx, sz = L[lev]["footprints"][fi]
+                cn, cdx, cbase, _ = L[lev - 1]["patches"][parent]
+                o = [o_zyx[2], o_zyx[1], o_zyx[0]]
+                for d in range(3):  # the six ghost slabs
+                    for lo_d, hi_d in ((-4, 0), (n[d], n[d] + 4)):
+                        lo_, hi_ = [], []
+                        for e in range(3):
+                            if e == d:
+                                lo_.append(lo_d)
+                                hi_.append(hi_d)
+                            elif e < d:
+                                lo_.append(0)
+                                hi_.append(n[e])
+                            else:
+                                lo_.append(-4)
+                                hi_.append(n[e] + 4)
+                        pb.append(dict(fn=n, cn=cn, fbase=base, cbase=cbase, lo=lo_, hi=hi_, origin=o, ratio=2))
+                rb.append(dict(fn=n, cn=cn, fbase=base, cbase=cbase, lo=o, hi=[o[e] + sz for e in range(3)],
+                               origin=o, ratio=2))
+                for d in range(3):
+                    a_, b_ = [e for e in range(3) if e != d]
+                    for side, fplane in ((-1, 0), (+1, n[d])):
+                        cell = o[d] - 1 if side < 0 else o[d] + sz
+                        if not 0 <= cell < cn[d]:
+                            continue  # the coarse neighbour lies in another coarse patch
+                        fs.append(dict(cn=cn, dir=d, plane=o[d] if side < 0 else o[d] + sz, side=side,
+                                       cbase=cbase, dx=cdx, a0=o[a_], a1=o[a_] + sz, b0=o[b_], b1=o[b_] + sz,
+                                       creg=coarse_dst[lev][(fi, d, side)],
+                                       freg=fine_dst[lev][(fi, d, fplane)], fa0=0, fb0=0, fna=n[a_],
+                                       fnb=n[b_], ratio=2))
+            ops[lev] = (ctu.make_level_boxes(pb), ctu.make_level_boxes(rb), ctu.make_reflux_sets(fs))
+
+    def sync(lev, coarse_new, fine_latest):
+        """Reflux level lev - 1, restrict level lev into it, clear the registers."""
+        pb, rb, fs = ops[lev]
+        ctxs[lev - 1].reflux(coarse_new, coarse_new.shape[1], reg, fs, stream=stream)
+        ctxs[lev - 1].restrict(coarse_new, coarse_new.shape[1], fine_latest, fine_latest.shape[1], rb,
+                               stream=stream)
+        r0, r1 = reg_range[lev]
+        reg[r0:r1].zero_()
+
+    def ghosts(lev, coarse_old, coarse_new, alpha, fine):
+        ctxs[lev].prolong(coarse_old, coarse_new, coarse_old.shape[1], alpha, fine, fine.shape[1], ops[lev][0],
+                          stream=stream)
+
     def coarse_step():
         # recursive subcycling: l0, then for each l1 substep its two l2 substeps
         lstep(0, A[0], B[0])
         for k in range(2):
-            lstep(1, *((A[1], B[1]) if k == 0 else (B[1], A[1])))
+            s1, d1 = (A[1], B[1]) if k == 0 else (B[1], A[1])
+            if ops:
+                ghosts(1, A[0], B[0], k / 2, s1)
+            lstep(1, s1, d1)
             for m in range(2):
-                lstep(2, *((A[2], B[2]) if m == 0 else (B[2], A[2])))
+                s2, d2 = (A[2], B[2]) if m == 0 else (B[2], A[2])
+                if ops:
+                    ghosts(2, s1, d1, m / 2, s2)
+                lstep(2, s2, d2)
+            if ops:
+                sync(2, d1, A[2])
+        if ops:
+            sync(1, B[0], A[1])
 
     def barrier():
         if pg is not None:
@@ -514,6 +587,8 @@ def run_amr(args):
             kern[f"l{lev}_{k_}"] = t_
         c.profile(False)
     launches = sum(c.launches() for c in ctxs[:1]) + 2 * ctxs[1].launches() + 4 * ctxs[2].launches()
+    if ops:  # prolongations 2 + 4, refluxes and restrictions 2 + 1 each
+        launches += 6 + 3 + 3
     if rank == 0:
         line = {"metric": METRIC, "value": upd / (ms * 1e-3), "unit": "cell-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -527,6 +602,8 @@ def run_amr(args):
                            "cell_updates_per_coarse_step": upd, "windows_rank0": sum(len(w) for w in wins),
                            "rank0_share_of_updates": my_upd / upd,
                            "parallelism": f"patch shards x{world}" if world > 1 else "single GPU",
+                           "level_ops": "prolongation of fine ghosts before every fine substep, reflux + "
+                                        "restriction at every synchronisation" if ops else "none",
                            "tiles_xw_seg": tiles,
                            "l2_flush": "inputs larger than L2"},
                 "gpu_launches": launches * args.steps, "clocks": clk,
@@ -675,6 +752,8 @@ def main():
     ap.add_argument("--skip-other", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--no-level-ops", action="store_true",
+                    help="amr: advance the levels without prolongation, restriction and reflux")
     ap.add_argument("--config", default="blast", choices=["blast", "amr", "srmhd"],
                     help="blast: the 256^3 headline workload; amr: batched AMR level advance; "
                          "srmhd: relativistic jet")

@@ -215,7 +215,7 @@ typedef struct {
                          fine cells for ctu_prolong, coarse cells for ctu_restrict */
     int origin[3];    /* coarse cell holding the fine patch's cell 0: fine cell x lies in
                          coarse cell origin + floor(x / ratio) on every active dimension */
-    int ratio;        /* refinement ratio >= 1 */
+    int ratio;        /* refinement ratio, 1 to 4 */
 } ctu_level_box;
 
 /* Eq. (prolong) + Eq. (intalpha): every fine cell x of each box takes

@@ -5,9 +5,10 @@
 //   k_restrict  restriction (average down), Eq. (avgdown);
 //   k_reflux    flux correction at coarse-fine interfaces from the flux
 //               registers, Eq. (fluxcorr) and Eq. (addreflux).
-// All three are data-parallel and HBM-bound: one thread per output cell
-// (prolongation, restriction) or coarse face (reflux), a grid-stride loop
-// over a box of cells, blockIdx.y = box.
+// All three are data-parallel and HBM-bound: one thread per coarse cell
+// (prolongation: its children inside the box; restriction: the cell) or
+// coarse face (reflux); the blocks of a launch are spread over the boxes in
+// proportion to their work (BlockMap).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,62 +39,94 @@ __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : 
 __device__ __forceinline__ double mc64(double dm, double dp)
 {
     const double m = fmin(0.5 * fabs(dm + dp), 2.0 * fmin(fabs(dm), fabs(dp)));
-    const bool same = (dm > 0.0 && dp > 0.0) || (dm < 0.0 && dp < 0.0);
+    const bool same = (dm > 0.0) == (dp > 0.0) && dm != 0.0 && dp != 0.0;
     return same ? copysign(m, dm) : 0.0;
 }
+
+// Blocks of a launch are spread over its boxes in proportion to their work:
+// block b serves box blk_box[b], as its (b - box_start[box])-th block.
+struct BlockMap {
+    const int *box_start;
+    const int *blk_box;
+    __device__ __forceinline__ void locate(int &box, long long &first) const
+    {
+        box = blk_box[blockIdx.x];
+        first = (long long)(blockIdx.x - box_start[box]) * AMR_BLOCK + threadIdx.x;
+    }
+};
 
 // Eq. (prolong) with Eq. (intalpha): fine cell x of the box takes
 // U* = (1 - alpha) U_old + alpha U_new of its coarse cell c = origin +
 // floor(x / r), plus, along each active dimension d, w_d times the
 // MC-limited central difference of U* there, w_d = ((x_d mod r) + 1/2)/r - 1/2
-// (the volume-coordinate ratio of Eq. prolong for Cartesian cells).
-__global__ void __launch_bounds__(AMR_BLOCK) k_prolong(const ctu_level_box *boxes, int ndim, const double *Uco,
-                                                        const double *Ucn, long long cs, double alpha, double *Uf,
-                                                        long long fs)
+// (the volume-coordinate ratio of Eq. prolong for Cartesian cells).  One
+// thread per coarse cell under the box: U* and its slopes are formed once
+// and written to the cell's children inside the box.
+__global__ void __launch_bounds__(AMR_BLOCK) k_prolong(const ctu_level_box *boxes, BlockMap map, int ndim,
+                                                        const double *Uco, const double *Ucn, long long cs,
+                                                        double alpha, double *Uf, long long fs)
 {
-    const ctu_level_box B = boxes[blockIdx.y];
+    int bi;
+    long long t;
+    map.locate(bi, t);
+    const ctu_level_box B = boxes[bi];
     const AmrGeom gc{{B.cn[0], B.cn[1], B.cn[2]}, ndim}, gf{{B.fn[0], B.fn[1], B.fn[2]}, ndim};
-    const int e0 = B.hi[0] - B.lo[0], e1 = B.hi[1] - B.lo[1], e2 = B.hi[2] - B.lo[2];
-    const long long cnt = (long long)e0 * e1 * e2;
+    const int r = B.ratio;
+    int clo[3], ce[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d < ndim) {
+            clo[d] = floordiv(B.lo[d], r);
+            ce[d] = floordiv(B.hi[d] - 1, r) + 1 - clo[d];
+        } else {
+            clo[d] = 0;
+            ce[d] = 1;
+        }
+    }
+    if (t >= (long long)ce[0] * ce[1] * ce[2]) return;
+    const int cr[3] = {clo[0] + (int)(t % ce[0]), clo[1] + (int)((t / ce[0]) % ce[1]),
+                       clo[2] + (int)(t / ((long long)ce[0] * ce[1]))};  // coarse cell, fine-patch frame
+    const long long c0 = B.cbase + gc.cell(B.origin[0] + cr[0], ndim > 1 ? B.origin[1] + cr[1] : 0,
+                                           ndim > 2 ? B.origin[2] + cr[2] : 0);
+    const long long st[3] = {1, gc.cell(0, 1, 0) - gc.cell(0, 0, 0), gc.cell(0, 0, 1) - gc.cell(0, 0, 0)};
     const double beta = 1.0 - alpha;
-    for (long long t = (long long)blockIdx.x * AMR_BLOCK + threadIdx.x; t < cnt;
-         t += (long long)gridDim.x * AMR_BLOCK) {
-        const int xf[3] = {B.lo[0] + (int)(t % e0), B.lo[1] + (int)((t / e0) % e1), B.lo[2] + (int)(t / ((long long)e0 * e1))};
-        int c[3];
-        double w[3];
+    const double ir = 1.0 / r;
+    // children of this coarse cell inside the box, their weights per
+    // dimension and their fine cell offsets
+    int k0[3], k1[3];
+    double w[3][4];  // ratio <= 4
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (d < ndim) {
-                const int fl = floordiv(xf[d], B.ratio);
-                c[d] = B.origin[d] + fl;
-                w[d] = ((xf[d] - B.ratio * fl) + 0.5) / B.ratio - 0.5;
-            } else {
-                c[d] = 0;
-                w[d] = 0.0;
-            }
-        }
-        const long long fi = B.fbase + gf.cell(xf[0], xf[1], xf[2]);
-        const long long c0 = B.cbase + gc.cell(c[0], c[1], c[2]);
-        long long cm[3], cp[3];
+    for (int d = 0; d < 3; ++d) {
+        const int f0 = d < ndim ? cr[d] * r : 0;
+        const int fe = d < ndim ? r : 1;
+        k0[d] = max(f0, B.lo[d]);
+        k1[d] = min(f0 + fe, B.hi[d]);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const long long st = d == 0 ? 1 : (d == 1 ? gc.cell(0, 1, 0) - gc.cell(0, 0, 0) : gc.cell(0, 0, 1) - gc.cell(0, 0, 0));
-            cm[d] = c0 - st;
-            cp[d] = c0 + st;
-        }
+        for (int m = 0; m < 4; ++m) w[d][m] = d < ndim ? ((k0[d] - f0 + m) + 0.5) * ir - 0.5 : 0.0;
+    }
+    const long long f00 = B.fbase + gf.cell(k0[0], k0[1], k0[2]);
+    const long long fsy = gf.cell(0, 1, 0) - gf.cell(0, 0, 0), fsz = gf.cell(0, 0, 1) - gf.cell(0, 0, 0);
+    const int nx = k1[0] - k0[0], ny = k1[1] - k0[1], nz = k1[2] - k0[2];
 #pragma unroll 1
-        for (int q = 0; q < 9; ++q) {
-            const double *Po = Uco + q * cs, *Pn = Ucn + q * cs;
-            const double u0 = beta * Po[c0] + alpha * Pn[c0];
-            double u = u0;
+    for (int q = 0; q < 9; ++q) {
+        const double *Po = Uco + q * cs, *Pn = Ucn + q * cs;
+        const double u0 = beta * Po[c0] + alpha * Pn[c0];
+        double s[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (d >= ndim) continue;
-                const double um = beta * Po[cm[d]] + alpha * Pn[cm[d]];
-                const double up = beta * Po[cp[d]] + alpha * Pn[cp[d]];
-                u += w[d] * mc64(u0 - um, up - u0);
+        for (int d = 0; d < 3; ++d) {
+            if (d >= ndim) continue;
+            const double um = beta * Po[c0 - st[d]] + alpha * Pn[c0 - st[d]];
+            const double up = beta * Po[c0 + st[d]] + alpha * Pn[c0 + st[d]];
+            s[d] = mc64(u0 - um, up - u0);
+        }
+        double *Pf = Uf + q * fs + f00;
+        for (int z = 0; z < nz; ++z) {
+            const double uz = u0 + w[2][z] * s[2];
+            for (int y = 0; y < ny; ++y) {
+                const double uy = uz + w[1][y] * s[1];
+                double *row = Pf + z * fsz + y * fsy;
+                for (int x = 0; x < nx; ++x) row[x] = uy + w[0][x] * s[0];
             }
-            Uf[q * fs + fi] = u;
         }
     }
 }
@@ -101,17 +134,19 @@ __global__ void __launch_bounds__(AMR_BLOCK) k_prolong(const ctu_level_box *boxe
 // Eq. (avgdown): coarse cell c of the box becomes the mean of its r^ndim
 // fine cells (c - origin) r + k (Cartesian: equal volumes), summed with the
 // innermost index along x.
-__global__ void __launch_bounds__(AMR_BLOCK) k_restrict(const ctu_level_box *boxes, int ndim, double *Uc,
-                                                         long long cs, const double *Uf, long long fs)
+__global__ void __launch_bounds__(AMR_BLOCK) k_restrict(const ctu_level_box *boxes, BlockMap map, int ndim,
+                                                         double *Uc, long long cs, const double *Uf, long long fs)
 {
-    const ctu_level_box B = boxes[blockIdx.y];
+    int bi;
+    long long t;
+    map.locate(bi, t);
+    const ctu_level_box B = boxes[bi];
     const AmrGeom gc{{B.cn[0], B.cn[1], B.cn[2]}, ndim}, gf{{B.fn[0], B.fn[1], B.fn[2]}, ndim};
     const int e0 = B.hi[0] - B.lo[0], e1 = B.hi[1] - B.lo[1], e2 = B.hi[2] - B.lo[2];
     const long long cnt = (long long)e0 * e1 * e2;
     const int r = B.ratio, k1 = ndim > 1 ? r : 1, k2 = ndim > 2 ? r : 1;
     const double nk = (double)r * k1 * k2;
-    for (long long t = (long long)blockIdx.x * AMR_BLOCK + threadIdx.x; t < cnt;
-         t += (long long)gridDim.x * AMR_BLOCK) {
+    if (t < cnt) {
         const int x = B.lo[0] + (int)(t % e0), y = B.lo[1] + (int)((t / e0) % e1),
                   z = B.lo[2] + (int)(t / ((long long)e0 * e1));
         const long long ci = B.cbase + gc.cell(x, y, z);
@@ -136,10 +171,13 @@ __global__ void __launch_bounds__(AMR_BLOCK) k_restrict(const ctu_level_box *box
 // faces (weight +1); the coarse cell beside it gains side x that total over
 // its volume.  A coarse cell next to several interfaces receives several
 // corrections, so the addition is atomic.
-__global__ void __launch_bounds__(AMR_BLOCK) k_reflux(const ctu_reflux_set *sets, int ndim, double *Uc, long long cs,
-                                                       const double *reg)
+__global__ void __launch_bounds__(AMR_BLOCK) k_reflux(const ctu_reflux_set *sets, BlockMap map, int ndim, double *Uc,
+                                                       long long cs, const double *reg)
 {
-    const ctu_reflux_set S = sets[blockIdx.y];
+    int si;
+    long long t;
+    map.locate(si, t);
+    const ctu_reflux_set S = sets[si];
     const AmrGeom gc{{S.cn[0], S.cn[1], S.cn[2]}, ndim};
     const int ea = S.dir == 0 ? 1 : 0, eb = S.dir == 2 ? 1 : 2;
     const int ra = ea < ndim ? S.ratio : 1, rb = eb < ndim ? S.ratio : 1;
@@ -147,8 +185,7 @@ __global__ void __launch_bounds__(AMR_BLOCK) k_reflux(const ctu_reflux_set *sets
     for (int d = 0; d < ndim; ++d) vol *= S.dx[d];
     const long long na = S.a1 - S.a0, nb = S.b1 - S.b0;
     const long long cnt = na * nb;
-    for (long long t = (long long)blockIdx.x * AMR_BLOCK + threadIdx.x; t < cnt;
-         t += (long long)gridDim.x * AMR_BLOCK) {
+    if (t < cnt) {
         const int a = S.a0 + (int)(t % na), b = S.b0 + (int)(t / na);
         int c[3];
         c[S.dir] = S.side > 0 ? S.plane : S.plane - 1;

@@ -590,25 +590,52 @@ ctu_status ctu_autotune(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t
 
 // ---------------------------------------------------------------- level operators
 
-// Device copy of a descriptor array (kind 0 prolong, 1 restrict, 2 reflux),
-// uploaded only when its contents change.
-static ctu_status op_table(ctu_ctx *ctx, int kind, const void *h, size_t bytes, cudaStream_t s, const void **out)
+// Device copy of a descriptor array (kind 0 prolong, 1 restrict, 2 reflux)
+// followed by its block map (first block of each descriptor, descriptor of
+// each block; blocks[i] = blocks of descriptor i), uploaded only when the
+// descriptors change.
+struct OpTable {
+    const void *desc;
+    BlockMap map;
+    unsigned nblocks;
+};
+
+static ctu_status op_table(ctu_ctx *ctx, int kind, const void *h, size_t bytes, int n, const long long *blocks,
+                           cudaStream_t s, OpTable *out)
 {
     std::vector<char> &c = ctx->opcache[kind];
+    long long tot = 0;
+    for (int i = 0; i < n; ++i) tot += blocks[i];
+    if (tot >= (1LL << 31)) return CTU_EINVAL;
+    const size_t dbytes = (bytes + 15) / 16 * 16;
+    const size_t need = dbytes + sizeof(int) * ((size_t)n + (size_t)tot);
     if (c.size() != bytes || std::memcmp(c.data(), h, bytes) != 0) {
-        if (bytes > ctx->opcap[kind]) {
-            CTU_CUDA(cudaStreamSynchronize(s));
+        std::vector<char> img(need);
+        std::memcpy(img.data(), h, bytes);
+        int *start = (int *)(img.data() + dbytes), *blk = start + n;
+        long long b = 0;
+        for (int i = 0; i < n; ++i) {
+            start[i] = (int)b;
+            for (long long k = 0; k < blocks[i]; ++k) blk[b + k] = i;
+            b += blocks[i];
+        }
+        CTU_CUDA(cudaStreamSynchronize(s));
+        if (need > ctx->opcap[kind]) {
             if (ctx->optab[kind]) cudaFree(ctx->optab[kind]);
             ctx->optab[kind] = nullptr;
             ctx->opcap[kind] = 0;
-            CTU_CUDA(cudaMalloc(&ctx->optab[kind], bytes));
-            ctx->opcap[kind] = bytes;
+            CTU_CUDA(cudaMalloc(&ctx->optab[kind], need));
+            ctx->opcap[kind] = need;
         }
-        CTU_CUDA(cudaMemcpyAsync(ctx->optab[kind], h, bytes, cudaMemcpyHostToDevice, s));
+        CTU_CUDA(cudaMemcpyAsync(ctx->optab[kind], img.data(), need, cudaMemcpyHostToDevice, s));
         CTU_CUDA(cudaStreamSynchronize(s));
         c.assign((const char *)h, (const char *)h + bytes);
     }
-    *out = ctx->optab[kind];
+    char *base = (char *)ctx->optab[kind];
+    out->desc = base;
+    out->map.box_start = (const int *)(base + dbytes);
+    out->map.blk_box = out->map.box_start + n;
+    out->nblocks = (unsigned)tot;
     return CTU_OK;
 }
 
@@ -638,7 +665,7 @@ static bool box_ok(const ctu_ctx *ctx, const ctu_level_box &B, int64_t cstride, 
                    long long *cells)
 {
     long long cc = 0, fc = 0;
-    if (!patch_extent(ctx, B.cn, &cc) || !patch_extent(ctx, B.fn, &fc) || B.ratio < 1) return false;
+    if (!patch_extent(ctx, B.cn, &cc) || !patch_extent(ctx, B.fn, &fc) || B.ratio < 1 || B.ratio > 4) return false;
     if (B.cbase < 0 || B.cbase + cc > cstride || B.fbase < 0 || B.fbase + fc > fstride) return false;
     const int *out_n = prolong ? B.fn : B.cn;
     long long cnt = 1;
@@ -667,33 +694,33 @@ static bool box_ok(const ctu_ctx *ctx, const ctu_level_box &B, int64_t cstride, 
     return true;
 }
 
-static unsigned amr_grid_x(long long maxcells)
-{
-    long long b = (maxcells + AMR_BLOCK - 1) / AMR_BLOCK;
-    if (b < 1) b = 1;
-    if (b > 4096) b = 4096;
-    return (unsigned)b;
-}
-
 ctu_status ctu_prolong(ctu_ctx *ctx, const double *Uc_old, const double *Uc_new, int64_t cstride, double alpha,
                        double *Uf, int64_t fstride, const ctu_level_box *boxes, int nbox, void *stream)
 {
     if (!ctx || !Uc_old || !Uc_new || !Uf || !boxes || nbox <= 0 || nbox > 65535 || !(alpha == alpha))
         return CTU_EINVAL;
     if (Uf == Uc_old || Uf == Uc_new) return CTU_EINVAL;
-    long long maxc = 0;
+    std::vector<long long> blocks(nbox);
     for (int i = 0; i < nbox; ++i) {
         long long c = 0;
         if (!box_ok(ctx, boxes[i], cstride, fstride, true, &c)) return CTU_EINVAL;
-        maxc = std::max(maxc, c);
+        // one thread per coarse cell under the box
+        long long cc = c > 0 ? 1 : 0;
+        for (int d = 0; d < ctx->cfg.ndim && cc; ++d) {
+            const ctu_level_box &B = boxes[i];
+            cc *= floordiv_h(B.hi[d] - 1, B.ratio) + 1 - floordiv_h(B.lo[d], B.ratio);
+        }
+        blocks[i] = (cc + AMR_BLOCK - 1) / AMR_BLOCK;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const void *d = nullptr;
-    ctu_status st = op_table(ctx, 0, boxes, sizeof(ctu_level_box) * nbox, s, &d);
+    OpTable T;
+    ctu_status st = op_table(ctx, 0, boxes, sizeof(ctu_level_box) * nbox, nbox, blocks.data(), s, &T);
     if (st != CTU_OK) return st;
-    if (maxc == 0) return CTU_OK;
-    k_prolong<<<dim3(amr_grid_x(maxc), (unsigned)nbox), AMR_BLOCK, 0, s>>>(
-        (const ctu_level_box *)d, ctx->cfg.ndim, Uc_old, Uc_new, cstride, alpha, Uf, fstride);
+    if (T.nblocks == 0) return CTU_OK;
+    if (ctx->prof) ctx->prof->mark("prolong", s);
+    k_prolong<<<T.nblocks, AMR_BLOCK, 0, s>>>((const ctu_level_box *)T.desc, T.map, ctx->cfg.ndim, Uc_old, Uc_new,
+                                             cstride, alpha, Uf, fstride);
+    if (ctx->prof) ctx->prof->mark(nullptr, s);
     CTU_CUDA(cudaGetLastError());
     return CTU_OK;
 }
@@ -702,20 +729,21 @@ ctu_status ctu_restrict(ctu_ctx *ctx, double *Uc, int64_t cstride, const double 
                         const ctu_level_box *boxes, int nbox, void *stream)
 {
     if (!ctx || !Uc || !Uf || !boxes || nbox <= 0 || nbox > 65535 || Uc == Uf) return CTU_EINVAL;
-    long long maxc = 0;
+    std::vector<long long> blocks(nbox);
     for (int i = 0; i < nbox; ++i) {
         long long c = 0;
         if (!box_ok(ctx, boxes[i], cstride, fstride, false, &c)) return CTU_EINVAL;
-        maxc = std::max(maxc, c);
+        blocks[i] = (c + AMR_BLOCK - 1) / AMR_BLOCK;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const void *d = nullptr;
-    ctu_status st = op_table(ctx, 1, boxes, sizeof(ctu_level_box) * nbox, s, &d);
+    OpTable T;
+    ctu_status st = op_table(ctx, 1, boxes, sizeof(ctu_level_box) * nbox, nbox, blocks.data(), s, &T);
     if (st != CTU_OK) return st;
-    if (maxc == 0) return CTU_OK;
-    k_restrict<<<dim3(amr_grid_x(maxc), (unsigned)nbox), AMR_BLOCK, 0, s>>>((const ctu_level_box *)d,
-                                                                             ctx->cfg.ndim, Uc, cstride, Uf,
-                                                                             fstride);
+    if (T.nblocks == 0) return CTU_OK;
+    if (ctx->prof) ctx->prof->mark("restrict", s);
+    k_restrict<<<T.nblocks, AMR_BLOCK, 0, s>>>((const ctu_level_box *)T.desc, T.map, ctx->cfg.ndim, Uc, cstride,
+                                              Uf, fstride);
+    if (ctx->prof) ctx->prof->mark(nullptr, s);
     CTU_CUDA(cudaGetLastError());
     return CTU_OK;
 }
@@ -725,7 +753,7 @@ ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *r
 {
     if (!ctx || !Uc || !reg || !sets || nset <= 0 || nset > 65535) return CTU_EINVAL;
     const int ndim = ctx->cfg.ndim;
-    long long maxc = 0;
+    std::vector<long long> blocks(nset);
     for (int i = 0; i < nset; ++i) {
         const ctu_reflux_set &S = sets[i];
         long long cc = 0;
@@ -742,15 +770,16 @@ ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *r
             return CTU_EINVAL;
         for (int d = 0; d < ndim; ++d)
             if (!(S.dx[d] > 0.0)) return CTU_EINVAL;
-        maxc = std::max(maxc, (long long)(S.a1 - S.a0) * (S.b1 - S.b0));
+        blocks[i] = ((long long)(S.a1 - S.a0) * (S.b1 - S.b0) + AMR_BLOCK - 1) / AMR_BLOCK;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const void *d = nullptr;
-    ctu_status st = op_table(ctx, 2, sets, sizeof(ctu_reflux_set) * nset, s, &d);
+    OpTable T;
+    ctu_status st = op_table(ctx, 2, sets, sizeof(ctu_reflux_set) * nset, nset, blocks.data(), s, &T);
     if (st != CTU_OK) return st;
-    if (maxc == 0) return CTU_OK;
-    k_reflux<<<dim3(amr_grid_x(maxc), (unsigned)nset), AMR_BLOCK, 0, s>>>((const ctu_reflux_set *)d, ndim, Uc,
-                                                                           cstride, reg);
+    if (T.nblocks == 0) return CTU_OK;
+    if (ctx->prof) ctx->prof->mark("reflux", s);
+    k_reflux<<<T.nblocks, AMR_BLOCK, 0, s>>>((const ctu_reflux_set *)T.desc, T.map, ndim, Uc, cstride, reg);
+    if (ctx->prof) ctx->prof->mark(nullptr, s);
     CTU_CUDA(cudaGetLastError());
     return CTU_OK;
 }
