@@ -41,8 +41,13 @@ template <> struct Tol<double> {
     static __device__ __forceinline__ double bt() { return 1.0e-24; }
     static __device__ __forceinline__ double hlld() { return 1.0e-12; }
 };
+// bt(): transverse field below which the Alfven basis is the degenerate
+// one.  The same relative threshold in both precisions, so that a state
+// with B_t != 0 in float64 (e.g. B_z = 0 exactly in 2-D, B_y small) keeps
+// the basis along B_t and exact zeros of v_z, B_z stay exact; bt2 above
+// 1e-24 a2 keeps B_t itself in the normal float range.
 template <> struct Tol<float> {
-    static __device__ __forceinline__ float bt() { return 1.0e-12f; }
+    static __device__ __forceinline__ float bt() { return 1.0e-24f; }
     static __device__ __forceinline__ float hlld() { return 1.0e-6f; }
 };
 
