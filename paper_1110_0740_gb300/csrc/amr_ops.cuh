@@ -35,12 +35,21 @@ struct AmrGeom {
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // Monotonised-central slope, Eq. (MClim): for dm, dp of one sign that sign
-// times min(|dm + dp|/2, 2|dm|, 2|dp|), else 0.
+// times min(|dm + dp|/2, 2|dm|, 2|dp|), else 0.  Non-negative float64
+// values order like their bit patterns, so the minima, absolute values and
+// sign tests run as integer operations; only the sum and the two exact
+// scalings by 1/2 and 2 use the FP64 pipe (GB300 issues 2 FP64 operations
+// per SM and cycle).
 __device__ __forceinline__ double mc64(double dm, double dp)
 {
-    const double m = fmin(0.5 * fabs(dm + dp), 2.0 * fmin(fabs(dm), fabs(dp)));
-    const bool same = (dm > 0.0) == (dp > 0.0) && dm != 0.0 && dp != 0.0;
-    return same ? copysign(m, dm) : 0.0;
+    const long long bm = __double_as_longlong(dm), bp = __double_as_longlong(dp);
+    const long long am = bm & 0x7FFFFFFFFFFFFFFFll, ap = bp & 0x7FFFFFFFFFFFFFFFll;
+    const bool same = ((bm ^ bp) >= 0) && am != 0 && ap != 0;
+    const double h = 0.5 * __longlong_as_double(__double_as_longlong(dm + dp) & 0x7FFFFFFFFFFFFFFFll);
+    const double t = 2.0 * __longlong_as_double(am < ap ? am : ap);
+    const long long bh = __double_as_longlong(h), bt = __double_as_longlong(t);
+    const long long m = bh < bt ? bh : bt;
+    return same ? __longlong_as_double(m | (bm & (long long)0x8000000000000000ull)) : 0.0;
 }
 
 // Blocks of a launch are spread over its boxes in proportion to their work:
@@ -62,6 +71,7 @@ struct BlockMap {
 // (the volume-coordinate ratio of Eq. prolong for Cartesian cells).  One
 // thread per coarse cell under the box: U* and its slopes are formed once
 // and written to the cell's children inside the box.
+template <bool BLEND>
 __global__ void __launch_bounds__(AMR_BLOCK) k_prolong(const ctu_level_box *boxes, BlockMap map, int ndim,
                                                         const double *Uco, const double *Ucn, long long cs,
                                                         double alpha, double *Uf, long long fs)
@@ -110,13 +120,15 @@ __global__ void __launch_bounds__(AMR_BLOCK) k_prolong(const ctu_level_box *boxe
 #pragma unroll 1
     for (int q = 0; q < 9; ++q) {
         const double *Po = Uco + q * cs, *Pn = Ucn + q * cs;
-        const double u0 = beta * Po[c0] + alpha * Pn[c0];
+        // U* at an offset from c0: blended, or (alpha 0 or 1) the one state
+        auto ustar = [&](long long o) { return BLEND ? beta * Po[o] + alpha * Pn[o] : Po[o]; };
+        const double u0 = ustar(c0);
         double s[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             if (d >= ndim) continue;
-            const double um = beta * Po[c0 - st[d]] + alpha * Pn[c0 - st[d]];
-            const double up = beta * Po[c0 + st[d]] + alpha * Pn[c0 + st[d]];
+            const double um = ustar(c0 - st[d]);
+            const double up = ustar(c0 + st[d]);
             s[d] = mc64(u0 - um, up - u0);
         }
         double *Pf = Uf + q * fs + f00;
@@ -146,6 +158,9 @@ __global__ void __launch_bounds__(AMR_BLOCK) k_restrict(const ctu_level_box *box
     const long long cnt = (long long)e0 * e1 * e2;
     const int r = B.ratio, k1 = ndim > 1 ? r : 1, k2 = ndim > 2 ? r : 1;
     const double nk = (double)r * k1 * k2;
+    // dividing by a power of two is multiplying by its exact reciprocal
+    const bool pow2 = (r & (r - 1)) == 0;
+    const double ink = 1.0 / nk;
     if (t < cnt) {
         const int x = B.lo[0] + (int)(t % e0), y = B.lo[1] + (int)((t / e0) % e1),
                   z = B.lo[2] + (int)(t / ((long long)e0 * e1));
@@ -161,7 +176,7 @@ __global__ void __launch_bounds__(AMR_BLOCK) k_restrict(const ctu_level_box *box
                         const int fz = ndim > 2 ? (z - B.origin[2]) * r + c2 : 0;
                         s += Uf[q * fs + B.fbase + gf.cell(fx, fy, fz)];
                     }
-            Uc[q * cs + ci] = s / nk;
+            Uc[q * cs + ci] = pow2 ? s * ink : s / nk;
         }
     }
 }

@@ -718,8 +718,13 @@ ctu_status ctu_prolong(ctu_ctx *ctx, const double *Uc_old, const double *Uc_new,
     if (st != CTU_OK) return st;
     if (T.nblocks == 0) return CTU_OK;
     if (ctx->prof) ctx->prof->mark("prolong", s);
-    k_prolong<<<T.nblocks, AMR_BLOCK, 0, s>>>((const ctu_level_box *)T.desc, T.map, ctx->cfg.ndim, Uc_old, Uc_new,
-                                             cstride, alpha, Uf, fstride);
+    if (alpha == 0.0 || alpha == 1.0)  // U* is one of the two states: no blend
+        k_prolong<false><<<T.nblocks, AMR_BLOCK, 0, s>>>((const ctu_level_box *)T.desc, T.map, ctx->cfg.ndim,
+                                                         alpha == 0.0 ? Uc_old : Uc_new,
+                                                         alpha == 0.0 ? Uc_old : Uc_new, cstride, alpha, Uf, fstride);
+    else
+        k_prolong<true><<<T.nblocks, AMR_BLOCK, 0, s>>>((const ctu_level_box *)T.desc, T.map, ctx->cfg.ndim,
+                                                        Uc_old, Uc_new, cstride, alpha, Uf, fstride);
     if (ctx->prof) ctx->prof->mark(nullptr, s);
     CTU_CUDA(cudaGetLastError());
     return CTU_OK;
