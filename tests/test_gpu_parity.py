@@ -99,3 +99,34 @@ def test_mixed_precision_lowbeta_accuracy(prec):
     g64, _, st = gpu_run(U0, n, 3, dx, 5, 0.3, precision=0, recon=1)
     assert st == 0
     assert np.all(l1rel(O.interior(g64, n, 3), R, odts[-1][1]) < TOL64)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_gpu_step_commutes_with_mirrors_and_swap(prec, tol):
+    """x -> -x, z -> -z (normal velocity and field odd, psi even) and the 2-D
+    x <-> y swap are symmetries of Eq. (1) + Eq. (glm2x2): the GPU step
+    commutes with them, to round-off in FP64 and to float accuracy in the
+    mixed path (the sweep order z, y, x is not itself mirror-symmetric, and
+    float32 rounding then differs)."""
+    from tests.mhd_setup import mirror_x, mirror_z, swap_xy
+    n = [24, 24, 1]
+    dx = [1.0 / 24] * 2
+    U = W.mhd_turb_2d(24, seed=4)
+    ref, _, st = gpu_run(U, n, 2, dx, 4, 0.4, precision=prec, recon=1)
+    assert st == 0
+    R = O.interior(ref, n, 2)
+    scale = np.abs(R).max(axis=(1, 2, 3))[:, None, None, None]
+    for f in (mirror_x, swap_xy):
+        got, _, st = gpu_run(f(U), n, 2, dx, 4, 0.4, precision=prec, recon=1)
+        assert st == 0
+        assert np.all(np.abs(O.interior(f(got), n, 2) - R) <= tol * scale)
+    n3 = [16, 16, 16]
+    U3 = W.mhd_blast_3d(16, seed=5, kmax=2)
+    d3 = [1.0 / 16] * 3
+    ref3, _, st = gpu_run(U3, n3, 3, d3, 3, 0.3, precision=prec, recon=1)
+    R3 = O.interior(ref3, n3, 3)
+    scale3 = np.abs(R3).max(axis=(1, 2, 3))[:, None, None, None]
+    for f in (mirror_x, mirror_z):
+        got, _, st = gpu_run(f(U3), n3, 3, d3, 3, 0.3, precision=prec, recon=1)
+        assert st == 0
+        assert np.all(np.abs(O.interior(f(got), n3, 3) - R3) <= tol * scale3)
