@@ -310,7 +310,16 @@ __device__ __forceinline__ R cell_speed(const R (&V)[NV], const StepArgs &a, con
     for (int d = 0; d < 3; ++d) {
         if (d >= a.ndim) continue;
         R s;
-        if (PHYS == PH_MHD) {
+        if (PHYS == PH_MHD && sizeof(R) == 4) {
+            // fast speed along d from the shared a^2 and B^2/rho
+            const R irho = R(1) / V[0];
+            const R a2 = g * V[4] * irho;
+            const R b2 = (V[5] * V[5] + V[6] * V[6] + V[7] * V[7]) * irho;
+            const R bn2 = V[5 + d] * V[5 + d] * irho;
+            const R bt2 = b2 - bn2;
+            const R disc = sqrt((a2 - b2) * (a2 - b2) + R(4) * a2 * bt2);
+            s = fabs(V[1 + d]) + sqrt(R(0.5) * (a2 + b2 + disc));
+        } else if (PHYS == PH_MHD) {
             const int b1 = 5 + (d == 0 ? 1 : 0), b2 = 5 + (d == 2 ? 1 : 2);
             s = fabs(V[1 + d]) + fast_speed(V[0], V[4], V[5 + d], V[b1], V[b2], g);
         } else {
