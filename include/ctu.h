@@ -259,6 +259,15 @@ typedef struct {
 ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *reg,
                       const ctu_reflux_set *sets, int nset, void *stream);
 
+/* Conservation diagnostics (a helper, not part of the step): writes to the
+ * device array d_out[10] the totals sum over interior cells of U_q times the
+ * cell volume (q = 0..8: mass, momentum, energy, magnetic flux, psi) and, in
+ * d_out[9], the largest |div B| over interior cells with central
+ * differences, sum_d (B_d(c + e_d) - B_d(c - e_d)) / (2 dx_d).  The sums are
+ * accumulated with float64 atomics, so their rounding order is not fixed. */
+ctu_status ctu_diagnostics(ctu_ctx *ctx, const double *U, int64_t stride,
+                           const ctu_patch *patches, int npatch, double *d_out, void *stream);
+
 /* Fill the ghost cells of every patch with periodic copies of its own
  * interior (helper for periodic boxes; not part of the step). */
 ctu_status ctu_fill_periodic(ctu_ctx *ctx, double *U, int64_t stride,

@@ -97,6 +97,8 @@ def lib():
         L.or_prolong.argtypes = [P, P, I3, D, P, I3, I3, I3, I3, I, I]
         L.or_restrict.restype = None
         L.or_restrict.argtypes = [P, I3, P, I3, I3, I3, I3, I, I]
+        L.or_diagnostics.restype = None
+        L.or_diagnostics.argtypes = [P, I3, I, P, P]
         L.or_reflux.restype = None
         L.or_reflux.argtypes = [P, I3, P, P, I, I, I, I, I, I, I, ctypes.c_long, ctypes.c_long,
                                 I, I, I, I, I, I]
@@ -132,6 +134,17 @@ def restrict(Uc, nc, Uf, nf, lo, hi, origin, ratio, ndim):
     lib().or_restrict(_dp(Uc), _i3(nc), _dp(Ufc), _i3(nf), _i3(lo), _i3(hi), _i3(origin), int(ratio),
                       int(ndim))
     return Uc
+
+
+def diagnostics(U, n, ndim, dx):
+    """Conserved totals (sum of U_q times the cell volume over the interior,
+    q = 0..8) and max |div B| (central differences): an array of 10."""
+    Uc = np.ascontiguousarray(U, dtype=np.float64)
+    assert Uc.shape == shape(n, ndim)
+    out = np.zeros(10)
+    d = list(dx) + [1.0] * (3 - len(dx))
+    lib().or_diagnostics(_dp(Uc), _i3(n), int(ndim), (ctypes.c_double * 3)(*d), _dp(out))
+    return out
 
 
 def reflux(Uc, nc, dxc, reg, dir, plane, side, a0, a1, b0, b1, creg, freg, fa0, fb0, fna, fnb, ratio, ndim):

@@ -2,7 +2,8 @@
  * CTU step (test infrastructure): coarse-to-fine prolongation with time
  * interpolation, Eq. (prolong) and Eq. (intalpha); restriction, Eq.
  * (avgdown); reflux, Eq. (fluxcorr) and Eq. (addreflux) of Mignone et al.
- * (2012), Section 4.  Cartesian geometry: the volume coordinate of a
+ * (2012), Section 4; and the conservation diagnostics of a patch (conserved
+ * totals, max |div B|).  Cartesian geometry: the volume coordinate of a
  * direction is the coordinate itself and a cell's volume the product of its
  * widths.
  *
@@ -154,4 +155,31 @@ void or_reflux(double *Uc, const int nc[3], const double dxc[3], const double *r
                 Uc[q * Sc + ci] += side * t / vol;
             }
         }
+}
+
+/* Diagnostics of one patch: out[q] = sum over interior cells of U_q times the
+ * cell volume (the conserved totals, q = 0..8), out[9] = max over interior
+ * cells of |div B| with central differences, sum_d (B_d(c + e_d) -
+ * B_d(c - e_d)) / (2 dx_d) over the active dimensions. */
+void or_diagnostics(const double *U, const int n[3], int ndim, const double dx[3], double out[10])
+{
+    const long S = cells(n, ndim);
+    double vol = 1.0;
+    for (int d = 0; d < ndim; ++d) vol *= dx[d];
+    for (int q = 0; q < 10; ++q) out[q] = 0.0;
+    for (int z = 0; z < n[2]; ++z)
+        for (int y = 0; y < n[1]; ++y)
+            for (int x = 0; x < n[0]; ++x) {
+                const long c = cell(n, ndim, x, y, z);
+                for (int q = 0; q < NV; ++q) out[q] += U[q * S + c] * vol;
+                double div = 0.0;
+                for (int d = 0; d < ndim; ++d) {
+                    int p[3] = {x, y, z}, m[3] = {x, y, z};
+                    p[d] += 1;
+                    m[d] -= 1;
+                    div += (U[(5 + d) * S + cell(n, ndim, p[0], p[1], p[2])] -
+                            U[(5 + d) * S + cell(n, ndim, m[0], m[1], m[2])]) / (2.0 * dx[d]);
+                }
+                if (fabs(div) > out[9]) out[9] = fabs(div);
+            }
 }

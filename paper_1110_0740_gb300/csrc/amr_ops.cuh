@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include "ctu.h"
+#include "ctu_kernels.cuh"
 
 namespace ctu {
 
@@ -218,6 +219,59 @@ __global__ void __launch_bounds__(AMR_BLOCK) k_reflux(const ctu_reflux_set *sets
                 }
             atomicAdd(Uc + q * cs + ci, S.side * tot / vol);
         }
+    }
+}
+
+// Conservation diagnostics of a batch: out[q] += U_q x cell volume over the
+// interior cells (q = 0..8), out[9] = max |div B| with central differences
+// (as the bits of a non-negative float64, which order like the values).
+// blockIdx.y = patch; per block a shared-memory reduction, then one atomic
+// per quantity.
+__global__ void __launch_bounds__(AMR_BLOCK) k_diagnostics(const DevPatch *patches, int ndim, const double *U,
+                                                            long long us, double *out)
+{
+    const DevPatch P = patches[blockIdx.y];
+    const AmrGeom g{{P.n[0], P.n[1], P.n[2]}, ndim};
+    const long long cnt = (long long)P.n[0] * P.n[1] * P.n[2];
+    double vol = 1.0;
+    for (int d = 0; d < ndim; ++d) vol *= P.dx[d];
+    double acc[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) acc[q] = 0.0;
+    for (long long t = (long long)blockIdx.x * AMR_BLOCK + threadIdx.x; t < cnt;
+         t += (long long)gridDim.x * AMR_BLOCK) {
+        const int x = (int)(t % P.n[0]), y = (int)((t / P.n[0]) % P.n[1]),
+                  z = (int)(t / ((long long)P.n[0] * P.n[1]));
+        const long long c = P.base + g.cell(x, y, z);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] += U[q * us + c] * vol;
+        double div = 0.0;
+        for (int d = 0; d < ndim; ++d) {
+            const long long st = d == 0 ? 1 : (d == 1 ? (long long)P.N[0] : (long long)P.N[0] * P.N[1]);
+            div += (U[(5 + d) * us + c + st] - U[(5 + d) * us + c - st]) / (2.0 * P.dx[d]);
+        }
+        acc[9] = fmax(acc[9], fabs(div));
+    }
+    __shared__ double red[10][AMR_BLOCK / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = q < 9 ? v + w : fmax(v, w);
+        }
+        if (lane == 0) red[q][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        const int q = threadIdx.x;
+        double v = red[q][0];
+        for (int k = 1; k < AMR_BLOCK / 32; ++k) v = q < 9 ? v + red[q][k] : fmax(v, red[q][k]);
+        if (q < 9)
+            atomicAdd(out + q, v);
+        else
+            atomicMax((unsigned long long *)(out + 9), (unsigned long long)__double_as_longlong(v));
     }
 }
 

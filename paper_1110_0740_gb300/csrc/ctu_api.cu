@@ -789,6 +789,26 @@ ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *r
     return CTU_OK;
 }
 
+ctu_status ctu_diagnostics(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patch *patches, int npatch,
+                           double *d_out, void *stream)
+{
+    if (!ctx || !U || !d_out) return CTU_EINVAL;
+    ctu_status st = validate_patches(ctx, stride, patches, npatch);
+    if (st != CTU_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = bind_patches(ctx, patches, npatch, s);
+    if (st != CTU_OK) return st;
+    long long maxc = 0;
+    for (const Group &G : ctx->groups) maxc = std::max(maxc, (long long)G.n[0] * G.n[1] * G.n[2]);
+    long long bx = (maxc + AMR_BLOCK - 1) / AMR_BLOCK;
+    if (bx > 1024) bx = 1024;
+    CTU_CUDA(cudaMemsetAsync(d_out, 0, 10 * sizeof(double), s));
+    k_diagnostics<<<dim3((unsigned)bx, (unsigned)npatch), AMR_BLOCK, 0, s>>>(ctx->dpatch, ctx->cfg.ndim, U, stride,
+                                                                             d_out);
+    CTU_CUDA(cudaGetLastError());
+    return CTU_OK;
+}
+
 ctu_status ctu_tile_params(ctu_ctx *ctx, const int n[3], int *xw, int *seg)
 {
     if (!ctx || !n || !xw || !seg) return CTU_EINVAL;

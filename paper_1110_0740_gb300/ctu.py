@@ -140,6 +140,8 @@ def _lib():
         L.ctu_restrict.restype = i32
         L.ctu_reflux.argtypes = [vp, vp, i64, vp, ctypes.POINTER(ctu_reflux_set), i32, vp]
         L.ctu_reflux.restype = i32
+        L.ctu_diagnostics.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp, vp]
+        L.ctu_diagnostics.restype = i32
         for f in ("ctu_init", "ctu_dt", "ctu_step", "ctu_flux_registers", "ctu_fill_periodic",
                   "ctu_status_sync", "ctu_last_launch_count"):
             getattr(L, f).restype = i32
@@ -253,6 +255,11 @@ def ctu_reflux(ctx, Uc, cstride, reg, sets, stream=None):
            "ctu_reflux")
 
 
+def ctu_diagnostics(ctx, U, stride, patches, d_out, stream=None):
+    _check(_lib().ctu_diagnostics(ctx, _ptr(U), int(stride), patches, len(patches), _ptr(d_out),
+                                  _stream(stream)), "ctu_diagnostics")
+
+
 def ctu_flux_registers(ctx, reg, windows):
     if reg is None or not windows:
         _check(_lib().ctu_flux_registers(ctx, None, None, 0), "ctu_flux_registers")
@@ -343,6 +350,9 @@ class Ctx:
 
     def reflux(self, Uc, cstride, reg, sets, stream=None):
         ctu_reflux(self.h, Uc, cstride, reg, sets, stream)
+
+    def diagnostics(self, U, stride, patches, d_out, stream=None):
+        ctu_diagnostics(self.h, U, stride, patches, d_out, stream)
 
     def fill_periodic(self, U, stride, patches, stream=None):
         ctu_fill_periodic(self.h, U, stride, patches, stream)

@@ -185,3 +185,28 @@ def test_two_level_hierarchy_on_the_gpu_conserves_and_matches_the_oracle():
     err = np.abs(O.interior(got, nc, 2) - O.interior(Ucn, nc, 2)).sum(axis=(1, 2, 3))
     ref = np.abs(O.interior(Ucn, nc, 2)).sum(axis=(1, 2, 3))
     assert np.all(err[:8] <= 1e-11 * ref[:8]), err / np.maximum(ref, 1e-300)
+
+
+def test_diagnostics_match_the_oracle():
+    """ctu_diagnostics over a batch of uneven patches: the conserved totals
+    are the sums of the oracle's per-patch totals and the largest |div B| is
+    the largest of theirs."""
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    shapes = [(16, 12, 8), (8, 8, 8), (24, 5, 7)]
+    dxs = [(0.05, 0.07, 0.06), (0.1, 0.1, 0.1), (1 / 24, 0.2, 0.1)]
+    src = W.mhd_blast_3d(32, seed=3, kmax=3)
+    arrays = [np.ascontiguousarray(src[:, :n[2] + 8, :n[1] + 8, :n[0] + 8]) for n in shapes]
+    P, bases = _pool(arrays)
+    dev = _dev()
+    U = torch.from_numpy(P).to(dev)
+    out = torch.zeros(10, dtype=torch.float64, device=dev)
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_MIXED))
+    ctx.diagnostics(U, P.shape[1], ctu.make_patches([(n, dx, b) for n, dx, b in zip(shapes, dxs, bases)]), out)
+    got = out.cpu().numpy()
+    ref = [O.diagnostics(A, list(n), 3, list(dx)) for A, n, dx in zip(arrays, shapes, dxs)]
+    tot = np.sum([r[:9] for r in ref], axis=0)
+    scale = np.sum([np.abs(r[:9]) for r in ref], axis=0) + 1e-300
+    assert np.all(np.abs(got[:9] - tot) <= 1e-13 * scale), (got[:9], tot)
+    assert got[9] == pytest.approx(max(r[9] for r in ref), rel=1e-14)
+    assert ctx.status_sync() == 0

@@ -215,3 +215,37 @@ def test_reflux_restores_conservation_of_two_levels():
     scale = np.abs(O.interior(Unew, nc, 2)).sum(axis=(1, 2, 3)) * hc * hc
     assert np.all(np.abs(total - total0)[:8] <= 1e-13 * scale[:8]), (total - total0)
     assert np.abs(no_reflux - total0)[[0, 4]].max() > 1e-8
+
+
+def test_diagnostics_closed_forms():
+    """Totals of a uniform state are value x volume; the central-difference
+    divergence of a linear field is its trace, of the central-difference
+    curl of any potential exactly zero (the differences commute)."""
+    rng = np.random.default_rng(21)
+    n, ndim = [10, 8, 6], 3
+    dx = [0.1, 0.2, 0.05]
+    U = np.zeros(O.shape(n, ndim))
+    vals = rng.standard_normal(9)
+    U[:] = vals[:, None, None, None]
+    g = O.ghosts(ndim)
+    z, y, x = np.meshgrid(*[(np.arange(-g[d], n[d] + g[d]) + 0.5) * dx[d] for d in (2, 1, 0)], indexing="ij")
+    a, b, c = 0.7, -1.3, 2.1
+    U[5], U[6], U[7] = 3.0 + a * x, -1.0 + b * y, 0.5 + c * z
+    out = O.diagnostics(U, n, ndim, dx)
+    vol = np.prod(dx) * np.prod(n)
+    for q in (0, 1, 2, 3, 4, 8):
+        assert out[q] == pytest.approx(vals[q] * vol, rel=1e-13)
+    assert out[5] == pytest.approx(np.mean(3.0 + a * x[4:-4, 4:-4, 4:-4]) * vol, rel=1e-12)
+    assert out[9] == pytest.approx(abs(a + b + c), rel=1e-12)
+    # 2-D: B = central-difference curl of a random A_z
+    n2 = [16, 12, 1]
+    d2 = [1.0 / 16, 1.0 / 12]
+    A = rng.standard_normal((12 + 8 + 2, 16 + 8 + 2))
+    U2 = np.zeros(O.shape(n2, 2))
+    U2[0] = 1.0
+    U2[5, 0] = (A[2:, 1:-1] - A[:-2, 1:-1]) / (2 * d2[1])
+    U2[6, 0] = -(A[1:-1, 2:] - A[1:-1, :-2]) / (2 * d2[0])
+    out2 = O.diagnostics(U2, n2, 2, d2)
+    scale = np.abs(U2[5:7]).max() / min(d2)
+    assert out2[9] <= 1e-13 * scale
+    assert out2[0] == pytest.approx(1.0, rel=1e-14)
