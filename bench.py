@@ -721,11 +721,20 @@ def precision_split_roofline(n, cells_per_s, hbm_gbs):
             "frac": cells_per_s / bounds[binding]}
 
 
+STEP_SOURCES = ("df.cuh", "mhd_device.cuh", "srmhd_device.cuh", "ctu_kernels.cuh", "ctu_launch.h",
+                "ctu_launch.cuh", "ctu_f32.cu", "_build.py")
+
+
 def kernel_source_hash():
+    """Hash of the sources the step's kernels are compiled from (with the
+    build flags), so that recorded per-kernel traffic stays valid across
+    changes elsewhere in the library."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1110_0740_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_1110_0740_gb300", "csrc", f), "rb") as fh:
+    pkg = os.path.join(ROOT, "paper_1110_0740_gb300")
+    for f in STEP_SOURCES:
+        path = os.path.join(pkg, f) if f == "_build.py" else os.path.join(pkg, "csrc", f)
+        with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
