@@ -81,8 +81,9 @@ def test_batch_of_uneven_patches_and_registers():
 
 def test_full_size_sampled_parity_256():
     """The bench workload (256^3, PPM, mixed and FP64, the bench's launch
-    configuration): one GPU step, then 6 sampled 6^3 blocks recomputed by the
-    oracle from their own ghosted neighbourhood of the same input."""
+    configuration: autotuned tiles for the mixed path): one GPU step, then 6
+    sampled 6^3 blocks recomputed by the oracle from their own ghosted
+    neighbourhood of the same input."""
     import torch
     from paper_1110_0740_gb300 import ctu
     n = 256
@@ -98,6 +99,8 @@ def test_full_size_sampled_parity_256():
         ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3))
         dtch = torch.zeros(2, dtype=torch.float64, device=dev)
         ctx.dt(U, stride, patches, dtch)
+        if prec == ctu.CTU_MIXED:  # the bench's tiles
+            ctx.autotune(U, Uo, stride, patches, dtch)
         ctx.step(U, Uo, stride, patches, dtch)
         assert ctx.status_sync() == 0
         dt, ch = dtch.cpu().tolist()
@@ -238,3 +241,102 @@ def test_autotune_changes_only_the_launch_shape(prec):
         xw, seg = tuned.tile_params(n)
         assert xw in (8, 16, 32) and seg in (4, 8, 16, 32, 64)
         assert ref.tile_params(n) == (32 if n[0] >= 24 else 16 if n[0] >= 12 else 8, 16)
+
+
+def test_full_size_lowbeta_sampled_256():
+    """The low-beta Mach-10 variant at 256^3 in the mixed path (autotuned
+    tiles): sampled 6^3 blocks against the oracle."""
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    n = 256
+    U0 = W.mhd_lowbeta_3d(n, seed=1)
+    dev = _dev()
+    U = torch.from_numpy(U0.reshape(9, -1)).to(dev)
+    Uo = torch.zeros_like(U)
+    stride = U.shape[1]
+    patches = ctu.make_patches([([n] * 3, [1.0 / n] * 3, 0)])
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_MIXED, cfl=0.3))
+    dtch = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.dt(U, stride, patches, dtch)
+    ctx.autotune(U, Uo, stride, patches, dtch)
+    ctx.step(U, Uo, stride, patches, dtch)
+    assert ctx.status_sync() == 0
+    dt, ch = dtch.cpu().tolist()
+    G = Uo.view(9, n + 8, n + 8, n + 8)
+    rng = np.random.default_rng(9)
+    for c in [rng.integers(0, n - 6, size=3) for _ in range(5)]:
+        k, j, i = int(c[2]), int(c[1]), int(c[0])
+        blk = U0[:, k:k + 14, j:j + 14, i:i + 14].copy()
+        R, bad = O.mhd_step(blk, [6, 6, 6], 3, [1.0 / n] * 3, dt, ch, recon=1)
+        assert bad == 0
+        got = G[:, k + 4:k + 10, j + 4:j + 10, i + 4:i + 10].cpu().numpy()
+        e = l1rel(got, O.interior(R, [6, 6, 6], 3), ch)
+        assert np.all(e <= 2e-5), (c, e)
+
+
+def test_full_amr_level_sampled():
+    """The AMR workload at full size (3 levels over 128^3, ~560 patches of
+    8^3..64^3): the finest level advanced in one batched, autotuned mixed
+    step and its ghosts prolonged from level 1 (alpha 1/2); sampled patches
+    of every size against the oracle's step and prolongation of that patch."""
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    H = W.amr_hierarchy(seed=0)
+    L1, L2 = H["levels"][1], H["levels"][2]
+    dev = _dev()
+    A1 = torch.from_numpy(L1["pool"]).to(dev)
+    B1 = A1 * 1.0
+    A2 = torch.from_numpy(L2["pool"]).to(dev)
+    B2 = torch.zeros_like(A2)
+    P2 = ctu.make_patches([p[:3] for p in L2["patches"]])
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_MIXED, cfl=0.3))
+    d = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.dt(A2, A2.shape[1], P2, d)
+    ctx.autotune(A2, B2, A2.shape[1], P2, d)
+    ctx.step(A2, B2, A2.shape[1], P2, d)
+    assert ctx.status_sync() == 0
+    dt, ch = d.cpu().tolist()
+    # ghost shells of every level-2 patch from its parent, between A1 and B1 (a perturbed copy)
+    B1[4] *= 1.01
+    boxes = []
+    for fi, (n, dx, base, _) in enumerate(L2["patches"]):
+        parent, o_zyx, sz = L2["footprints"][fi]
+        cn, _, cbase, _ = L1["patches"][parent]
+        o = [o_zyx[2], o_zyx[1], o_zyx[0]]
+        for dd in range(3):
+            for lo_d, hi_d in ((-4, 0), (n[dd], n[dd] + 4)):
+                lo_ = [lo_d if e == dd else (0 if e < dd else -4) for e in range(3)]
+                hi_ = [hi_d if e == dd else (n[e] if e < dd else n[e] + 4) for e in range(3)]
+                boxes.append(dict(fn=n, cn=cn, fbase=base, cbase=cbase, lo=lo_, hi=hi_, origin=o, ratio=2))
+    F = torch.zeros_like(A2)
+    ctx.prolong(A1, B1, A1.shape[1], 0.5, F, F.shape[1], ctu.make_level_boxes(boxes))
+    got_step = B2.cpu().numpy()
+    got_pro = F.cpu().numpy()
+    pool1, pool1n = L1["pool"], B1.cpu().numpy()
+    by_size = {}
+    for fi, (n, dx, base, _) in enumerate(L2["patches"]):
+        by_size.setdefault(n[0], []).append(fi)
+    for size, idx in sorted(by_size.items()):
+        for fi in idx[:2]:
+            n, dx, base, _ = L2["patches"][fi]
+            N = [v + 8 for v in n]
+            cells = N[0] * N[1] * N[2]
+            blk = L2["pool"][:, base:base + cells].reshape(9, N[2], N[1], N[0])
+            R, bad = O.mhd_step(blk, list(n), 3, list(dx), dt, ch, recon=1)
+            assert bad == 0
+            G = got_step[:, base:base + cells].reshape(blk.shape)
+            e = l1rel(O.interior(G, list(n), 3), O.interior(R, list(n), 3), ch)
+            assert np.all(e <= 2e-5), (size, fi, e)
+            parent, o_zyx, sz = L2["footprints"][fi]
+            cn, _, cbase, _ = L1["patches"][parent]
+            Nc = [v + 8 for v in cn]
+            cc = Nc[0] * Nc[1] * Nc[2]
+            Co = pool1[:, cbase:cbase + cc].reshape(9, Nc[2], Nc[1], Nc[0])
+            Cn = pool1n[:, cbase:cbase + cc].reshape(9, Nc[2], Nc[1], Nc[0])
+            ref = np.zeros(O.shape(list(n), 3))
+            o = [o_zyx[2], o_zyx[1], o_zyx[0]]
+            for b in boxes:
+                if b["fbase"] == base:
+                    O.prolong(Co, Cn, list(cn), 0.5, ref, list(n), b["lo"], b["hi"], o, 2, 3)
+            Gp = got_pro[:, base:base + cells].reshape(blk.shape)
+            assert np.allclose(Gp, ref, rtol=1e-14, atol=1e-14), (size, fi)
