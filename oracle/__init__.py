@@ -60,6 +60,8 @@ def lib():
         L.or_mhd_step.restype = I
         L.or_mhd_step.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, I, I,
                                   ctypes.POINTER(ctypes.c_long), P, I, P]
+        L.or_mhd_floor.restype = ctypes.c_long
+        L.or_mhd_floor.argtypes = [P, I, I, I, I, D, D, D]
         L.or_mhd_max_speed.restype = D
         L.or_mhd_max_speed.argtypes = [P, I, I, I, I, D, D, D, D]
         L.or_mhd_eigen.restype = None
@@ -239,6 +241,14 @@ def mhd_step(U, n, ndim, dx, dt, ch, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
                             win.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(wgt),
                             nwin, regp)
     return Un, bad
+
+
+def mhd_floor(U, n, ndim, p_floor, rho_floor, gamma=5.0 / 3.0):
+    """The optional floors of the updated state (see or_mhd_floor), applied in
+    place to the interior cells of U; returns the number of floored cells."""
+    assert U.dtype == np.float64 and U.flags.c_contiguous and U.shape == shape(n, ndim)
+    return int(lib().or_mhd_floor(_dp(U), int(n[0]), int(n[1]), int(n[2]), int(ndim), float(gamma),
+                                  float(p_floor), float(rho_floor)))
 
 
 def boundary_windows(n, ndim, weight=1.0, base=0):

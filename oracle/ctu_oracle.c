@@ -27,6 +27,8 @@
  *                                  (ppm_parabolic_lim)
  *   - linear reconstruction:       Section 3.2, Eq. (Linear)
  *   - flux-register contribution:  Section 4.2, Eq. (fluxcorr)
+ *   - optional density and pressure floors on the updated state: a reading
+ *     (the paper fixes none), or_mhd_floor
  * The paper gives neither the primitive eigenvectors nor the Riemann solver
  * formulas; they are written here from the mathematics: the eigenvectors are
  * derived from the primitive Jacobian of Eq. (1) (Roe-Balsara normalisation),
@@ -812,4 +814,50 @@ int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
         free(F[d]);
     }
     return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* Optional floors on the updated state                                */
+/* ------------------------------------------------------------------ */
+
+/* The paper fixes no floor (its Section 5 only reports where a state turned
+ * non-physical); this is the reading the library follows.  Applied to the
+ * interior cells of U after the update and the psi damping:
+ *   1. rho < rho_floor: rho becomes rho_floor; m, E, B and psi are kept;
+ *   2. with that density, p = (Gamma-1)(E - m^2/(2 rho) - B^2/2); when
+ *      p < p_floor, E becomes p_floor/(Gamma-1) + m^2/(2 rho) + B^2/2.
+ * A floor of 0 is off.  A NaN state fails both tests and is left as it is.
+ * Returns the number of cells that met either floor. */
+long or_mhd_floor(double *U, int nx, int ny, int nz, int ndim, double gam, double p_floor, double rho_floor)
+{
+    grid_t G;
+    int c[3];
+    long count = 0;
+    grid_init(&G, nx, ny, nz, ndim);
+    const long nc = G.ncell;
+    for (c[2] = 0; c[2] < G.n[2]; c[2]++)
+        for (c[1] = 0; c[1] < G.n[1]; c[1]++)
+            for (c[0] = 0; c[0] < G.n[0]; c[0]++) {
+                const long id = cidx(&G, c);
+                int hit = 0;
+                double rho = U[id];
+                if (rho_floor > 0.0 && rho < rho_floor) {
+                    rho = rho_floor;
+                    U[id] = rho;
+                    hit = 1;
+                }
+                if (p_floor > 0.0) {
+                    double m2 = U[nc + id] * U[nc + id] + U[2 * nc + id] * U[2 * nc + id] +
+                                U[3 * nc + id] * U[3 * nc + id];
+                    double B2 = U[5 * nc + id] * U[5 * nc + id] + U[6 * nc + id] * U[6 * nc + id] +
+                                U[7 * nc + id] * U[7 * nc + id];
+                    double p = (gam - 1.0) * (U[4 * nc + id] - 0.5 * m2 / rho - 0.5 * B2);
+                    if (p < p_floor) {
+                        U[4 * nc + id] = p_floor / (gam - 1.0) + 0.5 * m2 / rho + 0.5 * B2;
+                        hit = 1;
+                    }
+                }
+                count += hit;
+            }
+    return count;
 }
