@@ -100,6 +100,20 @@ typedef struct {
                          exp(-glm_alpha c_h dt / min dx) per step */
     int nghost;       /* must be 4 */
     int trace_mode;   /* CTU_TRACE_ALL or CTU_TRACE_UPWIND */
+    /* Optional floors of the updated state, >= 0, 0 = off; CTU_MHD only
+     * (CTU_SRMHD with a floor returns CTU_EUNSUPPORTED).  The paper fixes no
+     * floor: its safeguard against non-physical states is the shock-flagged
+     * hybrid integration of its appendix on shock detection (not built).
+     * After the update and the psi damping of every ctu_step, an interior
+     * cell with rho < rho_floor takes rho = rho_floor (m, E, B, psi kept);
+     * then, with that density, a cell with
+     * p = (Gamma-1)(E - m^2/(2 rho) - B^2/2) < p_floor takes
+     * E = p_floor/(Gamma-1) + m^2/(2 rho) + B^2/2, in float64 in every
+     * precision.  Floored cells are counted (ctu_floor_count).  A
+     * non-positive state met inside a step (cell centres, interface states)
+     * still sets CTU_ENEGATIVE with floors on. */
+    double p_floor;
+    double rho_floor;
 } ctu_config;
 
 typedef struct {
@@ -162,6 +176,11 @@ ctu_status ctu_step(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t str
 ctu_status ctu_step_next_dt(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t stride,
                             const ctu_patch *patches, int npatch, const double *d_dt_ch,
                             double *d_dt_ch_next, void *stream);
+
+/* The number of interior cells the floors (ctu_config.p_floor, rho_floor)
+ * changed since the context was created or this function last returned;
+ * resets the count.  Synchronises the stream.  *count is a host int64. */
+ctu_status ctu_floor_count(ctu_ctx *ctx, int64_t *count, void *stream);
 
 /* Bind (or, with reg == NULL or nwin == 0, unbind) flux-register windows.
  * `win` is a host array copied at call time; `reg` is a device float64 array
@@ -322,8 +341,9 @@ int ctu_profile_read(ctu_ctx *ctx, int i, const char **name, double *total_ms, l
  * start of every call): calls that overlap on the GPU -- on different
  * streams, or from different threads -- race and corrupt each other.
  *
- * cfg: as for ctu_init.  U_in, U_out, stride, patches, npatch, d_dt_ch: as
- * for ctu_step.  wait_status != 0: synchronise the stream and return the
+ * cfg: as for ctu_init, without floors (a non-zero p_floor or rho_floor
+ * returns CTU_EUNSUPPORTED).  U_in, U_out, stride, patches, npatch, d_dt_ch:
+ * as for ctu_step.  wait_status != 0: synchronise the stream and return the
  * device status of this call (CTU_OK, CTU_ENEGATIVE or CTU_ENAN);
  * wait_status == 0: return after enqueueing. */
 #define CTU_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)

@@ -100,6 +100,8 @@ def lib():
         L.or_restrict.restype = None
         L.or_restrict.argtypes = [P, I3, P, I3, I3, I3, I3, I, I]
         L.or_diagnostics.restype = None
+        L.or_tag.restype = ctypes.c_long
+        L.or_tag.argtypes = [P, I3, I, I, D, D, P, ctypes.POINTER(ctypes.c_ubyte)]
         L.or_diagnostics.argtypes = [P, I3, I, P, P]
         L.or_reflux.restype = None
         L.or_reflux.argtypes = [P, I3, P, P, I, I, I, I, I, I, I, ctypes.c_long, ctypes.c_long,
@@ -136,6 +138,20 @@ def restrict(Uc, nc, Uf, nf, lo, hi, origin, ratio, ndim):
     lib().or_restrict(_dp(Uc), _i3(nc), _dp(Ufc), _i3(nf), _i3(lo), _i3(hi), _i3(origin), int(ratio),
                       int(ndim))
     return Uc
+
+
+def tag(U, n, ndim, kind, eps, chi_r):
+    """Eq. (RefCrit) refinement tags of one ghost-filled patch: returns
+    (tag uint8, chi float64, count), both arrays in the ghosted layout with
+    only interior entries written (tag 0 and chi 0 elsewhere).  kind: 0
+    density, 1 total energy, 2 B^2/rho, 3 E/rho."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    assert U.shape == shape(n, ndim)
+    chi = np.zeros(U.shape[1:])
+    t = np.zeros(U.shape[1:], dtype=np.uint8)
+    cnt = lib().or_tag(_dp(U), _i3(n), int(ndim), int(kind), float(eps), float(chi_r), _dp(chi),
+                       t.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+    return t, chi, int(cnt)
 
 
 def diagnostics(U, n, ndim, dx):

@@ -2,8 +2,9 @@
  * CTU step (test infrastructure): coarse-to-fine prolongation with time
  * interpolation, Eq. (prolong) and Eq. (intalpha); restriction, Eq.
  * (avgdown); reflux, Eq. (fluxcorr) and Eq. (addreflux) of Mignone et al.
- * (2012), Section 4; and the conservation diagnostics of a patch (conserved
- * totals, max |div B|).  Cartesian geometry: the volume coordinate of a
+ * (2012), Section 4; the refinement criterion, Eq. (RefCrit) of Section 4
+ * (second-derivative error norm); and the conservation diagnostics of a
+ * patch (conserved totals, max |div B|).  Cartesian geometry: the volume coordinate of a
  * direction is the coordinate itself and a cell's volume the product of its
  * widths.
  *
@@ -182,4 +183,57 @@ void or_diagnostics(const double *U, const int n[3], int ndim, const double dx[3
                 }
                 if (fabs(div) > out[9]) out[9] = fabs(div);
             }
+}
+
+/* The quantity sigma(U) of the refinement criterion: 0 density (rho, or D in
+ * relativistic MHD), 1 total energy density E, 2 B^2 / rho, 3 E / rho. */
+static double tag_sigma(const double *U, long S, long c, int kind)
+{
+    switch (kind) {
+    case 0: return U[c];
+    case 1: return U[4 * S + c];
+    case 2: return (U[5 * S + c] * U[5 * S + c] + U[6 * S + c] * U[6 * S + c] + U[7 * S + c] * U[7 * S + c]) / U[c];
+    default: return U[4 * S + c] / U[c];
+    }
+}
+
+/* Eq. (RefCrit), Section 4 (refinement criteria): for every interior cell,
+ *   chi = sqrt( sum_d (D+ - D-)^2 / sum_d (|D+| + |D-| + eps sigma_ref,d)^2 )
+ * over the active dimensions, with the undivided differences
+ * D+ = sigma(c + e_d) - sigma(c), D- = sigma(c) - sigma(c - e_d) and
+ * sigma_ref,d = |sigma(c + e_d)| + 2 |sigma(c)| + |sigma(c - e_d)|; the cell is
+ * tagged when chi > chi_r.  Reads one ghost layer.  chi and tag are arrays of
+ * the patch's ghosted layout (only interior entries written; chi may be
+ * NULL).  A cell whose denominator is 0 (sigma = 0 at all its stencil points)
+ * gets chi = NaN and no tag.  Returns the number of tagged cells. */
+long or_tag(const double *U, const int n[3], int ndim, int kind, double eps, double chi_r, double *chi,
+            unsigned char *tag)
+{
+    const long S = cells(n, ndim);
+    long count = 0;
+    for (int z = 0; z < n[2]; ++z)
+        for (int y = 0; y < n[1]; ++y)
+            for (int x = 0; x < n[0]; ++x) {
+                const long c = cell(n, ndim, x, y, z);
+                const double s0 = tag_sigma(U, S, c, kind);
+                double num = 0.0, den = 0.0;
+                for (int d = 0; d < ndim; ++d) {
+                    int p[3] = {x, y, z}, m[3] = {x, y, z};
+                    p[d] += 1;
+                    m[d] -= 1;
+                    const double sp = tag_sigma(U, S, cell(n, ndim, p[0], p[1], p[2]), kind);
+                    const double sm = tag_sigma(U, S, cell(n, ndim, m[0], m[1], m[2]), kind);
+                    const double dp = sp - s0, dm = s0 - sm;
+                    const double a = dp - dm;
+                    num += a * a;
+                    const double ref = fabs(sp) + 2.0 * fabs(s0) + fabs(sm);
+                    const double b = fabs(dp) + fabs(dm) + eps * ref;
+                    den += b * b;
+                }
+                const double x_ = sqrt(num / den);
+                if (chi) chi[c] = x_;
+                tag[c] = x_ > chi_r ? 1 : 0;
+                count += tag[c];
+            }
+    return count;
 }

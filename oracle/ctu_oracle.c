@@ -820,8 +820,9 @@ int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
 /* Optional floors on the updated state                                */
 /* ------------------------------------------------------------------ */
 
-/* The paper fixes no floor (its Section 5 only reports where a state turned
- * non-physical); this is the reading the library follows.  Applied to the
+/* The paper fixes no floor (its safeguard against non-physical states is
+ * the shock-flagged hybrid integration of its appendix on shock detection);
+ * this is the reading the library follows.  Applied to the
  * interior cells of U after the update and the psi damping:
  *   1. rho < rho_floor: rho becomes rho_floor; m, E, B and psi are kept;
  *   2. with that density, p = (Gamma-1)(E - m^2/(2 rho) - B^2/2); when

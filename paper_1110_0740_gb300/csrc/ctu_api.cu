@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <array>
 #include <cstdint>
 #include <cstdlib>
@@ -131,6 +132,7 @@ struct ctu_ctx {
     // status, reduction word, per-step parameters
     unsigned int *dstatus = nullptr;
     unsigned long long *dmax = nullptr;
+    unsigned long long *dfloor = nullptr;  // cells the floors changed
     StepParams *dsp = nullptr;
     // flux registers
     std::vector<ctu_flux_window> hwin;
@@ -416,12 +418,17 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
     if (!(cfg->glm_alpha >= 0.0)) return CTU_EINVAL;
     if (cfg->nghost != 4) return CTU_EINVAL;
     if (cfg->trace_mode != CTU_TRACE_ALL && cfg->trace_mode != CTU_TRACE_UPWIND) return CTU_EINVAL;
+    if (!(cfg->p_floor >= 0.0 && cfg->p_floor < INFINITY) || !(cfg->rho_floor >= 0.0 && cfg->rho_floor < INFINITY))
+        return CTU_EINVAL;
+    if (cfg->physics == CTU_SRMHD && (cfg->p_floor != 0.0 || cfg->rho_floor != 0.0)) return CTU_EUNSUPPORTED;
     ctu_ctx *ctx = new (std::nothrow) ctu_ctx();
     if (!ctx) return CTU_ENOMEM;
     ctx->cfg = *cfg;
     if (cudaGetDevice(&ctx->device) != cudaSuccess ||
         cudaMalloc(&ctx->dstatus, sizeof(unsigned int)) != cudaSuccess ||
         cudaMalloc(&ctx->dmax, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&ctx->dfloor, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->dfloor, 0, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&ctx->dsp, sizeof(StepParams)) != cudaSuccess ||
         cudaMemset(ctx->dstatus, 0, sizeof(unsigned int)) != cudaSuccess) {
         ctu_destroy(ctx);
@@ -439,6 +446,7 @@ void ctu_destroy(ctu_ctx *ctx)
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->dstatus) cudaFree(ctx->dstatus);
     if (ctx->dmax) cudaFree(ctx->dmax);
+    if (ctx->dfloor) cudaFree(ctx->dfloor);
     if (ctx->dsp) cudaFree(ctx->dsp);
     if (ctx->dwin) cudaFree(ctx->dwin);
     if (ctx->dwstart) cudaFree(ctx->dwstart);
@@ -473,6 +481,65 @@ ctu_status ctu_dt(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patch
     return CTU_OK;
 }
 
+// Optional floors of the updated state, applied to the interior cells of
+// every patch after the step (the library's reading; the paper fixes no
+// floor): rho < rho_floor takes rho_floor, then a pressure below p_floor,
+// evaluated with that density, is raised to p_floor through E alone.  Every
+// operation is an explicitly rounded float64 operation in the order the
+// expressions are written (no contraction), so a cell's decision and result
+// depend only on its stored state.  One thread per interior cell; one
+// atomic per warp counts the cells changed.
+constexpr int FLOOR_BLOCK = 256;
+__global__ void __launch_bounds__(FLOOR_BLOCK) k_floor(const DevPatch *patches, double *U, long long us, double gm1,
+                                                      double p_floor, double rho_floor, unsigned long long *count)
+{
+    const DevPatch P = patches[blockIdx.y];
+    const long long cnt = (long long)P.n[0] * P.n[1] * P.n[2];
+    unsigned hits = 0;
+    for (long long t = (long long)blockIdx.x * FLOOR_BLOCK + threadIdx.x; t < cnt;
+         t += (long long)gridDim.x * FLOOR_BLOCK) {
+        const long long row = t / P.n[0];
+        const int x = (int)(t - row * P.n[0]);
+        const int y = (int)(row % P.n[1]), z = (int)(row / P.n[1]);
+        const long long c = P.base + ((long long)(z + P.g[2]) * P.N[1] + (y + P.g[1])) * P.N[0] + (x + P.g[0]);
+        double rho = U[c];
+        bool hit = false;
+        if (rho_floor > 0.0 && rho < rho_floor) {
+            rho = rho_floor;
+            U[c] = rho;
+            hit = true;
+        }
+        if (p_floor > 0.0) {
+            const double m0 = U[us + c], m1 = U[2 * us + c], m2 = U[3 * us + c];
+            const double b0 = U[5 * us + c], b1 = U[6 * us + c], b2 = U[7 * us + c];
+            const double mm = __dadd_rn(__dadd_rn(__dmul_rn(m0, m0), __dmul_rn(m1, m1)), __dmul_rn(m2, m2));
+            const double bb = __dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)), __dmul_rn(b2, b2));
+            const double ek = __ddiv_rn(__dmul_rn(0.5, mm), rho), em = __dmul_rn(0.5, bb);
+            const double p = __dmul_rn(gm1, __dsub_rn(__dsub_rn(U[4 * us + c], ek), em));
+            if (p < p_floor) {
+                U[4 * us + c] = __dadd_rn(__dadd_rn(__ddiv_rn(p_floor, gm1), ek), em);
+                hit = true;
+            }
+        }
+        hits += hit;
+    }
+    for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
+    if ((threadIdx.x & 31) == 0 && hits) atomicAdd(count, (unsigned long long)hits);
+}
+
+static bool floors_on(const ctu_ctx *ctx) { return ctx->cfg.p_floor > 0.0 || ctx->cfg.rho_floor > 0.0; }
+
+static int launch_floor(ctu_ctx *ctx, double *U, int64_t stride, int npatch, cudaStream_t s)
+{
+    long long maxc = 0;
+    for (const Group &G : ctx->groups) maxc = std::max(maxc, (long long)G.n[0] * G.n[1] * G.n[2]);
+    long long bx = (maxc + FLOOR_BLOCK - 1) / FLOOR_BLOCK;
+    if (bx > 65535) bx = 65535;
+    k_floor<<<dim3((unsigned)bx, (unsigned)npatch, 1), FLOOR_BLOCK, 0, s>>>(
+        ctx->dpatch, U, stride, ctx->cfg.gamma - 1.0, ctx->cfg.p_floor, ctx->cfg.rho_floor, ctx->dfloor);
+    return 1;
+}
+
 static ctu_status step_common(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t stride,
                               const ctu_patch *patches, int npatch, const double *d_dt_ch, double *d_next,
                               void *stream)
@@ -488,14 +555,24 @@ static ctu_status step_common(ctu_ctx *ctx, const double *U_in, double *U_out, i
     StepArgs a = make_args(ctx, U_in, U_out, stride, npatch, d_dt_ch);
     LaunchInfo li = make_info(ctx);
     int n = 0;
+    const bool floors = floors_on(ctx);
     if (d_next) {
         CTU_CUDA(cudaMemsetAsync(ctx->dmax, 0, sizeof(unsigned long long), s));
-        a.nextmax = ctx->dmax;
+        // with floors, the CFL speed is taken after them, from U_out
+        if (!floors) a.nextmax = ctx->dmax;
     }
     if (ctx->cfg.precision != CTU_FP64)
         n = launch_step<float>(a, li, s);
     else
         n = launch_step<double>(a, li, s);
+    if (floors) {
+        n += launch_floor(ctx, U_out, stride, npatch, s);
+        if (d_next) {
+            StepArgs b = make_args(ctx, U_out, nullptr, stride, npatch, nullptr);
+            n += ctx->cfg.precision != CTU_FP64 ? launch_maxspeed<float>(b, li, ctx->dmax, s)
+                                                : launch_maxspeed<double>(b, li, ctx->dmax, s);
+        }
+    }
     if (d_next) {
         k_dt_finalize<<<1, 1, 0, s>>>(ctx->dmax, ctx->cfg.cfl, ctx->dxmin, d_next);
         ++n;
@@ -882,6 +959,18 @@ ctu_status ctu_fill_periodic(ctu_ctx *ctx, double *U, int64_t stride, const ctu_
     if (bx > (1LL << 20)) bx = 1LL << 20;
     k_fill_periodic<<<dim3((unsigned)bx, (unsigned)npatch, 1), 256, 0, s>>>(ctx->dpatch, ctx->cfg.ndim, U, stride);
     CTU_CUDA(cudaGetLastError());
+    return CTU_OK;
+}
+
+ctu_status ctu_floor_count(ctu_ctx *ctx, int64_t *count, void *stream)
+{
+    if (!ctx || !count) return CTU_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long h = 0;
+    CTU_CUDA(cudaStreamSynchronize(s));
+    CTU_CUDA(cudaMemcpy(&h, ctx->dfloor, sizeof(h), cudaMemcpyDeviceToHost));
+    CTU_CUDA(cudaMemset(ctx->dfloor, 0, sizeof(h)));
+    *count = (int64_t)h;
     return CTU_OK;
 }
 

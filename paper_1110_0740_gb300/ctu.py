@@ -31,7 +31,8 @@ class ctu_config(ctypes.Structure):
                 ("ndim", ctypes.c_int), ("recon", ctypes.c_int), ("predictor", ctypes.c_int),
                 ("riemann", ctypes.c_int), ("precision", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("glm_alpha", ctypes.c_double), ("nghost", ctypes.c_int),
-                ("trace_mode", ctypes.c_int)]
+                ("trace_mode", ctypes.c_int), ("p_floor", ctypes.c_double),
+                ("rho_floor", ctypes.c_double)]
 
 
 class ctu_patch(ctypes.Structure):
@@ -115,6 +116,7 @@ def _lib():
         L.ctu_flux_registers.argtypes = [vp, vp, ctypes.POINTER(ctu_flux_window), i32]
         L.ctu_fill_periodic.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp]
         L.ctu_status_sync.argtypes = [vp, vp]
+        L.ctu_floor_count.argtypes = [vp, ctypes.POINTER(i64), vp]
         L.ctu_destroy.argtypes = [vp]
         L.ctu_destroy.restype = None
         L.ctu_strerror.argtypes = [i32]
@@ -171,10 +173,11 @@ def _check(code, where):
 
 def make_config(ndim=3, gamma=5.0 / 3.0, recon=CTU_PPM, precision=CTU_FP64, cfl=0.3,
                 glm_alpha=0.1, trace_mode=CTU_TRACE_ALL, physics=CTU_MHD, riemann=CTU_HLLD,
-                predictor=CTU_CHAR_TRACE, eos=CTU_EOS_IDEAL):
+                predictor=CTU_CHAR_TRACE, eos=CTU_EOS_IDEAL, p_floor=0.0, rho_floor=0.0):
     return ctu_config(physics=physics, eos=eos, gamma=gamma, ndim=ndim, recon=recon,
                       predictor=predictor, riemann=riemann, precision=precision, cfl=cfl,
-                      glm_alpha=glm_alpha, nghost=4, trace_mode=trace_mode)
+                      glm_alpha=glm_alpha, nghost=4, trace_mode=trace_mode, p_floor=p_floor,
+                      rho_floor=rho_floor)
 
 
 def make_patches(specs):
@@ -282,6 +285,13 @@ def ctu_status_sync(ctx, stream=None):
     return _lib().ctu_status_sync(ctx, _stream(stream))
 
 
+def ctu_floor_count(ctx, stream=None):
+    """Cells the floors changed since the last call (resets; synchronises)."""
+    c = ctypes.c_int64(0)
+    _check(_lib().ctu_floor_count(ctx, ctypes.byref(c), _stream(stream)), "ctu_floor_count")
+    return int(c.value)
+
+
 def ctu_last_launch_count(ctx):
     return _lib().ctu_last_launch_count(ctx)
 
@@ -359,6 +369,9 @@ class Ctx:
 
     def status_sync(self, stream=None):
         return ctu_status_sync(self.h, stream)
+
+    def floor_count(self, stream=None):
+        return ctu_floor_count(self.h, stream)
 
     def launches(self):
         return ctu_last_launch_count(self.h)

@@ -31,3 +31,23 @@ def test_strerror_without_gpu():
     from paper_1110_0740_gb300 import ctu
     assert ctu.ctu_strerror(0) == "ok"
     assert "invalid" in ctu.ctu_strerror(1)
+
+
+def test_floor_config_validation_without_gpu():
+    """Host-side validation of the floors returns before any CUDA call:
+    a negative or infinite floor is CTU_EINVAL, a floor with the
+    relativistic physics or with the allocation-free step CTU_EUNSUPPORTED."""
+    import ctypes
+    from paper_1110_0740_gb300 import ctu
+    L = ctu._lib()
+    h = ctypes.c_void_p()
+    for pf, rf in ((-1.0, 0.0), (0.0, -0.5), (float("inf"), 0.0), (0.0, float("nan"))):
+        cfg = ctu.make_config(p_floor=pf, rho_floor=rf)
+        assert L.ctu_init(ctypes.byref(cfg), ctypes.byref(h)) == ctu.STATUS.index("CTU_EINVAL")
+    cfg = ctu.make_config(physics=ctu.CTU_SRMHD, predictor=ctu.CTU_MUSCL_HANCOCK, riemann=ctu.CTU_HLL,
+                          recon=ctu.CTU_LINEAR_MC, gamma=4.0 / 3.0, p_floor=1e-6)
+    assert L.ctu_init(ctypes.byref(cfg), ctypes.byref(h)) == ctu.STATUS.index("CTU_EUNSUPPORTED")
+    cfg = ctu.make_config(rho_floor=1e-6)
+    patches = ctu.make_patches([([8, 8, 8], [0.1] * 3, 0)])
+    st = L.ctu_step_noalloc(ctypes.byref(cfg), 16, 32, 4096, patches, 1, 48, 0, 0)
+    assert st == ctu.STATUS.index("CTU_EUNSUPPORTED")
