@@ -670,6 +670,110 @@ def run_srmhd(args):
         print(json.dumps(line))
 
 
+def run_tag(args):
+    """Refinement tagging, Eq. (RefCrit), on the 256^3 blast state: one
+    ctu_tag launch per step over the patch (sigma = density, then B^2/rho;
+    eps 0.01, chi_r 0.1, the paper's values), L2 flushed before every launch,
+    each launch timed with CUDA events on its stream.  The kernel is HBM-bound:
+    algorithmic bytes are sigma's inputs over the interior plus one ghost
+    layer (8 B per input variable) and one tag byte per interior cell."""
+    import numpy as np
+    import torch
+    from paper_1110_0740_gb300 import ctu, workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    U0 = W.mhd_blast_3d(n, seed=rank)
+    Uh = torch.from_numpy(U0.reshape(9, -1))
+    U = Uh.to(dev)
+    stride = U.shape[1]
+    tags = torch.zeros(stride, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    patches = ctu.make_patches([([n] * 3, [1.0 / n] * 3, 0)])
+    stream = torch.cuda.current_stream()
+    ctx = ctu.Ctx(ctu.make_config(ndim=3))
+    peaks, src = measured_peaks()
+    cells = n ** 3
+    kinds = {"density": (ctu.CTU_TAG_DENSITY, 1), "B2_over_rho": (ctu.CTU_TAG_B2_OVER_RHO, 4)}
+    res = {}
+    clocks = Clocks(local)
+    clocks.start()
+    for name, (kind, nvar) in kinds.items():
+        for _ in range(args.warmup):
+            ctx.tag(U, stride, patches, kind, 0.01, 0.1, tags, cnt)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.tag(U, stride, patches, kind, 0.01, 0.1, tags, cnt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / args.steps
+        nbytes = 8 * nvar * (n + 2) ** 3 + cells
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "value": world * cells / (ms * 1e-3), "tagged": int(cnt.item()),
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                  "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                                  "algorithmic_bytes": nbytes, "peak_source": f"{src} hbm_gbs"}}
+    clk = clocks.stop()
+    st = ctx.status_sync()
+    # end to end through the public API: the pool from pinned host memory,
+    # the tags back to pinned host memory, every step
+    Uh_pin = Uh.pin_memory()
+    th = torch.empty(stride, dtype=torch.uint8).pin_memory()
+    E = max(1, min(args.steps, 3))
+    for it in range(E + 1):
+        if it == 1:
+            torch.cuda.synchronize()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+        U.copy_(Uh_pin, non_blocking=True)
+        ctx.tag(U, stride, patches, ctu.CTU_TAG_DENSITY, 0.01, 0.1, tags, cnt)
+        th.copy_(tags, non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ems = t0.elapsed_time(t1) / E
+    ctx.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        import oracle as O
+        m = min(96, n)
+        blk = np.ascontiguousarray(U0[:, :m + 8, :m + 8, :m + 8])
+        t = time.perf_counter()
+        reps = 0
+        while True:
+            O.tag(blk, [m] * 3, 3, 0, 0.01, 0.1)
+            reps += 1
+            el = time.perf_counter() - t
+            if el > 10.0 or reps >= 64:
+                break
+        cpu = {"value": reps * m ** 3 / el, "unit": "cell evaluations/s", "cores": 1, "kind": "oracle",
+               "sample": f"or_tag of a {m}^3 block of the same state (density), {reps} passes",
+               "seconds": el}
+    if rank == 0:
+        main_ = res["density"]
+        line = {"metric": "refinement-criterion cell evaluations/s (Eq. RefCrit)", "value": main_["value"],
+                "unit": "cells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": main_["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": f"Eq. RefCrit tags of the {n}^3 blast state, sigma = density, eps 0.01, "
+                                       "chi_r 0.1", "l2_flush": "256 MB write before every launch"},
+                "roofline": main_["roofline"], "b2_over_rho": res["B2_over_rho"], "tagged_cells": main_["tagged"],
+                "cpu_baseline": cpu,
+                "e2e": {"value": world * cells / (ems * 1e-3), "unit": "cells/s",
+                        "h2d_bytes_per_step": int(U.numel() * 8), "d2h_bytes_per_step": int(stride),
+                        "ms_per_step": ems},
+                "gpu_launches": args.steps, "clocks": clk, "status": ctu.STATUS[st],
+                "gpu": torch.cuda.get_device_name(dev)}
+        print(json.dumps(line))
+
+
 def _profile_numbers(name):
     vals = {}
     try:
@@ -763,9 +867,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-level-ops", action="store_true",
                     help="amr: advance the levels without prolongation, restriction and reflux")
-    ap.add_argument("--config", default="blast", choices=["blast", "amr", "srmhd"],
+    ap.add_argument("--config", default="blast", choices=["blast", "amr", "srmhd", "tag"],
                     help="blast: the 256^3 headline workload; amr: batched AMR level advance; "
-                         "srmhd: relativistic jet")
+                         "srmhd: relativistic jet; tag: refinement tagging of the 256^3 state")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -775,6 +879,8 @@ def main():
         run_amr(args)
     elif args.config == "srmhd":
         run_srmhd(args)
+    elif args.config == "tag":
+        run_tag(args)
     else:
         run_ours(args)
 

@@ -182,6 +182,37 @@ ctu_status ctu_step_next_dt(ctu_ctx *ctx, const double *U_in, double *U_out, int
  * resets the count.  Synchronises the stream.  *count is a host int64. */
 ctu_status ctu_floor_count(ctu_ctx *ctx, int64_t *count, void *stream);
 
+/* ---- Refinement tagging (Section 4, refinement criteria) ----------------
+ * The quantity sigma(U) the criterion is taken of: density (rho, or D in
+ * relativistic MHD), total energy density E, B^2/rho, E/rho. */
+enum { CTU_TAG_DENSITY = 0, CTU_TAG_ENERGY = 1, CTU_TAG_B2_OVER_RHO = 2, CTU_TAG_E_OVER_RHO = 3 };
+
+/* Eq. (RefCrit), the second-derivative error norm: for every interior cell
+ * of every patch,
+ *   chi = sqrt( sum_d (D+ - D-)^2 / sum_d (|D+| + |D-| + eps sigma_ref,d)^2 )
+ * over the active dimensions d, with D+ = sigma(c + e_d) - sigma(c),
+ * D- = sigma(c) - sigma(c - e_d) and sigma_ref,d = |sigma(c + e_d)| +
+ * 2 |sigma(c)| + |sigma(c - e_d)|; the cell is tagged when chi > chi_r.  A
+ * cell whose denominator is 0 has chi = NaN and no tag.  Every decision is
+ * the one float64 evaluation of the definition, in the order written, would
+ * take (cells that a float32 evaluation cannot decide with certainty are
+ * re-evaluated in float64).
+ *   U, stride, patches, npatch: as for ctu_step (one ghost layer is read).
+ *   sigma: CTU_TAG_*;  eps >= 0 (the paper uses 0.01);  chi_r >= 0.
+ *   tags: device uint8 array in the pool layout (>= stride entries):
+ *         tags[base + ghosted cell] = 1 or 0 for every interior cell; other
+ *         entries are not written.
+ *   d_count: nullable device int64 array of npatch entries: set to the
+ *         number of tagged cells of each patch.
+ *   chi: nullable device float64 array in the pool layout: when given,
+ *         every interior cell's chi is written (and every cell is evaluated
+ *         in float64).
+ * Enqueues on `stream`; the first call with a new patch list uploads its
+ * table (synchronises).  Errors: CTU_EINVAL for a bad argument or patch. */
+ctu_status ctu_tag(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patch *patches, int npatch,
+                   int sigma, double eps, double chi_r, unsigned char *tags, int64_t *d_count,
+                   double *chi, void *stream);
+
 /* Bind (or, with reg == NULL or nwin == 0, unbind) flux-register windows.
  * `win` is a host array copied at call time; `reg` is a device float64 array
  * the caller owns and zeroes.  Windows must not overlap in reg. */

@@ -113,10 +113,10 @@ struct ctu_ctx {
     std::map<std::array<int, 3>, std::array<int, 2>> tune;
     bool tuning = false;  // steps of ctu_autotune leave the flux registers alone
     // device copies of the level-operator descriptors (prolong, restrict,
-    // reflux), re-uploaded when a call brings different contents
-    std::vector<char> opcache[3];
-    void *optab[3] = {nullptr, nullptr, nullptr};
-    size_t opcap[3] = {0, 0, 0};
+    // reflux, tag), re-uploaded when a call brings different contents
+    std::vector<char> opcache[4];
+    void *optab[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t opcap[4] = {0, 0, 0, 0};
     int device = 0;
     // patch list cache (caller order) and its device table (grouped order)
     std::vector<ctu_patch> hpatch;
@@ -133,6 +133,8 @@ struct ctu_ctx {
     unsigned int *dstatus = nullptr;
     unsigned long long *dmax = nullptr;
     unsigned long long *dfloor = nullptr;  // cells the floors changed
+    unsigned long long *dtagcnt = nullptr;  // per-patch tag counts when the caller gives none
+    int dtagcnt_cap = 0;
     StepParams *dsp = nullptr;
     // flux registers
     std::vector<ctu_flux_window> hwin;
@@ -447,6 +449,7 @@ void ctu_destroy(ctu_ctx *ctx)
     if (ctx->dstatus) cudaFree(ctx->dstatus);
     if (ctx->dmax) cudaFree(ctx->dmax);
     if (ctx->dfloor) cudaFree(ctx->dfloor);
+    if (ctx->dtagcnt) cudaFree(ctx->dtagcnt);
     if (ctx->dsp) cudaFree(ctx->dsp);
     if (ctx->dwin) cudaFree(ctx->dwin);
     if (ctx->dwstart) cudaFree(ctx->dwstart);
@@ -671,6 +674,18 @@ ctu_status ctu_autotune(ctu_ctx *ctx, const double *U_in, double *U_out, int64_t
 // followed by its block map (first block of each descriptor, descriptor of
 // each block; blocks[i] = blocks of descriptor i), uploaded only when the
 // descriptors change.
+static ctu_status ensure_tag_scratch(ctu_ctx *ctx, int npatch)
+{
+    if (npatch <= ctx->dtagcnt_cap) return CTU_OK;
+    CTU_CUDA(cudaDeviceSynchronize());
+    if (ctx->dtagcnt) cudaFree(ctx->dtagcnt);
+    ctx->dtagcnt = nullptr;
+    ctx->dtagcnt_cap = 0;
+    CTU_CUDA(cudaMalloc(&ctx->dtagcnt, sizeof(unsigned long long) * npatch));
+    ctx->dtagcnt_cap = npatch;
+    return CTU_OK;
+}
+
 struct OpTable {
     const void *desc;
     BlockMap map;
@@ -861,6 +876,61 @@ ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *r
     if (T.nblocks == 0) return CTU_OK;
     if (ctx->prof) ctx->prof->mark("reflux", s);
     k_reflux<<<T.nblocks, AMR_BLOCK, 0, s>>>((const ctu_reflux_set *)T.desc, T.map, ndim, Uc, cstride, reg);
+    if (ctx->prof) ctx->prof->mark(nullptr, s);
+    CTU_CUDA(cudaGetLastError());
+    return CTU_OK;
+}
+
+ctu_status ctu_tag(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patch *patches, int npatch, int sigma,
+                   double eps, double chi_r, unsigned char *tags, int64_t *d_count, double *chi, void *stream)
+{
+    if (!ctx || !U || !tags || !patches || npatch <= 0) return CTU_EINVAL;
+    if (sigma < CTU_TAG_DENSITY || sigma > CTU_TAG_E_OVER_RHO) return CTU_EINVAL;
+    if (!(eps >= 0.0 && eps < INFINITY) || !(chi_r >= 0.0 && chi_r < INFINITY)) return CTU_EINVAL;
+    ctu_status st = validate_patches(ctx, stride, patches, npatch);
+    if (st != CTU_OK) return st;
+    std::vector<TagPatch> tp(npatch);
+    std::vector<long long> blocks(npatch);
+    for (int i = 0; i < npatch; ++i) {
+        for (int d = 0; d < 3; ++d) tp[i].n[d] = patches[i].n[d];
+        tp[i].pad = 0;
+        tp[i].base = patches[i].base;
+        const long long c = (long long)patches[i].n[0] * patches[i].n[1] * patches[i].n[2];
+        blocks[i] = (c + AMR_BLOCK - 1) / AMR_BLOCK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // per-patch counts: the caller's array, else the context's scratch word
+    unsigned long long *cnt = (unsigned long long *)d_count;
+    if (!cnt) {
+        st = ensure_tag_scratch(ctx, npatch);
+        if (st != CTU_OK) return st;
+        cnt = ctx->dtagcnt;
+    }
+    OpTable T;
+    st = op_table(ctx, 3, tp.data(), sizeof(TagPatch) * npatch, npatch, blocks.data(), s, &T);
+    if (st != CTU_OK) return st;
+    CTU_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * npatch, s));
+    const double f = TagFilter::margin(sigma, eps, chi_r);
+    const float filt = f < 1.0 ? (float)f : INFINITY, eps32 = (float)eps, c2 = (float)(chi_r * chi_r);
+    const TagPatch *D = (const TagPatch *)T.desc;
+    const int nd = ctx->cfg.ndim;
+    if (ctx->prof) ctx->prof->mark("tag", s);
+#define CTU_TAG_LAUNCH(K)                                                                                         \
+    do {                                                                                                         \
+        if (chi)                                                                                                 \
+            k_tag<K, true><<<T.nblocks, AMR_BLOCK, 0, s>>>(D, T.map, nd, U, stride, eps, chi_r, eps32, c2, filt, \
+                                                           tags, cnt, chi);                                      \
+        else                                                                                                     \
+            k_tag<K, false><<<T.nblocks, AMR_BLOCK, 0, s>>>(D, T.map, nd, U, stride, eps, chi_r, eps32, c2,     \
+                                                            filt, tags, cnt, chi);                               \
+    } while (0)
+    switch (sigma) {
+    case CTU_TAG_DENSITY: CTU_TAG_LAUNCH(0); break;
+    case CTU_TAG_ENERGY: CTU_TAG_LAUNCH(1); break;
+    case CTU_TAG_B2_OVER_RHO: CTU_TAG_LAUNCH(2); break;
+    default: CTU_TAG_LAUNCH(3); break;
+    }
+#undef CTU_TAG_LAUNCH
     if (ctx->prof) ctx->prof->mark(nullptr, s);
     CTU_CUDA(cudaGetLastError());
     return CTU_OK;

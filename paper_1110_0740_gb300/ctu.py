@@ -21,6 +21,7 @@ CTU_CHAR_TRACE, CTU_MUSCL_HANCOCK = 0, 1
 CTU_HLLD, CTU_HLL = 0, 1
 CTU_FP64, CTU_MIXED, CTU_MIXED_IFACE64 = 0, 1, 2
 CTU_TRACE_ALL, CTU_TRACE_UPWIND = 0, 1
+CTU_TAG_DENSITY, CTU_TAG_ENERGY, CTU_TAG_B2_OVER_RHO, CTU_TAG_E_OVER_RHO = 0, 1, 2, 3
 
 STATUS = ["CTU_OK", "CTU_EINVAL", "CTU_ENOMEM", "CTU_ECUDA", "CTU_EUNSUPPORTED", "CTU_ENEGATIVE",
           "CTU_ENAN", "CTU_ERECOVERY", "CTU_ESUPERLUMINAL", "CTU_ETIMEOUT", "CTU_ETOOLARGE"]
@@ -117,6 +118,7 @@ def _lib():
         L.ctu_fill_periodic.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp]
         L.ctu_status_sync.argtypes = [vp, vp]
         L.ctu_floor_count.argtypes = [vp, ctypes.POINTER(i64), vp]
+        L.ctu_tag.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, i32, dbl, dbl, vp, vp, vp, vp]
         L.ctu_destroy.argtypes = [vp]
         L.ctu_destroy.restype = None
         L.ctu_strerror.argtypes = [i32]
@@ -285,6 +287,12 @@ def ctu_status_sync(ctx, stream=None):
     return _lib().ctu_status_sync(ctx, _stream(stream))
 
 
+def ctu_tag(ctx, U, stride, patches, sigma, eps, chi_r, tags, d_count=None, chi=None, stream=None):
+    _check(_lib().ctu_tag(ctx, _ptr(U), int(stride), patches, len(patches), int(sigma), float(eps),
+                          float(chi_r), _ptr(tags), _ptr(d_count) if d_count is not None else None,
+                          _ptr(chi) if chi is not None else None, _stream(stream)), "ctu_tag")
+
+
 def ctu_floor_count(ctx, stream=None):
     """Cells the floors changed since the last call (resets; synchronises)."""
     c = ctypes.c_int64(0)
@@ -369,6 +377,9 @@ class Ctx:
 
     def status_sync(self, stream=None):
         return ctu_status_sync(self.h, stream)
+
+    def tag(self, U, stride, patches, sigma, eps, chi_r, tags, d_count=None, chi=None, stream=None):
+        ctu_tag(self.h, U, stride, patches, sigma, eps, chi_r, tags, d_count, chi, stream)
 
     def floor_count(self, stream=None):
         return ctu_floor_count(self.h, stream)

@@ -104,8 +104,7 @@ def _run_oracle(U0, n, steps, pf, rf):
         dts.append((dt, ch))
         U, bad = O.mhd_step(U, n, 3, dx, dt, ch, recon=1)
         assert bad == 0
-        I = O.interior(U, n, 3)
-        near.append(I)
+        near.append(O.interior(U, n, 3).copy())  # before the floors act on U
         counts.append(O.mhd_floor(U, n, 3, pf, rf))
     U = O.fill_periodic(U, n, 3)
     nxt = O.dt_ch(O.mhd_max_speed(U, n, 3, dx), dx, 3, 0.3)
