@@ -275,140 +275,4 @@ __global__ void __launch_bounds__(AMR_BLOCK) k_diagnostics(const DevPatch *patch
     }
 }
 
-// ---- Refinement criterion, Eq. (RefCrit) (Section 4) ----------------------
-// chi = sqrt(sum_d (D+ - D-)^2 / sum_d (|D+| + |D-| + eps sigma_ref,d)^2) of
-// sigma(U) over the active dimensions, D+ = sigma(c + e_d) - sigma(c),
-// D- = sigma(c) - sigma(c - e_d), sigma_ref,d = |sigma(c + e_d)| +
-// 2|sigma(c)| + |sigma(c - e_d)|; a cell is tagged when chi > chi_r.
-//
-// The decision runs in float32 first.  With every sigma value carried to
-// within k u |sigma| (u = 2^-24; k = 1 for rho and E, 4 for E/rho, 8 for
-// B^2/rho), each difference, sum and reference value of direction d is off
-// by at most (k + 2.02) u R_d (R_d the exact sigma_ref,d), and the
-// denominator's eps R_d term bounds the relative error of every ratio; so
-// Q = num - chi_r^2 den is known to within M (num + chi_r^2 den), M from
-// TagFilter::margin.  A cell whose float32 Q clears twice that margin takes
-// the sign of Q; every other cell (and every cell whose values leave the
-// range where the bound holds, 1e-12 <= R_d <= 1e17 and no denormal
-// intermediate) is decided by the float64 path, written as explicitly
-// rounded operations in the order of the definition, whose chi is the
-// definition's to the last bit.
-struct TagPatch {
-    int n[3];
-    int pad;
-    long long base;
-};
-
-template <int KIND>
-__device__ __forceinline__ double tag_sigma64(const double *U, long long us, long long c)
-{
-    if (KIND == 0) return U[c];
-    if (KIND == 1) return U[4 * us + c];
-    if (KIND == 2) {
-        const double b0 = U[5 * us + c], b1 = U[6 * us + c], b2 = U[7 * us + c];
-        return __ddiv_rn(__dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)), __dmul_rn(b2, b2)), U[c]);
-    }
-    return __ddiv_rn(U[4 * us + c], U[c]);
-}
-
-// sigma in float32 from float32-rounded inputs; ok = false where an
-// intermediate would lose its relative accuracy (denormal or overflow).
-template <int KIND>
-__device__ __forceinline__ float tag_sigma32(const double *U, long long us, long long c, bool &ok)
-{
-    if (KIND == 0) return (float)U[c];
-    if (KIND == 1) return (float)U[4 * us + c];
-    const float r = (float)U[c];
-    ok &= r >= 1e-30f && r <= 1e30f;
-    if (KIND == 2) {
-        const float b0 = (float)U[5 * us + c], b1 = (float)U[6 * us + c], b2 = (float)U[7 * us + c];
-        const float bb = __fadd_rn(__fadd_rn(__fmul_rn(b0, b0), __fmul_rn(b1, b1)), __fmul_rn(b2, b2));
-        ok &= bb == 0.0f || (bb >= 1e-30f && bb <= 1e30f);
-        return __fdiv_rn(bb, r);
-    }
-    const float e = (float)U[4 * us + c];
-    ok &= e == 0.0f || (fabsf(e) >= 1e-30f && fabsf(e) <= 1e30f);
-    return __fdiv_rn(e, r);
-}
-
-template <int KIND, bool CHI>
-__global__ void __launch_bounds__(AMR_BLOCK) k_tag(const TagPatch *tp, BlockMap map, int ndim, const double *U,
-                                                    long long us, double eps, double chi_r, float eps32,
-                                                    float c2, float filt, unsigned char *tags,
-                                                    unsigned long long *counts, double *chi)
-{
-    int bi;
-    long long t;
-    map.locate(bi, t);
-    const TagPatch P = tp[bi];
-    const long long cnt = (long long)P.n[0] * P.n[1] * P.n[2];
-    bool tag = false;
-    if (t < cnt) {
-        const long long row = t / P.n[0];
-        const int x = (int)(t - row * P.n[0]);
-        const int y = (int)(row % P.n[1]), z = (int)(row / P.n[1]);
-        const int g1 = ndim > 1 ? AMR_NG : 0, g2 = ndim > 2 ? AMR_NG : 0;
-        const long long N0 = P.n[0] + 2 * AMR_NG, N1 = P.n[1] + 2 * g1;
-        const long long c = P.base + ((long long)(z + g2) * N1 + (y + g1)) * N0 + (x + AMR_NG);
-        const long long st[3] = {1, N0, N0 * N1};
-        bool decided = false;
-        if (!CHI) {
-            bool ok = true;
-            const float s0 = tag_sigma32<KIND>(U, us, c, ok);
-            float num = 0.0f, den = 0.0f;
-            for (int d = 0; d < ndim; ++d) {
-                const float sp = tag_sigma32<KIND>(U, us, c + st[d], ok);
-                const float sm = tag_sigma32<KIND>(U, us, c - st[d], ok);
-                const float a = sp - s0, b = s0 - sm, d2 = a - b;
-                const float R = fabsf(sp) + 2.0f * fabsf(s0) + fabsf(sm);
-                ok &= R >= 1e-12f && R <= 1e17f;
-                const float T = fabsf(a) + fabsf(b) + eps32 * R;
-                num += d2 * d2;
-                den += T * T;
-            }
-            const float Q = num - c2 * den;
-            if (ok && fabsf(Q) > filt * (num + c2 * den)) {
-                tag = Q > 0.0f;
-                decided = true;
-            }
-        }
-        if (!decided) {
-            const double s0 = tag_sigma64<KIND>(U, us, c);
-            double num = 0.0, den = 0.0;
-            for (int d = 0; d < ndim; ++d) {
-                const double sp = tag_sigma64<KIND>(U, us, c + st[d]);
-                const double sm = tag_sigma64<KIND>(U, us, c - st[d]);
-                const double dp = __dsub_rn(sp, s0), dm = __dsub_rn(s0, sm);
-                const double a = __dsub_rn(dp, dm);
-                num = __dadd_rn(num, __dmul_rn(a, a));
-                const double ref = __dadd_rn(__dadd_rn(fabs(sp), __dmul_rn(2.0, fabs(s0))), fabs(sm));
-                const double b = __dadd_rn(__dadd_rn(fabs(dp), fabs(dm)), __dmul_rn(eps, ref));
-                den = __dadd_rn(den, __dmul_rn(b, b));
-            }
-            const double x_ = __dsqrt_rn(__ddiv_rn(num, den));
-            if (CHI) chi[c] = x_;
-            tag = x_ > chi_r;
-        }
-        tags[c] = tag ? 1 : 0;
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, tag);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(counts + bi, (unsigned long long)__popc(m));
-}
-
-// The float32 decision margin 2M of k_tag for sigma kind `kind` (infinite
-// where the bound is too loose to be worth a float32 pass: eps or chi_r
-// below 1e-3, or M above 0.05).
-struct TagFilter {
-    static double margin(int kind, double eps, double chi_r)
-    {
-        const double u = 5.9604644775390625e-08;  // 2^-24
-        if (!(eps >= 1e-3) || !(chi_r >= 1e-3)) return INFINITY;
-        const double k = kind == 2 ? 8.0 : (kind == 3 ? 4.0 : 1.0), ck = k + 2.02;
-        const double eT = (ck + eps * (k + 3.02)) * u / eps + 1.01 * u;
-        const double eden = 2.0 * eT + eT * eT + 3.0 * u;
-        const double M = ck * u / (eps * chi_r) + ck * ck * u * u / (eps * eps * chi_r * chi_r) + eden + 5.02 * u;
-        return M > 0.05 ? INFINITY : 2.0 * M;
-    }
-};
-
 } // namespace ctu

@@ -20,6 +20,7 @@
 
 #include "ctu.h"
 #include "amr_ops.cuh"
+#include "tag_ops.cuh"
 #include "ctu_launch.h"
 
 using namespace ctu;
@@ -113,10 +114,11 @@ struct ctu_ctx {
     std::map<std::array<int, 3>, std::array<int, 2>> tune;
     bool tuning = false;  // steps of ctu_autotune leave the flux registers alone
     // device copies of the level-operator descriptors (prolong, restrict,
-    // reflux, tag), re-uploaded when a call brings different contents
-    std::vector<char> opcache[4];
-    void *optab[4] = {nullptr, nullptr, nullptr, nullptr};
-    size_t opcap[4] = {0, 0, 0, 0};
+    // reflux, tiled and flat tagging), re-uploaded when a call brings
+    // different contents
+    std::vector<char> opcache[5];
+    void *optab[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t opcap[5] = {0, 0, 0, 0, 0};
     int device = 0;
     // patch list cache (caller order) and its device table (grouped order)
     std::vector<ctu_patch> hpatch;
@@ -881,6 +883,23 @@ ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *r
     return CTU_OK;
 }
 
+}  // extern "C"
+
+template <int K>
+static void launch_tag(const OpTable &T, TagArgs a, bool tile, cudaStream_t s)
+{
+    a.tp = (const TagPatch *)T.desc;
+    a.map = T.map;
+    if (tile)
+        k_tag_tile<K><<<T.nblocks, TAG_TILE, 0, s>>>(a);
+    else if (a.chi)
+        k_tag_flat<K, true><<<T.nblocks, AMR_BLOCK, 0, s>>>(a);
+    else
+        k_tag_flat<K, false><<<T.nblocks, AMR_BLOCK, 0, s>>>(a);
+}
+
+extern "C" {
+
 ctu_status ctu_tag(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patch *patches, int npatch, int sigma,
                    double eps, double chi_r, unsigned char *tags, int64_t *d_count, double *chi, void *stream)
 {
@@ -889,49 +908,67 @@ ctu_status ctu_tag(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patc
     if (!(eps >= 0.0 && eps < INFINITY) || !(chi_r >= 0.0 && chi_r < INFINITY)) return CTU_EINVAL;
     ctu_status st = validate_patches(ctx, stride, patches, npatch);
     if (st != CTU_OK) return st;
-    std::vector<TagPatch> tp(npatch);
-    std::vector<long long> blocks(npatch);
+    // patches of a plane width >= 16 in 2-D and 3-D march in tiles; the rest
+    // (and every patch when chi is written) take one cell per thread
+    std::vector<TagPatch> tp[2];
+    std::vector<long long> blocks[2];
+    const int nd = ctx->cfg.ndim;
     for (int i = 0; i < npatch; ++i) {
-        for (int d = 0; d < 3; ++d) tp[i].n[d] = patches[i].n[d];
-        tp[i].pad = 0;
-        tp[i].base = patches[i].base;
-        const long long c = (long long)patches[i].n[0] * patches[i].n[1] * patches[i].n[2];
-        blocks[i] = (c + AMR_BLOCK - 1) / AMR_BLOCK;
+        TagPatch q;
+        for (int d = 0; d < 3; ++d) q.n[d] = patches[i].n[d];
+        q.slot = i;
+        q.base = patches[i].base;
+        const bool tile = !chi && nd >= 2 && q.n[0] >= 16;
+        const long long b = tile ? (long long)((q.n[0] + TAG_TX - 1) / TAG_TX) * ((q.n[1] + TAG_TY - 1) / TAG_TY) *
+                                       ((q.n[2] + TAG_SZ - 1) / TAG_SZ)
+                                 : ((long long)q.n[0] * q.n[1] * q.n[2] + AMR_BLOCK - 1) / AMR_BLOCK;
+        tp[tile].push_back(q);
+        blocks[tile].push_back(b);
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // per-patch counts: the caller's array, else the context's scratch word
+    // per-patch counts: the caller's array, else the context's scratch
     unsigned long long *cnt = (unsigned long long *)d_count;
     if (!cnt) {
         st = ensure_tag_scratch(ctx, npatch);
         if (st != CTU_OK) return st;
         cnt = ctx->dtagcnt;
     }
-    OpTable T;
-    st = op_table(ctx, 3, tp.data(), sizeof(TagPatch) * npatch, npatch, blocks.data(), s, &T);
-    if (st != CTU_OK) return st;
-    CTU_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * npatch, s));
-    const double f = TagFilter::margin(sigma, eps, chi_r);
-    const float filt = f < 1.0 ? (float)f : INFINITY, eps32 = (float)eps, c2 = (float)(chi_r * chi_r);
-    const TagPatch *D = (const TagPatch *)T.desc;
-    const int nd = ctx->cfg.ndim;
-    if (ctx->prof) ctx->prof->mark("tag", s);
-#define CTU_TAG_LAUNCH(K)                                                                                         \
-    do {                                                                                                         \
-        if (chi)                                                                                                 \
-            k_tag<K, true><<<T.nblocks, AMR_BLOCK, 0, s>>>(D, T.map, nd, U, stride, eps, chi_r, eps32, c2, filt, \
-                                                           tags, cnt, chi);                                      \
-        else                                                                                                     \
-            k_tag<K, false><<<T.nblocks, AMR_BLOCK, 0, s>>>(D, T.map, nd, U, stride, eps, chi_r, eps32, c2,     \
-                                                            filt, tags, cnt, chi);                               \
-    } while (0)
-    switch (sigma) {
-    case CTU_TAG_DENSITY: CTU_TAG_LAUNCH(0); break;
-    case CTU_TAG_ENERGY: CTU_TAG_LAUNCH(1); break;
-    case CTU_TAG_B2_OVER_RHO: CTU_TAG_LAUNCH(2); break;
-    default: CTU_TAG_LAUNCH(3); break;
+    OpTable T[2];
+    for (int g = 0; g < 2; ++g) {
+        T[g].nblocks = 0;
+        if (tp[g].empty()) continue;
+        st = op_table(ctx, 3 + g, tp[g].data(), sizeof(TagPatch) * tp[g].size(), (int)tp[g].size(),
+                      blocks[g].data(), s, &T[g]);
+        if (st != CTU_OK) return st;
     }
-#undef CTU_TAG_LAUNCH
+    CTU_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * npatch, s));
+    const double f = tag_margin(sigma, eps, chi_r);
+    TagArgs a;
+    a.ndim = nd;
+    a.U = U;
+    a.us = stride;
+    a.eps = eps;
+    a.chi_r = chi_r;
+    a.eps32 = (float)eps;
+    a.c2 = (float)(chi_r * chi_r);
+    a.filt = f < 1.0 ? (float)f : INFINITY;
+    a.tags = tags;
+    a.counts = cnt;
+    a.chi = chi;
+    if (ctx->prof) ctx->prof->mark("tag", s);
+    int launches = 0;
+    for (int g = 0; g < 2; ++g) {
+        if (T[g].nblocks == 0) continue;
+        switch (sigma) {
+        case CTU_TAG_DENSITY: launch_tag<0>(T[g], a, g == 1, s); break;
+        case CTU_TAG_ENERGY: launch_tag<1>(T[g], a, g == 1, s); break;
+        case CTU_TAG_B2_OVER_RHO: launch_tag<2>(T[g], a, g == 1, s); break;
+        default: launch_tag<3>(T[g], a, g == 1, s); break;
+        }
+        ++launches;
+    }
     if (ctx->prof) ctx->prof->mark(nullptr, s);
+    ctx->last_launches = launches;
     CTU_CUDA(cudaGetLastError());
     return CTU_OK;
 }

@@ -3,8 +3,9 @@ or_tag: chi bit-exact (the float64 path is the definition in its order with
 IEEE division and square root), tags and per-patch counts bit-exact also on
 the float32-filtered path -- at the paper's threshold and at the median chi,
 where half of the cells sit near the threshold -- for every sigma kind, over
-batches of ragged patches in 1, 2 and 3 dimensions, the full 256^3 blast and
-the whole finest level of the AMR hierarchy."""
+batches of ragged patches in 1, 2 and 3 dimensions (both launch shapes: the
+tiled march and one cell per thread), the full 256^3 blast and the whole
+finest level of the AMR hierarchy."""
 import numpy as np
 import pytest
 
@@ -71,8 +72,10 @@ def _check(blocks, shapes, ndim, kind, eps, chi_r, want_chi):
 
 
 def _blocks3(seed):
-    big = W.mhd_blast_3d(32, seed=seed)
-    shapes = [[21, 13, 11], [8, 8, 8], [32, 32, 32], [5, 17, 9], [1, 1, 1]]
+    big = W.mhd_blast_3d(48, seed=seed)
+    # tiled (x width >= 16) and one-cell-per-thread patches, ragged tiles
+    # in x and y, several z segments with a ragged last one
+    shapes = [[21, 13, 11], [8, 8, 8], [48, 48, 48], [5, 17, 9], [1, 1, 1], [40, 9, 37], [16, 8, 16]]
     blocks = [np.ascontiguousarray(big[:, :n[2] + 8, :n[1] + 8, :n[0] + 8]) for n in shapes]
     return blocks, shapes
 
