@@ -100,6 +100,12 @@ def lib():
         L.or_restrict.restype = None
         L.or_restrict.argtypes = [P, I3, P, I3, I3, I3, I3, I, I]
         L.or_diagnostics.restype = None
+        LP = ctypes.POINTER(ctypes.c_long)
+        for f in ("or_copy_boxes", "or_pack_boxes", "or_unpack_boxes"):
+            getattr(L, f).restype = None
+        L.or_copy_boxes.argtypes = [P, ctypes.c_long, P, ctypes.c_long, I3, LP, LP, I, I]
+        L.or_pack_boxes.argtypes = [P, P, ctypes.c_long, I3, LP, I, I]
+        L.or_unpack_boxes.argtypes = [P, ctypes.c_long, P, I3, LP, I, I]
         L.or_tag.restype = ctypes.c_long
         L.or_tag.argtypes = [P, I3, I, I, D, D, P, ctypes.POINTER(ctypes.c_ubyte)]
         L.or_diagnostics.argtypes = [P, I3, I, P, P]
@@ -138,6 +144,44 @@ def restrict(Uc, nc, Uf, nf, lo, hi, origin, ratio, ndim):
     lib().or_restrict(_dp(Uc), _i3(nc), _dp(Ufc), _i3(nf), _i3(lo), _i3(hi), _i3(origin), int(ratio),
                       int(ndim))
     return Uc
+
+
+def _boxes(boxes):
+    """boxes: dicts with dn, sn, lo, hi, shift (3 ints each), dbase, sbase."""
+    nb = len(boxes)
+    b = np.zeros((max(1, nb), 16), dtype=np.int32)
+    db = np.zeros(max(1, nb), dtype=np.int64)
+    sb = np.zeros(max(1, nb), dtype=np.int64)
+    for i, x in enumerate(boxes):
+        b[i, 0:3], b[i, 3:6], b[i, 6:9], b[i, 9:12], b[i, 12:15] = x["dn"], x["sn"], x["lo"], x["hi"], x["shift"]
+        db[i], sb[i] = x["dbase"], x["sbase"]
+    LP = ctypes.POINTER(ctypes.c_long)
+    return (b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), db.ctypes.data_as(LP), sb.ctypes.data_as(LP),
+            (b, db, sb))
+
+
+def copy_boxes(Ud, Us, boxes, ndim):
+    """Same-level ghost exchange copy (or_copy_boxes) between float64 pools
+    [9][stride] (Ud may be Us)."""
+    assert Ud.dtype == np.float64 and Ud.flags.c_contiguous and Us.flags.c_contiguous
+    bp, dp, sp, keep = _boxes(boxes)
+    lib().or_copy_boxes(_dp(Ud), Ud.shape[1], _dp(Us), Us.shape[1], bp, dp, sp, len(boxes), int(ndim))
+
+
+def box_cells(b):
+    return int(np.prod([h - l for l, h in zip(b["lo"], b["hi"])]))
+
+
+def pack_boxes(Us, boxes, ndim):
+    buf = np.zeros(NVAR * sum(box_cells(b) for b in boxes))
+    bp, dp, sp, keep = _boxes(boxes)
+    lib().or_pack_boxes(_dp(buf), _dp(Us), Us.shape[1], bp, sp, len(boxes), int(ndim))
+    return buf
+
+
+def unpack_boxes(Ud, buf, boxes, ndim):
+    bp, dp, sp, keep = _boxes(boxes)
+    lib().or_unpack_boxes(_dp(Ud), Ud.shape[1], _dp(np.ascontiguousarray(buf)), bp, dp, len(boxes), int(ndim))
 
 
 def tag(U, n, ndim, kind, eps, chi_r):

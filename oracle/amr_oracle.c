@@ -2,7 +2,8 @@
  * CTU step (test infrastructure): coarse-to-fine prolongation with time
  * interpolation, Eq. (prolong) and Eq. (intalpha); restriction, Eq.
  * (avgdown); reflux, Eq. (fluxcorr) and Eq. (addreflux) of Mignone et al.
- * (2012), Section 4; the refinement criterion, Eq. (RefCrit) of Section 4
+ * (2012), Section 4; the same-level ghost exchange (copy, pack, unpack);
+ * the refinement criterion, Eq. (RefCrit) of Section 4
  * (second-derivative error norm); and the conservation diagnostics of a
  * patch (conserved totals, max |div B|).  Cartesian geometry: the volume coordinate of a
  * direction is the coordinate itself and a cell's volume the product of its
@@ -236,4 +237,67 @@ long or_tag(const double *U, const int n[3], int ndim, int kind, double eps, dou
                 count += tag[c];
             }
     return count;
+}
+
+/* Same-level ghost exchange, the copy step of Section 4's level advance (a
+ * patch's ghost cells that lie over a sibling's interior take the sibling's
+ * values).  Box b copies the cells x in [lo, hi) of the destination patch
+ * (interior coordinates, ghosts included) from cell x + shift of the source
+ * patch, all nine variables.  Boxes are given as 16 ints each:
+ *   dn[3], sn[3], lo[3], hi[3], shift[3], pad
+ * with the pool offsets of the destination and source patches in dbase[b],
+ * sbase[b].  Udst and Usrc may be the same pool. */
+void or_copy_boxes(double *Ud, long dstride, const double *Us, long sstride, const int *box, const long *dbase,
+                   const long *sbase, int nbox, int ndim)
+{
+    for (int b = 0; b < nbox; ++b) {
+        const int *B = box + 16 * b;
+        const int *dn = B, *sn = B + 3, *lo = B + 6, *hi = B + 9, *sh = B + 12;
+        for (int z = lo[2]; z < hi[2]; ++z)
+            for (int y = lo[1]; y < hi[1]; ++y)
+                for (int x = lo[0]; x < hi[0]; ++x) {
+                    const long di = dbase[b] + cell(dn, ndim, x, y, z);
+                    const long si = sbase[b] + cell(sn, ndim, x + sh[0], y + sh[1], z + sh[2]);
+                    for (int q = 0; q < NV; ++q) Ud[q * dstride + di] = Us[q * sstride + si];
+                }
+    }
+}
+
+/* Packing for an exchange between processes: the source cells of every box,
+ * box after box, each as [q][z][y][x] over the box's extent; unpacking
+ * writes such a buffer into the destination cells. */
+void or_pack_boxes(double *buf, const double *Us, long sstride, const int *box, const long *sbase, int nbox,
+                   int ndim)
+{
+    long o = 0;
+    for (int b = 0; b < nbox; ++b) {
+        const int *B = box + 16 * b;
+        const int *sn = B + 3, *lo = B + 6, *hi = B + 9, *sh = B + 12;
+        const long ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2], nc = ex * ey * ez;
+        for (int q = 0; q < NV; ++q)
+            for (int z = lo[2]; z < hi[2]; ++z)
+                for (int y = lo[1]; y < hi[1]; ++y)
+                    for (int x = lo[0]; x < hi[0]; ++x)
+                        buf[o + q * nc + ((long)(z - lo[2]) * ey + (y - lo[1])) * ex + (x - lo[0])] =
+                            Us[q * sstride + sbase[b] + cell(sn, ndim, x + sh[0], y + sh[1], z + sh[2])];
+        o += NV * nc;
+    }
+}
+
+void or_unpack_boxes(double *Ud, long dstride, const double *buf, const int *box, const long *dbase, int nbox,
+                     int ndim)
+{
+    long o = 0;
+    for (int b = 0; b < nbox; ++b) {
+        const int *B = box + 16 * b;
+        const int *dn = B, *lo = B + 6, *hi = B + 9;
+        const long ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2], nc = ex * ey * ez;
+        for (int q = 0; q < NV; ++q)
+            for (int z = lo[2]; z < hi[2]; ++z)
+                for (int y = lo[1]; y < hi[1]; ++y)
+                    for (int x = lo[0]; x < hi[0]; ++x)
+                        Ud[q * dstride + dbase[b] + cell(dn, ndim, x, y, z)] =
+                            buf[o + q * nc + ((long)(z - lo[2]) * ey + (y - lo[1])) * ex + (x - lo[0])];
+        o += NV * nc;
+    }
 }
