@@ -378,7 +378,10 @@ def run_amr(args):
     spherical shock; one coarse step = level 0 once, level 1 twice, level 2
     four times (dt_l = dt_0 / 2^l, common c_h), all seven batched ctu_step
     calls captured in one CUDA graph; flux-register windows on both sides of
-    every coarse-fine interface.  dt_0 is fixed before timing from ctu_dt on
+    every coarse-fine interface; on one GPU, before every level step the
+    ghosts are filled (prolongation from the parent level in time, then the
+    same-level exchange from siblings) and at every synchronisation the
+    parent is refluxed and restricted.  dt_0 is fixed before timing from ctu_dt on
     every level (dt_0 = min_l 2^l dt_l).  With N > 1 ranks every rank builds
     the same hierarchy and advances its shard of each level (patches split by
     cell count, Section 4); the ranks agree on dt_0 (one scalar reduction) and
@@ -475,7 +478,17 @@ def run_amr(args):
     # (reflux first, so that a correction landing on a covered coarse cell is
     # overwritten by the restriction), and the interface registers zeroed
     ops = None
+    xch, xunc = {}, {}
     if world == 1 and not args.no_level_ops:
+        from paper_1110_0740_gb300 import exchange as X
+        # same-level ghost exchange: ghosts over a sibling's interior (or a
+        # periodic image of one) are copied from it, after the prolongation
+        for lev, lv in enumerate(L):
+            specs = [((o[2], o[1], o[0]), (sz_, sz_, sz_), p_[2]) for (o, sz_), p_ in zip(lv["origins"], lv["patches"])]
+            xb = X.plan(specs, [128 * 2 ** lev] * 3, [True] * 3, 3)
+            xunc[lev] = X.uncovered(xb, len(specs), [sp[1] for sp in specs], 3)
+            if xb:
+                xch[lev] = ctu.make_copy_boxes(xb)
         ops = {}
         for lev in range(1, len(L)):
             pb, rb, fs = [], [], []
@@ -483,20 +496,9 @@ def run_amr(args):
                 parent, o_zyx, sz = L[lev]["footprints"][fi]
                 cn, cdx, cbase, _ = L[lev - 1]["patches"][parent]
                 o = [o_zyx[2], o_zyx[1], o_zyx[0]]
-                for d in range(3):  # the six ghost slabs
-                    for lo_d, hi_d in ((-4, 0), (n[d], n[d] + 4)):
-                        lo_, hi_ = [], []
-                        for e in range(3):
-                            if e == d:
-                                lo_.append(lo_d)
-                                hi_.append(hi_d)
-                            elif e < d:
-                                lo_.append(0)
-                                hi_.append(n[e])
-                            else:
-                                lo_.append(-4)
-                                hi_.append(n[e] + 4)
-                        pb.append(dict(fn=n, cn=cn, fbase=base, cbase=cbase, lo=lo_, hi=hi_, origin=o, ratio=2))
+                # the ghost cells no sibling covers: the coarse-fine boundary
+                for lo_, hi_ in xunc[lev][fi]:
+                    pb.append(dict(fn=n, cn=cn, fbase=base, cbase=cbase, lo=lo_, hi=hi_, origin=o, ratio=2))
                 rb.append(dict(fn=n, cn=cn, fbase=base, cbase=cbase, lo=o, hi=[o[e] + sz for e in range(3)],
                                origin=o, ratio=2))
                 for d in range(3):
@@ -521,12 +523,19 @@ def run_amr(args):
         r0, r1 = reg_range[lev]
         reg[r0:r1].zero_()
 
+    def exchange(lev, U):
+        if lev in xch:
+            ctxs[lev].copy(U, U.shape[1], U, U.shape[1], xch[lev], stream=stream)
+
     def ghosts(lev, coarse_old, coarse_new, alpha, fine):
         ctxs[lev].prolong(coarse_old, coarse_new, coarse_old.shape[1], alpha, fine, fine.shape[1], ops[lev][0],
                           stream=stream)
+        exchange(lev, fine)
 
     def coarse_step():
         # recursive subcycling: l0, then for each l1 substep its two l2 substeps
+        if ops:
+            exchange(0, A[0])
         lstep(0, A[0], B[0])
         for k in range(2):
             s1, d1 = (A[1], B[1]) if k == 0 else (B[1], A[1])
@@ -587,8 +596,8 @@ def run_amr(args):
             kern[f"l{lev}_{k_}"] = t_
         c.profile(False)
     launches = sum(c.launches() for c in ctxs[:1]) + 2 * ctxs[1].launches() + 4 * ctxs[2].launches()
-    if ops:  # prolongations 2 + 4, refluxes and restrictions 2 + 1 each
-        launches += 6 + 3 + 3
+    if ops:  # prolongations 2 + 4, refluxes and restrictions 2 + 1 each, exchanges 1 + 2 + 4
+        launches += 6 + 3 + 3 + sum(2 ** lev for lev in xch)
     if rank == 0:
         line = {"metric": METRIC, "value": upd / (ms * 1e-3), "unit": "cell-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -602,8 +611,11 @@ def run_amr(args):
                            "cell_updates_per_coarse_step": upd, "windows_rank0": sum(len(w) for w in wins),
                            "rank0_share_of_updates": my_upd / upd,
                            "parallelism": f"patch shards x{world}" if world > 1 else "single GPU",
-                           "level_ops": "prolongation of fine ghosts before every fine substep, reflux + "
-                                        "restriction at every synchronisation" if ops else "none",
+                           "level_ops": "ghost fill before every level step: same-level exchange from "
+                                        "siblings, prolongation (in time) of the remaining coarse-fine ghosts "
+                                        "on levels 1, 2; reflux + restriction at every synchronisation"
+                                        if ops else "none",
+                           "exchange_boxes_per_level": {lev: len(b) for lev, b in xch.items()},
                            "tiles_xw_seg": tiles,
                            "l2_flush": "inputs larger than L2"},
                 "gpu_launches": launches * args.steps, "clocks": clk,

@@ -182,6 +182,43 @@ ctu_status ctu_step_next_dt(ctu_ctx *ctx, const double *U_in, double *U_out, int
  * resets the count.  Synchronises the stream.  *count is a host int64. */
 ctu_status ctu_floor_count(ctu_ctx *ctx, int64_t *count, void *stream);
 
+/* ---- Same-level ghost exchange (Section 4, level advance) ---------------
+ * A patch's ghost cells that lie over the interior of a sibling patch (or a
+ * periodic image of one) take the sibling's values; a box lists such cells.
+ * Box b covers the destination cells x in [lo, hi) -- interior coordinates
+ * of the destination patch, ghosts included (-4 .. n+3 on active
+ * dimensions; 0 .. 1 on inactive ones) -- and reads source cell x + shift
+ * of the source patch (within its ghosted extent).  All nine variables are
+ * copied. */
+typedef struct {
+    int32_t dn[3];    /* destination patch interior extent */
+    int32_t sn[3];    /* source patch interior extent */
+    int32_t lo[3];    /* destination cells [lo, hi) */
+    int32_t hi[3];
+    int32_t shift[3]; /* source cell = destination cell + shift */
+    int32_t pad;
+    int64_t dbase;    /* pool offset of the destination patch's first ghost cell */
+    int64_t sbase;    /* pool offset of the source patch's first ghost cell */
+} ctu_copy_box;
+
+/* Copy every box from U_src into U_dst (pools of stride sstride / dstride;
+ * they may be the same pool, but no cell a box writes may be read by any
+ * box of the same call).  Errors: CTU_EINVAL when a box leaves its patch's
+ * ghosted extent or a patch leaves its pool.  Enqueues on `stream`; the
+ * first call with a new box list uploads it (synchronises). */
+ctu_status ctu_copy(ctu_ctx *ctx, double *U_dst, int64_t dstride, const double *U_src, int64_t sstride,
+                    const ctu_copy_box *boxes, int nbox, void *stream);
+
+/* For an exchange between processes: ctu_pack writes the source cells of
+ * every box, box after box, each as float64 [q][z][y][x] over the box's
+ * extent, into the device buffer buf (9 * sum of box cells doubles);
+ * ctu_unpack writes such a buffer into the destination cells.  Only the
+ * source (pack) or destination (unpack) fields of a box are used. */
+ctu_status ctu_pack(ctu_ctx *ctx, double *buf, const double *U_src, int64_t sstride,
+                    const ctu_copy_box *boxes, int nbox, void *stream);
+ctu_status ctu_unpack(ctu_ctx *ctx, double *U_dst, int64_t dstride, const double *buf,
+                      const ctu_copy_box *boxes, int nbox, void *stream);
+
 /* ---- Refinement tagging (Section 4, refinement criteria) ----------------
  * The quantity sigma(U) the criterion is taken of: density (rho, or D in
  * relativistic MHD), total energy density E, B^2/rho, E/rho. */

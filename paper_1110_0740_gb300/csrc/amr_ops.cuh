@@ -275,4 +275,48 @@ __global__ void __launch_bounds__(AMR_BLOCK) k_diagnostics(const DevPatch *patch
     }
 }
 
+// Same-level ghost exchange: one thread per destination cell of a box, all
+// nine variables; MODE 0 copies pool to pool, 1 packs the source cells into
+// a buffer ([q][z][y][x] per box, boxes one after another), 2 unpacks a
+// buffer into the destination cells.  HBM-bound: 72 B read and 72 B written
+// per cell.
+struct CopyDesc {
+    int dn[3], sn[3], lo[3], ext[3], shift[3], pad;
+    long long dbase, sbase, boff;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(AMR_BLOCK) k_copy(const CopyDesc *boxes, BlockMap map, int ndim, double *Ud,
+                                                     long long ds, const double *Us, long long ss)
+{
+    int bi;
+    long long t;
+    map.locate(bi, t);
+    const CopyDesc B = boxes[bi];
+    const long long nc = (long long)B.ext[0] * B.ext[1] * B.ext[2];
+    if (t >= nc) return;
+    const unsigned t32 = (unsigned)t, row = t32 / (unsigned)B.ext[0];
+    const unsigned zz = row / (unsigned)B.ext[1];
+    const int x = B.lo[0] + (int)(t32 - row * (unsigned)B.ext[0]);
+    const int y = B.lo[1] + (int)(row - zz * (unsigned)B.ext[1]), z = B.lo[2] + (int)zz;
+    if (MODE == 0 || MODE == 1) {
+        const AmrGeom gs{{B.sn[0], B.sn[1], B.sn[2]}, ndim};
+        const long long si = B.sbase + gs.cell(x + B.shift[0], y + B.shift[1], z + B.shift[2]);
+        if (MODE == 0) {
+            const AmrGeom gd{{B.dn[0], B.dn[1], B.dn[2]}, ndim};
+            const long long di = B.dbase + gd.cell(x, y, z);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) Ud[q * ds + di] = Us[q * ss + si];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) Ud[B.boff + q * nc + t] = Us[q * ss + si];
+        }
+    } else {
+        const AmrGeom gd{{B.dn[0], B.dn[1], B.dn[2]}, ndim};
+        const long long di = B.dbase + gd.cell(x, y, z);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Ud[q * ds + di] = Us[B.boff + q * nc + t];
+    }
+}
+
 } // namespace ctu

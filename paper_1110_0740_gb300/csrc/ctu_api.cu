@@ -114,11 +114,11 @@ struct ctu_ctx {
     std::map<std::array<int, 3>, std::array<int, 2>> tune;
     bool tuning = false;  // steps of ctu_autotune leave the flux registers alone
     // device copies of the level-operator descriptors (prolong, restrict,
-    // reflux, tiled and flat tagging), re-uploaded when a call brings
-    // different contents
-    std::vector<char> opcache[5];
-    void *optab[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    size_t opcap[5] = {0, 0, 0, 0, 0};
+    // reflux, tiled and flat tagging, exchange copy / pack / unpack),
+    // re-uploaded when a call brings different contents
+    std::vector<char> opcache[8];
+    void *optab[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t opcap[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int device = 0;
     // patch list cache (caller order) and its device table (grouped order)
     std::vector<ctu_patch> hpatch;
@@ -969,6 +969,99 @@ ctu_status ctu_tag(ctu_ctx *ctx, const double *U, int64_t stride, const ctu_patc
     }
     if (ctx->prof) ctx->prof->mark(nullptr, s);
     ctx->last_launches = launches;
+    CTU_CUDA(cudaGetLastError());
+    return CTU_OK;
+}
+
+// Checks every box against its patches and pools (mode 0 both sides, 1 the
+// source, 2 the destination) and builds the device descriptors.
+static ctu_status copy_table(ctu_ctx *ctx, int mode, const ctu_copy_box *boxes, int nbox, int64_t dstride,
+                             int64_t sstride, cudaStream_t s, OpTable *T)
+{
+    if (!boxes || nbox <= 0 || nbox > (1 << 24)) return CTU_EINVAL;
+    const int nd = ctx->cfg.ndim;
+    std::vector<CopyDesc> D(nbox);
+    std::vector<long long> blocks(nbox);
+    long long off = 0;
+    for (int i = 0; i < nbox; ++i) {
+        const ctu_copy_box &b = boxes[i];
+        CopyDesc &c = D[i];
+        long long cells = 1, dc = 0, sc = 0;
+        for (int d = 0; d < 3; ++d) {
+            c.dn[d] = b.dn[d];
+            c.sn[d] = b.sn[d];
+            c.lo[d] = b.lo[d];
+            c.ext[d] = b.hi[d] - b.lo[d];
+            c.shift[d] = b.shift[d];
+            if (c.ext[d] < 1) return CTU_EINVAL;
+            cells *= c.ext[d];
+            const int g = d < nd ? 4 : 0;
+            if (mode != 1) {
+                if (b.dn[d] < 1 || (d >= nd && b.dn[d] != 1) || b.lo[d] < -g || b.hi[d] > b.dn[d] + g) return CTU_EINVAL;
+            }
+            if (mode != 2) {
+                if (b.sn[d] < 1 || (d >= nd && b.sn[d] != 1) || b.lo[d] + b.shift[d] < -g ||
+                    b.hi[d] + b.shift[d] > b.sn[d] + g)
+                    return CTU_EINVAL;
+            }
+        }
+        if (cells >= (1LL << 31)) return CTU_EINVAL;
+        c.pad = 0;
+        c.dbase = b.dbase;
+        c.sbase = b.sbase;
+        c.boff = off;
+        off += 9 * cells;
+        if (mode != 1) {
+            if (!patch_extent(ctx, b.dn, &dc) || b.dbase < 0 || b.dbase + dc > dstride) return CTU_EINVAL;
+        }
+        if (mode != 2) {
+            if (!patch_extent(ctx, b.sn, &sc) || b.sbase < 0 || b.sbase + sc > sstride) return CTU_EINVAL;
+        }
+        blocks[i] = (cells + AMR_BLOCK - 1) / AMR_BLOCK;
+    }
+    return op_table(ctx, 5 + mode, D.data(), sizeof(CopyDesc) * nbox, nbox, blocks.data(), s, T);
+}
+
+ctu_status ctu_copy(ctu_ctx *ctx, double *U_dst, int64_t dstride, const double *U_src, int64_t sstride,
+                    const ctu_copy_box *boxes, int nbox, void *stream)
+{
+    if (!ctx || !U_dst || !U_src) return CTU_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpTable T;
+    ctu_status st = copy_table(ctx, 0, boxes, nbox, dstride, sstride, s, &T);
+    if (st != CTU_OK) return st;
+    if (ctx->prof) ctx->prof->mark("exchange", s);
+    k_copy<0><<<T.nblocks, AMR_BLOCK, 0, s>>>((const CopyDesc *)T.desc, T.map, ctx->cfg.ndim, U_dst, dstride, U_src,
+                                             sstride);
+    if (ctx->prof) ctx->prof->mark(nullptr, s);
+    CTU_CUDA(cudaGetLastError());
+    return CTU_OK;
+}
+
+ctu_status ctu_pack(ctu_ctx *ctx, double *buf, const double *U_src, int64_t sstride, const ctu_copy_box *boxes,
+                    int nbox, void *stream)
+{
+    if (!ctx || !buf || !U_src) return CTU_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpTable T;
+    ctu_status st = copy_table(ctx, 1, boxes, nbox, 0, sstride, s, &T);
+    if (st != CTU_OK) return st;
+    k_copy<1><<<T.nblocks, AMR_BLOCK, 0, s>>>((const CopyDesc *)T.desc, T.map, ctx->cfg.ndim, buf, 0, U_src,
+                                             sstride);
+    CTU_CUDA(cudaGetLastError());
+    return CTU_OK;
+}
+
+ctu_status ctu_unpack(ctu_ctx *ctx, double *U_dst, int64_t dstride, const double *buf, const ctu_copy_box *boxes,
+                      int nbox, void *stream)
+{
+    if (!ctx || !buf || !U_dst) return CTU_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpTable T;
+    ctu_status st = copy_table(ctx, 2, boxes, nbox, dstride, 0, s, &T);
+    if (st != CTU_OK) return st;
+    k_copy<2><<<T.nblocks, AMR_BLOCK, 0, s>>>((const CopyDesc *)T.desc, T.map, ctx->cfg.ndim, U_dst, dstride, buf,
+                                             0);
     CTU_CUDA(cudaGetLastError());
     return CTU_OK;
 }

@@ -48,6 +48,24 @@ class ctu_flux_window(ctypes.Structure):
                 ("dst", ctypes.c_int64)]
 
 
+class ctu_copy_box(ctypes.Structure):
+    _fields_ = [("dn", ctypes.c_int32 * 3), ("sn", ctypes.c_int32 * 3), ("lo", ctypes.c_int32 * 3),
+                ("hi", ctypes.c_int32 * 3), ("shift", ctypes.c_int32 * 3), ("pad", ctypes.c_int32),
+                ("dbase", ctypes.c_int64), ("sbase", ctypes.c_int64)]
+
+
+def make_copy_boxes(boxes):
+    """boxes: dicts with dn, sn, lo, hi, shift, dbase, sbase (exchange.plan)."""
+    arr = (ctu_copy_box * len(boxes))()
+    for i, b in enumerate(boxes):
+        for k in ("dn", "sn", "lo", "hi", "shift"):
+            getattr(arr[i], k)[:] = [int(v) for v in b[k]]
+        arr[i].pad = 0
+        arr[i].dbase = int(b["dbase"])
+        arr[i].sbase = int(b["sbase"])
+    return arr
+
+
 class ctu_level_box(ctypes.Structure):
     _fields_ = [("fn", ctypes.c_int32 * 3), ("cn", ctypes.c_int32 * 3), ("fbase", ctypes.c_int64),
                 ("cbase", ctypes.c_int64), ("lo", ctypes.c_int32 * 3), ("hi", ctypes.c_int32 * 3),
@@ -118,6 +136,9 @@ def _lib():
         L.ctu_fill_periodic.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp]
         L.ctu_status_sync.argtypes = [vp, vp]
         L.ctu_floor_count.argtypes = [vp, ctypes.POINTER(i64), vp]
+        L.ctu_copy.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctu_copy_box), i32, vp]
+        L.ctu_pack.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctu_copy_box), i32, vp]
+        L.ctu_unpack.argtypes = [vp, vp, i64, vp, ctypes.POINTER(ctu_copy_box), i32, vp]
         L.ctu_tag.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, i32, dbl, dbl, vp, vp, vp, vp]
         L.ctu_destroy.argtypes = [vp]
         L.ctu_destroy.restype = None
@@ -293,6 +314,21 @@ def ctu_tag(ctx, U, stride, patches, sigma, eps, chi_r, tags, d_count=None, chi=
                           _ptr(chi) if chi is not None else None, _stream(stream)), "ctu_tag")
 
 
+def ctu_copy(ctx, U_dst, dstride, U_src, sstride, boxes, stream=None):
+    _check(_lib().ctu_copy(ctx, _ptr(U_dst), int(dstride), _ptr(U_src), int(sstride), boxes, len(boxes),
+                           _stream(stream)), "ctu_copy")
+
+
+def ctu_pack(ctx, buf, U_src, sstride, boxes, stream=None):
+    _check(_lib().ctu_pack(ctx, _ptr(buf), _ptr(U_src), int(sstride), boxes, len(boxes), _stream(stream)),
+           "ctu_pack")
+
+
+def ctu_unpack(ctx, U_dst, dstride, buf, boxes, stream=None):
+    _check(_lib().ctu_unpack(ctx, _ptr(U_dst), int(dstride), _ptr(buf), boxes, len(boxes), _stream(stream)),
+           "ctu_unpack")
+
+
 def ctu_floor_count(ctx, stream=None):
     """Cells the floors changed since the last call (resets; synchronises)."""
     c = ctypes.c_int64(0)
@@ -380,6 +416,15 @@ class Ctx:
 
     def tag(self, U, stride, patches, sigma, eps, chi_r, tags, d_count=None, chi=None, stream=None):
         ctu_tag(self.h, U, stride, patches, sigma, eps, chi_r, tags, d_count, chi, stream)
+
+    def copy(self, U_dst, dstride, U_src, sstride, boxes, stream=None):
+        ctu_copy(self.h, U_dst, dstride, U_src, sstride, boxes, stream)
+
+    def pack(self, buf, U_src, sstride, boxes, stream=None):
+        ctu_pack(self.h, buf, U_src, sstride, boxes, stream)
+
+    def unpack(self, U_dst, dstride, buf, boxes, stream=None):
+        ctu_unpack(self.h, U_dst, dstride, buf, boxes, stream)
 
     def floor_count(self, stream=None):
         return ctu_floor_count(self.h, stream)

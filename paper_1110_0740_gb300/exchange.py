@@ -113,3 +113,53 @@ def torch_sendrecv(like):
         return rb
 
     return sr
+
+
+def _subtract(r, c):
+    """Box r minus box c as disjoint boxes ((lo, hi) lists of 3 ints)."""
+    lo, hi = list(r[0]), list(r[1])
+    if any(max(lo[d], c[0][d]) >= min(hi[d], c[1][d]) for d in range(3)):
+        return [r]
+    out = []
+    for d in range(3):
+        if lo[d] < c[0][d]:
+            a, b = list(lo), list(hi)
+            b[d] = c[0][d]
+            out.append((a, b))
+            lo[d] = c[0][d]
+        if hi[d] > c[1][d]:
+            a, b = list(lo), list(hi)
+            a[d] = c[1][d]
+            out.append((a, b))
+            hi[d] = c[1][d]
+    return out
+
+
+def ghost_slabs(n, ndim):
+    """The ghost shell of a patch as 2 ndim disjoint boxes (patch
+    coordinates): along d, the two slabs of 4 layers, spanning the interior
+    in the dimensions before d and the ghosted extent in those after it."""
+    g = [GHOST if d < ndim else 0 for d in range(3)]
+    out = []
+    for d in range(ndim):
+        for lo_d, hi_d in ((-GHOST, 0), (n[d], n[d] + GHOST)):
+            lo = [lo_d if e == d else (0 if e < d else -g[e]) for e in range(3)]
+            hi = [hi_d if e == d else (n[e] if e < d else n[e] + g[e]) for e in range(3)]
+            out.append((lo, hi))
+    return out
+
+
+def uncovered(boxes, npatch, sizes, ndim):
+    """Per patch, the ghost cells no exchange box writes, as disjoint boxes
+    (patch coordinates): the coarse-fine and physical boundary, left to
+    prolongation and boundary conditions.  sizes[i] is patch i's n."""
+    cover = [[] for _ in range(npatch)]
+    for b in boxes:
+        cover[b["dst"]].append((b["lo"], b["hi"]))
+    out = []
+    for i in range(npatch):
+        rest = ghost_slabs(sizes[i], ndim)
+        for c in cover[i]:
+            rest = [p for r in rest for p in _subtract(r, c)]
+        out.append(rest)
+    return out

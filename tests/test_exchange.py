@@ -213,3 +213,38 @@ def test_two_gloo_ranks_exchange_like_one_process():
     assert sorted(got) == list(range(len(parts)))
     for i, (lo, n) in enumerate(parts):
         assert np.array_equal(got[i], _wrapped(big, lo, n, 3)), i
+
+
+def _mask(n, ndim, boxes):
+    g = [G if d < ndim else 0 for d in range(3)]
+    m = np.zeros([n[2] + 2 * g[2], n[1] + 2 * g[1], n[0] + 2 * g[0]], dtype=np.int32)
+    for lo, hi in boxes:
+        m[lo[2] + g[2]:hi[2] + g[2], lo[1] + g[1]:hi[1] + g[1], lo[0] + g[0]:hi[0] + g[0]] += 1
+    return m
+
+
+def test_exchange_and_uncovered_boxes_tile_the_ghost_shell():
+    """On every patch of the AMR hierarchy's finest level (non-periodic) and
+    of a periodic decomposition, the exchange boxes and the uncovered boxes
+    together cover each ghost cell exactly once and no interior cell."""
+    from paper_1110_0740_gb300 import workloads as W
+    H = W.amr_hierarchy(seed=2, base=32, target=60)
+    cases = []
+    lv = H["levels"][2]
+    cases.append(([((o[2], o[1], o[0]), (s, s, s), 0) for (o, s) in lv["origins"]], [128] * 3, [False] * 3, 3))
+    domain, parts, _ = _setup(3, 0)
+    cases.append(([(lo, n, 0) for lo, n in parts], domain, [True] * 3, 3))
+    cases.append(([(lo, n, 0) for lo, n in parts], domain, [False, True, False], 3))
+    domain2, parts2, _ = _setup(2, 0)
+    cases.append(([(lo, n, 0) for lo, n in parts2], domain2, [False] * 3, 2))
+    for specs, dom, per, ndim in cases:
+        boxes = X.plan(specs, dom, per, ndim)
+        unc = X.uncovered(boxes, len(specs), [s[1] for s in specs], ndim)
+        for i, (lo, n, _) in enumerate(specs):
+            m = _mask(n, ndim, [(b["lo"], b["hi"]) for b in boxes if b["dst"] == i] + unc[i])
+            inner = np.zeros_like(m, dtype=bool)
+            g = [G if d < ndim else 0 for d in range(3)]
+            inner[g[2]:g[2] + n[2], g[1]:g[1] + n[1], g[0]:g[0] + n[0]] = True
+            assert np.all(m[inner] == 0) and np.all(m[~inner] == 1), (i, per)
+        if all(per[:ndim]):
+            assert all(not u for u in unc)
