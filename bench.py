@@ -306,6 +306,13 @@ def run_ours(args):
                             "derived: 152 SMs x 2 FP64 lanes x 2 x 2070 MHz (GB300 nominal 1.25 TF)"),
             "flops_per_launch": f_top, "kernel_avg_ms": top_avg,
             "kernels_ms_per_step": {k: v[0] / res["K"] for k, v in kern.items()}}
+    # the FMA-throughput microbenchmark of the same pipe, beside the derived peak
+    try:
+        fma = ctu.ctu_fma_peak(not mixed, (1 << 16) if mixed else (1 << 12)) / 1e12
+        roof["fma_measured"] = {"tflops": fma, "frac": achieved / fma,
+                                "what": "ctu_fma_peak: 8 independent FMA chains per thread, 16 x 256 threads per SM"}
+    except ctu.CtuError:
+        roof["fma_measured"] = None
     step_ms = sum(v[0] for v in kern.values()) / res["K"]
     roof["step"] = {"flops": sum(fl.values()), "achieved_tflops": sum(fl.values()) / (step_ms * 1e-3) / 1e12,
                     "frac": sum(fl.values()) / (step_ms * 1e-3) / 1e12 / peak_tf}

@@ -385,6 +385,15 @@ ctu_status ctu_profile(ctu_ctx *ctx, int enable);
  * time in ms and its launch count.  Returns 0 when profiling is off. */
 int ctu_profile_read(ctu_ctx *ctx, int i, const char **name, double *total_ms, long long *launches);
 
+/* FMA-throughput microbenchmark of the non-tensor pipes on the current
+ * device (a measurement aid; the paper has no counterpart): every thread of
+ * a grid of 16 blocks of 256 threads per SM runs 8 independent chains of
+ * `iters` fused multiply-adds in float32 (fp64 = 0) or float64 (fp64 = 1);
+ * *flops_per_s = 2 x FMAs / CUDA-event time of the timed launch (after one
+ * shorter warm-up launch).  Synchronises the stream; allocates a small
+ * scratch array. */
+ctu_status ctu_fma_peak(int fp64, int iters, double *flops_per_s, void *stream);
+
 /* ---- Allocation-free step ------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory, such as a host framework whose caching

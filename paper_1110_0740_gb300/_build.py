@@ -10,7 +10,8 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "libctu.so"
-SOURCES = ["ctu_api.cu", "ctu_f64.cu", "ctu_f32.cu", "ctu_f32i.cu", "ctu_sr32.cu", "ctu_noalloc.cu"]
+SOURCES = ["ctu_api.cu", "ctu_f64.cu", "ctu_f32.cu", "ctu_f32i.cu", "ctu_sr32.cu", "ctu_noalloc.cu",
+           "fma_peak.cu"]
 # The float32 stages of the mixed paths divide and take square roots with the
 # approximate hardware forms (<= 2 ulp) and flush float32 denormals; float64
 # arithmetic is unaffected by these flags.

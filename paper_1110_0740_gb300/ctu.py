@@ -136,6 +136,7 @@ def _lib():
         L.ctu_fill_periodic.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp]
         L.ctu_status_sync.argtypes = [vp, vp]
         L.ctu_floor_count.argtypes = [vp, ctypes.POINTER(i64), vp]
+        L.ctu_fma_peak.argtypes = [i32, i32, ctypes.POINTER(dbl), vp]
         L.ctu_copy.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctu_copy_box), i32, vp]
         L.ctu_pack.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctu_copy_box), i32, vp]
         L.ctu_unpack.argtypes = [vp, vp, i64, vp, ctypes.POINTER(ctu_copy_box), i32, vp]
@@ -312,6 +313,13 @@ def ctu_tag(ctx, U, stride, patches, sigma, eps, chi_r, tags, d_count=None, chi=
     _check(_lib().ctu_tag(ctx, _ptr(U), int(stride), patches, len(patches), int(sigma), float(eps),
                           float(chi_r), _ptr(tags), _ptr(d_count) if d_count is not None else None,
                           _ptr(chi) if chi is not None else None, _stream(stream)), "ctu_tag")
+
+
+def ctu_fma_peak(fp64, iters=1 << 16, stream=None):
+    """Measured FMA throughput (flop/s) of the float32 or float64 pipe."""
+    v = ctypes.c_double(0.0)
+    _check(_lib().ctu_fma_peak(int(bool(fp64)), int(iters), ctypes.byref(v), _stream(stream)), "ctu_fma_peak")
+    return v.value
 
 
 def ctu_copy(ctx, U_dst, dstride, U_src, sstride, boxes, stream=None):
