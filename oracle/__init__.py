@@ -70,6 +70,8 @@ def lib():
         L.or_mhd_riemann.argtypes = [P, P, D, D, P]
         L.or_mhd_char_predict.restype = None
         L.or_mhd_char_predict.argtypes = [P, D, D, D, I, I, P, P]
+        L.or_mhd_char_predict_dx.restype = None
+        L.or_mhd_char_predict_dx.argtypes = [P, D, D, D, D, I, I, P, P]
         L.or_mhd_prim2cons.restype = None
         L.or_mhd_prim2cons.argtypes = [P, D, P]
         L.or_mhd_cons2prim.restype = I
@@ -355,12 +357,14 @@ def mhd_riemann(VL, VR, gamma, ch):
     return F
 
 
-def mhd_char_predict(vs, gamma, ch, dtdx, recon, upwind=0):
+def mhd_char_predict(vs, gamma, ch, dtdx, recon, upwind=0, dx=0.0):
+    """Normal predictor of one cell (or_mhd_char_predict_dx); recon 0 MC,
+    1 PPM, 2 MinMod, 3 harmonic, 4 Van Albada, 5 WENO3 (uses dx)."""
     vs = np.ascontiguousarray(vs, dtype=np.float64).reshape(5, NVAR)
     Vp = np.zeros(NVAR)
     Vm = np.zeros(NVAR)
-    lib().or_mhd_char_predict(_dp(vs), float(gamma), float(ch), float(dtdx), int(recon),
-                              int(upwind), _dp(Vp), _dp(Vm))
+    lib().or_mhd_char_predict_dx(_dp(vs), float(gamma), float(ch), float(dtdx), float(dx), int(recon),
+                                 int(upwind), _dp(Vp), _dp(Vm))
     return Vp, Vm
 
 

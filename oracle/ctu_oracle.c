@@ -25,7 +25,10 @@
  *   - PPM, MC limiter, MinMod, parabolic limiter:
  *                                  Section 3.2, Eq. (ppm1), (MClim), (minmod),
  *                                  (ppm_parabolic_lim)
- *   - linear reconstruction:       Section 3.2, Eq. (Linear)
+ *   - linear reconstruction:       Section 3.2, Eq. (Linear) with the MC,
+ *                                  MinMod, harmonic (harmonic_lim) or Van
+ *                                  Albada (vanalbada_lim) slope
+ *   - improved third-order WENO:   Section 3.2, Eq. (WENO3), (WENO3a)
  *   - flux-register contribution:  Section 4.2, Eq. (fluxcorr)
  *   - optional density and pressure floors on the updated state: a reading
  *     (the paper fixes none), or_mhd_floor
@@ -440,18 +443,43 @@ static double mc_slope(double dm, double dp)
     return minmod(0.5 * (dp + dm), 2.0 * minmod(dm, dp));
 }
 
+/* Limited slope of the linear reconstruction from the backward and forward
+ * undivided differences: recon 0 MC, Eq. (MClim); 2 MinMod, Eq. (minmod);
+ * 3 harmonic mean, Eq. (harmonic_lim); 4 Van Albada, Eq. (vanalbada_lim). */
+static double lin_slope(double dm, double dp, int recon)
+{
+    if (recon == 2)
+        return minmod(dm, dp);
+    if (recon == 3)
+        return dp * dm > 0.0 ? 2.0 * dp * dm / (dp + dm) : 0.0;
+    if (recon == 4)
+        return dp * dm > 0.0 ? dp * dm * (dp + dm) / (dp * dp + dm * dm) : 0.0;
+    return mc_slope(dm, dp);
+}
+
 /* Interface values w_(i,+) and w_(i,-) of one characteristic field from the
  * stencil w[0..4] = w_(i,-2) .. w_(i,+2).  recon = 1: PPM, Eq. (ppm1) with
- * the parabolic limiter of Eq. (ppm_parabolic_lim); recon = 0: linear,
- * Eq. (Linear) with the MC limiter. */
-static void reconstruct(const double *w, int recon, double *wp, double *wm)
+ * the parabolic limiter of Eq. (ppm_parabolic_lim); recon = 5: improved
+ * third-order WENO, Eq. (WENO3) with the weights of Eq. (WENO3a), dx the
+ * cell width; otherwise linear, Eq. (Linear), with the slope of lin_slope. */
+static void reconstruct(const double *w, int recon, double dx, double *wp, double *wm)
 {
     double w0 = w[2];
-    double s0 = mc_slope(w[2] - w[1], w[3] - w[2]);
-    if (recon == 0) {
+    if (recon == 5) {
+        double dp = w[3] - w[2], dm = w[2] - w[1];
+        double d2 = (dp - dm) * (dp - dm);
+        double ap = 1.0 + d2 / (dx * dx + dp * dp);
+        double am = 1.0 + d2 / (dx * dx + dm * dm);
+        *wp = w0 + (ap * dp + 0.5 * am * dm) / (2.0 * ap + am);
+        *wm = w0 - (am * dm + 0.5 * ap * dp) / (2.0 * am + ap);
+        return;
+    }
+    if (recon != 1) {
+        double s0 = lin_slope(w[2] - w[1], w[3] - w[2], recon);
         *wp = w0 + 0.5 * s0;
         *wm = w0 - 0.5 * s0;
     } else {
+        double s0 = mc_slope(w[2] - w[1], w[3] - w[2]);
         double sm = mc_slope(w[1] - w[0], w[2] - w[1]);
         double sp = mc_slope(w[3] - w[2], w[4] - w[3]);
         double p = 0.5 * (w0 + w[3]) - (sp - s0) / 6.0;
@@ -495,8 +523,8 @@ static void trace(double wp, double w0, double wm, double nu, int upwind,
  * order.  Outputs the time-centred interface primitives V*_(i,+), V*_(i,-)
  * (local order), including the S_Bx dBn/dx and S_psi dpsi/dx sources.
  */
-void or_mhd_char_predict(const double *vs, double gam, double ch, double dtdx,
-                         int recon, int upwind, double *Vp, double *Vm)
+void or_mhd_char_predict_dx(const double *vs, double gam, double ch, double dtdx, double dx,
+                            int recon, int upwind, double *Vp, double *Vm)
 {
     double lam[NVAR], L[NVAR * NVAR], R[NVAR * NVAR];
     double tp[NVAR], tm[NVAR], rp[NVAR], rm[NVAR];
@@ -514,7 +542,7 @@ void or_mhd_char_predict(const double *vs, double gam, double ch, double dtdx,
                 s += L[k * NVAR + q] * vs[l * NVAR + q];
             w[l] = s;
         }
-        reconstruct(w, recon, &rp[k], &rm[k]);
+        reconstruct(w, recon, dx, &rp[k], &rm[k]);
         trace(rp[k], w[2], rm[k], lam[k] * dtdx, upwind, &tp[k], &tm[k]);
     }
     for (q = 0; q < NVAR; q++) {
@@ -545,6 +573,14 @@ void or_mhd_char_predict(const double *vs, double gam, double ch, double dtdx,
         Vp[q] += 0.5 * dtdx * src[q];
         Vm[q] += 0.5 * dtdx * src[q];
     }
+}
+
+/* or_mhd_char_predict_dx for the reconstructions that do not use the cell
+ * width (all but WENO3). */
+void or_mhd_char_predict(const double *vs, double gam, double ch, double dtdx,
+                         int recon, int upwind, double *Vp, double *Vm)
+{
+    or_mhd_char_predict_dx(vs, gam, ch, dtdx, 0.0, recon, upwind, Vp, Vm);
 }
 
 /* ------------------------------------------------------------------ */
@@ -712,7 +748,7 @@ int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                     for (l = 0; l < 5; l++)
                         for (q = 0; q < NVAR; q++)
                             vs[l * NVAR + q] = V[PERM[d][q] * nc + id + (l - 2) * st];
-                    or_mhd_char_predict(vs, gam, ch, dt / h[d], recon, upwind, Vp, Vm);
+                    or_mhd_char_predict_dx(vs, gam, ch, dt / h[d], h[d], recon, upwind, Vp, Vm);
                     /* transverse increments L^n_d' = -(F_(d',+) - F_(d',-))/dx_d' */
                     for (q = 0; q < NVAR; q++)
                         T[q] = 0.0;
