@@ -94,3 +94,27 @@ def test_travelling_eigenmode_converges(recon, floor_):
         errs.append(np.abs(O.interior(U, n, 2) - U0).sum() / 1e-6 / (N * N))
     order = np.log2(errs[1] / errs[2])
     assert order > floor_, (errs, order)
+
+
+@pytest.mark.parametrize("recon", [MINMOD, HARMONIC, VANALBADA, WENO3])
+def test_sod_against_the_exact_solution(recon):
+    """Sod's problem (B = 0) in 1-D: L1(rho) against Toro's exact solution
+    decreases at about first order (the shock and contact are captured) and
+    is small at N = 200, for every reconstruction."""
+    from paper_1110_0740_gb300 import workloads as W
+    g = 1.4
+    errs = []
+    for N in (50, 100, 200):
+        n = [N, 1, 1]
+        x = (np.arange(N) + 0.5) / N
+        rho = np.where(x < 0.5, 1.0, 0.125)[None, None, :]
+        p = np.where(x < 0.5, 1.0, 0.1)[None, None, :]
+        z = np.zeros_like(rho)
+        U = np.zeros(O.shape(n, 1))
+        O.interior(U, n, 1)[:] = W.ideal_cons([rho, z, z, z, p, z, z, z, z], g)
+        U, t, _ = O.mhd_run(U, n, 1, [1.0 / N, 1.0, 1.0], 0, 0.8, gamma=g, recon=recon, bc="outflow", t_end=0.2)
+        ex = O.euler_sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), g, (x - 0.5) / t)[:, 0]
+        errs.append(np.abs(O.interior(U, n, 1)[0].ravel() - ex).mean())
+    order = np.log2(errs[0] / errs[-1]) / 2
+    assert 0.7 < order < 1.4, errs
+    assert errs[-1] < 6e-3, errs
