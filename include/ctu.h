@@ -56,7 +56,19 @@ typedef enum {
 
 enum { CTU_MHD = 0, CTU_SRMHD = 1 };
 enum { CTU_EOS_IDEAL = 0, CTU_EOS_TM = 1 };
-enum { CTU_LINEAR_MC = 0, CTU_PPM = 1 };
+/* reconstruction (Section 3.2) of the characteristic variables:
+ *   CTU_LINEAR_MC        linear, Eq. (Linear), MC slope Eq. (MClim)
+ *   CTU_PPM              PPM, Eq. (ppm1) + parabolic limiter (ppm_parabolic_lim)
+ *   CTU_LINEAR_MINMOD    linear with the MinMod slope, Eq. (minmod)
+ *   CTU_LINEAR_HARMONIC  linear with the harmonic-mean slope, Eq. (harmonic_lim)
+ *   CTU_LINEAR_VANALBADA linear with the Van Albada slope, Eq. (vanalbada_lim)
+ *   CTU_WENO3            improved third-order WENO, Eq. (WENO3), (WENO3a); its
+ *                        weights take the characteristic variables of the
+ *                        Roe-Balsara normalised left eigenvectors
+ * The last four: ideal MHD in CTU_FP64 or CTU_MIXED (CTU_MIXED_IFACE64 and
+ * ctu_step_noalloc return CTU_EUNSUPPORTED). */
+enum { CTU_LINEAR_MC = 0, CTU_PPM = 1, CTU_LINEAR_MINMOD = 2, CTU_LINEAR_HARMONIC = 3, CTU_LINEAR_VANALBADA = 4,
+       CTU_WENO3 = 5 };
 enum { CTU_CHAR_TRACE = 0, CTU_MUSCL_HANCOCK = 1 };
 enum { CTU_HLLD = 0, CTU_HLL = 1 };
 /* precision:
@@ -91,7 +103,7 @@ typedef struct {
     int eos;          /* CTU_EOS_IDEAL */
     double gamma;     /* ratio of specific heats, > 1 */
     int ndim;         /* 1, 2 or 3 active dimensions; v_z, B_z always carried */
-    int recon;        /* CTU_LINEAR_MC or CTU_PPM (Section 3.2) */
+    int recon;        /* CTU_LINEAR_MC, CTU_PPM, ... (above; Section 3.2) */
     int predictor;    /* CTU_CHAR_TRACE (MHD) or CTU_MUSCL_HANCOCK (SRMHD) */
     int riemann;      /* CTU_HLLD (MHD) or CTU_HLL (SRMHD) */
     int precision;    /* CTU_FP64, CTU_MIXED or CTU_MIXED_IFACE64 (above) */

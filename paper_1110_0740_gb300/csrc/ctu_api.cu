@@ -345,6 +345,7 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.gm1f = (float)(ctx->cfg.gamma - 1.0);
     a.glm_alpha = ctx->cfg.glm_alpha;
     a.upwind = ctx->cfg.trace_mode == CTU_TRACE_UPWIND;
+    a.limiter = ctx->cfg.recon;
     a.U = Uin;
     a.Uout = Uout;
     a.ustride = stride;
@@ -366,7 +367,8 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
     LaunchInfo li;
     li.groups = ctx->groups.data();
     li.ngroups = (int)ctx->groups.size();
-    li.recon = ctx->cfg.recon == CTU_PPM;
+    const int r = ctx->cfg.recon;
+    li.recon = r == CTU_PPM ? RECON_PPM : (r == CTU_LINEAR_MC ? RECON_MC : (r == CTU_WENO3 ? RECON_WENO3 : RECON_LIN));
     li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
     li.physics = ctx->cfg.physics == CTU_SRMHD ? PH_SR : PH_MHD;
     li.scratch = ctx->scratch;
@@ -378,11 +380,13 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
 namespace ctu {
 template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
-    return li.physics == PH_SR ? launch_step_sr<double>(a, li, s) : launch_step_impl<double, 1>(a, li, s);
+    if (li.physics == PH_SR) return launch_step_sr<double>(a, li, s);
+    return li.recon >= RECON_LIN ? launch_step_var<double, 1>(a, li, s) : launch_step_impl<double, 1>(a, li, s);
 }
 template <> int launch_step<float>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<float>(a, li, s);
+    if (li.recon >= RECON_LIN) return launch_step_var<float, 0>(a, li, s);
     return li.iface64 ? launch_step_impl<float, 1>(a, li, s) : launch_step_impl<float, 0>(a, li, s);
 }
 } // namespace ctu
@@ -405,7 +409,7 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
     if (cfg->eos != CTU_EOS_IDEAL) return CTU_EUNSUPPORTED;
     if (!(cfg->gamma > 1.0)) return CTU_EINVAL;
     if (cfg->ndim < 1 || cfg->ndim > 3) return CTU_EINVAL;
-    if (cfg->recon != CTU_LINEAR_MC && cfg->recon != CTU_PPM) return CTU_EINVAL;
+    if (cfg->recon < CTU_LINEAR_MC || cfg->recon > CTU_WENO3) return CTU_EINVAL;
     if (cfg->predictor != CTU_CHAR_TRACE && cfg->predictor != CTU_MUSCL_HANCOCK) return CTU_EINVAL;
     if (cfg->riemann != CTU_HLLD && cfg->riemann != CTU_HLL) return CTU_EINVAL;
     // implemented combinations: MHD with characteristic tracing + HLLD;
@@ -418,6 +422,9 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
         return CTU_EUNSUPPORTED;
     if (cfg->precision != CTU_FP64 && cfg->precision != CTU_MIXED && cfg->precision != CTU_MIXED_IFACE64)
         return CTU_EINVAL;
+    // the other reconstructions are built for the FP64 and CTU_MIXED paths
+    if (cfg->recon != CTU_LINEAR_MC && cfg->recon != CTU_PPM && cfg->precision == CTU_MIXED_IFACE64)
+        return CTU_EUNSUPPORTED;
     if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return CTU_EINVAL;
     if (!(cfg->glm_alpha >= 0.0)) return CTU_EINVAL;
     if (cfg->nghost != 4) return CTU_EINVAL;

@@ -70,6 +70,7 @@ struct StepArgs {
     float gamf, gm1f;      // Gamma, Gamma-1 in float
     double glm_alpha;
     int upwind;
+    int limiter;           // linear reconstruction's slope (CTU_LINEAR_*), RECON_LIN kernels
     const double *U;       // pool in
     double *Uout;          // pool out
     long long ustride;     // pool variable stride
@@ -435,7 +436,8 @@ __device__ __forceinline__ unsigned int trace_cell_t(const StepArgs &a, const De
     R pl[NV], ml[NV], pg[NV], mg[NV];
     unsigned int f = 0;
     if (PHYS == PH_MHD) {
-        char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind != 0, pl, ml);
+        char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind != 0, a.limiter,
+                             PPM == RECON_WENO3 ? R(P.dx[D] * P.dx[D]) : R(0), pl, ml);
     } else {
         double U0[NV];
         const long long gi = P.base + (c - P.soff);

@@ -132,7 +132,16 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
 // MHD: PPM or MC-linear characteristic tracing.
 template <class R, int IF64> int launch_step_impl(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
-    return li.recon ? launch_step_t<PH_MHD, R, 1, IF64>(a, li, s) : launch_step_t<PH_MHD, R, 0, IF64>(a, li, s);
+    return li.recon == RECON_PPM ? launch_step_t<PH_MHD, R, RECON_PPM, IF64>(a, li, s)
+                                 : launch_step_t<PH_MHD, R, RECON_MC, IF64>(a, li, s);
+}
+
+// MHD with the other reconstructions of Section 3.2: linear with the MinMod,
+// harmonic or Van Albada slope, or improved WENO3.
+template <class R, int IF64> int launch_step_var(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
+{
+    return li.recon == RECON_WENO3 ? launch_step_t<PH_MHD, R, RECON_WENO3, IF64>(a, li, s)
+                                   : launch_step_t<PH_MHD, R, RECON_LIN, IF64>(a, li, s);
 }
 
 // SRMHD: MUSCL-Hancock with MC-linear primitive slopes.

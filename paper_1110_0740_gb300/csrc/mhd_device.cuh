@@ -71,14 +71,53 @@ template <class R> __device__ __forceinline__ R mc_slope(R dm, R dp)
     return dm * dp > R(0) ? copysign(m, dm) : R(0);
 }
 
-// Interface values w_(i,+/-) of one characteristic field from w_(i-2..i+2):
-// PPM, Eq. (ppm1) + parabolic limiter Eq. (ppm_parabolic_lim), or linear,
-// Eq. (Linear).
-template <class R, int PPM>
-__device__ __forceinline__ void reconstruct(R w0m2, R w0m1, R w0, R w0p1, R w0p2, R &wp, R &wm)
+// The linear reconstruction's other slopes (RECON_LIN, chosen at run time
+// by lim = CTU_LINEAR_*): MinMod, Eq. (minmod); harmonic mean, Eq.
+// (harmonic_lim); Van Albada, Eq. (vanalbada_lim).
+template <class R> __device__ __forceinline__ R lin_slope(R dm, R dp, int lim)
 {
+    const R prod = dm * dp;
+    R s;
+    if (lim == 2)
+        s = copysign(fmin(fabs(dm), fabs(dp)), dm);
+    else if (lim == 3)
+        s = R(2) * prod / (dm + dp);
+    else
+        s = prod * (dm + dp) / (dm * dm + dp * dp);
+    return prod > R(0) ? s : R(0);
+}
+
+// Reconstruction kinds of the kernel templates: MC-linear, PPM, linear with a
+// run-time slope, improved WENO3.
+enum { RECON_MC = 0, RECON_PPM = 1, RECON_LIN = 2, RECON_WENO3 = 3 };
+
+// Interface values w_(i,+/-) of one characteristic field from w_(i-2..i+2):
+// PPM, Eq. (ppm1) + parabolic limiter Eq. (ppm_parabolic_lim); linear,
+// Eq. (Linear), with the MC slope or the slope `lim` selects; improved WENO3,
+// Eq. (WENO3) with the weights of Eq. (WENO3a), where eps2 is the square of
+// the cell width in this field's units (the Delta x^2 of Eq. WENO3a divided by
+// the square of the factor that turns this field into the Roe-Balsara
+// characteristic variable).
+template <class R, int PPM>
+__device__ __forceinline__ void reconstruct(R w0m2, R w0m1, R w0, R w0p1, R w0p2, int lim, R eps2, R &wp, R &wm)
+{
+    if (PPM == RECON_WENO3) {
+        const R dp = w0p1 - w0, dm = w0 - w0m1;
+        const R d2 = (dp - dm) * (dp - dm);
+        const R ap = R(1) + d2 / (eps2 + dp * dp);
+        const R am = R(1) + d2 / (eps2 + dm * dm);
+        wp = w0 + (ap * dp + R(0.5) * am * dm) / (R(2) * ap + am);
+        wm = w0 - (am * dm + R(0.5) * ap * dp) / (R(2) * am + ap);
+        return;
+    }
+    if (PPM == RECON_LIN) {
+        const R s = lin_slope(w0 - w0m1, w0p1 - w0, lim);
+        wp = w0 + R(0.5) * s;
+        wm = w0 - R(0.5) * s;
+        return;
+    }
     R s0 = mc_slope(w0 - w0m1, w0p1 - w0);
-    if (!PPM) {
+    if (PPM == RECON_MC) {
         wp = w0 + R(0.5) * s0;
         wm = w0 - R(0.5) * s0;
         return;
@@ -126,8 +165,8 @@ __device__ __forceinline__ void trace(R wp, R w0, R wm, R nu, bool upwind, R &tp
 // reconstruction and tracing are positively homogeneous, so the result is
 // unchanged.
 template <class R, int PPM>
-__device__ __forceinline__ void char_predict(const R (&vs)[5][NV], R gam, R ch, R dtdx, bool upwind,
-                                             R (&Vp)[NV], R (&Vm)[NV])
+__device__ __forceinline__ void char_predict(const R (&vs)[5][NV], R gam, R ch, R dtdx, bool upwind, int lim,
+                                             R dx2, R (&Vp)[NV], R (&Vm)[NV])
 {
     const R rho = vs[2][0], u = vs[2][1], v1c = vs[2][2], v2c = vs[2][3], pc = vs[2][4];
     const R Bn = vs[2][5], B1c = vs[2][6], B2c = vs[2][7];
@@ -197,24 +236,29 @@ __device__ __forceinline__ void char_predict(const R (&vs)[5][NV], R gam, R ch, 
     }
     R rp, rm, tpf_p, tmf_p, tpf_m, tmf_m, tpa_p, tma_p, tpa_m, tma_m;
     R tps_p, tms_p, tps_m, tms_m, tpe, tme, tpg_p, tmg_p, tpg_m, tmg_m;
-    reconstruct<R, PPM>(wf_m[0], wf_m[1], wf_m[2], wf_m[3], wf_m[4], rp, rm);
+    // WENO3's cell-width term in each field's units: the fields above are the
+    // Roe-Balsara characteristic variables times 2 a^2 (fast, slow), 2
+    // (Alfven, GLM) and 1 (entropy)
+    const R e_fs = PPM == RECON_WENO3 ? dx2 * (R(4) * a2 * a2) : R(0);
+    const R e_ag = PPM == RECON_WENO3 ? dx2 * R(4) : R(0);
+    reconstruct<R, PPM>(wf_m[0], wf_m[1], wf_m[2], wf_m[3], wf_m[4], lim, e_fs, rp, rm);
     trace(rp, wf_m[2], rm, (u - cf) * dtdx, upwind, tpf_m, tmf_m);
-    reconstruct<R, PPM>(wa_m[0], wa_m[1], wa_m[2], wa_m[3], wa_m[4], rp, rm);
+    reconstruct<R, PPM>(wa_m[0], wa_m[1], wa_m[2], wa_m[3], wa_m[4], lim, e_ag, rp, rm);
     trace(rp, wa_m[2], rm, (u - ca) * dtdx, upwind, tpa_m, tma_m);
-    reconstruct<R, PPM>(ws_m[0], ws_m[1], ws_m[2], ws_m[3], ws_m[4], rp, rm);
+    reconstruct<R, PPM>(ws_m[0], ws_m[1], ws_m[2], ws_m[3], ws_m[4], lim, e_fs, rp, rm);
     trace(rp, ws_m[2], rm, (u - cs) * dtdx, upwind, tps_m, tms_m);
-    reconstruct<R, PPM>(we[0], we[1], we[2], we[3], we[4], rp, rm);
+    reconstruct<R, PPM>(we[0], we[1], we[2], we[3], we[4], lim, dx2, rp, rm);
     trace(rp, we[2], rm, u * dtdx, upwind, tpe, tme);
-    reconstruct<R, PPM>(ws_p[0], ws_p[1], ws_p[2], ws_p[3], ws_p[4], rp, rm);
+    reconstruct<R, PPM>(ws_p[0], ws_p[1], ws_p[2], ws_p[3], ws_p[4], lim, e_fs, rp, rm);
     trace(rp, ws_p[2], rm, (u + cs) * dtdx, upwind, tps_p, tms_p);
-    reconstruct<R, PPM>(wa_p[0], wa_p[1], wa_p[2], wa_p[3], wa_p[4], rp, rm);
+    reconstruct<R, PPM>(wa_p[0], wa_p[1], wa_p[2], wa_p[3], wa_p[4], lim, e_ag, rp, rm);
     trace(rp, wa_p[2], rm, (u + ca) * dtdx, upwind, tpa_p, tma_p);
-    reconstruct<R, PPM>(wf_p[0], wf_p[1], wf_p[2], wf_p[3], wf_p[4], rp, rm);
+    reconstruct<R, PPM>(wf_p[0], wf_p[1], wf_p[2], wf_p[3], wf_p[4], lim, e_fs, rp, rm);
     trace(rp, wf_p[2], rm, (u + cf) * dtdx, upwind, tpf_p, tmf_p);
     R gpr, gmr, gpl, gml; // reconstructed (untraced) GLM fields at + and - interfaces
-    reconstruct<R, PPM>(wg_m[0], wg_m[1], wg_m[2], wg_m[3], wg_m[4], gpl, gml);
+    reconstruct<R, PPM>(wg_m[0], wg_m[1], wg_m[2], wg_m[3], wg_m[4], lim, e_ag, gpl, gml);
     trace(gpl, wg_m[2], gml, -ch * dtdx, upwind, tpg_m, tmg_m);
-    reconstruct<R, PPM>(wg_p[0], wg_p[1], wg_p[2], wg_p[3], wg_p[4], gpr, gmr);
+    reconstruct<R, PPM>(wg_p[0], wg_p[1], wg_p[2], wg_p[3], wg_p[4], lim, e_ag, gpr, gmr);
     trace(gpr, wg_p[2], gmr, ch * dtdx, upwind, tpg_p, tmg_p);
 
     // recombination with the right eigenvectors (scaled accordingly)

@@ -17,6 +17,7 @@ from . import _build
 CTU_MHD, CTU_SRMHD = 0, 1
 CTU_EOS_IDEAL, CTU_EOS_TM = 0, 1
 CTU_LINEAR_MC, CTU_PPM = 0, 1
+CTU_LINEAR_MINMOD, CTU_LINEAR_HARMONIC, CTU_LINEAR_VANALBADA, CTU_WENO3 = 2, 3, 4, 5
 CTU_CHAR_TRACE, CTU_MUSCL_HANCOCK = 0, 1
 CTU_HLLD, CTU_HLL = 0, 1
 CTU_FP64, CTU_MIXED, CTU_MIXED_IFACE64 = 0, 1, 2
