@@ -35,6 +35,9 @@ N_CELLS = 256
 WORKLOAD = ("3D ideal MHD 256^3 periodic patch, seeded |k|<=8 spectrum in rho/v/B + "
             "100x pressure sphere (r=0.1); PPM + characteristic tracing, HLLD, GLM, CFL 0.3")
 METRIC = "MHD cell-updates/s per CTU step"
+# reconstruction of the characteristic variables (Section 3.2): the workload's
+# PPM, and the other choices the library offers (measured with --recon)
+RECONS = {"ppm": 1, "mc": 0, "minmod": 2, "harmonic": 3, "vanalbada": 4, "weno3": 5}
 # Per-SM unit counts x max SM clock (2070 MHz) x 152 SMs, 2 flops per FMA.
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
@@ -213,7 +216,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def make(prec):
-        c = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3))
+        c = ctu.Ctx(ctu.make_config(ndim=3, recon=RECONS[args.recon], precision=prec, cfl=0.3))
         c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
         if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
@@ -294,7 +297,7 @@ def run_ours(args):
     kern = res["kern"]
     top_name, (top_ms, top_cnt) = max(kern.items(), key=lambda kv: kv[1][0])
     top_avg = top_ms / max(1, top_cnt)
-    fl = kernel_flops(n)
+    fl = kernel_flops(n, args.recon)
     mixed = primary == ctu.CTU_MIXED
     peak_tf = (FP32_PEAK if mixed else FP64_PEAK) / 1e12
     f_top = fl.get(top_name, 0.0)
@@ -321,7 +324,7 @@ def run_ours(args):
     roof["hbm_step"] = {"algorithmic_bytes": nbytes, "achieved_gbs": hbm_achieved,
                         "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
                         "peak_source": f"{src} hbm_gbs"}
-    if mixed:
+    if mixed and args.recon == "ppm":
         roof["precision_split"] = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
 
     # end-to-end through the public API with host buffers
@@ -367,7 +370,9 @@ def run_ours(args):
                 "steps": res["K"], "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if primary == ctu.CTU_MIXED else "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "cells_per_gpu": cells, "patches_per_gpu": 1,
+                "config": {"workload": WORKLOAD if args.recon == "ppm" else
+                           WORKLOAD.replace("PPM", f"{args.recon} reconstruction"),
+                           "recon": args.recon, "cells_per_gpu": cells, "patches_per_gpu": 1,
                            "precision": args.precision, "l2_flush": "inputs (1.3 GB) > L2",
                            "parallelism": f"replicas x{world}", "tiles_xw_seg": tiles.get("xw_seg")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path,
@@ -806,13 +811,13 @@ def _profile_numbers(name):
     return vals
 
 
-def kernel_flops(n):
+def kernel_flops(n, recon="ppm"):
     """Algorithmic flops per launch of each kernel group of one 3-D PPM step
     on an n^3 patch: the oracle's operation counts per interior cell
     (profiles/flops_per_cell.txt, exact-zero operands not counted) times n^3."""
     c = {k: float(v) for k, v in _profile_numbers("flops_per_cell.txt").items()}
     cells = float(n) ** 3
-    sweep = c.get("sweep_per_direction_ppm", 0.0)
+    sweep = c.get("sweep_per_direction_" + ("linear" if recon == "mc" else recon), 0.0)
     # sweeps run z, y, x; the x sweep finishes the update and the next dt
     return {"prim": c.get("prim", 0.0) * cells, "flux1": 3 * c.get("flux1_per_direction", 0.0) * cells,
             "sweep_z": sweep * cells, "sweep_y": sweep * cells,
@@ -886,6 +891,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-level-ops", action="store_true",
                     help="amr: advance the levels without prolongation, restriction and reflux")
+    ap.add_argument("--recon", default="ppm", choices=sorted(RECONS),
+                    help="blast: reconstruction of the characteristic variables (the workload uses ppm)")
     ap.add_argument("--config", default="blast", choices=["blast", "amr", "srmhd", "tag"],
                     help="blast: the 256^3 headline workload; amr: batched AMR level advance; "
                          "srmhd: relativistic jet; tag: refinement tagging of the 256^3 state")

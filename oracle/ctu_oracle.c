@@ -18,7 +18,8 @@
  *                                  Section 3.1, Eq. (transv) with Pi = 0
  *   - CFL time step:               Section 3.1, Eq. (Ca)
  *   - characteristic projection:   Section 3.2, Eq. (char_var)
- *   - upwind characteristic tracing with w_ref = w_(+/-):
+ *   - characteristic tracing, no reference state or the reference states
+ *     w_(+/-), w_(i,0) and Colella-Woodward's with upwind selection:
  *                                  Section 3.2, Eq. (wnorm_predp), (wnorm_predm)
  *   - right-eigenvector recombination with the S_Bx and S_psi sources:
  *                                  Section 3.2 (V*_{i,+/-} expansion)
@@ -499,21 +500,35 @@ static void reconstruct(const double *w, int recon, double dx, double *wp, doubl
 }
 
 /* Characteristic tracing of one field to t^(n+1/2), Eq. (wnorm_predp) and
- * (wnorm_predm) with w_ref = w_(+/-).
- * upwind = 0 (default): no reference state, every field is traced to both
+ * (wnorm_predm), w*_(+/-) = w_ref,(+/-) + beta_(+/-) (traced - w_ref,(+/-)):
+ * mode = 0 (default): no reference state, every field is traced to both
  *   interfaces (beta_+ = beta_- = 1), the choice Section 3.2 recommends for
- *   smooth flows so that waves not reaching an edge still enter its value.
- * upwind = 1: the literal selection beta_+ = [nu > 0], beta_- = [nu < 0]. */
-static void trace(double wp, double w0, double wm, double nu, int upwind,
+ *   smooth flows so that waves not reaching an edge still enter its value;
+ * mode = 1: w_ref = w_(+/-) with the upwind selection beta_+ = [nu > 0],
+ *   beta_- = [nu < 0];
+ * mode = 2: w_ref = w_(i,0), the cell-centre value (Rider et al. 2007),
+ *   upwind selection;
+ * mode = 3: the reference state of Colella & Woodward (1984), the field
+ *   traced with nu_max = max(0, max nu) to the + interface and with
+ *   nu_min = min(0, min nu) to the - interface, upwind selection. */
+static void trace(double wp, double w0, double wm, double nu, int mode, double numax, double numin,
                   double *tp, double *tm)
 {
     double dw = wp - wm;
     double d2w = wp - 2.0 * w0 + wm;
-    *tp = wp;
-    *tm = wm;
-    if (!upwind || nu > 0.0)
+    double rp = wp, rm = wm;
+    if (mode == 2) {
+        rp = w0;
+        rm = w0;
+    } else if (mode == 3) {
+        rp = wp - 0.5 * numax * (dw + d2w * (3.0 - 2.0 * numax));
+        rm = wm - 0.5 * numin * (dw - d2w * (3.0 + 2.0 * numin));
+    }
+    *tp = rp;
+    *tm = rm;
+    if (mode == 0 || nu > 0.0)
         *tp = wp - 0.5 * nu * (dw + d2w * (3.0 - 2.0 * nu));
-    if (!upwind || nu < 0.0)
+    if (mode == 0 || nu < 0.0)
         *tm = wm - 0.5 * nu * (dw - d2w * (3.0 + 2.0 * nu));
 }
 
@@ -534,6 +549,9 @@ void or_mhd_char_predict_dx(const double *vs, double gam, double ch, double dtdx
     int k, l, q;
 
     or_mhd_eigen(V0, gam, ch, lam, L, R);
+    /* the extreme Courant numbers of the seven MHD waves (u -/+ c_f) for the
+     * reference state of trace mode 3 */
+    const double numax = fmax(0.0, lam[6] * dtdx), numin = fmin(0.0, lam[0] * dtdx);
     for (k = 0; k < NVAR; k++) {
         double w[5];
         for (l = 0; l < 5; l++) {
@@ -543,7 +561,7 @@ void or_mhd_char_predict_dx(const double *vs, double gam, double ch, double dtdx
             w[l] = s;
         }
         reconstruct(w, recon, dx, &rp[k], &rm[k]);
-        trace(rp[k], w[2], rm[k], lam[k] * dtdx, upwind, &tp[k], &tm[k]);
+        trace(rp[k], w[2], rm[k], lam[k] * dtdx, upwind, numax, numin, &tp[k], &tm[k]);
     }
     for (q = 0; q < NVAR; q++) {
         double sp = 0.0, sm = 0.0;

@@ -76,6 +76,7 @@ int main()
     for (int i = 0; i < 45 * K; ++i)
         if (scanf("%lf", &S[i]) != 1) return 1;
     double r_riem = 0, r_pred0 = 0, r_pred1 = 0, r_p2c = 0, r_c2p = 0, r_cf = 0;
+    double r_predv[4] = {0, 0, 0, 0};
     for (int k = 0; k < K; ++k) {
         Flop vs[45], VL[9], VR[9], F[9], Vp[9], Vm[9], U[9], V[9];
         for (int i = 0; i < 45; ++i) vs[i] = Flop(S[45 * k + i]);
@@ -92,6 +93,11 @@ int main()
         fc::g = fc::Counts();
         or_mhd_char_predict(vs, Flop(gam), Flop(ch), Flop(dtdx), 1, 0, Vp, Vm);
         r_pred1 += total(fc::g);
+        for (int r = 2; r <= 5; ++r) {
+            fc::g = fc::Counts();
+            or_mhd_char_predict_dx(vs, Flop(gam), Flop(ch), Flop(dtdx), Flop(0.1), r, 0, Vp, Vm);
+            r_predv[r - 2] += total(fc::g);
+        }
         fc::g = fc::Counts();
         or_mhd_prim2cons(VL, Flop(gam), U);
         r_p2c += total(fc::g);
@@ -104,5 +110,7 @@ int main()
     }
     printf("riemann %.2f\npredict_linear %.2f\npredict_ppm %.2f\nprim2cons %.2f\ncons2prim %.2f\ncfast %.2f\n",
            r_riem / K, r_pred0 / K, r_pred1 / K, r_p2c / K, r_c2p / K, r_cf / K);
+    printf("predict_minmod %.2f\npredict_harmonic %.2f\npredict_vanalbada %.2f\npredict_weno3 %.2f\n",
+           r_predv[0] / K, r_predv[1] / K, r_predv[2] / K, r_predv[3] / K);
     return 0;
 }

@@ -10,7 +10,7 @@ the step, in the large-patch limit:
 
   prim        1 x cons2prim
   flux1 (d)   1 x riemann
-  sweep (d)   predict + 2 prim2cons + 2 cons2prim + riemann
+  sweep (d)   predict (per reconstruction) + 2 prim2cons + 2 cons2prim + riemann
               + 18 (half-step transverse increments of two directions,
                     9 x (sub, mul) each) + 18 (U* + dt/2 T) + 18 (flux
                     difference x 1/dx)
@@ -73,8 +73,9 @@ def main():
         c[k] = float(v)
     prim = c["cons2prim"]
     flux1 = c["riemann"]
+    recons = ("ppm", "linear", "minmod", "harmonic", "vanalbada", "weno3")
     sweep = {r: c[f"predict_{r}"] + 2 * c["prim2cons"] + 2 * c["cons2prim"] + c["riemann"] + 54
-             for r in ("ppm", "linear")}
+             for r in recons}
     update = 9 * 2 + 9 * 2 + 1
     nextdt = c["cons2prim"] + 3 * (c["cfast"] + 2)
     lines = ["# oracle flops per call, exact-zero operands not counted (averages over %d stencils"
@@ -84,8 +85,9 @@ def main():
     lines += ["# per interior cell update, large-patch limit, 3-D",
               f"prim {prim:.1f}", f"flux1_per_direction {flux1:.1f}",
               f"sweep_per_direction_ppm {sweep['ppm']:.1f}",
-              f"sweep_per_direction_linear {sweep['linear']:.1f}",
-              f"update {update:.1f}", f"next_dt {nextdt:.1f}",
+              f"sweep_per_direction_linear {sweep['linear']:.1f}"]
+    lines += [f"sweep_per_direction_{r} {sweep[r]:.1f}" for r in recons[2:]]
+    lines += [f"update {update:.1f}", f"next_dt {nextdt:.1f}",
               f"step_total_ppm {prim + 3 * flux1 + 3 * sweep['ppm'] + update + nextdt:.1f}"]
     text = "\n".join(lines) + "\n"
     print(text)
