@@ -88,8 +88,16 @@ enum { CTU_FP64 = 0, CTU_MIXED = 1, CTU_MIXED_IFACE64 = 2 };
  *                    interfaces (no reference state); second order for
  *                    smooth flows with HLLD, the default.
  *   CTU_TRACE_UPWIND the literal upwind selection beta_+ = [nu > 0],
- *                    beta_- = [nu < 0]. */
-enum { CTU_TRACE_ALL = 0, CTU_TRACE_UPWIND = 1 };
+ *                    beta_- = [nu < 0].
+ *   CTU_TRACE_CENTER upwind selection with the reference state w_ref =
+ *                    w_(i,0), the cell-centre value.
+ *   CTU_TRACE_CW84   upwind selection with Colella & Woodward's reference
+ *                    state: the field traced with nu_max = max(0, (u + c_f)
+ *                    dt/dx) to the + and nu_min = min(0, (u - c_f) dt/dx) to
+ *                    the - interface.
+ * The last two: ideal MHD in CTU_FP64 or CTU_MIXED (CTU_MIXED_IFACE64 and
+ * ctu_step_noalloc return CTU_EUNSUPPORTED). */
+enum { CTU_TRACE_ALL = 0, CTU_TRACE_UPWIND = 1, CTU_TRACE_CENTER = 2, CTU_TRACE_CW84 = 3 };
 
 typedef struct {
     int physics;      /* CTU_MHD: ideal MHD (Section 2.1), requires

@@ -344,7 +344,7 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.gamf = (float)ctx->cfg.gamma;
     a.gm1f = (float)(ctx->cfg.gamma - 1.0);
     a.glm_alpha = ctx->cfg.glm_alpha;
-    a.upwind = ctx->cfg.trace_mode == CTU_TRACE_UPWIND;
+    a.upwind = ctx->cfg.trace_mode;
     a.limiter = ctx->cfg.recon;
     a.U = Uin;
     a.Uout = Uout;
@@ -368,7 +368,10 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
     li.groups = ctx->groups.data();
     li.ngroups = (int)ctx->groups.size();
     const int r = ctx->cfg.recon;
-    li.recon = r == CTU_PPM ? RECON_PPM : (r == CTU_LINEAR_MC ? RECON_MC : (r == CTU_WENO3 ? RECON_WENO3 : RECON_LIN));
+    const bool ref = ctx->cfg.trace_mode >= CTU_TRACE_CENTER;
+    li.recon = r == CTU_PPM ? (ref ? RECON_PPM_REF : RECON_PPM)
+             : r == CTU_LINEAR_MC ? (ref ? RECON_MC_REF : RECON_MC)
+             : r == CTU_WENO3 ? RECON_WENO3 : RECON_LIN;
     li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
     li.physics = ctx->cfg.physics == CTU_SRMHD ? PH_SR : PH_MHD;
     li.scratch = ctx->scratch;
@@ -381,12 +384,14 @@ namespace ctu {
 template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<double>(a, li, s);
-    return li.recon >= RECON_LIN ? launch_step_var<double, 1>(a, li, s) : launch_step_impl<double, 1>(a, li, s);
+    if (li.recon >= RECON_PPM_REF) return launch_step_var<double, 1, 1>(a, li, s);
+    return li.recon >= RECON_LIN ? launch_step_var<double, 1, 0>(a, li, s) : launch_step_impl<double, 1>(a, li, s);
 }
 template <> int launch_step<float>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<float>(a, li, s);
-    if (li.recon >= RECON_LIN) return launch_step_var<float, 0>(a, li, s);
+    if (li.recon >= RECON_PPM_REF) return launch_step_var<float, 0, 1>(a, li, s);
+    if (li.recon >= RECON_LIN) return launch_step_var<float, 0, 0>(a, li, s);
     return li.iface64 ? launch_step_impl<float, 1>(a, li, s) : launch_step_impl<float, 0>(a, li, s);
 }
 } // namespace ctu
@@ -423,12 +428,12 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
     if (cfg->precision != CTU_FP64 && cfg->precision != CTU_MIXED && cfg->precision != CTU_MIXED_IFACE64)
         return CTU_EINVAL;
     // the other reconstructions are built for the FP64 and CTU_MIXED paths
-    if (cfg->recon != CTU_LINEAR_MC && cfg->recon != CTU_PPM && cfg->precision == CTU_MIXED_IFACE64)
+    if ((cfg->recon > CTU_PPM || cfg->trace_mode > CTU_TRACE_UPWIND) && cfg->precision == CTU_MIXED_IFACE64)
         return CTU_EUNSUPPORTED;
     if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return CTU_EINVAL;
     if (!(cfg->glm_alpha >= 0.0)) return CTU_EINVAL;
     if (cfg->nghost != 4) return CTU_EINVAL;
-    if (cfg->trace_mode != CTU_TRACE_ALL && cfg->trace_mode != CTU_TRACE_UPWIND) return CTU_EINVAL;
+    if (cfg->trace_mode < CTU_TRACE_ALL || cfg->trace_mode > CTU_TRACE_CW84) return CTU_EINVAL;
     if (!(cfg->p_floor >= 0.0 && cfg->p_floor < INFINITY) || !(cfg->rho_floor >= 0.0 && cfg->rho_floor < INFINITY))
         return CTU_EINVAL;
     if (cfg->physics == CTU_SRMHD && (cfg->p_floor != 0.0 || cfg->rho_floor != 0.0)) return CTU_EUNSUPPORTED;

@@ -69,7 +69,7 @@ struct StepArgs {
     double igm;            // 1/(Gamma-1)
     float gamf, gm1f;      // Gamma, Gamma-1 in float
     double glm_alpha;
-    int upwind;
+    int upwind;            // tracing mode (CTU_TRACE_*); 2 and 3 only in the reference-state kernels
     int limiter;           // linear reconstruction's slope (CTU_LINEAR_*), RECON_LIN kernels
     const double *U;       // pool in
     double *Uout;          // pool out
@@ -436,7 +436,7 @@ __device__ __forceinline__ unsigned int trace_cell_t(const StepArgs &a, const De
     R pl[NV], ml[NV], pg[NV], mg[NV];
     unsigned int f = 0;
     if (PHYS == PH_MHD) {
-        char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind != 0, a.limiter,
+        char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind, a.limiter,
                              PPM == RECON_WENO3 ? R(P.dx[D] * P.dx[D]) : R(0), pl, ml);
     } else {
         double U0[NV];

@@ -136,12 +136,16 @@ template <class R, int IF64> int launch_step_impl(const StepArgs &a, const Launc
                                  : launch_step_t<PH_MHD, R, RECON_MC, IF64>(a, li, s);
 }
 
-// MHD with the other reconstructions of Section 3.2: linear with the MinMod,
-// harmonic or Van Albada slope, or improved WENO3.
-template <class R, int IF64> int launch_step_var(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
+// MHD with the other reconstructions of Section 3.2 (G = 0: linear with the
+// MinMod, harmonic or Van Albada slope, or improved WENO3) or with the
+// reference states of the tracing (G = 1: PPM or MC-linear).
+template <class R, int IF64, int G> int launch_step_var(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
-    return li.recon == RECON_WENO3 ? launch_step_t<PH_MHD, R, RECON_WENO3, IF64>(a, li, s)
-                                   : launch_step_t<PH_MHD, R, RECON_LIN, IF64>(a, li, s);
+    if (G == 0)
+        return li.recon == RECON_WENO3 ? launch_step_t<PH_MHD, R, RECON_WENO3, IF64>(a, li, s)
+                                       : launch_step_t<PH_MHD, R, RECON_LIN, IF64>(a, li, s);
+    return li.recon == RECON_PPM_REF ? launch_step_t<PH_MHD, R, RECON_PPM_REF, IF64>(a, li, s)
+                                     : launch_step_t<PH_MHD, R, RECON_MC_REF, IF64>(a, li, s);
 }
 
 // SRMHD: MUSCL-Hancock with MC-linear primitive slopes.

@@ -30,7 +30,7 @@ struct Group {
 struct LaunchInfo {
     const Group *groups;   // host array, largest patches first
     int ngroups;
-    int recon;             // RECON_MC, RECON_PPM, RECON_LIN or RECON_WENO3
+    int recon;             // RECON_* kernel kind (reconstruction, reference-state tracing)
     int iface64;           // mixed path: 1 = float64 interface-state recovery
     int physics;           // PH_MHD or PH_SR
     void *scratch;         // SCRATCH_ARRAYS * sstride elements of R
@@ -48,6 +48,6 @@ template <class R> int launch_maxspeed(const StepArgs &a, const LaunchInfo &li, 
 // unit each.
 template <class R, int IF64> int launch_step_impl(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
 template <class R> int launch_step_sr(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
-template <class R, int IF64> int launch_step_var(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
+template <class R, int IF64, int G> int launch_step_var(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
 
 } // namespace ctu

@@ -68,7 +68,8 @@ extern "C" ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in
     if (!cfg || !U_in || !U_out || !d_dt_ch || U_in == U_out || !patches) return CTU_EINVAL;
     if (cfg->physics != CTU_MHD || cfg->eos != CTU_EOS_IDEAL || cfg->predictor != CTU_CHAR_TRACE ||
         cfg->riemann != CTU_HLLD || cfg->p_floor != 0.0 || cfg->rho_floor != 0.0 ||
-        (cfg->recon > CTU_PPM && cfg->recon <= CTU_WENO3))
+        (cfg->recon > CTU_PPM && cfg->recon <= CTU_WENO3) ||
+        (cfg->trace_mode > CTU_TRACE_UPWIND && cfg->trace_mode <= CTU_TRACE_CW84))
         return CTU_EUNSUPPORTED;
     if (!(cfg->gamma > 1.0) || cfg->ndim < 1 || cfg->ndim > 3 || cfg->nghost != 4 ||
         (cfg->recon != CTU_LINEAR_MC && cfg->recon != CTU_PPM) ||
@@ -144,7 +145,7 @@ extern "C" ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in
     a.gamf = (float)cfg->gamma;
     a.gm1f = (float)(cfg->gamma - 1.0);
     a.glm_alpha = cfg->glm_alpha;
-    a.upwind = cfg->trace_mode == CTU_TRACE_UPWIND;
+    a.upwind = cfg->trace_mode;
     a.limiter = cfg->recon;
     a.U = U_in;
     a.Uout = U_out;

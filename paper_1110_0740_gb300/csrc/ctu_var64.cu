@@ -3,5 +3,5 @@
 #include "ctu_launch.cuh"
 
 namespace ctu {
-template int launch_step_var<double, 1>(const StepArgs &, const LaunchInfo &, cudaStream_t);
+template int launch_step_var<double, 1, 0>(const StepArgs &, const LaunchInfo &, cudaStream_t);
 } // namespace ctu

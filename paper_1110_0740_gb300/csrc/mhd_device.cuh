@@ -88,8 +88,16 @@ template <class R> __device__ __forceinline__ R lin_slope(R dm, R dp, int lim)
 }
 
 // Reconstruction kinds of the kernel templates: MC-linear, PPM, linear with a
-// run-time slope, improved WENO3.
-enum { RECON_MC = 0, RECON_PPM = 1, RECON_LIN = 2, RECON_WENO3 = 3 };
+// run-time slope, improved WENO3, and PPM and MC-linear again in kernels that
+// also offer the reference states of the tracing (the kinds from RECON_LIN
+// on take the tracing mode at run time among all four; RECON_MC and
+// RECON_PPM among the first two, as before).
+enum { RECON_MC = 0, RECON_PPM = 1, RECON_LIN = 2, RECON_WENO3 = 3, RECON_PPM_REF = 4, RECON_MC_REF = 5 };
+
+__host__ __device__ constexpr int recon_base(int r)
+{
+    return r == RECON_PPM_REF ? RECON_PPM : (r == RECON_MC_REF ? RECON_MC : r);
+}
 
 // Interface values w_(i,+/-) of one characteristic field from w_(i-2..i+2):
 // PPM, Eq. (ppm1) + parabolic limiter Eq. (ppm_parabolic_lim); linear,
@@ -98,9 +106,10 @@ enum { RECON_MC = 0, RECON_PPM = 1, RECON_LIN = 2, RECON_WENO3 = 3 };
 // the cell width in this field's units (the Delta x^2 of Eq. WENO3a divided by
 // the square of the factor that turns this field into the Roe-Balsara
 // characteristic variable).
-template <class R, int PPM>
+template <class R, int RK>
 __device__ __forceinline__ void reconstruct(R w0m2, R w0m1, R w0, R w0p1, R w0p2, int lim, R eps2, R &wp, R &wm)
 {
+    constexpr int PPM = recon_base(RK);
     if (PPM == RECON_WENO3) {
         const R dp = w0p1 - w0, dm = w0 - w0m1;
         const R d2 = (dp - dm) * (dp - dm);
@@ -137,18 +146,32 @@ __device__ __forceinline__ void reconstruct(R w0m2, R w0m1, R w0, R w0p1, R w0p2
 }
 
 // Tracing of one characteristic field to t^(n+1/2), Eq. (wnorm_predp) and
-// (wnorm_predm) with w_ref = w_(+/-).  upwind = false traces every field to
-// both interfaces (no reference state); upwind = true applies
-// beta_+ = [nu > 0], beta_- = [nu < 0].
-template <class R>
-__device__ __forceinline__ void trace(R wp, R w0, R wm, R nu, bool upwind, R &tp, R &tm)
+// (wnorm_predm), w* = w_ref + beta (traced - w_ref).  mode 0
+// (CTU_TRACE_ALL) traces every field to both interfaces (no reference
+// state); the others apply beta_+ = [nu > 0], beta_- = [nu < 0] with
+// w_ref = w_(+/-) (1, CTU_TRACE_UPWIND), the cell-centre value w_(i,0)
+// (2, CTU_TRACE_CENTER) or Colella-Woodward's state, the field traced with
+// numax to the + and numin to the - interface (3, CTU_TRACE_CW84).  Modes 2
+// and 3 exist only where REF is set.
+template <class R, bool REF>
+__device__ __forceinline__ void trace(R wp, R w0, R wm, R nu, int mode, R numax, R numin, R &tp, R &tm)
 {
     R dw = wp - wm;
     R d2w = wp - R(2) * w0 + wm;
     const R up = wp - R(0.5) * nu * (dw + d2w * (R(3) - R(2) * nu));
     const R um = wm - R(0.5) * nu * (dw - d2w * (R(3) + R(2) * nu));
-    tp = (!upwind | (nu > R(0))) ? up : wp;
-    tm = (!upwind | (nu < R(0))) ? um : wm;
+    R rp = wp, rm = wm;
+    if (REF) {
+        if (mode == 2) {
+            rp = w0;
+            rm = w0;
+        } else if (mode == 3) {
+            rp = wp - R(0.5) * numax * (dw + d2w * (R(3) - R(2) * numax));
+            rm = wm - R(0.5) * numin * (dw - d2w * (R(3) + R(2) * numin));
+        }
+    }
+    tp = ((mode == 0) | (nu > R(0))) ? up : rp;
+    tm = ((mode == 0) | (nu < R(0))) ? um : rm;
 }
 
 // ---------------------------------------------------------------- normal predictor
@@ -165,9 +188,10 @@ __device__ __forceinline__ void trace(R wp, R w0, R wm, R nu, bool upwind, R &tp
 // reconstruction and tracing are positively homogeneous, so the result is
 // unchanged.
 template <class R, int PPM>
-__device__ __forceinline__ void char_predict(const R (&vs)[5][NV], R gam, R ch, R dtdx, bool upwind, int lim,
+__device__ __forceinline__ void char_predict(const R (&vs)[5][NV], R gam, R ch, R dtdx, int upwind, int lim,
                                              R dx2, R (&Vp)[NV], R (&Vm)[NV])
 {
+    constexpr bool REF = PPM >= RECON_LIN;
     const R rho = vs[2][0], u = vs[2][1], v1c = vs[2][2], v2c = vs[2][3], pc = vs[2][4];
     const R Bn = vs[2][5], B1c = vs[2][6], B2c = vs[2][7];
     const R a2 = gam * pc / rho;
@@ -241,25 +265,28 @@ __device__ __forceinline__ void char_predict(const R (&vs)[5][NV], R gam, R ch, 
     // (Alfven, GLM) and 1 (entropy)
     const R e_fs = PPM == RECON_WENO3 ? dx2 * (R(4) * a2 * a2) : R(0);
     const R e_ag = PPM == RECON_WENO3 ? dx2 * R(4) : R(0);
+    // the extreme Courant numbers of the seven MHD waves, for mode 3
+    const R numax = REF ? fmax(R(0), (u + cf) * dtdx) : R(0);
+    const R numin = REF ? fmin(R(0), (u - cf) * dtdx) : R(0);
     reconstruct<R, PPM>(wf_m[0], wf_m[1], wf_m[2], wf_m[3], wf_m[4], lim, e_fs, rp, rm);
-    trace(rp, wf_m[2], rm, (u - cf) * dtdx, upwind, tpf_m, tmf_m);
+    trace<R, REF>(rp, wf_m[2], rm, (u - cf) * dtdx, upwind, numax, numin, tpf_m, tmf_m);
     reconstruct<R, PPM>(wa_m[0], wa_m[1], wa_m[2], wa_m[3], wa_m[4], lim, e_ag, rp, rm);
-    trace(rp, wa_m[2], rm, (u - ca) * dtdx, upwind, tpa_m, tma_m);
+    trace<R, REF>(rp, wa_m[2], rm, (u - ca) * dtdx, upwind, numax, numin, tpa_m, tma_m);
     reconstruct<R, PPM>(ws_m[0], ws_m[1], ws_m[2], ws_m[3], ws_m[4], lim, e_fs, rp, rm);
-    trace(rp, ws_m[2], rm, (u - cs) * dtdx, upwind, tps_m, tms_m);
+    trace<R, REF>(rp, ws_m[2], rm, (u - cs) * dtdx, upwind, numax, numin, tps_m, tms_m);
     reconstruct<R, PPM>(we[0], we[1], we[2], we[3], we[4], lim, dx2, rp, rm);
-    trace(rp, we[2], rm, u * dtdx, upwind, tpe, tme);
+    trace<R, REF>(rp, we[2], rm, u * dtdx, upwind, numax, numin, tpe, tme);
     reconstruct<R, PPM>(ws_p[0], ws_p[1], ws_p[2], ws_p[3], ws_p[4], lim, e_fs, rp, rm);
-    trace(rp, ws_p[2], rm, (u + cs) * dtdx, upwind, tps_p, tms_p);
+    trace<R, REF>(rp, ws_p[2], rm, (u + cs) * dtdx, upwind, numax, numin, tps_p, tms_p);
     reconstruct<R, PPM>(wa_p[0], wa_p[1], wa_p[2], wa_p[3], wa_p[4], lim, e_ag, rp, rm);
-    trace(rp, wa_p[2], rm, (u + ca) * dtdx, upwind, tpa_p, tma_p);
+    trace<R, REF>(rp, wa_p[2], rm, (u + ca) * dtdx, upwind, numax, numin, tpa_p, tma_p);
     reconstruct<R, PPM>(wf_p[0], wf_p[1], wf_p[2], wf_p[3], wf_p[4], lim, e_fs, rp, rm);
-    trace(rp, wf_p[2], rm, (u + cf) * dtdx, upwind, tpf_p, tmf_p);
+    trace<R, REF>(rp, wf_p[2], rm, (u + cf) * dtdx, upwind, numax, numin, tpf_p, tmf_p);
     R gpr, gmr, gpl, gml; // reconstructed (untraced) GLM fields at + and - interfaces
     reconstruct<R, PPM>(wg_m[0], wg_m[1], wg_m[2], wg_m[3], wg_m[4], lim, e_ag, gpl, gml);
-    trace(gpl, wg_m[2], gml, -ch * dtdx, upwind, tpg_m, tmg_m);
+    trace<R, REF>(gpl, wg_m[2], gml, -ch * dtdx, upwind, numax, numin, tpg_m, tmg_m);
     reconstruct<R, PPM>(wg_p[0], wg_p[1], wg_p[2], wg_p[3], wg_p[4], lim, e_ag, gpr, gmr);
-    trace(gpr, wg_p[2], gmr, ch * dtdx, upwind, tpg_p, tmg_p);
+    trace<R, REF>(gpr, wg_p[2], gmr, ch * dtdx, upwind, numax, numin, tpg_p, tmg_p);
 
     // recombination with the right eigenvectors (scaled accordingly)
     const R i2a2 = R(0.5) / a2;

@@ -56,3 +56,30 @@ def test_unsupported_combinations():
     with pytest.raises(ctu.CtuError) as e:
         ctu.Ctx(ctu.make_config(recon=6))
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("recon,mode", [(1, 2), (1, 3), (0, 2), (0, 3), (5, 3), (3, 2), (5, 1)])
+def test_reference_states_3d(recon, mode):
+    """The reference states of the tracing (cell centre, Colella-Woodward) with
+    PPM and MC-linear, and combined with the other reconstructions."""
+    n = [24, 20, 16]
+    U0 = W.mhd_blast_3d(24, seed=10 + mode)[:, :24, :28, :32].copy()
+    dx = [1.0 / 24] * 3
+    ref, od = oracle_run(U0, n, 3, dx, 4, 0.3, recon=recon, trace_mode=mode)
+    R = O.interior(ref, n, 3)
+    for prec, tol in ((0, 1e-11), (1, 2e-5)):
+        got, _, st = gpu_run(U0, n, 3, dx, 4, 0.3, precision=prec, recon=recon, trace_mode=mode)
+        assert st == 0
+        e = l1rel(O.interior(got, n, 3), R, od[-1][1])
+        assert np.all(e <= tol), (recon, mode, prec, e)
+
+
+def test_reference_state_unsupported_combinations():
+    from paper_1110_0740_gb300 import ctu
+    for mode in (2, 3):
+        with pytest.raises(ctu.CtuError) as e:
+            ctu.Ctx(ctu.make_config(trace_mode=mode, precision=ctu.CTU_MIXED_IFACE64))
+        assert e.value.code == 4
+    with pytest.raises(ctu.CtuError) as e:
+        ctu.Ctx(ctu.make_config(trace_mode=4))
+    assert e.value.code == 1
