@@ -423,6 +423,49 @@ int or_mhd_riemann(const double *VL0, const double *VR0, double gam, double ch,
     return bad;
 }
 
+/* HLL flux (Harten, Lax & van Leer), the more diffusive solver of the
+ * hybrid integration (appendix on shock detection): the same exact GLM face
+ * solve and the same outer wave speeds S_L, S_R as or_mhd_riemann, then the
+ * single HLL average state.  Returns 1 if an input state has rho <= 0 or
+ * p <= 0. */
+int or_mhd_riemann_hll(const double *VL0, const double *VR0, double gam, double ch, double *F)
+{
+    double VL[NVAR], VR[NVAR], UL[NVAR], UR[NVAR], FL[NVAR], FR[NVAR];
+    double Bm, pm, cfL, cfR, cmax, SL, SR;
+    int q, bad;
+    for (q = 0; q < NVAR; q++) {
+        VL[q] = VL0[q];
+        VR[q] = VR0[q];
+    }
+    bad = !(VL[0] > 0.0 && VL[4] > 0.0 && VR[0] > 0.0 && VR[4] > 0.0);
+    Bm = 0.5 * (VL[5] + VR[5]) - 0.5 * (VR[8] - VL[8]) / ch;
+    pm = 0.5 * (VL[8] + VR[8]) - 0.5 * ch * (VR[5] - VL[5]);
+    VL[5] = Bm;
+    VR[5] = Bm;
+    or_mhd_prim2cons(VL, gam, UL);
+    or_mhd_prim2cons(VR, gam, UR);
+    mhd_flux(VL, UL, FL);
+    mhd_flux(VR, UR, FR);
+    cfL = or_mhd_cfast(VL, gam);
+    cfR = or_mhd_cfast(VR, gam);
+    cmax = fmax(cfL, cfR);
+    SL = fmin(VL[1], VR[1]) - cmax;
+    SR = fmax(VL[1], VR[1]) + cmax;
+    if (SL >= 0.0) {
+        for (q = 0; q < NVAR; q++)
+            F[q] = FL[q];
+    } else if (SR <= 0.0) {
+        for (q = 0; q < NVAR; q++)
+            F[q] = FR[q];
+    } else {
+        for (q = 0; q < NVAR; q++)
+            F[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) / (SR - SL);
+    }
+    F[5] = pm;
+    F[8] = ch * ch * Bm;
+    return bad;
+}
+
 /* ------------------------------------------------------------------ */
 /* Reconstruction, Section 3.2                                         */
 /* ------------------------------------------------------------------ */
@@ -636,6 +679,92 @@ static long dstride(const grid_t *G, int d)
 }
 
 /* ------------------------------------------------------------------ */
+/* Shock detection of the hybrid integration (appendix)                */
+/* ------------------------------------------------------------------ */
+
+/* Flags of the hybrid integration from the primitive field V (all ghosted
+ * cells).  A cell c is shocked (bit 1) when
+ *   sum_d |q(c + e_d) - q(c - e_d)| / min(q(c + e_d), q(c - e_d)) > eps_q
+ *   and  sum_d (v_d(c + e_d) - v_d(c - e_d)) / (2 dx_d) < 0,
+ * q the thermal (qkind 0) or magnetic (qkind 1, B^2/2) pressure, over the
+ * active dimensions; evaluated on the cells within three layers of the
+ * interior ([-3, n + 3) on active dimensions).  A cell is reconstructed with
+ * the MinMod limiter (bit 2) when a shocked cell lies within `reach` cells
+ * of it along an active axis (its reconstruction stencil: 2 for PPM, 1 for
+ * the three-point reconstructions); evaluated on [-1, n + 1).  Faces next to
+ * a shocked cell take the HLL solver. */
+static void shock_flags(const grid_t *G, const double *V, const double *h, double eps_q, int qkind, int reach,
+                        unsigned char *flags)
+{
+    const long nc = G->ncell;
+    int c[3], lo[3], hi[3], d;
+    memset(flags, 0, (size_t)nc);
+    for (d = 0; d < 3; d++) {
+        lo[d] = d < G->ndim ? -3 : 0;
+        hi[d] = d < G->ndim ? G->n[d] + 3 : 1;
+    }
+    for (c[2] = lo[2]; c[2] < hi[2]; c[2]++)
+        for (c[1] = lo[1]; c[1] < hi[1]; c[1]++)
+            for (c[0] = lo[0]; c[0] < hi[0]; c[0]++) {
+                const long id = cidx(G, c);
+                double S = 0.0, D = 0.0;
+                for (d = 0; d < G->ndim; d++) {
+                    const long st = dstride(G, d), ip = id + st, im = id - st;
+                    double qp, qm;
+                    if (qkind == 0) {
+                        qp = V[4 * nc + ip];
+                        qm = V[4 * nc + im];
+                    } else {
+                        qp = 0.5 * (V[5 * nc + ip] * V[5 * nc + ip] + V[6 * nc + ip] * V[6 * nc + ip] +
+                                    V[7 * nc + ip] * V[7 * nc + ip]);
+                        qm = 0.5 * (V[5 * nc + im] * V[5 * nc + im] + V[6 * nc + im] * V[6 * nc + im] +
+                                    V[7 * nc + im] * V[7 * nc + im]);
+                    }
+                    S += fabs(qp - qm) / fmin(qp, qm);
+                    D += (V[(1 + d) * nc + ip] - V[(1 + d) * nc + im]) / (2.0 * h[d]);
+                }
+                if (S > eps_q && D < 0.0)
+                    flags[id] = 1;
+            }
+    for (d = 0; d < 3; d++) {
+        lo[d] = d < G->ndim ? -1 : 0;
+        hi[d] = d < G->ndim ? G->n[d] + 1 : 1;
+    }
+    for (c[2] = lo[2]; c[2] < hi[2]; c[2]++)
+        for (c[1] = lo[1]; c[1] < hi[1]; c[1]++)
+            for (c[0] = lo[0]; c[0] < hi[0]; c[0]++) {
+                const long id = cidx(G, c);
+                int m = 0;
+                for (d = 0; d < G->ndim; d++)
+                    for (int k = -reach; k <= reach; k++)
+                        m |= flags[id + k * dstride(G, d)] & 1;
+                if (m)
+                    flags[id] |= 2;
+            }
+}
+
+/* The flags of shock_flags for a ghost-filled patch U (test access). */
+void or_mhd_shock_flags(const double *U, int nx, int ny, int nz, int ndim, double dx, double dy, double dz,
+                        double gam, double eps_q, int qkind, int reach, unsigned char *flags)
+{
+    grid_t G;
+    double h[3] = {dx, dy, dz};
+    grid_init(&G, nx, ny, nz, ndim);
+    const long nc = G.ncell;
+    double *V = (double *)malloc(sizeof(double) * NVAR * nc);
+    for (long id = 0; id < nc; id++) {
+        double Uc[NVAR], Vc[NVAR];
+        for (int q = 0; q < NVAR; q++)
+            Uc[q] = U[q * nc + id];
+        or_mhd_cons2prim(Uc, gam, Vc);
+        for (int q = 0; q < NVAR; q++)
+            V[q * nc + id] = Vc[q];
+    }
+    shock_flags(&G, V, h, eps_q, qkind, reach, flags);
+    free(V);
+}
+
+/* ------------------------------------------------------------------ */
 /* CFL, Eq. (Ca)                                                       */
 /* ------------------------------------------------------------------ */
 
@@ -684,11 +813,32 @@ double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
  * transverse cell widths) and F the n+1/2 flux through the face in +d.
  * Returns the number of states met with rho <= 0 or p <= 0.
  */
+int or_mhd_step_hybrid(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
+                       double dx, double dy, double dz, double dt, double ch,
+                       double gam, double glm_alpha, int recon, int upwind,
+                       const long *win, const double *wgt, int nwin, double *reg,
+                       int shock, double eps_q, int qkind);
+
 int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                 double dx, double dy, double dz, double dt, double ch,
                 double gam, double glm_alpha, int recon, int upwind,
                 const long *win, const double *wgt, int nwin, double *reg)
 {
+    return or_mhd_step_hybrid(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win,
+                              wgt, nwin, reg, 0, 0.0, 0);
+}
+
+/* or_mhd_step with the hybrid integration of the appendix on shock detection
+ * when shock != 0: the flags of shock_flags (eps_q, qkind) on V^n select
+ * the HLL solver at the faces of shocked cells (first-order and n+1/2
+ * fluxes) and the MinMod linear reconstruction for the cells near them. */
+int or_mhd_step_hybrid(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
+                       double dx, double dy, double dz, double dt, double ch,
+                       double gam, double glm_alpha, int recon, int upwind,
+                       const long *win, const double *wgt, int nwin, double *reg,
+                       int shock, double eps_q, int qkind)
+{
+    unsigned char *flags = NULL;
     grid_t G;
     double h[3] = {dx, dy, dz};
     double *V, *F1[3] = {0, 0, 0}, *Up[3] = {0, 0, 0}, *Um[3] = {0, 0, 0}, *F[3] = {0, 0, 0};
@@ -707,6 +857,10 @@ int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
         bad += or_mhd_cons2prim(Uc, gam, Vc);
         for (q = 0; q < NVAR; q++)
             V[q * nc + id] = Vc[q];
+    }
+    if (shock) {
+        flags = (unsigned char *)malloc((size_t)nc);
+        shock_flags(&G, V, h, eps_q, qkind, recon == 1 ? 2 : 1, flags);
     }
 
     /* 2. first-order Godunov fluxes F^n_d = R(U_c, U_(c+e_d)) on the faces the
@@ -736,7 +890,10 @@ int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                         VL[q] = V[PERM[d][q] * nc + id];
                         VR[q] = V[PERM[d][q] * nc + id + st];
                     }
-                    or_mhd_riemann(VL, VR, gam, ch, Fl);
+                    if (flags && ((flags[id] | flags[id + st]) & 1))
+                        or_mhd_riemann_hll(VL, VR, gam, ch, Fl);
+                    else
+                        or_mhd_riemann(VL, VR, gam, ch, Fl);
                     for (q = 0; q < NVAR; q++)
                         F1[d][PERM[d][q] * nc + id] = Fl[q];
                 }
@@ -766,7 +923,8 @@ int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                     for (l = 0; l < 5; l++)
                         for (q = 0; q < NVAR; q++)
                             vs[l * NVAR + q] = V[PERM[d][q] * nc + id + (l - 2) * st];
-                    or_mhd_char_predict_dx(vs, gam, ch, dt / h[d], h[d], recon, upwind, Vp, Vm);
+                    or_mhd_char_predict_dx(vs, gam, ch, dt / h[d], h[d], (flags && (flags[id] & 2)) ? 2 : recon,
+                                           upwind, Vp, Vm);
                     /* transverse increments L^n_d' = -(F_(d',+) - F_(d',-))/dx_d' */
                     for (q = 0; q < NVAR; q++)
                         T[q] = 0.0;
@@ -814,7 +972,10 @@ int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                         VL[q] = VLg[PERM[d][q]];
                         VR[q] = VRg[PERM[d][q]];
                     }
-                    or_mhd_riemann(VL, VR, gam, ch, Fl);
+                    if (flags && ((flags[id] | flags[id + st]) & 1))
+                        or_mhd_riemann_hll(VL, VR, gam, ch, Fl);
+                    else
+                        or_mhd_riemann(VL, VR, gam, ch, Fl);
                     for (q = 0; q < NVAR; q++)
                         F[d][PERM[d][q] * nc + id] = Fl[q];
                 }
@@ -860,6 +1021,7 @@ int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                 }
     }
 
+    free(flags);
     free(V);
     for (d = 0; d < 3; d++) {
         free(F1[d]);
