@@ -134,6 +134,21 @@ typedef struct {
      * still sets CTU_ENEGATIVE with floors on. */
     double p_floor;
     double rho_floor;
+    /* The hybrid integration of the paper's appendix on shock detection
+     * (shock_detect = 1; 0 = off): a cell within three layers of the
+     * interior is shocked when
+     *   sum_d |q(c + e_d) - q(c - e_d)| / min(q(c + e_d), q(c - e_d))
+     *   > shock_eps  and  div v < 0 (central differences),
+     * q the thermal (shock_q = 0) or magnetic (1, B^2/2) pressure of the
+     * step's initial state.  The faces of shocked cells take the HLL solver
+     * (first-order and n+1/2 fluxes) and cells whose reconstruction stencil
+     * reaches a shocked cell take linear MinMod reconstruction.  The paper's
+     * default threshold is 5.  Ideal MHD with CTU_PPM or CTU_LINEAR_MC,
+     * trace_mode CTU_TRACE_ALL or CTU_TRACE_UPWIND, CTU_FP64 or CTU_MIXED
+     * (else CTU_EUNSUPPORTED); not in ctu_step_noalloc. */
+    int shock_detect;
+    int shock_q;
+    double shock_eps;
 } ctu_config;
 
 typedef struct {

@@ -318,7 +318,9 @@ static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStr
 static ctu_status ensure_scratch(ctu_ctx *ctx)
 {
     const size_t elt = ctx->cfg.precision == CTU_FP64 ? sizeof(double) : sizeof(float);
-    const size_t need = (size_t)SCRATCH_ARRAYS * (size_t)ctx->sstride * elt;
+    // + the shock flags of the hybrid integration, one byte per scratch cell
+    const size_t need = (size_t)SCRATCH_ARRAYS * (size_t)ctx->sstride * elt +
+                        (ctx->cfg.shock_detect ? (size_t)ctx->sstride + 256 : 0);
     if (need <= ctx->scratch_bytes) return CTU_OK;
     if (ctx->scratch) {
         CTU_CUDA(cudaDeviceSynchronize());
@@ -346,6 +348,14 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.glm_alpha = ctx->cfg.glm_alpha;
     a.upwind = ctx->cfg.trace_mode;
     a.limiter = ctx->cfg.recon;
+    a.shock_eps = ctx->cfg.shock_eps;
+    a.shock_q = ctx->cfg.shock_q;
+    a.flags = nullptr;
+    if (ctx->cfg.shock_detect && ctx->scratch) {
+        const size_t elt = ctx->cfg.precision == CTU_FP64 ? sizeof(double) : sizeof(float);
+        const size_t off = ((size_t)SCRATCH_ARRAYS * (size_t)ctx->sstride * elt + 255) / 256 * 256;
+        a.flags = (unsigned char *)ctx->scratch + off;
+    }
     a.U = Uin;
     a.Uout = Uout;
     a.ustride = stride;
@@ -369,8 +379,9 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
     li.ngroups = (int)ctx->groups.size();
     const int r = ctx->cfg.recon;
     const bool ref = ctx->cfg.trace_mode >= CTU_TRACE_CENTER;
-    li.recon = r == CTU_PPM ? (ref ? RECON_PPM_REF : RECON_PPM)
-             : r == CTU_LINEAR_MC ? (ref ? RECON_MC_REF : RECON_MC)
+    const bool hyb = ctx->cfg.shock_detect != 0;
+    li.recon = r == CTU_PPM ? (hyb ? RECON_PPM_HYB : (ref ? RECON_PPM_REF : RECON_PPM))
+             : r == CTU_LINEAR_MC ? (hyb ? RECON_MC_HYB : (ref ? RECON_MC_REF : RECON_MC))
              : r == CTU_WENO3 ? RECON_WENO3 : RECON_LIN;
     li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
     li.physics = ctx->cfg.physics == CTU_SRMHD ? PH_SR : PH_MHD;
@@ -384,12 +395,14 @@ namespace ctu {
 template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<double>(a, li, s);
+    if (recon_hybrid(li.recon)) return launch_step_var<double, 1, 2>(a, li, s);
     if (li.recon >= RECON_PPM_REF) return launch_step_var<double, 1, 1>(a, li, s);
     return li.recon >= RECON_LIN ? launch_step_var<double, 1, 0>(a, li, s) : launch_step_impl<double, 1>(a, li, s);
 }
 template <> int launch_step<float>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<float>(a, li, s);
+    if (recon_hybrid(li.recon)) return launch_step_var<float, 0, 2>(a, li, s);
     if (li.recon >= RECON_PPM_REF) return launch_step_var<float, 0, 1>(a, li, s);
     if (li.recon >= RECON_LIN) return launch_step_var<float, 0, 0>(a, li, s);
     return li.iface64 ? launch_step_impl<float, 1>(a, li, s) : launch_step_impl<float, 0>(a, li, s);
@@ -437,6 +450,16 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
     if (!(cfg->p_floor >= 0.0 && cfg->p_floor < INFINITY) || !(cfg->rho_floor >= 0.0 && cfg->rho_floor < INFINITY))
         return CTU_EINVAL;
     if (cfg->physics == CTU_SRMHD && (cfg->p_floor != 0.0 || cfg->rho_floor != 0.0)) return CTU_EUNSUPPORTED;
+    if (cfg->shock_detect != 0 && cfg->shock_detect != 1) return CTU_EINVAL;
+    if (cfg->shock_detect) {
+        if (!(cfg->shock_eps > 0.0 && cfg->shock_eps < INFINITY) || (cfg->shock_q != 0 && cfg->shock_q != 1))
+            return CTU_EINVAL;
+        // the hybrid integration: ideal MHD, PPM or MC-linear, tracing
+        // without or with the w_(+/-) reference, FP64 or CTU_MIXED
+        if (cfg->physics != CTU_MHD || (cfg->recon != CTU_PPM && cfg->recon != CTU_LINEAR_MC) ||
+            cfg->trace_mode > CTU_TRACE_UPWIND || cfg->precision == CTU_MIXED_IFACE64)
+            return CTU_EUNSUPPORTED;
+    }
     ctu_ctx *ctx = new (std::nothrow) ctu_ctx();
     if (!ctx) return CTU_ENOMEM;
     ctx->cfg = *cfg;

@@ -70,7 +70,12 @@ struct StepArgs {
     float gamf, gm1f;      // Gamma, Gamma-1 in float
     double glm_alpha;
     int upwind;            // tracing mode (CTU_TRACE_*); 2 and 3 only in the reference-state kernels
-    int limiter;           // linear reconstruction's slope (CTU_LINEAR_*), RECON_LIN kernels
+    int limiter;
+    // hybrid integration (shock flags): per scratch cell, bit 1 shocked (HLL
+    // at its faces), bit 2 MinMod reconstruction; null when off
+    unsigned char *flags;
+    double shock_eps;
+    int shock_q;           // 0 thermal, 1 magnetic pressure           // linear reconstruction's slope (CTU_LINEAR_*), RECON_LIN kernels
     const double *U;       // pool in
     double *Uout;          // pool out
     long long ustride;     // pool variable stride
@@ -436,7 +441,8 @@ __device__ __forceinline__ unsigned int trace_cell_t(const StepArgs &a, const De
     R pl[NV], ml[NV], pg[NV], mg[NV];
     unsigned int f = 0;
     if (PHYS == PH_MHD) {
-        char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind, a.limiter,
+        const int lim = recon_hybrid(PPM) ? ((a.flags[c] & 2) ? 2 : 0) : a.limiter;
+        char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind, lim,
                              PPM == RECON_WENO3 ? R(P.dx[D] * P.dx[D]) : R(0), pl, ml);
     } else {
         double U0[NV];
@@ -483,7 +489,8 @@ __device__ __forceinline__ void riemann_any(const R (&L)[NV], const R (&Rr)[NV],
 // n+1/2 flux through a D-face from the left cell's + state and the right
 // cell's - state (both global order); flux returned in global order.
 template <int PHYS, class R, int D>
-__device__ __forceinline__ void face_flux(const R (&Lg)[NV], const R (&Rg)[NV], R gam, R ch, R (&Fg)[NV])
+__device__ __forceinline__ void face_flux(const R (&Lg)[NV], const R (&Rg)[NV], R gam, R ch, R (&Fg)[NV],
+                                          bool hll = false)
 {
     R L[NV], Rr[NV], F[NV];
 #pragma unroll
@@ -491,7 +498,10 @@ __device__ __forceinline__ void face_flux(const R (&Lg)[NV], const R (&Rg)[NV], 
         L[q] = Lg[gperm<D>(q)];
         Rr[q] = Rg[gperm<D>(q)];
     }
-    riemann_any<PHYS, R>(L, Rr, gam, ch, F);
+    if (PHYS == PH_MHD && hll)
+        riemann_hll(L, Rr, gam, ch, F);
+    else
+        riemann_any<PHYS, R>(L, Rr, gam, ch, F);
 #pragma unroll
     for (int q = 0; q < NV; ++q) Fg[gperm<D>(q)] = F[q];
 }
@@ -701,6 +711,125 @@ __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, GroupTable gt, R *Vs
     for (int q = 0; q < NV; ++q) Vs[q * a.sstride + P.soff + c] = V[q];
 }
 
+// ---- hybrid integration: shock flags (appendix on shock detection) ----
+// A cell within three layers of the interior is shocked when
+//   S = sum_d |q(c + e_d) - q(c - e_d)| / min(q(c + e_d), q(c - e_d)) > eps_q
+//   and D = sum_d (v_d(c + e_d) - v_d(c - e_d)) / (2 dx_d) < 0
+// (q the thermal or magnetic pressure).  Both sums are formed from the
+// working-precision primitives; a cell whose S or D lies within the
+// relative margin of its threshold that bounds the difference between these
+// primitives and float64 ones (1e-4 in float32, 1e-9 in float64) is decided
+// again from the float64 state, in explicitly rounded operations in the
+// order of the definition, so each flag is the float64 definition's.
+__device__ __forceinline__ void prim_exact(const StepArgs &a, long long g, double gm1, int d, int qk, double &q,
+                                           double &v)
+{
+    const double *U = a.U;
+    const long long us = a.ustride;
+    const double rho = U[g];
+    if (qk == 0) {
+        const double m0 = U[us + g], m1 = U[2 * us + g], m2 = U[3 * us + g];
+        const double b0 = U[5 * us + g], b1 = U[6 * us + g], b2 = U[7 * us + g];
+        const double mm = __dadd_rn(__dadd_rn(__dmul_rn(m0, m0), __dmul_rn(m1, m1)), __dmul_rn(m2, m2));
+        const double bb = __dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)), __dmul_rn(b2, b2));
+        q = __dmul_rn(gm1, __dsub_rn(__dsub_rn(U[4 * us + g], __ddiv_rn(__dmul_rn(0.5, mm), rho)), __dmul_rn(0.5, bb)));
+    } else {
+        const double b0 = U[5 * us + g], b1 = U[6 * us + g], b2 = U[7 * us + g];
+        q = __dmul_rn(0.5, __dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)), __dmul_rn(b2, b2)));
+    }
+    v = __ddiv_rn(U[(1 + d) * us + g], rho);
+}
+
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_shock(StepArgs a, GroupTable gt, const R *Vs)
+{
+    const Where w = locate(gt);
+    const DevPatch P = a.patches[w.patch];
+    const int c = w.b * BLOCK + threadIdx.x;
+    if (c >= P.N[0] * P.N[1] * P.N[2]) return;
+    const int gx = c % P.N[0], gy = (c / P.N[0]) % P.N[1], gz = c / (P.N[0] * P.N[1]);
+    const int x[3] = {gx - P.g[0], gy - P.g[1], gz - P.g[2]};
+    bool in = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d < a.ndim) in &= x[d] >= -3 && x[d] < P.n[d] + 3;
+    unsigned char f = 0;
+    if (in) {
+        const long long sc = P.soff + c;
+        const long long ss = a.sstride;
+        const long long st[3] = {1, P.N[0], (long long)P.N[0] * P.N[1]};
+        const R eps = (R)a.shock_eps;
+        R S = R(0), D = R(0), Bd = R(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= a.ndim) break;
+            const long long ip = sc + st[d], im = sc - st[d];
+            R qp, qm;
+            if (a.shock_q == 0) {
+                qp = Vs[4 * ss + ip];
+                qm = Vs[4 * ss + im];
+            } else {
+                qp = R(0.5) * (Vs[5 * ss + ip] * Vs[5 * ss + ip] + Vs[6 * ss + ip] * Vs[6 * ss + ip] +
+                               Vs[7 * ss + ip] * Vs[7 * ss + ip]);
+                qm = R(0.5) * (Vs[5 * ss + im] * Vs[5 * ss + im] + Vs[6 * ss + im] * Vs[6 * ss + im] +
+                               Vs[7 * ss + im] * Vs[7 * ss + im]);
+            }
+            S += fabs(qp - qm) / fmin(qp, qm);
+            const R h2 = R(0.5) * pidx<R>(P, d);
+            const R vp = Vs[(1 + d) * ss + ip], vm = Vs[(1 + d) * ss + im];
+            D += (vp - vm) * h2;
+            Bd += (fabs(vp) + fabs(vm)) * h2;
+        }
+        const R tol = sizeof(R) == 4 ? R(1e-4) : R(1e-9);
+        const R ms = tol * (S + eps + R(1)), md = tol * Bd;
+        const bool s_yes = S - eps > ms, s_no = eps - S > ms;
+        const bool d_yes = D < -md, d_no = D > md;
+        if (s_yes && d_yes) {
+            f = 1;
+        } else if (!(s_no || d_no)) {
+            const long long g = P.base + c;
+            const double gm1 = a.gam - 1.0;
+            double Se = 0.0, De = 0.0;
+            for (int d = 0; d < a.ndim; ++d) {
+                const long long sg = d == 0 ? 1 : (d == 1 ? (long long)P.N[0] : (long long)P.N[0] * P.N[1]);
+                double qp, qm, vp, vm;
+                prim_exact(a, g + sg, gm1, d, a.shock_q, qp, vp);
+                prim_exact(a, g - sg, gm1, d, a.shock_q, qm, vm);
+                Se = __dadd_rn(Se, __ddiv_rn(fabs(__dsub_rn(qp, qm)), fmin(qp, qm)));
+                De = __dadd_rn(De, __ddiv_rn(__dsub_rn(vp, vm), __dmul_rn(2.0, P.dx[d])));
+            }
+            f = (Se > a.shock_eps && De < 0.0) ? 1 : 0;
+        }
+    }
+    a.flags[P.soff + c] = f;
+}
+
+// MinMod flag (bit 2) on the cells [-1, n + 1): a shocked cell within
+// `reach` cells along an active axis (2 for PPM, 1 for MC-linear).
+static __global__ void __launch_bounds__(BLOCK) k_minmod(StepArgs a, GroupTable gt, int reach)
+{
+    const Where w = locate(gt);
+    const DevPatch P = a.patches[w.patch];
+    const int c = w.b * BLOCK + threadIdx.x;
+    if (c >= P.N[0] * P.N[1] * P.N[2]) return;
+    const int gx = c % P.N[0], gy = (c / P.N[0]) % P.N[1], gz = c / (P.N[0] * P.N[1]);
+    const int x[3] = {gx - P.g[0], gy - P.g[1], gz - P.g[2]};
+    bool in = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d < a.ndim) in &= x[d] >= -1 && x[d] < P.n[d] + 1;
+    if (!in) return;
+    const long long sc = P.soff + c;
+    const long long st[3] = {1, P.N[0], (long long)P.N[0] * P.N[1]};
+    unsigned m = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= a.ndim) break;
+        for (int k = -reach; k <= reach; ++k) m |= a.flags[sc + k * st[d]];
+    }
+    if (m & 1) a.flags[sc] |= 2;
+}
+
 // First-order flux divergences L1_D = (F^n_(c - e_D/2) - F^n_(c + e_D/2)) / dx_D
 // (Eq. transv; F^n from the cell-centred states) on the cells that the
 // sweeps of the other directions trace: c_D in [0, n_D), the other active
@@ -709,7 +838,7 @@ __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, GroupTable gt, R *Vs
 //          cells, the lower face of a cell arriving from the previous lane.
 //   D = y, z: one thread per segment of SEG cells marching along D with the
 //          previous face flux and cell state in registers.
-template <int PHYS, class R, int D>
+template <int PHYS, class R, int D, bool HYB = false>
 __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const R *Vs, R *L1)
 {
     const Where wh = locate(gt);
@@ -739,7 +868,10 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const
                 L[q] = Vs[q * a.sstride + c - 1];
                 Rr[q] = Vs[q * a.sstride + c];
             }
-            riemann_any<PHYS, R>(L, Rr, gam, ch, F);
+            if (HYB && PHYS == PH_MHD && ((a.flags[c - 1] | a.flags[c]) & 1))
+                riemann_hll(L, Rr, gam, ch, F);
+            else
+                riemann_any<PHYS, R>(L, Rr, gam, ch, F);
         } else {
 #pragma unroll
             for (int q = 0; q < NV; ++q) F[q] = R(0);
@@ -784,7 +916,10 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const
                 for (int q = 0; q < NV; ++q) Vn[q] = Vs[gperm<D>(q) * a.sstride + c + st];
             }
             R F[NV];
-            riemann_any<PHYS, R>(Vl, Vr, gam, ch, F);
+            if (HYB && PHYS == PH_MHD && ((a.flags[c - st] | a.flags[c]) & 1))
+                riemann_hll(Vl, Vr, gam, ch, F);
+            else
+                riemann_any<PHYS, R>(Vl, Vr, gam, ch, F);
             if (j > j0) {  // cell j - 1
 #pragma unroll
                 for (int q = 0; q < NV; ++q) Ld[gperm<D>(q) * a.sstride + c - st] = (Fp[q] - F[q]) * iD;
@@ -854,7 +989,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
         R L[NV], Rr[NV], F[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) { L[q] = sP[me][q]; Rr[q] = sM[me + 1][q]; }
-        face_flux<PHYS, R, 0>(L, Rr, gam, ch, F);
+        face_flux<PHYS, R, 0>(L, Rr, gam, ch, F, recon_hybrid(PPM) && ((a.flags[c] | a.flags[c + 1]) & 1));
 #pragma unroll
         for (int q = 0; q < NV; ++q) sF[me][q] = F[q];
         // faces on plane i+1; the tile's last face belongs to the next tile
@@ -995,7 +1130,8 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, G
         auto faces = [&](int j, long long cj, const R (&Vm)[NV], const R *Ap, long long as, const double *Up,
                          long long us) {
             R F[NV];
-            face_flux<PHYS, R, D>(Pprev, Vm, gam, ch, F);
+            face_flux<PHYS, R, D>(Pprev, Vm, gam, ch, F,
+                                  recon_hybrid(PPM) && ((a.flags[cj - st] | a.flags[cj]) & 1));
             // plane j; (a, b) = (x, o) are the two non-D dimensions in
             // increasing order; a segment's last face belongs to the next
             if (wb >= 0 && (j < j1 || j1 == nD)) {

@@ -92,12 +92,20 @@ template <class R> __device__ __forceinline__ R lin_slope(R dm, R dp, int lim)
 // also offer the reference states of the tracing (the kinds from RECON_LIN
 // on take the tracing mode at run time among all four; RECON_MC and
 // RECON_PPM among the first two, as before).
-enum { RECON_MC = 0, RECON_PPM = 1, RECON_LIN = 2, RECON_WENO3 = 3, RECON_PPM_REF = 4, RECON_MC_REF = 5 };
+// The hybrid kinds (RECON_PPM_HYB, RECON_MC_HYB) reconstruct with MinMod
+// where the shock flags ask for it (lim == 2 at run time).
+enum {
+    RECON_MC = 0, RECON_PPM = 1, RECON_LIN = 2, RECON_WENO3 = 3, RECON_PPM_REF = 4, RECON_MC_REF = 5,
+    RECON_PPM_HYB = 6, RECON_MC_HYB = 7
+};
 
 __host__ __device__ constexpr int recon_base(int r)
 {
-    return r == RECON_PPM_REF ? RECON_PPM : (r == RECON_MC_REF ? RECON_MC : r);
+    return (r == RECON_PPM_REF || r == RECON_PPM_HYB) ? RECON_PPM
+                                                      : ((r == RECON_MC_REF || r == RECON_MC_HYB) ? RECON_MC : r);
 }
+
+__host__ __device__ constexpr bool recon_hybrid(int r) { return r == RECON_PPM_HYB || r == RECON_MC_HYB; }
 
 // Interface values w_(i,+/-) of one characteristic field from w_(i-2..i+2):
 // PPM, Eq. (ppm1) + parabolic limiter Eq. (ppm_parabolic_lim); linear,
@@ -110,6 +118,13 @@ template <class R, int RK>
 __device__ __forceinline__ void reconstruct(R w0m2, R w0m1, R w0, R w0p1, R w0p2, int lim, R eps2, R &wp, R &wm)
 {
     constexpr int PPM = recon_base(RK);
+    if (recon_hybrid(RK) && lim == 2) {  // MinMod near a shock
+        const R dm = w0 - w0m1, dp = w0p1 - w0;
+        const R s = dm * dp > R(0) ? copysign(fmin(fabs(dm), fabs(dp)), dm) : R(0);
+        wp = w0 + R(0.5) * s;
+        wm = w0 - R(0.5) * s;
+        return;
+    }
     if (PPM == RECON_WENO3) {
         const R dp = w0p1 - w0, dm = w0 - w0m1;
         const R d2 = (dp - dm) * (dp - dm);
@@ -191,7 +206,7 @@ template <class R, int PPM>
 __device__ __forceinline__ void char_predict(const R (&vs)[5][NV], R gam, R ch, R dtdx, int upwind, int lim,
                                              R dx2, R (&Vp)[NV], R (&Vm)[NV])
 {
-    constexpr bool REF = PPM >= RECON_LIN;
+    constexpr bool REF = PPM >= RECON_LIN && !recon_hybrid(PPM);
     const R rho = vs[2][0], u = vs[2][1], v1c = vs[2][2], v2c = vs[2][3], pc = vs[2][4];
     const R Bn = vs[2][5], B1c = vs[2][6], B2c = vs[2][7];
     const R a2 = gam * pc / rho;
@@ -459,6 +474,61 @@ __device__ __forceinline__ bool riemann_hlld(const R (&L)[NV], const R (&Rt)[NV]
                 for (int q = 0; q < 8; ++q) G[q] = FR[q] + SR * (UsR[q] - UR[q]) + SRs * (Uss[q] - UsR[q]);
             }
         }
+    }
+    F[0] = G[0]; F[1] = G[1]; F[2] = G[2]; F[3] = G[3]; F[4] = G[4];
+    F[5] = pm;
+    F[6] = G[6]; F[7] = G[7];
+    F[8] = ch * ch * Bm;
+    return bad;
+}
+
+// HLL flux (Harten, Lax & van Leer), the solver of the hybrid integration at
+// the faces of shocked cells: the same GLM face solve and outer wave speeds
+// as riemann_hlld, then the single HLL average state.
+template <class R>
+__device__ __forceinline__ bool riemann_hll(const R (&L)[NV], const R (&Rt)[NV], R gam, R ch, R (&F)[NV])
+{
+    const bool bad = !(L[0] > R(0) && L[4] > R(0) && Rt[0] > R(0) && Rt[4] > R(0));
+    const R Bm = R(0.5) * (L[5] + Rt[5]) - R(0.5) * (Rt[8] - L[8]) / ch;
+    const R pm = R(0.5) * (L[8] + Rt[8]) - R(0.5) * ch * (Rt[5] - L[5]);
+    const R Bn = Bm;
+    const R igm = R(1) / (gam - R(1));
+    const R rL = L[0], uL = L[1], vL = L[2], wL = L[3], pL = L[4], yL = L[6], zL = L[7];
+    const R rR = Rt[0], uR = Rt[1], vR = Rt[2], wR = Rt[3], pR = Rt[4], yR = Rt[6], zR = Rt[7];
+    const R BsqL = Bn * Bn + yL * yL + zL * zL;
+    const R BsqR = Bn * Bn + yR * yR + zR * zR;
+    const R ptL = pL + R(0.5) * BsqL, ptR = pR + R(0.5) * BsqR;
+    const R EL = pL * igm + R(0.5) * rL * (uL * uL + vL * vL + wL * wL) + R(0.5) * BsqL;
+    const R ER = pR * igm + R(0.5) * rR * (uR * uR + vR * vR + wR * wR) + R(0.5) * BsqR;
+    const R vBL = uL * Bn + vL * yL + wL * zL;
+    const R vBR = uR * Bn + vR * yR + wR * zR;
+    R FL[8], FR[8], UL[8], UR[8];
+    FL[0] = rL * uL; FL[1] = rL * uL * uL + ptL - Bn * Bn; FL[2] = rL * uL * vL - Bn * yL;
+    FL[3] = rL * uL * wL - Bn * zL; FL[4] = (EL + ptL) * uL - Bn * vBL; FL[5] = R(0);
+    FL[6] = uL * yL - Bn * vL; FL[7] = uL * zL - Bn * wL;
+    FR[0] = rR * uR; FR[1] = rR * uR * uR + ptR - Bn * Bn; FR[2] = rR * uR * vR - Bn * yR;
+    FR[3] = rR * uR * wR - Bn * zR; FR[4] = (ER + ptR) * uR - Bn * vBR; FR[5] = R(0);
+    FR[6] = uR * yR - Bn * vR; FR[7] = uR * zR - Bn * wR;
+    UL[0] = rL; UL[1] = rL * uL; UL[2] = rL * vL; UL[3] = rL * wL; UL[4] = EL; UL[5] = Bn;
+    UL[6] = yL; UL[7] = zL;
+    UR[0] = rR; UR[1] = rR * uR; UR[2] = rR * vR; UR[3] = rR * wR; UR[4] = ER; UR[5] = Bn;
+    UR[6] = yR; UR[7] = zR;
+    const R cfL = fast_speed(rL, pL, Bn, yL, zL, gam);
+    const R cfR = fast_speed(rR, pR, Bn, yR, zR, gam);
+    const R cmax = fmax(cfL, cfR);
+    const R SL = fmin(uL, uR) - cmax;
+    const R SR = fmax(uL, uR) + cmax;
+    R G[8];
+    if (SL >= R(0)) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) G[q] = FL[q];
+    } else if (SR <= R(0)) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) G[q] = FR[q];
+    } else {
+        const R iw = R(1) / (SR - SL);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) G[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) * iw;
     }
     F[0] = G[0]; F[1] = G[1]; F[2] = G[2]; F[3] = G[3]; F[4] = G[4];
     F[5] = pm;
