@@ -216,7 +216,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def make(prec):
-        c = ctu.Ctx(ctu.make_config(ndim=3, recon=RECONS[args.recon], precision=prec, cfl=0.3))
+        c = ctu.Ctx(ctu.make_config(ndim=3, recon=RECONS[args.recon], precision=prec, cfl=0.3,
+                                    shock=(args.shock, 0) if args.shock else None))
         c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
         if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
@@ -324,7 +325,7 @@ def run_ours(args):
     roof["hbm_step"] = {"algorithmic_bytes": nbytes, "achieved_gbs": hbm_achieved,
                         "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
                         "peak_source": f"{src} hbm_gbs"}
-    if mixed and args.recon == "ppm":
+    if mixed and args.recon == "ppm" and not args.shock:
         roof["precision_split"] = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
 
     # end-to-end through the public API with host buffers
@@ -370,9 +371,11 @@ def run_ours(args):
                 "steps": res["K"], "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if primary == ctu.CTU_MIXED else "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD if args.recon == "ppm" else
-                           WORKLOAD.replace("PPM", f"{args.recon} reconstruction"),
-                           "recon": args.recon, "cells_per_gpu": cells, "patches_per_gpu": 1,
+                "config": {"workload": (WORKLOAD if args.recon == "ppm" else
+                                        WORKLOAD.replace("PPM", f"{args.recon} reconstruction"))
+                           + (f"; hybrid integration (shock flags, eps_q {args.shock})" if args.shock else ""),
+                           "recon": args.recon, "shock_eps": args.shock or None,
+                           "cells_per_gpu": cells, "patches_per_gpu": 1,
                            "precision": args.precision, "l2_flush": "inputs (1.3 GB) > L2",
                            "parallelism": f"replicas x{world}", "tiles_xw_seg": tiles.get("xw_seg")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path,
@@ -891,6 +894,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-level-ops", action="store_true",
                     help="amr: advance the levels without prolongation, restriction and reflux")
+    ap.add_argument("--shock", type=float, default=0.0,
+                    help="blast: the hybrid integration with this shock threshold (thermal pressure; 0 = off)")
     ap.add_argument("--recon", default="ppm", choices=sorted(RECONS),
                     help="blast: reconstruction of the characteristic variables (the workload uses ppm)")
     ap.add_argument("--config", default="blast", choices=["blast", "amr", "srmhd", "tag"],
