@@ -123,7 +123,8 @@ typedef struct {
     /* Optional floors of the updated state, >= 0, 0 = off; CTU_MHD only
      * (CTU_SRMHD with a floor returns CTU_EUNSUPPORTED).  The paper fixes no
      * floor: its safeguard against non-physical states is the shock-flagged
-     * hybrid integration of its appendix on shock detection (not built).
+     * hybrid integration of its appendix on shock detection (shock_detect
+     * below).
      * After the update and the psi damping of every ctu_step, an interior
      * cell with rho < rho_floor takes rho = rho_floor (m, E, B, psi kept);
      * then, with that density, a cell with
