@@ -5,7 +5,10 @@
  *
  * What it follows (Mignone et al. 2012):
  *   - RMHD equations, total pressure and energy: Section 2.2, Eq. (rmhd);
- *     ideal-gas enthalpy w = rho + Gamma p/(Gamma-1), Eq. (gammaEos);
+ *     ideal-gas enthalpy w = rho + Gamma p/(Gamma-1), Eq. (gammaEos), or
+ *     the Taub-Mathews enthalpy w = 5/2 p + sqrt(9/4 p^2 + rho^2),
+ *     Eq. (TMEos).  Every function takes `gam`: Gamma of the ideal gas
+ *     (> 1), or 0 for the Taub-Mathews equation of state;
  *   - GLM cleaning and its operator-split source: Section 3, Eq. (glm2x2);
  *   - unsplit update, n+1/2 Riemann problems, corner-coupled states with
  *     first-order transverse fluxes: Section 3.1, Eq. (update), (ctu_flux),
@@ -40,6 +43,25 @@ static const int PERM_R[3][NVAR] = {
     {0, 3, 1, 2, 4, 7, 5, 6, 8},
 };
 
+/* Enthalpy density w(rho, p): Eq. (gammaEos) for gam > 0, Eq. (TMEos) for
+ * gam == 0. */
+static double enthalpy(double rho, double p, double gam)
+{
+    if (gam > 0.0)
+        return rho + gam / (gam - 1.0) * p;
+    return 2.5 * p + sqrt(2.25 * p * p + rho * rho);
+}
+
+/* Sound speed squared c_s^2 = (dp/de)_s / h for enthalpy density w:
+ * Gamma p / w for the ideal gas; p (5 w - 8 p) / (3 w (w - p)) for the
+ * Taub-Mathews equation of state (Mignone & McKinney 2007). */
+static double sound2(double p, double w, double gam)
+{
+    if (gam > 0.0)
+        return gam * p / w;
+    return p * (5.0 * w - 8.0 * p) / (3.0 * w * (w - p));
+}
+
 /* U(V), Section 2.2: D = rho gamma, m = (W + B^2) v - (v.B) B,
  * E = W - p + (B^2 + E_el^2)/2 - D with W = w gamma^2, E_el = -v x B. */
 void or_srmhd_prim2cons(const double *V, double gam, double *U)
@@ -49,7 +71,7 @@ void or_srmhd_prim2cons(const double *V, double gam, double *U)
     double v2 = vx * vx + vy * vy + vz * vz;
     double lor2 = 1.0 / (1.0 - v2);
     double lor = sqrt(lor2);
-    double w = rho + gam / (gam - 1.0) * p;
+    double w = enthalpy(rho, p, gam);
     double W = w * lor2;
     double B2 = bx * bx + by * by + bz * bz;
     double vB = vx * bx + vy * by + vz * bz;
@@ -66,8 +88,11 @@ void or_srmhd_prim2cons(const double *V, double gam, double *U)
 }
 
 /* f(W) = W - p(W) + B^2 (1 + v^2(W))/2 - S^2/(2 W^2) - (E + D) and f'(W),
- * with v^2(W) = (m^2 W^2 + S^2 (2W + B^2)) / (W^2 (W + B^2)^2) and
- * p = (Gamma-1)/Gamma (W (1 - v^2) - D sqrt(1 - v^2)).
+ * with v^2(W) = (m^2 W^2 + S^2 (2W + B^2)) / (W^2 (W + B^2)^2) and p from
+ * w = W (1 - v^2) and rho = D sqrt(1 - v^2): the ideal gas
+ * p = (Gamma-1)/Gamma (w - rho) (g1 = (Gamma-1)/Gamma > 0), or, for g1 = 0,
+ * the inverse of Eq. (TMEos), p = (5 w - sqrt(9 w^2 + 16 rho^2))/8,
+ * evaluated as 2 (w - rho)(w + rho)/(5 w + sqrt(9 w^2 + 16 rho^2)).
  * Returns 0 if v^2 >= 1 (W below the physical range), 1 otherwise. */
 static int rec_eval(double W, double D, double m2, double S2, double B2, double tau, double g1,
                     double *f, double *df, double *v2o, double *po)
@@ -83,8 +108,17 @@ static int rec_eval(double W, double D, double m2, double S2, double B2, double 
     dDn = 2.0 * W * Wb * (2.0 * W + B2);
     dv2 = (dN * Dn - N * dDn) / (Dn * Dn);
     s = sqrt(1.0 - v2);
-    p = g1 * (W * (1.0 - v2) - D * s);
-    dp = g1 * ((1.0 - v2) + dv2 * (0.5 * D / s - W));
+    if (g1 > 0.0) {
+        p = g1 * (W * (1.0 - v2) - D * s);
+        dp = g1 * ((1.0 - v2) + dv2 * (0.5 * D / s - W));
+    } else {
+        double w = W * (1.0 - v2), rho = D * s;
+        double q = sqrt(9.0 * w * w + 16.0 * rho * rho);
+        double dpdw = (5.0 - 9.0 * w / q) / 8.0, dpdr = -2.0 * rho / q;
+        p = 2.0 * (w - rho) * (w + rho) / (5.0 * w + q);
+        /* dw/dW = (1 - v^2) - W dv^2/dW, drho/dW = -D dv^2/dW / (2 sqrt(1 - v^2)) */
+        dp = dpdw * ((1.0 - v2) - W * dv2) - dpdr * 0.5 * D * dv2 / s;
+    }
     *f = W - p + 0.5 * B2 * (1.0 + v2) - 0.5 * S2 / (W * W) - tau;
     *df = 1.0 - dp + 0.5 * B2 * dv2 + S2 / (W * W * W);
     *v2o = v2;
@@ -103,7 +137,7 @@ int or_srmhd_cons2prim(const double *U, double gam, double *V)
     double B2 = bx * bx + by * by + bz * bz;
     double S = mx * bx + my * by + mz * bz;
     double S2 = S * S;
-    double g1 = (gam - 1.0) / gam;
+    double g1 = gam > 0.0 ? (gam - 1.0) / gam : 0.0;
     double Wlo = 0.0, Whi, W, f = 0.0, df = 1.0, v2 = 0.0, p = 0.0;
     int it, k, conv = 0;
 
@@ -162,8 +196,8 @@ void or_srmhd_fast_speeds(const double *V, double gam, double *lm, double *lp)
     double v2 = V[1] * V[1] + V[2] * V[2] + V[3] * V[3];
     double B2 = V[5] * V[5] + V[6] * V[6] + V[7] * V[7];
     double vB = V[1] * V[5] + V[2] * V[6] + V[3] * V[7];
-    double rh = rho + gam / (gam - 1.0) * p; /* rho h = w */
-    double cs2 = gam * p / rh;
+    double rh = enthalpy(rho, p, gam); /* rho h = w */
+    double cs2 = sound2(p, rh, gam);
     double b2 = B2 * (1.0 - v2) + vB * vB; /* comoving b^2 = B^2/gamma^2 + (v.B)^2 */
     double ca2 = b2 / (rh + b2);
     double a2 = cs2 + ca2 - cs2 * ca2;
@@ -185,7 +219,7 @@ static void rflux(const double *V, const double *U, double gam, double ch, doubl
     double bx = V[5], by = V[6], bz = V[7];
     double v2 = vx * vx + vy * vy + vz * vz;
     double lor2 = 1.0 / (1.0 - v2);
-    double w = V[0] + gam / (gam - 1.0) * p;
+    double w = enthalpy(V[0], p, gam);
     double W = w * lor2;
     double ex = -(vy * bz - vz * by), ey = -(vz * bx - vx * bz), ez = -(vx * by - vy * bx);
     double B2 = bx * bx + by * by + bz * bz;

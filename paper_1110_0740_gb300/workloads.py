@@ -172,14 +172,17 @@ def mhd_lowbeta_3d(n=256, seed=0, gamma=5.0 / 3.0, kmax=8, beta=0.01, mach=10.0,
 
 
 def srmhd_cons(V, gamma):
-    """Conserved state (D, m, E - D... see below) of an ideal-gas special
-    relativistic MHD initial condition from primitives (rho, v, p, B, psi):
+    """Conserved state (D, m, E - D... see below) of a special relativistic
+    MHD initial condition from primitives (rho, v, p, B, psi):
     D = rho gamma, m = (W + B^2) v - (v.B) B, E = W - p + (B^2 + E_el^2)/2 - D
-    with W = (rho + Gamma p/(Gamma-1)) gamma^2 and E_el = -v x B."""
+    with W = w gamma^2, E_el = -v x B and the enthalpy density of the ideal
+    gas, w = rho + Gamma p/(Gamma-1) (gamma = Gamma > 1), or of the
+    Taub-Mathews gas, w = 5/2 p + sqrt(9/4 p^2 + rho^2) (gamma = 0)."""
     rho, vx, vy, vz, p, bx, by, bz, psi = V
     v2 = vx * vx + vy * vy + vz * vz
     lor2 = 1.0 / (1.0 - v2)
-    W = (rho + gamma / (gamma - 1.0) * p) * lor2
+    w = rho + gamma / (gamma - 1.0) * p if gamma > 0 else 2.5 * p + np.sqrt(2.25 * p * p + rho * rho)
+    W = w * lor2
     B2 = bx * bx + by * by + bz * bz
     vB = vx * bx + vy * by + vz * bz
     E2 = B2 * v2 - vB * vB
@@ -195,7 +198,8 @@ def srmhd_jet_3d(n=256, seed=0, gamma=4.0 / 3.0, lorentz=10.0, rho_ratio=0.01, s
     (smooth tanh edge over ~2 cells), ambient rho = rho_ratio at rest, uniform
     p = p0, uniform B_z set so that sigma = B^2/(rho h gamma^2) = `sigma` on
     the beam axis, and seeded 1 % perturbations of rho and of the transverse
-    velocity.  Periodic unit cube; returns U with ghosts."""
+    velocity.  gamma = 0 takes the Taub-Mathews equation of state.  Periodic
+    unit cube; returns U with ghosts."""
     rng = np.random.default_rng(seed)
     x = (np.arange(n) + 0.5) / n
     c = rng.uniform(0.3, 0.7, size=2)
@@ -212,7 +216,8 @@ def srmhd_jet_3d(n=256, seed=0, gamma=4.0 / 3.0, lorentz=10.0, rho_ratio=0.01, s
     vy = pert * (2.0 * rng.random((n, n, n)) - 1.0) * prof3
     vz = vz * np.sqrt(np.maximum(1.0 - (vx ** 2 + vy ** 2) / np.maximum(vz ** 2, 1e-300), 0.0))
     p = np.full((n, n, n), p0)
-    h_axis = 1.0 + gamma / (gamma - 1.0) * p0 / 1.0
+    # specific enthalpy on the axis (rho = 1): ideal gas, or Taub-Mathews (gamma = 0)
+    h_axis = 1.0 + gamma / (gamma - 1.0) * p0 if gamma > 0 else 2.5 * p0 + np.sqrt(2.25 * p0 * p0 + 1.0)
     bz0 = np.sqrt(sigma * 1.0 * h_axis * lorentz ** 2)
     z = np.zeros((n, n, n))
     U = srmhd_cons([rho, vx, vy, vz, p, z, z, z + bz0, z], gamma)
