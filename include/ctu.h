@@ -108,8 +108,10 @@ typedef struct {
                          primitive recovery (Newton-Raphson) is float64 in
                          both precisions.  Other combinations return
                          CTU_EUNSUPPORTED. */
-    int eos;          /* CTU_EOS_IDEAL */
-    double gamma;     /* ratio of specific heats, > 1 */
+    int eos;          /* CTU_EOS_IDEAL: ideal gas, Eq. (gammaEos);
+                         CTU_EOS_TM: Taub-Mathews, Eq. (TMEos), CTU_SRMHD only
+                         (CTU_MHD returns CTU_EUNSUPPORTED) */
+    double gamma;     /* ratio of specific heats, > 1 (ignored with CTU_EOS_TM) */
     int ndim;         /* 1, 2 or 3 active dimensions; v_z, B_z always carried */
     int recon;        /* CTU_LINEAR_MC, CTU_PPM, ... (above; Section 3.2) */
     int predictor;    /* CTU_CHAR_TRACE (MHD) or CTU_MUSCL_HANCOCK (SRMHD) */
@@ -119,7 +121,7 @@ typedef struct {
     double glm_alpha; /* c_h^2/c_p^2 = glm_alpha * c_h / min(dx): psi decays by
                          exp(-glm_alpha c_h dt / min dx) per step */
     int nghost;       /* must be 4 */
-    int trace_mode;   /* CTU_TRACE_ALL or CTU_TRACE_UPWIND */
+    int trace_mode;   /* CTU_TRACE_* (above) */
     /* Optional floors of the updated state, >= 0, 0 = off; CTU_MHD only
      * (CTU_SRMHD with a floor returns CTU_EUNSUPPORTED).  The paper fixes no
      * floor: its safeguard against non-physical states is the shock-flagged

@@ -341,10 +341,12 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.patches = ctx->dpatch;
     a.npatch = np;
     a.ndim = ctx->cfg.ndim;
-    a.gam = ctx->cfg.gamma;
-    a.igm = 1.0 / (ctx->cfg.gamma - 1.0);
-    a.gamf = (float)ctx->cfg.gamma;
-    a.gm1f = (float)(ctx->cfg.gamma - 1.0);
+    // the relativistic path reads gam == 0 as the Taub-Mathews equation of state
+    const bool tm = ctx->cfg.eos == CTU_EOS_TM;
+    a.gam = tm ? 0.0 : ctx->cfg.gamma;
+    a.igm = tm ? 0.0 : 1.0 / (ctx->cfg.gamma - 1.0);
+    a.gamf = (float)a.gam;
+    a.gm1f = tm ? 0.0f : (float)(ctx->cfg.gamma - 1.0);
     a.glm_alpha = ctx->cfg.glm_alpha;
     a.upwind = ctx->cfg.trace_mode;
     a.limiter = ctx->cfg.recon;
@@ -424,8 +426,10 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
     if (!cfg || !out) return CTU_EINVAL;
     *out = nullptr;
     if (cfg->physics != CTU_MHD && cfg->physics != CTU_SRMHD) return CTU_EINVAL;
-    if (cfg->eos != CTU_EOS_IDEAL) return CTU_EUNSUPPORTED;
-    if (!(cfg->gamma > 1.0)) return CTU_EINVAL;
+    if (cfg->eos != CTU_EOS_IDEAL && cfg->eos != CTU_EOS_TM) return CTU_EINVAL;
+    // the Taub-Mathews equation of state belongs to relativistic MHD
+    if (cfg->eos == CTU_EOS_TM && cfg->physics != CTU_SRMHD) return CTU_EUNSUPPORTED;
+    if (cfg->eos == CTU_EOS_IDEAL && !(cfg->gamma > 1.0)) return CTU_EINVAL;
     if (cfg->ndim < 1 || cfg->ndim > 3) return CTU_EINVAL;
     if (cfg->recon < CTU_LINEAR_MC || cfg->recon > CTU_WENO3) return CTU_EINVAL;
     if (cfg->predictor != CTU_CHAR_TRACE && cfg->predictor != CTU_MUSCL_HANCOCK) return CTU_EINVAL;

@@ -420,7 +420,7 @@ __device__ __forceinline__ unsigned int sr_interface(const R (&W)[NV], const R (
     // Newton starts from the W of the predicted state V* (the transverse
     // correction T is an O(dt) change)
     const double v2 = (double)W[1] * W[1] + (double)W[2] * W[2] + (double)W[3] * W[3];
-    const double W0 = ((double)W[0] + a.gam * a.igm * (double)W[4]) * rcp64(1.0 - v2);
+    const double W0 = sr_w<double>((double)W[0], (double)W[4], a.gam) * rcp64(1.0 - v2);
 #pragma unroll
     for (int q = 0; q < NV; ++q) U[q] += (double)T[q];
     const unsigned int st = sr_prim<R>(U, a.gam, V, W0);

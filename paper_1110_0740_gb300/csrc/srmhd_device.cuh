@@ -1,6 +1,8 @@
 // srmhd_device.cuh -- device arithmetic of special-relativistic MHD (GLM):
 // Section 2.2 of Mignone et al. (2012), Eq. (rmhd) with the ideal-gas
-// enthalpy of Eq. (gammaEos); the primitive MUSCL-Hancock normal predictor
+// enthalpy of Eq. (gammaEos) or the Taub-Mathews one of Eq. (TMEos) (every
+// function's gam: Gamma, or 0 for Taub-Mathews); the primitive MUSCL-Hancock
+// normal predictor
 // of Section 3.3; HLL fluxes (Harten, Lax & van Leer) with the exact (B_n,
 // psi) GLM face solve (Dedner et al. 2002); signal speeds from the effective
 // sound speed a^2 = c_s^2 + c_a^2 - c_s^2 c_a^2 (Leismann et al. 2005, Del
@@ -52,6 +54,22 @@ template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return
 template <class T> __device__ __forceinline__ T sqrt_t(T x) { return x > T(0) ? x * rsqrt_t<T>(x) : T(0); }
 template <> __device__ __forceinline__ float sqrt_t<float>(float x) { return sqrtf(x); }
 
+// Enthalpy density w(rho, p): the ideal gas of Eq. (gammaEos) for gam > 0
+// (Gamma = gam), the Taub-Mathews gas of Eq. (TMEos) for gam == 0.
+template <class T> __device__ __forceinline__ T sr_w(T rho, T p, T gam)
+{
+    if (gam > T(0)) return rho + gam * rcp_t<T>(gam - T(1)) * p;
+    return T(2.5) * p + sqrt_t<T>(T(2.25) * p * p + rho * rho);
+}
+
+// Sound speed squared for enthalpy density w: Gamma p / w (ideal gas), or
+// p (5 w - 8 p) / (3 w (w - p)) (Taub-Mathews, Mignone & McKinney 2007).
+template <class T> __device__ __forceinline__ T sr_cs2(T p, T w, T gam)
+{
+    if (gam > T(0)) return gam * p / w;
+    return p * (T(5) * w - T(8) * p) / (T(3) * w * (w - p));
+}
+
 // U(V) in precision T (T = double for states that feed a recovery).
 template <class T, class R>
 __device__ __forceinline__ void sr_cons(const R (&V)[NV], T gam, T (&U)[NV])
@@ -60,7 +78,7 @@ __device__ __forceinline__ void sr_cons(const R (&V)[NV], T gam, T (&U)[NV])
     const T bx = V[5], by = V[6], bz = V[7];
     const T v2 = vx * vx + vy * vy + vz * vz;
     const T lor2 = rcp_t<T>(T(1) - v2);
-    const T W = (rho + gam * rcp_t<T>(gam - T(1)) * p) * lor2;
+    const T W = sr_w<T>(rho, p, gam) * lor2;
     const T B2 = bx * bx + by * by + bz * bz;
     const T vB = vx * bx + vy * by + vz * bz;
     const T E2 = B2 * v2 - vB * vB;
@@ -78,8 +96,10 @@ __device__ __forceinline__ void sr_cons(const R (&V)[NV], T gam, T (&U)[NV])
 // f(W) and f'(W) of the energy equation at fixed D, |m|^2, S = m.B, B^2,
 // tau = E + D: f = W - p + B^2 (1 + v^2)/2 - S^2/(2 W^2) - tau with
 // v^2(W) = (m^2 W^2 + S^2 (2W + B^2)) / (W^2 (W + B^2)^2),
-// p = (Gamma-1)/Gamma (W (1 - v^2) - D sqrt(1 - v^2)).  false if v^2 >= 1.
-// The same with dv^2/dW and dp/dW.
+// p from w = W (1 - v^2) and rho = D sqrt(1 - v^2): the ideal gas
+// p = (Gamma-1)/Gamma (w - rho) for g1 = (Gamma-1)/Gamma > 0, or for g1 == 0
+// the Taub-Mathews inverse 2 (w - rho)(w + rho)/(5 w + sqrt(9 w^2 + 16 rho^2)).
+// false if v^2 >= 1.  The same with dv^2/dW and dp/dW.
 __device__ __forceinline__ bool sr_energy_d(double W, double D, double m2, double S2, double B2, double tau,
                                             double g1, double &f, double &df, double &v2, double &p, double &dv2,
                                             double &dp)
@@ -95,8 +115,17 @@ __device__ __forceinline__ bool sr_energy_d(double W, double D, double m2, doubl
     dv2 = (dN * Dn - N * dDn) * iDn * iDn;
     const double is = rsqrt64(1.0 - v2);  // gamma
     const double s = (1.0 - v2) * is;
-    p = g1 * (W * (1.0 - v2) - D * s);
-    dp = g1 * ((1.0 - v2) + dv2 * (0.5 * D * is - W));
+    if (g1 > 0.0) {
+        p = g1 * (W * (1.0 - v2) - D * s);
+        dp = g1 * ((1.0 - v2) + dv2 * (0.5 * D * is - W));
+    } else {
+        const double w = W * (1.0 - v2), rho = D * s;
+        const double q2 = 9.0 * w * w + 16.0 * rho * rho;
+        const double iq = rsqrt64(q2), q = q2 * iq;
+        const double dpdw = 0.625 - 1.125 * w * iq, dpdr = -2.0 * rho * iq;
+        p = 2.0 * (w - rho) * (w + rho) * rcp64(5.0 * w + q);
+        dp = dpdw * ((1.0 - v2) - W * dv2) - dpdr * 0.5 * D * dv2 * is;
+    }
     const double iW = rcp64(W);
     f = W - p + 0.5 * B2 * (1.0 + v2) - 0.5 * S2 * iW * iW - tau;
     df = 1.0 - dp + 0.5 * B2 * dv2 + S2 * iW * iW * iW;
@@ -126,8 +155,18 @@ __device__ __forceinline__ bool sr_energy_f(float W, float D, float m2, float S2
     const float dv2 = (dN * Dn - N * dDn) * iDn * iDn;
     const float is = rsqrtf(1.0f - v2);
     const float sq = (1.0f - v2) * is;
-    const float p = g1 * (W * (1.0f - v2) - D * sq);
-    const float dp = g1 * ((1.0f - v2) + dv2 * (0.5f * D * is - W));
+    float p, dp;
+    if (g1 > 0.0f) {
+        p = g1 * (W * (1.0f - v2) - D * sq);
+        dp = g1 * ((1.0f - v2) + dv2 * (0.5f * D * is - W));
+    } else {
+        const float w = W * (1.0f - v2), rho = D * sq;
+        const float q2 = 9.0f * w * w + 16.0f * rho * rho;
+        const float iq = rsqrtf(q2), q = q2 * iq;
+        const float dpdw = 0.625f - 1.125f * w * iq, dpdr = -2.0f * rho * iq;
+        p = 2.0f * (w - rho) * (w + rho) / (5.0f * w + q);
+        dp = dpdw * ((1.0f - v2) - W * dv2) - dpdr * 0.5f * D * dv2 * is;
+    }
     const float iW = 1.0f / W;
     f = W - p + 0.5f * B2 * (1.0f + v2) - 0.5f * S2 * iW * iW - tau;
     df = 1.0f - dp + 0.5f * B2 * dv2 + S2 * iW * iW * iW;
@@ -171,7 +210,7 @@ __device__ __forceinline__ unsigned int sr_prim64(const double (&U)[NV], double 
     const double B2 = U[5] * U[5] + U[6] * U[6] + U[7] * U[7];
     const double S = U[1] * U[5] + U[2] * U[6] + U[3] * U[7];
     const double S2 = S * S;
-    const double g1 = (gam - 1.0) * rcp64(gam);
+    const double g1 = gam > 0.0 ? (gam - 1.0) * rcp64(gam) : 0.0;
     V[5] = U[5]; V[6] = U[6]; V[7] = U[7]; V[8] = U[8];
     if (!(D > 0.0) || !(tau > 0.0)) {
         V[0] = D; V[1] = V[2] = V[3] = 0.0; V[4] = 0.0;
@@ -243,7 +282,7 @@ __device__ __forceinline__ unsigned int sr_prim_mixed(const double (&U)[NV], dou
     const double B2 = U[5] * U[5] + U[6] * U[6] + U[7] * U[7];
     const double S = U[1] * U[5] + U[2] * U[6] + U[3] * U[7];
     const double S2 = S * S;
-    const double g1 = (gam - 1.0) * rcp64(gam);
+    const double g1 = gam > 0.0 ? (gam - 1.0) * rcp64(gam) : 0.0;
     if (!(D > 0.0) || !(tau > 0.0)) return sr_prim64(U, gam, V, W0);
     auto tof = [](double x) {
         const df h = df_split(x);
@@ -299,8 +338,8 @@ __device__ __forceinline__ void sr_speeds(const R (&V)[NV], R gam, R &lm, R &lp)
     const R v2 = V[1] * V[1] + V[2] * V[2] + V[3] * V[3];
     const R B2 = V[5] * V[5] + V[6] * V[6] + V[7] * V[7];
     const R vB = V[1] * V[5] + V[2] * V[6] + V[3] * V[7];
-    const R rh = V[0] + gam * rcp_t<R>(gam - R(1)) * V[4];
-    const R cs2 = gam * V[4] / rh;
+    const R rh = sr_w<R>(V[0], V[4], gam);
+    const R cs2 = sr_cs2<R>(V[4], rh, gam);
     const R b2 = B2 * (R(1) - v2) + vB * vB;
     const R ca2 = b2 * rcp_t<R>(rh + b2);
     const R a2 = cs2 + ca2 - cs2 * ca2;
@@ -321,7 +360,7 @@ __device__ __forceinline__ void sr_flux(const R (&V)[NV], const R (&U)[NV], R ga
     const R vx = V[1], vy = V[2], vz = V[3], p = V[4];
     const R bx = V[5], by = V[6], bz = V[7];
     const R v2 = vx * vx + vy * vy + vz * vz;
-    const R W = (V[0] + gam * rcp_t<R>(gam - R(1)) * p) * rcp_t<R>(R(1) - v2);
+    const R W = sr_w<R>(V[0], p, gam) * rcp_t<R>(R(1) - v2);
     const R ex = -(vy * bz - vz * by), ey = -(vz * bx - vx * bz), ez = -(vx * by - vy * bx);
     const R pt = p + R(0.5) * (bx * bx + by * by + bz * bz + ex * ex + ey * ey + ez * ez);
     F[0] = U[0] * vx;
@@ -397,7 +436,7 @@ __device__ __forceinline__ unsigned int sr_mh_predict(const R (&vm1)[NV], const 
     for (int q = 0; q < NV; ++q) Us[q] = U0[q] - (double)(h * (Fp[q] - Fm[q]));
     // Newton starts from the cell-centre W = w gamma^2 (U* is an O(dt) update of U_i)
     const double v2c = (double)v0[1] * v0[1] + (double)v0[2] * v0[2] + (double)v0[3] * v0[3];
-    const double Wc = ((double)v0[0] + gamd * rcp64(gamd - 1.0) * (double)v0[4]) * rcp64(1.0 - v2c);
+    const double Wc = sr_w<double>((double)v0[0], (double)v0[4], gamd) * rcp64(1.0 - v2c);
     const unsigned int st = sr_prim<R>(Us, gamd, Vs, Wc);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {

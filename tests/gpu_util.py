@@ -31,7 +31,7 @@ def l1rel(got, ref, ch=None, group_floor=False):
 
 
 def gpu_run(U0, n, ndim, dx, steps, cfl, precision=0, recon=1, trace_mode=0, glm_alpha=0.1,
-            gamma=5.0 / 3.0, physics=0):
+            gamma=5.0 / 3.0, physics=0, eos=0):
     """Advance one periodic patch `steps` steps on the GPU; returns
     (U ghosted numpy, list of (dt, ch), status)."""
     import torch
@@ -43,7 +43,7 @@ def gpu_run(U0, n, ndim, dx, steps, cfl, precision=0, recon=1, trace_mode=0, glm
     if physics == ctu.CTU_SRMHD:
         cfg = ctu.make_config(ndim=ndim, gamma=gamma, recon=ctu.CTU_LINEAR_MC, precision=precision,
                               cfl=cfl, glm_alpha=glm_alpha, physics=ctu.CTU_SRMHD,
-                              predictor=ctu.CTU_MUSCL_HANCOCK, riemann=ctu.CTU_HLL)
+                              predictor=ctu.CTU_MUSCL_HANCOCK, riemann=ctu.CTU_HLL, eos=eos)
     else:
         cfg = ctu.make_config(ndim=ndim, gamma=gamma, recon=recon, precision=precision, cfl=cfl,
                               glm_alpha=glm_alpha, trace_mode=trace_mode)

@@ -103,3 +103,47 @@ def test_srmhd_bad_state_flags():
     ctx.step(U, Uo, U.shape[1], p, dtch)
     assert ctu.STATUS[ctx.status_sync()] in ("CTU_ENEGATIVE", "CTU_ERECOVERY", "CTU_ESUPERLUMINAL",
                                              "CTU_ENAN")
+
+
+@pytest.mark.parametrize("prec,tol", [(0, TOL64), (1, 2e-4)])
+def test_srmhd_taub_mathews_jet_3d(prec, tol):
+    """The Taub-Mathews equation of state (Eq. TMEos): the gamma-10 beam on
+    24^3, 5 steps, against the oracle with the same equation of state.  The
+    beam runs at p0 = 0.05: at the workload's 0.01 the Taub-Mathews gas,
+    stiffer when cold (Gamma -> 5/3), reaches negative pressure at the beam
+    edge by the second step in the oracle and on the GPU alike."""
+    n = [24, 24, 24]
+    U0 = W.srmhd_jet_3d(24, seed=8, gamma=0.0, p0=0.05)
+    dx = [1 / 24] * 3
+    got, gd, st = gpu_run(U0, n, 3, dx, 5, 0.3, precision=prec, gamma=0.0, physics=1, eos=1)
+    assert st == 0
+    ref, _, od = O.srmhd_run(U0, n, 3, dx, 5, 0.3, gamma=0.0)
+    for (a, b), (c, d) in zip(gd, od):
+        assert abs(a - c) <= (1e-13 if prec == 0 else 1e-5) * c
+    e = l1rel(O.interior(got, n, 3), O.interior(ref, n, 3), od[-1][1], group_floor=True)
+    assert np.all(e <= tol), e
+
+
+def test_srmhd_taub_mathews_hot_wave_fp64():
+    """A hot (p/rho ~ 10) relativistic 2-D wave with the Taub-Mathews gas."""
+    n = [32, 32, 1]
+    x = (np.arange(32) + 0.5) / 32
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    rho = 1 + 0.3 * np.sin(2 * np.pi * (X + Y))
+    z = np.zeros_like(rho)
+    Vp = [rho, 0.3 + 0.1 * np.cos(2 * np.pi * Y), z + 0.4, z + 0.1, 10.0 + np.sin(2 * np.pi * X),
+          z + 0.3, 0.4 + 0.1 * np.cos(2 * np.pi * X), z + 0.2, z]
+    U0 = np.zeros(O.shape(n, 2))
+    O.interior(U0, n, 2)[:] = W.srmhd_cons(Vp, 0.0)[:, None]
+    got, gd, st = gpu_run(U0, n, 2, [1 / 32, 1 / 32], 10, 0.4, gamma=0.0, physics=1, eos=1)
+    assert st == 0
+    ref, _, od = O.srmhd_run(U0, n, 2, [1 / 32, 1 / 32, 1.0], 10, 0.4, gamma=0.0)
+    e = l1rel(O.interior(got, n, 2), O.interior(ref, n, 2), od[-1][1])
+    assert np.all(e <= TOL64), e
+
+
+def test_taub_mathews_is_relativistic_only():
+    from paper_1110_0740_gb300 import ctu
+    with pytest.raises(ctu.CtuError) as e:
+        ctu.Ctx(ctu.make_config(eos=ctu.CTU_EOS_TM))
+    assert e.value.code == 4
