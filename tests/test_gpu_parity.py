@@ -130,3 +130,30 @@ def test_gpu_step_commutes_with_mirrors_and_swap(prec, tol):
         got, _, st = gpu_run(f(U3), n3, 3, d3, 3, 0.3, precision=prec, recon=1)
         assert st == 0
         assert np.all(np.abs(O.interior(f(got), n3, 3) - R3) <= tol * scale3)
+
+
+@pytest.mark.parametrize("shape", [[2000, 6, 5], [7, 1500, 6], [6, 5, 1800]])
+def test_extreme_aspect_patches(shape):
+    """Long thin patches along each axis (tile and marching-segment index
+    arithmetic at large extents, ragged in the short dimensions): FP64 and
+    mixed, 2 steps, against the oracle."""
+    n = list(shape)
+    rng = np.random.default_rng(sum(n))
+    shp = O.shape(n, 3)
+    # a smooth state with a gentle gradient along the long axis
+    ax = int(np.argmax(n))
+    c = (np.arange(shp[3 - ax]) + 0.5) / shp[3 - ax]
+    view = [1, 1, 1]
+    view[2 - ax] = shp[3 - ax]
+    prof = np.sin(2 * np.pi * 3 * c).reshape(view)
+    z = np.zeros(shp[1:])
+    V = [1.0 + 0.2 * prof + z, 0.3 * prof + z, 0.1 + z, -0.2 * prof + z, 1.0 + 0.1 * prof + z,
+         0.5 + z, 0.4 * prof + z, 0.3 + z, z]
+    U0 = W.ideal_cons(V, 5.0 / 3.0) + 1e-3 * rng.normal(size=shp) * np.array([1, 0, 0, 0, 1, 0, 0, 0, 0])[:, None, None, None]
+    dx = [1.0 / max(n)] * 3
+    ref, od = oracle_run(U0, n, 3, dx, 2, 0.3, recon=1)
+    for prec, tol in ((0, TOL64), (1, 2e-5)):
+        got, _, st = gpu_run(U0, n, 3, dx, 2, 0.3, precision=prec, recon=1)
+        assert st == 0
+        e = l1rel(O.interior(got, n, 3), O.interior(ref, n, 3), od[-1][1])
+        assert np.all(e <= tol), (shape, prec, e)
