@@ -125,3 +125,32 @@ def test_hybrid_survives_where_the_plain_step_fails():
     a, b = O.interior(U, n, 2), O.interior(R, n, 2)
     for q in (0, 1, 2, 4, 5, 6):
         assert abs(b[q].sum() - a[q].sum()) <= 1e-12 * (np.abs(a[q]).sum() + 1.0)
+
+
+@pytest.mark.parametrize("recon,reach", [(1, 2), (0, 1)])
+def test_hybrid_step_changes_exactly_the_reach_of_the_flags(recon, reach):
+    """1-D: a jump between cells 11 and 12 with converging flow, on a gently
+    modulated background (so that MinMod and the scheme's reconstruction
+    differ everywhere).  Cells 11 and 12 are shocked; the hybrid step
+    differs from the plain one exactly on the cells whose update uses a face
+    next to a shocked cell or a MinMod interface state: [11 - reach - 1,
+    12 + reach + 1] (MinMod on the cells within `reach` of a shocked cell,
+    2 for PPM and 1 for MC)."""
+    n = [24, 1, 1]
+    shp = O.shape(n, 1)
+    c = np.arange(shp[3]) - 4
+    mod = 1.0 + 0.01 * np.sin(0.7 * c)
+    rho = mod.copy()
+    p = np.where(c < 12, 1.0, 10.0) * mod
+    v = np.where(c < 12, 0.5, -0.5) + 0.01 * np.cos(0.9 * c)
+    z = np.zeros_like(rho)
+    U = np.zeros(shp)
+    U[:, 0, 0] = W.ideal_cons([rho, v, z, z, p, z + 0.3, z + 0.2, z + 0.1, z], G)
+    dx = [1.0 / 24]
+    f = O.mhd_shock_flags(U, n, 1, dx, 5.0, 0, reach)
+    assert np.nonzero(f[0, 0, 4:-4] & 1)[0].tolist() == [11, 12]
+    dt, ch = 0.002, 1.0
+    a, _ = O.mhd_step(U, n, 1, dx, dt, ch, recon=recon)
+    b, _ = O.mhd_step(U, n, 1, dx, dt, ch, recon=recon, shock=(5.0, 0))
+    diff = np.any(np.abs(O.interior(a, n, 1) - O.interior(b, n, 1)) > 1e-14, axis=(0, 1, 2))
+    assert np.nonzero(diff)[0].tolist() == list(range(11 - reach - 1, 12 + reach + 2))
