@@ -163,3 +163,32 @@ def uncovered(boxes, npatch, sizes, ndim):
             rest = [p for r in rest for p in _subtract(r, c)]
         out.append(rest)
     return out
+
+
+def ship_registers(items, rank, reg, sendrecv):
+    """Flux-register windows to the rank that applies the reflux (Eq.
+    fluxcorr, addreflux): a fine window accumulates on the rank that owns
+    the fine patch, while the correction lands on the coarse patch's owner.
+    items: (src_rank, src_off, dst_rank, dst_off, size) per window whose two
+    ranks differ (doubles of the register arrays); every rank passes the same
+    list.  reg: this rank's register array (a 1-D tensor); the received
+    windows overwrite reg[dst_off : dst_off + size] (ranges a rank receives
+    must not overlap ranges it sends).  Per peer, in increasing rank, one
+    sendrecv of the windows in list order."""
+    import torch
+    send, recv = {}, {}
+    for it in items:
+        s, so, d, do, n = it
+        if s == rank and d != rank:
+            send.setdefault(d, []).append((so, n))
+        elif d == rank and s != rank:
+            recv.setdefault(s, []).append((do, n))
+    for peer in sorted(set(send) | set(recv)):
+        parts = [reg[o:o + n] for o, n in send.get(peer, [])]
+        sb = torch.cat(parts) if parts else reg[:0]
+        nr = sum(n for _, n in recv.get(peer, []))
+        rb = sendrecv(peer, sb, nr)
+        pos = 0
+        for o, n in recv.get(peer, []):
+            reg[o:o + n] = rb[pos:pos + n]
+            pos += n

@@ -248,3 +248,63 @@ def test_exchange_and_uncovered_boxes_tile_the_ghost_shell():
             assert np.all(m[inner] == 0) and np.all(m[~inner] == 1), (i, per)
         if all(per[:ndim]):
             assert all(not u for u in unc)
+
+
+def _reg_rank_main(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        items, regs = _reg_case(world)
+        reg = torch.from_numpy(regs[rank].copy())
+        X.ship_registers(items, rank, reg, X.torch_sendrecv(reg))
+        out.put((rank, reg.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def _reg_case(world, S=400):
+    """Register arrays of every rank (seeded) and windows of random sizes,
+    each accumulated on one rank and refluxed on another (or the same)."""
+    rng = np.random.default_rng(4)
+    regs = [rng.normal(size=S) for _ in range(world)]
+    items, used = [], [set() for _ in range(world)]
+    for _ in range(12):
+        s, d = (int(v) for v in rng.integers(0, world, 2))
+        n = int(rng.integers(1, 20))
+        so = int(rng.integers(0, S - n))
+        # destination ranges of one rank do not overlap each other
+        while True:
+            do = int(rng.integers(0, S - n))
+            if not (set(range(do, do + n)) & used[d]):
+                used[d] |= set(range(do, do + n))
+                break
+        items.append((s, so, d, do, n))
+    return items, regs
+
+
+def test_registers_reach_the_coarse_owner():
+    """Two gloo ranks ship register windows: every window whose ranks differ
+    arrives at its destination range, everything else is untouched."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = 2
+    procs = [ctx.Process(target=_reg_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    items, regs = _reg_case(world)
+    want = [r.copy() for r in regs]
+    for s, so, d, do, n in items:
+        if s != d:
+            want[d][do:do + n] = regs[s][so:so + n]
+    assert any(s != d for s, _, d, _, _ in items)
+    for r in range(world):
+        assert np.array_equal(got[r], want[r])
