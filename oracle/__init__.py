@@ -62,9 +62,11 @@ def lib():
                                   ctypes.POINTER(ctypes.c_long), P, I, P]
         L.or_mhd_floor.restype = ctypes.c_long
         L.or_mhd_floor.argtypes = [P, I, I, I, I, D, D, D]
-        L.or_mhd_step_hybrid.restype = I
-        L.or_mhd_step_hybrid.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, I, I,
-                                         ctypes.POINTER(ctypes.c_long), P, I, P, I, D, I]
+        L.or_mhd_step_ex.restype = I
+        L.or_mhd_step_ex.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, I, I,
+                                     ctypes.POINTER(ctypes.c_long), P, I, P, I, I, D, I]
+        L.or_mhd_riemann_hllc.restype = I
+        L.or_mhd_riemann_hllc.argtypes = [P, P, D, D, P]
         L.or_mhd_riemann_hll.restype = I
         L.or_mhd_riemann_hll.argtypes = [P, P, D, D, P]
         L.or_mhd_shock_flags.restype = None
@@ -285,7 +287,7 @@ def fill_outflow(U, n, ndim):
 # ---------------------------------------------------------------- MHD step
 
 def mhd_step(U, n, ndim, dx, dt, ch, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
-             windows=None, reg=None, upwind=0, shock=None):
+             windows=None, reg=None, upwind=0, shock=None, riemann=0):
     """One CTU step of a ghost-filled patch; returns (Unew, n_bad_states).
 
     windows: optional list of (d, f, a0, a1, b0, b1, dst, weight) flux-register
@@ -305,11 +307,11 @@ def mhd_step(U, n, ndim, dx, dt, ch, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
         assert reg.dtype == np.float64 and reg.flags.c_contiguous
         regp = _dp(reg)
     sh = (0, 0.0, 0) if shock is None else (1, float(shock[0]), int(shock[1]))
-    bad = lib().or_mhd_step_hybrid(_dp(U), _dp(Un), int(n[0]), int(n[1]), int(n[2]), int(ndim),
-                                   float(dx[0]), float(dx[1]), float(dx[2]), float(dt), float(ch),
-                                   float(gamma), float(glm_alpha), int(recon), int(upwind),
-                                   win.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(wgt),
-                                   nwin, regp, *sh)
+    bad = lib().or_mhd_step_ex(_dp(U), _dp(Un), int(n[0]), int(n[1]), int(n[2]), int(ndim),
+                               float(dx[0]), float(dx[1]), float(dx[2]), float(dt), float(ch),
+                               float(gamma), float(glm_alpha), int(recon), int(upwind),
+                               win.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(wgt),
+                               nwin, regp, int(riemann), *sh)
     return Un, bad
 
 
@@ -323,6 +325,14 @@ def mhd_shock_flags(U, n, ndim, dx, eps_q=5.0, qkind=0, reach=2, gamma=5.0 / 3.0
                              float(dx[2]), float(gamma), float(eps_q), int(qkind), int(reach),
                              f.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
     return f
+
+
+def mhd_riemann_hllc(VL, VR, gamma, ch):
+    VL = np.ascontiguousarray(VL, dtype=np.float64)
+    VR = np.ascontiguousarray(VR, dtype=np.float64)
+    F = np.zeros(NVAR)
+    lib().or_mhd_riemann_hllc(_dp(VL), _dp(VR), float(gamma), float(ch), _dp(F))
+    return F
 
 
 def mhd_riemann_hll(VL, VR, gamma, ch):
@@ -431,7 +441,7 @@ def euler_sample(left, right, gamma, xi):
 
 
 def mhd_run(U, n, ndim, dx, steps, cfl, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
-            bc="periodic", t_end=None, upwind=0, shock=None):
+            bc="periodic", t_end=None, upwind=0, shock=None, riemann=0):
     """Advance a patch `steps` CTU steps (or up to t_end), filling ghosts each
     step; returns (U, t, dts)."""
     U = np.array(U, dtype=np.float64, copy=True)
@@ -449,7 +459,8 @@ def mhd_run(U, n, ndim, dx, steps, cfl, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
         dt, ch = dt_ch(m, list(dx), ndim, cfl)
         if t_end is not None and t + dt > t_end:
             dt = t_end - t
-        U, bad = mhd_step(U, n, ndim, dx, dt, ch, gamma, glm_alpha, recon, upwind=upwind, shock=shock)
+        U, bad = mhd_step(U, n, ndim, dx, dt, ch, gamma, glm_alpha, recon, upwind=upwind, shock=shock,
+                          riemann=riemann)
         if bad:
             raise FloatingPointError(f"oracle met {bad} unphysical states at step {k}")
         t += dt

@@ -466,6 +466,79 @@ int or_mhd_riemann_hll(const double *VL0, const double *VR0, double gam, double 
     return bad;
 }
 
+/* HLLC flux for MHD (Li 2005): the GLM face solve and outer speeds of
+ * or_mhd_riemann; the HLL average state U_hll gives the contact speed
+ * S_M = (rho u)_hll / rho_hll and the transverse field and velocity of both
+ * star states, B*_t = B_t,hll, v*_t = (rho v_t)_hll / rho_hll; with the
+ * total pressure p*_t = rho_L (S_L - u_L)(S_M - u_L) + p_t,L each star state
+ * is rho* = rho (S - u)/(S - S_M), (rho u)* = rho* S_M,
+ * (rho v_t)* = (rho v_t (S - u) - B_n (B*_t - B_t))/(S - S_M),
+ * E* = (E (S - u) - p_t u + p*_t S_M + B_n (v.B - v*.B*))/(S - S_M), and the
+ * flux is F + S (U* - U) on the side of the contact the face lies on.
+ * Returns 1 if an input state has rho <= 0 or p <= 0. */
+int or_mhd_riemann_hllc(const double *VL0, const double *VR0, double gam, double ch, double *F)
+{
+    double VL[NVAR], VR[NVAR], UL[NVAR], UR[NVAR], FL[NVAR], FR[NVAR], Uh[NVAR];
+    double Bm, pm, cfL, cfR, cmax, SL, SR;
+    int q, bad;
+    for (q = 0; q < NVAR; q++) {
+        VL[q] = VL0[q];
+        VR[q] = VR0[q];
+    }
+    bad = !(VL[0] > 0.0 && VL[4] > 0.0 && VR[0] > 0.0 && VR[4] > 0.0);
+    Bm = 0.5 * (VL[5] + VR[5]) - 0.5 * (VR[8] - VL[8]) / ch;
+    pm = 0.5 * (VL[8] + VR[8]) - 0.5 * ch * (VR[5] - VL[5]);
+    VL[5] = Bm;
+    VR[5] = Bm;
+    or_mhd_prim2cons(VL, gam, UL);
+    or_mhd_prim2cons(VR, gam, UR);
+    mhd_flux(VL, UL, FL);
+    mhd_flux(VR, UR, FR);
+    cfL = or_mhd_cfast(VL, gam);
+    cfR = or_mhd_cfast(VR, gam);
+    cmax = fmax(cfL, cfR);
+    SL = fmin(VL[1], VR[1]) - cmax;
+    SR = fmax(VL[1], VR[1]) + cmax;
+    if (SL >= 0.0) {
+        for (q = 0; q < NVAR; q++)
+            F[q] = FL[q];
+    } else if (SR <= 0.0) {
+        for (q = 0; q < NVAR; q++)
+            F[q] = FR[q];
+    } else {
+        const double Bn = Bm;
+        for (q = 0; q < NVAR; q++)
+            Uh[q] = (SR * UR[q] - SL * UL[q] - FR[q] + FL[q]) / (SR - SL);
+        const double SM = Uh[1] / Uh[0];
+        const double vy = Uh[2] / Uh[0], vz = Uh[3] / Uh[0];
+        const double By = Uh[6], Bz = Uh[7];
+        const double ptL = VL[4] + 0.5 * (Bn * Bn + VL[6] * VL[6] + VL[7] * VL[7]);
+        const double ptR = VR[4] + 0.5 * (Bn * Bn + VR[6] * VR[6] + VR[7] * VR[7]);
+        const double pts = VL[0] * (SL - VL[1]) * (SM - VL[1]) + ptL;
+        const double vBs = SM * Bn + vy * By + vz * Bz;
+        const int right = SM < 0.0;
+        const double *V = right ? VR : VL, *U = right ? UR : UL, *Fa = right ? FR : FL;
+        const double S = right ? SR : SL, pt = right ? ptR : ptL;
+        const double sd = S - V[1], den = S - SM;
+        double Us[NVAR];
+        const double vB = V[1] * Bn + V[2] * V[6] + V[3] * V[7];
+        Us[0] = V[0] * sd / den;
+        Us[1] = Us[0] * SM;
+        Us[2] = (V[0] * V[2] * sd - Bn * (By - V[6])) / den;
+        Us[3] = (V[0] * V[3] * sd - Bn * (Bz - V[7])) / den;
+        Us[4] = (U[4] * sd - pt * V[1] + pts * SM + Bn * (vB - vBs)) / den;
+        Us[5] = Bn;
+        Us[6] = By;
+        Us[7] = Bz;
+        Us[8] = U[8];
+        for (q = 0; q < NVAR; q++)
+            F[q] = Fa[q] + S * (Us[q] - U[q]);
+    }
+    F[5] = pm;
+    F[8] = ch * ch * Bm;
+    return bad;
+}
+
 /* ------------------------------------------------------------------ */
 /* Reconstruction, Section 3.2                                         */
 /* ------------------------------------------------------------------ */
@@ -813,30 +886,44 @@ double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
  * transverse cell widths) and F the n+1/2 flux through the face in +d.
  * Returns the number of states met with rho <= 0 or p <= 0.
  */
-int or_mhd_step_hybrid(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
-                       double dx, double dy, double dz, double dt, double ch,
-                       double gam, double glm_alpha, int recon, int upwind,
-                       const long *win, const double *wgt, int nwin, double *reg,
-                       int shock, double eps_q, int qkind);
+int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
+                   double dx, double dy, double dz, double dt, double ch,
+                   double gam, double glm_alpha, int recon, int upwind,
+                   const long *win, const double *wgt, int nwin, double *reg,
+                   int solver, int shock, double eps_q, int qkind);
 
 int or_mhd_step(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                 double dx, double dy, double dz, double dt, double ch,
                 double gam, double glm_alpha, int recon, int upwind,
                 const long *win, const double *wgt, int nwin, double *reg)
 {
-    return or_mhd_step_hybrid(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win,
-                              wgt, nwin, reg, 0, 0.0, 0);
+    return or_mhd_step_ex(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win,
+                          wgt, nwin, reg, 0, 0, 0.0, 0);
 }
 
-/* or_mhd_step with the hybrid integration of the appendix on shock detection
- * when shock != 0: the flags of shock_flags (eps_q, qkind) on V^n select
- * the HLL solver at the faces of shocked cells (first-order and n+1/2
- * fluxes) and the MinMod linear reconstruction for the cells near them. */
-int or_mhd_step_hybrid(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
-                       double dx, double dy, double dz, double dt, double ch,
-                       double gam, double glm_alpha, int recon, int upwind,
-                       const long *win, const double *wgt, int nwin, double *reg,
-                       int shock, double eps_q, int qkind)
+/* The Riemann solver of a face: HLL next to a cell the hybrid integration
+ * flagged, else HLLD (solver 0) or HLLC (solver 2). */
+static int face_riemann(const double *VL, const double *VR, double gam, double ch, int solver, int hll,
+                        double *F)
+{
+    if (hll)
+        return or_mhd_riemann_hll(VL, VR, gam, ch, F);
+    if (solver == 2)
+        return or_mhd_riemann_hllc(VL, VR, gam, ch, F);
+    return or_mhd_riemann(VL, VR, gam, ch, F);
+}
+
+/* or_mhd_step with the Riemann solver `solver` (0 HLLD, 2 HLLC; the same
+ * solver for the first-order and the n+1/2 fluxes) and, when shock != 0,
+ * the hybrid integration of the appendix on shock detection: the flags of
+ * shock_flags (eps_q, qkind) on V^n select the HLL solver at the faces of
+ * shocked cells (first-order and n+1/2 fluxes) and the MinMod linear
+ * reconstruction for the cells near them. */
+int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
+                   double dx, double dy, double dz, double dt, double ch,
+                   double gam, double glm_alpha, int recon, int upwind,
+                   const long *win, const double *wgt, int nwin, double *reg,
+                   int solver, int shock, double eps_q, int qkind)
 {
     unsigned char *flags = NULL;
     grid_t G;
@@ -890,10 +977,7 @@ int or_mhd_step_hybrid(const double *U, double *Unew, int nx, int ny, int nz, in
                         VL[q] = V[PERM[d][q] * nc + id];
                         VR[q] = V[PERM[d][q] * nc + id + st];
                     }
-                    if (flags && ((flags[id] | flags[id + st]) & 1))
-                        or_mhd_riemann_hll(VL, VR, gam, ch, Fl);
-                    else
-                        or_mhd_riemann(VL, VR, gam, ch, Fl);
+                    face_riemann(VL, VR, gam, ch, solver, flags && ((flags[id] | flags[id + st]) & 1), Fl);
                     for (q = 0; q < NVAR; q++)
                         F1[d][PERM[d][q] * nc + id] = Fl[q];
                 }
@@ -972,10 +1056,7 @@ int or_mhd_step_hybrid(const double *U, double *Unew, int nx, int ny, int nz, in
                         VL[q] = VLg[PERM[d][q]];
                         VR[q] = VRg[PERM[d][q]];
                     }
-                    if (flags && ((flags[id] | flags[id + st]) & 1))
-                        or_mhd_riemann_hll(VL, VR, gam, ch, Fl);
-                    else
-                        or_mhd_riemann(VL, VR, gam, ch, Fl);
+                    face_riemann(VL, VR, gam, ch, solver, flags && ((flags[id] | flags[id + st]) & 1), Fl);
                     for (q = 0; q < NVAR; q++)
                         F[d][PERM[d][q] * nc + id] = Fl[q];
                 }
