@@ -217,7 +217,8 @@ def run_ours(args):
 
     def make(prec):
         c = ctu.Ctx(ctu.make_config(ndim=3, recon=RECONS[args.recon], precision=prec, cfl=0.3,
-                                    shock=(args.shock, 0) if args.shock else None))
+                                    shock=(args.shock, 0) if args.shock else None,
+                                    riemann=ctu.CTU_HLLC if args.riemann == "hllc" else ctu.CTU_HLLD))
         c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
         if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
@@ -325,7 +326,7 @@ def run_ours(args):
     roof["hbm_step"] = {"algorithmic_bytes": nbytes, "achieved_gbs": hbm_achieved,
                         "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
                         "peak_source": f"{src} hbm_gbs"}
-    if mixed and args.recon == "ppm" and not args.shock:
+    if mixed and args.recon == "ppm" and not args.shock and args.riemann == "hlld":
         roof["precision_split"] = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
 
     # end-to-end through the public API with host buffers
@@ -373,7 +374,8 @@ def run_ours(args):
                 "dtype": "f32+f64" if primary == ctu.CTU_MIXED else "f64", "data": "synthetic",
                 "config": {"workload": (WORKLOAD if args.recon == "ppm" else
                                         WORKLOAD.replace("PPM", f"{args.recon} reconstruction"))
-                           + (f"; hybrid integration (shock flags, eps_q {args.shock})" if args.shock else ""),
+                           + (f"; hybrid integration (shock flags, eps_q {args.shock})" if args.shock else "")
+                           + ("; HLLC in place of HLLD" if args.riemann == "hllc" else ""),
                            "recon": args.recon, "shock_eps": args.shock or None,
                            "cells_per_gpu": cells, "patches_per_gpu": 1,
                            "precision": args.precision, "l2_flush": "inputs (1.3 GB) > L2",
@@ -894,6 +896,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-level-ops", action="store_true",
                     help="amr: advance the levels without prolongation, restriction and reflux")
+    ap.add_argument("--riemann", default="hlld", choices=["hlld", "hllc"],
+                    help="blast: the Riemann solver (the workload uses HLLD)")
     ap.add_argument("--shock", type=float, default=0.0,
                     help="blast: the hybrid integration with this shock threshold (thermal pressure; 0 = off)")
     ap.add_argument("--recon", default="ppm", choices=sorted(RECONS),

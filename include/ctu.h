@@ -70,7 +70,11 @@ enum { CTU_EOS_IDEAL = 0, CTU_EOS_TM = 1 };
 enum { CTU_LINEAR_MC = 0, CTU_PPM = 1, CTU_LINEAR_MINMOD = 2, CTU_LINEAR_HARMONIC = 3, CTU_LINEAR_VANALBADA = 4,
        CTU_WENO3 = 5 };
 enum { CTU_CHAR_TRACE = 0, CTU_MUSCL_HANCOCK = 1 };
-enum { CTU_HLLD = 0, CTU_HLL = 1 };
+/* Riemann solver: CTU_HLLD (MHD; Miyoshi & Kusano 2005), CTU_HLL (SRMHD),
+ * CTU_HLLC (MHD; Li 2005: PPM or MC-linear, trace modes ALL or UPWIND,
+ * CTU_FP64 or CTU_MIXED, no hybrid integration; else CTU_EUNSUPPORTED).
+ * The first-order transverse fluxes take the same solver. */
+enum { CTU_HLLD = 0, CTU_HLL = 1, CTU_HLLC = 2 };
 /* precision:
  *   CTU_FP64          all arithmetic in float64.
  *   CTU_MIXED         tracing, characteristic projections, Riemann fluxes and
@@ -115,7 +119,7 @@ typedef struct {
     int ndim;         /* 1, 2 or 3 active dimensions; v_z, B_z always carried */
     int recon;        /* CTU_LINEAR_MC, CTU_PPM, ... (above; Section 3.2) */
     int predictor;    /* CTU_CHAR_TRACE (MHD) or CTU_MUSCL_HANCOCK (SRMHD) */
-    int riemann;      /* CTU_HLLD (MHD) or CTU_HLL (SRMHD) */
+    int riemann;      /* CTU_HLLD or CTU_HLLC (MHD), CTU_HLL (SRMHD) */
     int precision;    /* CTU_FP64, CTU_MIXED or CTU_MIXED_IFACE64 (above) */
     double cfl;       /* C_a of Eq. (Ca): <= 1 in 2D, <= 1/2 in 3D */
     double glm_alpha; /* c_h^2/c_p^2 = glm_alpha * c_h / min(dx): psi decays by

@@ -382,8 +382,9 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
     const int r = ctx->cfg.recon;
     const bool ref = ctx->cfg.trace_mode >= CTU_TRACE_CENTER;
     const bool hyb = ctx->cfg.shock_detect != 0;
-    li.recon = r == CTU_PPM ? (hyb ? RECON_PPM_HYB : (ref ? RECON_PPM_REF : RECON_PPM))
-             : r == CTU_LINEAR_MC ? (hyb ? RECON_MC_HYB : (ref ? RECON_MC_REF : RECON_MC))
+    const bool hllc = ctx->cfg.physics == CTU_MHD && ctx->cfg.riemann == CTU_HLLC;
+    li.recon = r == CTU_PPM ? (hllc ? RECON_PPM_HLLC : (hyb ? RECON_PPM_HYB : (ref ? RECON_PPM_REF : RECON_PPM)))
+             : r == CTU_LINEAR_MC ? (hllc ? RECON_MC_HLLC : (hyb ? RECON_MC_HYB : (ref ? RECON_MC_REF : RECON_MC)))
              : r == CTU_WENO3 ? RECON_WENO3 : RECON_LIN;
     li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
     li.physics = ctx->cfg.physics == CTU_SRMHD ? PH_SR : PH_MHD;
@@ -397,6 +398,7 @@ namespace ctu {
 template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<double>(a, li, s);
+    if (recon_hllc(li.recon)) return launch_step_var<double, 1, 3>(a, li, s);
     if (recon_hybrid(li.recon)) return launch_step_var<double, 1, 2>(a, li, s);
     if (li.recon >= RECON_PPM_REF) return launch_step_var<double, 1, 1>(a, li, s);
     return li.recon >= RECON_LIN ? launch_step_var<double, 1, 0>(a, li, s) : launch_step_impl<double, 1>(a, li, s);
@@ -404,6 +406,7 @@ template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cud
 template <> int launch_step<float>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<float>(a, li, s);
+    if (recon_hllc(li.recon)) return launch_step_var<float, 0, 3>(a, li, s);
     if (recon_hybrid(li.recon)) return launch_step_var<float, 0, 2>(a, li, s);
     if (li.recon >= RECON_PPM_REF) return launch_step_var<float, 0, 1>(a, li, s);
     if (li.recon >= RECON_LIN) return launch_step_var<float, 0, 0>(a, li, s);
@@ -433,10 +436,16 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
     if (cfg->ndim < 1 || cfg->ndim > 3) return CTU_EINVAL;
     if (cfg->recon < CTU_LINEAR_MC || cfg->recon > CTU_WENO3) return CTU_EINVAL;
     if (cfg->predictor != CTU_CHAR_TRACE && cfg->predictor != CTU_MUSCL_HANCOCK) return CTU_EINVAL;
-    if (cfg->riemann != CTU_HLLD && cfg->riemann != CTU_HLL) return CTU_EINVAL;
-    // implemented combinations: MHD with characteristic tracing + HLLD;
-    // SRMHD with MUSCL-Hancock (MC-linear primitive slopes) + HLL
-    if (cfg->physics == CTU_MHD && (cfg->predictor != CTU_CHAR_TRACE || cfg->riemann != CTU_HLLD))
+    if (cfg->riemann != CTU_HLLD && cfg->riemann != CTU_HLL && cfg->riemann != CTU_HLLC) return CTU_EINVAL;
+    // implemented combinations: MHD with characteristic tracing + HLLD (or
+    // HLLC with PPM / MC-linear, trace modes ALL / UPWIND, FP64 or CTU_MIXED,
+    // no hybrid integration); SRMHD with MUSCL-Hancock (MC-linear primitive
+    // slopes) + HLL
+    if (cfg->physics == CTU_MHD && (cfg->predictor != CTU_CHAR_TRACE || cfg->riemann == CTU_HLL))
+        return CTU_EUNSUPPORTED;
+    if (cfg->physics == CTU_MHD && cfg->riemann == CTU_HLLC &&
+        ((cfg->recon != CTU_PPM && cfg->recon != CTU_LINEAR_MC) || cfg->trace_mode > CTU_TRACE_UPWIND ||
+         cfg->precision == CTU_MIXED_IFACE64 || cfg->shock_detect))
         return CTU_EUNSUPPORTED;
     if (cfg->physics == CTU_SRMHD &&
         (cfg->predictor != CTU_MUSCL_HANCOCK || cfg->riemann != CTU_HLL || cfg->recon != CTU_LINEAR_MC ||

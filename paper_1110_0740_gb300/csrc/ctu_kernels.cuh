@@ -488,7 +488,7 @@ __device__ __forceinline__ void riemann_any(const R (&L)[NV], const R (&Rr)[NV],
 
 // n+1/2 flux through a D-face from the left cell's + state and the right
 // cell's - state (both global order); flux returned in global order.
-template <int PHYS, class R, int D>
+template <int PHYS, class R, int D, bool HLLC = false>
 __device__ __forceinline__ void face_flux(const R (&Lg)[NV], const R (&Rg)[NV], R gam, R ch, R (&Fg)[NV],
                                           bool hll = false)
 {
@@ -500,6 +500,8 @@ __device__ __forceinline__ void face_flux(const R (&Lg)[NV], const R (&Rg)[NV], 
     }
     if (PHYS == PH_MHD && hll)
         riemann_hll(L, Rr, gam, ch, F);
+    else if (PHYS == PH_MHD && HLLC)
+        riemann_hllc(L, Rr, gam, ch, F);
     else
         riemann_any<PHYS, R>(L, Rr, gam, ch, F);
 #pragma unroll
@@ -838,7 +840,7 @@ static __global__ void __launch_bounds__(BLOCK) k_minmod(StepArgs a, GroupTable 
 //          cells, the lower face of a cell arriving from the previous lane.
 //   D = y, z: one thread per segment of SEG cells marching along D with the
 //          previous face flux and cell state in registers.
-template <int PHYS, class R, int D, bool HYB = false>
+template <int PHYS, class R, int D, bool HYB = false, bool HLLC = false>
 __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const R *Vs, R *L1)
 {
     const Where wh = locate(gt);
@@ -870,6 +872,8 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const
             }
             if (HYB && PHYS == PH_MHD && ((a.flags[c - 1] | a.flags[c]) & 1))
                 riemann_hll(L, Rr, gam, ch, F);
+            else if (HLLC && PHYS == PH_MHD)
+                riemann_hllc(L, Rr, gam, ch, F);
             else
                 riemann_any<PHYS, R>(L, Rr, gam, ch, F);
         } else {
@@ -918,6 +922,8 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const
             R F[NV];
             if (HYB && PHYS == PH_MHD && ((a.flags[c - st] | a.flags[c]) & 1))
                 riemann_hll(Vl, Vr, gam, ch, F);
+            else if (HLLC && PHYS == PH_MHD)
+                riemann_hllc(Vl, Vr, gam, ch, F);
             else
                 riemann_any<PHYS, R>(Vl, Vr, gam, ch, F);
             if (j > j0) {  // cell j - 1
@@ -989,7 +995,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
         R L[NV], Rr[NV], F[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) { L[q] = sP[me][q]; Rr[q] = sM[me + 1][q]; }
-        face_flux<PHYS, R, 0>(L, Rr, gam, ch, F, recon_hybrid(PPM) && ((a.flags[c] | a.flags[c + 1]) & 1));
+        face_flux<PHYS, R, 0, recon_hllc(PPM)>(L, Rr, gam, ch, F,
+                                               recon_hybrid(PPM) && ((a.flags[c] | a.flags[c + 1]) & 1));
 #pragma unroll
         for (int q = 0; q < NV; ++q) sF[me][q] = F[q];
         // faces on plane i+1; the tile's last face belongs to the next tile
@@ -1130,8 +1137,8 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, G
         auto faces = [&](int j, long long cj, const R (&Vm)[NV], const R *Ap, long long as, const double *Up,
                          long long us) {
             R F[NV];
-            face_flux<PHYS, R, D>(Pprev, Vm, gam, ch, F,
-                                  recon_hybrid(PPM) && ((a.flags[cj - st] | a.flags[cj]) & 1));
+            face_flux<PHYS, R, D, recon_hllc(PPM)>(Pprev, Vm, gam, ch, F,
+                                                   recon_hybrid(PPM) && ((a.flags[cj - st] | a.flags[cj]) & 1));
             // plane j; (a, b) = (x, o) are the two non-D dimensions in
             // increasing order; a segment's last face belongs to the next
             if (wb >= 0 && (j < j1 || j1 == nD)) {

@@ -106,14 +106,14 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         CTU_MARK("flux1");
         n += over_groups(
             li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 0, G.xw, G.seg); },
-            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 0, recon_hybrid(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 0, recon_hybrid(PPM), recon_hllc(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
         n += over_groups(
             li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 1, G.xw, G.seg); },
-            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 1, recon_hybrid(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 1, recon_hybrid(PPM), recon_hllc(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
         if (a.ndim > 2)
             n += over_groups(
                 li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 2, G.xw, G.seg); },
-                [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 2, recon_hybrid(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+                [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 2, recon_hybrid(PPM), recon_hllc(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
         CTU_MARK(nullptr);
     }
     // sweeps in the order z, y, x: the first writes A = L_D, the middle one
@@ -150,11 +150,15 @@ template <class R, int IF64> int launch_step_impl(const StepArgs &a, const Launc
 
 // MHD with the other reconstructions of Section 3.2 (G = 0: linear with the
 // MinMod, harmonic or Van Albada slope, or improved WENO3), with the
-// reference states of the tracing (G = 1: PPM or MC-linear), or with the
-// hybrid integration (G = 2: PPM or MC-linear).
+// reference states of the tracing (G = 1: PPM or MC-linear), with the
+// hybrid integration (G = 2: PPM or MC-linear), or with the HLLC solver
+// (G = 3: PPM or MC-linear).
 template <class R, int IF64, int G> int launch_step_var(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
-    if constexpr (G == 2)  // the hybrid integration of the shock-detection appendix
+    if constexpr (G == 3)  // the HLLC solver
+        return li.recon == RECON_PPM_HLLC ? launch_step_t<PH_MHD, R, RECON_PPM_HLLC, IF64>(a, li, s)
+                                          : launch_step_t<PH_MHD, R, RECON_MC_HLLC, IF64>(a, li, s);
+    else if constexpr (G == 2)  // the hybrid integration of the shock-detection appendix
         return li.recon == RECON_PPM_HYB ? launch_step_t<PH_MHD, R, RECON_PPM_HYB, IF64>(a, li, s)
                                          : launch_step_t<PH_MHD, R, RECON_MC_HYB, IF64>(a, li, s);
     else if constexpr (G == 0)

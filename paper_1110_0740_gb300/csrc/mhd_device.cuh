@@ -94,18 +94,21 @@ template <class R> __device__ __forceinline__ R lin_slope(R dm, R dp, int lim)
 // RECON_PPM among the first two, as before).
 // The hybrid kinds (RECON_PPM_HYB, RECON_MC_HYB) reconstruct with MinMod
 // where the shock flags ask for it (lim == 2 at run time).
+// RECON_PPM_HLLC and RECON_MC_HLLC take the HLLC solver on every face.
 enum {
     RECON_MC = 0, RECON_PPM = 1, RECON_LIN = 2, RECON_WENO3 = 3, RECON_PPM_REF = 4, RECON_MC_REF = 5,
-    RECON_PPM_HYB = 6, RECON_MC_HYB = 7
+    RECON_PPM_HYB = 6, RECON_MC_HYB = 7, RECON_PPM_HLLC = 8, RECON_MC_HLLC = 9
 };
 
 __host__ __device__ constexpr int recon_base(int r)
 {
-    return (r == RECON_PPM_REF || r == RECON_PPM_HYB) ? RECON_PPM
-                                                      : ((r == RECON_MC_REF || r == RECON_MC_HYB) ? RECON_MC : r);
+    return (r == RECON_PPM_REF || r == RECON_PPM_HYB || r == RECON_PPM_HLLC)
+               ? RECON_PPM
+               : ((r == RECON_MC_REF || r == RECON_MC_HYB || r == RECON_MC_HLLC) ? RECON_MC : r);
 }
 
 __host__ __device__ constexpr bool recon_hybrid(int r) { return r == RECON_PPM_HYB || r == RECON_MC_HYB; }
+__host__ __device__ constexpr bool recon_hllc(int r) { return r == RECON_PPM_HLLC || r == RECON_MC_HLLC; }
 
 // Interface values w_(i,+/-) of one characteristic field from w_(i-2..i+2):
 // PPM, Eq. (ppm1) + parabolic limiter Eq. (ppm_parabolic_lim); linear,
@@ -206,7 +209,7 @@ template <class R, int PPM>
 __device__ __forceinline__ void char_predict(const R (&vs)[5][NV], R gam, R ch, R dtdx, int upwind, int lim,
                                              R dx2, R (&Vp)[NV], R (&Vm)[NV])
 {
-    constexpr bool REF = PPM >= RECON_LIN && !recon_hybrid(PPM);
+    constexpr bool REF = PPM >= RECON_LIN && PPM <= RECON_MC_REF;
     const R rho = vs[2][0], u = vs[2][1], v1c = vs[2][2], v2c = vs[2][3], pc = vs[2][4];
     const R Bn = vs[2][5], B1c = vs[2][6], B2c = vs[2][7];
     const R a2 = gam * pc / rho;
@@ -529,6 +532,92 @@ __device__ __forceinline__ bool riemann_hll(const R (&L)[NV], const R (&Rt)[NV],
         const R iw = R(1) / (SR - SL);
 #pragma unroll
         for (int q = 0; q < 8; ++q) G[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) * iw;
+    }
+    F[0] = G[0]; F[1] = G[1]; F[2] = G[2]; F[3] = G[3]; F[4] = G[4];
+    F[5] = pm;
+    F[6] = G[6]; F[7] = G[7];
+    F[8] = ch * ch * Bm;
+    return bad;
+}
+
+// HLLC flux for MHD (Li 2005): the GLM face solve and outer speeds of
+// riemann_hlld; the HLL average state gives the contact speed
+// S_M = (rho u)_hll / rho_hll and the star states' transverse field and
+// velocity, B*_t = B_t,hll and v*_t = (rho v_t)_hll / rho_hll; with
+// p*_t = rho_L (S_L - u_L)(S_M - u_L) + p_t,L each star state is
+// rho* = rho (S - u)/(S - S_M), (rho u)* = rho* S_M,
+// (rho v_t)* = (rho v_t (S - u) - B_n (B*_t - B_t))/(S - S_M),
+// E* = (E (S - u) - p_t u + p*_t S_M + B_n (v.B - v*.B*))/(S - S_M), and
+// the flux is F + S (U* - U) on the face's side of the contact.
+template <class R>
+__device__ __forceinline__ bool riemann_hllc(const R (&L)[NV], const R (&Rt)[NV], R gam, R ch, R (&F)[NV])
+{
+    const bool bad = !(L[0] > R(0) && L[4] > R(0) && Rt[0] > R(0) && Rt[4] > R(0));
+    const R Bm = R(0.5) * (L[5] + Rt[5]) - R(0.5) * (Rt[8] - L[8]) / ch;
+    const R pm = R(0.5) * (L[8] + Rt[8]) - R(0.5) * ch * (Rt[5] - L[5]);
+    const R Bn = Bm;
+    const R igm = R(1) / (gam - R(1));
+    const R rL = L[0], uL = L[1], vL = L[2], wL = L[3], pL = L[4], yL = L[6], zL = L[7];
+    const R rR = Rt[0], uR = Rt[1], vR = Rt[2], wR = Rt[3], pR = Rt[4], yR = Rt[6], zR = Rt[7];
+    const R BsqL = Bn * Bn + yL * yL + zL * zL;
+    const R BsqR = Bn * Bn + yR * yR + zR * zR;
+    const R ptL = pL + R(0.5) * BsqL, ptR = pR + R(0.5) * BsqR;
+    const R EL = pL * igm + R(0.5) * rL * (uL * uL + vL * vL + wL * wL) + R(0.5) * BsqL;
+    const R ER = pR * igm + R(0.5) * rR * (uR * uR + vR * vR + wR * wR) + R(0.5) * BsqR;
+    const R vBL = uL * Bn + vL * yL + wL * zL;
+    const R vBR = uR * Bn + vR * yR + wR * zR;
+    R FL[8], FR[8], UL[8], UR[8];
+    FL[0] = rL * uL; FL[1] = rL * uL * uL + ptL - Bn * Bn; FL[2] = rL * uL * vL - Bn * yL;
+    FL[3] = rL * uL * wL - Bn * zL; FL[4] = (EL + ptL) * uL - Bn * vBL; FL[5] = R(0);
+    FL[6] = uL * yL - Bn * vL; FL[7] = uL * zL - Bn * wL;
+    FR[0] = rR * uR; FR[1] = rR * uR * uR + ptR - Bn * Bn; FR[2] = rR * uR * vR - Bn * yR;
+    FR[3] = rR * uR * wR - Bn * zR; FR[4] = (ER + ptR) * uR - Bn * vBR; FR[5] = R(0);
+    FR[6] = uR * yR - Bn * vR; FR[7] = uR * zR - Bn * wR;
+    UL[0] = rL; UL[1] = rL * uL; UL[2] = rL * vL; UL[3] = rL * wL; UL[4] = EL; UL[5] = Bn;
+    UL[6] = yL; UL[7] = zL;
+    UR[0] = rR; UR[1] = rR * uR; UR[2] = rR * vR; UR[3] = rR * wR; UR[4] = ER; UR[5] = Bn;
+    UR[6] = yR; UR[7] = zR;
+    const R cfL = fast_speed(rL, pL, Bn, yL, zL, gam);
+    const R cfR = fast_speed(rR, pR, Bn, yR, zR, gam);
+    const R cmax = fmax(cfL, cfR);
+    const R SL = fmin(uL, uR) - cmax;
+    const R SR = fmax(uL, uR) + cmax;
+    R G[8];
+    if (SL >= R(0)) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) G[q] = FL[q];
+    } else if (SR <= R(0)) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) G[q] = FR[q];
+    } else {
+        const R iw = R(1) / (SR - SL);
+        R Uh[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Uh[q] = (SR * UR[q] - SL * UL[q] - FR[q] + FL[q]) * iw;
+        const R irh = R(1) / Uh[0];
+        const R SM = Uh[1] * irh, vs = Uh[2] * irh, ws = Uh[3] * irh;
+        const R ys = Uh[6], zs = Uh[7];
+        const R pts = rL * (SL - uL) * (SM - uL) + ptL;
+        const R vBs = SM * Bn + vs * ys + ws * zs;
+        const bool right = SM < R(0);
+        const R rr = right ? rR : rL, uu = right ? uR : uL, vv = right ? vR : vL, ww = right ? wR : wL;
+        const R yy = right ? yR : yL, zz = right ? zR : zL, EE = right ? ER : EL, pt = right ? ptR : ptL;
+        const R vB = right ? vBR : vBL, S = right ? SR : SL;
+        const R sd = S - uu, iden = R(1) / (S - SM);
+        R Us[8];
+        Us[0] = rr * sd * iden;
+        Us[1] = Us[0] * SM;
+        Us[2] = (rr * vv * sd - Bn * (ys - yy)) * iden;
+        Us[3] = (rr * ww * sd - Bn * (zs - zz)) * iden;
+        Us[4] = (EE * sd - pt * uu + pts * SM + Bn * (vB - vBs)) * iden;
+        Us[5] = Bn;
+        Us[6] = ys;
+        Us[7] = zs;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const R Fa = right ? FR[q] : FL[q], Ua = right ? UR[q] : UL[q];
+            G[q] = Fa + S * (Us[q] - Ua);
+        }
     }
     F[0] = G[0]; F[1] = G[1]; F[2] = G[2]; F[3] = G[3]; F[4] = G[4];
     F[5] = pm;

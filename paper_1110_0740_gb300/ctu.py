@@ -19,7 +19,7 @@ CTU_EOS_IDEAL, CTU_EOS_TM = 0, 1
 CTU_LINEAR_MC, CTU_PPM = 0, 1
 CTU_LINEAR_MINMOD, CTU_LINEAR_HARMONIC, CTU_LINEAR_VANALBADA, CTU_WENO3 = 2, 3, 4, 5
 CTU_CHAR_TRACE, CTU_MUSCL_HANCOCK = 0, 1
-CTU_HLLD, CTU_HLL = 0, 1
+CTU_HLLD, CTU_HLL, CTU_HLLC = 0, 1, 2
 CTU_FP64, CTU_MIXED, CTU_MIXED_IFACE64 = 0, 1, 2
 CTU_TRACE_ALL, CTU_TRACE_UPWIND, CTU_TRACE_CENTER, CTU_TRACE_CW84 = 0, 1, 2, 3
 CTU_TAG_DENSITY, CTU_TAG_ENERGY, CTU_TAG_B2_OVER_RHO, CTU_TAG_E_OVER_RHO = 0, 1, 2, 3
