@@ -330,28 +330,56 @@ def run_ours(args):
         roof["precision_split"] = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
 
     # end-to-end through the public API with host buffers
+    # every step copies its whole input state from pinned host memory and
+    # reads its whole result back; with two device copies of each, the copy
+    # of step k + 1's input and the read-back of step k - 1's result run on
+    # their own streams (both copy directions) while step k computes, as a
+    # caller streaming states through the library would arrange it
     e2e = None
     if not args.skip_e2e:
         c = make(primary)
         Uh_pin = Uh.pin_memory()
-        Uout_pin = torch.empty_like(Uh_pin).pin_memory()
-        E = max(1, min(args.steps, 3))
-        for it in range(E + 1):
-            if it == 1:
-                barrier()
-                t0 = torch.cuda.Event(enable_timing=True)
-                t1 = torch.cuda.Event(enable_timing=True)
-                t0.record(stream)
-            U.copy_(Uh_pin, non_blocking=True)
-            step(c)
-            Uout_pin.copy_(Uo, non_blocking=True)
-        t1.record(stream)
+        Ubuf = [U, torch.empty_like(U)]
+        Obuf = [Uo, torch.empty_like(Uo)]
+        Oh = [torch.empty_like(Uh_pin).pin_memory() for _ in range(2)]
+        s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_cmp = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+
+        def pipeline(K):
+            for k in range(K):
+                b = k % 2
+                if k >= 2:
+                    s_in.wait_event(ev_cmp[b])  # step k - 2 has read input buffer b
+                with torch.cuda.stream(s_in):
+                    Ubuf[b].copy_(Uh_pin, non_blocking=True)
+                    ev_in[b].record(s_in)
+                s_cmp.wait_event(ev_in[b])
+                if k >= 2:
+                    s_cmp.wait_event(ev_out[b])  # result buffer b has been read back
+                c.step_next_dt(Ubuf[b], Obuf[b], stride, patches, dtch, dtn, stream=s_cmp)
+                ev_cmp[b].record(s_cmp)
+                s_out.wait_event(ev_cmp[b])
+                with torch.cuda.stream(s_out):
+                    Oh[b].copy_(Obuf[b], non_blocking=True)
+                    ev_out[b].record(s_out)
+
+        E = max(4, args.steps)  # the timed steps include the pipeline's fill and drain
+        pipeline(2)
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(s_in)
+        pipeline(E)
+        t1.record(s_out)
         barrier()
         ems = t0.elapsed_time(t1) / E
         c.close()
         e2e = {"value": world * cells / (ems * 1e-3), "unit": "cell-updates/s",
                "h2d_bytes_per_step": int(U.numel() * 8), "d2h_bytes_per_step": int(Uo.numel() * 8),
-               "ms_per_step": ems}
+               "ms_per_step": ems, "steps": E,
+               "overlap": "two device buffers; input copy, step and read-back on three streams"}
 
     fp64_path = None
     if other in results:
