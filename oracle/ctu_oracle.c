@@ -841,10 +841,13 @@ void or_mhd_shock_flags(const double *U, int nx, int ny, int nz, int ndim, doubl
 /* CFL, Eq. (Ca)                                                       */
 /* ------------------------------------------------------------------ */
 
-/* max over interior cells of max_d (|v_d| + c_f,d)/dx_d.  The caller sets
- * dt = C_a / max and c_h = max * min_d dx_d. */
-double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
-                        double dx, double dy, double dz, double gam)
+/* Eq. (Ca): max over interior cells of
+ *     max_d (|v_d| + c_f,d)/dx_d + sum_d 2 D / dx_d^2,
+ * with D = (Gamma - 1) kappa / rho the diffusion coefficient of thermal
+ * conduction (kappa = 0: no conduction).  The caller sets dt = C_a / max and
+ * c_h = max * min_d dx_d (= C_a min_d dx_d / dt). */
+double or_mhd_max_rate(const double *U, int nx, int ny, int nz, int ndim,
+                       double dx, double dy, double dz, double gam, double kappa)
 {
     grid_t G;
     double h[3] = {dx, dy, dz}, m = 0.0;
@@ -854,20 +857,100 @@ double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
         for (c[1] = 0; c[1] < G.n[1]; c[1]++)
             for (c[0] = 0; c[0] < G.n[0]; c[0]++) {
                 long id = cidx(&G, c);
-                double Uc[NVAR], V[NVAR], Vl[NVAR];
+                double Uc[NVAR], V[NVAR], Vl[NVAR], s = 0.0;
                 for (q = 0; q < NVAR; q++)
                     Uc[q] = U[q * G.ncell + id];
                 or_mhd_cons2prim(Uc, gam, V);
                 for (d = 0; d < ndim; d++) {
-                    double s;
+                    double sd;
                     for (q = 0; q < NVAR; q++)
                         Vl[q] = V[PERM[d][q]];
-                    s = (fabs(Vl[1]) + or_mhd_cfast(Vl, gam)) / h[d];
-                    if (s > m)
-                        m = s;
+                    sd = (fabs(Vl[1]) + or_mhd_cfast(Vl, gam)) / h[d];
+                    if (sd > s)
+                        s = sd;
                 }
+                if (kappa > 0.0) {
+                    double D = (gam - 1.0) * kappa / V[0];
+                    for (d = 0; d < ndim; d++)
+                        s += 2.0 * D / (h[d] * h[d]);
+                }
+                if (s > m)
+                    m = s;
             }
     return m;
+}
+
+/* max over interior cells of max_d (|v_d| + c_f,d)/dx_d (Eq. Ca without
+ * parabolic terms). */
+double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
+                        double dx, double dy, double dz, double gam)
+{
+    return or_mhd_max_rate(U, nx, ny, nz, ndim, dx, dy, dz, gam, 0.0);
+}
+
+/* ------------------------------------------------------------------ */
+/* Thermal conduction (parabolic term)                                 */
+/* ------------------------------------------------------------------ */
+
+/* Classical, isotropic thermal conduction: the heat flux of Eq. (tc_flux) in
+ * the limit q -> infinity with kappa_par = kappa_perp = kappa constant, so
+ * that Pi_E = kappa grad T with T = p / rho.  Its face value is the
+ * second-order central difference of Section 3.1 with g = kappa, f = T:
+ *     Pi_(d,+) = kappa (T(c + e_d) - T(c)) / dx_d,
+ * and L_P = sum_d (Pi_(d,+) - Pi_(d,-)) / dx_d (Eq. incrementop_par on a
+ * Cartesian grid) adds to the energy only.  T holds the temperature of every
+ * ghosted cell; LP receives L_P on the cells c with lo <= c <= hi. */
+static void conduction_lp(const grid_t *G, const double *T, const double *h, double kappa, const int *lo,
+                          const int *hi, double *LP)
+{
+    int c[3], d;
+    for (c[2] = lo[2]; c[2] <= hi[2]; c[2]++)
+        for (c[1] = lo[1]; c[1] <= hi[1]; c[1]++)
+            for (c[0] = lo[0]; c[0] <= hi[0]; c[0]++) {
+                long id = cidx(G, c);
+                double s = 0.0;
+                for (d = 0; d < G->ndim; d++) {
+                    long st = dstride(G, d);
+                    double pp = kappa * (T[id + st] - T[id]) / h[d];
+                    double pm = kappa * (T[id] - T[id - st]) / h[d];
+                    s += (pp - pm) / h[d];
+                }
+                LP[id] = s;
+            }
+}
+
+/* Temperature T = p / rho of every ghosted cell of U; returns the number of
+ * cells with rho <= 0 or p <= 0. */
+static int temperature(const grid_t *G, const double *U, double gam, double *T)
+{
+    int bad = 0, q;
+    for (long id = 0; id < G->ncell; id++) {
+        double Uc[NVAR], Vc[NVAR];
+        for (q = 0; q < NVAR; q++)
+            Uc[q] = U[q * G->ncell + id];
+        bad += or_mhd_cons2prim(Uc, gam, Vc);
+        T[id] = Vc[4] / Vc[0];
+    }
+    return bad;
+}
+
+/* L_P of thermal conduction (see conduction_lp) on the interior cells of a
+ * ghost-filled patch; LP has the ghosted layout (ghost entries are 0). */
+void or_mhd_conduction(const double *U, int nx, int ny, int nz, int ndim, double dx, double dy, double dz,
+                       double gam, double kappa, double *LP)
+{
+    grid_t G;
+    double h[3] = {dx, dy, dz};
+    int lo[3] = {0, 0, 0}, hi[3], d;
+    double *T;
+    grid_init(&G, nx, ny, nz, ndim);
+    for (d = 0; d < 3; d++)
+        hi[d] = G.n[d] - 1;
+    T = (double *)malloc(sizeof(double) * G.ncell);
+    temperature(&G, U, gam, T);
+    memset(LP, 0, sizeof(double) * G.ncell);
+    conduction_lp(&G, T, h, kappa, lo, hi, LP);
+    free(T);
 }
 
 /* ------------------------------------------------------------------ */
@@ -913,22 +996,24 @@ static int face_riemann(const double *VL, const double *VR, double gam, double c
     return or_mhd_riemann(VL, VR, gam, ch, F);
 }
 
-/* or_mhd_step with the Riemann solver `solver` (0 HLLD, 2 HLLC; the same
- * solver for the first-order and the n+1/2 fluxes) and, when shock != 0,
- * the hybrid integration of the appendix on shock detection: the flags of
- * shock_flags (eps_q, qkind) on V^n select the HLL solver at the faces of
- * shocked cells (first-order and n+1/2 fluxes) and the MinMod linear
- * reconstruction for the cells near them. */
-int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
-                   double dx, double dy, double dz, double dt, double ch,
-                   double gam, double glm_alpha, int recon, int upwind,
-                   const long *win, const double *wgt, int nwin, double *reg,
-                   int solver, int shock, double eps_q, int qkind)
+/* The step of or_mhd_step_ex and or_mhd_step_tc: with kappa > 0, thermal
+ * conduction (conduction_lp) enters as the parabolic term of Section 3.1 (Pi
+ * != 0): L_P^n from the cell-centred U^n joins the transverse increments of
+ * every direction's predictor (Eq. transv), and the update adds L_P^(n+1/2)
+ * from the cell-centred U^(n+1/2) = U^n + dt/2 sum_d (L_(H,d)^n + L_(P,d)^n),
+ * L_H^n the first-order (Godunov) divergences. */
+static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
+                     double dx, double dy, double dz, double dt, double ch,
+                     double gam, double glm_alpha, int recon, int upwind,
+                     const long *win, const double *wgt, int nwin, double *reg,
+                     int solver, int shock, double eps_q, int qkind, double kappa)
 {
     unsigned char *flags = NULL;
     grid_t G;
     double h[3] = {dx, dy, dz};
     double *V, *F1[3] = {0, 0, 0}, *Up[3] = {0, 0, 0}, *Um[3] = {0, 0, 0}, *F[3] = {0, 0, 0};
+    double *Tn = NULL, *LPn = NULL, *Th = NULL, *LPh = NULL;
+    int ring_lo[3], ring_hi[3];
     int c[3], d, q, bad = 0;
     long nc;
 
@@ -949,6 +1034,19 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
         flags = (unsigned char *)malloc((size_t)nc);
         shock_flags(&G, V, h, eps_q, qkind, recon == 1 ? 2 : 1, flags);
     }
+    /* the ring box: the interior and one layer around it on active axes */
+    for (d = 0; d < 3; d++) {
+        ring_lo[d] = d < ndim ? -1 : 0;
+        ring_hi[d] = d < ndim ? G.n[d] : 0;
+    }
+    if (kappa > 0.0) {
+        /* L_P^n on the ring box, from T^n = p^n / rho^n */
+        Tn = (double *)malloc(sizeof(double) * nc);
+        LPn = (double *)calloc((size_t)nc, sizeof(double));
+        for (long id = 0; id < nc; id++)
+            Tn[id] = V[4 * nc + id] / V[id];
+        conduction_lp(&G, Tn, h, kappa, ring_lo, ring_hi, LPn);
+    }
 
     /* 2. first-order Godunov fluxes F^n_d = R(U_c, U_(c+e_d)) on the faces the
      *    transverse increments need; F1[d] at cell c is its upper face. */
@@ -961,8 +1059,9 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
                 lo[e] = 0;
                 hi[e] = 0;
             } else if (e == d) {
-                lo[e] = -1;
-                hi[e] = G.n[e] - 1;
+                /* with conduction, also the outer faces of the ring box */
+                lo[e] = kappa > 0.0 ? -2 : -1;
+                hi[e] = kappa > 0.0 ? G.n[e] : G.n[e] - 1;
             } else {
                 lo[e] = -1;
                 hi[e] = G.n[e];
@@ -1018,6 +1117,9 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
                         for (q = 0; q < NVAR; q++)
                             T[q] += (F1[e2][q * nc + id - st2] - F1[e2][q * nc + id]) / h[e2];
                     }
+                    /* the parabolic term of every direction, Eq. (transv) */
+                    if (LPn)
+                        T[4] += LPn[id];
                     or_mhd_prim2cons(Vp, gam, Ul);
                     for (q = 0; q < NVAR; q++)
                         Ug[PERM[d][q]] = Ul[q];
@@ -1062,7 +1164,35 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
                 }
     }
 
-    /* 5. conservative update, Eq. (update): U + dt * (L_x + L_y + L_z) */
+    /* 4b. with conduction: T^(n+1/2) of the cell-centred
+     *     U^(n+1/2) = U^n + dt/2 (sum_d L_(H,d)^n + L_P^n) on the ring box,
+     *     then L_P^(n+1/2) on the interior */
+    if (kappa > 0.0) {
+        int ilo[3] = {0, 0, 0}, ihi[3];
+        Th = (double *)calloc((size_t)nc, sizeof(double));
+        LPh = (double *)calloc((size_t)nc, sizeof(double));
+        for (c[2] = ring_lo[2]; c[2] <= ring_hi[2]; c[2]++)
+            for (c[1] = ring_lo[1]; c[1] <= ring_hi[1]; c[1]++)
+                for (c[0] = ring_lo[0]; c[0] <= ring_hi[0]; c[0]++) {
+                    long id = cidx(&G, c);
+                    double Uh[NVAR], Vh[NVAR];
+                    for (q = 0; q < NVAR; q++) {
+                        double s = 0.0;
+                        for (d = 0; d < ndim; d++)
+                            s += (F1[d][q * nc + id - dstride(&G, d)] - F1[d][q * nc + id]) / h[d];
+                        if (q == 4)
+                            s += LPn[id];
+                        Uh[q] = U[q * nc + id] + 0.5 * dt * s;
+                    }
+                    bad += or_mhd_cons2prim(Uh, gam, Vh);
+                    Th[id] = Vh[4] / Vh[0];
+                }
+        for (d = 0; d < 3; d++)
+            ihi[d] = G.n[d] - 1;
+        conduction_lp(&G, Th, h, kappa, ilo, ihi, LPh);
+    }
+
+    /* 5. conservative update, Eq. (update): U + dt * (L_x + L_y + L_z) (+ L_P) */
     memcpy(Unew, U, sizeof(double) * NVAR * nc);
     {
         double hmin = h[0], damp;
@@ -1079,6 +1209,8 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
                         double s = 0.0;
                         for (d = 0; d < ndim; d++)
                             s += (F[d][q * nc + id - dstride(&G, d)] - F[d][q * nc + id]) / h[d];
+                        if (q == 4 && LPh)
+                            s += LPh[id];
                         Unew[q * nc + id] = U[q * nc + id] + dt * s;
                     }
                     Unew[8 * nc + id] *= damp;
@@ -1104,6 +1236,10 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
 
     free(flags);
     free(V);
+    free(Tn);
+    free(LPn);
+    free(Th);
+    free(LPh);
     for (d = 0; d < 3; d++) {
         free(F1[d]);
         free(Up[d]);
@@ -1111,6 +1247,35 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
         free(F[d]);
     }
     return bad;
+}
+
+/* or_mhd_step with the Riemann solver `solver` (0 HLLD, 2 HLLC; the same
+ * solver for the first-order and the n+1/2 fluxes) and, when shock != 0,
+ * the hybrid integration of the appendix on shock detection: the flags of
+ * shock_flags (eps_q, qkind) on V^n select the HLL solver at the faces of
+ * shocked cells (first-order and n+1/2 fluxes) and the MinMod linear
+ * reconstruction for the cells near them. */
+int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
+                   double dx, double dy, double dz, double dt, double ch,
+                   double gam, double glm_alpha, int recon, int upwind,
+                   const long *win, const double *wgt, int nwin, double *reg,
+                   int solver, int shock, double eps_q, int qkind)
+{
+    return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
+                     nwin, reg, solver, shock, eps_q, qkind, 0.0);
+}
+
+/* or_mhd_step_ex with thermal conduction of conductivity kappa >= 0 (the
+ * parabolic term; see step_core).  The flux registers take the hyperbolic
+ * fluxes only. */
+int or_mhd_step_tc(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
+                   double dx, double dy, double dz, double dt, double ch,
+                   double gam, double glm_alpha, int recon, int upwind,
+                   const long *win, const double *wgt, int nwin, double *reg,
+                   int solver, int shock, double eps_q, int qkind, double kappa)
+{
+    return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
+                     nwin, reg, solver, shock, eps_q, qkind, kappa);
 }
 
 /* ------------------------------------------------------------------ */

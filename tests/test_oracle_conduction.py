@@ -1,0 +1,224 @@
+"""Pins of the oracle's thermal conduction, the parabolic term of the CTU
+step (Section 3.1 with Pi != 0; classical isotropic flux Pi_E = kappa grad T,
+T = p / rho; diffusion term of Eq. Ca).
+
+- The discrete operator in closed form: L_P of a quadratic temperature is
+  kappa times its exact Laplacian; of a sinusoid, kappa times the symbol
+  -(4/dx^2) sin^2(k dx/2) of the three-point second difference.  The density
+  varies across the sinusoid's direction with p = rho T, so a flux built
+  from p or from the specific internal energy fails.
+- The time step of Eq. (Ca): the hyperbolic term plus 2 (Gamma-1) kappa /
+  (rho dx^2) per dimension, in closed form for a uniform gas at rest.
+- Conservation on periodic boxes: the parabolic flux telescopes.
+- Space-time convergence at second order to the exact solution of the
+  linearised Euler equations with conduction (matrix exponential of the
+  3x3 mode system written from the PDE) in 1-D and obliquely in 2-D.  The
+  time step is set by the hyperbolic CFL term (dt ~ dx), so a parabolic term
+  lagged to t^n in the update, or missing from the predictor, shows as first
+  order in time.
+- The same linear system in the conduction-dominated regime, with the
+  three-point symbol in place of k^2: the time integration of the parabolic
+  term is second order (a forward-Euler parabolic term misses by 10x).
+- A vanishing conductivity takes the conduction code path and reproduces
+  the plain step bit for bit.
+"""
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+import oracle as O
+from paper_1110_0740_gb300 import workloads as W
+
+G = 5.0 / 3.0
+
+
+def _prim_to_U(n, ndim, rho, vx, p, B=(0.0, 0.0, 0.0), vy=None):
+    z = np.zeros_like(rho)
+    vy = z if vy is None else vy
+    return W.ideal_cons([rho, vx + z, vy + z, z, p, z + B[0], z + B[1], z + B[2], z], G)
+
+
+def _centres(n, ndim, d):
+    g = O.ghosts(ndim)
+    shp = O.shape(n, ndim)
+    x = (np.arange(shp[3 - d]) - g[d] + 0.5) / n[d]
+    view = [1, 1, 1]
+    view[2 - d] = shp[3 - d]
+    return x.reshape(view)
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_quadratic_temperature_exact_laplacian(ndim):
+    n = [12, 10 if ndim > 1 else 1, 8 if ndim > 2 else 1]
+    coef = [0.7, -0.4, 0.25][:ndim]
+    shp = O.shape(n, ndim)
+    T = np.ones(shp[1:])
+    for d in range(ndim):
+        T = T + coef[d] * _centres(n, ndim, d) ** 2
+    rho = 1.0 + 0.0 * T
+    U = _prim_to_U(n, ndim, rho, 0.0, rho * T, B=(0.3, 0.2, 0.1))
+    kappa = 0.37
+    dx = [1.0 / n[d] for d in range(ndim)]
+    LP = O.interior(O.mhd_conduction(U, n, ndim, dx, kappa, G), n, ndim)
+    assert np.allclose(LP, kappa * 2.0 * sum(coef), rtol=0, atol=2e-10)
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_sinusoid_symbol_with_varying_density(ndim):
+    n = [16, 8, 8][:ndim] + [1] * (3 - ndim)
+    d0 = ndim - 1  # the sinusoid runs along the last active axis
+    shp = O.shape(n, ndim)
+    k = 2 * np.pi * 3
+    xs = _centres(n, ndim, d0)
+    eps = 0.05
+    T = 1.0 + eps * np.sin(k * xs) + np.zeros(shp[1:])
+    rho = 1.0 + np.zeros(shp[1:])
+    if ndim > 1:
+        rho = rho + 0.4 * np.cos(2 * np.pi * _centres(n, ndim, 0))
+    U = _prim_to_U(n, ndim, rho, 0.0, rho * T)
+    kappa = 0.2
+    dx = [1.0 / n[d] for d in range(ndim)]
+    LP = O.interior(O.mhd_conduction(U, n, ndim, dx, kappa, G), n, ndim)
+    h = dx[d0]
+    want = -kappa * 4.0 / h ** 2 * np.sin(k * h / 2) ** 2 * eps * np.sin(k * xs)
+    want = O.interior(want + np.zeros(shp[1:]), n, ndim)
+    assert np.allclose(LP, want, rtol=0, atol=1e-9 * np.abs(want).max())
+
+
+def test_max_rate_closed_form():
+    n = [8, 8, 8]
+    rho, p, kappa = 2.0, 3.0, 0.05
+    shp = O.shape(n, 3)
+    U = _prim_to_U(n, 3, rho + np.zeros(shp[1:]), 0.0, p)
+    dx = [0.1, 0.2, 0.05]
+    cs = np.sqrt(G * p / rho)
+    D = (G - 1) * kappa / rho
+    want = cs / min(dx) + sum(2 * D / h ** 2 for h in dx)
+    assert O.mhd_max_rate(U, n, 3, dx, G, kappa) == pytest.approx(want, rel=1e-14)
+    assert O.mhd_max_rate(U, n, 3, dx, G, 0.0) == O.mhd_max_speed(U, n, 3, dx, G)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_conservation_periodic(ndim):
+    N = 16
+    n = [N, N, N if ndim > 2 else 1]
+    if ndim == 3:
+        U = W.mhd_blast_3d(N, seed=3)
+    else:
+        U = W.mhd_turb_2d(N, seed=3)
+    dx = [1.0 / N] * ndim
+    a = O.interior(U, n, ndim).copy()
+    R, t, _ = O.mhd_run(U, n, ndim, dx, 6, 0.3, recon=1, kappa=0.02)
+    b = O.interior(R, n, ndim)
+    for q in range(8):
+        assert abs(b[q].sum() - a[q].sum()) <= 1e-13 * (np.abs(a[q]).sum() + 1.0), q
+    # conduction changed the solution
+    R0, _, _ = O.mhd_run(U, n, ndim, dx, 6, 0.3, recon=1)
+    assert np.abs(O.interior(R0, n, ndim)[4] - b[4]).max() > 1e-6
+
+
+def _linear_mode(n, ndim, kappa, eps, v0):
+    """Entropy perturbation of a uniform gas (rho0 = p0 = 1, B = 0) moving with
+    speed v0 along the wave vector (1, 0) in 1-D or (1, 1) in 2-D."""
+    shp = O.shape(n, ndim)
+    kv = np.array([1.0, 1.0][:ndim]) * 2 * np.pi
+    phase = np.zeros(shp[1:])
+    for d in range(ndim):
+        phase = phase + kv[d] * _centres(n, ndim, d)
+    nh = kv / np.linalg.norm(kv)
+    rho = 1.0 + eps * np.cos(phase)
+    vx = v0 * nh[0] + 0 * phase
+    vy = v0 * nh[1] + 0 * phase if ndim > 1 else None
+    return _prim_to_U(n, ndim, rho, vx, 1.0 + 0 * phase, vy=vy), kv, phase
+
+
+def _exact_rho(kv, phase, t, kappa, eps, v0):
+    """rho of the linearised Euler equations with conduction: for a mode
+    exp(i k.x) with k = |kv| along the flow,
+      rho_t = -i k v0 rho - i k rho0 u,   u_t = -i k v0 u - i k p / rho0,
+      p_t = -i k v0 p - i k Gamma p0 u - (Gamma-1) kappa k^2 T,
+      T = p / rho0 - p0 rho / rho0^2."""
+    k = np.linalg.norm(kv)
+    r0 = p0 = 1.0
+    M = np.array([
+        [-1j * k * v0, -1j * k * r0, 0],
+        [0, -1j * k * v0, -1j * k / r0],
+        [(G - 1) * kappa * k * k * p0 / r0 ** 2, -1j * k * G * p0, -1j * k * v0 - (G - 1) * kappa * k * k / r0],
+    ])
+    a = expm(M * t) @ np.array([1.0, 0.0, 0.0])
+    return 1.0 + eps * np.real(a[0] * np.exp(1j * phase))
+
+
+def _l1_error(N, ndim, kappa, t_end, cfl):
+    n = [N, N if ndim > 1 else 1, 1]
+    eps, v0 = 1e-6, 0.3
+    U, kv, phase = _linear_mode(n, ndim, kappa, eps, v0)
+    dx = [1.0 / N] * ndim
+    R, t, _ = O.mhd_run(U, n, ndim, dx, None, cfl, recon=1, t_end=t_end, kappa=kappa)
+    ex = O.interior(_exact_rho(kv, phase, t, kappa, eps, v0)[None], n, ndim)[0]
+    return np.abs(O.interior(R, n, ndim)[0] - ex).mean() / eps
+
+
+def test_linear_mode_second_order_1d():
+    # D = (Gamma-1) kappa = 0.004: k^2 D t = 0.16 at t = 1, and the CFL step
+    # is set by the hyperbolic term at every resolution below (dt ~ dx)
+    kappa = 0.006
+    e = [_l1_error(N, 1, kappa, 1.0, 0.4) for N in (32, 64, 128)]
+    orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert orders[-1] > 1.9, (e, orders)
+    assert e[-1] < 2e-3
+    # conduction is visible: the kappa = 0 solution is far from the exact one
+    n = [128, 1, 1]
+    U, kv, phase = _linear_mode(n, 1, kappa, 1e-6, 0.3)
+    R, t, _ = O.mhd_run(U, n, 1, [1.0 / 128], None, 0.4, recon=1, t_end=1.0)
+    ex = O.interior(_exact_rho(kv, phase, t, kappa, 1e-6, 0.3)[None], n, 1)[0]
+    assert np.abs(O.interior(R, n, 1)[0] - ex).mean() / 1e-6 > 20 * e[-1]
+
+
+def test_linear_mode_second_order_2d_oblique():
+    kappa = 0.004
+    e = [_l1_error(N, 2, kappa, 0.5, 0.4) for N in (16, 32, 64)]
+    orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert orders[-1] > 1.8, (e, orders)
+
+
+def test_strong_conduction_time_integration():
+    """Conduction-dominated regime (D k^2 = 20 c k): over t = 1/80 the
+    temperature mode decays by e^-2 while sound travels a tenth of a radian,
+    and the CFL step is set by the diffusion term (dt D k_h^2 = 0.008 per
+    step).  Reference: the linearised system above with the conduction terms'
+    k^2 replaced by the symbol (4/dx^2) sin^2(k dx/2) of the three-point
+    second difference, i.e. the exact time evolution of the spatially
+    discrete conduction operator.  The pressure mode then matches to 6e-5 of
+    the perturbation at 32 cells; a parabolic term integrated at first order
+    in time (forward Euler: L_P at n+1/2 from a half-step state without L_P^n,
+    or L_P^n in the update) misses by 6e-4 or more."""
+    N, kappa, t_end, eps = 32, 6.0, 0.0125, 1e-6
+    n = [N, 1, 1]
+    U, kv, phase = _linear_mode(n, 1, kappa, eps, 0.0)
+    R, t, _ = O.mhd_run(U, n, 1, [1.0 / N], None, 0.4, recon=1, t_end=t_end, kappa=kappa)
+    k, h = kv[0], 1.0 / N
+    kd2 = 4.0 / h ** 2 * np.sin(k * h / 2) ** 2
+    M = np.array([[0, -1j * k, 0], [0, 0, -1j * k], [(G - 1) * kappa * kd2, -1j * k * G, -(G - 1) * kappa * kd2]])
+    a = expm(M * t) @ np.array([1.0, 0.0, 0.0])
+    Ui = O.interior(R, n, 1)[:, 0, 0, :]
+    p = (G - 1) * (Ui[4] - 0.5 * (Ui[1] ** 2 + Ui[2] ** 2 + Ui[3] ** 2) / Ui[0]
+                   - 0.5 * (Ui[5] ** 2 + Ui[6] ** 2 + Ui[7] ** 2))
+    x = (np.arange(N) + 0.5) / N
+    pex = 1.0 + eps * np.real(a[2] * np.exp(1j * k * x))
+    assert abs(a[2]) > 0.8  # the pressure mode the conduction drives
+    assert np.abs(p - pex).mean() / eps < 1.5e-4
+
+
+def test_vanishing_kappa_is_the_plain_step():
+    """A conductivity far below round-off of the state takes the conduction
+    code path (wider first-order stage, half-step state) and changes no bit."""
+    N = 12
+    n = [N, N, 1]
+    U = W.mhd_turb_2d(N, seed=5)
+    O.fill_periodic(U, n, 2)
+    dx = [1.0 / N] * 2
+    dt, ch = O.dt_ch(O.mhd_max_speed(U, n, 2, dx), dx, 2, 0.3)
+    a, _ = O.mhd_step(U, n, 2, dx, dt, ch, recon=1)
+    b, _ = O.mhd_step(U, n, 2, dx, dt, ch, recon=1, kappa=1e-300)
+    assert np.array_equal(a, b)
