@@ -218,8 +218,10 @@ def run_ours(args):
     def make(prec):
         c = ctu.Ctx(ctu.make_config(ndim=3, recon=RECONS[args.recon], precision=prec, cfl=0.3,
                                     shock=(args.shock, 0) if args.shock else None,
-                                    riemann=ctu.CTU_HLLC if args.riemann == "hllc" else ctu.CTU_HLLD))
-        c.flux_registers(reg, windows)
+                                    riemann=ctu.CTU_HLLC if args.riemann == "hllc" else ctu.CTU_HLLD,
+                                    kappa=args.kappa))
+        if not args.kappa:  # the registers carry hyperbolic fluxes only
+            c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
         if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
             c.autotune(U, Uo, stride, patches, dtch)
@@ -326,7 +328,7 @@ def run_ours(args):
     roof["hbm_step"] = {"algorithmic_bytes": nbytes, "achieved_gbs": hbm_achieved,
                         "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
                         "peak_source": f"{src} hbm_gbs"}
-    if mixed and args.recon == "ppm" and not args.shock and args.riemann == "hlld":
+    if mixed and args.recon == "ppm" and not args.shock and args.riemann == "hlld" and not args.kappa:
         roof["precision_split"] = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
 
     # end-to-end through the public API with host buffers
@@ -403,7 +405,9 @@ def run_ours(args):
                 "config": {"workload": (WORKLOAD if args.recon == "ppm" else
                                         WORKLOAD.replace("PPM", f"{args.recon} reconstruction"))
                            + (f"; hybrid integration (shock flags, eps_q {args.shock})" if args.shock else "")
-                           + ("; HLLC in place of HLLD" if args.riemann == "hllc" else ""),
+                           + ("; HLLC in place of HLLD" if args.riemann == "hllc" else "")
+                           + (f"; thermal conduction, kappa {args.kappa} (no flux registers)"
+                              if args.kappa else ""),
                            "recon": args.recon, "shock_eps": args.shock or None,
                            "cells_per_gpu": cells, "patches_per_gpu": 1,
                            "precision": args.precision, "l2_flush": "inputs (1.3 GB) > L2",
@@ -884,7 +888,7 @@ def precision_split_roofline(n, cells_per_s, hbm_gbs):
 
 
 STEP_SOURCES = ("df.cuh", "mhd_device.cuh", "srmhd_device.cuh", "ctu_kernels.cuh", "ctu_launch.h",
-                "ctu_launch.cuh", "ctu_f32.cu", "_build.py")
+                "ctu_launch.cuh", "tc_ops.cuh", "ctu_f32.cu", "_build.py")
 
 
 def kernel_source_hash():
@@ -927,6 +931,9 @@ def main():
                     help="amr: advance the levels without prolongation, restriction and reflux")
     ap.add_argument("--riemann", default="hlld", choices=["hlld", "hllc"],
                     help="blast: the Riemann solver (the workload uses HLLD)")
+    ap.add_argument("--kappa", type=float, default=0.0,
+                    help="blast: thermal conduction with this conductivity (0 = off); flux registers "
+                         "are then not bound")
     ap.add_argument("--shock", type=float, default=0.0,
                     help="blast: the hybrid integration with this shock threshold (thermal pressure; 0 = off)")
     ap.add_argument("--recon", default="ppm", choices=sorted(RECONS),

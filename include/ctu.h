@@ -156,6 +156,25 @@ typedef struct {
     int shock_detect;
     int shock_q;
     double shock_eps;
+    /* Thermal conduction, the parabolic term of Section 3.1 (Pi != 0):
+     * kappa >= 0 the isotropic conductivity of the classical heat flux
+     * (Eq. tc_flux with q -> infinity and kappa_par = kappa_perp = kappa),
+     * Pi_E = kappa grad T with T = p / rho; 0 = off.  Face fluxes are the
+     * central differences Pi_(d,+) = kappa (T(c + e_d) - T(c)) / dx_d, and
+     * L_P = sum_d (Pi_(d,+) - Pi_(d,-)) / dx_d (energy only) enters
+     *   - every direction's predictor at t^n (Eq. transv), from U^n, and
+     *   - the update (Eq. update) at n+1/2, from the cell-centred
+     *     U^(n+1/2) = U^n + dt/2 (sum_d L_(H,d)^n + L_P^n), L_(H,d)^n the
+     *     first-order Godunov divergences.
+     * The CFL rate of ctu_dt and ctu_step_next_dt gains
+     * sum_d 2 D / dx_d^2, D = (Gamma-1) kappa / rho (Eq. Ca).  Ideal MHD with
+     * CTU_PPM or CTU_LINEAR_MC, CTU_HLLD, trace_mode CTU_TRACE_ALL or
+     * CTU_TRACE_UPWIND, no hybrid integration, CTU_FP64 or CTU_MIXED (else
+     * CTU_EUNSUPPORTED); T^(n+1/2) and the update's parabolic term are float64
+     * in both precisions.  Flux registers carry hyperbolic fluxes only, so a
+     * step with kappa > 0 and a bound register array returns
+     * CTU_EUNSUPPORTED; not in ctu_step_noalloc. */
+    double kappa;
 } ctu_config;
 
 typedef struct {
@@ -192,8 +211,9 @@ typedef struct ctu_ctx ctu_ctx;
 ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out);
 
 /* CFL time step, Eq. (Ca): M = max over the interior cells of all patches of
- * max_d (|v_d| + c_f,d) / dx_d; then dt = cfl / M and c_h = M * min dx (the
- * GLM speed, equal to cfl * min dx / dt).  Writes {dt, c_h} to the device
+ * max_d (|v_d| + c_f,d) / dx_d (+ sum_d 2 (Gamma-1) kappa / (rho dx_d^2) with
+ * thermal conduction); then dt = cfl / M and c_h = M * min dx (the GLM
+ * speed, equal to cfl * min dx / dt).  Writes {dt, c_h} to the device
  * array d_dt_ch[2]; if h_dt_ch is non-null it also copies them there and
  * synchronises the stream.  U: device pool; patches: host array. */
 ctu_status ctu_dt(ctu_ctx *ctx, const double *U, int64_t stride,

@@ -315,12 +315,29 @@ static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStr
     return upload_windows(ctx, s);
 }
 
-static ctu_status ensure_scratch(ctu_ctx *ctx)
+// Scratch layout: SCRATCH_ARRAYS planes of the working precision, then (each
+// 256-byte aligned) the shock flags of the hybrid integration (one byte per
+// scratch cell) and, with thermal conduction, L_P^n (one word of the working
+// precision) and T^(n+1/2) (one double) per scratch cell.
+struct ScratchOffsets {
+    size_t flags, lp, th, total;
+};
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+static ScratchOffsets scratch_offsets(const ctu_ctx *ctx)
 {
     const size_t elt = ctx->cfg.precision == CTU_FP64 ? sizeof(double) : sizeof(float);
-    // + the shock flags of the hybrid integration, one byte per scratch cell
-    const size_t need = (size_t)SCRATCH_ARRAYS * (size_t)ctx->sstride * elt +
-                        (ctx->cfg.shock_detect ? (size_t)ctx->sstride + 256 : 0);
+    const size_t S = (size_t)ctx->sstride;
+    ScratchOffsets o;
+    o.flags = align256((size_t)SCRATCH_ARRAYS * S * elt);
+    o.lp = align256(o.flags + (ctx->cfg.shock_detect ? S : 0));
+    o.th = align256(o.lp + (ctx->cfg.kappa > 0.0 ? S * elt : 0));
+    o.total = o.th + (ctx->cfg.kappa > 0.0 ? S * sizeof(double) : 0);
+    return o;
+}
+
+static ctu_status ensure_scratch(ctu_ctx *ctx)
+{
+    const size_t need = scratch_offsets(ctx).total;
     if (need <= ctx->scratch_bytes) return CTU_OK;
     if (ctx->scratch) {
         CTU_CUDA(cudaDeviceSynchronize());
@@ -353,10 +370,18 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.shock_eps = ctx->cfg.shock_eps;
     a.shock_q = ctx->cfg.shock_q;
     a.flags = nullptr;
-    if (ctx->cfg.shock_detect && ctx->scratch) {
-        const size_t elt = ctx->cfg.precision == CTU_FP64 ? sizeof(double) : sizeof(float);
-        const size_t off = ((size_t)SCRATCH_ARRAYS * (size_t)ctx->sstride * elt + 255) / 256 * 256;
-        a.flags = (unsigned char *)ctx->scratch + off;
+    a.kappa = ctx->cfg.kappa;
+    a.kappaf = (float)ctx->cfg.kappa;
+    a.gm1lo = tm ? 0.0f : (float)((ctx->cfg.gamma - 1.0) - (double)a.gm1f);
+    a.lp = nullptr;
+    a.th = nullptr;
+    if (ctx->scratch) {
+        const ScratchOffsets o = scratch_offsets(ctx);
+        if (ctx->cfg.shock_detect) a.flags = (unsigned char *)ctx->scratch + o.flags;
+        if (ctx->cfg.kappa > 0.0) {
+            a.lp = (const unsigned char *)ctx->scratch + o.lp;
+            a.th = (double *)((unsigned char *)ctx->scratch + o.th);
+        }
     }
     a.U = Uin;
     a.Uout = Uout;
@@ -383,8 +408,12 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
     const bool ref = ctx->cfg.trace_mode >= CTU_TRACE_CENTER;
     const bool hyb = ctx->cfg.shock_detect != 0;
     const bool hllc = ctx->cfg.physics == CTU_MHD && ctx->cfg.riemann == CTU_HLLC;
-    li.recon = r == CTU_PPM ? (hllc ? RECON_PPM_HLLC : (hyb ? RECON_PPM_HYB : (ref ? RECON_PPM_REF : RECON_PPM)))
-             : r == CTU_LINEAR_MC ? (hllc ? RECON_MC_HLLC : (hyb ? RECON_MC_HYB : (ref ? RECON_MC_REF : RECON_MC)))
+    const bool tc = ctx->cfg.kappa > 0.0;
+    li.recon = r == CTU_PPM
+                   ? (tc ? RECON_PPM_TC
+                         : (hllc ? RECON_PPM_HLLC : (hyb ? RECON_PPM_HYB : (ref ? RECON_PPM_REF : RECON_PPM))))
+             : r == CTU_LINEAR_MC
+                   ? (tc ? RECON_MC_TC : (hllc ? RECON_MC_HLLC : (hyb ? RECON_MC_HYB : (ref ? RECON_MC_REF : RECON_MC))))
              : r == CTU_WENO3 ? RECON_WENO3 : RECON_LIN;
     li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
     li.physics = ctx->cfg.physics == CTU_SRMHD ? PH_SR : PH_MHD;
@@ -398,6 +427,7 @@ namespace ctu {
 template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<double>(a, li, s);
+    if (recon_tc(li.recon)) return launch_step_var<double, 1, 4>(a, li, s);
     if (recon_hllc(li.recon)) return launch_step_var<double, 1, 3>(a, li, s);
     if (recon_hybrid(li.recon)) return launch_step_var<double, 1, 2>(a, li, s);
     if (li.recon >= RECON_PPM_REF) return launch_step_var<double, 1, 1>(a, li, s);
@@ -406,6 +436,7 @@ template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cud
 template <> int launch_step<float>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<float>(a, li, s);
+    if (recon_tc(li.recon)) return launch_step_var<float, 0, 4>(a, li, s);
     if (recon_hllc(li.recon)) return launch_step_var<float, 0, 3>(a, li, s);
     if (recon_hybrid(li.recon)) return launch_step_var<float, 0, 2>(a, li, s);
     if (li.recon >= RECON_PPM_REF) return launch_step_var<float, 0, 1>(a, li, s);
@@ -473,6 +504,14 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
             cfg->trace_mode > CTU_TRACE_UPWIND || cfg->precision == CTU_MIXED_IFACE64)
             return CTU_EUNSUPPORTED;
     }
+    if (!(cfg->kappa >= 0.0 && cfg->kappa < INFINITY)) return CTU_EINVAL;
+    // thermal conduction: ideal MHD, PPM or MC-linear, HLLD, tracing without
+    // or with the w_(+/-) reference, no hybrid integration, FP64 or CTU_MIXED
+    if (cfg->kappa > 0.0 &&
+        (cfg->physics != CTU_MHD || (cfg->recon != CTU_PPM && cfg->recon != CTU_LINEAR_MC) ||
+         cfg->riemann != CTU_HLLD || cfg->trace_mode > CTU_TRACE_UPWIND || cfg->shock_detect ||
+         cfg->precision == CTU_MIXED_IFACE64))
+        return CTU_EUNSUPPORTED;
     ctu_ctx *ctx = new (std::nothrow) ctu_ctx();
     if (!ctx) return CTU_ENOMEM;
     ctx->cfg = *cfg;
@@ -598,6 +637,9 @@ static ctu_status step_common(ctu_ctx *ctx, const double *U_in, double *U_out, i
                               void *stream)
 {
     if (!ctx || !U_in || !U_out || !d_dt_ch || U_in == U_out) return CTU_EINVAL;
+    // flux registers carry hyperbolic fluxes only
+    const bool tc = ctx->cfg.kappa > 0.0;
+    if (tc && ctx->reg && !ctx->hwin.empty()) return CTU_EUNSUPPORTED;
     ctu_status st = validate_patches(ctx, stride, patches, npatch);
     if (st != CTU_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -611,7 +653,9 @@ static ctu_status step_common(ctu_ctx *ctx, const double *U_in, double *U_out, i
     const bool floors = floors_on(ctx);
     if (d_next) {
         CTU_CUDA(cudaMemsetAsync(ctx->dmax, 0, sizeof(unsigned long long), s));
-        // with floors, the CFL speed is taken after them, from U_out
+        // with floors, the CFL rate is taken after them, from U_out (with
+        // conduction the step's last kernel, the conduction update, reduces
+        // it in place of the last sweep)
         if (!floors) a.nextmax = ctx->dmax;
     }
     if (ctx->cfg.precision != CTU_FP64)

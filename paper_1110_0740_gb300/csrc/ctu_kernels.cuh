@@ -70,12 +70,19 @@ struct StepArgs {
     float gamf, gm1f;      // Gamma, Gamma-1 in float
     double glm_alpha;
     int upwind;            // tracing mode (CTU_TRACE_*); 2 and 3 only in the reference-state kernels
-    int limiter;
+    int limiter;           // linear reconstruction's slope (CTU_LINEAR_*), RECON_LIN kernels
     // hybrid integration (shock flags): per scratch cell, bit 1 shocked (HLL
     // at its faces), bit 2 MinMod reconstruction; null when off
     unsigned char *flags;
     double shock_eps;
-    int shock_q;           // 0 thermal, 1 magnetic pressure           // linear reconstruction's slope (CTU_LINEAR_*), RECON_LIN kernels
+    int shock_q;           // 0 thermal, 1 magnetic pressure
+    // thermal conduction (the RECON_*_TC kernels): conductivity, L_P^n per
+    // scratch cell (words of the working precision) and T^(n+1/2) (doubles)
+    double kappa;
+    float kappaf;          // kappa in float
+    float gm1lo;           // (Gamma-1) - gm1f in float: Gamma-1 as a double-float pair
+    const void *lp;
+    double *th;
     const double *U;       // pool in
     double *Uout;          // pool out
     long long ustride;     // pool variable stride
@@ -440,6 +447,12 @@ __device__ __forceinline__ unsigned int trace_cell_t(const StepArgs &a, const De
 {
     R pl[NV], ml[NV], pg[NV], mg[NV];
     unsigned int f = 0;
+    // thermal conduction: dt/2 L_P^n joins the half-step increments of every
+    // direction (Eq. transv with Pi != 0)
+    R Tc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Tc[q] = T[q];
+    if constexpr (recon_tc(PPM)) Tc[4] += R(0.5) * pdt<R>(a.sp) * static_cast<const R *>(a.lp)[c];
     if (PHYS == PH_MHD) {
         const int lim = recon_hybrid(PPM) ? ((a.flags[c] & 2) ? 2 : 0) : a.limiter;
         char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind, lim,
@@ -457,11 +470,11 @@ __device__ __forceinline__ unsigned int trace_cell_t(const StepArgs &a, const De
         mg[gperm<D>(q)] = ml[q];
     }
     if (PHYS == PH_MHD) {
-        f |= interface_state<R, IFACE64>(pg, T, a, Vp);
-        f |= interface_state<R, IFACE64>(mg, T, a, Vm);
+        f |= interface_state<R, IFACE64>(pg, Tc, a, Vp);
+        f |= interface_state<R, IFACE64>(mg, Tc, a, Vm);
     } else {
-        f |= sr_interface<R>(pg, T, a, Vp);
-        f |= sr_interface<R>(mg, T, a, Vm);
+        f |= sr_interface<R>(pg, Tc, a, Vp);
+        f |= sr_interface<R>(mg, Tc, a, Vm);
     }
     return f;
 }
@@ -1309,6 +1322,12 @@ __global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, GroupTable gt, u
         const unsigned int f = prim_any<PHYS, R>(U, a, V);
         if (f) atomicOr(a.status, f);
         m = cell_speed<PHYS, R>(V, a, P);
+        if (a.kappa > 0.0) {  // thermal conduction: + sum_d 2 D / dx_d^2, D = (Gamma-1) kappa / rho
+            const R D = (sizeof(R) == 8 ? (R)((a.gam - 1.0) * a.kappa) : (R)(a.gm1f * a.kappaf)) / V[0];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (d < a.ndim) m += R(2) * D * (pidx<R>(P, d) * pidx<R>(P, d));
+        }
     }
     block_max_to<R>(m, out);
 }

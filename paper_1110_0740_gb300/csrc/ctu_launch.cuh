@@ -5,6 +5,7 @@
 #include <atomic>
 
 #include "ctu_launch.h"
+#include "tc_ops.cuh"
 
 namespace ctu {
 
@@ -116,6 +117,15 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
                 [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 2, recon_hybrid(PPM), recon_hllc(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
         CTU_MARK(nullptr);
     }
+    if constexpr (recon_tc(PPM)) {  // thermal conduction: L_P^n and T^(n+1/2)
+        CTU_MARK("tc_half");
+        n += over_groups(
+            li, [&](const Group &G) { return Tiles::prim(G.N); },
+            [&](const GroupTable &gt, unsigned nb) {
+                k_tc_half<R><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
+            });
+        CTU_MARK(nullptr);
+    }
     // sweeps in the order z, y, x: the first writes A = L_D, the middle one
     // adds to it, and the x sweep (thread per cell) finishes the update
     if (a.ndim > 2) {
@@ -131,13 +141,25 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
             n += launch_sweep_m<PHYS, R, PPM, IF64, 1, SW_MID>(a, li, Vs, L1, A, s);
         CTU_MARK(nullptr);
     }
+    // with conduction the next step's CFL rate is taken after its update
+    StepArgs ax = a;
+    if constexpr (recon_tc(PPM)) ax.nextmax = nullptr;
     CTU_MARK("sweep_x");
     n += over_groups(
         li, [&](const Group &G) { return Tiles::sweep_x(G.n, G.xw); },
         [&](const GroupTable &gt, unsigned nb) {
-            k_sweep_x<PHYS, R, PPM, IF64, 1><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, A);
+            k_sweep_x<PHYS, R, PPM, IF64, 1><<<nb, BLOCK, 0, s>>>(ax, gt, Vs, L1, A);
         });
     CTU_MARK(nullptr);
+    if constexpr (recon_tc(PPM)) {  // thermal conduction: + dt L_P^(n+1/2)
+        CTU_MARK("tc_update");
+        n += over_groups(
+            li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
+            [&](const GroupTable &gt, unsigned nb) {
+                k_tc_update<PHYS, R><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
+            });
+        CTU_MARK(nullptr);
+    }
     return n;
 }
 
@@ -151,11 +173,15 @@ template <class R, int IF64> int launch_step_impl(const StepArgs &a, const Launc
 // MHD with the other reconstructions of Section 3.2 (G = 0: linear with the
 // MinMod, harmonic or Van Albada slope, or improved WENO3), with the
 // reference states of the tracing (G = 1: PPM or MC-linear), with the
-// hybrid integration (G = 2: PPM or MC-linear), or with the HLLC solver
-// (G = 3: PPM or MC-linear).
+// hybrid integration (G = 2: PPM or MC-linear), with the HLLC solver
+// (G = 3: PPM or MC-linear), or with thermal conduction (G = 4: PPM or
+// MC-linear).
 template <class R, int IF64, int G> int launch_step_var(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
-    if constexpr (G == 3)  // the HLLC solver
+    if constexpr (G == 4)  // thermal conduction
+        return li.recon == RECON_PPM_TC ? launch_step_t<PH_MHD, R, RECON_PPM_TC, IF64>(a, li, s)
+                                        : launch_step_t<PH_MHD, R, RECON_MC_TC, IF64>(a, li, s);
+    else if constexpr (G == 3)  // the HLLC solver
         return li.recon == RECON_PPM_HLLC ? launch_step_t<PH_MHD, R, RECON_PPM_HLLC, IF64>(a, li, s)
                                           : launch_step_t<PH_MHD, R, RECON_MC_HLLC, IF64>(a, li, s);
     else if constexpr (G == 2)  // the hybrid integration of the shock-detection appendix

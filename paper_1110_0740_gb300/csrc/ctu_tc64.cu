@@ -1,0 +1,7 @@
+// FP64 MHD path, PPM or MC-linear, with thermal conduction (the parabolic
+// term of the CTU step).
+#include "ctu_launch.cuh"
+
+namespace ctu {
+template int launch_step_var<double, 1, 4>(const StepArgs &, const LaunchInfo &, cudaStream_t);
+} // namespace ctu

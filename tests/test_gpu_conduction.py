@@ -1,0 +1,177 @@
+"""Thermal conduction (the parabolic term of the CTU step) on the GPU against
+the oracle: 3-D blast with PPM, 2-D turbulence with MC-linear and the 1-D
+linear mode, float64 (relative L1 1e-11) and mixed (the float tracing bar of
+the plain step); a ragged batch of patches in one call; the CFL rate with
+its diffusion term (ctu_dt and the step's next dt); refusal with bound flux
+registers."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1110_0740_gb300 import workloads as W
+from tests.gpu_util import gpu_run, l1rel, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+
+
+def _dev():
+    import torch
+    return torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("trace_mode", [0, 1])
+def test_conduction_3d_blast_ppm(trace_mode):
+    n = [24, 24, 24]
+    U0 = W.mhd_blast_3d(24, seed=31)
+    dx = [1.0 / 24] * 3
+    kappa = 0.01
+    ref, od = oracle_run(U0, n, 3, dx, 4, 0.3, recon=1, trace_mode=trace_mode, kappa=kappa)
+    plain, _ = oracle_run(U0, n, 3, dx, 4, 0.3, recon=1, trace_mode=trace_mode)
+    R = O.interior(ref, n, 3)
+    # the conduction changes the energy well above the tolerances below
+    assert np.abs(R[4] - O.interior(plain, n, 3)[4]).sum() > 1e-3 * np.abs(R[4]).sum()
+    for prec, tol in ((0, TOL64), (1, 2e-5)):
+        got, gd, st = gpu_run(U0, n, 3, dx, 4, 0.3, precision=prec, recon=1, trace_mode=trace_mode, kappa=kappa)
+        assert st == 0
+        e = l1rel(O.interior(got, n, 3), R, od[-1][1])
+        assert np.all(e <= tol), (prec, e)
+        if prec == 0:
+            assert np.allclose(np.array(gd), np.array(od), rtol=1e-13, atol=0)
+
+
+def test_conduction_2d_turbulence_mc():
+    n = [48, 48, 1]
+    U0 = W.mhd_turb_2d(48, seed=32)
+    dx = [1.0 / 48] * 2
+    kappa = 0.02
+    ref, od = oracle_run(U0, n, 2, dx, 10, 0.4, recon=0, kappa=kappa)
+    R = O.interior(ref, n, 2)
+    for prec, tol in ((0, TOL64), (1, 1e-4)):
+        got, _, st = gpu_run(U0, n, 2, dx, 10, 0.4, precision=prec, recon=0, kappa=kappa)
+        assert st == 0
+        G = O.interior(got, n, 2)
+        assert not np.any(G[3]) and not np.any(G[7])
+        e = l1rel(G, R, od[-1][1])
+        assert np.all(e <= tol), (prec, e)
+
+
+def test_conduction_1d_diffusion_dominated():
+    """1-D, a density wave on a moving gas in the regime where the diffusion
+    term sets dt (oracle pins: the linear thermal mode)."""
+    N = 64
+    n = [N, 1, 1]
+    shp = O.shape(n, 1)
+    x = (np.arange(shp[3]) - 4 + 0.5) / N
+    rho = 1.0 + 0.2 * np.cos(2 * np.pi * x)
+    z = np.zeros_like(rho)
+    U0 = np.zeros(shp)
+    U0[:, 0, 0] = W.ideal_cons([rho, z + 0.3, z, z, z + 1.0, z + 0.4, z + 0.2, z, z], 5.0 / 3.0)
+    dx = [1.0 / N]
+    kappa = 0.5
+    ref, od = oracle_run(U0, n, 1, dx, 30, 0.4, recon=1, kappa=kappa)
+    R = O.interior(ref, n, 1)
+    for prec, tol in ((0, TOL64), (1, 2e-5)):
+        got, gd, st = gpu_run(U0, n, 1, dx, 30, 0.4, precision=prec, recon=1, kappa=kappa)
+        assert st == 0
+        e = l1rel(O.interior(got, n, 1), R, od[-1][1], group_floor=True)
+        assert np.all(e <= tol), (prec, e)
+    # the diffusion term sets dt here
+    m_h = O.mhd_max_speed(U0, n, 1, dx)
+    m = O.mhd_max_rate(U0, n, 1, dx, 5.0 / 3.0, kappa)
+    assert m > 3 * m_h
+
+
+def test_conduction_batch_of_uneven_patches():
+    """Four patches of different shapes and cell widths in one call, each
+    against the oracle run patch by patch with the batch's dt."""
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    shapes = [(16, 16, 16), (8, 8, 8), (11, 1, 7), (5, 9, 3)]
+    dxs = [(1 / 16,) * 3, (1 / 8,) * 3, (0.05, 0.07, 0.06), (0.08, 0.05, 0.1)]
+    src = W.mhd_blast_3d(32, seed=33, kmax=3)
+    arrays, bases, base = [], [], 0
+    for i, n in enumerate(shapes):
+        A = np.zeros(O.shape(list(n), 3))
+        A[:] = src[:, 2 * i:2 * i + n[2] + 8, i:i + n[1] + 8, 3 * i:3 * i + n[0] + 8]
+        arrays.append(A)
+        bases.append(base)
+        base += A[0].size + 13
+    stride = base
+    pool = np.zeros((9, stride))
+    for A, b in zip(arrays, bases):
+        pool[:, b:b + A[0].size] = A.reshape(9, -1)
+    dev = _dev()
+    U = torch.from_numpy(pool).to(dev)
+    Uo = torch.zeros_like(U)
+    kappa = 0.004
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_FP64, cfl=0.3, kappa=kappa))
+    patches = ctu.make_patches([(n, dx, b) for n, dx, b in zip(shapes, dxs, bases)])
+    dtch = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.dt(U, stride, patches, dtch)
+    ctx.step(U, Uo, stride, patches, dtch)
+    assert ctx.status_sync() == 0
+    dt, ch = dtch.cpu().tolist()
+    m = max(O.mhd_max_rate(A, list(n), 3, list(dx), 5.0 / 3.0, kappa) for A, n, dx in zip(arrays, shapes, dxs))
+    dt_ref = 0.3 / m
+    assert abs(dt - dt_ref) <= 1e-13 * dt_ref
+    out = Uo.cpu().numpy()
+    for A, n, dx, b in zip(arrays, shapes, dxs, bases):
+        R, bad = O.mhd_step(A, list(n), 3, list(dx), dt, ch, recon=1, kappa=kappa)
+        assert bad == 0
+        G = out[:, b:b + A[0].size].reshape(A.shape)
+        e = l1rel(O.interior(G, list(n), 3), O.interior(R, list(n), 3), ch)
+        assert np.all(e <= TOL64), (n, e)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_conduction_next_dt_matches_ctu_dt(prec):
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    n = [20, 12, 16]
+    U0 = np.zeros(O.shape(n, 3))
+    O.interior(U0, n, 3)[:] = O.interior(W.mhd_blast_3d(20, seed=4, kmax=3), [20] * 3, 3)[:, :16, :12, :]
+    O.fill_periodic(U0, n, 3)
+    dev = _dev()
+    U = torch.from_numpy(U0.reshape(9, -1).copy()).to(dev)
+    Ua, Ub = torch.zeros_like(U), torch.zeros_like(U)
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=0.05))
+    p = ctu.make_patches([(n, [1 / 20, 1 / 12, 1 / 16], 0)])
+    d0 = torch.zeros(2, dtype=torch.float64, device=dev)
+    d1 = torch.zeros_like(d0)
+    d2 = torch.zeros_like(d0)
+    ctx.dt(U, U.shape[1], p, d0)
+    ctx.step(U, Ua, U.shape[1], p, d0)
+    ctx.step_next_dt(U, Ub, U.shape[1], p, d0, d1)
+    ctx.dt(Ub, U.shape[1], p, d2)
+    assert ctx.status_sync() == 0
+    assert torch.equal(Ua, Ub)
+    a, b = d1.cpu().numpy(), d2.cpu().numpy()
+    assert np.allclose(a, b, rtol=1e-13 if prec == 0 else 1e-6, atol=0), (a, b)
+    # and against the oracle's rate (float64)
+    if prec == 0:
+        m = O.mhd_max_rate(U0, n, 3, [1 / 20, 1 / 12, 1 / 16], 5.0 / 3.0, 0.05)
+        assert abs(d0.cpu().numpy()[0] - 0.3 / m) <= 1e-14 * 0.3 / m
+
+
+def test_conduction_refuses_bound_registers():
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    n = [8, 8, 8]
+    U0 = W.mhd_blast_3d(8, seed=1, kmax=2)
+    dev = _dev()
+    U = torch.from_numpy(U0.reshape(9, -1).copy()).to(dev)
+    Uo = torch.zeros_like(U)
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, kappa=0.01))
+    p = ctu.make_patches([(n, [1 / 8] * 3, 0)])
+    d0 = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.dt(U, U.shape[1], p, d0)
+    reg = torch.zeros(9 * 64, dtype=torch.float64, device=dev)
+    ctx.flux_registers(reg, [(0, 0, 0, 0, 8, 0, 8, 1.0, 0)])
+    with pytest.raises(ctu.CtuError) as e:
+        ctx.step(U, Uo, U.shape[1], p, d0)
+    assert e.value.code == 4
+    ctx.flux_registers(None, [])
+    ctx.step(U, Uo, U.shape[1], p, d0)
+    assert ctx.status_sync() == 0
