@@ -1226,11 +1226,18 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
         for (q = 0; q < NVAR; q++)
             for (long jb = 0; jb < nb; jb++)
                 for (long ja = 0; ja < na; ja++) {
+                    long id;
+                    double flux;
                     c[wd] = (int)W[1] - 1; /* F[d] at cell c is its upper face */
                     c[a] = (int)(W[2] + ja);
                     c[b] = (int)(W[4] + jb);
-                    reg[W[6] + (q * nb + jb) * na + ja] +=
-                        wgt[w] * dt * area * F[wd][q * nc + cidx(&G, c)];
+                    id = cidx(&G, c);
+                    flux = F[wd][q * nc + id];
+                    /* with conduction the energy flux through the face is
+                     * F - Pi^(n+1/2), Pi = kappa (T(c + e_d) - T(c)) / dx_d */
+                    if (q == 4 && Th)
+                        flux -= kappa * (Th[id + dstride(&G, wd)] - Th[id]) / h[wd];
+                    reg[W[6] + (q * nb + jb) * na + ja] += wgt[w] * dt * area * flux;
                 }
     }
 
@@ -1266,8 +1273,8 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
 }
 
 /* or_mhd_step_ex with thermal conduction of conductivity kappa >= 0 (the
- * parabolic term; see step_core).  The flux registers take the hyperbolic
- * fluxes only. */
+ * parabolic term; see step_core).  The flux registers take the energy flux
+ * F_E - Pi_E^(n+1/2) through their faces. */
 int or_mhd_step_tc(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                    double dx, double dy, double dz, double dt, double ch,
                    double gam, double glm_alpha, int recon, int upwind,

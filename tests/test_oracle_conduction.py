@@ -19,6 +19,9 @@ T = p / rho; diffusion term of Eq. Ca).
 - The same linear system in the conduction-dominated regime, with the
   three-point symbol in place of k^2: the time integration of the parabolic
   term is second order (a forward-Euler parabolic term misses by 10x).
+- Two levels (a fine patch in a periodic coarse one, two substeps): with
+  the parabolic flux in the flux registers, reflux restores conservation to
+  round-off; without reflux it does not.
 - A vanishing conductivity takes the conduction code path and reproduces
   the plain step bit for bit.
 """
@@ -222,3 +225,52 @@ def test_vanishing_kappa_is_the_plain_step():
     a, _ = O.mhd_step(U, n, 2, dx, dt, ch, recon=1)
     b, _ = O.mhd_step(U, n, 2, dx, dt, ch, recon=1, kappa=1e-300)
     assert np.array_equal(a, b)
+
+
+def test_reflux_with_conduction_restores_conservation_of_two_levels():
+    """The two-level case of the AMR pins with conduction: the registers take
+    F_E - Pi_E^(n+1/2), and restriction plus reflux conserve the totals to
+    round-off; the energy without reflux misses by far more."""
+    Nc = 32
+    nc = [Nc, Nc, 1]
+    hc = 1.0 / Nc
+    hf = hc / 2
+    kappa = 0.002
+    U = W.mhd_turb_2d(Nc, seed=6)
+    lo, hi = 8, 24
+    nfc = hi - lo
+    nf = [2 * nfc, 2 * nfc, 1]
+    total0 = O.interior(U, nc, 2).sum(axis=(1, 2, 3)) * hc * hc
+    cw, off, sets = [], 0, []
+    for d in (0, 1):
+        for side, f in ((-1, lo), (+1, hi)):
+            cw.append((d, f, lo, hi, 0, 1, off, -1.0))
+            sets.append([d, f, side, lo, hi, 0, 1, off])
+            off += 9 * nfc
+    fw, fsize = O.boundary_windows(nf, 2, weight=1.0, base=off)
+    reg = np.zeros(off + fsize)
+    O.fill_periodic(U, nc, 2)
+    dt, ch = O.dt_ch(O.mhd_max_rate(U, nc, 2, [hc, hc], G, kappa), [hc, hc], 2, 0.4)
+    Unew, bad = O.mhd_step(U, nc, 2, [hc, hc, 1], dt, ch, recon=1, windows=cw, reg=reg, kappa=kappa)
+    assert bad == 0
+    origin = [lo, lo, 0]
+    Uf = np.zeros(O.shape(nf, 2))
+    O.prolong(U, Unew, nc, 0.0, Uf, nf, [-4, -4, 0], [nf[0] + 4, nf[1] + 4, 1], origin, 2, 2)
+    for q in range(2):
+        Ufn, bad = O.mhd_step(Uf, nf, 2, [hf, hf, 1], dt / 2, ch, recon=1, windows=fw, reg=reg, kappa=kappa)
+        assert bad == 0
+        Uf = Ufn.copy()
+        for (l0, h0) in (((-4, -4), (0, nf[1] + 4)), ((nf[0], -4), (nf[0] + 4, nf[1] + 4)),
+                         ((0, -4), (nf[0], 0)), ((0, nf[1]), (nf[0], nf[1] + 4))):
+            O.prolong(U, Unew, nc, (q + 1) / 2, Uf, nf, [l0[0], l0[1], 0], [h0[0], h0[1], 1], origin, 2, 2)
+    O.restrict(Unew, nc, Uf, nf, [lo, lo, 0], [hi, hi, 1], origin, 2, 2)
+    no_reflux = O.interior(Unew, nc, 2).sum(axis=(1, 2, 3)) * hc * hc
+    fwin = {(w[0], w[1]): w for w in fw}
+    for d, f, side, a0, a1, b0, b1, creg in sets:
+        w = fwin[(d, 0 if side < 0 else nf[d])]
+        O.reflux(Unew, nc, [hc, hc], reg, d, f, side, a0, a1, b0, b1, creg, w[6], 0, 0, w[3] - w[2],
+                 w[5] - w[4], 2, 2)
+    total = O.interior(Unew, nc, 2).sum(axis=(1, 2, 3)) * hc * hc
+    scale = np.abs(O.interior(Unew, nc, 2)).sum(axis=(1, 2, 3)) * hc * hc
+    assert np.all(np.abs(total - total0)[:8] <= 1e-13 * scale[:8]), (total - total0)
+    assert np.abs(no_reflux - total0)[4] > 1e-8
