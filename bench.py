@@ -220,8 +220,7 @@ def run_ours(args):
                                     shock=(args.shock, 0) if args.shock else None,
                                     riemann=ctu.CTU_HLLC if args.riemann == "hllc" else ctu.CTU_HLLD,
                                     kappa=args.kappa))
-        if not args.kappa:  # the registers carry hyperbolic fluxes only
-            c.flux_registers(reg, windows)
+        c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
         if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
             c.autotune(U, Uo, stride, patches, dtch)
@@ -406,8 +405,7 @@ def run_ours(args):
                                         WORKLOAD.replace("PPM", f"{args.recon} reconstruction"))
                            + (f"; hybrid integration (shock flags, eps_q {args.shock})" if args.shock else "")
                            + ("; HLLC in place of HLLD" if args.riemann == "hllc" else "")
-                           + (f"; thermal conduction, kappa {args.kappa} (no flux registers)"
-                              if args.kappa else ""),
+                           + (f"; thermal conduction, kappa {args.kappa}" if args.kappa else ""),
                            "recon": args.recon, "shock_eps": args.shock or None,
                            "cells_per_gpu": cells, "patches_per_gpu": 1,
                            "precision": args.precision, "l2_flush": "inputs (1.3 GB) > L2",
@@ -932,8 +930,7 @@ def main():
     ap.add_argument("--riemann", default="hlld", choices=["hlld", "hllc"],
                     help="blast: the Riemann solver (the workload uses HLLD)")
     ap.add_argument("--kappa", type=float, default=0.0,
-                    help="blast: thermal conduction with this conductivity (0 = off); flux registers "
-                         "are then not bound")
+                    help="blast: thermal conduction with this conductivity (0 = off)")
     ap.add_argument("--shock", type=float, default=0.0,
                     help="blast: the hybrid integration with this shock threshold (thermal pressure; 0 = off)")
     ap.add_argument("--recon", default="ppm", choices=sorted(RECONS),

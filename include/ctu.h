@@ -170,10 +170,10 @@ typedef struct {
      * sum_d 2 D / dx_d^2, D = (Gamma-1) kappa / rho (Eq. Ca).  Ideal MHD with
      * CTU_PPM or CTU_LINEAR_MC, CTU_HLLD, trace_mode CTU_TRACE_ALL or
      * CTU_TRACE_UPWIND, no hybrid integration, CTU_FP64 or CTU_MIXED (else
-     * CTU_EUNSUPPORTED); T^(n+1/2) and the update's parabolic term are float64
-     * in both precisions.  Flux registers carry hyperbolic fluxes only, so a
-     * step with kappa > 0 and a bound register array returns
-     * CTU_EUNSUPPORTED; not in ctu_step_noalloc. */
+     * CTU_EUNSUPPORTED).  T^(n+1/2) and the update's parabolic term are
+     * float64 (CTU_FP64) or double-float with a float64 energy update
+     * (CTU_MIXED).  Bound flux registers take the energy flux
+     * F_E - Pi_E^(n+1/2) through their faces.  Not in ctu_step_noalloc. */
     double kappa;
 } ctu_config;
 

@@ -637,9 +637,6 @@ static ctu_status step_common(ctu_ctx *ctx, const double *U_in, double *U_out, i
                               void *stream)
 {
     if (!ctx || !U_in || !U_out || !d_dt_ch || U_in == U_out) return CTU_EINVAL;
-    // flux registers carry hyperbolic fluxes only
-    const bool tc = ctx->cfg.kappa > 0.0;
-    if (tc && ctx->reg && !ctx->hwin.empty()) return CTU_EUNSUPPORTED;
     ctu_status st = validate_patches(ctx, stride, patches, npatch);
     if (st != CTU_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;

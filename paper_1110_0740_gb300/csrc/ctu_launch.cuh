@@ -119,10 +119,16 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     }
     if constexpr (recon_tc(PPM)) {  // thermal conduction: L_P^n and T^(n+1/2)
         CTU_MARK("tc_half");
+        if (a.ndim > 1)
+            n += over_groups(
+                li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
+                [&](const GroupTable &gt, unsigned nb) {
+                    k_tc_half<R, false><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
+                });
         n += over_groups(
-            li, [&](const Group &G) { return Tiles::prim(G.N); },
+            li, [&](const Group &G) { return ((long long)tc_shell_cells(G.n, a.ndim) + BLOCK - 1) / BLOCK; },
             [&](const GroupTable &gt, unsigned nb) {
-                k_tc_half<R><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
+                k_tc_half<R, true><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
             });
         CTU_MARK(nullptr);
     }

@@ -25,15 +25,6 @@
 
 namespace ctu {
 
-// Interior-relative coordinates of ghosted cell c of patch P.
-__device__ __forceinline__ void tc_coords(const DevPatch &P, int c, int &i, int &j, int &k)
-{
-    const int row = c / P.N[0];
-    i = c - row * P.N[0] - P.g[0];
-    j = row % P.N[1] - P.g[1];
-    k = row / P.N[1] - P.g[2];
-}
-
 // Adds (F(c - e_D/2) - F(c + e_D/2)) / dx_D at scratch cell c to s (global
 // order), F from the cell-centred primitive states as in k_div1.
 template <class R, int D>
@@ -60,25 +51,75 @@ template <class R> __device__ __forceinline__ R tc_gk(const StepArgs &a);
 template <> __device__ __forceinline__ double tc_gk<double>(const StepArgs &a) { return (a.gam - 1.0) * a.kappa; }
 template <> __device__ __forceinline__ float tc_gk<float>(const StepArgs &a) { return a.gm1f * a.kappaf; }
 
-// One thread per ghosted cell (the k_prim tiling); cells outside the ring
-// box return at once.  L1: the first-order divergences (global order, ndim
-// > 1); LP: L_P^n per scratch cell (R); Th: T^(n+1/2) per scratch cell, a
-// double (FP64 path) or the double-float pair (hi, lo) (mixed path).
-template <class R>
+// L1: the first-order divergences (global order, ndim > 1); LP: L_P^n per
+// scratch cell (R); Th: T^(n+1/2) per scratch cell, a double (FP64 path) or
+// the double-float pair (hi, lo) (mixed path).
+// Cells of the ring box outside the interior (its outer layer), enumerated
+// compactly: the two x-faces (x = -1, n_x; y, z over the ring), the two
+// y-faces (x inside; z over the ring), the two z-faces (x, y inside); in 1-D
+// the whole ring box (the first-order stage does not run).
+__host__ __device__ __forceinline__ int tc_shell_cells(const int *n, int ndim)
+{
+    if (ndim == 1) return n[0] + 2;
+    const int e1 = n[1] + 2, e2 = ndim > 2 ? n[2] + 2 : 1;
+    return 2 * e1 * e2 + 2 * n[0] * e2 + (ndim > 2 ? 2 * n[0] * n[1] : 0);
+}
+
+__device__ __forceinline__ void tc_shell_coords(const DevPatch &P, int ndim, int t, int (&x)[3])
+{
+    if (ndim == 1) {
+        x[0] = t - 1;
+        x[1] = x[2] = 0;
+        return;
+    }
+    const int e1 = P.n[1] + 2, e2 = ndim > 2 ? P.n[2] + 2 : 1, lo2 = ndim > 2 ? 1 : 0;
+    const int cx = 2 * e1 * e2, cy = 2 * P.n[0] * e2;
+    if (t < cx) {
+        const int side = t / (e1 * e2), r = t - side * e1 * e2;
+        x[0] = side ? P.n[0] : -1;
+        x[1] = r % e1 - 1;
+        x[2] = r / e1 - lo2;
+    } else if (t < cx + cy) {
+        t -= cx;
+        const int side = t / (P.n[0] * e2), r = t - side * P.n[0] * e2;
+        x[0] = r % P.n[0];
+        x[1] = side ? P.n[1] : -1;
+        x[2] = r / P.n[0] - lo2;
+    } else {
+        t -= cx + cy;
+        const int side = t / (P.n[0] * P.n[1]), r = t - side * P.n[0] * P.n[1];
+        x[0] = r % P.n[0];
+        x[1] = r / P.n[0];
+        x[2] = side ? P.n[2] : -1;
+    }
+}
+
+// SHELL = false: the interior cells (ndim > 1), whose first-order
+// divergences the first-order stage formed in every direction, one thread
+// per cell in the k_maxspeed tiling; SHELL = true: the ring's outer layer
+// (tc_shell_cells), which solves the missing faces itself.  The split keeps
+// the Riemann solver, and its registers, out of the kernel that covers
+// almost all cells.
+template <class R, bool SHELL>
 __global__ void __launch_bounds__(BLOCK) k_tc_half(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *LP,
                                                    double *Th)
 {
     const Where w = locate(gt);
     const DevPatch P = a.patches[w.patch];
-    const int cl = w.b * BLOCK + threadIdx.x;
-    if (cl >= P.N[0] * P.N[1] * P.N[2]) return;
     int x[3];
-    tc_coords(P, cl, x[0], x[1], x[2]);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int lo = d < a.ndim ? -1 : 0, hi = d < a.ndim ? P.n[d] : 0;
-        if (x[d] < lo || x[d] > hi) return;
+    if constexpr (SHELL) {
+        const int t = w.b * BLOCK + threadIdx.x;
+        if (t >= tc_shell_cells(P.n, a.ndim)) return;
+        tc_shell_coords(P, a.ndim, t, x);
+    } else {
+        const Tile tl(w.xw);
+        const int T0 = (P.n[0] + tl.xw - 1) / tl.xw, T1 = (P.n[1] + tl.rows - 1) / tl.rows;
+        x[0] = (w.b % T0) * tl.xw + tl.tx();
+        x[1] = ((w.b / T0) % T1) * tl.rows + tl.ty();
+        x[2] = w.b / (T0 * T1);
+        if (x[0] >= P.n[0] || x[1] >= P.n[1] || x[2] >= P.n[2]) return;
     }
+    const int cl = lcell(P, x[0], x[1], x[2]);
     const long long S = a.sstride;
     const long long c = P.soff + cl;
     // L_P^n from T^n = p^n / rho^n
@@ -103,16 +144,17 @@ __global__ void __launch_bounds__(BLOCK) k_tc_half(StepArgs a, GroupTable gt, co
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         if (d >= a.ndim) continue;
-        if (a.ndim > 1 && x[d] >= 0 && x[d] < P.n[d]) {  // formed by the first-order stage
+        if (!SHELL || (a.ndim > 1 && x[d] >= 0 && x[d] < P.n[d])) {  // formed by the first-order stage
             const R *Ld = L1 + (long long)d * NV * S + c;
 #pragma unroll
-            for (int q = 0; q < NV; ++q) s[q] += Ld[q * S];
-        } else if (d == 0) {
-            tc_div1<R, 0>(a, P, Vs, c, gam, ch, s);
-        } else if (d == 1) {
-            tc_div1<R, 1>(a, P, Vs, c, gam, ch, s);
-        } else {
-            tc_div1<R, 2>(a, P, Vs, c, gam, ch, s);
+            for (int q = 0; q < 8; ++q) s[q] += Ld[q * S];
+        } else if constexpr (SHELL) {
+            if (d == 0)
+                tc_div1<R, 0>(a, P, Vs, c, gam, ch, s);
+            else if (d == 1)
+                tc_div1<R, 1>(a, P, Vs, c, gam, ch, s);
+            else
+                tc_div1<R, 2>(a, P, Vs, c, gam, ch, s);
         }
     }
     s[4] += lp;
@@ -151,9 +193,36 @@ __global__ void __launch_bounds__(BLOCK) k_tc_half(StepArgs a, GroupTable gt, co
     }
 }
 
+// Flux-register windows of the face of plane `plane` normal to D (transverse
+// coordinates ca, cb in increasing dimension order): the energy flux through
+// it gains -Pi^(n+1/2) (Eq. fluxcorr with the parabolic flux).
+template <class R, int D>
+__device__ __forceinline__ void tc_register(const StepArgs &a, const DevPatch &P, int patch, int plane, int ca,
+                                            int cb, R pi, double dt)
+{
+    const int B = window_base(a, patch, D);
+    if (B < 0) return;
+    const int w0 = window_first(a, B, plane), w1 = window_first(a, B, plane + 1);
+    if (w1 > w0) register_face_var<R, D>(a, P, w0, w1, ca, cb, 4, -pi, dt);
+}
+
+template <class R>
+__device__ __forceinline__ void tc_register_d(const StepArgs &a, const DevPatch &P, int patch, int d, int plane,
+                                              const int (&x)[3], R pi, double dt)
+{
+    if (d == 0)
+        tc_register<R, 0>(a, P, patch, plane, x[1], x[2], pi, dt);
+    else if (d == 1)
+        tc_register<R, 1>(a, P, patch, plane, x[0], x[2], pi, dt);
+    else
+        tc_register<R, 2>(a, P, patch, plane, x[0], x[1], pi, dt);
+}
+
 // U_out's energy += dt L_P^(n+1/2) on the interior cells (the k_maxspeed
-// tiling); with next != null also the CFL rate of the updated cell, Eq. (Ca)
-// with the diffusion term, folded into *next.
+// tiling); the flux registers of the cell's lower faces (and of its upper
+// faces on the patch's last plane) gain -dt Pi; with next != null also the
+// CFL rate of the updated cell, Eq. (Ca) with the diffusion term, folded
+// into *next.
 template <int PHYS, class R>
 __global__ void __launch_bounds__(BLOCK) k_tc_update(StepArgs a, GroupTable gt, const double *Th,
                                                      unsigned long long *next)
@@ -170,6 +239,7 @@ __global__ void __launch_bounds__(BLOCK) k_tc_update(StepArgs a, GroupTable gt, 
         const long long c = P.soff + cl;
         double *Uo = a.Uout + P.base + cl;
         double E;
+        const int x[3] = {i, j, k};
         if constexpr (sizeof(R) == 8) {
             const double Tc = Th[c];
             double lp = 0.0;
@@ -177,8 +247,14 @@ __global__ void __launch_bounds__(BLOCK) k_tc_update(StepArgs a, GroupTable gt, 
             for (int d = 0; d < 3; ++d) {
                 if (d >= a.ndim) continue;
                 const long long st = dstr(P, d);
+                const double up = Th[c + st] - Tc, dn = Tc - Th[c - st];
                 const double kd = a.kappa * (P.idx[d] * P.idx[d]);
-                lp = fma((Th[c + st] - Tc) - (Tc - Th[c - st]), kd, lp);
+                lp = fma(up - dn, kd, lp);
+                if (a.reg) {
+                    const double kh = a.kappa * P.idx[d];
+                    tc_register_d<double>(a, P, wh.patch, d, x[d], x, kh * dn, a.sp->dt);
+                    if (x[d] == P.n[d] - 1) tc_register_d<double>(a, P, wh.patch, d, x[d] + 1, x, kh * up, a.sp->dt);
+                }
             }
             E = fma(a.sp->dt, lp, Uo[4 * a.ustride]);
         } else {
@@ -195,6 +271,11 @@ __global__ void __launch_bounds__(BLOCK) k_tc_update(StepArgs a, GroupTable gt, 
                 const float up = df_add(df{tp.x, tp.y}, df_neg(Tc)).hi;
                 const float dn = df_add(Tc, df_neg(df{tm.x, tm.y})).hi;
                 lp = fmaf(up - dn, a.kappaf * (P.idxf[d] * P.idxf[d]), lp);
+                if (a.reg) {
+                    const float kh = a.kappaf * P.idxf[d];
+                    tc_register_d<float>(a, P, wh.patch, d, x[d], x, kh * dn, a.sp->dt);
+                    if (x[d] == P.n[d] - 1) tc_register_d<float>(a, P, wh.patch, d, x[d] + 1, x, kh * up, a.sp->dt);
+                }
             }
             E = fma(a.sp->dt, f2d_int(lp), Uo[4 * a.ustride]);
         }

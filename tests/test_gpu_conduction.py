@@ -2,8 +2,8 @@
 the oracle: 3-D blast with PPM, 2-D turbulence with MC-linear and the 1-D
 linear mode, float64 (relative L1 1e-11) and mixed (the float tracing bar of
 the plain step); a ragged batch of patches in one call; the CFL rate with
-its diffusion term (ctu_dt and the step's next dt); refusal with bound flux
-registers."""
+its diffusion term (ctu_dt and the step's next dt); flux registers with the
+parabolic energy flux."""
 import numpy as np
 import pytest
 
@@ -155,23 +155,53 @@ def test_conduction_next_dt_matches_ctu_dt(prec):
         assert abs(d0.cpu().numpy()[0] - 0.3 / m) <= 1e-14 * 0.3 / m
 
 
-def test_conduction_refuses_bound_registers():
+@pytest.mark.parametrize("prec", [0, 1])
+def test_conduction_flux_registers(prec):
+    """Register windows on every boundary face and on an interior plane of a
+    3-D patch, two steps accumulated: with conduction the energy entries
+    carry F_E - Pi_E^(n+1/2), as in the oracle (which conserves two levels
+    with them, see the oracle pins)."""
     import torch
     from paper_1110_0740_gb300 import ctu
-    n = [8, 8, 8]
-    U0 = W.mhd_blast_3d(8, seed=1, kmax=2)
+    n = [12, 10, 8]
+    dx = [1 / 12, 1 / 10, 1 / 8]
+    U0 = np.zeros(O.shape(n, 3))
+    O.interior(U0, n, 3)[:] = O.interior(W.mhd_blast_3d(12, seed=34, kmax=3), [12] * 3, 3)[:, :8, :10, :]
+    O.fill_periodic(U0, n, 3)
+    windows, ws, off = [], [], 0
+    for d in range(3):
+        a_, b_ = [e for e in range(3) if e != d]
+        for plane in (0, n[d] // 2, n[d]):
+            windows.append((0, d, plane, 0, n[a_], 0, n[b_], 0.75, off))
+            ws.append((d, plane, 0, n[a_], 0, n[b_], off, 0.75))
+            off += 9 * n[a_] * n[b_]
     dev = _dev()
+    kappa = 0.02
     U = torch.from_numpy(U0.reshape(9, -1).copy()).to(dev)
     Uo = torch.zeros_like(U)
-    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, kappa=0.01))
-    p = ctu.make_patches([(n, [1 / 8] * 3, 0)])
-    d0 = torch.zeros(2, dtype=torch.float64, device=dev)
-    ctx.dt(U, U.shape[1], p, d0)
-    reg = torch.zeros(9 * 64, dtype=torch.float64, device=dev)
-    ctx.flux_registers(reg, [(0, 0, 0, 0, 8, 0, 8, 1.0, 0)])
-    with pytest.raises(ctu.CtuError) as e:
-        ctx.step(U, Uo, U.shape[1], p, d0)
-    assert e.value.code == 4
-    ctx.flux_registers(None, [])
-    ctx.step(U, Uo, U.shape[1], p, d0)
+    reg = torch.zeros(off, dtype=torch.float64, device=dev)
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=kappa))
+    p = ctu.make_patches([(n, dx, 0)])
+    ctx.flux_registers(reg, windows)
+    dtch = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.dt(U, U.shape[1], p, dtch)
+    ctx.step(U, Uo, U.shape[1], p, dtch)
+    ctx.step(U, Uo, U.shape[1], p, dtch)
     assert ctx.status_sync() == 0
+    dt, ch = dtch.cpu().tolist()
+    ref = np.zeros(off)
+    R, bad = O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref, kappa=kappa)
+    O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref, kappa=kappa)
+    assert bad == 0
+    got = reg.cpu().numpy()
+    # the energy entries differ from the hyperbolic-only registers
+    ref0 = np.zeros(off)
+    O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref0)
+    O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref0)
+    scale = np.abs(ref).max()
+    assert np.abs(ref - ref0).max() > 1e-4 * scale
+    tol = 1e-12 if prec == 0 else 2e-5
+    assert np.abs(got - ref).max() <= tol * scale, np.abs(got - ref).max() / scale
+    G = Uo.cpu().numpy().reshape(U0.shape)
+    e = l1rel(O.interior(G, n, 3), O.interior(R, n, 3), ch)
+    assert np.all(e <= (TOL64 if prec == 0 else 2e-5)), e
