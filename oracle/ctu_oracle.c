@@ -843,11 +843,13 @@ void or_mhd_shock_flags(const double *U, int nx, int ny, int nz, int ndim, doubl
 
 /* Eq. (Ca): max over interior cells of
  *     max_d (|v_d| + c_f,d)/dx_d + sum_d 2 D / dx_d^2,
- * with D = (Gamma - 1) kappa / rho the diffusion coefficient of thermal
- * conduction (kappa = 0: no conduction).  The caller sets dt = C_a / max and
- * c_h = max * min_d dx_d (= C_a min_d dx_d / dt). */
-double or_mhd_max_rate(const double *U, int nx, int ny, int nz, int ndim,
-                       double dx, double dy, double dz, double gam, double kappa)
+ * with D the largest diffusion coefficient of the cell:
+ * max((Gamma - 1) kappa / rho, (4/3) nu), the diffusivities of the temperature
+ * under conduction and of the longitudinal velocity under viscosity (0 for
+ * kappa = nu = 0).  The caller sets dt = C_a / max and c_h = max * min_d dx_d
+ * (= C_a min_d dx_d / dt). */
+double or_mhd_max_rate_par(const double *U, int nx, int ny, int nz, int ndim,
+                           double dx, double dy, double dz, double gam, double kappa, double nu)
 {
     grid_t G;
     double h[3] = {dx, dy, dz}, m = 0.0;
@@ -869,8 +871,8 @@ double or_mhd_max_rate(const double *U, int nx, int ny, int nz, int ndim,
                     if (sd > s)
                         s = sd;
                 }
-                if (kappa > 0.0) {
-                    double D = (gam - 1.0) * kappa / V[0];
+                if (kappa > 0.0 || nu > 0.0) {
+                    double D = fmax((gam - 1.0) * kappa / V[0], 4.0 / 3.0 * nu);
                     for (d = 0; d < ndim; d++)
                         s += 2.0 * D / (h[d] * h[d]);
                 }
@@ -880,77 +882,156 @@ double or_mhd_max_rate(const double *U, int nx, int ny, int nz, int ndim,
     return m;
 }
 
+/* or_mhd_max_rate_par with conduction alone. */
+double or_mhd_max_rate(const double *U, int nx, int ny, int nz, int ndim,
+                       double dx, double dy, double dz, double gam, double kappa)
+{
+    return or_mhd_max_rate_par(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, 0.0);
+}
+
 /* max over interior cells of max_d (|v_d| + c_f,d)/dx_d (Eq. Ca without
  * parabolic terms). */
 double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
                         double dx, double dy, double dz, double gam)
 {
-    return or_mhd_max_rate(U, nx, ny, nz, ndim, dx, dy, dz, gam, 0.0);
+    return or_mhd_max_rate_par(U, nx, ny, nz, ndim, dx, dy, dz, gam, 0.0, 0.0);
 }
 
 /* ------------------------------------------------------------------ */
-/* Thermal conduction (parabolic term)                                 */
+/* Parabolic terms: thermal conduction and viscosity                   */
 /* ------------------------------------------------------------------ */
 
-/* Classical, isotropic thermal conduction: the heat flux of Eq. (tc_flux) in
- * the limit q -> infinity with kappa_par = kappa_perp = kappa constant, so
- * that Pi_E = kappa grad T with T = p / rho.  Its face value is the
- * second-order central difference of Section 3.1 with g = kappa, f = T:
- *     Pi_(d,+) = kappa (T(c + e_d) - T(c)) / dx_d,
- * and L_P = sum_d (Pi_(d,+) - Pi_(d,-)) / dx_d (Eq. incrementop_par on a
- * Cartesian grid) adds to the energy only.  T holds the temperature of every
- * ghosted cell; LP receives L_P on the cells c with lo <= c <= hi. */
-static void conduction_lp(const grid_t *G, const double *T, const double *h, double kappa, const int *lo,
-                          const int *hi, double *LP)
+/* The parabolic fluxes of Section 2.1.1 on a Cartesian grid, from the
+ * cell-centred fields W = (rho, v_x, v_y, v_z, T) (five arrays of ncell
+ * values, T = p / rho):
+ *   - classical isotropic thermal conduction, the heat flux of Eq. (tc_flux)
+ *     in the limit q -> infinity with kappa_par = kappa_perp = kappa:
+ *     Pi_E += kappa dT/dx_d;
+ *   - isotropic viscosity, the stress of Eq. (visc_tens) with constant
+ *     kinematic viscosity nu:
+ *     tau_(d,i) = rho nu (dv_i/dx_d + dv_d/dx_i - (2/3) delta_(di) div v),
+ *     Pi_(m_i) = tau_(d,i) and Pi_E += v . tau_d (the energy flux of the
+ *     viscous stresses).
+ * Face values follow Section 3.1 (Pi = g(U) df(U)/dx with g at the mean of
+ * the two cells' states and second-order central differences): at the face
+ * between c and c + e_d,
+ *     df/dx_d = (f(c + e_d) - f(c)) / dx_d,
+ *     df/dx_t = [f(c + e_t) - f(c - e_t) + f(c + e_d + e_t) - f(c + e_d - e_t)]
+ *               / (4 dx_t)  for an active t != d (0 on an inactive axis),
+ *     rho_f = (rho(c) + rho(c + e_d)) / 2,
+ *     v_f = (rho v (c) + rho v (c + e_d)) / (rho(c) + rho(c + e_d)),
+ * the last two being the density and velocity of the mean conserved state.
+ * Pi[1..3] receive the momentum fluxes and Pi[4] the energy flux. */
+static void parabolic_face(const grid_t *G, const double *W, const double *h, double kappa, double nu, long id,
+                           int d, double *Pi)
 {
-    int c[3], d;
+    const long nc = G->ncell, st = dstride(G, d), ip = id + st;
+    int q;
+    for (q = 0; q < NVAR; q++)
+        Pi[q] = 0.0;
+    if (kappa > 0.0)
+        Pi[4] += kappa * (W[4 * nc + ip] - W[4 * nc + id]) / h[d];
+    if (nu > 0.0) {
+        double grad[3][3], div = 0.0, rf, vf[3];
+        int i, t;
+        for (t = 0; t < 3; t++)
+            for (i = 0; i < 3; i++) {
+                const double *v = W + (1 + i) * nc;
+                if (t == d) {
+                    grad[t][i] = (v[ip] - v[id]) / h[d];
+                } else if (t < G->ndim) {
+                    const long s2 = dstride(G, t);
+                    grad[t][i] = (v[id + s2] - v[id - s2] + v[ip + s2] - v[ip - s2]) / (4.0 * h[t]);
+                } else {
+                    grad[t][i] = 0.0;
+                }
+            }
+        for (i = 0; i < 3; i++)
+            div += grad[i][i];
+        rf = 0.5 * (W[id] + W[ip]);
+        for (i = 0; i < 3; i++)
+            vf[i] = (W[id] * W[(1 + i) * nc + id] + W[ip] * W[(1 + i) * nc + ip]) / (W[id] + W[ip]);
+        for (i = 0; i < 3; i++) {
+            double tau = rf * nu * (grad[d][i] + grad[i][d] - (i == d ? 2.0 / 3.0 * div : 0.0));
+            Pi[1 + i] += tau;
+            Pi[4] += vf[i] * tau;
+        }
+    }
+}
+
+/* L_P = sum_d (Pi_(d,+) - Pi_(d,-)) / dx_d (Eq. incrementop_par, Cartesian)
+ * for the momentum and the energy, LP[q * ncell + id] (q = 1..4), on the
+ * cells lo <= c <= hi; the other entries are left as they are. */
+static void parabolic_lp(const grid_t *G, const double *W, const double *h, double kappa, double nu, const int *lo,
+                         const int *hi, double *LP)
+{
+    int c[3], d, q;
     for (c[2] = lo[2]; c[2] <= hi[2]; c[2]++)
         for (c[1] = lo[1]; c[1] <= hi[1]; c[1]++)
             for (c[0] = lo[0]; c[0] <= hi[0]; c[0]++) {
                 long id = cidx(G, c);
-                double s = 0.0;
+                double s[NVAR] = {0}, Pp[NVAR], Pm[NVAR];
                 for (d = 0; d < G->ndim; d++) {
-                    long st = dstride(G, d);
-                    double pp = kappa * (T[id + st] - T[id]) / h[d];
-                    double pm = kappa * (T[id] - T[id - st]) / h[d];
-                    s += (pp - pm) / h[d];
+                    parabolic_face(G, W, h, kappa, nu, id, d, Pp);
+                    parabolic_face(G, W, h, kappa, nu, id - dstride(G, d), d, Pm);
+                    for (q = 1; q <= 4; q++)
+                        s[q] += (Pp[q] - Pm[q]) / h[d];
                 }
-                LP[id] = s;
+                for (q = 1; q <= 4; q++)
+                    LP[q * G->ncell + id] = s[q];
             }
 }
 
-/* Temperature T = p / rho of every ghosted cell of U; returns the number of
- * cells with rho <= 0 or p <= 0. */
-static int temperature(const grid_t *G, const double *U, double gam, double *T)
+/* The fields W = (rho, v, T) of every ghosted cell of U; returns the number
+ * of cells with rho <= 0 or p <= 0. */
+static int parabolic_fields(const grid_t *G, const double *U, double gam, double *W)
 {
     int bad = 0, q;
-    for (long id = 0; id < G->ncell; id++) {
+    const long nc = G->ncell;
+    for (long id = 0; id < nc; id++) {
         double Uc[NVAR], Vc[NVAR];
         for (q = 0; q < NVAR; q++)
-            Uc[q] = U[q * G->ncell + id];
+            Uc[q] = U[q * nc + id];
         bad += or_mhd_cons2prim(Uc, gam, Vc);
-        T[id] = Vc[4] / Vc[0];
+        W[id] = Vc[0];
+        for (q = 1; q <= 3; q++)
+            W[q * nc + id] = Vc[q];
+        W[4 * nc + id] = Vc[4] / Vc[0];
     }
     return bad;
 }
 
-/* L_P of thermal conduction (see conduction_lp) on the interior cells of a
- * ghost-filled patch; LP has the ghosted layout (ghost entries are 0). */
-void or_mhd_conduction(const double *U, int nx, int ny, int nz, int ndim, double dx, double dy, double dz,
-                       double gam, double kappa, double *LP)
+/* L_P of conduction and viscosity on the interior cells of a ghost-filled
+ * patch: LP[q * ncell + id] for the momentum (q = 1..3) and the energy
+ * (q = 4), ghosted layout (the other entries are 0). */
+void or_mhd_parabolic(const double *U, int nx, int ny, int nz, int ndim, double dx, double dy, double dz,
+                      double gam, double kappa, double nu, double *LP)
 {
     grid_t G;
     double h[3] = {dx, dy, dz};
     int lo[3] = {0, 0, 0}, hi[3], d;
-    double *T;
+    double *W;
     grid_init(&G, nx, ny, nz, ndim);
     for (d = 0; d < 3; d++)
         hi[d] = G.n[d] - 1;
-    T = (double *)malloc(sizeof(double) * G.ncell);
-    temperature(&G, U, gam, T);
-    memset(LP, 0, sizeof(double) * G.ncell);
-    conduction_lp(&G, T, h, kappa, lo, hi, LP);
-    free(T);
+    W = (double *)malloc(sizeof(double) * 5 * G.ncell);
+    parabolic_fields(&G, U, gam, W);
+    memset(LP, 0, sizeof(double) * NVAR * G.ncell);
+    parabolic_lp(&G, W, h, kappa, nu, lo, hi, LP);
+    free(W);
+}
+
+/* The energy component of or_mhd_parabolic with conduction alone. */
+void or_mhd_conduction(const double *U, int nx, int ny, int nz, int ndim, double dx, double dy, double dz,
+                       double gam, double kappa, double *LP)
+{
+    grid_t G;
+    double *A;
+    grid_init(&G, nx, ny, nz, ndim);
+    A = (double *)malloc(sizeof(double) * NVAR * G.ncell);
+    or_mhd_parabolic(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, 0.0, A);
+    memcpy(LP, A + 4 * G.ncell, sizeof(double) * G.ncell);
+    free(A);
 }
 
 /* ------------------------------------------------------------------ */
@@ -996,23 +1077,25 @@ static int face_riemann(const double *VL, const double *VR, double gam, double c
     return or_mhd_riemann(VL, VR, gam, ch, F);
 }
 
-/* The step of or_mhd_step_ex and or_mhd_step_tc: with kappa > 0, thermal
- * conduction (conduction_lp) enters as the parabolic term of Section 3.1 (Pi
- * != 0): L_P^n from the cell-centred U^n joins the transverse increments of
- * every direction's predictor (Eq. transv), and the update adds L_P^(n+1/2)
- * from the cell-centred U^(n+1/2) = U^n + dt/2 sum_d (L_(H,d)^n + L_(P,d)^n),
- * L_H^n the first-order (Godunov) divergences. */
+/* The step of or_mhd_step_ex, or_mhd_step_tc and or_mhd_step_par: with
+ * kappa > 0 or nu > 0, conduction and viscosity (parabolic_lp) enter as the
+ * parabolic term of Section 3.1 (Pi != 0): L_P^n from the cell-centred U^n
+ * joins the transverse increments of every direction's predictor (Eq.
+ * transv), and the update adds L_P^(n+1/2) from the cell-centred
+ * U^(n+1/2) = U^n + dt/2 sum_d (L_(H,d)^n + L_(P,d)^n), L_H^n the first-order
+ * (Godunov) divergences. */
 static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                      double dx, double dy, double dz, double dt, double ch,
                      double gam, double glm_alpha, int recon, int upwind,
                      const long *win, const double *wgt, int nwin, double *reg,
-                     int solver, int shock, double eps_q, int qkind, double kappa)
+                     int solver, int shock, double eps_q, int qkind, double kappa, double nu)
 {
+    const int par = kappa > 0.0 || nu > 0.0;
     unsigned char *flags = NULL;
     grid_t G;
     double h[3] = {dx, dy, dz};
     double *V, *F1[3] = {0, 0, 0}, *Up[3] = {0, 0, 0}, *Um[3] = {0, 0, 0}, *F[3] = {0, 0, 0};
-    double *Tn = NULL, *LPn = NULL, *Th = NULL, *LPh = NULL;
+    double *Wn = NULL, *LPn = NULL, *Wh = NULL, *LPh = NULL;
     int ring_lo[3], ring_hi[3];
     int c[3], d, q, bad = 0;
     long nc;
@@ -1039,13 +1122,16 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
         ring_lo[d] = d < ndim ? -1 : 0;
         ring_hi[d] = d < ndim ? G.n[d] : 0;
     }
-    if (kappa > 0.0) {
-        /* L_P^n on the ring box, from T^n = p^n / rho^n */
-        Tn = (double *)malloc(sizeof(double) * nc);
-        LPn = (double *)calloc((size_t)nc, sizeof(double));
-        for (long id = 0; id < nc; id++)
-            Tn[id] = V[4 * nc + id] / V[id];
-        conduction_lp(&G, Tn, h, kappa, ring_lo, ring_hi, LPn);
+    if (par) {
+        /* L_P^n on the ring box, from W^n = (rho, v, p / rho)^n */
+        Wn = (double *)malloc(sizeof(double) * 5 * nc);
+        LPn = (double *)calloc((size_t)NVAR * nc, sizeof(double));
+        for (long id = 0; id < nc; id++) {
+            for (q = 0; q < 4; q++)
+                Wn[q * nc + id] = V[q * nc + id];
+            Wn[4 * nc + id] = V[4 * nc + id] / V[id];
+        }
+        parabolic_lp(&G, Wn, h, kappa, nu, ring_lo, ring_hi, LPn);
     }
 
     /* 2. first-order Godunov fluxes F^n_d = R(U_c, U_(c+e_d)) on the faces the
@@ -1059,9 +1145,9 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                 lo[e] = 0;
                 hi[e] = 0;
             } else if (e == d) {
-                /* with conduction, also the outer faces of the ring box */
-                lo[e] = kappa > 0.0 ? -2 : -1;
-                hi[e] = kappa > 0.0 ? G.n[e] : G.n[e] - 1;
+                /* with parabolic terms, also the outer faces of the ring box */
+                lo[e] = par ? -2 : -1;
+                hi[e] = par ? G.n[e] : G.n[e] - 1;
             } else {
                 lo[e] = -1;
                 hi[e] = G.n[e];
@@ -1119,7 +1205,8 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                     }
                     /* the parabolic term of every direction, Eq. (transv) */
                     if (LPn)
-                        T[4] += LPn[id];
+                        for (q = 1; q <= 4; q++)
+                            T[q] += LPn[q * nc + id];
                     or_mhd_prim2cons(Vp, gam, Ul);
                     for (q = 0; q < NVAR; q++)
                         Ug[PERM[d][q]] = Ul[q];
@@ -1164,13 +1251,13 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                 }
     }
 
-    /* 4b. with conduction: T^(n+1/2) of the cell-centred
+    /* 4b. with parabolic terms: W^(n+1/2) of the cell-centred
      *     U^(n+1/2) = U^n + dt/2 (sum_d L_(H,d)^n + L_P^n) on the ring box,
      *     then L_P^(n+1/2) on the interior */
-    if (kappa > 0.0) {
+    if (par) {
         int ilo[3] = {0, 0, 0}, ihi[3];
-        Th = (double *)calloc((size_t)nc, sizeof(double));
-        LPh = (double *)calloc((size_t)nc, sizeof(double));
+        Wh = (double *)calloc((size_t)5 * nc, sizeof(double));
+        LPh = (double *)calloc((size_t)NVAR * nc, sizeof(double));
         for (c[2] = ring_lo[2]; c[2] <= ring_hi[2]; c[2]++)
             for (c[1] = ring_lo[1]; c[1] <= ring_hi[1]; c[1]++)
                 for (c[0] = ring_lo[0]; c[0] <= ring_hi[0]; c[0]++) {
@@ -1180,16 +1267,17 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                         double s = 0.0;
                         for (d = 0; d < ndim; d++)
                             s += (F1[d][q * nc + id - dstride(&G, d)] - F1[d][q * nc + id]) / h[d];
-                        if (q == 4)
-                            s += LPn[id];
+                        s += LPn[q * nc + id];
                         Uh[q] = U[q * nc + id] + 0.5 * dt * s;
                     }
                     bad += or_mhd_cons2prim(Uh, gam, Vh);
-                    Th[id] = Vh[4] / Vh[0];
+                    for (q = 0; q < 4; q++)
+                        Wh[q * nc + id] = Vh[q];
+                    Wh[4 * nc + id] = Vh[4] / Vh[0];
                 }
         for (d = 0; d < 3; d++)
             ihi[d] = G.n[d] - 1;
-        conduction_lp(&G, Th, h, kappa, ilo, ihi, LPh);
+        parabolic_lp(&G, Wh, h, kappa, nu, ilo, ihi, LPh);
     }
 
     /* 5. conservative update, Eq. (update): U + dt * (L_x + L_y + L_z) (+ L_P) */
@@ -1209,8 +1297,8 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                         double s = 0.0;
                         for (d = 0; d < ndim; d++)
                             s += (F[d][q * nc + id - dstride(&G, d)] - F[d][q * nc + id]) / h[d];
-                        if (q == 4 && LPh)
-                            s += LPh[id];
+                        if (LPh)
+                            s += LPh[q * nc + id];
                         Unew[q * nc + id] = U[q * nc + id] + dt * s;
                     }
                     Unew[8 * nc + id] *= damp;
@@ -1233,19 +1321,22 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                     c[b] = (int)(W[4] + jb);
                     id = cidx(&G, c);
                     flux = F[wd][q * nc + id];
-                    /* with conduction the energy flux through the face is
-                     * F - Pi^(n+1/2), Pi = kappa (T(c + e_d) - T(c)) / dx_d */
-                    if (q == 4 && Th)
-                        flux -= kappa * (Th[id + dstride(&G, wd)] - Th[id]) / h[wd];
+                    /* with parabolic terms the flux through the face is
+                     * F - Pi^(n+1/2) (momentum and energy) */
+                    if (Wh && q >= 1 && q <= 4) {
+                        double Pi[NVAR];
+                        parabolic_face(&G, Wh, h, kappa, nu, id, wd, Pi);
+                        flux -= Pi[q];
+                    }
                     reg[W[6] + (q * nb + jb) * na + ja] += wgt[w] * dt * area * flux;
                 }
     }
 
     free(flags);
     free(V);
-    free(Tn);
+    free(Wn);
     free(LPn);
-    free(Th);
+    free(Wh);
     free(LPh);
     for (d = 0; d < 3; d++) {
         free(F1[d]);
@@ -1269,12 +1360,24 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
                    int solver, int shock, double eps_q, int qkind)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, 0.0);
+                     nwin, reg, solver, shock, eps_q, qkind, 0.0, 0.0);
 }
 
-/* or_mhd_step_ex with thermal conduction of conductivity kappa >= 0 (the
- * parabolic term; see step_core).  The flux registers take the energy flux
- * F_E - Pi_E^(n+1/2) through their faces. */
+/* or_mhd_step_ex with thermal conduction of conductivity kappa >= 0 and
+ * viscosity of kinematic viscosity nu >= 0 (the parabolic terms; see
+ * step_core and parabolic_face).  The flux registers take the fluxes
+ * F - Pi^(n+1/2) of the momentum and the energy through their faces. */
+int or_mhd_step_par(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
+                    double dx, double dy, double dz, double dt, double ch,
+                    double gam, double glm_alpha, int recon, int upwind,
+                    const long *win, const double *wgt, int nwin, double *reg,
+                    int solver, int shock, double eps_q, int qkind, double kappa, double nu)
+{
+    return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
+                     nwin, reg, solver, shock, eps_q, qkind, kappa, nu);
+}
+
+/* or_mhd_step_par with conduction alone. */
 int or_mhd_step_tc(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                    double dx, double dy, double dz, double dt, double ch,
                    double gam, double glm_alpha, int recon, int upwind,
@@ -1282,7 +1385,7 @@ int or_mhd_step_tc(const double *U, double *Unew, int nx, int ny, int nz, int nd
                    int solver, int shock, double eps_q, int qkind, double kappa)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, kappa);
+                     nwin, reg, solver, shock, eps_q, qkind, kappa, 0.0);
 }
 
 /* ------------------------------------------------------------------ */
