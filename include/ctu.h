@@ -175,6 +175,16 @@ typedef struct {
      * (CTU_MIXED).  Bound flux registers take the energy flux
      * F_E - Pi_E^(n+1/2) through their faces.  Not in ctu_step_noalloc. */
     double kappa;
+    /* Viscosity, the other parabolic term built: nu >= 0 the constant
+     * kinematic viscosity of the stress of Eq. (visc_tens),
+     * tau = rho nu (grad v + grad v^T - (2/3) I div v); 0 = off.  Momentum flux
+     * tau and energy flux v . tau per face, with the normal derivative as for
+     * kappa, each transverse derivative the mean of the two cells' central
+     * differences, rho and v at the face those of the mean conserved state.
+     * It enters the predictors, the update and the registers as kappa does,
+     * and the CFL diffusion coefficient becomes
+     * D = max((Gamma-1) kappa / rho, (4/3) nu).  Same combinations as kappa. */
+    double nu;
 } ctu_config;
 
 typedef struct {
@@ -211,9 +221,9 @@ typedef struct ctu_ctx ctu_ctx;
 ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out);
 
 /* CFL time step, Eq. (Ca): M = max over the interior cells of all patches of
- * max_d (|v_d| + c_f,d) / dx_d (+ sum_d 2 (Gamma-1) kappa / (rho dx_d^2) with
- * thermal conduction); then dt = cfl / M and c_h = M * min dx (the GLM
- * speed, equal to cfl * min dx / dt).  Writes {dt, c_h} to the device
+ * max_d (|v_d| + c_f,d) / dx_d (+ sum_d 2 D / dx_d^2 with the parabolic
+ * terms, D = max((Gamma-1) kappa / rho, (4/3) nu)); then dt = cfl / M and
+ * c_h = M * min dx (the GLM speed, equal to cfl * min dx / dt).  Writes {dt, c_h} to the device
  * array d_dt_ch[2]; if h_dt_ch is non-null it also copies them there and
  * synchronises the stream.  U: device pool; patches: host array. */
 ctu_status ctu_dt(ctu_ctx *ctx, const double *U, int64_t stride,

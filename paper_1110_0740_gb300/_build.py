@@ -12,14 +12,14 @@ OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "libctu.so"
 SOURCES = ["ctu_api.cu", "ctu_f64.cu", "ctu_f32.cu", "ctu_f32i.cu", "ctu_sr32.cu", "ctu_noalloc.cu",
            "fma_peak.cu", "ctu_var32.cu", "ctu_var64.cu", "ctu_ref32.cu", "ctu_ref64.cu", "ctu_hyb32.cu",
-           "ctu_hyb64.cu", "ctu_hllc32.cu", "ctu_hllc64.cu", "ctu_tc32.cu", "ctu_tc64.cu"]
+           "ctu_hyb64.cu", "ctu_hllc32.cu", "ctu_hllc64.cu", "ctu_par32.cu", "ctu_par64.cu"]
 # The float32 stages of the mixed paths divide and take square roots with the
 # approximate hardware forms (<= 2 ulp) and flush float32 denormals; float64
 # arithmetic is unaffected by these flags.
 FLOAT_FAST = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
 SOURCE_FLAGS = {"ctu_f32.cu": FLOAT_FAST, "ctu_f32i.cu": FLOAT_FAST, "ctu_sr32.cu": FLOAT_FAST,
                 "ctu_var32.cu": FLOAT_FAST, "ctu_ref32.cu": FLOAT_FAST, "ctu_hyb32.cu": FLOAT_FAST,
-                "ctu_hllc32.cu": FLOAT_FAST, "ctu_tc32.cu": FLOAT_FAST}
+                "ctu_hllc32.cu": FLOAT_FAST, "ctu_par32.cu": FLOAT_FAST}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -317,8 +317,9 @@ static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStr
 
 // Scratch layout: SCRATCH_ARRAYS planes of the working precision, then (each
 // 256-byte aligned) the shock flags of the hybrid integration (one byte per
-// scratch cell) and, with thermal conduction, L_P^n (one word of the working
-// precision) and T^(n+1/2) (one double) per scratch cell.
+// scratch cell) and, with the parabolic terms, L_P^n (four words of the
+// working precision) and the half-step fields (one 8-byte plane, T; five
+// with viscosity) per scratch cell.
 struct ScratchOffsets {
     size_t flags, lp, th, total;
 };
@@ -329,9 +330,10 @@ static ScratchOffsets scratch_offsets(const ctu_ctx *ctx)
     const size_t S = (size_t)ctx->sstride;
     ScratchOffsets o;
     o.flags = align256((size_t)SCRATCH_ARRAYS * S * elt);
+    const bool par = ctx->cfg.kappa > 0.0 || ctx->cfg.nu > 0.0;
     o.lp = align256(o.flags + (ctx->cfg.shock_detect ? S : 0));
-    o.th = align256(o.lp + (ctx->cfg.kappa > 0.0 ? S * elt : 0));
-    o.total = o.th + (ctx->cfg.kappa > 0.0 ? S * sizeof(double) : 0);
+    o.th = align256(o.lp + (par ? 4 * S * elt : 0));
+    o.total = o.th + (par ? (ctx->cfg.nu > 0.0 ? 5 : 1) * S * sizeof(double) : 0);
     return o;
 }
 
@@ -371,14 +373,18 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.shock_q = ctx->cfg.shock_q;
     a.flags = nullptr;
     a.kappa = ctx->cfg.kappa;
+    a.nu = ctx->cfg.nu;
     a.kappaf = (float)ctx->cfg.kappa;
+    a.nuf = (float)ctx->cfg.nu;
+    a.par_cond = ctx->cfg.kappa > 0.0;
+    a.par_visc = ctx->cfg.nu > 0.0;
     a.gm1lo = tm ? 0.0f : (float)((ctx->cfg.gamma - 1.0) - (double)a.gm1f);
     a.lp = nullptr;
     a.th = nullptr;
     if (ctx->scratch) {
         const ScratchOffsets o = scratch_offsets(ctx);
         if (ctx->cfg.shock_detect) a.flags = (unsigned char *)ctx->scratch + o.flags;
-        if (ctx->cfg.kappa > 0.0) {
+        if (a.par_cond || a.par_visc) {
             a.lp = (const unsigned char *)ctx->scratch + o.lp;
             a.th = (double *)((unsigned char *)ctx->scratch + o.th);
         }
@@ -408,12 +414,13 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
     const bool ref = ctx->cfg.trace_mode >= CTU_TRACE_CENTER;
     const bool hyb = ctx->cfg.shock_detect != 0;
     const bool hllc = ctx->cfg.physics == CTU_MHD && ctx->cfg.riemann == CTU_HLLC;
-    const bool tc = ctx->cfg.kappa > 0.0;
+    const bool par = ctx->cfg.kappa > 0.0 || ctx->cfg.nu > 0.0;
     li.recon = r == CTU_PPM
-                   ? (tc ? RECON_PPM_TC
-                         : (hllc ? RECON_PPM_HLLC : (hyb ? RECON_PPM_HYB : (ref ? RECON_PPM_REF : RECON_PPM))))
+                   ? (par ? RECON_PPM_PAR
+                          : (hllc ? RECON_PPM_HLLC : (hyb ? RECON_PPM_HYB : (ref ? RECON_PPM_REF : RECON_PPM))))
              : r == CTU_LINEAR_MC
-                   ? (tc ? RECON_MC_TC : (hllc ? RECON_MC_HLLC : (hyb ? RECON_MC_HYB : (ref ? RECON_MC_REF : RECON_MC))))
+                   ? (par ? RECON_MC_PAR
+                          : (hllc ? RECON_MC_HLLC : (hyb ? RECON_MC_HYB : (ref ? RECON_MC_REF : RECON_MC))))
              : r == CTU_WENO3 ? RECON_WENO3 : RECON_LIN;
     li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
     li.physics = ctx->cfg.physics == CTU_SRMHD ? PH_SR : PH_MHD;
@@ -427,7 +434,7 @@ namespace ctu {
 template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<double>(a, li, s);
-    if (recon_tc(li.recon)) return launch_step_var<double, 1, 4>(a, li, s);
+    if (recon_par(li.recon)) return launch_step_var<double, 1, 4>(a, li, s);
     if (recon_hllc(li.recon)) return launch_step_var<double, 1, 3>(a, li, s);
     if (recon_hybrid(li.recon)) return launch_step_var<double, 1, 2>(a, li, s);
     if (li.recon >= RECON_PPM_REF) return launch_step_var<double, 1, 1>(a, li, s);
@@ -436,7 +443,7 @@ template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cud
 template <> int launch_step<float>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<float>(a, li, s);
-    if (recon_tc(li.recon)) return launch_step_var<float, 0, 4>(a, li, s);
+    if (recon_par(li.recon)) return launch_step_var<float, 0, 4>(a, li, s);
     if (recon_hllc(li.recon)) return launch_step_var<float, 0, 3>(a, li, s);
     if (recon_hybrid(li.recon)) return launch_step_var<float, 0, 2>(a, li, s);
     if (li.recon >= RECON_PPM_REF) return launch_step_var<float, 0, 1>(a, li, s);
@@ -504,10 +511,11 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
             cfg->trace_mode > CTU_TRACE_UPWIND || cfg->precision == CTU_MIXED_IFACE64)
             return CTU_EUNSUPPORTED;
     }
-    if (!(cfg->kappa >= 0.0 && cfg->kappa < INFINITY)) return CTU_EINVAL;
-    // thermal conduction: ideal MHD, PPM or MC-linear, HLLD, tracing without
+    if (!(cfg->kappa >= 0.0 && cfg->kappa < INFINITY) || !(cfg->nu >= 0.0 && cfg->nu < INFINITY))
+        return CTU_EINVAL;
+    // the parabolic terms: ideal MHD, PPM or MC-linear, HLLD, tracing without
     // or with the w_(+/-) reference, no hybrid integration, FP64 or CTU_MIXED
-    if (cfg->kappa > 0.0 &&
+    if ((cfg->kappa > 0.0 || cfg->nu > 0.0) &&
         (cfg->physics != CTU_MHD || (cfg->recon != CTU_PPM && cfg->recon != CTU_LINEAR_MC) ||
          cfg->riemann != CTU_HLLD || cfg->trace_mode > CTU_TRACE_UPWIND || cfg->shock_detect ||
          cfg->precision == CTU_MIXED_IFACE64))

@@ -76,11 +76,15 @@ struct StepArgs {
     unsigned char *flags;
     double shock_eps;
     int shock_q;           // 0 thermal, 1 magnetic pressure
-    // thermal conduction (the RECON_*_TC kernels): conductivity, L_P^n per
-    // scratch cell (words of the working precision) and T^(n+1/2) (doubles)
-    double kappa;
-    float kappaf;          // kappa in float
+    // parabolic terms (the RECON_*_PAR kernels): conductivity kappa and
+    // kinematic viscosity nu (par_cond, par_visc: nonzero when on), L_P^n per
+    // scratch cell (4 planes of the working precision: momentum, energy) and
+    // the half-step fields (planes of 8 bytes: T, then rho and v with
+    // viscosity)
+    double kappa, nu;
+    float kappaf, nuf;     // kappa, nu in float
     float gm1lo;           // (Gamma-1) - gm1f in float: Gamma-1 as a double-float pair
+    int par_cond, par_visc;
     const void *lp;
     double *th;
     const double *U;       // pool in
@@ -447,12 +451,20 @@ __device__ __forceinline__ unsigned int trace_cell_t(const StepArgs &a, const De
 {
     R pl[NV], ml[NV], pg[NV], mg[NV];
     unsigned int f = 0;
-    // thermal conduction: dt/2 L_P^n joins the half-step increments of every
+    // parabolic terms: dt/2 L_P^n joins the half-step increments of every
     // direction (Eq. transv with Pi != 0)
     R Tc[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) Tc[q] = T[q];
-    if constexpr (recon_tc(PPM)) Tc[4] += R(0.5) * pdt<R>(a.sp) * static_cast<const R *>(a.lp)[c];
+    if constexpr (recon_par(PPM)) {
+        const R *lp = static_cast<const R *>(a.lp) + c;
+        const R hd = R(0.5) * pdt<R>(a.sp);
+        Tc[4] += hd * lp[3 * a.sstride];
+        if (a.par_visc) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Tc[1 + q] += hd * lp[q * a.sstride];
+        }
+    }
     if (PHYS == PH_MHD) {
         const int lim = recon_hybrid(PPM) ? ((a.flags[c] & 2) ? 2 : 0) : a.limiter;
         char_predict<R, PPM>(vs, pgam<R>(a), ch, dtdx, a.upwind, lim,
@@ -1322,8 +1334,10 @@ __global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, GroupTable gt, u
         const unsigned int f = prim_any<PHYS, R>(U, a, V);
         if (f) atomicOr(a.status, f);
         m = cell_speed<PHYS, R>(V, a, P);
-        if (a.kappa > 0.0) {  // thermal conduction: + sum_d 2 D / dx_d^2, D = (Gamma-1) kappa / rho
-            const R D = (sizeof(R) == 8 ? (R)((a.gam - 1.0) * a.kappa) : (R)(a.gm1f * a.kappaf)) / V[0];
+        if (a.par_cond | a.par_visc) {  // parabolic terms: + sum_d 2 D / dx_d^2
+            // D = max((Gamma-1) kappa / rho, (4/3) nu)
+            const R D = max((sizeof(R) == 8 ? (R)((a.gam - 1.0) * a.kappa) : (R)(a.gm1f * a.kappaf)) / V[0],
+                            R(4.0 / 3.0) * (sizeof(R) == 8 ? (R)a.nu : (R)a.nuf));
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 if (d < a.ndim) m += R(2) * D * (pidx<R>(P, d) * pidx<R>(P, d));

@@ -3,9 +3,10 @@
 #pragma once
 
 #include <atomic>
+#include <type_traits>
 
 #include "ctu_launch.h"
-#include "tc_ops.cuh"
+#include "par_ops.cuh"
 
 namespace ctu {
 
@@ -117,19 +118,26 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
                 [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 2, recon_hybrid(PPM), recon_hllc(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
         CTU_MARK(nullptr);
     }
-    if constexpr (recon_tc(PPM)) {  // thermal conduction: L_P^n and T^(n+1/2)
-        CTU_MARK("tc_half");
-        if (a.ndim > 1)
+    if constexpr (recon_par(PPM)) {  // parabolic terms: L_P^n and the half-step fields
+        CTU_MARK("par_half");
+        auto half = [&](auto visc) {
+            constexpr bool V = decltype(visc)::value;
+            if (a.ndim > 1)
+                n += over_groups(
+                    li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
+                    [&](const GroupTable &gt, unsigned nb) {
+                        k_par_half<R, false, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
+                    });
             n += over_groups(
-                li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
+                li, [&](const Group &G) { return ((long long)par_shell_cells(G.n, a.ndim) + BLOCK - 1) / BLOCK; },
                 [&](const GroupTable &gt, unsigned nb) {
-                    k_tc_half<R, false><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
+                    k_par_half<R, true, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
                 });
-        n += over_groups(
-            li, [&](const Group &G) { return ((long long)tc_shell_cells(G.n, a.ndim) + BLOCK - 1) / BLOCK; },
-            [&](const GroupTable &gt, unsigned nb) {
-                k_tc_half<R, true><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
-            });
+        };
+        if (a.par_visc)
+            half(std::true_type{});
+        else
+            half(std::false_type{});
         CTU_MARK(nullptr);
     }
     // sweeps in the order z, y, x: the first writes A = L_D, the middle one
@@ -147,9 +155,9 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
             n += launch_sweep_m<PHYS, R, PPM, IF64, 1, SW_MID>(a, li, Vs, L1, A, s);
         CTU_MARK(nullptr);
     }
-    // with conduction the next step's CFL rate is taken after its update
+    // with parabolic terms the next step's CFL rate is taken after their update
     StepArgs ax = a;
-    if constexpr (recon_tc(PPM)) ax.nextmax = nullptr;
+    if constexpr (recon_par(PPM)) ax.nextmax = nullptr;
     CTU_MARK("sweep_x");
     n += over_groups(
         li, [&](const Group &G) { return Tiles::sweep_x(G.n, G.xw); },
@@ -157,12 +165,15 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
             k_sweep_x<PHYS, R, PPM, IF64, 1><<<nb, BLOCK, 0, s>>>(ax, gt, Vs, L1, A);
         });
     CTU_MARK(nullptr);
-    if constexpr (recon_tc(PPM)) {  // thermal conduction: + dt L_P^(n+1/2)
-        CTU_MARK("tc_update");
+    if constexpr (recon_par(PPM)) {  // parabolic terms: + dt L_P^(n+1/2)
+        CTU_MARK("par_update");
         n += over_groups(
             li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
             [&](const GroupTable &gt, unsigned nb) {
-                k_tc_update<PHYS, R><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
+                if (a.par_visc)
+                    k_par_update<PHYS, R, true><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
+                else
+                    k_par_update<PHYS, R, false><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
             });
         CTU_MARK(nullptr);
     }
@@ -180,13 +191,13 @@ template <class R, int IF64> int launch_step_impl(const StepArgs &a, const Launc
 // MinMod, harmonic or Van Albada slope, or improved WENO3), with the
 // reference states of the tracing (G = 1: PPM or MC-linear), with the
 // hybrid integration (G = 2: PPM or MC-linear), with the HLLC solver
-// (G = 3: PPM or MC-linear), or with thermal conduction (G = 4: PPM or
-// MC-linear).
+// (G = 3: PPM or MC-linear), or with the parabolic terms, conduction and
+// viscosity (G = 4: PPM or MC-linear).
 template <class R, int IF64, int G> int launch_step_var(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
-    if constexpr (G == 4)  // thermal conduction
-        return li.recon == RECON_PPM_TC ? launch_step_t<PH_MHD, R, RECON_PPM_TC, IF64>(a, li, s)
-                                        : launch_step_t<PH_MHD, R, RECON_MC_TC, IF64>(a, li, s);
+    if constexpr (G == 4)  // the parabolic terms
+        return li.recon == RECON_PPM_PAR ? launch_step_t<PH_MHD, R, RECON_PPM_PAR, IF64>(a, li, s)
+                                         : launch_step_t<PH_MHD, R, RECON_MC_PAR, IF64>(a, li, s);
     else if constexpr (G == 3)  // the HLLC solver
         return li.recon == RECON_PPM_HLLC ? launch_step_t<PH_MHD, R, RECON_PPM_HLLC, IF64>(a, li, s)
                                           : launch_step_t<PH_MHD, R, RECON_MC_HLLC, IF64>(a, li, s);

@@ -1,5 +1,5 @@
-// Mixed MHD path (CTU_MIXED), PPM or MC-linear, with thermal conduction (the
-// parabolic term; float64 half-step temperature and update).
+// Mixed MHD path (CTU_MIXED), PPM or MC-linear, with the parabolic terms
+// (thermal conduction, viscosity).
 #include "ctu_launch.cuh"
 
 namespace ctu {

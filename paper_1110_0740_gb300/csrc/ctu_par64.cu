@@ -1,5 +1,5 @@
-// FP64 MHD path, PPM or MC-linear, with thermal conduction (the parabolic
-// term of the CTU step).
+// FP64 MHD path, PPM or MC-linear, with the parabolic terms
+// (thermal conduction, viscosity).
 #include "ctu_launch.cuh"
 
 namespace ctu {

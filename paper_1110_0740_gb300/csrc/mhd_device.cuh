@@ -95,24 +95,25 @@ template <class R> __device__ __forceinline__ R lin_slope(R dm, R dp, int lim)
 // The hybrid kinds (RECON_PPM_HYB, RECON_MC_HYB) reconstruct with MinMod
 // where the shock flags ask for it (lim == 2 at run time).
 // RECON_PPM_HLLC and RECON_MC_HLLC take the HLLC solver on every face.
-// RECON_PPM_TC and RECON_MC_TC add thermal conduction (tracing modes ALL and
-// UPWIND, as RECON_PPM and RECON_MC).
+// RECON_PPM_PAR and RECON_MC_PAR add the parabolic terms, thermal
+// conduction and viscosity (tracing modes ALL and UPWIND, as RECON_PPM and
+// RECON_MC).
 enum {
     RECON_MC = 0, RECON_PPM = 1, RECON_LIN = 2, RECON_WENO3 = 3, RECON_PPM_REF = 4, RECON_MC_REF = 5,
-    RECON_PPM_HYB = 6, RECON_MC_HYB = 7, RECON_PPM_HLLC = 8, RECON_MC_HLLC = 9, RECON_PPM_TC = 10,
-    RECON_MC_TC = 11
+    RECON_PPM_HYB = 6, RECON_MC_HYB = 7, RECON_PPM_HLLC = 8, RECON_MC_HLLC = 9, RECON_PPM_PAR = 10,
+    RECON_MC_PAR = 11
 };
 
 __host__ __device__ constexpr int recon_base(int r)
 {
-    return (r == RECON_PPM_REF || r == RECON_PPM_HYB || r == RECON_PPM_HLLC || r == RECON_PPM_TC)
+    return (r == RECON_PPM_REF || r == RECON_PPM_HYB || r == RECON_PPM_HLLC || r == RECON_PPM_PAR)
                ? RECON_PPM
-               : ((r == RECON_MC_REF || r == RECON_MC_HYB || r == RECON_MC_HLLC || r == RECON_MC_TC) ? RECON_MC : r);
+               : ((r == RECON_MC_REF || r == RECON_MC_HYB || r == RECON_MC_HLLC || r == RECON_MC_PAR) ? RECON_MC : r);
 }
 
 __host__ __device__ constexpr bool recon_hybrid(int r) { return r == RECON_PPM_HYB || r == RECON_MC_HYB; }
 __host__ __device__ constexpr bool recon_hllc(int r) { return r == RECON_PPM_HLLC || r == RECON_MC_HLLC; }
-__host__ __device__ constexpr bool recon_tc(int r) { return r == RECON_PPM_TC || r == RECON_MC_TC; }
+__host__ __device__ constexpr bool recon_par(int r) { return r == RECON_PPM_PAR || r == RECON_MC_PAR; }
 
 // Interface values w_(i,+/-) of one characteristic field from w_(i-2..i+2):
 // PPM, Eq. (ppm1) + parabolic limiter Eq. (ppm_parabolic_lim); linear,

@@ -1,0 +1,398 @@
+// par_ops.cuh -- the parabolic terms of the CTU step (Section 3.1 with
+// Pi != 0): classical isotropic thermal conduction (Eq. tc_flux with
+// q -> infinity, kappa_par = kappa_perp = kappa), Pi_E = kappa grad T with
+// T = p / rho, and isotropic viscosity (Eq. visc_tens, constant kinematic
+// viscosity nu), tau = rho nu (grad v + grad v^T - (2/3) I div v) with the
+// momentum flux Pi_m = tau and the energy flux Pi_E += v . tau.
+//
+// Face values (the central differences of Section 3.1, g(U) at the mean of
+// the two cells' states): at the face between c and c + e_d the normal
+// derivative is (f(c + e_d) - f(c)) / dx_d, a transverse one (active t != d)
+// the mean of the two cells' central differences,
+//   [f(c + e_t) - f(c - e_t) + f(c + e_d + e_t) - f(c + e_d - e_t)] / (4 dx_t),
+// rho_f the mean density and v_f = (rho v (c) + rho v (c + e_d)) /
+// (rho(c) + rho(c + e_d)); L_P = sum_d (Pi_(d,+) - Pi_(d,-)) / dx_d acts on the
+// momentum and the energy.
+//
+// Kernels around the hyperbolic step:
+//   k_par_half   after the first-order stage, on the ring box (the interior
+//                and one layer around it): L_P^n from the primitive fields of
+//                U^n (the predictors of every direction add dt/2 L_P^n, Eq.
+//                transv), and the fields (T, rho, v) of the cell-centred
+//                U^(n+1/2) = U^n + dt/2 (sum_d L_(H,d)^n + L_P^n).  L_(H,d)^n is
+//                the first-order stage's divergence where that stage formed
+//                it; the ring's outer layer (a launch of its own, SHELL)
+//                solves the missing faces with the same solver
+//   k_par_update U^(n+1) += dt L_P^(n+1/2) on the interior (Eq. update), the
+//                flux registers' momentum and energy take -dt A Pi, and on
+//                request the CFL rate of the result (with the diffusion
+//                term), in place of the fused reduction of the last sweep
+// The n+1/2 fields and the update are float64 (FP64 path) or double-float
+// with float64 update FMAs (mixed path: no other FP64-pipe instruction).
+// With nu = 0 only the temperature is formed and stored.
+#pragma once
+
+#include "ctu_kernels.cuh"
+
+namespace ctu {
+
+// Planes of the half-step fields (8 bytes per scratch cell each): T, then
+// with viscosity rho, v_x, v_y, v_z.  Field index f: 0 rho, 1..3 v, 4 T.
+__host__ __device__ __forceinline__ int par_plane(int f) { return f == 4 ? 0 : f + 1; }
+
+// Adds (F(c - e_D/2) - F(c + e_D/2)) / dx_D at scratch cell c to s (global
+// order), F from the cell-centred primitive states as in k_div1.
+template <class R, int D>
+__device__ __forceinline__ void par_div1(const StepArgs &a, const DevPatch &P, const R *Vs, long long c, R gam,
+                                         R ch, R (&s)[NV])
+{
+    const long long st = dstr(P, D);
+    R Vm[NV], V0[NV], Vp[NV], Fm[NV], Fp[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        Vm[q] = Vs[gperm<D>(q) * a.sstride + c - st];
+        V0[q] = Vs[gperm<D>(q) * a.sstride + c];
+        Vp[q] = Vs[gperm<D>(q) * a.sstride + c + st];
+    }
+    riemann_any<PH_MHD, R>(Vm, V0, gam, ch, Fm);
+    riemann_any<PH_MHD, R>(V0, Vp, gam, ch, Fp);
+    const R iD = pidx<R>(P, D);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) s[gperm<D>(q)] += (Fm[q] - Fp[q]) * iD;
+}
+
+// (Gamma - 1) kappa, nu and kappa in the working precision.
+template <class R> __device__ __forceinline__ R par_gk(const StepArgs &a);
+template <> __device__ __forceinline__ double par_gk<double>(const StepArgs &a) { return (a.gam - 1.0) * a.kappa; }
+template <> __device__ __forceinline__ float par_gk<float>(const StepArgs &a) { return a.gm1f * a.kappaf; }
+template <class R> __device__ __forceinline__ R par_nu(const StepArgs &a);
+template <> __device__ __forceinline__ double par_nu<double>(const StepArgs &a) { return a.nu; }
+template <> __device__ __forceinline__ float par_nu<float>(const StepArgs &a) { return a.nuf; }
+template <class R> __device__ __forceinline__ R par_kappa(const StepArgs &a);
+template <> __device__ __forceinline__ double par_kappa<double>(const StepArgs &a) { return a.kappa; }
+template <> __device__ __forceinline__ float par_kappa<float>(const StepArgs &a) { return a.kappaf; }
+
+// Parabolic fluxes through the face between scratch cells c and c + e_d:
+// Pi[0..2] momentum, Pi[3] energy.  get(f, i): field f of cell i; dif(f, i, j):
+// field f of cell i minus that of cell j.
+template <class R, bool VISC, class Get, class Dif>
+__device__ __forceinline__ void par_face(const StepArgs &a, const DevPatch &P, long long c, int d, Get get,
+                                         Dif dif, R (&Pi)[4])
+{
+    const long long st = dstr(P, d), cp = c + st;
+    const R ih = pidx<R>(P, d);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Pi[q] = R(0);
+    if (a.par_cond) Pi[3] = par_kappa<R>(a) * dif(4, cp, c) * ih;
+    if constexpr (VISC) {
+        R g[3][3];  // g[t][i] = dv_i / dx_t at the face
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t == d) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) g[t][i] = dif(1 + i, cp, c) * ih;
+            } else if (t < a.ndim) {
+                const long long s2 = dstr(P, t);
+                const R q4 = R(0.25) * pidx<R>(P, t);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) g[t][i] = (dif(1 + i, c + s2, c - s2) + dif(1 + i, cp + s2, cp - s2)) * q4;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) g[t][i] = R(0);
+            }
+        }
+        const R div = g[0][0] + g[1][1] + g[2][2];
+        const R r0 = get(0, c), r1 = get(0, cp);
+        const R rnu = R(0.5) * (r0 + r1) * par_nu<R>(a);
+        const R irs = R(1) / (r0 + r1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const R tau = rnu * (g[d][i] + g[i][d] - (i == d ? R(2.0 / 3.0) * div : R(0)));
+            const R vf = (r0 * get(1 + i, c) + r1 * get(1 + i, cp)) * irs;
+            Pi[i] += tau;
+            Pi[3] += vf * tau;
+        }
+    }
+}
+
+// L_P at scratch cell c: sum_d (Pi(c, d) - Pi(c - e_d, d)) / dx_d; faces(d,
+// Pm, Pp) receives each direction's lower and upper face fluxes.
+template <class R, bool VISC, class Get, class Dif, class Faces>
+__device__ __forceinline__ void par_lp(const StepArgs &a, const DevPatch &P, long long c, Get get, Dif dif,
+                                       R (&lp)[4], Faces faces)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) lp[q] = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= a.ndim) continue;
+        R Pp[4], Pm[4];
+        par_face<R, VISC>(a, P, c, d, get, dif, Pp);
+        par_face<R, VISC>(a, P, c - dstr(P, d), d, get, dif, Pm);
+        const R ih = pidx<R>(P, d);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lp[q] += (Pp[q] - Pm[q]) * ih;
+        faces(d, Pm, Pp);
+    }
+}
+
+// Cells of the ring box outside the interior (its outer layer), enumerated
+// compactly: the two x-faces (x = -1, n_x; y, z over the ring), the two
+// y-faces (x inside; z over the ring), the two z-faces (x, y inside); in 1-D
+// the whole ring box (the first-order stage does not run).
+__host__ __device__ __forceinline__ int par_shell_cells(const int *n, int ndim)
+{
+    if (ndim == 1) return n[0] + 2;
+    const int e1 = n[1] + 2, e2 = ndim > 2 ? n[2] + 2 : 1;
+    return 2 * e1 * e2 + 2 * n[0] * e2 + (ndim > 2 ? 2 * n[0] * n[1] : 0);
+}
+
+__device__ __forceinline__ void par_shell_coords(const DevPatch &P, int ndim, int t, int (&x)[3])
+{
+    if (ndim == 1) {
+        x[0] = t - 1;
+        x[1] = x[2] = 0;
+        return;
+    }
+    const int e1 = P.n[1] + 2, e2 = ndim > 2 ? P.n[2] + 2 : 1, lo2 = ndim > 2 ? 1 : 0;
+    const int cx = 2 * e1 * e2, cy = 2 * P.n[0] * e2;
+    if (t < cx) {
+        const int side = t / (e1 * e2), r = t - side * e1 * e2;
+        x[0] = side ? P.n[0] : -1;
+        x[1] = r % e1 - 1;
+        x[2] = r / e1 - lo2;
+    } else if (t < cx + cy) {
+        t -= cx;
+        const int side = t / (P.n[0] * e2), r = t - side * P.n[0] * e2;
+        x[0] = r % P.n[0];
+        x[1] = side ? P.n[1] : -1;
+        x[2] = r / P.n[0] - lo2;
+    } else {
+        t -= cx + cy;
+        const int side = t / (P.n[0] * P.n[1]), r = t - side * P.n[0] * P.n[1];
+        x[0] = r % P.n[0];
+        x[1] = r / P.n[0];
+        x[2] = side ? P.n[2] : -1;
+    }
+}
+
+// SHELL = false: the interior cells (ndim > 1), whose first-order
+// divergences the first-order stage formed in every direction, one thread
+// per cell in the k_maxspeed tiling; SHELL = true: the ring's outer layer
+// (par_shell_cells), which solves the missing faces itself.  The split keeps
+// the Riemann solver, and its registers, out of the kernel that covers
+// almost all cells.  L1: the first-order divergences (global order, ndim >
+// 1); LP: L_P^n per scratch cell, 4 planes of R (momentum, energy); Wh: the
+// half-step fields (par_plane), doubles (FP64 path) or double-float pairs
+// (hi, lo) (mixed path).  VISC: with viscosity (a.par_visc).
+template <class R, bool SHELL, bool VISC>
+__global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *LP,
+                                                    double *Wh)
+{
+    const Where w = locate(gt);
+    const DevPatch P = a.patches[w.patch];
+    int x[3];
+    if constexpr (SHELL) {
+        const int t = w.b * BLOCK + threadIdx.x;
+        if (t >= par_shell_cells(P.n, a.ndim)) return;
+        par_shell_coords(P, a.ndim, t, x);
+    } else {
+        const Tile tl(w.xw);
+        const int T0 = (P.n[0] + tl.xw - 1) / tl.xw, T1 = (P.n[1] + tl.rows - 1) / tl.rows;
+        x[0] = (w.b % T0) * tl.xw + tl.tx();
+        x[1] = ((w.b / T0) % T1) * tl.rows + tl.ty();
+        x[2] = w.b / (T0 * T1);
+        if (x[0] >= P.n[0] || x[1] >= P.n[1] || x[2] >= P.n[2]) return;
+    }
+    const int cl = lcell(P, x[0], x[1], x[2]);
+    const long long S = a.sstride;
+    const long long c = P.soff + cl;
+    // L_P^n from the primitive fields of U^n (T = p / rho)
+    auto get = [&](int f, long long i) -> R { return f == 4 ? Vs[4 * S + i] / Vs[i] : Vs[f * S + i]; };
+    auto dif = [&](int f, long long i, long long j) -> R { return get(f, i) - get(f, j); };
+    R lp[4];
+    par_lp<R, VISC>(a, P, c, get, dif, lp, [](int, const R (&)[4], const R (&)[4]) {});
+    LP[3 * S + c] = lp[3];
+    if constexpr (VISC) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) LP[q * S + c] = lp[q];
+    }
+    // the cell-centred half-step state and its fields
+    const R gam = pgam<R>(a), ch = pch<R>(a.sp);
+    R s[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) s[q] = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= a.ndim) continue;
+        if (!SHELL || (a.ndim > 1 && x[d] >= 0 && x[d] < P.n[d])) {  // formed by the first-order stage
+            const R *Ld = L1 + (long long)d * NV * S + c;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s[q] += Ld[q * S];
+        } else if constexpr (SHELL) {
+            if (d == 0)
+                par_div1<R, 0>(a, P, Vs, c, gam, ch, s);
+            else if (d == 1)
+                par_div1<R, 1>(a, P, Vs, c, gam, ch, s);
+            else
+                par_div1<R, 2>(a, P, Vs, c, gam, ch, s);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (VISC || q == 3) s[1 + q] += lp[q];
+    const long long gi = P.base + cl;
+    if constexpr (sizeof(R) == 8) {
+        const double hdt = 0.5 * a.sp->dt;
+        double U[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) U[q] = a.U[q * a.ustride + gi] + hdt * s[q];
+        const double rho = U[0];
+        const double m2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
+        const double b2 = U[5] * U[5] + U[6] * U[6] + U[7] * U[7];
+        const double p = (a.gam - 1.0) * (U[4] - 0.5 * m2 / rho - 0.5 * b2);
+        const unsigned int f = state_flags(rho, p);
+        if (f) atomicOr(a.status, f);
+        Wh[c] = p / rho;
+        if constexpr (VISC) {
+            Wh[S + c] = rho;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Wh[(2 + q) * S + c] = U[1 + q] / rho;
+        }
+    } else {
+        // double-float (no FP64-pipe instruction): U^(n+1/2) = U^n + (dt/2) s
+        // with the product exact, then p, T = p / rho and v = m / rho to
+        // ~2^-44; stored as float pairs (hi, lo)
+        const float hdt = 0.5f * a.sp->dtf;
+        df U[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) U[q] = df_add(df_split(a.U[q * a.ustride + gi]), two_prod(hdt, s[q]));
+        const df m2 = df_add(df_add(df_sqr(U[1]), df_sqr(U[2])), df_sqr(U[3]));
+        const df b2 = df_add(df_add(df_sqr(U[5]), df_sqr(U[6])), df_sqr(U[7]));
+        const df ke = df_scale(df_div(m2, U[0]), 0.5f);
+        const df eint = df_add(df_add(U[4], df_neg(ke)), df_neg(df_scale(b2, 0.5f)));
+        const df p = df_mul(eint, df{a.gm1f, a.gm1lo});
+        const df T = df_div(p, U[0]);
+        unsigned int f = 0;
+        if (!(U[0].hi > 0.0f) || !(p.hi > 0.0f)) f |= ST_NEG;
+        if (!isfinite(U[0].hi) || !isfinite(p.hi)) f |= ST_NAN;
+        if (f) atomicOr(a.status, f);
+        float2 *W2 = reinterpret_cast<float2 *>(Wh);
+        W2[c] = make_float2(T.hi, T.lo);
+        if constexpr (VISC) {
+            W2[S + c] = make_float2(U[0].hi, U[0].lo);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const df v = df_div(U[1 + q], U[0]);
+                W2[(2 + q) * S + c] = make_float2(v.hi, v.lo);
+            }
+        }
+    }
+}
+
+// Flux-register windows of the face of plane `plane` normal to D (transverse
+// coordinates ca, cb in increasing dimension order): the momentum and energy
+// fluxes through it gain -Pi^(n+1/2) (Eq. fluxcorr with the parabolic flux).
+template <class R, bool VISC, int D>
+__device__ __forceinline__ void par_register(const StepArgs &a, const DevPatch &P, int patch, int plane, int ca,
+                                             int cb, const R (&pi)[4], double dt)
+{
+    const int B = window_base(a, patch, D);
+    if (B < 0) return;
+    const int w0 = window_first(a, B, plane), w1 = window_first(a, B, plane + 1);
+    if (w1 <= w0) return;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (q == 3 || VISC) register_face_var<R, D>(a, P, w0, w1, ca, cb, 1 + q, -pi[q], dt);
+}
+
+template <class R, bool VISC>
+__device__ __forceinline__ void par_register_d(const StepArgs &a, const DevPatch &P, int patch, int d, int plane,
+                                               const int (&x)[3], const R (&pi)[4], double dt)
+{
+    if (d == 0)
+        par_register<R, VISC, 0>(a, P, patch, plane, x[1], x[2], pi, dt);
+    else if (d == 1)
+        par_register<R, VISC, 1>(a, P, patch, plane, x[0], x[2], pi, dt);
+    else
+        par_register<R, VISC, 2>(a, P, patch, plane, x[0], x[1], pi, dt);
+}
+
+// U_out's momentum and energy += dt L_P^(n+1/2) on the interior cells (the
+// k_maxspeed tiling); the flux registers of the cell's lower faces (and of
+// its upper faces on the patch's last plane) gain -dt A Pi; with next !=
+// null also the CFL rate of the updated cell, Eq. (Ca) with the diffusion
+// term, folded into *next.
+template <int PHYS, class R, bool VISC>
+__global__ void __launch_bounds__(BLOCK) k_par_update(StepArgs a, GroupTable gt, const double *Wh,
+                                                      unsigned long long *next)
+{
+    const Where wh = locate(gt);
+    const DevPatch P = a.patches[wh.patch];
+    const Tile t(wh.xw);
+    const int T0 = (P.n[0] + t.xw - 1) / t.xw, T1 = (P.n[1] + t.rows - 1) / t.rows;
+    const int b = wh.b;
+    const int i = (b % T0) * t.xw + t.tx(), j = ((b / T0) % T1) * t.rows + t.ty(), k = b / (T0 * T1);
+    R m = R(0);
+    if (i < P.n[0] && j < P.n[1] && k < P.n[2]) {
+        const int cl = lcell(P, i, j, k);
+        const long long S = a.sstride;
+        const long long c = P.soff + cl;
+        const int x[3] = {i, j, k};
+        const double dt = a.sp->dt;
+        // the flux registers of the cell's lower faces, and of its upper
+        // faces on the patch's last plane
+        auto faces = [&](int d, const R (&Pm)[4], const R (&Pp)[4]) {
+            if (!a.reg) return;
+            par_register_d<R, VISC>(a, P, wh.patch, d, x[d], x, Pm, dt);
+            if (x[d] == P.n[d] - 1) par_register_d<R, VISC>(a, P, wh.patch, d, x[d] + 1, x, Pp, dt);
+        };
+        R lp[4];
+        if constexpr (sizeof(R) == 8) {
+            auto get = [&](int f, long long n) -> double { return Wh[par_plane(f) * S + n]; };
+            auto dif = [&](int f, long long n1, long long n2) -> double { return get(f, n1) - get(f, n2); };
+            par_lp<R, VISC>(a, P, c, get, dif, lp, faces);
+        } else {
+            // temperature differences of the double-float fields, exact to
+            // float; the velocity, a coefficient of a small increment, in
+            // float
+            const float2 *W2 = reinterpret_cast<const float2 *>(Wh);
+            auto get = [&](int f, long long n) -> float { return W2[par_plane(f) * S + n].x; };
+            auto dif = [&](int f, long long n1, long long n2) -> float {
+                const float2 u = W2[par_plane(f) * S + n1], v = W2[par_plane(f) * S + n2];
+                return f == 4 ? df_add(df{u.x, u.y}, df{-v.x, -v.y}).hi : u.x - v.x;
+            };
+            par_lp<R, VISC>(a, P, c, get, dif, lp, faces);
+        }
+        double *Uo = a.Uout + P.base + cl;
+        constexpr bool visc = VISC;
+        double U[NV];
+        U[4] = fma(dt, widen<R>(lp[3]), Uo[4 * a.ustride]);
+        Uo[4 * a.ustride] = U[4];
+#pragma unroll
+        for (int q = 1; q <= 3; ++q) {
+            if (visc) {
+                U[q] = fma(dt, widen<R>(lp[q - 1]), Uo[q * a.ustride]);
+                Uo[q * a.ustride] = U[q];
+            }
+        }
+        if (next) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+                if (q == 0 || q > 4 || !visc) {
+                    if (q != 4) U[q] = Uo[q * a.ustride];
+                }
+            R V[NV];
+            const unsigned int f = prim_any<PHYS, R>(U, a, V);
+            if (f) atomicOr(a.status, f);
+            m = cell_speed<PHYS, R>(V, a, P);
+            const R D = max(par_gk<R>(a) / V[0], R(4.0 / 3.0) * par_nu<R>(a));
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (d < a.ndim) m += R(2) * D * (pidx<R>(P, d) * pidx<R>(P, d));
+        }
+    }
+    if (next) block_max_to<R>(m, next);
+}
+
+} // namespace ctu

@@ -53,27 +53,30 @@ def test_floor_config_validation_without_gpu():
     assert st == ctu.STATUS.index("CTU_EUNSUPPORTED")
 
 
-def test_conduction_config_validation_without_gpu():
-    """Host-side validation of thermal conduction returns before any CUDA
-    call: a negative, infinite or NaN conductivity is CTU_EINVAL; conduction
-    outside ideal MHD with PPM or MC-linear, HLLD, trace modes ALL or UPWIND,
+def test_parabolic_config_validation_without_gpu():
+    """Host-side validation of the parabolic terms returns before any CUDA
+    call: a negative, infinite or NaN conductivity or viscosity is
+    CTU_EINVAL; either term outside ideal MHD with PPM or MC-linear, HLLD, trace modes ALL or UPWIND,
     no hybrid integration and FP64 or CTU_MIXED is CTU_EUNSUPPORTED, and so is
-    the allocation-free step with conduction."""
+    the allocation-free step with either."""
     import ctypes
     from paper_1110_0740_gb300 import ctu
     L = ctu._lib()
     h = ctypes.c_void_p()
     for k in (-1e-3, float("inf"), float("nan")):
-        cfg = ctu.make_config(kappa=k)
-        assert L.ctu_init(ctypes.byref(cfg), ctypes.byref(h)) == ctu.STATUS.index("CTU_EINVAL")
+        for kw in (dict(kappa=k), dict(nu=k)):
+            cfg = ctu.make_config(**kw)
+            assert L.ctu_init(ctypes.byref(cfg), ctypes.byref(h)) == ctu.STATUS.index("CTU_EINVAL")
     bad = (dict(recon=ctu.CTU_WENO3), dict(recon=ctu.CTU_LINEAR_MINMOD), dict(trace_mode=ctu.CTU_TRACE_CENTER),
            dict(riemann=ctu.CTU_HLLC), dict(shock=(5.0, 0)), dict(precision=ctu.CTU_MIXED_IFACE64),
            dict(physics=ctu.CTU_SRMHD, predictor=ctu.CTU_MUSCL_HANCOCK, riemann=ctu.CTU_HLL,
                 recon=ctu.CTU_LINEAR_MC, gamma=4.0 / 3.0))
     for kw in bad:
-        cfg = ctu.make_config(kappa=0.01, **kw)
-        assert L.ctu_init(ctypes.byref(cfg), ctypes.byref(h)) == ctu.STATUS.index("CTU_EUNSUPPORTED"), kw
-    cfg = ctu.make_config(kappa=0.01)
+        for par in (dict(kappa=0.01), dict(nu=0.01)):
+            cfg = ctu.make_config(**par, **kw)
+            assert L.ctu_init(ctypes.byref(cfg), ctypes.byref(h)) == ctu.STATUS.index("CTU_EUNSUPPORTED"), kw
     patches = ctu.make_patches([([8, 8, 8], [0.1] * 3, 0)])
-    st = L.ctu_step_noalloc(ctypes.byref(cfg), 16, 32, 4096, patches, 1, 48, 0, 0)
-    assert st == ctu.STATUS.index("CTU_EUNSUPPORTED")
+    for par in (dict(kappa=0.01), dict(nu=0.01)):
+        cfg = ctu.make_config(**par)
+        st = L.ctu_step_noalloc(ctypes.byref(cfg), 16, 32, 4096, patches, 1, 48, 0, 0)
+        assert st == ctu.STATUS.index("CTU_EUNSUPPORTED")

@@ -1,9 +1,9 @@
-"""Thermal conduction (the parabolic term of the CTU step) on the GPU against
-the oracle: 3-D blast with PPM, 2-D turbulence with MC-linear and the 1-D
-linear mode, float64 (relative L1 1e-11) and mixed (the float tracing bar of
-the plain step); a ragged batch of patches in one call; the CFL rate with
-its diffusion term (ctu_dt and the step's next dt); flux registers with the
-parabolic energy flux."""
+"""The parabolic terms of the CTU step, thermal conduction and viscosity, on
+the GPU against the oracle: 3-D blast with PPM, 2-D turbulence with
+MC-linear and 1-D diffusion-dominated cases, float64 (relative L1 1e-11) and
+mixed (the float tracing bar of the plain step); a ragged batch of patches
+in one call; the CFL rate with its diffusion term (ctu_dt and the step's
+next dt); flux registers with the parabolic momentum and energy fluxes."""
 import numpy as np
 import pytest
 
@@ -21,19 +21,20 @@ def _dev():
     return torch.device("cuda:0")
 
 
-@pytest.mark.parametrize("trace_mode", [0, 1])
-def test_conduction_3d_blast_ppm(trace_mode):
+@pytest.mark.parametrize("trace_mode,kappa,nu", [(0, 0.01, 0.0), (1, 0.01, 0.0), (0, 0.0, 0.01), (1, 0.005, 0.005)])
+def test_parabolic_3d_blast_ppm(trace_mode, kappa, nu):
     n = [24, 24, 24]
     U0 = W.mhd_blast_3d(24, seed=31)
     dx = [1.0 / 24] * 3
-    kappa = 0.01
-    ref, od = oracle_run(U0, n, 3, dx, 4, 0.3, recon=1, trace_mode=trace_mode, kappa=kappa)
+    ref, od = oracle_run(U0, n, 3, dx, 4, 0.3, recon=1, trace_mode=trace_mode, kappa=kappa, nu=nu)
     plain, _ = oracle_run(U0, n, 3, dx, 4, 0.3, recon=1, trace_mode=trace_mode)
     R = O.interior(ref, n, 3)
-    # the conduction changes the energy well above the tolerances below
-    assert np.abs(R[4] - O.interior(plain, n, 3)[4]).sum() > 1e-3 * np.abs(R[4]).sum()
+    # the parabolic terms change the state well above the tolerances below
+    q = 4 if kappa else 1
+    assert np.abs(R[q] - O.interior(plain, n, 3)[q]).sum() > 1e-3 * np.abs(R[q]).sum()
     for prec, tol in ((0, TOL64), (1, 2e-5)):
-        got, gd, st = gpu_run(U0, n, 3, dx, 4, 0.3, precision=prec, recon=1, trace_mode=trace_mode, kappa=kappa)
+        got, gd, st = gpu_run(U0, n, 3, dx, 4, 0.3, precision=prec, recon=1, trace_mode=trace_mode, kappa=kappa,
+                              nu=nu)
         assert st == 0
         e = l1rel(O.interior(got, n, 3), R, od[-1][1])
         assert np.all(e <= tol), (prec, e)
@@ -41,15 +42,15 @@ def test_conduction_3d_blast_ppm(trace_mode):
             assert np.allclose(np.array(gd), np.array(od), rtol=1e-13, atol=0)
 
 
-def test_conduction_2d_turbulence_mc():
+@pytest.mark.parametrize("kappa,nu", [(0.02, 0.0), (0.0, 0.01), (0.01, 0.01)])
+def test_parabolic_2d_turbulence_mc(kappa, nu):
     n = [48, 48, 1]
     U0 = W.mhd_turb_2d(48, seed=32)
     dx = [1.0 / 48] * 2
-    kappa = 0.02
-    ref, od = oracle_run(U0, n, 2, dx, 10, 0.4, recon=0, kappa=kappa)
+    ref, od = oracle_run(U0, n, 2, dx, 10, 0.4, recon=0, kappa=kappa, nu=nu)
     R = O.interior(ref, n, 2)
     for prec, tol in ((0, TOL64), (1, 1e-4)):
-        got, _, st = gpu_run(U0, n, 2, dx, 10, 0.4, precision=prec, recon=0, kappa=kappa)
+        got, _, st = gpu_run(U0, n, 2, dx, 10, 0.4, precision=prec, recon=0, kappa=kappa, nu=nu)
         assert st == 0
         G = O.interior(got, n, 2)
         assert not np.any(G[3]) and not np.any(G[7])
@@ -57,9 +58,10 @@ def test_conduction_2d_turbulence_mc():
         assert np.all(e <= tol), (prec, e)
 
 
-def test_conduction_1d_diffusion_dominated():
-    """1-D, a density wave on a moving gas in the regime where the diffusion
-    term sets dt (oracle pins: the linear thermal mode)."""
+@pytest.mark.parametrize("kappa,nu", [(0.5, 0.0), (0.0, 0.3), (0.2, 0.2)])
+def test_parabolic_1d_diffusion_dominated(kappa, nu):
+    """1-D, a density wave with a transverse shear on a moving gas, in the
+    regime where the diffusion term sets dt (oracle pins: the linear modes)."""
     N = 64
     n = [N, 1, 1]
     shp = O.shape(n, 1)
@@ -67,23 +69,24 @@ def test_conduction_1d_diffusion_dominated():
     rho = 1.0 + 0.2 * np.cos(2 * np.pi * x)
     z = np.zeros_like(rho)
     U0 = np.zeros(shp)
-    U0[:, 0, 0] = W.ideal_cons([rho, z + 0.3, z, z, z + 1.0, z + 0.4, z + 0.2, z, z], 5.0 / 3.0)
+    U0[:, 0, 0] = W.ideal_cons([rho, z + 0.3, 0.1 * np.sin(2 * np.pi * x), z, z + 1.0, z + 0.4, z + 0.2, z, z],
+                               5.0 / 3.0)
     dx = [1.0 / N]
-    kappa = 0.5
-    ref, od = oracle_run(U0, n, 1, dx, 30, 0.4, recon=1, kappa=kappa)
+    ref, od = oracle_run(U0, n, 1, dx, 30, 0.4, recon=1, kappa=kappa, nu=nu)
     R = O.interior(ref, n, 1)
     for prec, tol in ((0, TOL64), (1, 2e-5)):
-        got, gd, st = gpu_run(U0, n, 1, dx, 30, 0.4, precision=prec, recon=1, kappa=kappa)
+        got, gd, st = gpu_run(U0, n, 1, dx, 30, 0.4, precision=prec, recon=1, kappa=kappa, nu=nu)
         assert st == 0
         e = l1rel(O.interior(got, n, 1), R, od[-1][1], group_floor=True)
         assert np.all(e <= tol), (prec, e)
     # the diffusion term sets dt here
     m_h = O.mhd_max_speed(U0, n, 1, dx)
-    m = O.mhd_max_rate(U0, n, 1, dx, 5.0 / 3.0, kappa)
+    m = O.mhd_max_rate(U0, n, 1, dx, 5.0 / 3.0, kappa, nu)
     assert m > 3 * m_h
 
 
-def test_conduction_batch_of_uneven_patches():
+@pytest.mark.parametrize("kappa,nu", [(0.004, 0.0), (0.002, 0.003)])
+def test_parabolic_batch_of_uneven_patches(kappa, nu):
     """Four patches of different shapes and cell widths in one call, each
     against the oracle run patch by patch with the batch's dt."""
     import torch
@@ -105,28 +108,27 @@ def test_conduction_batch_of_uneven_patches():
     dev = _dev()
     U = torch.from_numpy(pool).to(dev)
     Uo = torch.zeros_like(U)
-    kappa = 0.004
-    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_FP64, cfl=0.3, kappa=kappa))
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_FP64, cfl=0.3, kappa=kappa, nu=nu))
     patches = ctu.make_patches([(n, dx, b) for n, dx, b in zip(shapes, dxs, bases)])
     dtch = torch.zeros(2, dtype=torch.float64, device=dev)
     ctx.dt(U, stride, patches, dtch)
     ctx.step(U, Uo, stride, patches, dtch)
     assert ctx.status_sync() == 0
     dt, ch = dtch.cpu().tolist()
-    m = max(O.mhd_max_rate(A, list(n), 3, list(dx), 5.0 / 3.0, kappa) for A, n, dx in zip(arrays, shapes, dxs))
+    m = max(O.mhd_max_rate(A, list(n), 3, list(dx), 5.0 / 3.0, kappa, nu) for A, n, dx in zip(arrays, shapes, dxs))
     dt_ref = 0.3 / m
     assert abs(dt - dt_ref) <= 1e-13 * dt_ref
     out = Uo.cpu().numpy()
     for A, n, dx, b in zip(arrays, shapes, dxs, bases):
-        R, bad = O.mhd_step(A, list(n), 3, list(dx), dt, ch, recon=1, kappa=kappa)
+        R, bad = O.mhd_step(A, list(n), 3, list(dx), dt, ch, recon=1, kappa=kappa, nu=nu)
         assert bad == 0
         G = out[:, b:b + A[0].size].reshape(A.shape)
         e = l1rel(O.interior(G, list(n), 3), O.interior(R, list(n), 3), ch)
         assert np.all(e <= TOL64), (n, e)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_conduction_next_dt_matches_ctu_dt(prec):
+@pytest.mark.parametrize("prec,nu", [(0, 0.0), (1, 0.0), (0, 0.03), (1, 0.03)])
+def test_parabolic_next_dt_matches_ctu_dt(prec, nu):
     import torch
     from paper_1110_0740_gb300 import ctu
     n = [20, 12, 16]
@@ -136,7 +138,7 @@ def test_conduction_next_dt_matches_ctu_dt(prec):
     dev = _dev()
     U = torch.from_numpy(U0.reshape(9, -1).copy()).to(dev)
     Ua, Ub = torch.zeros_like(U), torch.zeros_like(U)
-    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=0.05))
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=0.05, nu=nu))
     p = ctu.make_patches([(n, [1 / 20, 1 / 12, 1 / 16], 0)])
     d0 = torch.zeros(2, dtype=torch.float64, device=dev)
     d1 = torch.zeros_like(d0)
@@ -151,16 +153,16 @@ def test_conduction_next_dt_matches_ctu_dt(prec):
     assert np.allclose(a, b, rtol=1e-13 if prec == 0 else 1e-6, atol=0), (a, b)
     # and against the oracle's rate (float64)
     if prec == 0:
-        m = O.mhd_max_rate(U0, n, 3, [1 / 20, 1 / 12, 1 / 16], 5.0 / 3.0, 0.05)
+        m = O.mhd_max_rate(U0, n, 3, [1 / 20, 1 / 12, 1 / 16], 5.0 / 3.0, 0.05, nu)
         assert abs(d0.cpu().numpy()[0] - 0.3 / m) <= 1e-14 * 0.3 / m
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_conduction_flux_registers(prec):
+@pytest.mark.parametrize("prec,nu", [(0, 0.0), (1, 0.0), (0, 0.02), (1, 0.02)])
+def test_parabolic_flux_registers(prec, nu):
     """Register windows on every boundary face and on an interior plane of a
-    3-D patch, two steps accumulated: with conduction the energy entries
-    carry F_E - Pi_E^(n+1/2), as in the oracle (which conserves two levels
-    with them, see the oracle pins)."""
+    3-D patch, two steps accumulated: with the parabolic terms the momentum
+    and energy entries carry F - Pi^(n+1/2), as in the oracle (which
+    conserves two levels with them, see the oracle pins)."""
     import torch
     from paper_1110_0740_gb300 import ctu
     n = [12, 10, 8]
@@ -180,7 +182,7 @@ def test_conduction_flux_registers(prec):
     U = torch.from_numpy(U0.reshape(9, -1).copy()).to(dev)
     Uo = torch.zeros_like(U)
     reg = torch.zeros(off, dtype=torch.float64, device=dev)
-    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=kappa))
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=kappa, nu=nu))
     p = ctu.make_patches([(n, dx, 0)])
     ctx.flux_registers(reg, windows)
     dtch = torch.zeros(2, dtype=torch.float64, device=dev)
@@ -190,8 +192,8 @@ def test_conduction_flux_registers(prec):
     assert ctx.status_sync() == 0
     dt, ch = dtch.cpu().tolist()
     ref = np.zeros(off)
-    R, bad = O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref, kappa=kappa)
-    O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref, kappa=kappa)
+    R, bad = O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref, kappa=kappa, nu=nu)
+    O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref, kappa=kappa, nu=nu)
     assert bad == 0
     got = reg.cpu().numpy()
     # the energy entries differ from the hyperbolic-only registers
