@@ -844,12 +844,12 @@ void or_mhd_shock_flags(const double *U, int nx, int ny, int nz, int ndim, doubl
 /* Eq. (Ca): max over interior cells of
  *     max_d (|v_d| + c_f,d)/dx_d + sum_d 2 D / dx_d^2,
  * with D the largest diffusion coefficient of the cell:
- * max((Gamma - 1) kappa / rho, (4/3) nu), the diffusivities of the temperature
- * under conduction and of the longitudinal velocity under viscosity (0 for
- * kappa = nu = 0).  The caller sets dt = C_a / max and c_h = max * min_d dx_d
+ * max((Gamma - 1) kappa / rho, (4/3) nu, eta), the diffusivities of the
+ * temperature under conduction, of the longitudinal velocity under viscosity
+ * and of B under resistivity (0 when all three are 0).  The caller sets dt = C_a / max and c_h = max * min_d dx_d
  * (= C_a min_d dx_d / dt). */
 double or_mhd_max_rate_par(const double *U, int nx, int ny, int nz, int ndim,
-                           double dx, double dy, double dz, double gam, double kappa, double nu)
+                           double dx, double dy, double dz, double gam, double kappa, double nu, double eta)
 {
     grid_t G;
     double h[3] = {dx, dy, dz}, m = 0.0;
@@ -871,8 +871,8 @@ double or_mhd_max_rate_par(const double *U, int nx, int ny, int nz, int ndim,
                     if (sd > s)
                         s = sd;
                 }
-                if (kappa > 0.0 || nu > 0.0) {
-                    double D = fmax((gam - 1.0) * kappa / V[0], 4.0 / 3.0 * nu);
+                if (kappa > 0.0 || nu > 0.0 || eta > 0.0) {
+                    double D = fmax(fmax((gam - 1.0) * kappa / V[0], 4.0 / 3.0 * nu), eta);
                     for (d = 0; d < ndim; d++)
                         s += 2.0 * D / (h[d] * h[d]);
                 }
@@ -886,7 +886,7 @@ double or_mhd_max_rate_par(const double *U, int nx, int ny, int nz, int ndim,
 double or_mhd_max_rate(const double *U, int nx, int ny, int nz, int ndim,
                        double dx, double dy, double dz, double gam, double kappa)
 {
-    return or_mhd_max_rate_par(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, 0.0);
+    return or_mhd_max_rate_par(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, 0.0, 0.0);
 }
 
 /* max over interior cells of max_d (|v_d| + c_f,d)/dx_d (Eq. Ca without
@@ -894,7 +894,7 @@ double or_mhd_max_rate(const double *U, int nx, int ny, int nz, int ndim,
 double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
                         double dx, double dy, double dz, double gam)
 {
-    return or_mhd_max_rate_par(U, nx, ny, nz, ndim, dx, dy, dz, gam, 0.0, 0.0);
+    return or_mhd_max_rate_par(U, nx, ny, nz, ndim, dx, dy, dz, gam, 0.0, 0.0, 0.0);
 }
 
 /* ------------------------------------------------------------------ */
@@ -902,8 +902,8 @@ double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
 /* ------------------------------------------------------------------ */
 
 /* The parabolic fluxes of Section 2.1.1 on a Cartesian grid, from the
- * cell-centred fields W = (rho, v_x, v_y, v_z, T) (five arrays of ncell
- * values, T = p / rho):
+ * cell-centred fields W = (rho, v_x, v_y, v_z, T, B_x, B_y, B_z) (eight
+ * arrays of ncell values, T = p / rho):
  *   - classical isotropic thermal conduction, the heat flux of Eq. (tc_flux)
  *     in the limit q -> infinity with kappa_par = kappa_perp = kappa:
  *     Pi_E += kappa dT/dx_d;
@@ -920,10 +920,13 @@ double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
  *               / (4 dx_t)  for an active t != d (0 on an inactive axis),
  *     rho_f = (rho(c) + rho(c + e_d)) / 2,
  *     v_f = (rho v (c) + rho v (c + e_d)) / (rho(c) + rho(c + e_d)),
- * the last two being the density and velocity of the mean conserved state.
- * Pi[1..3] receive the momentum fluxes and Pi[4] the energy flux. */
-static void parabolic_face(const grid_t *G, const double *W, const double *h, double kappa, double nu, long id,
-                           int d, double *Pi)
+ * the last two being the density and velocity of the mean conserved state;
+ *   - resistivity with constant eta (the induction term -curl(eta J),
+ *     J = curl B, and the energy flux -eta J x B of Section 2.1.1).
+ * Pi[1..3] receive the momentum fluxes, Pi[4] the energy flux and Pi[5..7]
+ * the fluxes of B.  W holds (rho, v_x, v_y, v_z, T, B_x, B_y, B_z). */
+static void parabolic_face(const grid_t *G, const double *W, const double *h, double kappa, double nu, double eta,
+                           long id, int d, double *Pi)
 {
     const long nc = G->ncell, st = dstride(G, d), ip = id + st;
     int q;
@@ -957,13 +960,39 @@ static void parabolic_face(const grid_t *G, const double *W, const double *h, do
             Pi[4] += vf[i] * tau;
         }
     }
+    if (eta > 0.0) {
+        /* resistivity: -curl(eta J) = div(eta (grad B^T - grad B)) for
+         * constant eta, so the flux of B_i along d is eta (dB_i/dx_d -
+         * dB_d/dx_i) (zero for B_d), and the energy flux -eta J x B along d
+         * is sum_i B_i,f times it, B_f the mean of the two cells */
+        double gb[3][3];
+        int i, t;
+        for (t = 0; t < 3; t++)
+            for (i = 0; i < 3; i++) {
+                const double *B = W + (5 + i) * nc;
+                if (t == d) {
+                    gb[t][i] = (B[ip] - B[id]) / h[d];
+                } else if (t < G->ndim) {
+                    const long s2 = dstride(G, t);
+                    gb[t][i] = (B[id + s2] - B[id - s2] + B[ip + s2] - B[ip - s2]) / (4.0 * h[t]);
+                } else {
+                    gb[t][i] = 0.0;
+                }
+            }
+        for (i = 0; i < 3; i++) {
+            double f = eta * (gb[d][i] - gb[i][d]);
+            double bf = 0.5 * (W[(5 + i) * nc + id] + W[(5 + i) * nc + ip]);
+            Pi[5 + i] += f;
+            Pi[4] += bf * f;
+        }
+    }
 }
 
 /* L_P = sum_d (Pi_(d,+) - Pi_(d,-)) / dx_d (Eq. incrementop_par, Cartesian)
- * for the momentum and the energy, LP[q * ncell + id] (q = 1..4), on the
+ * for the momentum, the energy and B, LP[q * ncell + id] (q = 1..7), on the
  * cells lo <= c <= hi; the other entries are left as they are. */
-static void parabolic_lp(const grid_t *G, const double *W, const double *h, double kappa, double nu, const int *lo,
-                         const int *hi, double *LP)
+static void parabolic_lp(const grid_t *G, const double *W, const double *h, double kappa, double nu, double eta,
+                         const int *lo, const int *hi, double *LP)
 {
     int c[3], d, q;
     for (c[2] = lo[2]; c[2] <= hi[2]; c[2]++)
@@ -972,18 +1001,18 @@ static void parabolic_lp(const grid_t *G, const double *W, const double *h, doub
                 long id = cidx(G, c);
                 double s[NVAR] = {0}, Pp[NVAR], Pm[NVAR];
                 for (d = 0; d < G->ndim; d++) {
-                    parabolic_face(G, W, h, kappa, nu, id, d, Pp);
-                    parabolic_face(G, W, h, kappa, nu, id - dstride(G, d), d, Pm);
-                    for (q = 1; q <= 4; q++)
+                    parabolic_face(G, W, h, kappa, nu, eta, id, d, Pp);
+                    parabolic_face(G, W, h, kappa, nu, eta, id - dstride(G, d), d, Pm);
+                    for (q = 1; q <= 7; q++)
                         s[q] += (Pp[q] - Pm[q]) / h[d];
                 }
-                for (q = 1; q <= 4; q++)
+                for (q = 1; q <= 7; q++)
                     LP[q * G->ncell + id] = s[q];
             }
 }
 
-/* The fields W = (rho, v, T) of every ghosted cell of U; returns the number
- * of cells with rho <= 0 or p <= 0. */
+/* The fields W = (rho, v, T, B) of every ghosted cell of U; returns the
+ * number of cells with rho <= 0 or p <= 0. */
 static int parabolic_fields(const grid_t *G, const double *U, double gam, double *W)
 {
     int bad = 0, q;
@@ -997,15 +1026,18 @@ static int parabolic_fields(const grid_t *G, const double *U, double gam, double
         for (q = 1; q <= 3; q++)
             W[q * nc + id] = Vc[q];
         W[4 * nc + id] = Vc[4] / Vc[0];
+        for (q = 5; q <= 7; q++)
+            W[q * nc + id] = Vc[q];
     }
     return bad;
 }
 
-/* L_P of conduction and viscosity on the interior cells of a ghost-filled
- * patch: LP[q * ncell + id] for the momentum (q = 1..3) and the energy
- * (q = 4), ghosted layout (the other entries are 0). */
+/* L_P of conduction, viscosity and resistivity on the interior cells of a
+ * ghost-filled patch: LP[q * ncell + id] for the momentum (q = 1..3), the
+ * energy (q = 4) and B (q = 5..7), ghosted layout (the other entries are
+ * 0). */
 void or_mhd_parabolic(const double *U, int nx, int ny, int nz, int ndim, double dx, double dy, double dz,
-                      double gam, double kappa, double nu, double *LP)
+                      double gam, double kappa, double nu, double eta, double *LP)
 {
     grid_t G;
     double h[3] = {dx, dy, dz};
@@ -1014,10 +1046,10 @@ void or_mhd_parabolic(const double *U, int nx, int ny, int nz, int ndim, double 
     grid_init(&G, nx, ny, nz, ndim);
     for (d = 0; d < 3; d++)
         hi[d] = G.n[d] - 1;
-    W = (double *)malloc(sizeof(double) * 5 * G.ncell);
+    W = (double *)malloc(sizeof(double) * 8 * G.ncell);
     parabolic_fields(&G, U, gam, W);
     memset(LP, 0, sizeof(double) * NVAR * G.ncell);
-    parabolic_lp(&G, W, h, kappa, nu, lo, hi, LP);
+    parabolic_lp(&G, W, h, kappa, nu, eta, lo, hi, LP);
     free(W);
 }
 
@@ -1029,7 +1061,7 @@ void or_mhd_conduction(const double *U, int nx, int ny, int nz, int ndim, double
     double *A;
     grid_init(&G, nx, ny, nz, ndim);
     A = (double *)malloc(sizeof(double) * NVAR * G.ncell);
-    or_mhd_parabolic(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, 0.0, A);
+    or_mhd_parabolic(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, 0.0, 0.0, A);
     memcpy(LP, A + 4 * G.ncell, sizeof(double) * G.ncell);
     free(A);
 }
@@ -1078,8 +1110,8 @@ static int face_riemann(const double *VL, const double *VR, double gam, double c
 }
 
 /* The step of or_mhd_step_ex, or_mhd_step_tc and or_mhd_step_par: with
- * kappa > 0 or nu > 0, conduction and viscosity (parabolic_lp) enter as the
- * parabolic term of Section 3.1 (Pi != 0): L_P^n from the cell-centred U^n
+ * kappa, nu or eta > 0, conduction, viscosity and resistivity (parabolic_lp)
+ * enter as the parabolic term of Section 3.1 (Pi != 0): L_P^n from the cell-centred U^n
  * joins the transverse increments of every direction's predictor (Eq.
  * transv), and the update adds L_P^(n+1/2) from the cell-centred
  * U^(n+1/2) = U^n + dt/2 sum_d (L_(H,d)^n + L_(P,d)^n), L_H^n the first-order
@@ -1088,9 +1120,9 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                      double dx, double dy, double dz, double dt, double ch,
                      double gam, double glm_alpha, int recon, int upwind,
                      const long *win, const double *wgt, int nwin, double *reg,
-                     int solver, int shock, double eps_q, int qkind, double kappa, double nu)
+                     int solver, int shock, double eps_q, int qkind, double kappa, double nu, double eta)
 {
-    const int par = kappa > 0.0 || nu > 0.0;
+    const int par = kappa > 0.0 || nu > 0.0 || eta > 0.0;
     unsigned char *flags = NULL;
     grid_t G;
     double h[3] = {dx, dy, dz};
@@ -1123,15 +1155,15 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
         ring_hi[d] = d < ndim ? G.n[d] : 0;
     }
     if (par) {
-        /* L_P^n on the ring box, from W^n = (rho, v, p / rho)^n */
-        Wn = (double *)malloc(sizeof(double) * 5 * nc);
+        /* L_P^n on the ring box, from W^n = (rho, v, p / rho, B)^n */
+        Wn = (double *)malloc(sizeof(double) * 8 * nc);
         LPn = (double *)calloc((size_t)NVAR * nc, sizeof(double));
         for (long id = 0; id < nc; id++) {
-            for (q = 0; q < 4; q++)
+            for (q = 0; q < 8; q++)
                 Wn[q * nc + id] = V[q * nc + id];
             Wn[4 * nc + id] = V[4 * nc + id] / V[id];
         }
-        parabolic_lp(&G, Wn, h, kappa, nu, ring_lo, ring_hi, LPn);
+        parabolic_lp(&G, Wn, h, kappa, nu, eta, ring_lo, ring_hi, LPn);
     }
 
     /* 2. first-order Godunov fluxes F^n_d = R(U_c, U_(c+e_d)) on the faces the
@@ -1205,7 +1237,7 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                     }
                     /* the parabolic term of every direction, Eq. (transv) */
                     if (LPn)
-                        for (q = 1; q <= 4; q++)
+                        for (q = 1; q <= 7; q++)
                             T[q] += LPn[q * nc + id];
                     or_mhd_prim2cons(Vp, gam, Ul);
                     for (q = 0; q < NVAR; q++)
@@ -1256,7 +1288,7 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
      *     then L_P^(n+1/2) on the interior */
     if (par) {
         int ilo[3] = {0, 0, 0}, ihi[3];
-        Wh = (double *)calloc((size_t)5 * nc, sizeof(double));
+        Wh = (double *)calloc((size_t)8 * nc, sizeof(double));
         LPh = (double *)calloc((size_t)NVAR * nc, sizeof(double));
         for (c[2] = ring_lo[2]; c[2] <= ring_hi[2]; c[2]++)
             for (c[1] = ring_lo[1]; c[1] <= ring_hi[1]; c[1]++)
@@ -1271,13 +1303,13 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                         Uh[q] = U[q * nc + id] + 0.5 * dt * s;
                     }
                     bad += or_mhd_cons2prim(Uh, gam, Vh);
-                    for (q = 0; q < 4; q++)
+                    for (q = 0; q < 8; q++)
                         Wh[q * nc + id] = Vh[q];
                     Wh[4 * nc + id] = Vh[4] / Vh[0];
                 }
         for (d = 0; d < 3; d++)
             ihi[d] = G.n[d] - 1;
-        parabolic_lp(&G, Wh, h, kappa, nu, ilo, ihi, LPh);
+        parabolic_lp(&G, Wh, h, kappa, nu, eta, ilo, ihi, LPh);
     }
 
     /* 5. conservative update, Eq. (update): U + dt * (L_x + L_y + L_z) (+ L_P) */
@@ -1322,10 +1354,10 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                     id = cidx(&G, c);
                     flux = F[wd][q * nc + id];
                     /* with parabolic terms the flux through the face is
-                     * F - Pi^(n+1/2) (momentum and energy) */
-                    if (Wh && q >= 1 && q <= 4) {
+                     * F - Pi^(n+1/2) (momentum, energy and B) */
+                    if (Wh && q >= 1 && q <= 7) {
                         double Pi[NVAR];
-                        parabolic_face(&G, Wh, h, kappa, nu, id, wd, Pi);
+                        parabolic_face(&G, Wh, h, kappa, nu, eta, id, wd, Pi);
                         flux -= Pi[q];
                     }
                     reg[W[6] + (q * nb + jb) * na + ja] += wgt[w] * dt * area * flux;
@@ -1360,21 +1392,22 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
                    int solver, int shock, double eps_q, int qkind)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, 0.0, 0.0);
+                     nwin, reg, solver, shock, eps_q, qkind, 0.0, 0.0, 0.0);
 }
 
-/* or_mhd_step_ex with thermal conduction of conductivity kappa >= 0 and
- * viscosity of kinematic viscosity nu >= 0 (the parabolic terms; see
- * step_core and parabolic_face).  The flux registers take the fluxes
- * F - Pi^(n+1/2) of the momentum and the energy through their faces. */
+/* or_mhd_step_ex with thermal conduction of conductivity kappa >= 0,
+ * viscosity of kinematic viscosity nu >= 0 and resistivity eta >= 0 (the
+ * parabolic terms; see step_core and parabolic_face).  The flux registers
+ * take the fluxes F - Pi^(n+1/2) of the momentum, the energy and B through
+ * their faces. */
 int or_mhd_step_par(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
                     double dx, double dy, double dz, double dt, double ch,
                     double gam, double glm_alpha, int recon, int upwind,
                     const long *win, const double *wgt, int nwin, double *reg,
-                    int solver, int shock, double eps_q, int qkind, double kappa, double nu)
+                    int solver, int shock, double eps_q, int qkind, double kappa, double nu, double eta)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, kappa, nu);
+                     nwin, reg, solver, shock, eps_q, qkind, kappa, nu, eta);
 }
 
 /* or_mhd_step_par with conduction alone. */
@@ -1385,7 +1418,7 @@ int or_mhd_step_tc(const double *U, double *Unew, int nx, int ny, int nz, int nd
                    int solver, int shock, double eps_q, int qkind, double kappa)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, kappa, 0.0);
+                     nwin, reg, solver, shock, eps_q, qkind, kappa, 0.0, 0.0);
 }
 
 /* ------------------------------------------------------------------ */
