@@ -219,7 +219,7 @@ def run_ours(args):
         c = ctu.Ctx(ctu.make_config(ndim=3, recon=RECONS[args.recon], precision=prec, cfl=0.3,
                                     shock=(args.shock, 0) if args.shock else None,
                                     riemann=ctu.CTU_HLLC if args.riemann == "hllc" else ctu.CTU_HLLD,
-                                    kappa=args.kappa, nu=args.nu))
+                                    kappa=args.kappa, nu=args.nu, eta=args.eta))
         c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
         if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
@@ -327,7 +327,7 @@ def run_ours(args):
     roof["hbm_step"] = {"algorithmic_bytes": nbytes, "achieved_gbs": hbm_achieved,
                         "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
                         "peak_source": f"{src} hbm_gbs"}
-    if mixed and args.recon == "ppm" and not args.shock and args.riemann == "hlld" and not args.kappa and not args.nu:
+    if mixed and args.recon == "ppm" and not args.shock and args.riemann == "hlld" and not args.kappa and not args.nu and not args.eta:
         roof["precision_split"] = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
 
     # end-to-end through the public API with host buffers
@@ -406,7 +406,8 @@ def run_ours(args):
                            + (f"; hybrid integration (shock flags, eps_q {args.shock})" if args.shock else "")
                            + ("; HLLC in place of HLLD" if args.riemann == "hllc" else "")
                            + (f"; thermal conduction, kappa {args.kappa}" if args.kappa else "")
-                           + (f"; viscosity, nu {args.nu}" if args.nu else ""),
+                           + (f"; viscosity, nu {args.nu}" if args.nu else "")
+                           + (f"; resistivity, eta {args.eta}" if args.eta else ""),
                            "recon": args.recon, "shock_eps": args.shock or None,
                            "cells_per_gpu": cells, "patches_per_gpu": 1,
                            "precision": args.precision, "l2_flush": "inputs (1.3 GB) > L2",
@@ -934,6 +935,8 @@ def main():
                     help="blast: thermal conduction with this conductivity (0 = off)")
     ap.add_argument("--nu", type=float, default=0.0,
                     help="blast: viscosity with this kinematic viscosity (0 = off)")
+    ap.add_argument("--eta", type=float, default=0.0,
+                    help="blast: resistivity with this magnetic diffusivity (0 = off)")
     ap.add_argument("--shock", type=float, default=0.0,
                     help="blast: the hybrid integration with this shock threshold (thermal pressure; 0 = off)")
     ap.add_argument("--recon", default="ppm", choices=sorted(RECONS),

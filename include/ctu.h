@@ -185,6 +185,14 @@ typedef struct {
      * and the CFL diffusion coefficient becomes
      * D = max((Gamma-1) kappa / rho, (4/3) nu).  Same combinations as kappa. */
     double nu;
+    /* Resistivity, the third parabolic term: eta >= 0 constant, the
+     * induction term -curl(eta J), J = curl B, i.e. the flux of B_i along d is
+     * eta (dB_i/dx_d - dB_d/dx_i), with the energy flux -eta J x B (B_f . that
+     * flux, B_f the mean of the two cells); 0 = off.  Derivatives as for nu;
+     * it enters the predictors, the update and the registers as kappa does,
+     * and D = max((Gamma-1) kappa / rho, (4/3) nu, eta).  Same combinations as
+     * kappa. */
+    double eta;
 } ctu_config;
 
 typedef struct {
@@ -222,7 +230,7 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out);
 
 /* CFL time step, Eq. (Ca): M = max over the interior cells of all patches of
  * max_d (|v_d| + c_f,d) / dx_d (+ sum_d 2 D / dx_d^2 with the parabolic
- * terms, D = max((Gamma-1) kappa / rho, (4/3) nu)); then dt = cfl / M and
+ * terms, D = max((Gamma-1) kappa / rho, (4/3) nu, eta)); then dt = cfl / M and
  * c_h = M * min dx (the GLM speed, equal to cfl * min dx / dt).  Writes {dt, c_h} to the device
  * array d_dt_ch[2]; if h_dt_ch is non-null it also copies them there and
  * synchronises the stream.  U: device pool; patches: host array. */

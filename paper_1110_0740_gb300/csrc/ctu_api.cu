@@ -317,9 +317,9 @@ static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStr
 
 // Scratch layout: SCRATCH_ARRAYS planes of the working precision, then (each
 // 256-byte aligned) the shock flags of the hybrid integration (one byte per
-// scratch cell) and, with the parabolic terms, L_P^n (four words of the
-// working precision) and the half-step fields (one 8-byte plane, T; five
-// with viscosity) per scratch cell.
+// scratch cell) and, with the parabolic terms, L_P^n (seven words of the
+// working precision) and the half-step fields (one 8-byte plane, T; eight
+// with viscosity or resistivity) per scratch cell.
 struct ScratchOffsets {
     size_t flags, lp, th, total;
 };
@@ -330,10 +330,11 @@ static ScratchOffsets scratch_offsets(const ctu_ctx *ctx)
     const size_t S = (size_t)ctx->sstride;
     ScratchOffsets o;
     o.flags = align256((size_t)SCRATCH_ARRAYS * S * elt);
-    const bool par = ctx->cfg.kappa > 0.0 || ctx->cfg.nu > 0.0;
+    const bool tensor = ctx->cfg.nu > 0.0 || ctx->cfg.eta > 0.0;
+    const bool par = ctx->cfg.kappa > 0.0 || tensor;
     o.lp = align256(o.flags + (ctx->cfg.shock_detect ? S : 0));
-    o.th = align256(o.lp + (par ? 4 * S * elt : 0));
-    o.total = o.th + (par ? (ctx->cfg.nu > 0.0 ? 5 : 1) * S * sizeof(double) : 0);
+    o.th = align256(o.lp + (par ? 7 * S * elt : 0));
+    o.total = o.th + (par ? (tensor ? 8 : 1) * S * sizeof(double) : 0);
     return o;
 }
 
@@ -374,17 +375,20 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.flags = nullptr;
     a.kappa = ctx->cfg.kappa;
     a.nu = ctx->cfg.nu;
+    a.eta = ctx->cfg.eta;
     a.kappaf = (float)ctx->cfg.kappa;
     a.nuf = (float)ctx->cfg.nu;
+    a.etaf = (float)ctx->cfg.eta;
     a.par_cond = ctx->cfg.kappa > 0.0;
     a.par_visc = ctx->cfg.nu > 0.0;
+    a.par_res = ctx->cfg.eta > 0.0;
     a.gm1lo = tm ? 0.0f : (float)((ctx->cfg.gamma - 1.0) - (double)a.gm1f);
     a.lp = nullptr;
     a.th = nullptr;
     if (ctx->scratch) {
         const ScratchOffsets o = scratch_offsets(ctx);
         if (ctx->cfg.shock_detect) a.flags = (unsigned char *)ctx->scratch + o.flags;
-        if (a.par_cond || a.par_visc) {
+        if (a.par_cond || a.par_visc || a.par_res) {
             a.lp = (const unsigned char *)ctx->scratch + o.lp;
             a.th = (double *)((unsigned char *)ctx->scratch + o.th);
         }
@@ -414,7 +418,7 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
     const bool ref = ctx->cfg.trace_mode >= CTU_TRACE_CENTER;
     const bool hyb = ctx->cfg.shock_detect != 0;
     const bool hllc = ctx->cfg.physics == CTU_MHD && ctx->cfg.riemann == CTU_HLLC;
-    const bool par = ctx->cfg.kappa > 0.0 || ctx->cfg.nu > 0.0;
+    const bool par = ctx->cfg.kappa > 0.0 || ctx->cfg.nu > 0.0 || ctx->cfg.eta > 0.0;
     li.recon = r == CTU_PPM
                    ? (par ? RECON_PPM_PAR
                           : (hllc ? RECON_PPM_HLLC : (hyb ? RECON_PPM_HYB : (ref ? RECON_PPM_REF : RECON_PPM))))
@@ -511,11 +515,12 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
             cfg->trace_mode > CTU_TRACE_UPWIND || cfg->precision == CTU_MIXED_IFACE64)
             return CTU_EUNSUPPORTED;
     }
-    if (!(cfg->kappa >= 0.0 && cfg->kappa < INFINITY) || !(cfg->nu >= 0.0 && cfg->nu < INFINITY))
+    if (!(cfg->kappa >= 0.0 && cfg->kappa < INFINITY) || !(cfg->nu >= 0.0 && cfg->nu < INFINITY) ||
+        !(cfg->eta >= 0.0 && cfg->eta < INFINITY))
         return CTU_EINVAL;
     // the parabolic terms: ideal MHD, PPM or MC-linear, HLLD, tracing without
     // or with the w_(+/-) reference, no hybrid integration, FP64 or CTU_MIXED
-    if ((cfg->kappa > 0.0 || cfg->nu > 0.0) &&
+    if ((cfg->kappa > 0.0 || cfg->nu > 0.0 || cfg->eta > 0.0) &&
         (cfg->physics != CTU_MHD || (cfg->recon != CTU_PPM && cfg->recon != CTU_LINEAR_MC) ||
          cfg->riemann != CTU_HLLD || cfg->trace_mode > CTU_TRACE_UPWIND || cfg->shock_detect ||
          cfg->precision == CTU_MIXED_IFACE64))

@@ -76,15 +76,15 @@ struct StepArgs {
     unsigned char *flags;
     double shock_eps;
     int shock_q;           // 0 thermal, 1 magnetic pressure
-    // parabolic terms (the RECON_*_PAR kernels): conductivity kappa and
-    // kinematic viscosity nu (par_cond, par_visc: nonzero when on), L_P^n per
-    // scratch cell (4 planes of the working precision: momentum, energy) and
-    // the half-step fields (planes of 8 bytes: T, then rho and v with
-    // viscosity)
-    double kappa, nu;
-    float kappaf, nuf;     // kappa, nu in float
-    float gm1lo;           // (Gamma-1) - gm1f in float: Gamma-1 as a double-float pair
-    int par_cond, par_visc;
+    // parabolic terms (the RECON_*_PAR kernels): conductivity kappa,
+    // kinematic viscosity nu and resistivity eta (par_cond, par_visc,
+    // par_res: nonzero when on), L_P^n per scratch cell (7 planes of the
+    // working precision: momentum, energy, B) and the half-step fields
+    // (planes of 8 bytes: T, then rho, v and B with viscosity or resistivity)
+    double kappa, nu, eta;
+    float kappaf, nuf, etaf;  // kappa, nu, eta in float
+    float gm1lo;              // (Gamma-1) - gm1f in float: Gamma-1 as a double-float pair
+    int par_cond, par_visc, par_res;
     const void *lp;
     double *th;
     const double *U;       // pool in
@@ -463,6 +463,10 @@ __device__ __forceinline__ unsigned int trace_cell_t(const StepArgs &a, const De
         if (a.par_visc) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) Tc[1 + q] += hd * lp[q * a.sstride];
+        }
+        if (a.par_res) {
+#pragma unroll
+            for (int q = 4; q < 7; ++q) Tc[1 + q] += hd * lp[q * a.sstride];
         }
     }
     if (PHYS == PH_MHD) {
@@ -1334,10 +1338,11 @@ __global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, GroupTable gt, u
         const unsigned int f = prim_any<PHYS, R>(U, a, V);
         if (f) atomicOr(a.status, f);
         m = cell_speed<PHYS, R>(V, a, P);
-        if (a.par_cond | a.par_visc) {  // parabolic terms: + sum_d 2 D / dx_d^2
-            // D = max((Gamma-1) kappa / rho, (4/3) nu)
-            const R D = max((sizeof(R) == 8 ? (R)((a.gam - 1.0) * a.kappa) : (R)(a.gm1f * a.kappaf)) / V[0],
-                            R(4.0 / 3.0) * (sizeof(R) == 8 ? (R)a.nu : (R)a.nuf));
+        if (a.par_cond | a.par_visc | a.par_res) {  // parabolic terms: + sum_d 2 D / dx_d^2
+            // D = max((Gamma-1) kappa / rho, (4/3) nu, eta)
+            const R D = max(max((sizeof(R) == 8 ? (R)((a.gam - 1.0) * a.kappa) : (R)(a.gm1f * a.kappaf)) / V[0],
+                                R(4.0 / 3.0) * (sizeof(R) == 8 ? (R)a.nu : (R)a.nuf)),
+                            sizeof(R) == 8 ? (R)a.eta : (R)a.etaf);
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 if (d < a.ndim) m += R(2) * D * (pidx<R>(P, d) * pidx<R>(P, d));

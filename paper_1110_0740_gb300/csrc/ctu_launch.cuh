@@ -120,8 +120,8 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     }
     if constexpr (recon_par(PPM)) {  // parabolic terms: L_P^n and the half-step fields
         CTU_MARK("par_half");
-        auto half = [&](auto visc) {
-            constexpr bool V = decltype(visc)::value;
+        auto half = [&](auto tm) {
+            constexpr int V = decltype(tm)::value;
             if (a.ndim > 1)
                 n += over_groups(
                     li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
@@ -134,10 +134,16 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
                     k_par_half<R, true, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
                 });
         };
-        if (a.par_visc)
-            half(std::true_type{});
+        // one kernel per combination of the terms beyond conduction
+        const int tm = (a.par_visc ? 1 : 0) | (a.par_res ? 2 : 0);
+        if (tm == 0)
+            half(std::integral_constant<int, 0>{});
+        else if (tm == 1)
+            half(std::integral_constant<int, 1>{});
+        else if (tm == 2)
+            half(std::integral_constant<int, 2>{});
         else
-            half(std::false_type{});
+            half(std::integral_constant<int, 3>{});
         CTU_MARK(nullptr);
     }
     // sweeps in the order z, y, x: the first writes A = L_D, the middle one
@@ -170,10 +176,15 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         n += over_groups(
             li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
             [&](const GroupTable &gt, unsigned nb) {
-                if (a.par_visc)
-                    k_par_update<PHYS, R, true><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
+                const int tm = (a.par_visc ? 1 : 0) | (a.par_res ? 2 : 0);
+                if (tm == 0)
+                    k_par_update<PHYS, R, 0><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
+                else if (tm == 1)
+                    k_par_update<PHYS, R, 1><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
+                else if (tm == 2)
+                    k_par_update<PHYS, R, 2><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
                 else
-                    k_par_update<PHYS, R, false><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
+                    k_par_update<PHYS, R, 3><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
             });
         CTU_MARK(nullptr);
     }
@@ -191,8 +202,8 @@ template <class R, int IF64> int launch_step_impl(const StepArgs &a, const Launc
 // MinMod, harmonic or Van Albada slope, or improved WENO3), with the
 // reference states of the tracing (G = 1: PPM or MC-linear), with the
 // hybrid integration (G = 2: PPM or MC-linear), with the HLLC solver
-// (G = 3: PPM or MC-linear), or with the parabolic terms, conduction and
-// viscosity (G = 4: PPM or MC-linear).
+// (G = 3: PPM or MC-linear), or with the parabolic terms, conduction,
+// viscosity and resistivity (G = 4: PPM or MC-linear).
 template <class R, int IF64, int G> int launch_step_var(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if constexpr (G == 4)  // the parabolic terms

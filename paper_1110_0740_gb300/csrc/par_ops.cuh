@@ -3,33 +3,38 @@
 // q -> infinity, kappa_par = kappa_perp = kappa), Pi_E = kappa grad T with
 // T = p / rho, and isotropic viscosity (Eq. visc_tens, constant kinematic
 // viscosity nu), tau = rho nu (grad v + grad v^T - (2/3) I div v) with the
-// momentum flux Pi_m = tau and the energy flux Pi_E += v . tau.
+// momentum flux Pi_m = tau and the energy flux Pi_E += v . tau, and
+// resistivity (constant eta), -curl(eta J) = div(eta (grad B^T - grad B)):
+// the flux of B_i along d is eta (dB_i/dx_d - dB_d/dx_i) and Pi_E gains
+// B_f . that flux (the energy flux -eta J x B).
 //
 // Face values (the central differences of Section 3.1, g(U) at the mean of
 // the two cells' states): at the face between c and c + e_d the normal
 // derivative is (f(c + e_d) - f(c)) / dx_d, a transverse one (active t != d)
 // the mean of the two cells' central differences,
 //   [f(c + e_t) - f(c - e_t) + f(c + e_d + e_t) - f(c + e_d - e_t)] / (4 dx_t),
-// rho_f the mean density and v_f = (rho v (c) + rho v (c + e_d)) /
-// (rho(c) + rho(c + e_d)); L_P = sum_d (Pi_(d,+) - Pi_(d,-)) / dx_d acts on the
-// momentum and the energy.
+// rho_f the mean density, v_f = (rho v (c) + rho v (c + e_d)) /
+// (rho(c) + rho(c + e_d)) and B_f the mean field; L_P = sum_d (Pi_(d,+) -
+// Pi_(d,-)) / dx_d acts on the momentum, the energy and B.
 //
 // Kernels around the hyperbolic step:
 //   k_par_half   after the first-order stage, on the ring box (the interior
 //                and one layer around it): L_P^n from the primitive fields of
 //                U^n (the predictors of every direction add dt/2 L_P^n, Eq.
-//                transv), and the fields (T, rho, v) of the cell-centred
+//                transv), and the fields (T, rho, v, B) of the cell-centred
 //                U^(n+1/2) = U^n + dt/2 (sum_d L_(H,d)^n + L_P^n).  L_(H,d)^n is
 //                the first-order stage's divergence where that stage formed
 //                it; the ring's outer layer (a launch of its own, SHELL)
 //                solves the missing faces with the same solver
 //   k_par_update U^(n+1) += dt L_P^(n+1/2) on the interior (Eq. update), the
-//                flux registers' momentum and energy take -dt A Pi, and on
+//                flux registers' momentum, energy and B take -dt A Pi, and on
 //                request the CFL rate of the result (with the diffusion
 //                term), in place of the fused reduction of the last sweep
 // The n+1/2 fields and the update are float64 (FP64 path) or double-float
 // with float64 update FMAs (mixed path: no other FP64-pipe instruction).
-// With nu = 0 only the temperature is formed and stored.
+// Each combination of the terms is a kernel of its own (template TM: bit 1
+// viscosity, bit 2 resistivity); conduction alone forms and stores only the
+// temperature.
 #pragma once
 
 #include "ctu_kernels.cuh"
@@ -37,8 +42,13 @@
 namespace ctu {
 
 // Planes of the half-step fields (8 bytes per scratch cell each): T, then
-// with viscosity rho, v_x, v_y, v_z.  Field index f: 0 rho, 1..3 v, 4 T.
-__host__ __device__ __forceinline__ int par_plane(int f) { return f == 4 ? 0 : f + 1; }
+// with viscosity or resistivity rho, v_x, v_y, v_z, B_x, B_y, B_z.  Field
+// index f: 0 rho, 1..3 v, 4 T, 5..7 B (the order of the primitive state).
+__host__ __device__ __forceinline__ int par_plane(int f) { return f == 4 ? 0 : (f < 4 ? f + 1 : f); }
+
+// Entries of L_P and of a face's Pi: 0..2 momentum, 3 energy, 4..6 B
+// (conserved component 1 + q).
+constexpr int NPAR = 7;
 
 // Adds (F(c - e_D/2) - F(c + e_D/2)) / dx_D at scratch cell c to s (global
 // order), F from the cell-centred primitive states as in k_div1.
@@ -61,7 +71,7 @@ __device__ __forceinline__ void par_div1(const StepArgs &a, const DevPatch &P, c
     for (int q = 0; q < NV; ++q) s[gperm<D>(q)] += (Fm[q] - Fp[q]) * iD;
 }
 
-// (Gamma - 1) kappa, nu and kappa in the working precision.
+// (Gamma - 1) kappa, nu, kappa and eta in the working precision.
 template <class R> __device__ __forceinline__ R par_gk(const StepArgs &a);
 template <> __device__ __forceinline__ double par_gk<double>(const StepArgs &a) { return (a.gam - 1.0) * a.kappa; }
 template <> __device__ __forceinline__ float par_gk<float>(const StepArgs &a) { return a.gm1f * a.kappaf; }
@@ -71,36 +81,63 @@ template <> __device__ __forceinline__ float par_nu<float>(const StepArgs &a) { 
 template <class R> __device__ __forceinline__ R par_kappa(const StepArgs &a);
 template <> __device__ __forceinline__ double par_kappa<double>(const StepArgs &a) { return a.kappa; }
 template <> __device__ __forceinline__ float par_kappa<float>(const StepArgs &a) { return a.kappaf; }
+template <class R> __device__ __forceinline__ R par_eta(const StepArgs &a);
+template <> __device__ __forceinline__ double par_eta<double>(const StepArgs &a) { return a.eta; }
+template <> __device__ __forceinline__ float par_eta<float>(const StepArgs &a) { return a.etaf; }
 
-// Parabolic fluxes through the face between scratch cells c and c + e_d:
-// Pi[0..2] momentum, Pi[3] energy.  get(f, i): field f of cell i; dif(f, i, j):
-// field f of cell i minus that of cell j.
-template <class R, bool VISC, class Get, class Dif>
+// Gradient of the fields f0 .. f0 + 2 at the face between c and cp = c + e_d:
+// g[t][i] = d f_(f0 + i) / dx_t.
+template <class R, class Dif>
+__device__ __forceinline__ void par_grad(const StepArgs &a, const DevPatch &P, long long c, long long cp, int d,
+                                         int f0, Dif dif, R (&g)[3][3])
+{
+    const R ih = pidx<R>(P, d);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        if (t == d) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) g[t][i] = dif(f0 + i, cp, c) * ih;
+        } else if (t < a.ndim) {
+            const long long s2 = dstr(P, t);
+            const R q4 = R(0.25) * pidx<R>(P, t);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) g[t][i] = (dif(f0 + i, c + s2, c - s2) + dif(f0 + i, cp + s2, cp - s2)) * q4;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) g[t][i] = R(0);
+        }
+    }
+}
+
+// Parabolic fluxes through the face between scratch cells c and c + e_d
+// (entries as NPAR).  get(f, i): field f of cell i; dif(f, i, j): field f of
+// cell i minus that of cell j.  TM: the terms beyond conduction compiled in,
+// bit 1 viscosity, bit 2 resistivity.
+template <class R, int TM, class Get, class Dif>
 __device__ __forceinline__ void par_face(const StepArgs &a, const DevPatch &P, long long c, int d, Get get,
-                                         Dif dif, R (&Pi)[4])
+                                         Dif dif, R (&Pi)[NPAR])
 {
     const long long st = dstr(P, d), cp = c + st;
     const R ih = pidx<R>(P, d);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Pi[q] = R(0);
+    for (int q = 0; q < NPAR; ++q) Pi[q] = R(0);
     if (a.par_cond) Pi[3] = par_kappa<R>(a) * dif(4, cp, c) * ih;
-    if constexpr (VISC) {
-        R g[3][3];  // g[t][i] = dv_i / dx_t at the face
+    if constexpr ((TM & 2) != 0) {
+        {
+            R g[3][3];  // g[t][i] = dB_i / dx_t at the face
+            par_grad<R>(a, P, c, cp, d, 5, dif, g);
+            const R eta = par_eta<R>(a);
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            if (t == d) {
-#pragma unroll
-                for (int i = 0; i < 3; ++i) g[t][i] = dif(1 + i, cp, c) * ih;
-            } else if (t < a.ndim) {
-                const long long s2 = dstr(P, t);
-                const R q4 = R(0.25) * pidx<R>(P, t);
-#pragma unroll
-                for (int i = 0; i < 3; ++i) g[t][i] = (dif(1 + i, c + s2, c - s2) + dif(1 + i, cp + s2, cp - s2)) * q4;
-            } else {
-#pragma unroll
-                for (int i = 0; i < 3; ++i) g[t][i] = R(0);
+            for (int i = 0; i < 3; ++i) {
+                const R f = eta * (g[d][i] - g[i][d]);
+                Pi[4 + i] = f;
+                Pi[3] += R(0.5) * (get(5 + i, c) + get(5 + i, cp)) * f;
             }
         }
+    }
+    if constexpr ((TM & 1) != 0) {
+        R g[3][3];  // g[t][i] = dv_i / dx_t at the face
+        par_grad<R>(a, P, c, cp, d, 1, dif, g);
         const R div = g[0][0] + g[1][1] + g[2][2];
         const R r0 = get(0, c), r1 = get(0, cp);
         const R rnu = R(0.5) * (r0 + r1) * par_nu<R>(a);
@@ -117,21 +154,21 @@ __device__ __forceinline__ void par_face(const StepArgs &a, const DevPatch &P, l
 
 // L_P at scratch cell c: sum_d (Pi(c, d) - Pi(c - e_d, d)) / dx_d; faces(d,
 // Pm, Pp) receives each direction's lower and upper face fluxes.
-template <class R, bool VISC, class Get, class Dif, class Faces>
+template <class R, int TM, class Get, class Dif, class Faces>
 __device__ __forceinline__ void par_lp(const StepArgs &a, const DevPatch &P, long long c, Get get, Dif dif,
-                                       R (&lp)[4], Faces faces)
+                                       R (&lp)[NPAR], Faces faces)
 {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) lp[q] = R(0);
+    for (int q = 0; q < NPAR; ++q) lp[q] = R(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         if (d >= a.ndim) continue;
-        R Pp[4], Pm[4];
-        par_face<R, VISC>(a, P, c, d, get, dif, Pp);
-        par_face<R, VISC>(a, P, c - dstr(P, d), d, get, dif, Pm);
+        R Pp[NPAR], Pm[NPAR];
+        par_face<R, TM>(a, P, c, d, get, dif, Pp);
+        par_face<R, TM>(a, P, c - dstr(P, d), d, get, dif, Pm);
         const R ih = pidx<R>(P, d);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) lp[q] += (Pp[q] - Pm[q]) * ih;
+        for (int q = 0; q < NPAR; ++q) lp[q] += (Pp[q] - Pm[q]) * ih;
         faces(d, Pm, Pp);
     }
 }
@@ -184,8 +221,8 @@ __device__ __forceinline__ void par_shell_coords(const DevPatch &P, int ndim, in
 // almost all cells.  L1: the first-order divergences (global order, ndim >
 // 1); LP: L_P^n per scratch cell, 4 planes of R (momentum, energy); Wh: the
 // half-step fields (par_plane), doubles (FP64 path) or double-float pairs
-// (hi, lo) (mixed path).  VISC: with viscosity (a.par_visc).
-template <class R, bool SHELL, bool VISC>
+// (hi, lo) (mixed path).  TM: bit 1 viscosity, bit 2 resistivity.
+template <class R, bool SHELL, int TM>
 __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *LP,
                                                     double *Wh)
 {
@@ -210,13 +247,15 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
     // L_P^n from the primitive fields of U^n (T = p / rho)
     auto get = [&](int f, long long i) -> R { return f == 4 ? Vs[4 * S + i] / Vs[i] : Vs[f * S + i]; };
     auto dif = [&](int f, long long i, long long j) -> R { return get(f, i) - get(f, j); };
-    R lp[4];
-    par_lp<R, VISC>(a, P, c, get, dif, lp, [](int, const R (&)[4], const R (&)[4]) {});
+    R lp[NPAR];
+    par_lp<R, TM>(a, P, c, get, dif, lp, [](int, const R (&)[NPAR], const R (&)[NPAR]) {});
     LP[3 * S + c] = lp[3];
-    if constexpr (VISC) {
+    // the components each term changes: momentum (viscosity), energy, B
+    // (resistivity)
+    auto on = [](int q) -> bool { return q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0); };
 #pragma unroll
-        for (int q = 0; q < 3; ++q) LP[q * S + c] = lp[q];
-    }
+    for (int q = 0; q < NPAR; ++q)
+        if (q != 3 && on(q)) LP[q * S + c] = lp[q];
     // the cell-centred half-step state and its fields
     const R gam = pgam<R>(a), ch = pch<R>(a.sp);
     R s[NV];
@@ -239,8 +278,8 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
         }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (VISC || q == 3) s[1 + q] += lp[q];
+    for (int q = 0; q < NPAR; ++q)
+        if (on(q)) s[1 + q] += lp[q];
     const long long gi = P.base + cl;
     if constexpr (sizeof(R) == 8) {
         const double hdt = 0.5 * a.sp->dt;
@@ -254,10 +293,16 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
         const unsigned int f = state_flags(rho, p);
         if (f) atomicOr(a.status, f);
         Wh[c] = p / rho;
-        if constexpr (VISC) {
-            Wh[S + c] = rho;
+        {
+            if constexpr ((TM & 1) != 0) {
+                Wh[S + c] = rho;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) Wh[(2 + q) * S + c] = U[1 + q] / rho;
+                for (int q = 0; q < 3; ++q) Wh[(2 + q) * S + c] = U[1 + q] / rho;
+            }
+            if constexpr ((TM & 2) != 0) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Wh[(5 + q) * S + c] = U[5 + q];
+            }
         }
     } else {
         // double-float (no FP64-pipe instruction): U^(n+1/2) = U^n + (dt/2) s
@@ -279,51 +324,58 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
         if (f) atomicOr(a.status, f);
         float2 *W2 = reinterpret_cast<float2 *>(Wh);
         W2[c] = make_float2(T.hi, T.lo);
-        if constexpr (VISC) {
-            W2[S + c] = make_float2(U[0].hi, U[0].lo);
+        {
+            if constexpr ((TM & 1) != 0) {
+                W2[S + c] = make_float2(U[0].hi, U[0].lo);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const df v = df_div(U[1 + q], U[0]);
-                W2[(2 + q) * S + c] = make_float2(v.hi, v.lo);
+                for (int q = 0; q < 3; ++q) {
+                    const df v = df_div(U[1 + q], U[0]);
+                    W2[(2 + q) * S + c] = make_float2(v.hi, v.lo);
+                }
+            }
+            if constexpr ((TM & 2) != 0) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) W2[(5 + q) * S + c] = make_float2(U[5 + q].hi, U[5 + q].lo);
             }
         }
     }
 }
 
 // Flux-register windows of the face of plane `plane` normal to D (transverse
-// coordinates ca, cb in increasing dimension order): the momentum and energy
-// fluxes through it gain -Pi^(n+1/2) (Eq. fluxcorr with the parabolic flux).
-template <class R, bool VISC, int D>
+// coordinates ca, cb in increasing dimension order): the momentum, energy and
+// B fluxes through it gain -Pi^(n+1/2) (Eq. fluxcorr with the parabolic flux).
+template <class R, int TM, int D>
 __device__ __forceinline__ void par_register(const StepArgs &a, const DevPatch &P, int patch, int plane, int ca,
-                                             int cb, const R (&pi)[4], double dt)
+                                             int cb, const R (&pi)[NPAR], double dt)
 {
     const int B = window_base(a, patch, D);
     if (B < 0) return;
     const int w0 = window_first(a, B, plane), w1 = window_first(a, B, plane + 1);
     if (w1 <= w0) return;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (q == 3 || VISC) register_face_var<R, D>(a, P, w0, w1, ca, cb, 1 + q, -pi[q], dt);
+    for (int q = 0; q < NPAR; ++q)
+        if (q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0))
+            register_face_var<R, D>(a, P, w0, w1, ca, cb, 1 + q, -pi[q], dt);
 }
 
-template <class R, bool VISC>
+template <class R, int TM>
 __device__ __forceinline__ void par_register_d(const StepArgs &a, const DevPatch &P, int patch, int d, int plane,
-                                               const int (&x)[3], const R (&pi)[4], double dt)
+                                               const int (&x)[3], const R (&pi)[NPAR], double dt)
 {
     if (d == 0)
-        par_register<R, VISC, 0>(a, P, patch, plane, x[1], x[2], pi, dt);
+        par_register<R, TM, 0>(a, P, patch, plane, x[1], x[2], pi, dt);
     else if (d == 1)
-        par_register<R, VISC, 1>(a, P, patch, plane, x[0], x[2], pi, dt);
+        par_register<R, TM, 1>(a, P, patch, plane, x[0], x[2], pi, dt);
     else
-        par_register<R, VISC, 2>(a, P, patch, plane, x[0], x[1], pi, dt);
+        par_register<R, TM, 2>(a, P, patch, plane, x[0], x[1], pi, dt);
 }
 
-// U_out's momentum and energy += dt L_P^(n+1/2) on the interior cells (the
+// U_out's momentum, energy and B += dt L_P^(n+1/2) on the interior cells (the
 // k_maxspeed tiling); the flux registers of the cell's lower faces (and of
 // its upper faces on the patch's last plane) gain -dt A Pi; with next !=
 // null also the CFL rate of the updated cell, Eq. (Ca) with the diffusion
 // term, folded into *next.
-template <int PHYS, class R, bool VISC>
+template <int PHYS, class R, int TM>
 __global__ void __launch_bounds__(BLOCK) k_par_update(StepArgs a, GroupTable gt, const double *Wh,
                                                       unsigned long long *next)
 {
@@ -342,51 +394,50 @@ __global__ void __launch_bounds__(BLOCK) k_par_update(StepArgs a, GroupTable gt,
         const double dt = a.sp->dt;
         // the flux registers of the cell's lower faces, and of its upper
         // faces on the patch's last plane
-        auto faces = [&](int d, const R (&Pm)[4], const R (&Pp)[4]) {
+        auto faces = [&](int d, const R (&Pm)[NPAR], const R (&Pp)[NPAR]) {
             if (!a.reg) return;
-            par_register_d<R, VISC>(a, P, wh.patch, d, x[d], x, Pm, dt);
-            if (x[d] == P.n[d] - 1) par_register_d<R, VISC>(a, P, wh.patch, d, x[d] + 1, x, Pp, dt);
+            par_register_d<R, TM>(a, P, wh.patch, d, x[d], x, Pm, dt);
+            if (x[d] == P.n[d] - 1) par_register_d<R, TM>(a, P, wh.patch, d, x[d] + 1, x, Pp, dt);
         };
-        R lp[4];
+        R lp[NPAR];
         if constexpr (sizeof(R) == 8) {
             auto get = [&](int f, long long n) -> double { return Wh[par_plane(f) * S + n]; };
             auto dif = [&](int f, long long n1, long long n2) -> double { return get(f, n1) - get(f, n2); };
-            par_lp<R, VISC>(a, P, c, get, dif, lp, faces);
+            par_lp<R, TM>(a, P, c, get, dif, lp, faces);
         } else {
             // temperature differences of the double-float fields, exact to
-            // float; the velocity, a coefficient of a small increment, in
-            // float
+            // float; those of v and B, coefficients of a small increment,
+            // in float
             const float2 *W2 = reinterpret_cast<const float2 *>(Wh);
             auto get = [&](int f, long long n) -> float { return W2[par_plane(f) * S + n].x; };
             auto dif = [&](int f, long long n1, long long n2) -> float {
                 const float2 u = W2[par_plane(f) * S + n1], v = W2[par_plane(f) * S + n2];
                 return f == 4 ? df_add(df{u.x, u.y}, df{-v.x, -v.y}).hi : u.x - v.x;
             };
-            par_lp<R, VISC>(a, P, c, get, dif, lp, faces);
+            par_lp<R, TM>(a, P, c, get, dif, lp, faces);
         }
         double *Uo = a.Uout + P.base + cl;
-        constexpr bool visc = VISC;
+        // the conserved components 1 + q the parabolic terms change
+        auto on = [](int q) -> bool { return q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0); };
         double U[NV];
-        U[4] = fma(dt, widen<R>(lp[3]), Uo[4 * a.ustride]);
-        Uo[4 * a.ustride] = U[4];
 #pragma unroll
-        for (int q = 1; q <= 3; ++q) {
-            if (visc) {
-                U[q] = fma(dt, widen<R>(lp[q - 1]), Uo[q * a.ustride]);
-                Uo[q * a.ustride] = U[q];
+        for (int q = 0; q < NPAR; ++q) {
+            if (on(q)) {
+                U[1 + q] = fma(dt, widen<R>(lp[q]), Uo[(1 + q) * a.ustride]);
+                Uo[(1 + q) * a.ustride] = U[1 + q];
             }
         }
         if (next) {
+            U[0] = Uo[0];
+            U[8] = Uo[8 * a.ustride];
 #pragma unroll
-            for (int q = 0; q < NV; ++q)
-                if (q == 0 || q > 4 || !visc) {
-                    if (q != 4) U[q] = Uo[q * a.ustride];
-                }
+            for (int q = 0; q < NPAR; ++q)
+                if (!on(q)) U[1 + q] = Uo[(1 + q) * a.ustride];
             R V[NV];
             const unsigned int f = prim_any<PHYS, R>(U, a, V);
             if (f) atomicOr(a.status, f);
             m = cell_speed<PHYS, R>(V, a, P);
-            const R D = max(par_gk<R>(a) / V[0], R(4.0 / 3.0) * par_nu<R>(a));
+            const R D = max(max(par_gk<R>(a) / V[0], R(4.0 / 3.0) * par_nu<R>(a)), par_eta<R>(a));
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 if (d < a.ndim) m += R(2) * D * (pidx<R>(P, d) * pidx<R>(P, d));

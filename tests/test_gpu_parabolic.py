@@ -1,9 +1,10 @@
-"""The parabolic terms of the CTU step, thermal conduction and viscosity, on
-the GPU against the oracle: 3-D blast with PPM, 2-D turbulence with
+"""The parabolic terms of the CTU step, thermal conduction, viscosity and
+resistivity, on the GPU against the oracle: 3-D blast with PPM, 2-D turbulence with
 MC-linear and 1-D diffusion-dominated cases, float64 (relative L1 1e-11) and
 mixed (the float tracing bar of the plain step); a ragged batch of patches
 in one call; the CFL rate with its diffusion term (ctu_dt and the step's
-next dt); flux registers with the parabolic momentum and energy fluxes."""
+next dt); flux registers with the parabolic momentum, energy and B
+fluxes."""
 import numpy as np
 import pytest
 
@@ -21,20 +22,21 @@ def _dev():
     return torch.device("cuda:0")
 
 
-@pytest.mark.parametrize("trace_mode,kappa,nu", [(0, 0.01, 0.0), (1, 0.01, 0.0), (0, 0.0, 0.01), (1, 0.005, 0.005)])
-def test_parabolic_3d_blast_ppm(trace_mode, kappa, nu):
+@pytest.mark.parametrize("trace_mode,kappa,nu,eta", [(0, 0.01, 0.0, 0.0), (1, 0.01, 0.0, 0.0), (0, 0.0, 0.01, 0.0),
+                                                     (0, 0.0, 0.0, 0.01), (1, 0.004, 0.004, 0.004)])
+def test_parabolic_3d_blast_ppm(trace_mode, kappa, nu, eta):
     n = [24, 24, 24]
     U0 = W.mhd_blast_3d(24, seed=31)
     dx = [1.0 / 24] * 3
-    ref, od = oracle_run(U0, n, 3, dx, 4, 0.3, recon=1, trace_mode=trace_mode, kappa=kappa, nu=nu)
+    ref, od = oracle_run(U0, n, 3, dx, 4, 0.3, recon=1, trace_mode=trace_mode, kappa=kappa, nu=nu, eta=eta)
     plain, _ = oracle_run(U0, n, 3, dx, 4, 0.3, recon=1, trace_mode=trace_mode)
     R = O.interior(ref, n, 3)
     # the parabolic terms change the state well above the tolerances below
-    q = 4 if kappa else 1
+    q = 4 if kappa else (1 if nu else 6)
     assert np.abs(R[q] - O.interior(plain, n, 3)[q]).sum() > 1e-3 * np.abs(R[q]).sum()
     for prec, tol in ((0, TOL64), (1, 2e-5)):
         got, gd, st = gpu_run(U0, n, 3, dx, 4, 0.3, precision=prec, recon=1, trace_mode=trace_mode, kappa=kappa,
-                              nu=nu)
+                              nu=nu, eta=eta)
         assert st == 0
         e = l1rel(O.interior(got, n, 3), R, od[-1][1])
         assert np.all(e <= tol), (prec, e)
@@ -42,15 +44,15 @@ def test_parabolic_3d_blast_ppm(trace_mode, kappa, nu):
             assert np.allclose(np.array(gd), np.array(od), rtol=1e-13, atol=0)
 
 
-@pytest.mark.parametrize("kappa,nu", [(0.02, 0.0), (0.0, 0.01), (0.01, 0.01)])
-def test_parabolic_2d_turbulence_mc(kappa, nu):
+@pytest.mark.parametrize("kappa,nu,eta", [(0.02, 0.0, 0.0), (0.0, 0.01, 0.0), (0.0, 0.0, 0.01), (0.01, 0.01, 0.01)])
+def test_parabolic_2d_turbulence_mc(kappa, nu, eta):
     n = [48, 48, 1]
     U0 = W.mhd_turb_2d(48, seed=32)
     dx = [1.0 / 48] * 2
-    ref, od = oracle_run(U0, n, 2, dx, 10, 0.4, recon=0, kappa=kappa, nu=nu)
+    ref, od = oracle_run(U0, n, 2, dx, 10, 0.4, recon=0, kappa=kappa, nu=nu, eta=eta)
     R = O.interior(ref, n, 2)
     for prec, tol in ((0, TOL64), (1, 1e-4)):
-        got, _, st = gpu_run(U0, n, 2, dx, 10, 0.4, precision=prec, recon=0, kappa=kappa, nu=nu)
+        got, _, st = gpu_run(U0, n, 2, dx, 10, 0.4, precision=prec, recon=0, kappa=kappa, nu=nu, eta=eta)
         assert st == 0
         G = O.interior(got, n, 2)
         assert not np.any(G[3]) and not np.any(G[7])
@@ -58,8 +60,8 @@ def test_parabolic_2d_turbulence_mc(kappa, nu):
         assert np.all(e <= tol), (prec, e)
 
 
-@pytest.mark.parametrize("kappa,nu", [(0.5, 0.0), (0.0, 0.3), (0.2, 0.2)])
-def test_parabolic_1d_diffusion_dominated(kappa, nu):
+@pytest.mark.parametrize("kappa,nu,eta", [(0.5, 0.0, 0.0), (0.0, 0.3, 0.0), (0.0, 0.0, 0.3), (0.2, 0.2, 0.2)])
+def test_parabolic_1d_diffusion_dominated(kappa, nu, eta):
     """1-D, a density wave with a transverse shear on a moving gas, in the
     regime where the diffusion term sets dt (oracle pins: the linear modes)."""
     N = 64
@@ -69,24 +71,24 @@ def test_parabolic_1d_diffusion_dominated(kappa, nu):
     rho = 1.0 + 0.2 * np.cos(2 * np.pi * x)
     z = np.zeros_like(rho)
     U0 = np.zeros(shp)
-    U0[:, 0, 0] = W.ideal_cons([rho, z + 0.3, 0.1 * np.sin(2 * np.pi * x), z, z + 1.0, z + 0.4, z + 0.2, z, z],
-                               5.0 / 3.0)
+    U0[:, 0, 0] = W.ideal_cons([rho, z + 0.3, 0.1 * np.sin(2 * np.pi * x), z, z + 1.0, z + 0.4,
+                                0.2 + 0.05 * np.cos(2 * np.pi * x), z, z], 5.0 / 3.0)
     dx = [1.0 / N]
-    ref, od = oracle_run(U0, n, 1, dx, 30, 0.4, recon=1, kappa=kappa, nu=nu)
+    ref, od = oracle_run(U0, n, 1, dx, 30, 0.4, recon=1, kappa=kappa, nu=nu, eta=eta)
     R = O.interior(ref, n, 1)
     for prec, tol in ((0, TOL64), (1, 2e-5)):
-        got, gd, st = gpu_run(U0, n, 1, dx, 30, 0.4, precision=prec, recon=1, kappa=kappa, nu=nu)
+        got, gd, st = gpu_run(U0, n, 1, dx, 30, 0.4, precision=prec, recon=1, kappa=kappa, nu=nu, eta=eta)
         assert st == 0
         e = l1rel(O.interior(got, n, 1), R, od[-1][1], group_floor=True)
         assert np.all(e <= tol), (prec, e)
     # the diffusion term sets dt here
     m_h = O.mhd_max_speed(U0, n, 1, dx)
-    m = O.mhd_max_rate(U0, n, 1, dx, 5.0 / 3.0, kappa, nu)
+    m = O.mhd_max_rate(U0, n, 1, dx, 5.0 / 3.0, kappa, nu, eta)
     assert m > 3 * m_h
 
 
-@pytest.mark.parametrize("kappa,nu", [(0.004, 0.0), (0.002, 0.003)])
-def test_parabolic_batch_of_uneven_patches(kappa, nu):
+@pytest.mark.parametrize("kappa,nu,eta", [(0.004, 0.0, 0.0), (0.002, 0.003, 0.003)])
+def test_parabolic_batch_of_uneven_patches(kappa, nu, eta):
     """Four patches of different shapes and cell widths in one call, each
     against the oracle run patch by patch with the batch's dt."""
     import torch
@@ -108,27 +110,30 @@ def test_parabolic_batch_of_uneven_patches(kappa, nu):
     dev = _dev()
     U = torch.from_numpy(pool).to(dev)
     Uo = torch.zeros_like(U)
-    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_FP64, cfl=0.3, kappa=kappa, nu=nu))
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_FP64, cfl=0.3, kappa=kappa, nu=nu,
+                                  eta=eta))
     patches = ctu.make_patches([(n, dx, b) for n, dx, b in zip(shapes, dxs, bases)])
     dtch = torch.zeros(2, dtype=torch.float64, device=dev)
     ctx.dt(U, stride, patches, dtch)
     ctx.step(U, Uo, stride, patches, dtch)
     assert ctx.status_sync() == 0
     dt, ch = dtch.cpu().tolist()
-    m = max(O.mhd_max_rate(A, list(n), 3, list(dx), 5.0 / 3.0, kappa, nu) for A, n, dx in zip(arrays, shapes, dxs))
+    m = max(O.mhd_max_rate(A, list(n), 3, list(dx), 5.0 / 3.0, kappa, nu, eta)
+            for A, n, dx in zip(arrays, shapes, dxs))
     dt_ref = 0.3 / m
     assert abs(dt - dt_ref) <= 1e-13 * dt_ref
     out = Uo.cpu().numpy()
     for A, n, dx, b in zip(arrays, shapes, dxs, bases):
-        R, bad = O.mhd_step(A, list(n), 3, list(dx), dt, ch, recon=1, kappa=kappa, nu=nu)
+        R, bad = O.mhd_step(A, list(n), 3, list(dx), dt, ch, recon=1, kappa=kappa, nu=nu, eta=eta)
         assert bad == 0
         G = out[:, b:b + A[0].size].reshape(A.shape)
         e = l1rel(O.interior(G, list(n), 3), O.interior(R, list(n), 3), ch)
         assert np.all(e <= TOL64), (n, e)
 
 
-@pytest.mark.parametrize("prec,nu", [(0, 0.0), (1, 0.0), (0, 0.03), (1, 0.03)])
-def test_parabolic_next_dt_matches_ctu_dt(prec, nu):
+@pytest.mark.parametrize("prec,nu,eta", [(0, 0.0, 0.0), (1, 0.0, 0.0), (0, 0.03, 0.0), (1, 0.03, 0.0), (0, 0.0, 0.08),
+                                         (1, 0.0, 0.08)])
+def test_parabolic_next_dt_matches_ctu_dt(prec, nu, eta):
     import torch
     from paper_1110_0740_gb300 import ctu
     n = [20, 12, 16]
@@ -138,7 +143,7 @@ def test_parabolic_next_dt_matches_ctu_dt(prec, nu):
     dev = _dev()
     U = torch.from_numpy(U0.reshape(9, -1).copy()).to(dev)
     Ua, Ub = torch.zeros_like(U), torch.zeros_like(U)
-    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=0.05, nu=nu))
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=0.05, nu=nu, eta=eta))
     p = ctu.make_patches([(n, [1 / 20, 1 / 12, 1 / 16], 0)])
     d0 = torch.zeros(2, dtype=torch.float64, device=dev)
     d1 = torch.zeros_like(d0)
@@ -153,15 +158,15 @@ def test_parabolic_next_dt_matches_ctu_dt(prec, nu):
     assert np.allclose(a, b, rtol=1e-13 if prec == 0 else 1e-6, atol=0), (a, b)
     # and against the oracle's rate (float64)
     if prec == 0:
-        m = O.mhd_max_rate(U0, n, 3, [1 / 20, 1 / 12, 1 / 16], 5.0 / 3.0, 0.05, nu)
+        m = O.mhd_max_rate(U0, n, 3, [1 / 20, 1 / 12, 1 / 16], 5.0 / 3.0, 0.05, nu, eta)
         assert abs(d0.cpu().numpy()[0] - 0.3 / m) <= 1e-14 * 0.3 / m
 
 
-@pytest.mark.parametrize("prec,nu", [(0, 0.0), (1, 0.0), (0, 0.02), (1, 0.02)])
-def test_parabolic_flux_registers(prec, nu):
+@pytest.mark.parametrize("prec,nu,eta", [(0, 0.0, 0.0), (1, 0.0, 0.0), (0, 0.02, 0.02), (1, 0.02, 0.02)])
+def test_parabolic_flux_registers(prec, nu, eta):
     """Register windows on every boundary face and on an interior plane of a
     3-D patch, two steps accumulated: with the parabolic terms the momentum
-    and energy entries carry F - Pi^(n+1/2), as in the oracle (which
+    energy and B entries carry F - Pi^(n+1/2), as in the oracle (which
     conserves two levels with them, see the oracle pins)."""
     import torch
     from paper_1110_0740_gb300 import ctu
@@ -182,7 +187,8 @@ def test_parabolic_flux_registers(prec, nu):
     U = torch.from_numpy(U0.reshape(9, -1).copy()).to(dev)
     Uo = torch.zeros_like(U)
     reg = torch.zeros(off, dtype=torch.float64, device=dev)
-    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=kappa, nu=nu))
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=kappa, nu=nu,
+                                  eta=eta))
     p = ctu.make_patches([(n, dx, 0)])
     ctx.flux_registers(reg, windows)
     dtch = torch.zeros(2, dtype=torch.float64, device=dev)
@@ -192,8 +198,8 @@ def test_parabolic_flux_registers(prec, nu):
     assert ctx.status_sync() == 0
     dt, ch = dtch.cpu().tolist()
     ref = np.zeros(off)
-    R, bad = O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref, kappa=kappa, nu=nu)
-    O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref, kappa=kappa, nu=nu)
+    R, bad = O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref, kappa=kappa, nu=nu, eta=eta)
+    O.mhd_step(U0, n, 3, dx, dt, ch, recon=1, windows=ws, reg=ref, kappa=kappa, nu=nu, eta=eta)
     assert bad == 0
     got = reg.cpu().numpy()
     # the energy entries differ from the hyperbolic-only registers
