@@ -70,13 +70,13 @@ def lib():
                                      ctypes.POINTER(ctypes.c_long), P, I, P, I, I, D, I, D]
         L.or_mhd_step_par.restype = I
         L.or_mhd_step_par.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, I, I,
-                                      ctypes.POINTER(ctypes.c_long), P, I, P, I, I, D, I, D, D, D]
+                                      ctypes.POINTER(ctypes.c_long), P, I, P, I, I, D, I, D, D, D, D]
         L.or_mhd_max_rate.restype = D
         L.or_mhd_max_rate.argtypes = [P, I, I, I, I, D, D, D, D, D]
         L.or_mhd_max_rate_par.restype = D
-        L.or_mhd_max_rate_par.argtypes = [P, I, I, I, I, D, D, D, D, D, D, D]
+        L.or_mhd_max_rate_par.argtypes = [P, I, I, I, I, D, D, D, D, D, D, D, D]
         L.or_mhd_parabolic.restype = None
-        L.or_mhd_parabolic.argtypes = [P, I, I, I, I, D, D, D, D, D, D, D, P]
+        L.or_mhd_parabolic.argtypes = [P, I, I, I, I, D, D, D, D, D, D, D, D, P]
         L.or_mhd_conduction.restype = None
         L.or_mhd_conduction.argtypes = [P, I, I, I, I, D, D, D, D, D, P]
         L.or_mhd_riemann_hllc.restype = I
@@ -301,13 +301,15 @@ def fill_outflow(U, n, ndim):
 # ---------------------------------------------------------------- MHD step
 
 def mhd_step(U, n, ndim, dx, dt, ch, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
-             windows=None, reg=None, upwind=0, shock=None, riemann=0, kappa=0.0, nu=0.0, eta=0.0):
+             windows=None, reg=None, upwind=0, shock=None, riemann=0, kappa=0.0, nu=0.0, eta=0.0,
+             kappa_par=None):
     """One CTU step of a ghost-filled patch; returns (Unew, n_bad_states).
 
     windows: optional list of (d, f, a0, a1, b0, b1, dst, weight) flux-register
     windows accumulated into the float64 array `reg` (see or_mhd_step).
     kappa > 0: with isotropic thermal conduction; nu > 0: with isotropic
-    viscosity; eta > 0: with resistivity (or_mhd_step_par)."""
+    viscosity; eta > 0: with resistivity (or_mhd_step_par).  kappa_par: the
+    conductivity along the field (None: kappa, isotropic)."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     assert U.shape == shape(n, ndim), (U.shape, shape(n, ndim))
     Un = np.empty_like(U)
@@ -328,8 +330,9 @@ def mhd_step(U, n, ndim, dx, dt, ch, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
             float(gamma), float(glm_alpha), int(recon), int(upwind),
             win.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(wgt),
             nwin, regp, int(riemann), *sh)
-    if nu > 0.0 or eta > 0.0:
-        bad = lib().or_mhd_step_par(*args, float(kappa), float(nu), float(eta))
+    kpar = kappa if kappa_par is None else kappa_par
+    if nu > 0.0 or eta > 0.0 or kpar != kappa:
+        bad = lib().or_mhd_step_par(*args, float(kappa), float(kpar), float(nu), float(eta))
     elif kappa > 0.0:
         bad = lib().or_mhd_step_tc(*args, float(kappa))
     else:
@@ -393,20 +396,22 @@ def mhd_max_speed(U, n, ndim, dx, gamma=5.0 / 3.0):
                                   float(dx[0]), float(dx[1]), float(dx[2]), float(gamma))
 
 
-def mhd_max_rate(U, n, ndim, dx, gamma=5.0 / 3.0, kappa=0.0, nu=0.0, eta=0.0):
+def mhd_max_rate(U, n, ndim, dx, gamma=5.0 / 3.0, kappa=0.0, nu=0.0, eta=0.0, kappa_par=None):
     """Eq. (Ca)'s max over interior cells of max_d (|v_d| + c_f,d)/dx_d
-    + sum_d 2 D / dx_d^2, D = max((Gamma - 1) kappa / rho, (4/3) nu, eta)."""
+    + sum_d 2 D / dx_d^2, D = max((Gamma - 1) max(kappa, kappa_par) / rho,
+    (4/3) nu, eta)."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     dx = list(dx) + [1.0] * (3 - len(dx))
-    if nu > 0.0 or eta > 0.0:
+    kpar = kappa if kappa_par is None else kappa_par
+    if nu > 0.0 or eta > 0.0 or kpar != kappa:
         return lib().or_mhd_max_rate_par(_dp(U), int(n[0]), int(n[1]), int(n[2]), int(ndim), float(dx[0]),
-                                         float(dx[1]), float(dx[2]), float(gamma), float(kappa), float(nu),
-                                         float(eta))
+                                         float(dx[1]), float(dx[2]), float(gamma), float(kappa), float(kpar),
+                                         float(nu), float(eta))
     return lib().or_mhd_max_rate(_dp(U), int(n[0]), int(n[1]), int(n[2]), int(ndim),
                                  float(dx[0]), float(dx[1]), float(dx[2]), float(gamma), float(kappa))
 
 
-def mhd_parabolic(U, n, ndim, dx, kappa, nu, gamma=5.0 / 3.0, eta=0.0):
+def mhd_parabolic(U, n, ndim, dx, kappa, nu, gamma=5.0 / 3.0, eta=0.0, kappa_par=None):
     """L_P of conduction, viscosity and resistivity (or_mhd_parabolic) on the
     interior cells: array of the shape of U, momentum in components 1..3,
     energy in 4 and B in 5..7 (the rest and the ghosts 0)."""
@@ -414,7 +419,8 @@ def mhd_parabolic(U, n, ndim, dx, kappa, nu, gamma=5.0 / 3.0, eta=0.0):
     dx = list(dx) + [1.0] * (3 - len(dx))
     LP = np.zeros(U.shape)
     lib().or_mhd_parabolic(_dp(U), int(n[0]), int(n[1]), int(n[2]), int(ndim), float(dx[0]), float(dx[1]),
-                           float(dx[2]), float(gamma), float(kappa), float(nu), float(eta), _dp(LP))
+                           float(dx[2]), float(gamma), float(kappa),
+                           float(kappa if kappa_par is None else kappa_par), float(nu), float(eta), _dp(LP))
     return LP
 
 
@@ -499,7 +505,8 @@ def euler_sample(left, right, gamma, xi):
 
 
 def mhd_run(U, n, ndim, dx, steps, cfl, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
-            bc="periodic", t_end=None, upwind=0, shock=None, riemann=0, kappa=0.0, nu=0.0, eta=0.0):
+            bc="periodic", t_end=None, upwind=0, shock=None, riemann=0, kappa=0.0, nu=0.0, eta=0.0,
+            kappa_par=None):
     """Advance a patch `steps` CTU steps (or up to t_end), filling ghosts each
     step; returns (U, t, dts)."""
     U = np.array(U, dtype=np.float64, copy=True)
@@ -513,13 +520,14 @@ def mhd_run(U, n, ndim, dx, steps, cfl, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
         if t_end is not None and t >= t_end * (1 - 1e-14):
             break
         fill(U, n, ndim)
-        m = (mhd_max_rate(U, n, ndim, dx, gamma, kappa, nu, eta) if kappa > 0.0 or nu > 0.0 or eta > 0.0
+        par = kappa > 0.0 or nu > 0.0 or eta > 0.0 or (kappa_par or 0.0) > 0.0
+        m = (mhd_max_rate(U, n, ndim, dx, gamma, kappa, nu, eta, kappa_par) if par
              else mhd_max_speed(U, n, ndim, dx, gamma))
         dt, ch = dt_ch(m, list(dx), ndim, cfl)
         if t_end is not None and t + dt > t_end:
             dt = t_end - t
         U, bad = mhd_step(U, n, ndim, dx, dt, ch, gamma, glm_alpha, recon, upwind=upwind, shock=shock,
-                          riemann=riemann, kappa=kappa, nu=nu, eta=eta)
+                          riemann=riemann, kappa=kappa, nu=nu, eta=eta, kappa_par=kappa_par)
         if bad:
             raise FloatingPointError(f"oracle met {bad} unphysical states at step {k}")
         t += dt

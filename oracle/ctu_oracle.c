@@ -844,12 +844,12 @@ void or_mhd_shock_flags(const double *U, int nx, int ny, int nz, int ndim, doubl
 /* Eq. (Ca): max over interior cells of
  *     max_d (|v_d| + c_f,d)/dx_d + sum_d 2 D / dx_d^2,
  * with D the largest diffusion coefficient of the cell:
- * max((Gamma - 1) kappa / rho, (4/3) nu, eta), the diffusivities of the
+ * max((Gamma - 1) max(kappa, kpar) / rho, (4/3) nu, eta), the diffusivities of the
  * temperature under conduction, of the longitudinal velocity under viscosity
  * and of B under resistivity (0 when all three are 0).  The caller sets dt = C_a / max and c_h = max * min_d dx_d
  * (= C_a min_d dx_d / dt). */
-double or_mhd_max_rate_par(const double *U, int nx, int ny, int nz, int ndim,
-                           double dx, double dy, double dz, double gam, double kappa, double nu, double eta)
+double or_mhd_max_rate_par(const double *U, int nx, int ny, int nz, int ndim, double dx, double dy, double dz,
+                           double gam, double kappa, double kpar, double nu, double eta)
 {
     grid_t G;
     double h[3] = {dx, dy, dz}, m = 0.0;
@@ -871,8 +871,8 @@ double or_mhd_max_rate_par(const double *U, int nx, int ny, int nz, int ndim,
                     if (sd > s)
                         s = sd;
                 }
-                if (kappa > 0.0 || nu > 0.0 || eta > 0.0) {
-                    double D = fmax(fmax((gam - 1.0) * kappa / V[0], 4.0 / 3.0 * nu), eta);
+                if (kappa > 0.0 || kpar > 0.0 || nu > 0.0 || eta > 0.0) {
+                    double D = fmax(fmax((gam - 1.0) * fmax(kappa, kpar) / V[0], 4.0 / 3.0 * nu), eta);
                     for (d = 0; d < ndim; d++)
                         s += 2.0 * D / (h[d] * h[d]);
                 }
@@ -886,7 +886,7 @@ double or_mhd_max_rate_par(const double *U, int nx, int ny, int nz, int ndim,
 double or_mhd_max_rate(const double *U, int nx, int ny, int nz, int ndim,
                        double dx, double dy, double dz, double gam, double kappa)
 {
-    return or_mhd_max_rate_par(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, 0.0, 0.0);
+    return or_mhd_max_rate_par(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, kappa, 0.0, 0.0);
 }
 
 /* max over interior cells of max_d (|v_d| + c_f,d)/dx_d (Eq. Ca without
@@ -894,7 +894,7 @@ double or_mhd_max_rate(const double *U, int nx, int ny, int nz, int ndim,
 double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
                         double dx, double dy, double dz, double gam)
 {
-    return or_mhd_max_rate_par(U, nx, ny, nz, ndim, dx, dy, dz, gam, 0.0, 0.0, 0.0);
+    return or_mhd_max_rate_par(U, nx, ny, nz, ndim, dx, dy, dz, gam, 0.0, 0.0, 0.0, 0.0);
 }
 
 /* ------------------------------------------------------------------ */
@@ -904,9 +904,11 @@ double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
 /* The parabolic fluxes of Section 2.1.1 on a Cartesian grid, from the
  * cell-centred fields W = (rho, v_x, v_y, v_z, T, B_x, B_y, B_z) (eight
  * arrays of ncell values, T = p / rho):
- *   - classical isotropic thermal conduction, the heat flux of Eq. (tc_flux)
- *     in the limit q -> infinity with kappa_par = kappa_perp = kappa:
- *     Pi_E += kappa dT/dx_d;
+ *   - classical thermal conduction, the heat flux of Eq. (tc_flux) in the
+ *     limit q -> infinity with constant kappa_perp = kappa and kappa_par = kpar:
+ *     Pi_E += kappa dT/dx_d + (kpar - kappa) b_d (b . grad T), b the unit
+ *     vector of the face's mean field (isotropic where it vanishes or
+ *     kpar = kappa);
  *   - isotropic viscosity, the stress of Eq. (visc_tens) with constant
  *     kinematic viscosity nu:
  *     tau_(d,i) = rho nu (dv_i/dx_d + dv_d/dx_i - (2/3) delta_(di) div v),
@@ -925,15 +927,40 @@ double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
  *     J = curl B, and the energy flux -eta J x B of Section 2.1.1).
  * Pi[1..3] receive the momentum fluxes, Pi[4] the energy flux and Pi[5..7]
  * the fluxes of B.  W holds (rho, v_x, v_y, v_z, T, B_x, B_y, B_z). */
-static void parabolic_face(const grid_t *G, const double *W, const double *h, double kappa, double nu, double eta,
-                           long id, int d, double *Pi)
+static void parabolic_face(const grid_t *G, const double *W, const double *h, double kappa, double kpar, double nu,
+                           double eta, long id, int d, double *Pi)
 {
     const long nc = G->ncell, st = dstride(G, d), ip = id + st;
     int q;
     for (q = 0; q < NVAR; q++)
         Pi[q] = 0.0;
-    if (kappa > 0.0)
+    if (kappa > 0.0 || kpar > 0.0)
         Pi[4] += kappa * (W[4 * nc + ip] - W[4 * nc + id]) / h[d];
+    if (kpar != kappa) {
+        /* anisotropic part of the classical heat flux of Eq. (tc_flux):
+         * (kappa_par - kappa_perp) b (b . grad T), b = B_f / |B_f| the
+         * direction of the face's mean field (none where B_f = 0) */
+        const double *T = W + 4 * nc;
+        double gt[3], bf[3], b2 = 0.0, bg = 0.0;
+        int t;
+        for (t = 0; t < 3; t++) {
+            if (t == d) {
+                gt[t] = (T[ip] - T[id]) / h[d];
+            } else if (t < G->ndim) {
+                const long s2 = dstride(G, t);
+                gt[t] = (T[id + s2] - T[id - s2] + T[ip + s2] - T[ip - s2]) / (4.0 * h[t]);
+            } else {
+                gt[t] = 0.0;
+            }
+            bf[t] = 0.5 * (W[(5 + t) * nc + id] + W[(5 + t) * nc + ip]);
+            b2 += bf[t] * bf[t];
+        }
+        if (b2 > 0.0) {
+            for (t = 0; t < 3; t++)
+                bg += bf[t] * gt[t];
+            Pi[4] += (kpar - kappa) * bf[d] * bg / b2;
+        }
+    }
     if (nu > 0.0) {
         double grad[3][3], div = 0.0, rf, vf[3];
         int i, t;
@@ -991,8 +1018,8 @@ static void parabolic_face(const grid_t *G, const double *W, const double *h, do
 /* L_P = sum_d (Pi_(d,+) - Pi_(d,-)) / dx_d (Eq. incrementop_par, Cartesian)
  * for the momentum, the energy and B, LP[q * ncell + id] (q = 1..7), on the
  * cells lo <= c <= hi; the other entries are left as they are. */
-static void parabolic_lp(const grid_t *G, const double *W, const double *h, double kappa, double nu, double eta,
-                         const int *lo, const int *hi, double *LP)
+static void parabolic_lp(const grid_t *G, const double *W, const double *h, double kappa, double kpar, double nu,
+                         double eta, const int *lo, const int *hi, double *LP)
 {
     int c[3], d, q;
     for (c[2] = lo[2]; c[2] <= hi[2]; c[2]++)
@@ -1001,8 +1028,8 @@ static void parabolic_lp(const grid_t *G, const double *W, const double *h, doub
                 long id = cidx(G, c);
                 double s[NVAR] = {0}, Pp[NVAR], Pm[NVAR];
                 for (d = 0; d < G->ndim; d++) {
-                    parabolic_face(G, W, h, kappa, nu, eta, id, d, Pp);
-                    parabolic_face(G, W, h, kappa, nu, eta, id - dstride(G, d), d, Pm);
+                    parabolic_face(G, W, h, kappa, kpar, nu, eta, id, d, Pp);
+                    parabolic_face(G, W, h, kappa, kpar, nu, eta, id - dstride(G, d), d, Pm);
                     for (q = 1; q <= 7; q++)
                         s[q] += (Pp[q] - Pm[q]) / h[d];
                 }
@@ -1037,7 +1064,7 @@ static int parabolic_fields(const grid_t *G, const double *U, double gam, double
  * energy (q = 4) and B (q = 5..7), ghosted layout (the other entries are
  * 0). */
 void or_mhd_parabolic(const double *U, int nx, int ny, int nz, int ndim, double dx, double dy, double dz,
-                      double gam, double kappa, double nu, double eta, double *LP)
+                      double gam, double kappa, double kpar, double nu, double eta, double *LP)
 {
     grid_t G;
     double h[3] = {dx, dy, dz};
@@ -1049,7 +1076,7 @@ void or_mhd_parabolic(const double *U, int nx, int ny, int nz, int ndim, double 
     W = (double *)malloc(sizeof(double) * 8 * G.ncell);
     parabolic_fields(&G, U, gam, W);
     memset(LP, 0, sizeof(double) * NVAR * G.ncell);
-    parabolic_lp(&G, W, h, kappa, nu, eta, lo, hi, LP);
+    parabolic_lp(&G, W, h, kappa, kpar, nu, eta, lo, hi, LP);
     free(W);
 }
 
@@ -1061,7 +1088,7 @@ void or_mhd_conduction(const double *U, int nx, int ny, int nz, int ndim, double
     double *A;
     grid_init(&G, nx, ny, nz, ndim);
     A = (double *)malloc(sizeof(double) * NVAR * G.ncell);
-    or_mhd_parabolic(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, 0.0, 0.0, A);
+    or_mhd_parabolic(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, kappa, 0.0, 0.0, A);
     memcpy(LP, A + 4 * G.ncell, sizeof(double) * G.ncell);
     free(A);
 }
@@ -1120,9 +1147,10 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                      double dx, double dy, double dz, double dt, double ch,
                      double gam, double glm_alpha, int recon, int upwind,
                      const long *win, const double *wgt, int nwin, double *reg,
-                     int solver, int shock, double eps_q, int qkind, double kappa, double nu, double eta)
+                     int solver, int shock, double eps_q, int qkind, double kappa, double kpar, double nu,
+                     double eta)
 {
-    const int par = kappa > 0.0 || nu > 0.0 || eta > 0.0;
+    const int par = kappa > 0.0 || kpar > 0.0 || nu > 0.0 || eta > 0.0;
     unsigned char *flags = NULL;
     grid_t G;
     double h[3] = {dx, dy, dz};
@@ -1163,7 +1191,7 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                 Wn[q * nc + id] = V[q * nc + id];
             Wn[4 * nc + id] = V[4 * nc + id] / V[id];
         }
-        parabolic_lp(&G, Wn, h, kappa, nu, eta, ring_lo, ring_hi, LPn);
+        parabolic_lp(&G, Wn, h, kappa, kpar, nu, eta, ring_lo, ring_hi, LPn);
     }
 
     /* 2. first-order Godunov fluxes F^n_d = R(U_c, U_(c+e_d)) on the faces the
@@ -1309,7 +1337,7 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                 }
         for (d = 0; d < 3; d++)
             ihi[d] = G.n[d] - 1;
-        parabolic_lp(&G, Wh, h, kappa, nu, eta, ilo, ihi, LPh);
+        parabolic_lp(&G, Wh, h, kappa, kpar, nu, eta, ilo, ihi, LPh);
     }
 
     /* 5. conservative update, Eq. (update): U + dt * (L_x + L_y + L_z) (+ L_P) */
@@ -1357,7 +1385,7 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                      * F - Pi^(n+1/2) (momentum, energy and B) */
                     if (Wh && q >= 1 && q <= 7) {
                         double Pi[NVAR];
-                        parabolic_face(&G, Wh, h, kappa, nu, eta, id, wd, Pi);
+                        parabolic_face(&G, Wh, h, kappa, kpar, nu, eta, id, wd, Pi);
                         flux -= Pi[q];
                     }
                     reg[W[6] + (q * nb + jb) * na + ja] += wgt[w] * dt * area * flux;
@@ -1392,11 +1420,12 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
                    int solver, int shock, double eps_q, int qkind)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, 0.0, 0.0, 0.0);
+                     nwin, reg, solver, shock, eps_q, qkind, 0.0, 0.0, 0.0, 0.0);
 }
 
-/* or_mhd_step_ex with thermal conduction of conductivity kappa >= 0,
- * viscosity of kinematic viscosity nu >= 0 and resistivity eta >= 0 (the
+/* or_mhd_step_ex with thermal conduction of conductivities kappa >= 0 across
+ * and kpar >= 0 along the field, viscosity of kinematic viscosity nu >= 0
+ * and resistivity eta >= 0 (the
  * parabolic terms; see step_core and parabolic_face).  The flux registers
  * take the fluxes F - Pi^(n+1/2) of the momentum, the energy and B through
  * their faces. */
@@ -1404,10 +1433,11 @@ int or_mhd_step_par(const double *U, double *Unew, int nx, int ny, int nz, int n
                     double dx, double dy, double dz, double dt, double ch,
                     double gam, double glm_alpha, int recon, int upwind,
                     const long *win, const double *wgt, int nwin, double *reg,
-                    int solver, int shock, double eps_q, int qkind, double kappa, double nu, double eta)
+                    int solver, int shock, double eps_q, int qkind, double kappa, double kpar, double nu,
+                    double eta)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, kappa, nu, eta);
+                     nwin, reg, solver, shock, eps_q, qkind, kappa, kpar, nu, eta);
 }
 
 /* or_mhd_step_par with conduction alone. */
@@ -1418,7 +1448,7 @@ int or_mhd_step_tc(const double *U, double *Unew, int nx, int ny, int nz, int nd
                    int solver, int shock, double eps_q, int qkind, double kappa)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, kappa, 0.0, 0.0);
+                     nwin, reg, solver, shock, eps_q, qkind, kappa, kappa, 0.0, 0.0);
 }
 
 /* ------------------------------------------------------------------ */

@@ -274,3 +274,103 @@ def test_reflux_with_conduction_restores_conservation_of_two_levels():
     scale = np.abs(O.interior(Unew, nc, 2)).sum(axis=(1, 2, 3)) * hc * hc
     assert np.all(np.abs(total - total0)[:8] <= 1e-13 * scale[:8]), (total - total0)
     assert np.abs(no_reflux - total0)[4] > 1e-8
+
+
+# ------------------------------------------------------------ anisotropic flux
+# F_class = kappa_par b (b . grad T) + kappa_perp (grad T - b (b . grad T)) of
+# Eq. (tc_flux), b = B / |B| at the face (the mean of the two cells).
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_anisotropic_field_along_x_closed_form(ndim):
+    """B along x, T = 1 + a x^2 + c y^2 (+ e z^2): the flux along x is
+    kappa_par dT/dx and across it kappa_perp dT/dy, so
+    L_P = kappa_par 2a + kappa_perp (2c + 2e), exactly."""
+    n = [12, 10, 8 if ndim > 2 else 1]
+    a, c, e = 0.6, -0.3, 0.2
+    shp = O.shape(n, ndim)
+    T = 1.0 + a * _centres(n, ndim, 0) ** 2 + c * _centres(n, ndim, 1) ** 2 + np.zeros(shp[1:])
+    if ndim > 2:
+        T = T + e * _centres(n, ndim, 2) ** 2
+    rho = 1.0 + 0.0 * T
+    U = _prim_to_U(n, ndim, rho, 0.0, rho * T, B=(0.7, 0.0, 0.0))
+    kperp, kpar = 0.05, 0.8
+    dx = [1.0 / n[d] for d in range(ndim)]
+    LP = O.interior(O.mhd_parabolic(U, n, ndim, dx, kperp, 0.0, G, kappa_par=kpar), n, ndim)
+    want = kpar * 2 * a + kperp * 2 * (c + (e if ndim > 2 else 0.0))
+    assert np.allclose(LP[4], want, rtol=0, atol=1e-10)
+
+
+def test_anisotropic_oblique_field_cross_terms():
+    """B along (1, 1)/sqrt(2), T = 1 + c x y: div F = (kappa_par - kappa_perp) c,
+    exactly (the transverse temperature derivatives at the faces)."""
+    n = [12, 10, 1]
+    c = 0.9
+    shp = O.shape(n, 2)
+    T = 1.0 + c * _centres(n, 2, 0) * _centres(n, 2, 1) + np.zeros(shp[1:])
+    rho = 1.0 + 0.0 * T
+    U = _prim_to_U(n, 2, rho, 0.0, rho * T, B=(0.5, 0.5, 0.0))
+    kperp, kpar = 0.1, 0.7
+    LP = O.interior(O.mhd_parabolic(U, n, 2, [1 / 12, 1 / 10], kperp, 0.0, G, kappa_par=kpar), n, 2)
+    assert np.allclose(LP[4], (kpar - kperp) * c, rtol=0, atol=1e-11)
+
+
+def test_anisotropic_equal_coefficients_is_isotropic():
+    N = 12
+    n = [N, N, 1]
+    U = W.mhd_turb_2d(N, seed=7)
+    O.fill_periodic(U, n, 2)
+    dx = [1.0 / N] * 2
+    dt, ch = O.dt_ch(O.mhd_max_rate(U, n, 2, dx, G, 0.02), dx, 2, 0.3)
+    a, _ = O.mhd_step(U, n, 2, dx, dt, ch, recon=1, kappa=0.02)
+    b, _ = O.mhd_step(U, n, 2, dx, dt, ch, recon=1, kappa=0.02, kappa_par=0.02, nu=1e-300)
+    assert np.array_equal(a, b)
+    # the rate takes the larger coefficient
+    assert O.mhd_max_rate(U, n, 2, dx, G, 0.01, kappa_par=0.05) == pytest.approx(
+        O.mhd_max_rate(U, n, 2, dx, G, 0.05), rel=1e-15)
+
+
+@pytest.mark.parametrize("along", [True, False])
+def test_anisotropic_mode_second_order(along):
+    """A temperature mode along x with a uniform field along x (decays with
+    kappa_par) or along y (kappa_perp): the linear system of the isotropic
+    pins with that coefficient, second-order convergence."""
+    kperp, kpar = 0.001, 0.006
+    k_eff = kpar if along else kperp
+
+    def err(N):
+        n = [N, 1, 1]
+        eps, v0 = 1e-6, 0.3
+        U, kv, phase = _linear_mode(n, 1, k_eff, eps, v0)
+        Bx, By = (1e-3, 0.0) if along else (0.0, 1e-3)
+        Ui = U.copy()
+        Ui[4] += 0.5 * (Bx * Bx + By * By)
+        Ui[5] += Bx
+        Ui[6] += By
+        R, t, _ = O.mhd_run(Ui, n, 1, [1.0 / N], None, 0.4, recon=1, t_end=1.0, kappa=kperp, kappa_par=kpar)
+        ex = O.interior(_exact_rho(kv, phase, t, k_eff, eps, v0)[None], n, 1)[0]
+        return np.abs(O.interior(R, n, 1)[0] - ex).mean() / eps
+
+    e = [err(N) for N in (32, 64, 128)]
+    orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert orders[-1] > 1.9, (e, orders)
+    assert e[-1] < 2e-3
+
+
+def test_anisotropic_oblique_field_quadratic_closed_form():
+    """B along (1, 1)/sqrt(2), T = 1 + c x^2 y: div F = 2 c kappa_perp y +
+    (kappa_par - kappa_perp) c (y + 2 x), exactly: the transverse derivative
+    of T at an x-face is the mean of the two cells' central differences
+    (c x^2 is quadratic across the face)."""
+    n = [12, 10, 1]
+    c = 0.9
+    shp = O.shape(n, 2)
+    x, y = _centres(n, 2, 0), _centres(n, 2, 1)
+    T = 1.0 + c * x * x * y + np.zeros(shp[1:])
+    rho = 1.0 + 0.0 * T
+    U = _prim_to_U(n, 2, rho, 0.0, rho * T, B=(0.5, 0.5, 0.0))
+    kperp, kpar = 0.1, 0.7
+    LP = O.interior(O.mhd_parabolic(U, n, 2, [1 / 12, 1 / 10], kperp, 0.0, G, kappa_par=kpar), n, 2)
+    X = O.interior((x + 0 * T)[None], n, 2)[0]
+    Y = O.interior((y + 0 * T)[None], n, 2)[0]
+    want = 2 * c * kperp * Y + (kpar - kperp) * c * (Y + 2 * X)
+    assert np.allclose(LP[4], want, rtol=0, atol=1e-11)
