@@ -219,7 +219,7 @@ def run_ours(args):
         c = ctu.Ctx(ctu.make_config(ndim=3, recon=RECONS[args.recon], precision=prec, cfl=0.3,
                                     shock=(args.shock, 0) if args.shock else None,
                                     riemann=ctu.CTU_HLLC if args.riemann == "hllc" else ctu.CTU_HLLD,
-                                    kappa=args.kappa, nu=args.nu, eta=args.eta))
+                                    kappa=args.kappa, nu=args.nu, eta=args.eta, kappa_par=args.kappa_par))
         c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
         if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
@@ -327,7 +327,8 @@ def run_ours(args):
     roof["hbm_step"] = {"algorithmic_bytes": nbytes, "achieved_gbs": hbm_achieved,
                         "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
                         "peak_source": f"{src} hbm_gbs"}
-    if mixed and args.recon == "ppm" and not args.shock and args.riemann == "hlld" and not args.kappa and not args.nu and not args.eta:
+    plain = not (args.shock or args.kappa or args.nu or args.eta or args.kappa_par)
+    if mixed and args.recon == "ppm" and args.riemann == "hlld" and plain:
         roof["precision_split"] = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
 
     # end-to-end through the public API with host buffers
@@ -406,6 +407,7 @@ def run_ours(args):
                            + (f"; hybrid integration (shock flags, eps_q {args.shock})" if args.shock else "")
                            + ("; HLLC in place of HLLD" if args.riemann == "hllc" else "")
                            + (f"; thermal conduction, kappa {args.kappa}" if args.kappa else "")
+                           + (f" (along the field {args.kappa_par})" if args.kappa_par else "")
                            + (f"; viscosity, nu {args.nu}" if args.nu else "")
                            + (f"; resistivity, eta {args.eta}" if args.eta else ""),
                            "recon": args.recon, "shock_eps": args.shock or None,
@@ -935,6 +937,8 @@ def main():
                     help="blast: thermal conduction with this conductivity (0 = off)")
     ap.add_argument("--nu", type=float, default=0.0,
                     help="blast: viscosity with this kinematic viscosity (0 = off)")
+    ap.add_argument("--kappa-par", type=float, default=0.0,
+                    help="blast: thermal conductivity along the field, --kappa then across it (0 = isotropic)")
     ap.add_argument("--eta", type=float, default=0.0,
                     help="blast: resistivity with this magnetic diffusivity (0 = off)")
     ap.add_argument("--shock", type=float, default=0.0,

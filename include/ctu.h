@@ -193,6 +193,14 @@ typedef struct {
      * and D = max((Gamma-1) kappa / rho, (4/3) nu, eta).  Same combinations as
      * kappa. */
     double eta;
+    /* Anisotropic conduction: kappa_par >= 0 the conductivity along the
+     * field, kappa then being the one across it (Eq. tc_flux, classical):
+     * Pi_E = kappa grad T + (kappa_par - kappa) b (b . grad T), b = B_f / |B_f|
+     * the direction of the face's mean field (isotropic where B_f = 0), the
+     * transverse derivatives of T as for nu.  0 = equal to kappa (isotropic).
+     * The CFL diffusion coefficient takes max(kappa, kappa_par).  Same
+     * combinations as kappa. */
+    double kappa_par;
 } ctu_config;
 
 typedef struct {
@@ -230,7 +238,8 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out);
 
 /* CFL time step, Eq. (Ca): M = max over the interior cells of all patches of
  * max_d (|v_d| + c_f,d) / dx_d (+ sum_d 2 D / dx_d^2 with the parabolic
- * terms, D = max((Gamma-1) kappa / rho, (4/3) nu, eta)); then dt = cfl / M and
+ * terms, D = max((Gamma-1) max(kappa, kappa_par) / rho, (4/3) nu, eta)); then
+ * dt = cfl / M and
  * c_h = M * min dx (the GLM speed, equal to cfl * min dx / dt).  Writes {dt, c_h} to the device
  * array d_dt_ch[2]; if h_dt_ch is non-null it also copies them there and
  * synchronises the stream.  U: device pool; patches: host array. */

@@ -319,7 +319,7 @@ static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStr
 // 256-byte aligned) the shock flags of the hybrid integration (one byte per
 // scratch cell) and, with the parabolic terms, L_P^n (seven words of the
 // working precision) and the half-step fields (one 8-byte plane, T; eight
-// with viscosity or resistivity) per scratch cell.
+// with viscosity, resistivity or anisotropic conduction) per scratch cell.
 struct ScratchOffsets {
     size_t flags, lp, th, total;
 };
@@ -330,8 +330,9 @@ static ScratchOffsets scratch_offsets(const ctu_ctx *ctx)
     const size_t S = (size_t)ctx->sstride;
     ScratchOffsets o;
     o.flags = align256((size_t)SCRATCH_ARRAYS * S * elt);
-    const bool tensor = ctx->cfg.nu > 0.0 || ctx->cfg.eta > 0.0;
-    const bool par = ctx->cfg.kappa > 0.0 || tensor;
+    const double kpar = ctx->cfg.kappa_par > 0.0 ? ctx->cfg.kappa_par : ctx->cfg.kappa;
+    const bool tensor = ctx->cfg.nu > 0.0 || ctx->cfg.eta > 0.0 || kpar != ctx->cfg.kappa;
+    const bool par = ctx->cfg.kappa > 0.0 || kpar > 0.0 || tensor;
     o.lp = align256(o.flags + (ctx->cfg.shock_detect ? S : 0));
     o.th = align256(o.lp + (par ? 7 * S * elt : 0));
     o.total = o.th + (par ? (tensor ? 8 : 1) * S * sizeof(double) : 0);
@@ -374,14 +375,18 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.shock_q = ctx->cfg.shock_q;
     a.flags = nullptr;
     a.kappa = ctx->cfg.kappa;
+    a.kpar = ctx->cfg.kappa_par > 0.0 ? ctx->cfg.kappa_par : ctx->cfg.kappa;
     a.nu = ctx->cfg.nu;
     a.eta = ctx->cfg.eta;
     a.kappaf = (float)ctx->cfg.kappa;
+    a.dkappaf = (float)(a.kpar - a.kappa);
+    a.kmaxf = (float)(a.kpar > a.kappa ? a.kpar : a.kappa);
     a.nuf = (float)ctx->cfg.nu;
     a.etaf = (float)ctx->cfg.eta;
-    a.par_cond = ctx->cfg.kappa > 0.0;
+    a.par_cond = a.kappa > 0.0 || a.kpar > 0.0;
     a.par_visc = ctx->cfg.nu > 0.0;
     a.par_res = ctx->cfg.eta > 0.0;
+    a.par_aniso = a.kpar != a.kappa;
     a.gm1lo = tm ? 0.0f : (float)((ctx->cfg.gamma - 1.0) - (double)a.gm1f);
     a.lp = nullptr;
     a.th = nullptr;
@@ -418,7 +423,7 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
     const bool ref = ctx->cfg.trace_mode >= CTU_TRACE_CENTER;
     const bool hyb = ctx->cfg.shock_detect != 0;
     const bool hllc = ctx->cfg.physics == CTU_MHD && ctx->cfg.riemann == CTU_HLLC;
-    const bool par = ctx->cfg.kappa > 0.0 || ctx->cfg.nu > 0.0 || ctx->cfg.eta > 0.0;
+    const bool par = ctx->cfg.kappa > 0.0 || ctx->cfg.kappa_par > 0.0 || ctx->cfg.nu > 0.0 || ctx->cfg.eta > 0.0;
     li.recon = r == CTU_PPM
                    ? (par ? RECON_PPM_PAR
                           : (hllc ? RECON_PPM_HLLC : (hyb ? RECON_PPM_HYB : (ref ? RECON_PPM_REF : RECON_PPM))))
@@ -516,11 +521,11 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
             return CTU_EUNSUPPORTED;
     }
     if (!(cfg->kappa >= 0.0 && cfg->kappa < INFINITY) || !(cfg->nu >= 0.0 && cfg->nu < INFINITY) ||
-        !(cfg->eta >= 0.0 && cfg->eta < INFINITY))
+        !(cfg->eta >= 0.0 && cfg->eta < INFINITY) || !(cfg->kappa_par >= 0.0 && cfg->kappa_par < INFINITY))
         return CTU_EINVAL;
     // the parabolic terms: ideal MHD, PPM or MC-linear, HLLD, tracing without
     // or with the w_(+/-) reference, no hybrid integration, FP64 or CTU_MIXED
-    if ((cfg->kappa > 0.0 || cfg->nu > 0.0 || cfg->eta > 0.0) &&
+    if ((cfg->kappa > 0.0 || cfg->kappa_par > 0.0 || cfg->nu > 0.0 || cfg->eta > 0.0) &&
         (cfg->physics != CTU_MHD || (cfg->recon != CTU_PPM && cfg->recon != CTU_LINEAR_MC) ||
          cfg->riemann != CTU_HLLD || cfg->trace_mode > CTU_TRACE_UPWIND || cfg->shock_detect ||
          cfg->precision == CTU_MIXED_IFACE64))

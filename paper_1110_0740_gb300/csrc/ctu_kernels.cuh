@@ -76,15 +76,17 @@ struct StepArgs {
     unsigned char *flags;
     double shock_eps;
     int shock_q;           // 0 thermal, 1 magnetic pressure
-    // parabolic terms (the RECON_*_PAR kernels): conductivity kappa,
-    // kinematic viscosity nu and resistivity eta (par_cond, par_visc,
-    // par_res: nonzero when on), L_P^n per scratch cell (7 planes of the
+    // parabolic terms (the RECON_*_PAR kernels): conductivities kappa and
+    // kpar (along the field), kinematic viscosity nu and resistivity eta
+    // (par_cond, par_visc, par_res, par_aniso: nonzero when on), L_P^n per
+    // scratch cell (7 planes of the
     // working precision: momentum, energy, B) and the half-step fields
     // (planes of 8 bytes: T, then rho, v and B with viscosity or resistivity)
-    double kappa, nu, eta;
-    float kappaf, nuf, etaf;  // kappa, nu, eta in float
-    float gm1lo;              // (Gamma-1) - gm1f in float: Gamma-1 as a double-float pair
-    int par_cond, par_visc, par_res;
+    double kappa, kpar, nu, eta;  // kappa: across the field (all directions when isotropic)
+    float kappaf, nuf, etaf;      // kappa, nu, eta in float
+    float dkappaf, kmaxf;         // kpar - kappa, max(kappa, kpar) in float
+    float gm1lo;                  // (Gamma-1) - gm1f in float: Gamma-1 as a double-float pair
+    int par_cond, par_visc, par_res, par_aniso;
     const void *lp;
     double *th;
     const double *U;       // pool in
@@ -1339,8 +1341,9 @@ __global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, GroupTable gt, u
         if (f) atomicOr(a.status, f);
         m = cell_speed<PHYS, R>(V, a, P);
         if (a.par_cond | a.par_visc | a.par_res) {  // parabolic terms: + sum_d 2 D / dx_d^2
-            // D = max((Gamma-1) kappa / rho, (4/3) nu, eta)
-            const R D = max(max((sizeof(R) == 8 ? (R)((a.gam - 1.0) * a.kappa) : (R)(a.gm1f * a.kappaf)) / V[0],
+            // D = max((Gamma-1) max(kappa, kpar) / rho, (4/3) nu, eta)
+            const R D = max(max((sizeof(R) == 8 ? (R)((a.gam - 1.0) * (a.kpar > a.kappa ? a.kpar : a.kappa))
+                                                : (R)(a.gm1f * a.kmaxf)) / V[0],
                                 R(4.0 / 3.0) * (sizeof(R) == 8 ? (R)a.nu : (R)a.nuf)),
                             sizeof(R) == 8 ? (R)a.eta : (R)a.etaf);
 #pragma unroll

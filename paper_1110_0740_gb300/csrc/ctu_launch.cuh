@@ -47,6 +47,27 @@ static int over_groups(const LaunchInfo &li, BPP bpp, GO go)
     return launches;
 }
 
+// The parabolic kernels' term mask (bit 1 viscosity, bit 2 resistivity, bit
+// 4 anisotropic conduction) and a call of f with it as a compile-time
+// constant.
+static inline int par_mask(const StepArgs &a)
+{
+    return (a.par_visc ? 1 : 0) | (a.par_res ? 2 : 0) | (a.par_aniso ? 4 : 0);
+}
+template <class F> static void with_tm(int tm, F &&f)
+{
+    switch (tm) {
+    case 0: f(std::integral_constant<int, 0>{}); break;
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    default: f(std::integral_constant<int, 7>{}); break;
+    }
+}
+
 // Kernels that stage through more than the default 48 KB of dynamic shared
 // memory are opted in once per device (the carveout set to its maximum, so
 // that the register-limited number of blocks still fits).
@@ -134,16 +155,8 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
                     k_par_half<R, true, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
                 });
         };
-        // one kernel per combination of the terms beyond conduction
-        const int tm = (a.par_visc ? 1 : 0) | (a.par_res ? 2 : 0);
-        if (tm == 0)
-            half(std::integral_constant<int, 0>{});
-        else if (tm == 1)
-            half(std::integral_constant<int, 1>{});
-        else if (tm == 2)
-            half(std::integral_constant<int, 2>{});
-        else
-            half(std::integral_constant<int, 3>{});
+        // one kernel per combination of the terms beyond isotropic conduction
+        with_tm(par_mask(a), half);
         CTU_MARK(nullptr);
     }
     // sweeps in the order z, y, x: the first writes A = L_D, the middle one
@@ -176,15 +189,9 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         n += over_groups(
             li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
             [&](const GroupTable &gt, unsigned nb) {
-                const int tm = (a.par_visc ? 1 : 0) | (a.par_res ? 2 : 0);
-                if (tm == 0)
-                    k_par_update<PHYS, R, 0><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
-                else if (tm == 1)
-                    k_par_update<PHYS, R, 1><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
-                else if (tm == 2)
-                    k_par_update<PHYS, R, 2><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
-                else
-                    k_par_update<PHYS, R, 3><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
+                with_tm(par_mask(a), [&](auto tm) {
+                    k_par_update<PHYS, R, decltype(tm)::value><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
+                });
             });
         CTU_MARK(nullptr);
     }

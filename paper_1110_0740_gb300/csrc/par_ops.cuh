@@ -1,7 +1,8 @@
 // par_ops.cuh -- the parabolic terms of the CTU step (Section 3.1 with
-// Pi != 0): classical isotropic thermal conduction (Eq. tc_flux with
-// q -> infinity, kappa_par = kappa_perp = kappa), Pi_E = kappa grad T with
-// T = p / rho, and isotropic viscosity (Eq. visc_tens, constant kinematic
+// Pi != 0): classical thermal conduction (Eq. tc_flux with q -> infinity),
+// Pi_E = kappa_perp grad T + (kappa_par - kappa_perp) b (b . grad T) with
+// T = p / rho and b the direction of the face's mean field, isotropic
+// viscosity (Eq. visc_tens, constant kinematic
 // viscosity nu), tau = rho nu (grad v + grad v^T - (2/3) I div v) with the
 // momentum flux Pi_m = tau and the energy flux Pi_E += v . tau, and
 // resistivity (constant eta), -curl(eta J) = div(eta (grad B^T - grad B)):
@@ -71,16 +72,23 @@ __device__ __forceinline__ void par_div1(const StepArgs &a, const DevPatch &P, c
     for (int q = 0; q < NV; ++q) s[gperm<D>(q)] += (Fm[q] - Fp[q]) * iD;
 }
 
-// (Gamma - 1) kappa, nu, kappa and eta in the working precision.
+// (Gamma - 1) max(kappa_perp, kappa_par), nu, kappa_perp, kappa_par -
+// kappa_perp and eta in the working precision.
 template <class R> __device__ __forceinline__ R par_gk(const StepArgs &a);
-template <> __device__ __forceinline__ double par_gk<double>(const StepArgs &a) { return (a.gam - 1.0) * a.kappa; }
-template <> __device__ __forceinline__ float par_gk<float>(const StepArgs &a) { return a.gm1f * a.kappaf; }
+template <> __device__ __forceinline__ double par_gk<double>(const StepArgs &a)
+{
+    return (a.gam - 1.0) * (a.kpar > a.kappa ? a.kpar : a.kappa);
+}
+template <> __device__ __forceinline__ float par_gk<float>(const StepArgs &a) { return a.gm1f * a.kmaxf; }
 template <class R> __device__ __forceinline__ R par_nu(const StepArgs &a);
 template <> __device__ __forceinline__ double par_nu<double>(const StepArgs &a) { return a.nu; }
 template <> __device__ __forceinline__ float par_nu<float>(const StepArgs &a) { return a.nuf; }
 template <class R> __device__ __forceinline__ R par_kappa(const StepArgs &a);
 template <> __device__ __forceinline__ double par_kappa<double>(const StepArgs &a) { return a.kappa; }
 template <> __device__ __forceinline__ float par_kappa<float>(const StepArgs &a) { return a.kappaf; }
+template <class R> __device__ __forceinline__ R par_dkappa(const StepArgs &a);
+template <> __device__ __forceinline__ double par_dkappa<double>(const StepArgs &a) { return a.kpar - a.kappa; }
+template <> __device__ __forceinline__ float par_dkappa<float>(const StepArgs &a) { return a.dkappaf; }
 template <class R> __device__ __forceinline__ R par_eta(const StepArgs &a);
 template <> __device__ __forceinline__ double par_eta<double>(const StepArgs &a) { return a.eta; }
 template <> __device__ __forceinline__ float par_eta<float>(const StepArgs &a) { return a.etaf; }
@@ -111,8 +119,9 @@ __device__ __forceinline__ void par_grad(const StepArgs &a, const DevPatch &P, l
 
 // Parabolic fluxes through the face between scratch cells c and c + e_d
 // (entries as NPAR).  get(f, i): field f of cell i; dif(f, i, j): field f of
-// cell i minus that of cell j.  TM: the terms beyond conduction compiled in,
-// bit 1 viscosity, bit 2 resistivity.
+// cell i minus that of cell j.  TM: the terms beyond isotropic conduction
+// compiled in, bit 1 viscosity, bit 2 resistivity, bit 4 anisotropic
+// conduction.
 template <class R, int TM, class Get, class Dif>
 __device__ __forceinline__ void par_face(const StepArgs &a, const DevPatch &P, long long c, int d, Get get,
                                          Dif dif, R (&Pi)[NPAR])
@@ -122,6 +131,27 @@ __device__ __forceinline__ void par_face(const StepArgs &a, const DevPatch &P, l
 #pragma unroll
     for (int q = 0; q < NPAR; ++q) Pi[q] = R(0);
     if (a.par_cond) Pi[3] = par_kappa<R>(a) * dif(4, cp, c) * ih;
+    if constexpr ((TM & 4) != 0) {
+        // anisotropic heat flux: + (kappa_par - kappa_perp) b (b . grad T),
+        // b the direction of the face's mean field (none where it vanishes)
+        R gt[3], bf[3];
+        R b2 = R(0), bg = R(0);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t == d) {
+                gt[t] = dif(4, cp, c) * ih;
+            } else if (t < a.ndim) {
+                const long long s2 = dstr(P, t);
+                gt[t] = (dif(4, c + s2, c - s2) + dif(4, cp + s2, cp - s2)) * (R(0.25) * pidx<R>(P, t));
+            } else {
+                gt[t] = R(0);
+            }
+            bf[t] = R(0.5) * (get(5 + t, c) + get(5 + t, cp));
+            b2 += bf[t] * bf[t];
+            bg += bf[t] * gt[t];
+        }
+        if (b2 > R(0)) Pi[3] += par_dkappa<R>(a) * bf[d] * bg / b2;
+    }
     if constexpr ((TM & 2) != 0) {
         {
             R g[3][3];  // g[t][i] = dB_i / dx_t at the face
@@ -221,7 +251,8 @@ __device__ __forceinline__ void par_shell_coords(const DevPatch &P, int ndim, in
 // almost all cells.  L1: the first-order divergences (global order, ndim >
 // 1); LP: L_P^n per scratch cell, 4 planes of R (momentum, energy); Wh: the
 // half-step fields (par_plane), doubles (FP64 path) or double-float pairs
-// (hi, lo) (mixed path).  TM: bit 1 viscosity, bit 2 resistivity.
+// (hi, lo) (mixed path).  TM: bit 1 viscosity, bit 2 resistivity, bit 4
+// anisotropic conduction (which needs the B fields).
 template <class R, bool SHELL, int TM>
 __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *LP,
                                                     double *Wh)
@@ -299,7 +330,7 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
 #pragma unroll
                 for (int q = 0; q < 3; ++q) Wh[(2 + q) * S + c] = U[1 + q] / rho;
             }
-            if constexpr ((TM & 2) != 0) {
+            if constexpr ((TM & 6) != 0) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) Wh[(5 + q) * S + c] = U[5 + q];
             }
@@ -333,7 +364,7 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
                     W2[(2 + q) * S + c] = make_float2(v.hi, v.lo);
                 }
             }
-            if constexpr ((TM & 2) != 0) {
+            if constexpr ((TM & 6) != 0) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) W2[(5 + q) * S + c] = make_float2(U[5 + q].hi, U[5 + q].lo);
             }
@@ -437,7 +468,7 @@ __global__ void __launch_bounds__(BLOCK) k_par_update(StepArgs a, GroupTable gt,
             const unsigned int f = prim_any<PHYS, R>(U, a, V);
             if (f) atomicOr(a.status, f);
             m = cell_speed<PHYS, R>(V, a, P);
-            const R D = max(max(par_gk<R>(a) / V[0], R(4.0 / 3.0) * par_nu<R>(a)), par_eta<R>(a));
+            const R D = max(max(par_gk<R>(a) / V[0], R(4.0 / 3.0) * par_nu<R>(a)), par_eta<R>(a));  // par_gk: max kappa
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 if (d < a.ndim) m += R(2) * D * (pidx<R>(P, d) * pidx<R>(P, d));

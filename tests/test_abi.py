@@ -64,7 +64,7 @@ def test_parabolic_config_validation_without_gpu():
     L = ctu._lib()
     h = ctypes.c_void_p()
     for k in (-1e-3, float("inf"), float("nan")):
-        for kw in (dict(kappa=k), dict(nu=k), dict(eta=k)):
+        for kw in (dict(kappa=k), dict(nu=k), dict(eta=k), dict(kappa_par=k)):
             cfg = ctu.make_config(**kw)
             assert L.ctu_init(ctypes.byref(cfg), ctypes.byref(h)) == ctu.STATUS.index("CTU_EINVAL")
     bad = (dict(recon=ctu.CTU_WENO3), dict(recon=ctu.CTU_LINEAR_MINMOD), dict(trace_mode=ctu.CTU_TRACE_CENTER),
@@ -72,11 +72,11 @@ def test_parabolic_config_validation_without_gpu():
            dict(physics=ctu.CTU_SRMHD, predictor=ctu.CTU_MUSCL_HANCOCK, riemann=ctu.CTU_HLL,
                 recon=ctu.CTU_LINEAR_MC, gamma=4.0 / 3.0))
     for kw in bad:
-        for par in (dict(kappa=0.01), dict(nu=0.01), dict(eta=0.01)):
+        for par in (dict(kappa=0.01), dict(nu=0.01), dict(eta=0.01), dict(kappa_par=0.01)):
             cfg = ctu.make_config(**par, **kw)
             assert L.ctu_init(ctypes.byref(cfg), ctypes.byref(h)) == ctu.STATUS.index("CTU_EUNSUPPORTED"), kw
     patches = ctu.make_patches([([8, 8, 8], [0.1] * 3, 0)])
-    for par in (dict(kappa=0.01), dict(nu=0.01), dict(eta=0.01)):
+    for par in (dict(kappa=0.01), dict(nu=0.01), dict(eta=0.01), dict(kappa_par=0.01)):
         cfg = ctu.make_config(**par)
         st = L.ctu_step_noalloc(ctypes.byref(cfg), 16, 32, 4096, patches, 1, 48, 0, 0)
         assert st == ctu.STATUS.index("CTU_EUNSUPPORTED")

@@ -213,3 +213,27 @@ def test_parabolic_flux_registers(prec, nu, eta):
     G = Uo.cpu().numpy().reshape(U0.shape)
     e = l1rel(O.interior(G, n, 3), O.interior(R, n, 3), ch)
     assert np.all(e <= (TOL64 if prec == 0 else 2e-5)), e
+
+
+@pytest.mark.parametrize("case", ["blast3d", "turb2d"])
+def test_anisotropic_conduction(case):
+    """Conduction along the field (kappa_par) ten times that across it, alone
+    and with viscosity and resistivity: FP64 at 1e-11 and mixed at the plain
+    step's bars, against the oracle."""
+    if case == "blast3d":
+        n, U0, dx, steps, cfl, recon, tol = [24] * 3, W.mhd_blast_3d(24, seed=35), [1 / 24] * 3, 4, 0.3, 1, 2e-5
+        nd = 3
+    else:
+        n, U0, dx, steps, cfl, recon, tol = [48, 48, 1], W.mhd_turb_2d(48, seed=36), [1 / 48] * 2, 10, 0.4, 0, 1e-4
+        nd = 2
+    for kw in (dict(kappa=0.002, kappa_par=0.02), dict(kappa=0.0, kappa_par=0.01, nu=0.003, eta=0.003)):
+        ref, od = oracle_run(U0, n, nd, dx, steps, cfl, recon=recon, **kw)
+        iso, _ = oracle_run(U0, n, nd, dx, steps, cfl, recon=recon, kappa=kw["kappa_par"],
+                            nu=kw.get("nu", 0.0), eta=kw.get("eta", 0.0))
+        R = O.interior(ref, n, nd)
+        assert np.abs(R[4] - O.interior(iso, n, nd)[4]).sum() > 1e-5 * np.abs(R[4]).sum()
+        for prec, t in ((0, TOL64), (1, tol)):
+            got, _, st = gpu_run(U0, n, nd, dx, steps, cfl, precision=prec, recon=recon, **kw)
+            assert st == 0
+            e = l1rel(O.interior(got, n, nd), R, od[-1][1])
+            assert np.all(e <= t), (kw, prec, e)
