@@ -70,13 +70,13 @@ def lib():
                                      ctypes.POINTER(ctypes.c_long), P, I, P, I, I, D, I, D]
         L.or_mhd_step_par.restype = I
         L.or_mhd_step_par.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, I, I,
-                                      ctypes.POINTER(ctypes.c_long), P, I, P, I, I, D, I, D, D, D, D]
+                                      ctypes.POINTER(ctypes.c_long), P, I, P, I, I, D, I, D, D, D, D, D]
         L.or_mhd_max_rate.restype = D
         L.or_mhd_max_rate.argtypes = [P, I, I, I, I, D, D, D, D, D]
         L.or_mhd_max_rate_par.restype = D
         L.or_mhd_max_rate_par.argtypes = [P, I, I, I, I, D, D, D, D, D, D, D, D]
         L.or_mhd_parabolic.restype = None
-        L.or_mhd_parabolic.argtypes = [P, I, I, I, I, D, D, D, D, D, D, D, D, P]
+        L.or_mhd_parabolic.argtypes = [P, I, I, I, I, D, D, D, D, D, D, D, D, D, P]
         L.or_mhd_conduction.restype = None
         L.or_mhd_conduction.argtypes = [P, I, I, I, I, D, D, D, D, D, P]
         L.or_mhd_riemann_hllc.restype = I
@@ -302,14 +302,15 @@ def fill_outflow(U, n, ndim):
 
 def mhd_step(U, n, ndim, dx, dt, ch, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
              windows=None, reg=None, upwind=0, shock=None, riemann=0, kappa=0.0, nu=0.0, eta=0.0,
-             kappa_par=None):
+             kappa_par=None, phi=0.0):
     """One CTU step of a ghost-filled patch; returns (Unew, n_bad_states).
 
     windows: optional list of (d, f, a0, a1, b0, b1, dst, weight) flux-register
     windows accumulated into the float64 array `reg` (see or_mhd_step).
     kappa > 0: with isotropic thermal conduction; nu > 0: with isotropic
     viscosity; eta > 0: with resistivity (or_mhd_step_par).  kappa_par: the
-    conductivity along the field (None: kappa, isotropic)."""
+    conductivity along the field (None: kappa, isotropic); phi > 0: the
+    saturated heat flux."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     assert U.shape == shape(n, ndim), (U.shape, shape(n, ndim))
     Un = np.empty_like(U)
@@ -331,8 +332,8 @@ def mhd_step(U, n, ndim, dx, dt, ch, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
             win.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(wgt),
             nwin, regp, int(riemann), *sh)
     kpar = kappa if kappa_par is None else kappa_par
-    if nu > 0.0 or eta > 0.0 or kpar != kappa:
-        bad = lib().or_mhd_step_par(*args, float(kappa), float(kpar), float(nu), float(eta))
+    if nu > 0.0 or eta > 0.0 or kpar != kappa or phi > 0.0:
+        bad = lib().or_mhd_step_par(*args, float(kappa), float(kpar), float(phi), float(nu), float(eta))
     elif kappa > 0.0:
         bad = lib().or_mhd_step_tc(*args, float(kappa))
     else:
@@ -411,7 +412,7 @@ def mhd_max_rate(U, n, ndim, dx, gamma=5.0 / 3.0, kappa=0.0, nu=0.0, eta=0.0, ka
                                  float(dx[0]), float(dx[1]), float(dx[2]), float(gamma), float(kappa))
 
 
-def mhd_parabolic(U, n, ndim, dx, kappa, nu, gamma=5.0 / 3.0, eta=0.0, kappa_par=None):
+def mhd_parabolic(U, n, ndim, dx, kappa, nu, gamma=5.0 / 3.0, eta=0.0, kappa_par=None, phi=0.0):
     """L_P of conduction, viscosity and resistivity (or_mhd_parabolic) on the
     interior cells: array of the shape of U, momentum in components 1..3,
     energy in 4 and B in 5..7 (the rest and the ghosts 0)."""
@@ -420,7 +421,8 @@ def mhd_parabolic(U, n, ndim, dx, kappa, nu, gamma=5.0 / 3.0, eta=0.0, kappa_par
     LP = np.zeros(U.shape)
     lib().or_mhd_parabolic(_dp(U), int(n[0]), int(n[1]), int(n[2]), int(ndim), float(dx[0]), float(dx[1]),
                            float(dx[2]), float(gamma), float(kappa),
-                           float(kappa if kappa_par is None else kappa_par), float(nu), float(eta), _dp(LP))
+                           float(kappa if kappa_par is None else kappa_par), float(phi), float(nu), float(eta),
+                           _dp(LP))
     return LP
 
 
@@ -506,7 +508,7 @@ def euler_sample(left, right, gamma, xi):
 
 def mhd_run(U, n, ndim, dx, steps, cfl, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
             bc="periodic", t_end=None, upwind=0, shock=None, riemann=0, kappa=0.0, nu=0.0, eta=0.0,
-            kappa_par=None):
+            kappa_par=None, phi=0.0):
     """Advance a patch `steps` CTU steps (or up to t_end), filling ghosts each
     step; returns (U, t, dts)."""
     U = np.array(U, dtype=np.float64, copy=True)
@@ -527,7 +529,7 @@ def mhd_run(U, n, ndim, dx, steps, cfl, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
         if t_end is not None and t + dt > t_end:
             dt = t_end - t
         U, bad = mhd_step(U, n, ndim, dx, dt, ch, gamma, glm_alpha, recon, upwind=upwind, shock=shock,
-                          riemann=riemann, kappa=kappa, nu=nu, eta=eta, kappa_par=kappa_par)
+                          riemann=riemann, kappa=kappa, nu=nu, eta=eta, kappa_par=kappa_par, phi=phi)
         if bad:
             raise FloatingPointError(f"oracle met {bad} unphysical states at step {k}")
         t += dt

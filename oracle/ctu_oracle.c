@@ -908,7 +908,8 @@ double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
  *     limit q -> infinity with constant kappa_perp = kappa and kappa_par = kpar:
  *     Pi_E += kappa dT/dx_d + (kpar - kappa) b_d (b . grad T), b the unit
  *     vector of the face's mean field (isotropic where it vanishes or
- *     kpar = kappa);
+ *     kpar = kappa); with phi > 0 the saturated form of the paper's appendix
+ *     on the heat flux (below);
  *   - isotropic viscosity, the stress of Eq. (visc_tens) with constant
  *     kinematic viscosity nu:
  *     tau_(d,i) = rho nu (dv_i/dx_d + dv_d/dx_i - (2/3) delta_(di) div v),
@@ -927,13 +928,49 @@ double or_mhd_max_speed(const double *U, int nx, int ny, int nz, int ndim,
  *     J = curl B, and the energy flux -eta J x B of Section 2.1.1).
  * Pi[1..3] receive the momentum fluxes, Pi[4] the energy flux and Pi[5..7]
  * the fluxes of B.  W holds (rho, v_x, v_y, v_z, T, B_x, B_y, B_z). */
-static void parabolic_face(const grid_t *G, const double *W, const double *h, double kappa, double kpar, double nu,
-                           double eta, long id, int d, double *Pi)
+static void parabolic_face(const grid_t *G, const double *W, const double *h, double kappa, double kpar, double phi,
+                           double nu, double eta, long id, int d, double *Pi)
 {
     const long nc = G->ncell, st = dstride(G, d), ip = id + st;
     int q;
     for (q = 0; q < NVAR; q++)
         Pi[q] = 0.0;
+    if (phi > 0.0 && (kappa > 0.0 || kpar > 0.0)) {
+        /* saturated conduction (the paper's appendix on the heat flux): the
+         * classical flux F = kappa_perp grad T + (kappa_par - kappa_perp)
+         * b (b . grad T) with the face gradient of T (normal two-point
+         * difference, transverse mean of central differences), the upwind
+         * saturated flux q = 5 phi p_u^(3/2) / sqrt(rho_f), p_u the pressure
+         * of the cell on the side F_d points away from (the left one when
+         * F_d < 0), and their harmonic mean q F_d / (|F| + q) */
+        const double *T = W + 4 * nc;
+        double gt[3], bf[3], b2 = 0.0, bg = 0.0, F[3], fm = 0.0, rf, pu, qs;
+        int t;
+        for (t = 0; t < 3; t++) {
+            if (t == d) {
+                gt[t] = (T[ip] - T[id]) / h[d];
+            } else if (t < G->ndim) {
+                const long s2 = dstride(G, t);
+                gt[t] = (T[id + s2] - T[id - s2] + T[ip + s2] - T[ip - s2]) / (4.0 * h[t]);
+            } else {
+                gt[t] = 0.0;
+            }
+            bf[t] = 0.5 * (W[(5 + t) * nc + id] + W[(5 + t) * nc + ip]);
+            b2 += bf[t] * bf[t];
+            bg += bf[t] * gt[t];
+        }
+        for (t = 0; t < 3; t++) {
+            F[t] = kappa * gt[t];
+            if (kpar != kappa && b2 > 0.0)
+                F[t] += (kpar - kappa) * bf[t] * bg / b2;
+            fm += F[t] * F[t];
+        }
+        fm = sqrt(fm);
+        rf = 0.5 * (W[id] + W[ip]);
+        pu = F[d] < 0.0 ? W[id] * T[id] : W[ip] * T[ip];
+        qs = 5.0 * phi * pu * sqrt(pu) / sqrt(rf);
+        Pi[4] += qs * F[d] / (fm + qs);
+    } else {
     if (kappa > 0.0 || kpar > 0.0)
         Pi[4] += kappa * (W[4 * nc + ip] - W[4 * nc + id]) / h[d];
     if (kpar != kappa) {
@@ -960,6 +997,7 @@ static void parabolic_face(const grid_t *G, const double *W, const double *h, do
                 bg += bf[t] * gt[t];
             Pi[4] += (kpar - kappa) * bf[d] * bg / b2;
         }
+    }
     }
     if (nu > 0.0) {
         double grad[3][3], div = 0.0, rf, vf[3];
@@ -1018,8 +1056,8 @@ static void parabolic_face(const grid_t *G, const double *W, const double *h, do
 /* L_P = sum_d (Pi_(d,+) - Pi_(d,-)) / dx_d (Eq. incrementop_par, Cartesian)
  * for the momentum, the energy and B, LP[q * ncell + id] (q = 1..7), on the
  * cells lo <= c <= hi; the other entries are left as they are. */
-static void parabolic_lp(const grid_t *G, const double *W, const double *h, double kappa, double kpar, double nu,
-                         double eta, const int *lo, const int *hi, double *LP)
+static void parabolic_lp(const grid_t *G, const double *W, const double *h, double kappa, double kpar, double phi,
+                         double nu, double eta, const int *lo, const int *hi, double *LP)
 {
     int c[3], d, q;
     for (c[2] = lo[2]; c[2] <= hi[2]; c[2]++)
@@ -1028,8 +1066,8 @@ static void parabolic_lp(const grid_t *G, const double *W, const double *h, doub
                 long id = cidx(G, c);
                 double s[NVAR] = {0}, Pp[NVAR], Pm[NVAR];
                 for (d = 0; d < G->ndim; d++) {
-                    parabolic_face(G, W, h, kappa, kpar, nu, eta, id, d, Pp);
-                    parabolic_face(G, W, h, kappa, kpar, nu, eta, id - dstride(G, d), d, Pm);
+                    parabolic_face(G, W, h, kappa, kpar, phi, nu, eta, id, d, Pp);
+                    parabolic_face(G, W, h, kappa, kpar, phi, nu, eta, id - dstride(G, d), d, Pm);
                     for (q = 1; q <= 7; q++)
                         s[q] += (Pp[q] - Pm[q]) / h[d];
                 }
@@ -1064,7 +1102,7 @@ static int parabolic_fields(const grid_t *G, const double *U, double gam, double
  * energy (q = 4) and B (q = 5..7), ghosted layout (the other entries are
  * 0). */
 void or_mhd_parabolic(const double *U, int nx, int ny, int nz, int ndim, double dx, double dy, double dz,
-                      double gam, double kappa, double kpar, double nu, double eta, double *LP)
+                      double gam, double kappa, double kpar, double phi, double nu, double eta, double *LP)
 {
     grid_t G;
     double h[3] = {dx, dy, dz};
@@ -1076,7 +1114,7 @@ void or_mhd_parabolic(const double *U, int nx, int ny, int nz, int ndim, double 
     W = (double *)malloc(sizeof(double) * 8 * G.ncell);
     parabolic_fields(&G, U, gam, W);
     memset(LP, 0, sizeof(double) * NVAR * G.ncell);
-    parabolic_lp(&G, W, h, kappa, kpar, nu, eta, lo, hi, LP);
+    parabolic_lp(&G, W, h, kappa, kpar, phi, nu, eta, lo, hi, LP);
     free(W);
 }
 
@@ -1088,7 +1126,7 @@ void or_mhd_conduction(const double *U, int nx, int ny, int nz, int ndim, double
     double *A;
     grid_init(&G, nx, ny, nz, ndim);
     A = (double *)malloc(sizeof(double) * NVAR * G.ncell);
-    or_mhd_parabolic(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, kappa, 0.0, 0.0, A);
+    or_mhd_parabolic(U, nx, ny, nz, ndim, dx, dy, dz, gam, kappa, kappa, 0.0, 0.0, 0.0, A);
     memcpy(LP, A + 4 * G.ncell, sizeof(double) * G.ncell);
     free(A);
 }
@@ -1147,8 +1185,8 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                      double dx, double dy, double dz, double dt, double ch,
                      double gam, double glm_alpha, int recon, int upwind,
                      const long *win, const double *wgt, int nwin, double *reg,
-                     int solver, int shock, double eps_q, int qkind, double kappa, double kpar, double nu,
-                     double eta)
+                     int solver, int shock, double eps_q, int qkind, double kappa, double kpar, double phi,
+                     double nu, double eta)
 {
     const int par = kappa > 0.0 || kpar > 0.0 || nu > 0.0 || eta > 0.0;
     unsigned char *flags = NULL;
@@ -1191,7 +1229,7 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                 Wn[q * nc + id] = V[q * nc + id];
             Wn[4 * nc + id] = V[4 * nc + id] / V[id];
         }
-        parabolic_lp(&G, Wn, h, kappa, kpar, nu, eta, ring_lo, ring_hi, LPn);
+        parabolic_lp(&G, Wn, h, kappa, kpar, phi, nu, eta, ring_lo, ring_hi, LPn);
     }
 
     /* 2. first-order Godunov fluxes F^n_d = R(U_c, U_(c+e_d)) on the faces the
@@ -1337,7 +1375,7 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                 }
         for (d = 0; d < 3; d++)
             ihi[d] = G.n[d] - 1;
-        parabolic_lp(&G, Wh, h, kappa, kpar, nu, eta, ilo, ihi, LPh);
+        parabolic_lp(&G, Wh, h, kappa, kpar, phi, nu, eta, ilo, ihi, LPh);
     }
 
     /* 5. conservative update, Eq. (update): U + dt * (L_x + L_y + L_z) (+ L_P) */
@@ -1385,7 +1423,7 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                      * F - Pi^(n+1/2) (momentum, energy and B) */
                     if (Wh && q >= 1 && q <= 7) {
                         double Pi[NVAR];
-                        parabolic_face(&G, Wh, h, kappa, kpar, nu, eta, id, wd, Pi);
+                        parabolic_face(&G, Wh, h, kappa, kpar, phi, nu, eta, id, wd, Pi);
                         flux -= Pi[q];
                     }
                     reg[W[6] + (q * nb + jb) * na + ja] += wgt[w] * dt * area * flux;
@@ -1420,11 +1458,11 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
                    int solver, int shock, double eps_q, int qkind)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, 0.0, 0.0, 0.0, 0.0);
+                     nwin, reg, solver, shock, eps_q, qkind, 0.0, 0.0, 0.0, 0.0, 0.0);
 }
 
 /* or_mhd_step_ex with thermal conduction of conductivities kappa >= 0 across
- * and kpar >= 0 along the field, viscosity of kinematic viscosity nu >= 0
+ * and kpar >= 0 along the field (saturated with phi > 0), viscosity of kinematic viscosity nu >= 0
  * and resistivity eta >= 0 (the
  * parabolic terms; see step_core and parabolic_face).  The flux registers
  * take the fluxes F - Pi^(n+1/2) of the momentum, the energy and B through
@@ -1433,11 +1471,11 @@ int or_mhd_step_par(const double *U, double *Unew, int nx, int ny, int nz, int n
                     double dx, double dy, double dz, double dt, double ch,
                     double gam, double glm_alpha, int recon, int upwind,
                     const long *win, const double *wgt, int nwin, double *reg,
-                    int solver, int shock, double eps_q, int qkind, double kappa, double kpar, double nu,
-                    double eta)
+                    int solver, int shock, double eps_q, int qkind, double kappa, double kpar, double phi,
+                    double nu, double eta)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, kappa, kpar, nu, eta);
+                     nwin, reg, solver, shock, eps_q, qkind, kappa, kpar, phi, nu, eta);
 }
 
 /* or_mhd_step_par with conduction alone. */
@@ -1448,7 +1486,7 @@ int or_mhd_step_tc(const double *U, double *Unew, int nx, int ny, int nz, int nd
                    int solver, int shock, double eps_q, int qkind, double kappa)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, kappa, kappa, 0.0, 0.0);
+                     nwin, reg, solver, shock, eps_q, qkind, kappa, kappa, 0.0, 0.0, 0.0);
 }
 
 /* ------------------------------------------------------------------ */

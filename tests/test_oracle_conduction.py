@@ -374,3 +374,88 @@ def test_anisotropic_oblique_field_quadratic_closed_form():
     Y = O.interior((y + 0 * T)[None], n, 2)[0]
     want = 2 * c * kperp * Y + (kpar - kperp) * c * (Y + 2 * X)
     assert np.allclose(LP[4], want, rtol=0, atol=1e-11)
+
+
+# ------------------------------------------------------------- saturated flux
+# The paper's appendix on the heat flux: F_c = q F_class / (|F_class| + q) at
+# each face, q = 5 phi p_u^(3/2) / sqrt(rho_f) with p_u upwind of F_class.
+
+def test_saturation_off_in_the_classical_limit():
+    """q >> |F_class| (phi huge): the harmonic mean is the classical flux."""
+    N = 12
+    n = [N, N, 1]
+    U = W.mhd_turb_2d(N, seed=8)
+    O.fill_periodic(U, n, 2)
+    dx = [1.0 / N] * 2
+    a = O.mhd_parabolic(U, n, 2, dx, 0.01, 0.0, G, kappa_par=0.05)
+    b = O.mhd_parabolic(U, n, 2, dx, 0.01, 0.0, G, kappa_par=0.05, phi=1e30)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-14 * np.abs(a).max())
+
+
+@pytest.mark.parametrize("sign", [-1.0, 1.0])
+def test_saturated_limit_upwind_closed_form(sign):
+    """q << |F_class| (phi tiny): each face carries q in the direction of
+    F_class, from the pressure of the upwind cell, so for T = 2 + s a x and
+    rho = 1 + 0.3 x (p = rho T): L_P = 5 phi s (p_u(i+1/2)^1.5 / sqrt(rho_(i+1/2))
+    - p_u(i-1/2)^1.5 / sqrt(rho_(i-1/2))) / dx, p_u the left cell's pressure
+    for s < 0 and the right cell's for s > 0 (to a relative q/|F| ~ 1e-9)."""
+    N = 16
+    n = [N, 1, 1]
+    h = 1.0 / N
+    x = _centres(n, 1, 0)
+    rho = 1.0 + 0.3 * x
+    T = 2.0 + sign * 0.5 * x
+    U = _prim_to_U(n, 1, rho + 0 * x, 0.0, rho * T)
+    kappa, phi = 1.0, 1e-10
+    LP = O.interior(O.mhd_parabolic(U, n, 1, [h], kappa, 0.0, G, phi=phi), n, 1)[4, 0, 0]
+    p = (rho * T)[0, 0]
+    r = rho[0, 0]
+    g = 4
+    i = np.arange(g, g + N)
+    up = (i if sign < 0 else i + 1)      # the upwind cell of face i + 1/2
+    um = (i - 1 if sign < 0 else i)      # of face i - 1/2
+    qp = 5 * phi * p[up] ** 1.5 / np.sqrt(0.5 * (r[i] + r[i + 1]))
+    qm = 5 * phi * p[um] ** 1.5 / np.sqrt(0.5 * (r[i - 1] + r[i]))
+    want = sign * (qp - qm) / h
+    assert np.allclose(LP, want, rtol=1e-7, atol=0)
+
+
+def test_saturated_conservation_periodic():
+    N = 16
+    n = [N, N, 1]
+    U = W.mhd_turb_2d(N, seed=9)
+    dx = [1.0 / N] * 2
+    a = O.interior(U, n, 2).copy()
+    R, t, _ = O.mhd_run(U, n, 2, dx, 6, 0.3, recon=1, kappa=0.05, phi=0.05)
+    b = O.interior(R, n, 2)
+    for q in range(8):
+        assert abs(b[q].sum() - a[q].sum()) <= 1e-13 * (np.abs(a[q]).sum() + 1.0), q
+    R0, _, _ = O.mhd_run(U, n, 2, dx, 6, 0.3, recon=1, kappa=0.05)
+    assert np.abs(O.interior(R0, n, 2)[4] - b[4]).max() > 1e-6
+
+
+def test_saturated_harmonic_mean_uses_the_flux_vector():
+    """2-D, T = 2 + a x + b y with p = 1 (rho = 1 / T): F_class = kappa (a, b)
+    at every face, exactly, and in the intermediate regime (q ~ |F|) each face
+    carries q F_d / (kappa sqrt(a^2 + b^2) + q), q = 5 phi / sqrt(rho_f)."""
+    n = [12, 10, 1]
+    dx = [1 / 12, 1 / 10]
+    a, b, kappa = 0.6, -0.8, 1.0
+    x, y = _centres(n, 2, 0), _centres(n, 2, 1)
+    T = 2.0 + a * x + b * y + 0 * x * y
+    rho = 1.0 / T
+    U = _prim_to_U(n, 2, rho, 0.0, rho * T)
+    fm = kappa * np.hypot(a, b)
+    phi = fm / 7.0
+    LP = O.interior(O.mhd_parabolic(U, n, 2, dx, kappa, 0.0, G, phi=phi), n, 2)[4, 0]
+    r = rho[0]
+    g = 4
+    j, i = np.meshgrid(np.arange(g, g + n[1]), np.arange(g, g + n[0]), indexing="ij")
+
+    def face(Fd, rl, rr):
+        q = 5 * phi / np.sqrt(0.5 * (rl + rr))
+        return q * Fd / (fm + q)
+
+    want = ((face(kappa * a, r[j, i], r[j, i + 1]) - face(kappa * a, r[j, i - 1], r[j, i])) / dx[0]
+            + (face(kappa * b, r[j, i], r[j + 1, i]) - face(kappa * b, r[j - 1, i], r[j, i])) / dx[1])
+    assert np.allclose(LP, want, rtol=1e-10, atol=1e-12)
