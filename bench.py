@@ -219,7 +219,8 @@ def run_ours(args):
         c = ctu.Ctx(ctu.make_config(ndim=3, recon=RECONS[args.recon], precision=prec, cfl=0.3,
                                     shock=(args.shock, 0) if args.shock else None,
                                     riemann=ctu.CTU_HLLC if args.riemann == "hllc" else ctu.CTU_HLLD,
-                                    kappa=args.kappa, nu=args.nu, eta=args.eta, kappa_par=args.kappa_par))
+                                    kappa=args.kappa, nu=args.nu, eta=args.eta, kappa_par=args.kappa_par,
+                                    tc_phi=args.tc_phi))
         c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
         if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
@@ -408,6 +409,7 @@ def run_ours(args):
                            + ("; HLLC in place of HLLD" if args.riemann == "hllc" else "")
                            + (f"; thermal conduction, kappa {args.kappa}" if args.kappa else "")
                            + (f" (along the field {args.kappa_par})" if args.kappa_par else "")
+                           + (f", saturated (phi {args.tc_phi})" if args.tc_phi else "")
                            + (f"; viscosity, nu {args.nu}" if args.nu else "")
                            + (f"; resistivity, eta {args.eta}" if args.eta else ""),
                            "recon": args.recon, "shock_eps": args.shock or None,
@@ -939,6 +941,8 @@ def main():
                     help="blast: viscosity with this kinematic viscosity (0 = off)")
     ap.add_argument("--kappa-par", type=float, default=0.0,
                     help="blast: thermal conductivity along the field, --kappa then across it (0 = isotropic)")
+    ap.add_argument("--tc-phi", type=float, default=0.0,
+                    help="blast: saturation parameter phi of the heat flux (0 = classical)")
     ap.add_argument("--eta", type=float, default=0.0,
                     help="blast: resistivity with this magnetic diffusivity (0 = off)")
     ap.add_argument("--shock", type=float, default=0.0,

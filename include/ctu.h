@@ -201,6 +201,13 @@ typedef struct {
      * The CFL diffusion coefficient takes max(kappa, kappa_par).  Same
      * combinations as kappa. */
     double kappa_par;
+    /* Saturated conduction (the paper's appendix on the heat flux): tc_phi > 0
+     * the parameter phi of the saturated flux q = 5 phi rho c_iso^3.  Each face
+     * carries q F_d / (|F| + q), F the classical flux above (its full face
+     * gradient of T), q = 5 phi p_u^(3/2) / sqrt(rho_f) with p_u the pressure of
+     * the upwind cell (the left one when F_d < 0) and rho_f the mean density.
+     * 0 = classical.  The CFL rate keeps the classical coefficients. */
+    double tc_phi;
 } ctu_config;
 
 typedef struct {

@@ -331,7 +331,7 @@ static ScratchOffsets scratch_offsets(const ctu_ctx *ctx)
     ScratchOffsets o;
     o.flags = align256((size_t)SCRATCH_ARRAYS * S * elt);
     const double kpar = ctx->cfg.kappa_par > 0.0 ? ctx->cfg.kappa_par : ctx->cfg.kappa;
-    const bool tensor = ctx->cfg.nu > 0.0 || ctx->cfg.eta > 0.0 || kpar != ctx->cfg.kappa;
+    const bool tensor = ctx->cfg.nu > 0.0 || ctx->cfg.eta > 0.0 || kpar != ctx->cfg.kappa || ctx->cfg.tc_phi > 0.0;
     const bool par = ctx->cfg.kappa > 0.0 || kpar > 0.0 || tensor;
     o.lp = align256(o.flags + (ctx->cfg.shock_detect ? S : 0));
     o.th = align256(o.lp + (par ? 7 * S * elt : 0));
@@ -387,6 +387,9 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.par_visc = ctx->cfg.nu > 0.0;
     a.par_res = ctx->cfg.eta > 0.0;
     a.par_aniso = a.kpar != a.kappa;
+    a.phi = ctx->cfg.tc_phi;
+    a.phif = (float)ctx->cfg.tc_phi;
+    a.par_sat = a.par_cond && ctx->cfg.tc_phi > 0.0;
     a.gm1lo = tm ? 0.0f : (float)((ctx->cfg.gamma - 1.0) - (double)a.gm1f);
     a.lp = nullptr;
     a.th = nullptr;
@@ -521,7 +524,8 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
             return CTU_EUNSUPPORTED;
     }
     if (!(cfg->kappa >= 0.0 && cfg->kappa < INFINITY) || !(cfg->nu >= 0.0 && cfg->nu < INFINITY) ||
-        !(cfg->eta >= 0.0 && cfg->eta < INFINITY) || !(cfg->kappa_par >= 0.0 && cfg->kappa_par < INFINITY))
+        !(cfg->eta >= 0.0 && cfg->eta < INFINITY) || !(cfg->kappa_par >= 0.0 && cfg->kappa_par < INFINITY) ||
+        !(cfg->tc_phi >= 0.0 && cfg->tc_phi < INFINITY))
         return CTU_EINVAL;
     // the parabolic terms: ideal MHD, PPM or MC-linear, HLLD, tracing without
     // or with the w_(+/-) reference, no hybrid integration, FP64 or CTU_MIXED

@@ -83,10 +83,12 @@ struct StepArgs {
     // working precision: momentum, energy, B) and the half-step fields
     // (planes of 8 bytes: T, then rho, v and B with viscosity or resistivity)
     double kappa, kpar, nu, eta;  // kappa: across the field (all directions when isotropic)
+    double phi;                   // saturation parameter of the heat flux (par_sat)
+    float phif;
     float kappaf, nuf, etaf;      // kappa, nu, eta in float
     float dkappaf, kmaxf;         // kpar - kappa, max(kappa, kpar) in float
     float gm1lo;                  // (Gamma-1) - gm1f in float: Gamma-1 as a double-float pair
-    int par_cond, par_visc, par_res, par_aniso;
+    int par_cond, par_visc, par_res, par_aniso, par_sat;
     const void *lp;
     double *th;
     const double *U;       // pool in

@@ -48,11 +48,11 @@ static int over_groups(const LaunchInfo &li, BPP bpp, GO go)
 }
 
 // The parabolic kernels' term mask (bit 1 viscosity, bit 2 resistivity, bit
-// 4 anisotropic conduction) and a call of f with it as a compile-time
+// 4 anisotropic or saturated conduction) and a call of f with it as a compile-time
 // constant.
 static inline int par_mask(const StepArgs &a)
 {
-    return (a.par_visc ? 1 : 0) | (a.par_res ? 2 : 0) | (a.par_aniso ? 4 : 0);
+    return (a.par_visc ? 1 : 0) | (a.par_res ? 2 : 0) | (a.par_aniso || a.par_sat ? 4 : 0);
 }
 template <class F> static void with_tm(int tm, F &&f)
 {

@@ -1,8 +1,8 @@
 // par_ops.cuh -- the parabolic terms of the CTU step (Section 3.1 with
-// Pi != 0): classical thermal conduction (Eq. tc_flux with q -> infinity),
-// Pi_E = kappa_perp grad T + (kappa_par - kappa_perp) b (b . grad T) with
-// T = p / rho and b the direction of the face's mean field, isotropic
-// viscosity (Eq. visc_tens, constant kinematic
+// Pi != 0): thermal conduction, Pi_E = kappa_perp grad T + (kappa_par -
+// kappa_perp) b (b . grad T) (the classical flux of Eq. tc_flux, T = p / rho,
+// b the direction of the face's mean field), saturated on request as in the
+// paper's appendix on the heat flux, isotropic viscosity (Eq. visc_tens, constant kinematic
 // viscosity nu), tau = rho nu (grad v + grad v^T - (2/3) I div v) with the
 // momentum flux Pi_m = tau and the energy flux Pi_E += v . tau, and
 // resistivity (constant eta), -curl(eta J) = div(eta (grad B^T - grad B)):
@@ -89,6 +89,9 @@ template <> __device__ __forceinline__ float par_kappa<float>(const StepArgs &a)
 template <class R> __device__ __forceinline__ R par_dkappa(const StepArgs &a);
 template <> __device__ __forceinline__ double par_dkappa<double>(const StepArgs &a) { return a.kpar - a.kappa; }
 template <> __device__ __forceinline__ float par_dkappa<float>(const StepArgs &a) { return a.dkappaf; }
+template <class R> __device__ __forceinline__ R par_phi(const StepArgs &a);
+template <> __device__ __forceinline__ double par_phi<double>(const StepArgs &a) { return a.phi; }
+template <> __device__ __forceinline__ float par_phi<float>(const StepArgs &a) { return a.phif; }
 template <class R> __device__ __forceinline__ R par_eta(const StepArgs &a);
 template <> __device__ __forceinline__ double par_eta<double>(const StepArgs &a) { return a.eta; }
 template <> __device__ __forceinline__ float par_eta<float>(const StepArgs &a) { return a.etaf; }
@@ -120,8 +123,8 @@ __device__ __forceinline__ void par_grad(const StepArgs &a, const DevPatch &P, l
 // Parabolic fluxes through the face between scratch cells c and c + e_d
 // (entries as NPAR).  get(f, i): field f of cell i; dif(f, i, j): field f of
 // cell i minus that of cell j.  TM: the terms beyond isotropic conduction
-// compiled in, bit 1 viscosity, bit 2 resistivity, bit 4 anisotropic
-// conduction.
+// compiled in, bit 1 viscosity, bit 2 resistivity, bit 4 the full face
+// gradient of T (anisotropic or saturated conduction).
 template <class R, int TM, class Get, class Dif>
 __device__ __forceinline__ void par_face(const StepArgs &a, const DevPatch &P, long long c, int d, Get get,
                                          Dif dif, R (&Pi)[NPAR])
@@ -130,10 +133,14 @@ __device__ __forceinline__ void par_face(const StepArgs &a, const DevPatch &P, l
     const R ih = pidx<R>(P, d);
 #pragma unroll
     for (int q = 0; q < NPAR; ++q) Pi[q] = R(0);
-    if (a.par_cond) Pi[3] = par_kappa<R>(a) * dif(4, cp, c) * ih;
-    if constexpr ((TM & 4) != 0) {
-        // anisotropic heat flux: + (kappa_par - kappa_perp) b (b . grad T),
-        // b the direction of the face's mean field (none where it vanishes)
+    if constexpr ((TM & 4) == 0) {
+        if (a.par_cond) Pi[3] = par_kappa<R>(a) * dif(4, cp, c) * ih;
+    } else {
+        // the full face gradient of T: anisotropic and/or saturated flux.
+        // F = kappa_perp grad T + (kappa_par - kappa_perp) b (b . grad T), b
+        // the direction of the face's mean field (none where it vanishes);
+        // saturated: q F_d / (|F| + q), q = 5 phi p_u^(3/2) / sqrt(rho_f), p_u
+        // the upwind pressure (the left cell's when F_d < 0)
         R gt[3], bf[3];
         R b2 = R(0), bg = R(0);
 #pragma unroll
@@ -146,11 +153,26 @@ __device__ __forceinline__ void par_face(const StepArgs &a, const DevPatch &P, l
             } else {
                 gt[t] = R(0);
             }
-            bf[t] = R(0.5) * (get(5 + t, c) + get(5 + t, cp));
+            bf[t] = a.par_aniso ? R(0.5) * (get(5 + t, c) + get(5 + t, cp)) : R(0);
             b2 += bf[t] * bf[t];
             bg += bf[t] * gt[t];
         }
-        if (b2 > R(0)) Pi[3] += par_dkappa<R>(a) * bf[d] * bg / b2;
+        const R kp = par_kappa<R>(a);
+        const R ak = b2 > R(0) ? par_dkappa<R>(a) * bg / b2 : R(0);
+        R F[3], f2 = R(0);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            F[t] = kp * gt[t] + ak * bf[t];
+            f2 += F[t] * F[t];
+        }
+        if (a.par_sat) {
+            const R r0 = get(0, c), r1 = get(0, cp);
+            const R pu = F[d] < R(0) ? r0 * get(4, c) : r1 * get(4, cp);
+            const R qs = R(5) * par_phi<R>(a) * pu * sqrt(pu) / sqrt(R(0.5) * (r0 + r1));
+            Pi[3] = qs * F[d] / (sqrt(f2) + qs);
+        } else {
+            Pi[3] = F[d];
+        }
     }
     if constexpr ((TM & 2) != 0) {
         {
@@ -252,7 +274,7 @@ __device__ __forceinline__ void par_shell_coords(const DevPatch &P, int ndim, in
 // 1); LP: L_P^n per scratch cell, 4 planes of R (momentum, energy); Wh: the
 // half-step fields (par_plane), doubles (FP64 path) or double-float pairs
 // (hi, lo) (mixed path).  TM: bit 1 viscosity, bit 2 resistivity, bit 4
-// anisotropic conduction (which needs the B fields).
+// anisotropic or saturated conduction (which need the B and rho fields).
 template <class R, bool SHELL, int TM>
 __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *LP,
                                                     double *Wh)
@@ -325,8 +347,8 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
         if (f) atomicOr(a.status, f);
         Wh[c] = p / rho;
         {
+            if constexpr ((TM & 5) != 0) Wh[S + c] = rho;
             if constexpr ((TM & 1) != 0) {
-                Wh[S + c] = rho;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) Wh[(2 + q) * S + c] = U[1 + q] / rho;
             }
@@ -356,8 +378,8 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
         float2 *W2 = reinterpret_cast<float2 *>(Wh);
         W2[c] = make_float2(T.hi, T.lo);
         {
+            if constexpr ((TM & 5) != 0) W2[S + c] = make_float2(U[0].hi, U[0].lo);
             if constexpr ((TM & 1) != 0) {
-                W2[S + c] = make_float2(U[0].hi, U[0].lo);
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     const df v = df_div(U[1 + q], U[0]);

@@ -36,7 +36,8 @@ class ctu_config(ctypes.Structure):
                 ("trace_mode", ctypes.c_int), ("p_floor", ctypes.c_double),
                 ("rho_floor", ctypes.c_double), ("shock_detect", ctypes.c_int), ("shock_q", ctypes.c_int),
                 ("shock_eps", ctypes.c_double), ("kappa", ctypes.c_double),
-                ("nu", ctypes.c_double), ("eta", ctypes.c_double), ("kappa_par", ctypes.c_double)]
+                ("nu", ctypes.c_double), ("eta", ctypes.c_double), ("kappa_par", ctypes.c_double),
+                ("tc_phi", ctypes.c_double)]
 
 
 class ctu_patch(ctypes.Structure):
@@ -201,18 +202,19 @@ def _check(code, where):
 def make_config(ndim=3, gamma=5.0 / 3.0, recon=CTU_PPM, precision=CTU_FP64, cfl=0.3,
                 glm_alpha=0.1, trace_mode=CTU_TRACE_ALL, physics=CTU_MHD, riemann=CTU_HLLD,
                 predictor=CTU_CHAR_TRACE, eos=CTU_EOS_IDEAL, p_floor=0.0, rho_floor=0.0, shock=None,
-                kappa=0.0, nu=0.0, eta=0.0, kappa_par=0.0):
+                kappa=0.0, nu=0.0, eta=0.0, kappa_par=0.0, tc_phi=0.0):
     """shock: None (off) or (eps_q, q) for the hybrid integration, q = 0
     thermal or 1 magnetic pressure.  kappa: isotropic thermal conductivity,
     nu: kinematic viscosity, eta: resistivity (0 = off); kappa_par: the
-    conductivity along the field, kappa then across it (0 = isotropic)."""
+    conductivity along the field, kappa then across it (0 = isotropic);
+    tc_phi: saturation parameter of the heat flux (0 = classical)."""
     return ctu_config(physics=physics, eos=eos, gamma=gamma, ndim=ndim, recon=recon,
                       predictor=predictor, riemann=riemann, precision=precision, cfl=cfl,
                       glm_alpha=glm_alpha, nghost=4, trace_mode=trace_mode, p_floor=p_floor,
                       rho_floor=rho_floor, shock_detect=0 if shock is None else 1,
                       shock_q=0 if shock is None else int(shock[1]),
                       shock_eps=0.0 if shock is None else float(shock[0]), kappa=float(kappa), nu=float(nu), eta=float(eta),
-                      kappa_par=float(kappa_par))
+                      kappa_par=float(kappa_par), tc_phi=float(tc_phi))
 
 
 def make_patches(specs):

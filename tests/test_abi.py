@@ -64,7 +64,7 @@ def test_parabolic_config_validation_without_gpu():
     L = ctu._lib()
     h = ctypes.c_void_p()
     for k in (-1e-3, float("inf"), float("nan")):
-        for kw in (dict(kappa=k), dict(nu=k), dict(eta=k), dict(kappa_par=k)):
+        for kw in (dict(kappa=k), dict(nu=k), dict(eta=k), dict(kappa_par=k), dict(tc_phi=k)):
             cfg = ctu.make_config(**kw)
             assert L.ctu_init(ctypes.byref(cfg), ctypes.byref(h)) == ctu.STATUS.index("CTU_EINVAL")
     bad = (dict(recon=ctu.CTU_WENO3), dict(recon=ctu.CTU_LINEAR_MINMOD), dict(trace_mode=ctu.CTU_TRACE_CENTER),

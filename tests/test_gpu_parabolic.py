@@ -237,3 +237,21 @@ def test_anisotropic_conduction(case):
             assert st == 0
             e = l1rel(O.interior(got, n, nd), R, od[-1][1])
             assert np.all(e <= t), (kw, prec, e)
+
+
+def test_saturated_conduction():
+    """The saturated heat flux (harmonic mean with the upwind saturated flux),
+    isotropic and anisotropic, on the 3-D blast whose hot sphere saturates:
+    FP64 at 1e-11 and mixed at the plain step's bar, against the oracle."""
+    n, dx = [24] * 3, [1 / 24] * 3
+    U0 = W.mhd_blast_3d(24, seed=37)
+    for kw in (dict(kappa=0.02, phi=0.01), dict(kappa=0.002, kappa_par=0.02, phi=0.01)):
+        ref, od = oracle_run(U0, n, 3, dx, 4, 0.3, recon=1, **kw)
+        cls, _ = oracle_run(U0, n, 3, dx, 4, 0.3, recon=1, **{k: v for k, v in kw.items() if k != "phi"})
+        R = O.interior(ref, n, 3)
+        assert np.abs(R[4] - O.interior(cls, n, 3)[4]).sum() > 1e-5 * np.abs(R[4]).sum()
+        for prec, t in ((0, TOL64), (1, 2e-5)):
+            got, _, st = gpu_run(U0, n, 3, dx, 4, 0.3, precision=prec, recon=1, **kw)
+            assert st == 0
+            e = l1rel(O.interior(got, n, 3), R, od[-1][1])
+            assert np.all(e <= t), (kw, prec, e)
