@@ -95,13 +95,15 @@ def test_level_operators_reject_boxes_outside_the_patches():
                      ctu.make_level_boxes([_box(nf, nc, 0, 0, [0, 0, 0], [8, 8, 8], [0, 0, 0], 2)]))
 
 
-def test_two_level_hierarchy_on_the_gpu_conserves_and_matches_the_oracle():
+@pytest.mark.parametrize("par", [{}, dict(kappa=0.002, kappa_par=0.006, nu=0.001, eta=0.001)])
+def test_two_level_hierarchy_on_the_gpu_conserves_and_matches_the_oracle(par):
     """Coarse 32^2 periodic patch (flux registers, weight -1, on the four
     coarse faces of the interface) and a 32^2 fine patch (ratio 2, weight +1
     registers on its boundary) advanced in FP64 on the GPU: ctu_step on both
     levels (two fine substeps with ghosts from ctu_prolong at alpha = 0, 1/2),
     ctu_restrict, ctu_reflux.  The result matches the same sequence in the
-    oracle and conserves mass, momentum, energy and magnetic flux."""
+    oracle and conserves mass, momentum, energy and magnetic flux, also with
+    the parabolic terms (whose fluxes the registers carry)."""
     import torch
     from paper_1110_0740_gb300 import ctu
     Nc = 32
@@ -125,7 +127,11 @@ def test_two_level_hierarchy_on_the_gpu_conserves_and_matches_the_oracle():
         for plane in (0, nf[d]):
             fw.append((0, d, plane, 0, nf[a_], 0, 1, 1.0, off))
             off += 9 * nf[a_]
-    dt, ch = O.dt_ch(O.mhd_max_speed(U, nc, 2, [hc, hc]), [hc, hc], 2, 0.4)
+    opar = dict(par)
+    if "kappa_par" in opar:
+        opar["kappa_par"] = par["kappa_par"]
+    rate = (O.mhd_max_rate(U, nc, 2, [hc, hc], 5.0 / 3.0, **par) if par else O.mhd_max_speed(U, nc, 2, [hc, hc]))
+    dt, ch = O.dt_ch(rate, [hc, hc], 2, 0.4)
     origin = [lo, lo, 0]
     dev = _dev()
     # ---- GPU
@@ -135,7 +141,7 @@ def test_two_level_hierarchy_on_the_gpu_conserves_and_matches_the_oracle():
     tUf = torch.from_numpy(Uf0.reshape(9, -1)).to(dev)
     tUfn = torch.zeros_like(tUf)
     reg = torch.zeros(off, dtype=torch.float64, device=dev)
-    cfg = ctu.make_config(ndim=2, recon=ctu.CTU_LINEAR_MC, precision=ctu.CTU_FP64, cfl=0.4)
+    cfg = ctu.make_config(ndim=2, recon=ctu.CTU_LINEAR_MC, precision=ctu.CTU_FP64, cfl=0.4, **par)
     cc, cf = ctu.Ctx(cfg), ctu.Ctx(cfg)
     cc.flux_registers(reg, cw)
     cf.flux_registers(reg, fw)
@@ -171,11 +177,11 @@ def test_two_level_hierarchy_on_the_gpu_conserves_and_matches_the_oracle():
     regr = np.zeros(off)
     cw_o = [(d, f, a0, a1, b0, b1, dst, wgt) for (_, d, f, a0, a1, b0, b1, wgt, dst) in cw]
     fw_o = [(d, pl, a0, a1, b0, b1, dst, wgt) for (_, d, pl, a0, a1, b0, b1, wgt, dst) in fw]
-    Ucn, bad = O.mhd_step(U, nc, 2, [hc, hc, 1], dt, ch, recon=0, windows=cw_o, reg=regr)
+    Ucn, bad = O.mhd_step(U, nc, 2, [hc, hc, 1], dt, ch, recon=0, windows=cw_o, reg=regr, **opar)
     Uf = np.zeros(O.shape(nf, 2))
     O.prolong(U, Ucn, nc, 0.0, Uf, nf, [-4, -4, 0], [nf[0] + 4, nf[1] + 4, 1], origin, 2, 2)
     for q in range(2):
-        Uf, bad = O.mhd_step(Uf, nf, 2, [hf, hf, 1], dt / 2, ch, recon=0, windows=fw_o, reg=regr)
+        Uf, bad = O.mhd_step(Uf, nf, 2, [hf, hf, 1], dt / 2, ch, recon=0, windows=fw_o, reg=regr, **opar)
         for b in shells:
             O.prolong(U, Ucn, nc, (q + 1) / 2, Uf, nf, list(b.lo), list(b.hi), origin, 2, 2)
     O.restrict(Ucn, nc, Uf, nf, [lo, lo, 0], [hi, hi, 1], origin, 2, 2)

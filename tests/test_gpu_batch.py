@@ -180,9 +180,11 @@ def test_step_next_dt_matches_ctu_dt_of_result(prec):
     assert np.allclose(a, b, rtol=1e-13 if prec == 0 else 1e-6, atol=0), (a, b)
 
 
-def test_cuda_graph_replay_matches_direct_step():
+@pytest.mark.parametrize("par", [{}, dict(kappa=0.002, kappa_par=0.006, tc_phi=0.05, nu=0.001, eta=0.001)])
+def test_cuda_graph_replay_matches_direct_step(par):
     """A level step captured in a CUDA graph and replayed gives bitwise the
-    same result as the direct call (patch list bound before capture)."""
+    same result as the direct call (patch list bound before capture), also
+    with the parabolic terms."""
     import torch
     from paper_1110_0740_gb300 import ctu
     H = W.amr_hierarchy(seed=2, base=32, target=40)
@@ -191,7 +193,7 @@ def test_cuda_graph_replay_matches_direct_step():
     U = torch.from_numpy(lv["pool"]).to(dev)
     A, B = torch.zeros_like(U), torch.zeros_like(U)
     P = ctu.make_patches([(n, dx, b) for (n, dx, b, _) in lv["patches"]])
-    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_MIXED))
+    ctx = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=ctu.CTU_MIXED, **par))
     d = torch.zeros(2, dtype=torch.float64, device=dev)
     ctx.dt(U, U.shape[1], P, d)
     s = torch.cuda.Stream(device=dev)
