@@ -175,16 +175,14 @@ __device__ __forceinline__ void par_face(const StepArgs &a, const DevPatch &P, l
         }
     }
     if constexpr ((TM & 2) != 0) {
-        {
-            R g[3][3];  // g[t][i] = dB_i / dx_t at the face
-            par_grad<R>(a, P, c, cp, d, 5, dif, g);
-            const R eta = par_eta<R>(a);
+        R g[3][3];  // g[t][i] = dB_i / dx_t at the face
+        par_grad<R>(a, P, c, cp, d, 5, dif, g);
+        const R eta = par_eta<R>(a);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const R f = eta * (g[d][i] - g[i][d]);
-                Pi[4 + i] = f;
-                Pi[3] += R(0.5) * (get(5 + i, c) + get(5 + i, cp)) * f;
-            }
+        for (int i = 0; i < 3; ++i) {
+            const R f = eta * (g[d][i] - g[i][d]);
+            Pi[4 + i] = f;
+            Pi[3] += R(0.5) * (get(5 + i, c) + get(5 + i, cp)) * f;
         }
     }
     if constexpr ((TM & 1) != 0) {

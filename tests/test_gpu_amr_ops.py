@@ -127,9 +127,6 @@ def test_two_level_hierarchy_on_the_gpu_conserves_and_matches_the_oracle(par):
         for plane in (0, nf[d]):
             fw.append((0, d, plane, 0, nf[a_], 0, 1, 1.0, off))
             off += 9 * nf[a_]
-    opar = dict(par)
-    if "kappa_par" in opar:
-        opar["kappa_par"] = par["kappa_par"]
     rate = (O.mhd_max_rate(U, nc, 2, [hc, hc], 5.0 / 3.0, **par) if par else O.mhd_max_speed(U, nc, 2, [hc, hc]))
     dt, ch = O.dt_ch(rate, [hc, hc], 2, 0.4)
     origin = [lo, lo, 0]
@@ -177,11 +174,11 @@ def test_two_level_hierarchy_on_the_gpu_conserves_and_matches_the_oracle(par):
     regr = np.zeros(off)
     cw_o = [(d, f, a0, a1, b0, b1, dst, wgt) for (_, d, f, a0, a1, b0, b1, wgt, dst) in cw]
     fw_o = [(d, pl, a0, a1, b0, b1, dst, wgt) for (_, d, pl, a0, a1, b0, b1, wgt, dst) in fw]
-    Ucn, bad = O.mhd_step(U, nc, 2, [hc, hc, 1], dt, ch, recon=0, windows=cw_o, reg=regr, **opar)
+    Ucn, bad = O.mhd_step(U, nc, 2, [hc, hc, 1], dt, ch, recon=0, windows=cw_o, reg=regr, **par)
     Uf = np.zeros(O.shape(nf, 2))
     O.prolong(U, Ucn, nc, 0.0, Uf, nf, [-4, -4, 0], [nf[0] + 4, nf[1] + 4, 1], origin, 2, 2)
     for q in range(2):
-        Uf, bad = O.mhd_step(Uf, nf, 2, [hf, hf, 1], dt / 2, ch, recon=0, windows=fw_o, reg=regr, **opar)
+        Uf, bad = O.mhd_step(Uf, nf, 2, [hf, hf, 1], dt / 2, ch, recon=0, windows=fw_o, reg=regr, **par)
         for b in shells:
             O.prolong(U, Ucn, nc, (q + 1) / 2, Uf, nf, list(b.lo), list(b.hi), origin, 2, 2)
     O.restrict(Ucn, nc, Uf, nf, [lo, lo, 0], [hi, hi, 1], origin, 2, 2)
