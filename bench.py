@@ -491,7 +491,8 @@ def run_amr(args):
     reg = torch.zeros(max(off, 1), dtype=torch.float64, device=dev)
     ctxs, A, B, P, D = [], [], [], [], []
     for lev, lv in enumerate(L):
-        c = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3))
+        c = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=args.kappa,
+                                    nu=args.nu, eta=args.eta, kappa_par=args.kappa_par, tc_phi=args.tc_phi))
         pool = torch.from_numpy(lv["pool"]).to(dev)
         A.append(pool)
         B.append(pool.clone())
@@ -658,7 +659,11 @@ def run_amr(args):
                 "dtype": "f32+f64" if prec == ctu.CTU_MIXED else "f64", "data": "synthetic",
                 "config": {"workload": "batched AMR level advance: 3-level hierarchy, ratio 2, base "
                                        "128^3, PPM+HLLD+GLM, subcycled 1/2/4 in one CUDA graph, "
-                                       "coarse-fine flux registers",
+                                       "coarse-fine flux registers"
+                                       + (f"; parabolic terms kappa {args.kappa} (along the field "
+                                          f"{args.kappa_par or args.kappa}, phi {args.tc_phi}), nu {args.nu}, "
+                                          f"eta {args.eta}"
+                                          if (args.kappa or args.kappa_par or args.nu or args.eta) else ""),
                            "patches_per_level": [len(lv["patches"]) for lv in L],
                            "patch_sizes_per_level": hist, "cells_per_level": cells,
                            "cell_updates_per_coarse_step": upd, "windows_rank0": sum(len(w) for w in wins),
@@ -936,15 +941,16 @@ def main():
     ap.add_argument("--riemann", default="hlld", choices=["hlld", "hllc"],
                     help="blast: the Riemann solver (the workload uses HLLD)")
     ap.add_argument("--kappa", type=float, default=0.0,
-                    help="blast: thermal conduction with this conductivity (0 = off)")
+                    help="blast, amr: thermal conduction with this conductivity (0 = off)")
     ap.add_argument("--nu", type=float, default=0.0,
-                    help="blast: viscosity with this kinematic viscosity (0 = off)")
+                    help="blast, amr: viscosity with this kinematic viscosity (0 = off)")
     ap.add_argument("--kappa-par", type=float, default=0.0,
-                    help="blast: thermal conductivity along the field, --kappa then across it (0 = isotropic)")
+                    help="blast, amr: thermal conductivity along the field, --kappa then across it "
+                         "(0 = isotropic)")
     ap.add_argument("--tc-phi", type=float, default=0.0,
-                    help="blast: saturation parameter phi of the heat flux (0 = classical)")
+                    help="blast, amr: saturation parameter phi of the heat flux (0 = classical)")
     ap.add_argument("--eta", type=float, default=0.0,
-                    help="blast: resistivity with this magnetic diffusivity (0 = off)")
+                    help="blast, amr: resistivity with this magnetic diffusivity (0 = off)")
     ap.add_argument("--shock", type=float, default=0.0,
                     help="blast: the hybrid integration with this shock threshold (thermal pressure; 0 = off)")
     ap.add_argument("--recon", default="ppm", choices=sorted(RECONS),
