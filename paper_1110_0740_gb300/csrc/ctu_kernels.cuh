@@ -685,16 +685,18 @@ struct Tiles {
     {
         return ((long long)N[0] * N[1] * N[2] + BLOCK - 1) / BLOCK;
     }
-    static long long div1(const int *n, int ndim, int D, int w, int seg)
+    // ext: along D also the ring's layers -1 and n_D (k_div1's EXT)
+    static long long div1(const int *n, int ndim, int D, int w, int seg, bool ext = false)
     {
         const int r = BLOCK / w;
+        const int x2 = ext ? 2 : 0;
         if (D == 0) {
             const int e1 = ndim > 1 ? n[1] + 2 : 1, e2 = ndim > 2 ? n[2] + 2 : 1;
-            return (long long)((n[0] + w - 2) / (w - 1)) * ((e1 + r - 1) / r) * e2;
+            return (long long)((n[0] + x2 + w - 2) / (w - 1)) * ((e1 + r - 1) / r) * e2;
         }
         const int O = D == 1 ? 2 : 1;
         const int eO = ndim > O ? n[O] + 2 : 1;
-        const long long nseg = (n[D] + seg - 1) / seg;
+        const long long nseg = (n[D] + x2 + seg - 1) / seg;
         return (long long)((n[0] + 2 + w - 1) / w) * ((eO * nseg + r - 1) / r);
     }
     static long long sweep_x(const int *n, int w)
@@ -868,12 +870,13 @@ static __global__ void __launch_bounds__(BLOCK) k_minmod(StepArgs a, GroupTable 
 // First-order flux divergences L1_D = (F^n_(c - e_D/2) - F^n_(c + e_D/2)) / dx_D
 // (Eq. transv; F^n from the cell-centred states) on the cells that the
 // sweeps of the other directions trace: c_D in [0, n_D), the other active
-// coordinates in [-1, n].
+// coordinates in [-1, n]; with EXT (the parabolic terms' half-step state)
+// c_D in [-1, n_D] as well, the whole ring box.
 //   D = x: one thread per face; a tile of xw lanes along x yields xw - 1
 //          cells, the lower face of a cell arriving from the previous lane.
 //   D = y, z: one thread per segment of SEG cells marching along D with the
 //          previous face flux and cell state in registers.
-template <int PHYS, class R, int D, bool HYB = false, bool HLLC = false>
+template <int PHYS, class R, int D, bool HYB = false, bool HLLC = false, bool EXT = false>
 __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const R *Vs, R *L1)
 {
     const Where wh = locate(gt);
@@ -888,12 +891,13 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const
         const int out = t.xw - 1;
         const int e1 = a.ndim > 1 ? P.n[1] + 2 : 1, e2 = a.ndim > 2 ? P.n[2] + 2 : 1;
         const int lo1 = a.ndim > 1 ? -1 : 0, lo2 = a.ndim > 2 ? -1 : 0;
-        const int T0 = (P.n[0] + out - 1) / out, T1 = (e1 + t.rows - 1) / t.rows;
+        constexpr int X = EXT ? 1 : 0;
+        const int T0 = (P.n[0] + 2 * X + out - 1) / out, T1 = (e1 + t.rows - 1) / t.rows;
         const int tx = t.tx();
-        const int i = (b % T0) * out + tx;  // this lane's face lies between cells i - 1 and i
+        const int i = (b % T0) * out + tx - X;  // this lane's face lies between cells i - 1 and i
         const int j = ((b / T0) % T1) * t.rows + t.ty();
         const int k = b / (T0 * T1);
-        const bool face = j < e1 && k < e2 && i <= P.n[0];
+        const bool face = j < e1 && k < e2 && i <= P.n[0] + X;
         const long long c = face ? P.soff + lcell(P, i, lo1 + j, lo2 + k) : 0;  // cell i
         R F[NV];
         if (face) {
@@ -923,15 +927,16 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const
         }
     } else {
         constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
+        constexpr int X = EXT ? 1 : 0;
         const int nD = P.n[D];
         const int eO = a.ndim > O ? P.n[O] + 2 : 1, loO = a.ndim > O ? -1 : 0;
-        const int nseg = (nD + SEGL - 1) / SEGL;
+        const int nseg = (nD + 2 * X + SEGL - 1) / SEGL;
         const int T0 = (P.n[0] + 2 + t.xw - 1) / t.xw;
         const int x = (b % T0) * t.xw + t.tx() - 1;
         const int comb = (b / T0) * t.rows + t.ty();
         const int o = comb / nseg, seg = comb % nseg;
         if (x > P.n[0] || o >= eO) return;
-        const int j0 = seg * SEGL, j1 = min(j0 + SEGL, nD);
+        const int j0 = seg * SEGL - X, j1 = min(j0 + SEGL, nD + X);
         const int st = dstr(P, D);
         int cc[3];
         cc[0] = x;

@@ -125,34 +125,34 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
             });
         CTU_MARK(nullptr);
     }
-    if (a.ndim > 1) {  // first-order stage: the transverse terms of the sweeps
+    // first-order stage: the transverse terms of the sweeps; with the
+    // parabolic terms over the whole ring box and in every direction (their
+    // half-step state needs sum_d L_(H,d)^n there, also in 1-D)
+    constexpr bool EXT = recon_par(PPM);
+    constexpr bool HY = recon_hybrid(PPM), HC = recon_hllc(PPM);
+    if (a.ndim > 1 || EXT) {
         CTU_MARK("flux1");
         n += over_groups(
-            li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 0, G.xw, G.seg); },
-            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 0, recon_hybrid(PPM), recon_hllc(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
-        n += over_groups(
-            li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 1, G.xw, G.seg); },
-            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 1, recon_hybrid(PPM), recon_hllc(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+            li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 0, G.xw, G.seg, EXT); },
+            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 0, HY, HC, EXT><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+        if (a.ndim > 1)
+            n += over_groups(
+                li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 1, G.xw, G.seg, EXT); },
+                [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 1, HY, HC, EXT><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
         if (a.ndim > 2)
             n += over_groups(
-                li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 2, G.xw, G.seg); },
-                [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 2, recon_hybrid(PPM), recon_hllc(PPM)><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+                li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 2, G.xw, G.seg, EXT); },
+                [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 2, HY, HC, EXT><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
         CTU_MARK(nullptr);
     }
     if constexpr (recon_par(PPM)) {  // parabolic terms: L_P^n and the half-step fields
         CTU_MARK("par_half");
         auto half = [&](auto tm) {
             constexpr int V = decltype(tm)::value;
-            if (a.ndim > 1)
-                n += over_groups(
-                    li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
-                    [&](const GroupTable &gt, unsigned nb) {
-                        k_par_half<R, false, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
-                    });
             n += over_groups(
-                li, [&](const Group &G) { return ((long long)par_shell_cells(G.n, a.ndim) + BLOCK - 1) / BLOCK; },
+                li, [&](const Group &G) { return ((long long)par_ring_cells(G.n, a.ndim) + BLOCK - 1) / BLOCK; },
                 [&](const GroupTable &gt, unsigned nb) {
-                    k_par_half<R, true, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
+                    k_par_half<R, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
                 });
         };
         // one kernel per combination of the terms beyond isotropic conduction

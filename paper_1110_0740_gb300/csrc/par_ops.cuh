@@ -23,10 +23,9 @@
 //                and one layer around it): L_P^n from the primitive fields of
 //                U^n (the predictors of every direction add dt/2 L_P^n, Eq.
 //                transv), and the fields (T, rho, v, B) of the cell-centred
-//                U^(n+1/2) = U^n + dt/2 (sum_d L_(H,d)^n + L_P^n).  L_(H,d)^n is
-//                the first-order stage's divergence where that stage formed
-//                it; the ring's outer layer (a launch of its own, SHELL)
-//                solves the missing faces with the same solver
+//                U^(n+1/2) = U^n + dt/2 (sum_d L_(H,d)^n + L_P^n), L_(H,d)^n the
+//                first-order stage's divergences, which that stage forms on
+//                the whole ring box for these kernels
 //   k_par_update U^(n+1) += dt L_P^(n+1/2) on the interior (Eq. update), the
 //                flux registers' momentum, energy and B take -dt A Pi, and on
 //                request the CFL rate of the result (with the diffusion
@@ -50,27 +49,6 @@ __host__ __device__ __forceinline__ int par_plane(int f) { return f == 4 ? 0 : (
 // Entries of L_P and of a face's Pi: 0..2 momentum, 3 energy, 4..6 B
 // (conserved component 1 + q).
 constexpr int NPAR = 7;
-
-// Adds (F(c - e_D/2) - F(c + e_D/2)) / dx_D at scratch cell c to s (global
-// order), F from the cell-centred primitive states as in k_div1.
-template <class R, int D>
-__device__ __forceinline__ void par_div1(const StepArgs &a, const DevPatch &P, const R *Vs, long long c, R gam,
-                                         R ch, R (&s)[NV])
-{
-    const long long st = dstr(P, D);
-    R Vm[NV], V0[NV], Vp[NV], Fm[NV], Fp[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        Vm[q] = Vs[gperm<D>(q) * a.sstride + c - st];
-        V0[q] = Vs[gperm<D>(q) * a.sstride + c];
-        Vp[q] = Vs[gperm<D>(q) * a.sstride + c + st];
-    }
-    riemann_any<PH_MHD, R>(Vm, V0, gam, ch, Fm);
-    riemann_any<PH_MHD, R>(V0, Vp, gam, ch, Fp);
-    const R iD = pidx<R>(P, D);
-#pragma unroll
-    for (int q = 0; q < NV; ++q) s[gperm<D>(q)] += (Fm[q] - Fp[q]) * iD;
-}
 
 // (Gamma - 1) max(kappa_perp, kappa_par), nu, kappa_perp, kappa_par -
 // kappa_perp and eta in the working precision.
@@ -223,75 +201,33 @@ __device__ __forceinline__ void par_lp(const StepArgs &a, const DevPatch &P, lon
     }
 }
 
-// Cells of the ring box outside the interior (its outer layer), enumerated
-// compactly: the two x-faces (x = -1, n_x; y, z over the ring), the two
-// y-faces (x inside; z over the ring), the two z-faces (x, y inside); in 1-D
-// the whole ring box (the first-order stage does not run).
-__host__ __device__ __forceinline__ int par_shell_cells(const int *n, int ndim)
+// Cells of the ring box (the interior and one layer around it on the active
+// axes), x fastest: coordinates in [-1, n_d] on active axes, 0 on the others.
+__host__ __device__ __forceinline__ int par_ring_cells(const int *n, int ndim)
 {
-    if (ndim == 1) return n[0] + 2;
-    const int e1 = n[1] + 2, e2 = ndim > 2 ? n[2] + 2 : 1;
-    return 2 * e1 * e2 + 2 * n[0] * e2 + (ndim > 2 ? 2 * n[0] * n[1] : 0);
+    return (n[0] + 2) * (ndim > 1 ? n[1] + 2 : 1) * (ndim > 2 ? n[2] + 2 : 1);
 }
 
-__device__ __forceinline__ void par_shell_coords(const DevPatch &P, int ndim, int t, int (&x)[3])
-{
-    if (ndim == 1) {
-        x[0] = t - 1;
-        x[1] = x[2] = 0;
-        return;
-    }
-    const int e1 = P.n[1] + 2, e2 = ndim > 2 ? P.n[2] + 2 : 1, lo2 = ndim > 2 ? 1 : 0;
-    const int cx = 2 * e1 * e2, cy = 2 * P.n[0] * e2;
-    if (t < cx) {
-        const int side = t / (e1 * e2), r = t - side * e1 * e2;
-        x[0] = side ? P.n[0] : -1;
-        x[1] = r % e1 - 1;
-        x[2] = r / e1 - lo2;
-    } else if (t < cx + cy) {
-        t -= cx;
-        const int side = t / (P.n[0] * e2), r = t - side * P.n[0] * e2;
-        x[0] = r % P.n[0];
-        x[1] = side ? P.n[1] : -1;
-        x[2] = r / P.n[0] - lo2;
-    } else {
-        t -= cx + cy;
-        const int side = t / (P.n[0] * P.n[1]), r = t - side * P.n[0] * P.n[1];
-        x[0] = r % P.n[0];
-        x[1] = r / P.n[0];
-        x[2] = side ? P.n[2] : -1;
-    }
-}
-
-// SHELL = false: the interior cells (ndim > 1), whose first-order
-// divergences the first-order stage formed in every direction, one thread
-// per cell in the k_maxspeed tiling; SHELL = true: the ring's outer layer
-// (par_shell_cells), which solves the missing faces itself.  The split keeps
-// the Riemann solver, and its registers, out of the kernel that covers
-// almost all cells.  L1: the first-order divergences (global order, ndim >
-// 1); LP: L_P^n per scratch cell, 4 planes of R (momentum, energy); Wh: the
-// half-step fields (par_plane), doubles (FP64 path) or double-float pairs
-// (hi, lo) (mixed path).  TM: bit 1 viscosity, bit 2 resistivity, bit 4
-// anisotropic or saturated conduction (which need the B and rho fields).
-template <class R, bool SHELL, int TM>
+// One thread per ring-box cell (par_ring_cells), whose first-order
+// divergences the first-order stage formed in every direction (its EXT
+// range).  L1: the first-order divergences (global order); LP: L_P^n per
+// scratch cell, 7 planes of R (momentum, energy, B); Wh: the half-step fields
+// (par_plane), doubles (FP64 path) or double-float pairs (hi, lo) (mixed
+// path).  TM: bit 1 viscosity, bit 2 resistivity, bit 4 anisotropic or
+// saturated conduction (which need the B and rho fields).
+template <class R, int TM>
 __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *LP,
                                                     double *Wh)
 {
     const Where w = locate(gt);
     const DevPatch P = a.patches[w.patch];
+    const int t = w.b * BLOCK + threadIdx.x;
+    if (t >= par_ring_cells(P.n, a.ndim)) return;
+    const int e0 = P.n[0] + 2, e1 = a.ndim > 1 ? P.n[1] + 2 : 1;
     int x[3];
-    if constexpr (SHELL) {
-        const int t = w.b * BLOCK + threadIdx.x;
-        if (t >= par_shell_cells(P.n, a.ndim)) return;
-        par_shell_coords(P, a.ndim, t, x);
-    } else {
-        const Tile tl(w.xw);
-        const int T0 = (P.n[0] + tl.xw - 1) / tl.xw, T1 = (P.n[1] + tl.rows - 1) / tl.rows;
-        x[0] = (w.b % T0) * tl.xw + tl.tx();
-        x[1] = ((w.b / T0) % T1) * tl.rows + tl.ty();
-        x[2] = w.b / (T0 * T1);
-        if (x[0] >= P.n[0] || x[1] >= P.n[1] || x[2] >= P.n[2]) return;
-    }
+    x[0] = t % e0 - 1;
+    x[1] = (t / e0) % e1 - (a.ndim > 1 ? 1 : 0);
+    x[2] = t / (e0 * e1) - (a.ndim > 2 ? 1 : 0);
     const int cl = lcell(P, x[0], x[1], x[2]);
     const long long S = a.sstride;
     const long long c = P.soff + cl;
@@ -308,25 +244,15 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
     for (int q = 0; q < NPAR; ++q)
         if (q != 3 && on(q)) LP[q * S + c] = lp[q];
     // the cell-centred half-step state and its fields
-    const R gam = pgam<R>(a), ch = pch<R>(a.sp);
     R s[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) s[q] = R(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         if (d >= a.ndim) continue;
-        if (!SHELL || (a.ndim > 1 && x[d] >= 0 && x[d] < P.n[d])) {  // formed by the first-order stage
-            const R *Ld = L1 + (long long)d * NV * S + c;
+        const R *Ld = L1 + (long long)d * NV * S + c;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) s[q] += Ld[q * S];
-        } else if constexpr (SHELL) {
-            if (d == 0)
-                par_div1<R, 0>(a, P, Vs, c, gam, ch, s);
-            else if (d == 1)
-                par_div1<R, 1>(a, P, Vs, c, gam, ch, s);
-            else
-                par_div1<R, 2>(a, P, Vs, c, gam, ch, s);
-        }
+        for (int q = 0; q < 8; ++q) s[q] += Ld[q * S];
     }
 #pragma unroll
     for (int q = 0; q < NPAR; ++q)
