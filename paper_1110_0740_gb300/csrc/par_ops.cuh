@@ -363,36 +363,68 @@ __global__ void __launch_bounds__(BLOCK) k_par_update(StepArgs a, GroupTable gt,
     const int b = wh.b;
     const int i = (b % T0) * t.xw + t.tx(), j = ((b / T0) % T1) * t.rows + t.ty(), k = b / (T0 * T1);
     R m = R(0);
-    if (i < P.n[0] && j < P.n[1] && k < P.n[2]) {
-        const int cl = lcell(P, i, j, k);
-        const long long S = a.sstride;
-        const long long c = P.soff + cl;
-        const int x[3] = {i, j, k};
-        const double dt = a.sp->dt;
-        // the flux registers of the cell's lower faces, and of its upper
-        // faces on the patch's last plane
-        auto faces = [&](int d, const R (&Pm)[NPAR], const R (&Pp)[NPAR]) {
-            if (!a.reg) return;
-            par_register_d<R, TM>(a, P, wh.patch, d, x[d], x, Pm, dt);
-            if (x[d] == P.n[d] - 1) par_register_d<R, TM>(a, P, wh.patch, d, x[d] + 1, x, Pp, dt);
-        };
-        R lp[NPAR];
-        if constexpr (sizeof(R) == 8) {
-            auto get = [&](int f, long long n) -> double { return Wh[par_plane(f) * S + n]; };
-            auto dif = [&](int f, long long n1, long long n2) -> double { return get(f, n1) - get(f, n2); };
-            par_lp<R, TM>(a, P, c, get, dif, lp, faces);
+    const bool act = i < P.n[0] && j < P.n[1] && k < P.n[2];
+    // the x-faces: every lane up to i = n_x evaluates its cell's lower face,
+    // and a cell's upper face is the next lane's lower face (the last lane
+    // of a tile row evaluates its own), taken by a shuffle within the row
+    const bool face0 = i <= P.n[0] && j < P.n[1] && k < P.n[2];
+    const int cl = face0 ? lcell(P, i, j, k) : 0;
+    const long long S = a.sstride;
+    const long long c = P.soff + cl;
+    const int x[3] = {i, j, k};
+    const double dt = a.sp->dt;
+    // the flux registers of the cell's lower faces, and of its upper faces on
+    // the patch's last plane
+    auto faces = [&](int d, const R (&Pm)[NPAR], const R (&Pp)[NPAR]) {
+        if (!a.reg) return;
+        par_register_d<R, TM>(a, P, wh.patch, d, x[d], x, Pm, dt);
+        if (x[d] == P.n[d] - 1) par_register_d<R, TM>(a, P, wh.patch, d, x[d] + 1, x, Pp, dt);
+    };
+    R lp[NPAR];
+    auto run = [&](auto get, auto dif) {
+        R Pm0[NPAR], Pp0[NPAR];
+        if (face0) {
+            par_face<R, TM>(a, P, c - 1, 0, get, dif, Pm0);
         } else {
-            // temperature differences of the double-float fields, exact to
-            // float; those of v and B, coefficients of a small increment,
-            // in float
-            const float2 *W2 = reinterpret_cast<const float2 *>(Wh);
-            auto get = [&](int f, long long n) -> float { return W2[par_plane(f) * S + n].x; };
-            auto dif = [&](int f, long long n1, long long n2) -> float {
+#pragma unroll
+            for (int q = 0; q < NPAR; ++q) Pm0[q] = R(0);
+        }
+#pragma unroll
+        for (int q = 0; q < NPAR; ++q) Pp0[q] = __shfl_down_sync(0xffffffffu, Pm0[q], 1, t.xw);
+        if (act && t.tx() == t.xw - 1) par_face<R, TM>(a, P, c, 0, get, dif, Pp0);
+        if (!act) return;
+        const R ih0 = pidx<R>(P, 0);
+#pragma unroll
+        for (int q = 0; q < NPAR; ++q) lp[q] = (Pp0[q] - Pm0[q]) * ih0;
+        faces(0, Pm0, Pp0);
+#pragma unroll
+        for (int d = 1; d < 3; ++d) {
+            if (d >= a.ndim) continue;
+            R Pp[NPAR], Pm[NPAR];
+            par_face<R, TM>(a, P, c, d, get, dif, Pp);
+            par_face<R, TM>(a, P, c - dstr(P, d), d, get, dif, Pm);
+            const R ih = pidx<R>(P, d);
+#pragma unroll
+            for (int q = 0; q < NPAR; ++q) lp[q] += (Pp[q] - Pm[q]) * ih;
+            faces(d, Pm, Pp);
+        }
+    };
+    if constexpr (sizeof(R) == 8) {
+        run([&](int f, long long n) -> double { return Wh[par_plane(f) * S + n]; },
+            [&](int f, long long n1, long long n2) -> double {
+                return Wh[par_plane(f) * S + n1] - Wh[par_plane(f) * S + n2];
+            });
+    } else {
+        // temperature differences of the double-float fields, exact to float;
+        // those of v and B, coefficients of a small increment, in float
+        const float2 *W2 = reinterpret_cast<const float2 *>(Wh);
+        run([&](int f, long long n) -> float { return W2[par_plane(f) * S + n].x; },
+            [&](int f, long long n1, long long n2) -> float {
                 const float2 u = W2[par_plane(f) * S + n1], v = W2[par_plane(f) * S + n2];
                 return f == 4 ? df_add(df{u.x, u.y}, df{-v.x, -v.y}).hi : u.x - v.x;
-            };
-            par_lp<R, TM>(a, P, c, get, dif, lp, faces);
-        }
+            });
+    }
+    if (act) {
         double *Uo = a.Uout + P.base + cl;
         // the conserved components 1 + q the parabolic terms change
         auto on = [](int q) -> bool { return q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0); };
