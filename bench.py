@@ -301,7 +301,7 @@ def run_ours(args):
     kern = res["kern"]
     top_name, (top_ms, top_cnt) = max(kern.items(), key=lambda kv: kv[1][0])
     top_avg = top_ms / max(1, top_cnt)
-    fl = kernel_flops(n, args.recon)
+    fl = kernel_flops(n, args.recon, args.kappa, args.kappa_par, args.tc_phi, args.nu, args.eta)
     mixed = primary == ctu.CTU_MIXED
     peak_tf = (FP32_PEAK if mixed else FP64_PEAK) / 1e12
     f_top = fl.get(top_name, 0.0)
@@ -874,17 +874,40 @@ def _profile_numbers(name):
     return vals
 
 
-def kernel_flops(n, recon="ppm"):
-    """Algorithmic flops per launch of each kernel group of one 3-D PPM step
-    on an n^3 patch: the oracle's operation counts per interior cell
-    (profiles/flops_per_cell.txt, exact-zero operands not counted) times n^3."""
+def kernel_flops(n, recon="ppm", kappa=0.0, kappa_par=0.0, tc_phi=0.0, nu=0.0, eta=0.0):
+    """Algorithmic flops per launch of each kernel group of one 3-D step on an
+    n^3 patch: the oracle's operation counts per interior cell
+    (profiles/flops_per_cell.txt, exact-zero operands not counted) times n^3.
+    With parabolic terms the x sweep leaves the update and the next dt to
+    par_update, and par_half forms L_P^n and the half-step fields."""
     c = {k: float(v) for k, v in _profile_numbers("flops_per_cell.txt").items()}
     cells = float(n) ** 3
     sweep = c.get("sweep_per_direction_" + ("linear" if recon == "mc" else recon), 0.0)
-    # sweeps run z, y, x; the x sweep finishes the update and the next dt
+    kp = kappa_par if kappa_par > 0 else kappa
+    if not (kappa or kappa_par or nu or eta):
+        # sweeps run z, y, x; the x sweep finishes the update and the next dt
+        return {"prim": c.get("prim", 0.0) * cells, "flux1": 3 * c.get("flux1_per_direction", 0.0) * cells,
+                "sweep_z": sweep * cells, "sweep_y": sweep * cells,
+                "sweep_x": (sweep + c.get("update", 0.0) + c.get("next_dt", 0.0)) * cells}
+    # one face flux: the conduction variant plus viscosity and resistivity
+    face = 0.0
+    if kappa or kp:
+        key = "par_face_" + ("sat" if tc_phi else "") + ("_" if tc_phi and kp != kappa else "") + \
+              ("aniso" if kp != kappa else ("" if tc_phi else "cond"))
+        face += c.get(key, 0.0)
+    if nu:
+        face += c.get("par_face_visc", 0.0)
+    if eta:
+        face += c.get("par_face_res", 0.0)
+    m = 1 + (3 if nu else 0) + (3 if eta else 0)
+    swp = sweep + m * c.get("sweep_par_per_component", 0.0)
+    half = (c.get("par_half_per_cell", 0.0) + 3 * face + m * c.get("par_half_per_component", 0.0)
+            + (c.get("par_half_visc", 0.0) if nu else 0.0))
+    upd = (3 * face + m * c.get("par_update_per_component", 0.0) + c.get("next_dt", 0.0)
+           + c.get("par_update_diffusion_number", 0.0))
     return {"prim": c.get("prim", 0.0) * cells, "flux1": 3 * c.get("flux1_per_direction", 0.0) * cells,
-            "sweep_z": sweep * cells, "sweep_y": sweep * cells,
-            "sweep_x": (sweep + c.get("update", 0.0) + c.get("next_dt", 0.0)) * cells}
+            "par_half": half * cells, "sweep_z": swp * cells, "sweep_y": swp * cells,
+            "sweep_x": (swp + c.get("update", 0.0)) * cells, "par_update": upd * cells}
 
 
 def precision_split_roofline(n, cells_per_s, hbm_gbs):

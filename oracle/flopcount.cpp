@@ -7,7 +7,9 @@
 // comparisons are not counted as flops; exp is counted on its own).  The driver reads states (local 1-D order) from
 // stdin and prints the average counts per call of or_mhd_riemann,
 // or_mhd_char_predict (linear and PPM), or_mhd_prim2cons and
-// or_mhd_cons2prim.
+// or_mhd_cons2prim, then the average counts per face of the parabolic
+// fluxes (Section 3.1): each conduction variant, viscosity and resistivity
+// on their own, over the faces of a 4^3 patch of generic fields.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -66,6 +68,47 @@ static double total(const fc::Counts &c)
     return (double)(c.add + c.mul + c.div + c.sqrt);
 }
 
+// Average flops of one parabolic face flux over the 3 x 64 faces of a 4^3
+// patch (3-D) whose fields (rho, v, T, B) are drawn from a fixed xorshift64
+// sequence: rho, T in [0.5, 1.5), v, B in [-1, 1).
+static double face_count(double kappa, double kpar, double phi, double nu, double eta)
+{
+    grid_t G;
+    grid_init(&G, 4, 4, 4, 3);
+    const long nc = G.ncell;
+    Flop *W = new Flop[8 * nc];
+    unsigned long long s = 88172645463325252ull;
+    auto rnd = [&]() {
+        s ^= s << 13;
+        s ^= s >> 7;
+        s ^= s << 17;
+        return (double)(s >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (long i = 0; i < nc; ++i) {
+        W[i] = Flop(0.5 + rnd());
+        for (int q = 1; q <= 3; ++q) W[q * nc + i] = Flop(2.0 * rnd() - 1.0);
+        W[4 * nc + i] = Flop(0.5 + rnd());
+        for (int q = 5; q <= 7; ++q) W[q * nc + i] = Flop(2.0 * rnd() - 1.0);
+    }
+    Flop h[3] = {Flop(0.25), Flop(0.25), Flop(0.25)};
+    double tot = 0.0;
+    int nf = 0;
+    for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < 4; ++j)
+            for (int i = 0; i < 4; ++i)
+                for (int d = 0; d < 3; ++d) {
+                    const int c[3] = {i, j, k};
+                    Flop Pi[NVAR];
+                    fc::g = fc::Counts();
+                    parabolic_face(&G, W, h, Flop(kappa), Flop(kpar), Flop(phi), Flop(nu), Flop(eta), cidx(&G, c), d,
+                                   Pi);
+                    tot += total(fc::g);
+                    ++nf;
+                }
+    delete[] W;
+    return tot / nf;
+}
+
 int main()
 {
     // input: count K, gamma, ch, dtdx, then K stencils of 5 x 9 values (local order)
@@ -112,5 +155,10 @@ int main()
            r_riem / K, r_pred0 / K, r_pred1 / K, r_p2c / K, r_c2p / K, r_cf / K);
     printf("predict_minmod %.2f\npredict_harmonic %.2f\npredict_vanalbada %.2f\npredict_weno3 %.2f\n",
            r_predv[0] / K, r_predv[1] / K, r_predv[2] / K, r_predv[3] / K);
+    printf("par_face_cond %.2f\npar_face_aniso %.2f\npar_face_sat %.2f\npar_face_sat_aniso %.2f\n",
+           face_count(1e-3, 1e-3, 0.0, 0.0, 0.0), face_count(1e-3, 1e-2, 0.0, 0.0, 0.0),
+           face_count(1e-3, 1e-3, 1e-2, 0.0, 0.0), face_count(1e-3, 1e-2, 1e-2, 0.0, 0.0));
+    printf("par_face_visc %.2f\npar_face_res %.2f\n", face_count(0.0, 0.0, 0.0, 1e-3, 0.0),
+           face_count(0.0, 0.0, 0.0, 0.0, 1e-3));
     return 0;
 }

@@ -17,6 +17,17 @@ the step, in the large-patch limit:
   update      9 x 2 (dt x sum + U) + 2 (sum of three directions) x 9 + 1 (psi)
   next dt     cons2prim + ndim x (cfast + 2)
 
+and the parabolic terms' stages (Section 3.1), per interior cell with
+m = 1 + 3 (viscosity) + 3 (resistivity) conserved components changed and
+one face flux per direction (par_face_* summed over the terms on):
+
+  par half    T of U^n (1) + 3 faces + m x 8 (L_P: three differences and
+              scalings, two sums) + 16 (three first-order divergences) + m
+              + 16 (U^n + dt/2 sum) + 17 (pressure, T) + 3 (v, viscosity)
+  par update  3 faces + m x 10 (L_P, dt FMA) + next dt + 13 (diffusion
+              number: D / rho, 3 x (1/dx^2, x D, x 2, +))
+  sweep (d)   + 2 m (dt/2 L_P in the predictor)
+
     python oracle/flopcount.py [--out profiles/flops_per_cell.txt]
 """
 import argparse
@@ -88,6 +99,9 @@ def main():
               f"sweep_per_direction_linear {sweep['linear']:.1f}"]
     lines += [f"sweep_per_direction_{r} {sweep[r]:.1f}" for r in recons[2:]]
     lines += [f"update {update:.1f}", f"next_dt {nextdt:.1f}",
+              "par_half_per_cell 50.0", "par_half_per_component 9.0", "par_half_visc 3.0",
+              "par_update_per_component 10.0", "par_update_diffusion_number 13.0",
+              "sweep_par_per_component 2.0",
               f"step_total_ppm {prim + 3 * flux1 + 3 * sweep['ppm'] + update + nextdt:.1f}"]
     text = "\n".join(lines) + "\n"
     print(text)

@@ -24,6 +24,37 @@ def test_algorithmic_bytes_closed_form():
     assert abs(per_cell - 6 * 9 * 8 * 2 / 256 - 151) < 0.1
 
 
+@pytest.mark.parametrize("terms", [dict(kappa=1e-3), dict(kappa=1e-3, kappa_par=1e-2),
+                                   dict(kappa=1e-3, tc_phi=1e-2), dict(kappa=1e-3, kappa_par=1e-2, tc_phi=1e-2),
+                                   dict(nu=1e-3), dict(eta=1e-3), dict(kappa=1e-3, nu=1e-3, eta=1e-3)])
+def test_kernel_flops_parabolic(terms):
+    """Every kernel group a step with parabolic terms launches has a flop
+    count, and the step's total is the plain step's plus the parabolic work:
+    L_P twice (three faces each), the half-step state, the predictor terms
+    and the diffusion number of the next dt."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = {k: float(v) for k, v in bench._profile_numbers("flops_per_cell.txt").items()}
+    plain = bench.kernel_flops(1, "ppm")
+    fl = bench.kernel_flops(1, "ppm", **terms)
+    for k in ("prim", "flux1", "par_half", "sweep_z", "sweep_y", "sweep_x", "par_update"):
+        assert fl[k] > 0, k
+    kappa, kp = terms.get("kappa", 0.0), terms.get("kappa_par", 0.0) or terms.get("kappa", 0.0)
+    face = 0.0
+    if kappa:
+        face += c["par_face_" + {(False, False): "cond", (True, False): "aniso", (False, True): "sat",
+                                 (True, True): "sat_aniso"}[(kp != kappa, bool(terms.get("tc_phi")))]]
+    face += c["par_face_visc"] if terms.get("nu") else 0.0
+    face += c["par_face_res"] if terms.get("eta") else 0.0
+    m = 1 + 3 * bool(terms.get("nu")) + 3 * bool(terms.get("eta"))
+    extra = (6 * face + m * (c["par_half_per_component"] + c["par_update_per_component"]
+                             + 3 * c["sweep_par_per_component"])
+             + c["par_half_per_cell"] + c["par_update_diffusion_number"] + (c["par_half_visc"] if terms.get("nu") else 0))
+    assert sum(fl.values()) == pytest.approx(sum(plain.values()) + extra, rel=1e-12)
+    # the counted face work of each term is not trivial
+    assert face >= 3
+
+
 def test_reference_arm_json_line():
     env = dict(os.environ)
     env.pop("RANK", None)
