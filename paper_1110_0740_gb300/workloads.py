@@ -112,13 +112,14 @@ def _field_3d(rng, n, kmax, deriv=False):
     return f / s, grads
 
 
-def mhd_blast_3d(n=256, seed=0, gamma=5.0 / 3.0, kmax=8):
+def mhd_blast_3d(n=256, seed=0, gamma=5.0 / 3.0, kmax=8, sphere=100.0):
     """3-D periodic ideal-MHD state on [0,1]^3 with a pressure sphere.
 
     rho = 1 + 0.2 f_rho, v = 0.5 (f_x, f_y, f_z), B = curl A with A a seeded
     random vector potential (modes 0 < |k| <= kmax) scaled to max |B| = 1,
-    p = 1 outside and 100 inside a sphere of radius 0.1 at a seeded centre
-    (periodic distance), psi = 0.  Returns U with ghosts, shape (9, n+8, n+8, n+8)."""
+    p = 1 outside and `sphere` (100) inside a sphere of radius 0.1 at a seeded
+    centre (periodic distance), psi = 0; sphere = 1 gives the smooth spectrum
+    alone.  Returns U with ghosts, shape (9, n+8, n+8, n+8)."""
     rng = np.random.default_rng(seed)
     frho = _field_3d(rng, n, kmax)
     vx = 0.5 * _field_3d(rng, n, kmax)
@@ -140,7 +141,7 @@ def mhd_blast_3d(n=256, seed=0, gamma=5.0 / 3.0, kmax=8):
     x = (np.arange(n) + 0.5) / n
     dxs = [np.minimum(np.abs(x - c[d]), 1.0 - np.abs(x - c[d])) for d in range(3)]
     r2 = dxs[2][:, None, None] ** 2 + dxs[1][None, :, None] ** 2 + dxs[0][None, None, :] ** 2
-    p = np.where(r2 < 0.01, 100.0, 1.0)
+    p = np.where(r2 < 0.01, float(sphere), 1.0)
     rho = 1.0 + 0.2 * frho
     z = np.zeros_like(rho)
     U = ideal_cons([rho, vx, vy, vz, p, bx, by, bz, z], gamma)

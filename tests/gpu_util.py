@@ -30,6 +30,18 @@ def l1rel(got, ref, ch=None, group_floor=False):
     return np.array(out)
 
 
+def maxrel(got, ref, ch=None):
+    """Per-variable elementwise bound: max|got - ref| / max|ref| (for psi the
+    denominator is c_h max|B|), so that an error confined to a few cells (a
+    tile seam, a patch corner) cannot hide in the L1 sum."""
+    out = []
+    for q in range(9):
+        num = np.abs(got[q] - ref[q]).max()
+        den = (ch if ch else 1.0) * np.abs(ref[5:8]).max() if q == 8 else np.abs(ref[q]).max()
+        out.append(num / den if den > 0 else (0.0 if num == 0 else np.inf))
+    return np.array(out)
+
+
 def gpu_run(U0, n, ndim, dx, steps, cfl, precision=0, recon=1, trace_mode=0, glm_alpha=0.1,
             gamma=5.0 / 3.0, physics=0, eos=0, riemann=0, kappa=0.0, nu=0.0, eta=0.0, kappa_par=0.0, phi=0.0):
     """Advance one periodic patch `steps` steps on the GPU; returns

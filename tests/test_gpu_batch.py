@@ -5,7 +5,7 @@ import pytest
 
 import oracle as O
 from paper_1110_0740_gb300 import workloads as W
-from tests.gpu_util import l1rel
+from tests.gpu_util import l1rel, maxrel
 
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-11
@@ -75,6 +75,8 @@ def test_batch_of_uneven_patches_and_registers():
         G = out[:, b:b + A[0].size].reshape(A.shape)
         e = l1rel(O.interior(G, list(n), 3), O.interior(R, list(n), 3), ch)
         assert np.all(e <= TOL64), (n, e)
+        em = maxrel(O.interior(G, list(n), 3), O.interior(R, list(n), 3), ch)
+        assert np.all(em <= TOL64), (n, em)
     scale = np.abs(ref_reg).max()
     assert np.abs(regs - ref_reg).max() <= 1e-12 * scale
 
@@ -113,6 +115,8 @@ def test_full_size_sampled_parity_256():
             got = G[:, k + 4:k + 10, j + 4:j + 10, i + 4:i + 10].cpu().numpy()
             e = l1rel(got, O.interior(R, [6, 6, 6], 3), ch)
             assert np.all(e <= tol), (prec, c, e)
+            em = maxrel(got, O.interior(R, [6, 6, 6], 3), ch)
+            assert np.all(em <= tol), (prec, c, em)
         ctx.close()
 
 

@@ -4,7 +4,7 @@ import pytest
 
 import oracle as O
 from paper_1110_0740_gb300 import workloads as W
-from tests.gpu_util import gpu_run, l1rel, oracle_run
+from tests.gpu_util import gpu_run, l1rel, maxrel, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -12,12 +12,16 @@ TOL64 = 1e-11
 
 
 def _check_fp64(got, ref, n, ndim, ch, tol=TOL64):
+    """Relative L1 per variable within tol, and the elementwise max error
+    within tol of each variable's largest magnitude."""
     G, Rf = O.interior(got, n, ndim), O.interior(ref, n, ndim)
     e = l1rel(G, Rf, ch)
     for q in range(9):
         if not np.any(Rf[q]):
             assert not np.any(G[q]), f"var {q} must stay exactly zero"
     assert np.all(e <= tol), e
+    em = maxrel(G, Rf, ch)
+    assert np.all(em <= tol), em
     return e
 
 
@@ -66,19 +70,22 @@ def test_1d_fp64():
     _check_fp64(got, ref, n, 1, odts[-1][1])
 
 
-def test_mixed_precision_matches_oracle_loosely():
-    """Mixed path (float32 tracing/Riemann, float64 recovery/update) stays
-    within 1e-4 relative L1 of the FP64 oracle on a smooth 3-D state."""
+def test_mixed_precision_on_a_smooth_state():
+    """Mixed path (float32 tracing/Riemann, float64 update) on a smooth 3-D
+    state: the blast's |k| <= 3 spectrum without its pressure sphere.  It
+    stays within 5e-6 relative L1 and 1e-5 elementwise of the FP64 oracle
+    (4.2e-7 and 5.7e-7 measured on a GB300)."""
     n = [24, 24, 24]
-    U0 = W.mhd_blast_3d(24, seed=10, kmax=3)
-    # smooth: drop the pressure sphere
-    Vp = U0.copy()
+    U0 = W.mhd_blast_3d(24, seed=10, kmax=3, sphere=1.0)
     dx = [1.0 / 24] * 3
-    got, _, st = gpu_run(Vp, n, 3, dx, 5, 0.3, precision=1, recon=1)
+    got, _, st = gpu_run(U0, n, 3, dx, 5, 0.3, precision=1, recon=1)
     assert st == 0
-    ref, odts = oracle_run(Vp, n, 3, dx, 5, 0.3, recon=1)
-    e = l1rel(O.interior(got, n, 3), O.interior(ref, n, 3), odts[-1][1])
-    assert np.all(e < 1e-4), e
+    ref, odts = oracle_run(U0, n, 3, dx, 5, 0.3, recon=1)
+    G, R = O.interior(got, n, 3), O.interior(ref, n, 3)
+    e = l1rel(G, R, odts[-1][1])
+    assert np.all(e < 5e-6), e
+    em = maxrel(G, R, odts[-1][1])
+    assert np.all(em < 1e-5), em
 
 
 @pytest.mark.parametrize("prec", [1, 2])
