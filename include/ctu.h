@@ -78,14 +78,19 @@ enum { CTU_HLLD = 0, CTU_HLL = 1, CTU_HLLC = 2 };
 /* precision:
  *   CTU_FP64          all arithmetic in float64.
  *   CTU_MIXED         tracing, characteristic projections, Riemann fluxes and
- *                     flux differences in float32; cell-centre pressure
- *                     recovery from the float64 state and the update
- *                     accumulation in float64; the n+1/2 interface pressure
- *                     is recovered in an exact increment form that has no
+ *                     flux differences in float32; the state and the update
+ *                     accumulation in float64.  The cell-centre pressure
+ *                     p = (Gamma-1)(E - m^2/2rho - B^2/2) is recovered from
+ *                     the float64 state in double-float arithmetic (pairs of
+ *                     floats, about 2^-44 relative to E) on the float32
+ *                     pipe, not in float64; the n+1/2 interface pressure is
+ *                     recovered in an exact increment form that has no
  *                     catastrophic cancellation and so runs in float32.
- *   CTU_MIXED_IFACE64 as CTU_MIXED, but the interface states are formed as
- *                     float64 conservative states and their pressure is
- *                     recovered in float64. */
+ *   CTU_MIXED_IFACE64 the literal split: as CTU_MIXED, but every pressure
+ *                     recovery runs in plain float64 -- the cell-centre
+ *                     states (the step's primitives and both CFL speeds)
+ *                     and the interface states, which are formed as float64
+ *                     conservative states.  PPM and MC-linear only. */
 enum { CTU_FP64 = 0, CTU_MIXED = 1, CTU_MIXED_IFACE64 = 2 };
 /* trace_mode: Section 3.2 normal predictor with w_ref = w_(+/-).
  *   CTU_TRACE_ALL    every characteristic field is traced to both
@@ -481,15 +486,6 @@ ctu_status ctu_profile(ctu_ctx *ctx, int enable);
  * time in ms and its launch count.  Returns 0 when profiling is off. */
 int ctu_profile_read(ctu_ctx *ctx, int i, const char **name, double *total_ms, long long *launches);
 
-/* FMA-throughput microbenchmark of the non-tensor pipes on the current
- * device (a measurement aid; the paper has no counterpart): every thread of
- * a grid of 16 blocks of 256 threads per SM runs 8 independent chains of
- * `iters` fused multiply-adds in float32 (fp64 = 0) or float64 (fp64 = 1);
- * *flops_per_s = 2 x FMAs / CUDA-event time of the timed launch (after one
- * shorter warm-up launch).  Synchronises the stream; allocates a small
- * scratch array. */
-ctu_status ctu_fma_peak(int fp64, int iters, double *flops_per_s, void *stream);
-
 /* ---- Allocation-free step ------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory, such as a host framework whose caching
@@ -509,16 +505,18 @@ ctu_status ctu_fma_peak(int fp64, int iters, double *flops_per_s, void *stream);
  *
  * The call allocates nothing (no cudaMalloc/cudaFree, no heap).  Its first
  * call on a device looks up the array's device address (set-up), so make
- * that first call before any stream capture.  All calls share the one array
+ * that first call before any stream capture.  The patch table reaches the
+ * array in kernel parameters, so no enqueued copy reads host memory after
+ * the call returns.  All calls share the one array
  * and it keeps the last call's contents (the status word is cleared at the
  * start of every call): calls that overlap on the GPU -- on different
  * streams, or from different threads -- race and corrupt each other.
  *
  * cfg: as for ctu_init, without floors (a non-zero p_floor or rho_floor
  * returns CTU_EUNSUPPORTED).  U_in, U_out, stride, patches, npatch, d_dt_ch:
- * as for ctu_step.  wait_status != 0: synchronise the stream and return the
- * device status of this call (CTU_OK, CTU_ENEGATIVE or CTU_ENAN);
- * wait_status == 0: return after enqueueing. */
+ * as for ctu_step.  wait_status != 0: copy the status word back,
+ * synchronise the stream and return the device status of this call (CTU_OK,
+ * CTU_ENEGATIVE or CTU_ENAN); wait_status == 0: return after enqueueing. */
 #define CTU_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
 #define CTU_NOALLOC_MAX_PATCHES 64
 ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in, double *U_out,

@@ -8,7 +8,8 @@ template int launch_step_impl<float, 0>(const StepArgs &, const LaunchInfo &, cu
 template <> int launch_maxspeed<float>(const StepArgs &a, const LaunchInfo &li, unsigned long long *out,
                                        cudaStream_t s)
 {
-    return li.physics == PH_SR ? launch_maxspeed_impl<PH_SR, float>(a, li, out, s)
-                               : launch_maxspeed_impl<PH_MHD, float>(a, li, out, s);
+    if (li.physics == PH_SR) return launch_maxspeed_impl<PH_SR, float>(a, li, out, s);
+    return li.iface64 ? launch_maxspeed_impl<PH_MHD, float, 1>(a, li, out, s)
+                      : launch_maxspeed_impl<PH_MHD, float>(a, li, out, s);
 }
 } // namespace ctu

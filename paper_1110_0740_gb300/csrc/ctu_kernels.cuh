@@ -309,10 +309,20 @@ template <class R> __device__ __forceinline__ double widen(R x);
 template <> __device__ __forceinline__ double widen<double>(double x) { return x; }
 template <> __device__ __forceinline__ double widen<float>(float x) { return f2d_int(x); }
 
-// V(U) for either physics (SRMHD: float64 Newton recovery).
-template <int PHYS, class R>
+// V(U) for either physics (SRMHD: float64 Newton recovery).  LIT64 (the
+// CTU_MIXED_IFACE64 kernels): the ideal-MHD pressure of a float state is
+// recovered in plain float64, p = (Gamma-1)(E - m^2/2rho - B^2/2), and V is
+// then rounded to R.
+template <int PHYS, class R, int LIT64 = 0>
 __device__ __forceinline__ unsigned int prim_any(const double (&U)[NV], const StepArgs &a, R (&V)[NV])
 {
+    if (PHYS == PH_MHD && LIT64 && sizeof(R) == 4) {
+        double Vd[NV];
+        const bool ok = prim_from_cons64(U, a.gam - 1.0, Vd);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) V[q] = (R)Vd[q];
+        return ok ? 0u : state_flags(Vd[0], Vd[4]);
+    }
     if (PHYS == PH_MHD) return prim_of<R>(U, a, V);
     double Vd[NV];
     const unsigned int st = sr_prim<R>(U, a.gam, Vd);
@@ -590,7 +600,7 @@ __device__ __forceinline__ void register_face_var(const StepArgs &a, const DevPa
 // Final update of one interior cell: U^(n+1) = U^n + dt s, psi source, and
 // the CFL speed of U^(n+1) if requested (returned in R; 0 otherwise).
 // u0: U^n of the cell.
-template <int PHYS, class R>
+template <int PHYS, class R, int LIT64 = 0>
 __device__ __forceinline__ R finish_cell_u(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
                                            const double (&u0)[NV], double dt, double damp, unsigned int &fl)
 {
@@ -602,7 +612,7 @@ __device__ __forceinline__ R finish_cell_u(const StepArgs &a, const DevPatch &P,
     for (int q = 0; q < NV; ++q) a.Uout[q * a.ustride + P.base + cl] = u[q];
     if (!a.nextmax) return R(0);
     R V[NV];
-    fl |= prim_any<PHYS, R>(u, a, V);
+    fl |= prim_any<PHYS, R, LIT64>(u, a, V);
     return cell_speed<PHYS, R>(V, a, P);
 }
 
@@ -629,14 +639,14 @@ __device__ __forceinline__ R finish_cell_inc(const StepArgs &a, const DevPatch &
     return cell_speed<PH_MHD, R>(V, a, P);
 }
 
-template <int PHYS, class R>
+template <int PHYS, class R, int LIT64 = 0>
 __device__ __forceinline__ R finish_cell(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
                                          double dt, double damp, unsigned int &fl)
 {
     double u0[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) u0[q] = a.U[q * a.ustride + P.base + cl];
-    return finish_cell_u<PHYS, R>(a, P, cl, s, u0, dt, damp, fl);
+    return finish_cell_u<PHYS, R, LIT64>(a, P, cl, s, u0, dt, damp, fl);
 }
 
 // Block maximum of a non-negative value, folded into *out as the bits of a
@@ -730,8 +740,9 @@ static __global__ void k_setup(const double *dtch, StepParams *sp)
 }
 
 // V = V(U) on every ghosted cell (a flat range of the patch region);
-// one block per BLOCK cells of a patch.
-template <int PHYS, class R>
+// one block per BLOCK cells of a patch.  LIT64: float64 pressure recovery in
+// the float kernels (CTU_MIXED_IFACE64).
+template <int PHYS, class R, int LIT64 = 0>
 __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, GroupTable gt, R *Vs)
 {
     const Where w = locate(gt);
@@ -742,7 +753,7 @@ __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, GroupTable gt, R *Vs
     R V[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) U[q] = a.U[q * a.ustride + P.base + c];
-    const unsigned int f = prim_any<PHYS, R>(U, a, V);
+    const unsigned int f = prim_any<PHYS, R, LIT64>(U, a, V);
     if (f) atomicOr(a.status, f);
 #pragma unroll
     for (int q = 0; q < NV; ++q) Vs[q * a.sstride + P.soff + c] = V[q];
@@ -1071,7 +1082,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
 #pragma unroll
                 for (int q = 0; q < NV; ++q) s[q] = A[q * a.sstride + c] + s[q];
             }
-            if constexpr (PHYS == PH_MHD && sizeof(R) == 4) {
+            if constexpr (PHYS == PH_MHD && sizeof(R) == 4 && !IFACE64) {
                 double u0[NV];
                 R Vn[NV];
 #pragma unroll
@@ -1081,7 +1092,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
                 }
                 m = finish_cell_inc<R>(a, P, cl, s, u0, Vn, dtd, dtr, damp, fl);
             } else {
-                m = finish_cell<PHYS, R>(a, P, cl, s, dtd, damp, fl);
+                m = finish_cell<PHYS, R, IFACE64>(a, P, cl, s, dtd, damp, fl);
             }
         }
         if (a.nextmax) block_max_to<R>(m, a.nextmax);
@@ -1195,13 +1206,13 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, G
                         s[q] = Ap[q * as] + s[q];
                         u[q] = Up[q * us];
                     }
-                    if constexpr (PHYS == PH_MHD && sizeof(R) == 4) {
+                    if constexpr (PHYS == PH_MHD && sizeof(R) == 4 && !IFACE64) {
                         R Vn[NV];  // V^n of cell j - 1, global order
 #pragma unroll
                         for (int q = 0; q < NV; ++q) Vn[gperm<D>(q)] = win[1][q];
                         mx = fmax(mx, finish_cell_inc<R>(a, P, (int)(cp - P.soff), s, u, Vn, dtd, dtr, damp, fl));
                     } else {
-                        mx = fmax(mx, finish_cell_u<PHYS, R>(a, P, (int)(cp - P.soff), s, u, dtd, damp, fl));
+                        mx = fmax(mx, finish_cell_u<PHYS, R, IFACE64>(a, P, (int)(cp - P.soff), s, u, dtd, damp, fl));
                     }
                 } else if constexpr (FIRST) {
 #pragma unroll
@@ -1328,7 +1339,7 @@ __global__ void __launch_bounds__(BLOCK, CTU_MARCH_MINB) k_sweep_m(StepArgs a, G
 }
 
 // ctu_dt: max over interior cells of max_d (|v_d| + c_f,d)/dx_d.
-template <int PHYS, class R>
+template <int PHYS, class R, int LIT64 = 0>
 __global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, GroupTable gt, unsigned long long *out)
 {
     const Where wh = locate(gt);
@@ -1344,7 +1355,7 @@ __global__ void __launch_bounds__(BLOCK) k_maxspeed(StepArgs a, GroupTable gt, u
         R V[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) U[q] = a.U[q * a.ustride + P.base + cl];
-        const unsigned int f = prim_any<PHYS, R>(U, a, V);
+        const unsigned int f = prim_any<PHYS, R, LIT64>(U, a, V);
         if (f) atomicOr(a.status, f);
         m = cell_speed<PHYS, R>(V, a, P);
         if (a.par_cond | a.par_visc | a.par_res) {  // parabolic terms: + sum_d 2 D / dx_d^2

@@ -111,7 +111,7 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     CTU_MARK("prim");
     n += over_groups(
         li, [&](const Group &G) { return Tiles::prim(G.N); },
-        [&](const GroupTable &gt, unsigned nb) { k_prim<PHYS, R><<<nb, BLOCK, 0, s>>>(a, gt, Vs); });
+        [&](const GroupTable &gt, unsigned nb) { k_prim<PHYS, R, IF64><<<nb, BLOCK, 0, s>>>(a, gt, Vs); });
     CTU_MARK(nullptr);
     if constexpr (recon_hybrid(PPM)) {  // shock flags of the hybrid integration
         CTU_MARK("shock");
@@ -236,13 +236,13 @@ template <class R> int launch_step_sr(const StepArgs &a, const LaunchInfo &li, c
     return launch_step_t<PH_SR, R, 0, 1>(a, li, s);
 }
 
-template <int PHYS, class R>
+template <int PHYS, class R, int LIT64 = 0>
 int launch_maxspeed_impl(const StepArgs &a, const LaunchInfo &li, unsigned long long *out, cudaStream_t s)
 {
     CTU_MARK("maxspeed");
     const int n = over_groups(
         li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
-        [&](const GroupTable &gt, unsigned nb) { k_maxspeed<PHYS, R><<<nb, BLOCK, 0, s>>>(a, gt, out); });
+        [&](const GroupTable &gt, unsigned nb) { k_maxspeed<PHYS, R, LIT64><<<nb, BLOCK, 0, s>>>(a, gt, out); });
     CTU_MARK(nullptr);
     return n;
 }
