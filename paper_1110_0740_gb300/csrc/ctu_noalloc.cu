@@ -43,6 +43,19 @@ unsigned char *g_base[kMaxDevices];  // device address of g_noalloc, per device
 // The one device array behind ctu_step_noalloc: [status | patch table | scratch].
 static __device__ __align__(256) unsigned char g_noalloc[kTotalBytes];
 
+// Patch descriptors travel to the array by value, in the parameters of a
+// small kernel (kChunk per launch, well inside the parameter space), so that
+// no copy reads the caller's host stack after the call has returned.
+constexpr int kChunk = 16;
+struct TableChunk {
+    DevPatch p[kChunk];
+};
+static __global__ void k_put_table(TableChunk c, int n, DevPatch *dst)
+{
+    const int i = (int)threadIdx.x;
+    if (i < n) dst[i] = c.p[i];
+}
+
 // Set-up, once per device with that device current: host code cannot use the
 // symbol g_noalloc as a device address (on the host it names a stand-in), so
 // the real address is looked up and cached.
@@ -133,8 +146,13 @@ extern "C" ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in
     // at zero; the per-step parameters and every scratch word the kernels read
     // are written earlier in the same call, so they need no clearing.
     if (cudaMemsetAsync(status, 0, sizeof(unsigned int), s) != cudaSuccess) return CTU_ECUDA;
-    if (cudaMemcpyAsync(dtab, table, sizeof(DevPatch) * npatch, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return CTU_ECUDA;
+    for (int i0 = 0; i0 < npatch; i0 += kChunk) {
+        const int m = npatch - i0 < kChunk ? npatch - i0 : kChunk;
+        TableChunk c;
+        std::memset(&c, 0, sizeof(c));
+        for (int i = 0; i < m; ++i) c.p[i] = table[i0 + i];
+        k_put_table<<<1, kChunk, 0, s>>>(c, m, dtab + i0);
+    }
 
     StepArgs a;
     std::memset(&a, 0, sizeof(a));
