@@ -11,8 +11,12 @@ CSRC = PKG / "csrc"
 OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "libctu.so"
 SOURCES = ["ctu_api.cu", "ctu_f64.cu", "ctu_f32.cu", "ctu_f32i.cu", "ctu_sr32.cu", "ctu_noalloc.cu",
-           "fma_peak.cu", "ctu_var32.cu", "ctu_var64.cu", "ctu_ref32.cu", "ctu_ref64.cu", "ctu_hyb32.cu",
+           "ctu_var32.cu", "ctu_var64.cu", "ctu_ref32.cu", "ctu_ref64.cu", "ctu_hyb32.cu",
            "ctu_hyb64.cu", "ctu_hllc32.cu", "ctu_hllc64.cu", "ctu_par32.cu", "ctu_par64.cu"]
+# The FMA-throughput microbenchmark (include/ctu_peaks.h) is a measurement aid
+# for the roofline, built as a library of its own beside libctu.so.
+PEAK_SOURCES = ["peaks/fma_peak.cu"]
+LIB_PEAKS = OUT_DIR / "libctu_peaks.so"
 # The float32 stages of the mixed paths divide and take square roots with the
 # approximate hardware forms (<= 2 ulp) and flush float32 denormals; float64
 # arithmetic is unaffected by these flags.
@@ -36,16 +40,25 @@ def flags(extra=()):
                    "-I", str(ROOT / "include"), "-I", str(CSRC)] + env + list(extra)
 
 
+def _link(objs, out):
+    tmp = OUT_DIR / f"{out.stem}.{os.getpid()}.so"
+    subprocess.run([nvcc(), "-shared", "-o", str(tmp)] + [str(o) for o in objs] + ARCH + ["-lcudart"],
+                   check=True)
+    os.replace(tmp, out)
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> Path:
+    """Build libctu.so (and the measurement library libctu_peaks.so); returns
+    the path of libctu.so."""
     OUT_DIR.mkdir(exist_ok=True)
-    deps = [CSRC / s for s in SOURCES] + list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) \
+    deps = [CSRC / s for s in SOURCES + PEAK_SOURCES] + list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) \
         + list((ROOT / "include").glob("*.h"))
-    if LIB.exists() and not force and not extra:
-        if LIB.stat().st_mtime >= max(p.stat().st_mtime for p in deps):
+    if LIB.exists() and LIB_PEAKS.exists() and not force and not extra:
+        if min(LIB.stat().st_mtime, LIB_PEAKS.stat().st_mtime) >= max(p.stat().st_mtime for p in deps):
             return LIB
     objs = []
     procs = []
-    for s in SOURCES:
+    for s in SOURCES + PEAK_SOURCES:
         o = OUT_DIR / (Path(s).stem + ".o")
         cmd = [nvcc(), "-c", str(CSRC / s), "-o", str(o)] + SOURCE_FLAGS.get(s, []) + flags(extra)
         if verbose:
@@ -61,10 +74,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> Path:
             failed.append(" ".join(cmd))
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-    tmp = OUT_DIR / f"libctu.{os.getpid()}.so"
-    subprocess.run([nvcc(), "-shared", "-o", str(tmp)] + [str(o) for o in objs] + ARCH + ["-lcudart"],
-                   check=True)
-    os.replace(tmp, LIB)
+    npk = len(PEAK_SOURCES)
+    _link(objs[:-npk], LIB)
+    _link(objs[-npk:], LIB_PEAKS)
     return LIB
 
 

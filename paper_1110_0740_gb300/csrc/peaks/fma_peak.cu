@@ -6,7 +6,7 @@
 // away, and is stored only in a branch no input takes.
 #include <cuda_runtime.h>
 
-#include "ctu.h"
+#include "ctu_peaks.h"
 
 namespace {
 

@@ -140,7 +140,6 @@ def _lib():
         L.ctu_fill_periodic.argtypes = [vp, vp, i64, ctypes.POINTER(ctu_patch), i32, vp]
         L.ctu_status_sync.argtypes = [vp, vp]
         L.ctu_floor_count.argtypes = [vp, ctypes.POINTER(i64), vp]
-        L.ctu_fma_peak.argtypes = [i32, i32, ctypes.POINTER(dbl), vp]
         L.ctu_copy.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctu_copy_box), i32, vp]
         L.ctu_pack.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctu_copy_box), i32, vp]
         L.ctu_unpack.argtypes = [vp, vp, i64, vp, ctypes.POINTER(ctu_copy_box), i32, vp]
@@ -328,10 +327,30 @@ def ctu_tag(ctx, U, stride, patches, sigma, eps, chi_r, tags, d_count=None, chi=
                           _ptr(chi) if chi is not None else None, _stream(stream)), "ctu_tag")
 
 
+_LP = None
+
+
+def _peaks_lib():
+    """The measurement library libctu_peaks.so (include/ctu_peaks.h), built
+    beside libctu.so."""
+    global _LP
+    if _LP is None:
+        p = _build.LIB_PEAKS
+        if not p.exists():
+            raise RuntimeError(f"libctu_peaks.so not built at {p}: run __graft_entry__.build()")
+        L = ctypes.CDLL(str(p))
+        L.ctu_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+        L.ctu_fma_peak.restype = ctypes.c_int
+        _LP = L
+    return _LP
+
+
 def ctu_fma_peak(fp64, iters=1 << 16, stream=None):
-    """Measured FMA throughput (flop/s) of the float32 or float64 pipe."""
+    """Measured FMA throughput (flop/s) of the float32 or float64 pipe
+    (measurement aid from libctu_peaks.so, not part of libctu.so)."""
     v = ctypes.c_double(0.0)
-    _check(_lib().ctu_fma_peak(int(bool(fp64)), int(iters), ctypes.byref(v), _stream(stream)), "ctu_fma_peak")
+    _check(_peaks_lib().ctu_fma_peak(int(bool(fp64)), int(iters), ctypes.byref(v), _stream(stream)),
+           "ctu_fma_peak")
     return v.value
 
 

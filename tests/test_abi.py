@@ -7,24 +7,35 @@ from pathlib import Path
 ROOT = Path(__file__).resolve().parents[1]
 
 
-def declared():
-    names = set()
-    for h in (ROOT / "include").glob("*.h"):
-        txt = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(ctu_\w+)\s*\(", txt, re.M):
-            names.add(m.group(1))
-    return names
+def declared(header="ctu.h"):
+    txt = re.sub(r"/\*.*?\*/", "", (ROOT / "include" / header).read_text(), flags=re.S)
+    return {m.group(1) for m in
+            re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(ctu_\w+)\s*\(", txt, re.M)}
+
+
+def test_every_header_is_checked():
+    assert sorted(h.name for h in (ROOT / "include").glob("*.h")) == ["ctu.h", "ctu_peaks.h"]
 
 
 def test_library_exports_every_declared_symbol():
     from paper_1110_0740_gb300 import _build
     lib = _build.build()
     L = ctypes.CDLL(str(lib))
-    names = declared()
+    names = declared("ctu.h")
     assert {"ctu_init", "ctu_dt", "ctu_step", "ctu_flux_registers", "ctu_status_sync",
             "ctu_step_noalloc"} <= names
     missing = [n for n in sorted(names) if not hasattr(L, n)]
     assert not missing, missing
+
+
+def test_measurement_library_is_separate():
+    """The FMA microbenchmark lives in libctu_peaks.so, not in libctu.so."""
+    from paper_1110_0740_gb300 import _build
+    _build.build()
+    P = ctypes.CDLL(str(_build.LIB_PEAKS))
+    assert declared("ctu_peaks.h") == {"ctu_fma_peak"}
+    assert hasattr(P, "ctu_fma_peak")
+    assert not hasattr(ctypes.CDLL(str(_build.LIB)), "ctu_fma_peak")
 
 
 def test_strerror_without_gpu():
