@@ -330,7 +330,22 @@ def run_ours(args):
                         "peak_source": f"{src} hbm_gbs"}
     plain = not (args.shock or args.kappa or args.nu or args.eta or args.kappa_par)
     if mixed and args.recon == "ppm" and args.riemann == "hlld" and plain:
-        roof["precision_split"] = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
+        ps = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
+        # the kernels run the float64-designated recoveries in double-float on
+        # the FP32 pipe, so the FP64 term of this bound does not bind them:
+        # the bound they face is the FP32 one, with every operation counted
+        ps["binds_these_kernels"] = False
+        ps["fp32_everything"] = {"flops_per_cell": ps["fp32_flops_per_cell"] + ps["fp64_flops_per_cell"],
+                                 "bound_cells_per_s": FP32_PEAK / (ps["fp32_flops_per_cell"]
+                                                                   + ps["fp64_flops_per_cell"]),
+                                 "frac": (value / world) / (FP32_PEAK / (ps["fp32_flops_per_cell"]
+                                                                         + ps["fp64_flops_per_cell"]))}
+        roof["precision_split"] = ps
+    roof["bases"] = ("frac: the dominant kernel's oracle-counted flops per launch / its CUDA-event time, "
+                     "against the FP32 (mixed) or FP64 pipe peak; step.frac: the whole step the same way; "
+                     "precision_split.frac: the split-precision whole-step bound, whose FP64 term these "
+                     "kernels do not face (double-float on the FP32 pipe); "
+                     "precision_split.fp32_everything.frac: the bound they face")
 
     # end-to-end through the public API with host buffers
     # every step copies its input state (the interior, 9 float64 fields of
@@ -345,60 +360,8 @@ def run_ours(args):
     e2e = None
     if not args.skip_e2e:
         c = make(primary)
-        box = ctu.make_copy_boxes([dict(dn=[n] * 3, sn=[n] * 3, lo=[0] * 3, hi=[n] * 3, shift=[0] * 3,
-                                        dbase=0, sbase=0)])
-        Ih_pin = Uh.reshape(9, n + 8, n + 8, n + 8)[:, 4:-4, 4:-4, 4:-4].contiguous().pin_memory()
-        Ubuf = [U, torch.empty_like(U)]
-        Obuf = [Uo, torch.empty_like(Uo)]
-        Ibuf = [torch.empty(Ih_pin.shape, dtype=torch.float64, device=dev) for _ in range(2)]
-        Pbuf = [torch.empty(Ih_pin.shape, dtype=torch.float64, device=dev) for _ in range(2)]
-        Oh = [torch.empty_like(Ih_pin).pin_memory() for _ in range(2)]
-        s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_cmp = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
-
-        def pipeline(K):
-            for k in range(K):
-                b = k % 2
-                if k >= 2:
-                    s_in.wait_event(ev_cmp[b])  # step k - 2 has read input buffer b
-                with torch.cuda.stream(s_in):
-                    Ibuf[b].copy_(Ih_pin, non_blocking=True)
-                    ev_in[b].record(s_in)
-                s_cmp.wait_event(ev_in[b])
-                if k >= 2:
-                    s_cmp.wait_event(ev_out[b])  # result buffer b has been read back
-                c.unpack(Ubuf[b], stride, Ibuf[b], box, stream=s_cmp)
-                c.fill_periodic(Ubuf[b], stride, patches, stream=s_cmp)
-                c.step_next_dt(Ubuf[b], Obuf[b], stride, patches, dtch, dtn, stream=s_cmp)
-                c.pack(Pbuf[b], Obuf[b], stride, box, stream=s_cmp)
-                ev_cmp[b].record(s_cmp)
-                s_out.wait_event(ev_cmp[b])
-                with torch.cuda.stream(s_out):
-                    Oh[b].copy_(Pbuf[b], non_blocking=True)
-                    ev_out[b].record(s_out)
-
-        E = max(4, args.steps)  # the timed steps include the pipeline's fill and drain
-        pipeline(2)
-        barrier()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(s_in)
-        pipeline(E)
-        t1.record(s_out)
-        barrier()
-        ems = t0.elapsed_time(t1) / E
-        torch.cuda.synchronize()
-        # the streamed result is the device step's (same input every step)
-        assert torch.equal(Oh[(E - 1) % 2], Obuf[(E - 1) % 2].reshape(9, n + 8, n + 8, n + 8)[:, 4:-4, 4:-4, 4:-4]
-                           .contiguous().cpu())
+        e2e = e2e_stream(c, Uh, U, Uo, n, stride, patches, dtch, dtn, max(4, args.steps), dev, world, barrier)
         c.close()
-        e2e = {"value": world * cells / (ems * 1e-3), "unit": "cell-updates/s",
-               "h2d_bytes_per_step": int(Ih_pin.numel() * 8), "d2h_bytes_per_step": int(Oh[0].numel() * 8),
-               "ms_per_step": ems, "steps": E,
-               "overlap": "two device buffers; packed-interior input copy, unpack + periodic ghost fill + "
-                          "step + pack, and read-back on three streams"}
 
     fp64_path = None
     if other in results:
@@ -439,6 +402,92 @@ def run_ours(args):
         print(json.dumps(line))
     if pg is not None:
         pg.destroy_process_group()
+
+
+def e2e_stream(c, Uh, U, Uo, n, stride, patches, dtch, dtn, E, dev, world, barrier):
+    """End to end through the public API with host buffers, one periodic n^3
+    patch: every step copies its input state (the interior, 9 float64 fields
+    of n^3 cells, packed) from pinned host memory and reads its result (the
+    updated interior, packed) back; on the device the library unpacks the
+    input into the ghosted patch, fills its periodic ghosts, steps and packs
+    the result (ctu_unpack, ctu_fill_periodic, ctu_step_next_dt, ctu_pack).
+    With two device copies of each buffer, the copy of step k + 1's input and
+    the read-back of step k - 1's result run on their own streams (both copy
+    directions) while step k computes, as a caller streaming states through
+    the library would arrange it.  The E timed steps include the pipeline's
+    fill and drain; the streamed result is checked against the device step."""
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    box = ctu.make_copy_boxes([dict(dn=[n] * 3, sn=[n] * 3, lo=[0] * 3, hi=[n] * 3, shift=[0] * 3,
+                                    dbase=0, sbase=0)])
+    Ih_pin = Uh.reshape(9, n + 8, n + 8, n + 8)[:, 4:-4, 4:-4, 4:-4].contiguous().pin_memory()
+    Ubuf = [U, torch.empty_like(U)]
+    Obuf = [Uo, torch.empty_like(Uo)]
+    Ibuf = [torch.empty(Ih_pin.shape, dtype=torch.float64, device=dev) for _ in range(2)]
+    Pbuf = [torch.empty(Ih_pin.shape, dtype=torch.float64, device=dev) for _ in range(2)]
+    Oh = [torch.empty_like(Ih_pin).pin_memory() for _ in range(2)]
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_cmp = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+
+    def pipeline(K):
+        for k in range(K):
+            b = k % 2
+            if k >= 2:
+                s_in.wait_event(ev_cmp[b])  # step k - 2 has read input buffer b
+            with torch.cuda.stream(s_in):
+                Ibuf[b].copy_(Ih_pin, non_blocking=True)
+                ev_in[b].record(s_in)
+            s_cmp.wait_event(ev_in[b])
+            if k >= 2:
+                s_cmp.wait_event(ev_out[b])  # result buffer b has been read back
+            c.unpack(Ubuf[b], stride, Ibuf[b], box, stream=s_cmp)
+            c.fill_periodic(Ubuf[b], stride, patches, stream=s_cmp)
+            c.step_next_dt(Ubuf[b], Obuf[b], stride, patches, dtch, dtn, stream=s_cmp)
+            c.pack(Pbuf[b], Obuf[b], stride, box, stream=s_cmp)
+            ev_cmp[b].record(s_cmp)
+            s_out.wait_event(ev_cmp[b])
+            with torch.cuda.stream(s_out):
+                Oh[b].copy_(Pbuf[b], non_blocking=True)
+                ev_out[b].record(s_out)
+
+    pipeline(2)
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(s_in)
+    pipeline(E)
+    t1.record(s_out)
+    barrier()
+    ems = t0.elapsed_time(t1) / E
+    torch.cuda.synchronize()
+    # the streamed result is the device step's (same input every step)
+    assert torch.equal(Oh[(E - 1) % 2], Obuf[(E - 1) % 2].reshape(9, n + 8, n + 8, n + 8)[:, 4:-4, 4:-4, 4:-4]
+                       .contiguous().cpu())
+    return {"value": world * n ** 3 / (ems * 1e-3), "unit": "cell-updates/s",
+            "h2d_bytes_per_step": int(Ih_pin.numel() * 8), "d2h_bytes_per_step": int(Oh[0].numel() * 8),
+            "ms_per_step": ems, "steps": E,
+            "overlap": "two device buffers; packed-interior input copy, unpack + periodic ghost fill + "
+                       "step + pack, and read-back on three streams"}
+
+
+def roofline_alu(kern, flops, mixed, traffic=None):
+    """Kernel roofline of the dominant kernel group: kern maps a kernel name
+    to (total ms, launches) over the timed region, flops maps it to the
+    algorithmic flops of one launch; ALU-bound on the FP32 pipe (mixed) or the
+    FP64 pipe."""
+    top_name, (top_ms, top_cnt) = max(kern.items(), key=lambda kv: kv[1][0])
+    top_avg = top_ms / max(1, top_cnt)
+    peak_tf = (FP32_PEAK if mixed else FP64_PEAK) / 1e12
+    f_top = flops.get(top_name, 0.0)
+    achieved = f_top / (top_avg * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+            "frac": achieved / peak_tf, "traffic": traffic, "kernel": top_name,
+            "pipe": "fp32" if mixed else "fp64",
+            "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if mixed else
+                            "derived: 152 SMs x 2 FP64 lanes x 2 x 2070 MHz (GB300 nominal 1.25 TF)"),
+            "flops_per_launch": f_top, "kernel_avg_ms": top_avg}
 
 
 def run_amr(args):
@@ -663,8 +712,82 @@ def run_amr(args):
     kern = {}
     for lev, c in enumerate(ctxs):
         for k_, (t_, n_) in c.profile_read().items():
-            kern[f"l{lev}_{k_}"] = t_
+            kern[f"l{lev}_{k_}"] = (t_, n_)
         c.profile(False)
+    # kernel roofline of the dominant step kernel (ALU-bound; flops per launch
+    # from the oracle's counts per interior cell times the level's cells on
+    # this rank); the level operators (prolongation, exchange, reflux,
+    # restriction) are float64 and carry no flop count
+    mixed = prec == ctu.CTU_MIXED
+    flops = {}
+    for lev in range(len(L)):
+        cl = sum(L[lev]["patches"][gi][0][0] * L[lev]["patches"][gi][0][1] * L[lev]["patches"][gi][0][2]
+                 for gi in mine[lev])
+        for k_, v_ in kernel_flops(1, "ppm", args.kappa, args.kappa_par, args.tc_phi, args.nu, args.eta,
+                                   cells=cl).items():
+            flops[f"l{lev}_{k_}"] = v_
+    roof = roofline_alu({k: v for k, v in kern.items() if k in flops}, flops, mixed)
+    roof["share_of_coarse_step"] = kern[roof["kernel"]][0] / sum(v[0] for v in kern.values())
+    # the oracle on a bounded sample of the finest level's patches (every size
+    # in turn), one step each, on one host core
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        import numpy as np
+        import oracle as O
+        L2 = L[-1]
+        by = {}
+        for gi, (n, dx, base, _) in enumerate(L2["patches"]):
+            by.setdefault(n[0], []).append(gi)
+        from itertools import zip_longest
+        order = [gi for grp in zip_longest(*[by[k] for k in sorted(by)]) for gi in grp if gi is not None]
+        dtl, chl = float(D[-1][0]), float(D[-1][1])
+        t0, done, used = time.perf_counter(), 0, 0
+        for gi in order:
+            n, dx, base, _ = L2["patches"][gi]
+            N = [v + 8 for v in n]
+            blk = np.ascontiguousarray(L2["pool"][:, base:base + N[0] * N[1] * N[2]].reshape(9, N[2], N[1], N[0]))
+            O.mhd_step(blk, list(n), 3, list(dx), dtl, chl, recon=1)
+            done += n[0] * n[1] * n[2]
+            used += 1
+            if time.perf_counter() - t0 > 10.0:
+                break
+        el = time.perf_counter() - t0
+        cpu = {"value": done / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{used} finest-level patches (sizes {sorted(by)} in turn), one CTU step each, 1 thread",
+               "seconds": el}
+    # end to end through the public API with host buffers: every coarse step
+    # copies every level's ghosted pool from pinned host memory, replays the
+    # captured coarse step and reads every level's result pool back
+    e2e = None
+    if world == 1 and not args.skip_e2e:
+        Hin = [torch.from_numpy(lv["pool"]).pin_memory() for lv in L]
+        outs = [B[0], A[1], A[2]]  # where the coarse step leaves each level
+        Hout = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+
+        def e2e_step():
+            for lev in range(len(L)):
+                A[lev].copy_(Hin[lev], non_blocking=True)
+            g.replay()
+            for lev in range(len(L)):
+                Hout[lev].copy_(outs[lev], non_blocking=True)
+
+        with torch.cuda.stream(stream):
+            e2e_step()
+        barrier()
+        E = max(3, args.steps)
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            t0e.record(stream)
+            for _ in range(E):
+                e2e_step()
+            t1e.record(stream)
+        barrier()
+        ems = t0e.elapsed_time(t1e) / E
+        e2e = {"value": upd / (ems * 1e-3), "unit": "cell-updates/s",
+               "h2d_bytes_per_step": int(sum(h.numel() * 8 for h in Hin)),
+               "d2h_bytes_per_step": int(sum(h.numel() * 8 for h in Hout)),
+               "ms_per_step": ems, "steps": E,
+               "overlap": "none: pools in, captured coarse step, pools out, in order on one stream"}
     launches = sum(c.launches() for c in ctxs[:1]) + 2 * ctxs[1].launches() + 4 * ctxs[2].launches()
     if ops:  # prolongations 2 + 4, refluxes and restrictions 2 + 1 each, exchanges 1 + 2 + 4
         launches += 6 + 3 + 3 + sum(2 ** lev for lev in xch)
@@ -692,8 +815,9 @@ def run_amr(args):
                            "exchange_boxes_per_level": {lev: len(b) for lev, b in xch.items()},
                            "tiles_xw_seg": tiles,
                            "l2_flush": "inputs larger than L2"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * args.steps, "clocks": clk,
-                "kernels_ms_per_coarse_step": kern,
+                "kernels_ms_per_coarse_step": {k: v[0] for k, v in kern.items()},
                 "status": [ctu.STATUS[x] for x in st], "gpu": torch.cuda.get_device_name(dev)}
         print(json.dumps(line))
     if pg is not None:
@@ -729,23 +853,66 @@ def run_srmhd(args):
             c.step_next_dt(U, Uo, stride, patches, d0, d1)
         torch.cuda.synchronize()
         c.profile(True)
+        if prec == ctu.CTU_MIXED:
+            clocks = Clocks(local)
+            clocks.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(K):
             c.step_next_dt(U, Uo, stride, patches, d0, d1)
         e1.record()
         torch.cuda.synchronize()
+        if prec == ctu.CTU_MIXED:
+            clk = clocks.stop()
         ms = e0.elapsed_time(e1) / K
         res[prec] = (ms, {k: v[0] / K for k, v in c.profile_read().items()}, c.status_sync(),
                      c.launches())
+        if prec == ctu.CTU_MIXED:
+            K_mixed = K
         c.close()
     ms, kern, st, nl = res[ctu.CTU_MIXED]
+    roof = roofline_alu({k: (v * K_mixed, K_mixed) for k, v in kern.items()},
+                        kernel_flops(n, physics="srmhd"), True)
+    # the oracle on a bounded sample: a 32^3 block of the jet (its true
+    # neighbours as ghosts), repeated steps for about 10 s, one host core
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        import oracle as O
+        sub, g_ = min(32, n), 4
+        c0 = [int(v * n) for v in (0.5, 0.5, 0.5)]
+        lo = [min(max(0, c - sub // 2), n - sub) for c in c0]
+        blk = U0[:, lo[2]:lo[2] + sub + 2 * g_, lo[1]:lo[1] + sub + 2 * g_, lo[0]:lo[0] + sub + 2 * g_].copy()
+        dx = [1.0 / n] * 3
+        m = O.srmhd_max_speed(blk, [sub] * 3, 3, dx)
+        dt, chs = O.dt_ch(m, dx, 3, 0.3)
+        t0, done = time.perf_counter(), 0
+        while time.perf_counter() - t0 < 10.0 and done < 64:
+            O.srmhd_step(blk, [sub] * 3, 3, dx, dt, chs, gamma=4.0 / 3.0)
+            done += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": sub ** 3 * done / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sub}^3 block of the {n}^3 jet, {done} CTU step(s), 1 thread", "seconds": el}
+    e2e = None
+    if not args.skip_e2e:
+        c = ctu.Ctx(ctu.make_config(ndim=3, gamma=4.0 / 3.0, recon=ctu.CTU_LINEAR_MC, precision=ctu.CTU_MIXED,
+                                    cfl=0.3, physics=ctu.CTU_SRMHD, predictor=ctu.CTU_MUSCL_HANCOCK,
+                                    riemann=ctu.CTU_HLL))
+        d0 = torch.zeros(2, dtype=torch.float64, device=dev)
+        d1 = torch.zeros_like(d0)
+        c.dt(U, stride, patches, d0)
+
+        def barrier():
+            torch.cuda.synchronize()
+        e2e = e2e_stream(c, torch.from_numpy(U0.reshape(9, -1)), U, Uo, n, stride, patches, d0, d1,
+                         max(4, args.steps), dev, world, barrier)
+        c.close()
     line = {"metric": METRIC, "value": world * n ** 3 / (ms * 1e-3), "unit": "cell-updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": "3D SRMHD 256^3 jet, Gamma 4/3, gamma 10 beam, density ratio 0.01,"
                                    " sigma 0.1; MUSCL-Hancock, HLL, GLM, float64 Newton recovery"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "kernels_ms_per_step": kern, "gpu_launches": nl * args.steps,
             "status": ctu.STATUS[st], "gpu": torch.cuda.get_device_name(dev)}
     if ctu.CTU_FP64 in res:
@@ -874,14 +1041,22 @@ def _profile_numbers(name):
     return vals
 
 
-def kernel_flops(n, recon="ppm", kappa=0.0, kappa_par=0.0, tc_phi=0.0, nu=0.0, eta=0.0):
+def kernel_flops(n, recon="ppm", kappa=0.0, kappa_par=0.0, tc_phi=0.0, nu=0.0, eta=0.0, cells=None,
+                 physics="mhd"):
     """Algorithmic flops per launch of each kernel group of one 3-D step on an
-    n^3 patch: the oracle's operation counts per interior cell
-    (profiles/flops_per_cell.txt, exact-zero operands not counted) times n^3.
-    With parabolic terms the x sweep leaves the update and the next dt to
-    par_update, and par_half forms L_P^n and the half-step fields."""
+    n^3 patch (or on `cells` interior cells, a batch): the oracle's operation
+    counts per interior cell (profiles/flops_per_cell.txt, exact-zero
+    operands not counted) times the cells.  With parabolic terms the x sweep
+    leaves the update and the next dt to par_update, and par_half forms L_P^n
+    and the half-step fields; one face flux is the count of the exact
+    combination of terms on."""
     c = {k: float(v) for k, v in _profile_numbers("flops_per_cell.txt").items()}
-    cells = float(n) ** 3
+    cells = float(n) ** 3 if cells is None else float(cells)
+    if physics == "srmhd":
+        sw = c.get("sr_sweep_per_direction", 0.0)
+        return {"prim": c.get("sr_prim", 0.0) * cells, "flux1": 3 * c.get("sr_flux1_per_direction", 0.0) * cells,
+                "sweep_z": sw * cells, "sweep_y": sw * cells,
+                "sweep_x": (sw + c.get("update", 0.0) + c.get("sr_next_dt", 0.0)) * cells}
     sweep = c.get("sweep_per_direction_" + ("linear" if recon == "mc" else recon), 0.0)
     kp = kappa_par if kappa_par > 0 else kappa
     if not (kappa or kappa_par or nu or eta):
@@ -889,16 +1064,12 @@ def kernel_flops(n, recon="ppm", kappa=0.0, kappa_par=0.0, tc_phi=0.0, nu=0.0, e
         return {"prim": c.get("prim", 0.0) * cells, "flux1": 3 * c.get("flux1_per_direction", 0.0) * cells,
                 "sweep_z": sweep * cells, "sweep_y": sweep * cells,
                 "sweep_x": (sweep + c.get("update", 0.0) + c.get("next_dt", 0.0)) * cells}
-    # one face flux: the conduction variant plus viscosity and resistivity
-    face = 0.0
+    # one face flux with every term on, counted together
+    cond = "none"
     if kappa or kp:
-        key = "par_face_" + ("sat" if tc_phi else "") + ("_" if tc_phi and kp != kappa else "") + \
-              ("aniso" if kp != kappa else ("" if tc_phi else "cond"))
-        face += c.get(key, 0.0)
-    if nu:
-        face += c.get("par_face_visc", 0.0)
-    if eta:
-        face += c.get("par_face_res", 0.0)
+        cond = ("sat_" if tc_phi else "") + ("aniso" if kp != kappa else ("" if tc_phi else "cond"))
+        cond = cond.rstrip("_")
+    face = c.get(f"par_mask_{cond}_{1 if nu else 0}_{1 if eta else 0}", 0.0)
     m = 1 + (3 if nu else 0) + (3 if eta else 0)
     swp = sweep + m * c.get("sweep_par_per_component", 0.0)
     half = (c.get("par_half_per_cell", 0.0) + 3 * face + m * c.get("par_half_per_component", 0.0)

@@ -61,6 +61,7 @@ using fc::exp;
 
 #define double Flop
 #include "ctu_oracle.c"
+#include "srmhd_oracle.c"
 #undef double
 
 static double total(const fc::Counts &c)
@@ -109,8 +110,50 @@ static double face_count(double kappa, double kpar, double phi, double nu, doubl
     return tot / nf;
 }
 
-int main()
+// Relativistic MHD (srmhd_oracle.c): input K, Gamma, ch, dtdx, then K
+// records of 3 x 9 primitive values (cells i - 1, i, i + 1, local order)
+// and 9 conserved values of cell i.  Prints the average counts per call.
+static int count_srmhd()
 {
+    int K;
+    double gam, ch, dtdx;
+    if (scanf("%d %lf %lf %lf", &K, &gam, &ch, &dtdx) != 4) return 1;
+    double r_riem = 0, r_pred = 0, r_p2c = 0, r_c2p = 0, r_fs = 0;
+    for (int k = 0; k < K; ++k) {
+        double in[36];
+        for (int i = 0; i < 36; ++i)
+            if (scanf("%lf", &in[i]) != 1) return 1;
+        Flop vs[27], U0[9], VL[9], VR[9], F[9], Vp[9], Vm[9], U[9], V[9], lm, lp;
+        for (int i = 0; i < 27; ++i) vs[i] = Flop(in[i]);
+        for (int q = 0; q < 9; ++q) {
+            U0[q] = Flop(in[27 + q]);
+            VL[q] = vs[9 + q];
+            VR[q] = vs[18 + q];
+        }
+        fc::g = fc::Counts();
+        or_srmhd_riemann(VL, VR, Flop(gam), Flop(ch), F);
+        r_riem += total(fc::g);
+        fc::g = fc::Counts();
+        or_srmhd_mh_predict(vs, U0, Flop(gam), Flop(ch), Flop(dtdx), Vp, Vm);
+        r_pred += total(fc::g);
+        fc::g = fc::Counts();
+        or_srmhd_prim2cons(VL, Flop(gam), U);
+        r_p2c += total(fc::g);
+        fc::g = fc::Counts();
+        or_srmhd_cons2prim(U0, Flop(gam), V);
+        r_c2p += total(fc::g);
+        fc::g = fc::Counts();
+        or_srmhd_fast_speeds(VL, Flop(gam), &lm, &lp);
+        r_fs += total(fc::g);
+    }
+    printf("sr_riemann %.2f\nsr_predict %.2f\nsr_prim2cons %.2f\nsr_cons2prim %.2f\nsr_fast_speeds %.2f\n",
+           r_riem / K, r_pred / K, r_p2c / K, r_c2p / K, r_fs / K);
+    return 0;
+}
+
+int main(int argc, char **argv)
+{
+    if (argc > 1 && !strcmp(argv[1], "srmhd")) return count_srmhd();
     // input: count K, gamma, ch, dtdx, then K stencils of 5 x 9 values (local order)
     int K;
     double gam, ch, dtdx;
@@ -160,5 +203,17 @@ int main()
            face_count(1e-3, 1e-3, 1e-2, 0.0, 0.0), face_count(1e-3, 1e-2, 1e-2, 0.0, 0.0));
     printf("par_face_visc %.2f\npar_face_res %.2f\n", face_count(0.0, 0.0, 0.0, 1e-3, 0.0),
            face_count(0.0, 0.0, 0.0, 0.0, 1e-3));
+    // every combination of the terms, counted together (work the terms share,
+    // the face means and differences, is counted once): par_mask_<c>_<v>_<r>
+    // with c = none, cond, aniso, sat, sat_aniso and v, r = 0/1
+    const char *cn[5] = {"none", "cond", "aniso", "sat", "sat_aniso"};
+    const double ck[5][3] = {{0, 0, 0}, {1e-3, 1e-3, 0}, {1e-3, 1e-2, 0}, {1e-3, 1e-3, 1e-2}, {1e-3, 1e-2, 1e-2}};
+    for (int c = 0; c < 5; ++c)
+        for (int v = 0; v < 2; ++v)
+            for (int r = 0; r < 2; ++r) {
+                if (c == 0 && v == 0 && r == 0) continue;
+                printf("par_mask_%s_%d_%d %.2f\n", cn[c], v, r,
+                       face_count(ck[c][0], ck[c][1], ck[c][2], v ? 1e-3 : 0.0, r ? 1e-3 : 0.0));
+            }
     return 0;
 }

@@ -40,12 +40,17 @@ def test_kernel_flops_parabolic(terms):
     for k in ("prim", "flux1", "par_half", "sweep_z", "sweep_y", "sweep_x", "par_update"):
         assert fl[k] > 0, k
     kappa, kp = terms.get("kappa", 0.0), terms.get("kappa_par", 0.0) or terms.get("kappa", 0.0)
-    face = 0.0
+    cond = "none"
     if kappa:
-        face += c["par_face_" + {(False, False): "cond", (True, False): "aniso", (False, True): "sat",
-                                 (True, True): "sat_aniso"}[(kp != kappa, bool(terms.get("tc_phi")))]]
-    face += c["par_face_visc"] if terms.get("nu") else 0.0
-    face += c["par_face_res"] if terms.get("eta") else 0.0
+        cond = {(False, False): "cond", (True, False): "aniso", (False, True): "sat",
+                (True, True): "sat_aniso"}[(kp != kappa, bool(terms.get("tc_phi")))]
+    # the face flux of the exact combination of terms, counted together
+    face = c[f"par_mask_{cond}_{int(bool(terms.get('nu')))}_{int(bool(terms.get('eta')))}"]
+    # one term alone: its combination count is its own line
+    if sum(bool(terms.get(k)) for k in ("nu", "eta")) + (cond != "none") == 1:
+        single = (c["par_face_" + cond] if cond != "none" else 0.0) + \
+            (c["par_face_visc"] if terms.get("nu") else 0.0) + (c["par_face_res"] if terms.get("eta") else 0.0)
+        assert face == single
     m = 1 + 3 * bool(terms.get("nu")) + 3 * bool(terms.get("eta"))
     extra = (6 * face + m * (c["par_half_per_component"] + c["par_update_per_component"]
                              + 3 * c["sweep_par_per_component"])
@@ -53,6 +58,17 @@ def test_kernel_flops_parabolic(terms):
     assert sum(fl.values()) == pytest.approx(sum(plain.values()) + extra, rel=1e-12)
     # the counted face work of each term is not trivial
     assert face >= 3
+
+
+def test_kernel_flops_srmhd_and_batches():
+    """The relativistic step's groups take the relativistic counts, and a
+    batch's flops scale with its interior cells."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = {k: float(v) for k, v in bench._profile_numbers("flops_per_cell.txt").items()}
+    sr = bench.kernel_flops(1, physics="srmhd")
+    assert sum(sr.values()) == pytest.approx(c["sr_step_total"], rel=1e-3)
+    assert bench.kernel_flops(4, cells=1000)["sweep_y"] == pytest.approx(1000 * bench.kernel_flops(1)["sweep_y"])
 
 
 def test_reference_arm_json_line():
