@@ -318,10 +318,12 @@ static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStr
 // Scratch layout: SCRATCH_ARRAYS planes of the working precision, then (each
 // 256-byte aligned) the shock flags of the hybrid integration (one byte per
 // scratch cell) and, with the parabolic terms, L_P^n (seven words of the
-// working precision) and the half-step fields (one 8-byte plane, T; eight
-// with viscosity, resistivity or anisotropic conduction) per scratch cell.
+// working precision), the half-step fields (one 8-byte plane, T; eight
+// with viscosity, resistivity or anisotropic conduction) and the face fluxes
+// of the parabolic face pass (3 directions x 7 words of the working
+// precision) per scratch cell.
 struct ScratchOffsets {
-    size_t flags, lp, th, total;
+    size_t flags, lp, th, pif, total;
 };
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 static ScratchOffsets scratch_offsets(const ctu_ctx *ctx)
@@ -335,7 +337,8 @@ static ScratchOffsets scratch_offsets(const ctu_ctx *ctx)
     const bool par = ctx->cfg.kappa > 0.0 || kpar > 0.0 || tensor;
     o.lp = align256(o.flags + (ctx->cfg.shock_detect ? S : 0));
     o.th = align256(o.lp + (par ? 7 * S * elt : 0));
-    o.total = o.th + (par ? (tensor ? 8 : 1) * S * sizeof(double) : 0);
+    o.pif = align256(o.th + (par ? (tensor ? 8 : 1) * S * sizeof(double) : 0));
+    o.total = o.pif + (par ? 3 * 7 * S * elt : 0);
     return o;
 }
 
@@ -393,12 +396,14 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.gm1lo = tm ? 0.0f : (float)((ctx->cfg.gamma - 1.0) - (double)a.gm1f);
     a.lp = nullptr;
     a.th = nullptr;
+    a.pif = nullptr;
     if (ctx->scratch) {
         const ScratchOffsets o = scratch_offsets(ctx);
         if (ctx->cfg.shock_detect) a.flags = (unsigned char *)ctx->scratch + o.flags;
         if (a.par_cond || a.par_visc || a.par_res) {
             a.lp = (const unsigned char *)ctx->scratch + o.lp;
             a.th = (double *)((unsigned char *)ctx->scratch + o.th);
+            a.pif = (unsigned char *)ctx->scratch + o.pif;
         }
     }
     a.U = Uin;

@@ -91,6 +91,7 @@ struct StepArgs {
     int par_cond, par_visc, par_res, par_aniso, par_sat;
     const void *lp;
     double *th;
+    void *pif;             // face fluxes of the parabolic face pass (3 x NPAR planes of R)
     const double *U;       // pool in
     double *Uout;          // pool out
     long long ustride;     // pool variable stride

@@ -150,9 +150,14 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         auto half = [&](auto tm) {
             constexpr int V = decltype(tm)::value;
             n += over_groups(
+                li, [&](const Group &G) { return ((long long)par_face_box(G.n, a.ndim, 1) + BLOCK - 1) / BLOCK; },
+                [&](const GroupTable &gt, unsigned nb) {
+                    k_par_faces<R, V, 1><<<nb, BLOCK, 0, s>>>(a, gt, Vs, a.th, (R *)a.pif);
+                });
+            n += over_groups(
                 li, [&](const Group &G) { return ((long long)par_ring_cells(G.n, a.ndim) + BLOCK - 1) / BLOCK; },
                 [&](const GroupTable &gt, unsigned nb) {
-                    k_par_half<R, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th);
+                    k_par_half<R, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th, (const R *)a.pif);
                 });
         };
         // one kernel per combination of the terms beyond isotropic conduction
@@ -186,13 +191,19 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     CTU_MARK(nullptr);
     if constexpr (recon_par(PPM)) {  // parabolic terms: + dt L_P^(n+1/2)
         CTU_MARK("par_update");
-        n += over_groups(
-            li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
-            [&](const GroupTable &gt, unsigned nb) {
-                with_tm(par_mask(a), [&](auto tm) {
-                    k_par_update<PHYS, R, decltype(tm)::value><<<nb, BLOCK, 0, s>>>(a, gt, a.th, a.nextmax);
+        with_tm(par_mask(a), [&](auto tm) {
+            constexpr int V = decltype(tm)::value;
+            n += over_groups(
+                li, [&](const Group &G) { return ((long long)par_face_box(G.n, a.ndim, 0) + BLOCK - 1) / BLOCK; },
+                [&](const GroupTable &gt, unsigned nb) {
+                    k_par_faces<R, V, 0><<<nb, BLOCK, 0, s>>>(a, gt, Vs, a.th, (R *)a.pif);
                 });
-            });
+            n += over_groups(
+                li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
+                [&](const GroupTable &gt, unsigned nb) {
+                    k_par_update<PHYS, R, V><<<nb, BLOCK, 0, s>>>(a, gt, (const R *)a.pif, a.nextmax);
+                });
+        });
         CTU_MARK(nullptr);
     }
     return n;

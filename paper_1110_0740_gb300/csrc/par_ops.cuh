@@ -19,6 +19,9 @@
 // Pi_(d,-)) / dx_d acts on the momentum, the energy and B.
 //
 // Kernels around the hyperbolic step:
+//   k_par_faces  the face pass: every face flux of the ring box (from the
+//                primitive fields of U^n) or of the interior (from the
+//                half-step fields) once, stored per face
 //   k_par_half   after the first-order stage, on the ring box (the interior
 //                and one layer around it): L_P^n from the primitive fields of
 //                U^n (the predictors of every direction add dt/2 L_P^n, Eq.
@@ -180,32 +183,106 @@ __device__ __forceinline__ void par_face(const StepArgs &a, const DevPatch &P, l
     }
 }
 
-// L_P at scratch cell c: sum_d (Pi(c, d) - Pi(c - e_d, d)) / dx_d; faces(d,
-// Pm, Pp) receives each direction's lower and upper face fluxes.
-template <class R, int TM, class Get, class Dif, class Faces>
-__device__ __forceinline__ void par_lp(const StepArgs &a, const DevPatch &P, long long c, Get get, Dif dif,
-                                       R (&lp)[NPAR], Faces faces)
-{
-#pragma unroll
-    for (int q = 0; q < NPAR; ++q) lp[q] = R(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (d >= a.ndim) continue;
-        R Pp[NPAR], Pm[NPAR];
-        par_face<R, TM>(a, P, c, d, get, dif, Pp);
-        par_face<R, TM>(a, P, c - dstr(P, d), d, get, dif, Pm);
-        const R ih = pidx<R>(P, d);
-#pragma unroll
-        for (int q = 0; q < NPAR; ++q) lp[q] += (Pp[q] - Pm[q]) * ih;
-        faces(d, Pm, Pp);
-    }
-}
-
 // Cells of the ring box (the interior and one layer around it on the active
 // axes), x fastest: coordinates in [-1, n_d] on active axes, 0 on the others.
 __host__ __device__ __forceinline__ int par_ring_cells(const int *n, int ndim)
 {
     return (n[0] + 2) * (ndim > 1 ? n[1] + 2 : 1) * (ndim > 2 ? n[2] + 2 : 1);
+}
+
+// Face pass: every face flux once.  For every cell c of the box [b, n - b]
+// on the active axes (b = -1 with HALF, the faces of the ring box, for
+// L_P^n; b = 0, the faces of the interior, for L_P^(n+1/2)), the flux
+// through its lower face along each active d whose transverse coordinates
+// lie in [b, n - 1 - b] is stored in PiF[(d NPAR + q) S + c] for the entries
+// q the terms change.  HALF: fields of U^n from the primitive state V (T =
+// p / rho); otherwise the half-step fields Wh (par_plane; double-float pairs
+// in the mixed path).
+__host__ __device__ __forceinline__ int par_face_box(const int *n, int ndim, int half)
+{
+    const int w = half ? 3 : 1;
+    return (n[0] + w) * (ndim > 1 ? n[1] + w : 1) * (ndim > 2 ? n[2] + w : 1);
+}
+
+template <class R, int TM, int HALF>
+__global__ void __launch_bounds__(BLOCK) k_par_faces(StepArgs a, GroupTable gt, const R *Vs, const double *Wh,
+                                                     R *PiF)
+{
+    const Where w = locate(gt);
+    const DevPatch P = a.patches[w.patch];
+    const int t = w.b * BLOCK + threadIdx.x;
+    if (t >= par_face_box(P.n, a.ndim, HALF)) return;
+    constexpr int bb = HALF ? -1 : 0;
+    const int e0 = P.n[0] + 1 - 2 * bb, e1 = a.ndim > 1 ? P.n[1] + 1 - 2 * bb : 1;
+    int x[3];
+    x[0] = t % e0 + bb;
+    x[1] = (t / e0) % e1 + (a.ndim > 1 ? bb : 0);
+    x[2] = t / (e0 * e1) + (a.ndim > 2 ? bb : 0);
+    const long long S = a.sstride;
+    const long long c = P.soff + lcell(P, x[0], x[1], x[2]);
+    auto on = [](int q) -> bool { return q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0); };
+    auto pass = [&](auto get, auto dif) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= a.ndim) continue;
+            bool ok = true;
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                if (e != d && e < a.ndim) ok &= x[e] <= P.n[e] - 1 - bb;
+            if (!ok) continue;
+            R Pi[NPAR];
+            par_face<R, TM>(a, P, c - dstr(P, d), d, get, dif, Pi);
+#pragma unroll
+            for (int q = 0; q < NPAR; ++q)
+                if (on(q)) PiF[(long long)(d * NPAR + q) * S + c] = Pi[q];
+        }
+    };
+    if constexpr (HALF) {
+        auto get = [&](int f, long long i) -> R { return f == 4 ? Vs[4 * S + i] / Vs[i] : Vs[f * S + i]; };
+        pass(get, [&](int f, long long i, long long j) -> R { return get(f, i) - get(f, j); });
+    } else if constexpr (sizeof(R) == 8) {
+        pass([&](int f, long long n) -> double { return Wh[par_plane(f) * S + n]; },
+             [&](int f, long long n1, long long n2) -> double {
+                 return Wh[par_plane(f) * S + n1] - Wh[par_plane(f) * S + n2];
+             });
+    } else {
+        // temperature differences of the double-float fields, exact to float;
+        // those of v and B, coefficients of a small increment, in float
+        const float2 *W2 = reinterpret_cast<const float2 *>(Wh);
+        pass([&](int f, long long n) -> float { return W2[par_plane(f) * S + n].x; },
+             [&](int f, long long n1, long long n2) -> float {
+                 const float2 u = W2[par_plane(f) * S + n1], v = W2[par_plane(f) * S + n2];
+                 return f == 4 ? df_add(df{u.x, u.y}, df{-v.x, -v.y}).hi : u.x - v.x;
+             });
+    }
+}
+
+// L_P at scratch cell c from the face pass: sum_d (Pi(c + e_d, d) -
+// Pi(c, d)) / dx_d in the order x, y, z; Pm, Pp receive each direction's
+// lower and upper face fluxes through faces(d, Pm, Pp).
+template <class R, int TM, class Faces>
+__device__ __forceinline__ void par_lp_faces(const StepArgs &a, const DevPatch &P, long long c, const R *PiF,
+                                             R (&lp)[NPAR], Faces faces)
+{
+    const long long S = a.sstride;
+#pragma unroll
+    for (int q = 0; q < NPAR; ++q) lp[q] = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= a.ndim) continue;
+        const long long st = dstr(P, d);
+        const R ih = pidx<R>(P, d);
+        R Pm[NPAR], Pp[NPAR];
+#pragma unroll
+        for (int q = 0; q < NPAR; ++q) {
+            const bool on = q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0);
+            const R *F = PiF + (long long)(d * NPAR + q) * S + c;
+            Pm[q] = on ? F[0] : R(0);
+            Pp[q] = on ? F[st] : R(0);
+            lp[q] += (Pp[q] - Pm[q]) * ih;
+        }
+        faces(d, Pm, Pp);
+    }
 }
 
 // One thread per ring-box cell (par_ring_cells), whose first-order
@@ -217,7 +294,7 @@ __host__ __device__ __forceinline__ int par_ring_cells(const int *n, int ndim)
 // saturated conduction (which need the B and rho fields).
 template <class R, int TM>
 __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *LP,
-                                                    double *Wh)
+                                                    double *Wh, const R *PiF)
 {
     const Where w = locate(gt);
     const DevPatch P = a.patches[w.patch];
@@ -231,11 +308,9 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
     const int cl = lcell(P, x[0], x[1], x[2]);
     const long long S = a.sstride;
     const long long c = P.soff + cl;
-    // L_P^n from the primitive fields of U^n (T = p / rho)
-    auto get = [&](int f, long long i) -> R { return f == 4 ? Vs[4 * S + i] / Vs[i] : Vs[f * S + i]; };
-    auto dif = [&](int f, long long i, long long j) -> R { return get(f, i) - get(f, j); };
+    // L_P^n from the face pass over the primitive fields of U^n (T = p / rho)
     R lp[NPAR];
-    par_lp<R, TM>(a, P, c, get, dif, lp, [](int, const R (&)[NPAR], const R (&)[NPAR]) {});
+    par_lp_faces<R, TM>(a, P, c, PiF, lp, [](int, const R (&)[NPAR], const R (&)[NPAR]) {});
     LP[3 * S + c] = lp[3];
     // the components each term changes: momentum (viscosity), energy, B
     // (resistivity)
@@ -348,12 +423,12 @@ __device__ __forceinline__ void par_register_d(const StepArgs &a, const DevPatch
 }
 
 // U_out's momentum, energy and B += dt L_P^(n+1/2) on the interior cells (the
-// k_maxspeed tiling); the flux registers of the cell's lower faces (and of
-// its upper faces on the patch's last plane) gain -dt A Pi; with next !=
-// null also the CFL rate of the updated cell, Eq. (Ca) with the diffusion
-// term, folded into *next.
+// k_maxspeed tiling), L_P^(n+1/2) from the face pass's fluxes PiF; the flux
+// registers of the cell's lower faces (and of its upper faces on the patch's
+// last plane) gain -dt A Pi; with next != null also the CFL rate of the
+// updated cell, Eq. (Ca) with the diffusion term, folded into *next.
 template <int PHYS, class R, int TM>
-__global__ void __launch_bounds__(BLOCK) k_par_update(StepArgs a, GroupTable gt, const double *Wh,
+__global__ void __launch_bounds__(BLOCK) k_par_update(StepArgs a, GroupTable gt, const R *PiF,
                                                       unsigned long long *next)
 {
     const Where wh = locate(gt);
@@ -364,12 +439,7 @@ __global__ void __launch_bounds__(BLOCK) k_par_update(StepArgs a, GroupTable gt,
     const int i = (b % T0) * t.xw + t.tx(), j = ((b / T0) % T1) * t.rows + t.ty(), k = b / (T0 * T1);
     R m = R(0);
     const bool act = i < P.n[0] && j < P.n[1] && k < P.n[2];
-    // the x-faces: every lane up to i = n_x evaluates its cell's lower face,
-    // and a cell's upper face is the next lane's lower face (the last lane
-    // of a tile row evaluates its own), taken by a shuffle within the row
-    const bool face0 = i <= P.n[0] && j < P.n[1] && k < P.n[2];
-    const int cl = face0 ? lcell(P, i, j, k) : 0;
-    const long long S = a.sstride;
+    const int cl = act ? lcell(P, i, j, k) : 0;
     const long long c = P.soff + cl;
     const int x[3] = {i, j, k};
     const double dt = a.sp->dt;
@@ -381,49 +451,7 @@ __global__ void __launch_bounds__(BLOCK) k_par_update(StepArgs a, GroupTable gt,
         if (x[d] == P.n[d] - 1) par_register_d<R, TM>(a, P, wh.patch, d, x[d] + 1, x, Pp, dt);
     };
     R lp[NPAR];
-    auto run = [&](auto get, auto dif) {
-        R Pm0[NPAR], Pp0[NPAR];
-        if (face0) {
-            par_face<R, TM>(a, P, c - 1, 0, get, dif, Pm0);
-        } else {
-#pragma unroll
-            for (int q = 0; q < NPAR; ++q) Pm0[q] = R(0);
-        }
-#pragma unroll
-        for (int q = 0; q < NPAR; ++q) Pp0[q] = __shfl_down_sync(0xffffffffu, Pm0[q], 1, t.xw);
-        if (act && t.tx() == t.xw - 1) par_face<R, TM>(a, P, c, 0, get, dif, Pp0);
-        if (!act) return;
-        const R ih0 = pidx<R>(P, 0);
-#pragma unroll
-        for (int q = 0; q < NPAR; ++q) lp[q] = (Pp0[q] - Pm0[q]) * ih0;
-        faces(0, Pm0, Pp0);
-#pragma unroll
-        for (int d = 1; d < 3; ++d) {
-            if (d >= a.ndim) continue;
-            R Pp[NPAR], Pm[NPAR];
-            par_face<R, TM>(a, P, c, d, get, dif, Pp);
-            par_face<R, TM>(a, P, c - dstr(P, d), d, get, dif, Pm);
-            const R ih = pidx<R>(P, d);
-#pragma unroll
-            for (int q = 0; q < NPAR; ++q) lp[q] += (Pp[q] - Pm[q]) * ih;
-            faces(d, Pm, Pp);
-        }
-    };
-    if constexpr (sizeof(R) == 8) {
-        run([&](int f, long long n) -> double { return Wh[par_plane(f) * S + n]; },
-            [&](int f, long long n1, long long n2) -> double {
-                return Wh[par_plane(f) * S + n1] - Wh[par_plane(f) * S + n2];
-            });
-    } else {
-        // temperature differences of the double-float fields, exact to float;
-        // those of v and B, coefficients of a small increment, in float
-        const float2 *W2 = reinterpret_cast<const float2 *>(Wh);
-        run([&](int f, long long n) -> float { return W2[par_plane(f) * S + n].x; },
-            [&](int f, long long n1, long long n2) -> float {
-                const float2 u = W2[par_plane(f) * S + n1], v = W2[par_plane(f) * S + n2];
-                return f == 4 ? df_add(df{u.x, u.y}, df{-v.x, -v.y}).hi : u.x - v.x;
-            });
-    }
+    if (act) par_lp_faces<R, TM>(a, P, c, PiF, lp, faces);
     if (act) {
         double *Uo = a.Uout + P.base + cl;
         // the conserved components 1 + q the parabolic terms change
