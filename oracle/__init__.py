@@ -65,6 +65,9 @@ def lib():
         L.or_mhd_step_ex.restype = I
         L.or_mhd_step_ex.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, I, I,
                                      ctypes.POINTER(ctypes.c_long), P, I, P, I, I, D, I]
+        L.or_mhd_step_mt.restype = I
+        L.or_mhd_step_mt.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, I, I,
+                                     ctypes.POINTER(ctypes.c_long), P, I, P, I, I, D, I]
         L.or_mhd_step_tc.restype = I
         L.or_mhd_step_tc.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, D, I, I,
                                      ctypes.POINTER(ctypes.c_long), P, I, P, I, I, D, I, D]
@@ -302,8 +305,12 @@ def fill_outflow(U, n, ndim):
 
 def mhd_step(U, n, ndim, dx, dt, ch, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
              windows=None, reg=None, upwind=0, shock=None, riemann=0, kappa=0.0, nu=0.0, eta=0.0,
-             kappa_par=None, phi=0.0):
+             kappa_par=None, phi=0.0, corner=0):
     """One CTU step of a ghost-filled patch; returns (Unew, n_bad_states).
+
+    corner = 1: the transverse fluxes from the normal predictor states (the
+    corner coupling of Mignone & Tzeferacos, or_mhd_step_mt; no parabolic
+    terms); 0: from the cell-centred states (Eq. transv).
 
     windows: optional list of (d, f, a0, a1, b0, b1, dst, weight) flux-register
     windows accumulated into the float64 array `reg` (see or_mhd_step).
@@ -332,7 +339,10 @@ def mhd_step(U, n, ndim, dx, dt, ch, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
             win.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(wgt),
             nwin, regp, int(riemann), *sh)
     kpar = kappa if kappa_par is None else kappa_par
-    if nu > 0.0 or eta > 0.0 or kpar != kappa or phi > 0.0:
+    if corner:
+        assert not (kappa > 0.0 or nu > 0.0 or eta > 0.0 or kpar > 0.0), "corner coupling with Pi = 0 only"
+        bad = lib().or_mhd_step_mt(*args)
+    elif nu > 0.0 or eta > 0.0 or kpar != kappa or phi > 0.0:
         bad = lib().or_mhd_step_par(*args, float(kappa), float(kpar), float(phi), float(nu), float(eta))
     elif kappa > 0.0:
         bad = lib().or_mhd_step_tc(*args, float(kappa))
@@ -508,7 +518,7 @@ def euler_sample(left, right, gamma, xi):
 
 def mhd_run(U, n, ndim, dx, steps, cfl, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
             bc="periodic", t_end=None, upwind=0, shock=None, riemann=0, kappa=0.0, nu=0.0, eta=0.0,
-            kappa_par=None, phi=0.0):
+            kappa_par=None, phi=0.0, corner=0):
     """Advance a patch `steps` CTU steps (or up to t_end), filling ghosts each
     step; returns (U, t, dts)."""
     U = np.array(U, dtype=np.float64, copy=True)
@@ -529,7 +539,8 @@ def mhd_run(U, n, ndim, dx, steps, cfl, gamma=5.0 / 3.0, glm_alpha=0.1, recon=1,
         if t_end is not None and t + dt > t_end:
             dt = t_end - t
         U, bad = mhd_step(U, n, ndim, dx, dt, ch, gamma, glm_alpha, recon, upwind=upwind, shock=shock,
-                          riemann=riemann, kappa=kappa, nu=nu, eta=eta, kappa_par=kappa_par, phi=phi)
+                          riemann=riemann, kappa=kappa, nu=nu, eta=eta, kappa_par=kappa_par, phi=phi,
+                          corner=corner)
         if bad:
             raise FloatingPointError(f"oracle met {bad} unphysical states at step {k}")
         t += dt

@@ -1186,7 +1186,7 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                      double gam, double glm_alpha, int recon, int upwind,
                      const long *win, const double *wgt, int nwin, double *reg,
                      int solver, int shock, double eps_q, int qkind, double kappa, double kpar, double phi,
-                     double nu, double eta)
+                     double nu, double eta, int corner)
 {
     const int par = kappa > 0.0 || kpar > 0.0 || nu > 0.0 || eta > 0.0;
     unsigned char *flags = NULL;
@@ -1232,8 +1232,14 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
         parabolic_lp(&G, Wn, h, kappa, kpar, phi, nu, eta, ring_lo, ring_hi, LPn);
     }
 
-    /* 2. first-order Godunov fluxes F^n_d = R(U_c, U_(c+e_d)) on the faces the
-     *    transverse increments need; F1[d] at cell c is its upper face. */
+    /* 2. the transverse fluxes on the faces the transverse increments need;
+     *    F1[d] at cell c is its upper face.  corner = 0: first-order Godunov
+     *    fluxes F^n_d = R(U_c, U_(c+e_d)) between cell-centred states (Eq.
+     *    transv).  corner = 1 (Pi = 0 only), the corner coupling of Mignone &
+     *    Tzeferacos (2010) that Section 3.1 refers to: the Riemann problem
+     *    between the normal predictor states of direction d, F*_d =
+     *    R(U*_(c,+), U*_(c+e_d,-)), U* from the characteristic predictor of
+     *    step 3 (time-centred along d, without transverse terms). */
     for (d = 0; d < ndim; d++) {
         long st = dstride(&G, d);
         int lo[3], hi[3], e;
@@ -1256,9 +1262,24 @@ static int step_core(const double *U, double *Unew, int nx, int ny, int nz, int 
                 for (c[0] = lo[0]; c[0] <= hi[0]; c[0]++) {
                     long id = cidx(&G, c);
                     double VL[NVAR], VR[NVAR], Fl[NVAR];
-                    for (q = 0; q < NVAR; q++) {
-                        VL[q] = V[PERM[d][q] * nc + id];
-                        VR[q] = V[PERM[d][q] * nc + id + st];
+                    if (corner) {
+                        double vs[5 * NVAR], Vx[NVAR];
+                        int l;
+                        for (l = 0; l < 5; l++)
+                            for (q = 0; q < NVAR; q++)
+                                vs[l * NVAR + q] = V[PERM[d][q] * nc + id + (l - 2) * st];
+                        or_mhd_char_predict_dx(vs, gam, ch, dt / h[d], h[d],
+                                               (flags && (flags[id] & 2)) ? 2 : recon, upwind, VL, Vx);
+                        for (l = 0; l < 5; l++)
+                            for (q = 0; q < NVAR; q++)
+                                vs[l * NVAR + q] = V[PERM[d][q] * nc + id + (l - 1) * st];
+                        or_mhd_char_predict_dx(vs, gam, ch, dt / h[d], h[d],
+                                               (flags && (flags[id + st] & 2)) ? 2 : recon, upwind, Vx, VR);
+                    } else {
+                        for (q = 0; q < NVAR; q++) {
+                            VL[q] = V[PERM[d][q] * nc + id];
+                            VR[q] = V[PERM[d][q] * nc + id + st];
+                        }
                     }
                     face_riemann(VL, VR, gam, ch, solver, flags && ((flags[id] | flags[id + st]) & 1), Fl);
                     for (q = 0; q < NVAR; q++)
@@ -1458,7 +1479,22 @@ int or_mhd_step_ex(const double *U, double *Unew, int nx, int ny, int nz, int nd
                    int solver, int shock, double eps_q, int qkind)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, 0.0, 0.0, 0.0, 0.0, 0.0);
+                     nwin, reg, solver, shock, eps_q, qkind, 0.0, 0.0, 0.0, 0.0, 0.0, 0);
+}
+
+/* or_mhd_step_ex with the corner coupling of Mignone & Tzeferacos (2010):
+ * the transverse fluxes of Eq. (transv) from the normal predictor states
+ * (step 2 of step_core with corner = 1) instead of the cell-centred states;
+ * the case Pi = 0 of Section 3.1 ("constructed exactly as illustrated by
+ * MT").  Six Riemann problems per zone as well, C_a <= 1/2 in 3-D. */
+int or_mhd_step_mt(const double *U, double *Unew, int nx, int ny, int nz, int ndim,
+                   double dx, double dy, double dz, double dt, double ch,
+                   double gam, double glm_alpha, int recon, int upwind,
+                   const long *win, const double *wgt, int nwin, double *reg,
+                   int solver, int shock, double eps_q, int qkind)
+{
+    return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
+                     nwin, reg, solver, shock, eps_q, qkind, 0.0, 0.0, 0.0, 0.0, 0.0, 1);
 }
 
 /* or_mhd_step_ex with thermal conduction of conductivities kappa >= 0 across
@@ -1475,7 +1511,7 @@ int or_mhd_step_par(const double *U, double *Unew, int nx, int ny, int nz, int n
                     double nu, double eta)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, kappa, kpar, phi, nu, eta);
+                     nwin, reg, solver, shock, eps_q, qkind, kappa, kpar, phi, nu, eta, 0);
 }
 
 /* or_mhd_step_par with conduction alone. */
@@ -1486,7 +1522,7 @@ int or_mhd_step_tc(const double *U, double *Unew, int nx, int ny, int nz, int nd
                    int solver, int shock, double eps_q, int qkind, double kappa)
 {
     return step_core(U, Unew, nx, ny, nz, ndim, dx, dy, dz, dt, ch, gam, glm_alpha, recon, upwind, win, wgt,
-                     nwin, reg, solver, shock, eps_q, qkind, kappa, kappa, 0.0, 0.0, 0.0);
+                     nwin, reg, solver, shock, eps_q, qkind, kappa, kappa, 0.0, 0.0, 0.0, 0);
 }
 
 /* ------------------------------------------------------------------ */
