@@ -220,7 +220,7 @@ def run_ours(args):
                                     shock=(args.shock, 0) if args.shock else None,
                                     riemann=ctu.CTU_HLLC if args.riemann == "hllc" else ctu.CTU_HLLD,
                                     kappa=args.kappa, nu=args.nu, eta=args.eta, kappa_par=args.kappa_par,
-                                    tc_phi=args.tc_phi))
+                                    tc_phi=args.tc_phi, corner=1 if args.corner == "mt" else 0))
         c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
         if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
@@ -301,7 +301,8 @@ def run_ours(args):
     kern = res["kern"]
     top_name, (top_ms, top_cnt) = max(kern.items(), key=lambda kv: kv[1][0])
     top_avg = top_ms / max(1, top_cnt)
-    fl = kernel_flops(n, args.recon, args.kappa, args.kappa_par, args.tc_phi, args.nu, args.eta)
+    fl = kernel_flops(n, args.recon, args.kappa, args.kappa_par, args.tc_phi, args.nu, args.eta,
+                      corner=args.corner)
     mixed = primary == ctu.CTU_MIXED
     peak_tf = (FP32_PEAK if mixed else FP64_PEAK) / 1e12
     f_top = fl.get(top_name, 0.0)
@@ -328,7 +329,7 @@ def run_ours(args):
     roof["hbm_step"] = {"algorithmic_bytes": nbytes, "achieved_gbs": hbm_achieved,
                         "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
                         "peak_source": f"{src} hbm_gbs"}
-    plain = not (args.shock or args.kappa or args.nu or args.eta or args.kappa_par)
+    plain = not (args.shock or args.kappa or args.nu or args.eta or args.kappa_par or args.corner == "mt")
     if mixed and args.recon == "ppm" and args.riemann == "hlld" and plain:
         ps = precision_split_roofline(n, value / world, peaks["hbm_gbs"])
         # the kernels run the float64-designated recoveries in double-float on
@@ -390,7 +391,9 @@ def run_ours(args):
                            + (f" (along the field {args.kappa_par})" if args.kappa_par else "")
                            + (f", saturated (phi {args.tc_phi})" if args.tc_phi else "")
                            + (f"; viscosity, nu {args.nu}" if args.nu else "")
-                           + (f"; resistivity, eta {args.eta}" if args.eta else ""),
+                           + (f"; resistivity, eta {args.eta}" if args.eta else "")
+                           + ("; corner coupling from the normal predictor states (Mignone & Tzeferacos)"
+                              if args.corner == "mt" else ""),
                            "recon": args.recon, "shock_eps": args.shock or None,
                            "cells_per_gpu": cells, "patches_per_gpu": 1,
                            "precision": args.precision, "l2_flush": "inputs (1.3 GB) > L2",
@@ -1042,7 +1045,7 @@ def _profile_numbers(name):
 
 
 def kernel_flops(n, recon="ppm", kappa=0.0, kappa_par=0.0, tc_phi=0.0, nu=0.0, eta=0.0, cells=None,
-                 physics="mhd"):
+                 physics="mhd", corner="cell"):
     """Algorithmic flops per launch of each kernel group of one 3-D step on an
     n^3 patch (or on `cells` interior cells, a batch): the oracle's operation
     counts per interior cell (profiles/flops_per_cell.txt, exact-zero
@@ -1059,6 +1062,13 @@ def kernel_flops(n, recon="ppm", kappa=0.0, kappa_par=0.0, tc_phi=0.0, nu=0.0, e
                 "sweep_x": (sw + c.get("update", 0.0) + c.get("sr_next_dt", 0.0)) * cells}
     sweep = c.get("sweep_per_direction_" + ("linear" if recon == "mc" else recon), 0.0)
     kp = kappa_par if kappa_par > 0 else kappa
+    if corner == "mt":
+        # the transverse fluxes from the normal predictor states: a predictor
+        # and a Riemann problem per cell and direction in place of flux1
+        pred = c.get("predict_" + ("linear" if recon == "mc" else recon), 0.0) + c.get("riemann", 0.0) + 18
+        return {"prim": c.get("prim", 0.0) * cells, "pred1": 3 * pred * cells,
+                "sweep_z": sweep * cells, "sweep_y": sweep * cells,
+                "sweep_x": (sweep + c.get("update", 0.0) + c.get("next_dt", 0.0)) * cells}
     if not (kappa or kappa_par or nu or eta):
         # sweeps run z, y, x; the x sweep finishes the update and the next dt
         return {"prim": c.get("prim", 0.0) * cells, "flux1": 3 * c.get("flux1_per_direction", 0.0) * cells,
@@ -1165,6 +1175,8 @@ def main():
                     help="blast: the hybrid integration with this shock threshold (thermal pressure; 0 = off)")
     ap.add_argument("--recon", default="ppm", choices=sorted(RECONS),
                     help="blast: reconstruction of the characteristic variables (the workload uses ppm)")
+    ap.add_argument("--corner", default="cell", choices=["cell", "mt"],
+                    help="transverse fluxes from cell-centred states (Eq. transv) or the normal predictor states")
     ap.add_argument("--config", default="blast", choices=["blast", "amr", "srmhd", "tag"],
                     help="blast: the 256^3 headline workload; amr: batched AMR level advance; "
                          "srmhd: relativistic jet; tag: refinement tagging of the 256^3 state")

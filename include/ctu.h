@@ -213,7 +213,21 @@ typedef struct {
      * the upwind cell (the left one when F_d < 0) and rho_f the mean density.
      * 0 = classical.  The CFL rate keeps the classical coefficients. */
     double tc_phi;
+    /* Corner coupling of the transverse terms, Section 3.1:
+     *   CTU_CORNER_CELL  the first-order Godunov fluxes between cell-centred
+     *                    states of Eq. (transv), the form the paper gives
+     *                    for Pi != 0 (default);
+     *   CTU_CORNER_MT    the case Pi = 0 "as illustrated by MT" (Mignone &
+     *                    Tzeferacos 2010): the transverse fluxes from Riemann
+     *                    problems between the normal predictor states of the
+     *                    other directions, F*_d = R(U*_(c,+), U*_(c+e_d,-)).
+     *                    Six Riemann problems per zone as well; ideal MHD,
+     *                    PPM or MC-linear, HLLD, trace modes ALL or UPWIND,
+     *                    no hybrid integration and no parabolic terms,
+     *                    CTU_FP64 or CTU_MIXED; else CTU_EUNSUPPORTED. */
+    int corner;
 } ctu_config;
+enum { CTU_CORNER_CELL = 0, CTU_CORNER_MT = 1 };
 
 typedef struct {
     int32_t n[3];     /* interior cells per dimension (1 for inactive ones) */

@@ -12,7 +12,8 @@ OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "libctu.so"
 SOURCES = ["ctu_api.cu", "ctu_f64.cu", "ctu_f32.cu", "ctu_f32i.cu", "ctu_sr32.cu", "ctu_noalloc.cu",
            "ctu_var32.cu", "ctu_var64.cu", "ctu_ref32.cu", "ctu_ref64.cu", "ctu_hyb32.cu",
-           "ctu_hyb64.cu", "ctu_hllc32.cu", "ctu_hllc64.cu", "ctu_par32.cu", "ctu_par64.cu"]
+           "ctu_hyb64.cu", "ctu_hllc32.cu", "ctu_hllc64.cu", "ctu_par32.cu", "ctu_par64.cu", "ctu_mt32.cu",
+           "ctu_mt64.cu"]
 # The FMA-throughput microbenchmark (include/ctu_peaks.h) is a measurement aid
 # for the roofline, built as a library of its own beside libctu.so.
 PEAK_SOURCES = ["peaks/fma_peak.cu"]
@@ -23,7 +24,7 @@ LIB_PEAKS = OUT_DIR / "libctu_peaks.so"
 FLOAT_FAST = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
 SOURCE_FLAGS = {"ctu_f32.cu": FLOAT_FAST, "ctu_f32i.cu": FLOAT_FAST, "ctu_sr32.cu": FLOAT_FAST,
                 "ctu_var32.cu": FLOAT_FAST, "ctu_ref32.cu": FLOAT_FAST, "ctu_hyb32.cu": FLOAT_FAST,
-                "ctu_hllc32.cu": FLOAT_FAST, "ctu_par32.cu": FLOAT_FAST}
+                "ctu_hllc32.cu": FLOAT_FAST, "ctu_par32.cu": FLOAT_FAST, "ctu_mt32.cu": FLOAT_FAST}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -439,6 +439,7 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
                    ? (par ? RECON_MC_PAR
                           : (hllc ? RECON_MC_HLLC : (hyb ? RECON_MC_HYB : (ref ? RECON_MC_REF : RECON_MC))))
              : r == CTU_WENO3 ? RECON_WENO3 : RECON_LIN;
+    if (ctx->cfg.corner == CTU_CORNER_MT) li.recon = r == CTU_PPM ? RECON_PPM_MT : RECON_MC_MT;
     li.iface64 = ctx->cfg.precision == CTU_MIXED_IFACE64;
     li.physics = ctx->cfg.physics == CTU_SRMHD ? PH_SR : PH_MHD;
     li.scratch = ctx->scratch;
@@ -451,6 +452,7 @@ namespace ctu {
 template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<double>(a, li, s);
+    if (recon_mt(li.recon)) return launch_step_mt<double, 1>(a, li, s);
     if (recon_par(li.recon)) return launch_step_var<double, 1, 4>(a, li, s);
     if (recon_hllc(li.recon)) return launch_step_var<double, 1, 3>(a, li, s);
     if (recon_hybrid(li.recon)) return launch_step_var<double, 1, 2>(a, li, s);
@@ -460,6 +462,7 @@ template <> int launch_step<double>(const StepArgs &a, const LaunchInfo &li, cud
 template <> int launch_step<float>(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
 {
     if (li.physics == PH_SR) return launch_step_sr<float>(a, li, s);
+    if (recon_mt(li.recon)) return launch_step_mt<float, 0>(a, li, s);
     if (recon_par(li.recon)) return launch_step_var<float, 0, 4>(a, li, s);
     if (recon_hllc(li.recon)) return launch_step_var<float, 0, 3>(a, li, s);
     if (recon_hybrid(li.recon)) return launch_step_var<float, 0, 2>(a, li, s);
@@ -538,6 +541,15 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
         (cfg->physics != CTU_MHD || (cfg->recon != CTU_PPM && cfg->recon != CTU_LINEAR_MC) ||
          cfg->riemann != CTU_HLLD || cfg->trace_mode > CTU_TRACE_UPWIND || cfg->shock_detect ||
          cfg->precision == CTU_MIXED_IFACE64))
+        return CTU_EUNSUPPORTED;
+    if (cfg->corner != CTU_CORNER_CELL && cfg->corner != CTU_CORNER_MT) return CTU_EINVAL;
+    // the corner coupling of Mignone & Tzeferacos: Pi = 0, ideal MHD, PPM or
+    // MC-linear, HLLD, trace modes ALL / UPWIND, FP64 or CTU_MIXED
+    if (cfg->corner == CTU_CORNER_MT &&
+        (cfg->physics != CTU_MHD || (cfg->recon != CTU_PPM && cfg->recon != CTU_LINEAR_MC) ||
+         cfg->riemann != CTU_HLLD || cfg->trace_mode > CTU_TRACE_UPWIND || cfg->shock_detect ||
+         cfg->precision == CTU_MIXED_IFACE64 || cfg->kappa > 0.0 || cfg->kappa_par > 0.0 || cfg->nu > 0.0 ||
+         cfg->eta > 0.0))
         return CTU_EUNSUPPORTED;
     ctu_ctx *ctx = new (std::nothrow) ctu_ctx();
     if (!ctx) return CTU_ENOMEM;

@@ -710,6 +710,14 @@ struct Tiles {
         const long long nseg = (n[D] + x2 + seg - 1) / seg;
         return (long long)((n[0] + 2 + w - 1) / w) * ((eO * nseg + r - 1) / r);
     }
+    // the corner coupling's transverse fluxes along x (k_pred<0>): traced
+    // cells [-1, n_x], rows and planes over the ring [-1, n]
+    static long long pred_x(const int *n, int ndim, int w)
+    {
+        const int r = BLOCK / w;
+        const int e1 = ndim > 1 ? n[1] + 2 : 1, e2 = ndim > 2 ? n[2] + 2 : 1;
+        return (long long)((n[0] + w - 3) / (w - 2)) * ((e1 + r - 1) / r) * e2;
+    }
     static long long sweep_x(const int *n, int w)
     {
         const int r = BLOCK / w;
@@ -986,6 +994,122 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const
                 Vl[q] = Vr[q];
                 Vr[q] = Vn[q];
             }
+        }
+    }
+}
+
+// The corner coupling of Mignone & Tzeferacos (2010) (the kinds
+// RECON_PPM_MT, RECON_MC_MT; Section 3.1 with Pi = 0): in place of k_div1,
+// the transverse fluxes come from Riemann problems between the normal
+// predictor states, F*_D = R(V*_(c,+), V*_(c+e_D,-)) (characteristic
+// predictor of Section 3.2, no transverse terms), and L1_D = (F*_(c - e_D/2)
+// - F*_(c + e_D/2)) / dx_D on the cells the sweeps of the other directions
+// trace: c_D in [0, n_D), the other active coordinates in [-1, n].
+//   D = x: one thread per traced cell c_x in [-1, n_x]; a tile of xw lanes
+//          yields xw - 2 cells, the right neighbour's - state and the left
+//          neighbour's face flux arriving by warp shuffles (a row of the
+//          tile lies within one warp).
+//   D = y, z: one thread per segment marching along D, the 5-cell stencil,
+//          the previous cell's + state and the previous face flux in
+//          registers (the k_div1 tiling).
+template <int PHYS, class R, int PPM, int D>
+__global__ void __launch_bounds__(BLOCK) k_pred(StepArgs a, GroupTable gt, const R *Vs, R *L1)
+{
+    const Where wh = locate(gt);
+    const DevPatch P = a.patches[wh.patch];
+    const Tile t(wh.xw);
+    const R gam = pgam<R>(a), ch = pch<R>(a.sp);
+    const R dtr = pdt<R>(a.sp);
+    const R iD = pidx<R>(P, D);
+    const R dtdx = dtr * iD;
+    R *Ld = L1 + (long long)D * NV * a.sstride;
+    const int b = wh.b;
+    if constexpr (D == 0) {
+        const int out = t.xw - 2;
+        const int e1 = a.ndim > 1 ? P.n[1] + 2 : 1, e2 = a.ndim > 2 ? P.n[2] + 2 : 1;
+        const int lo1 = a.ndim > 1 ? -1 : 0, lo2 = a.ndim > 2 ? -1 : 0;
+        const int T0 = (P.n[0] + out - 1) / out, T1 = (e1 + t.rows - 1) / t.rows;
+        const int tx = t.tx();
+        const int i = (b % T0) * out - 1 + tx;  // traced cell, >= -1
+        const int j = ((b / T0) % T1) * t.rows + t.ty();
+        const int k = b / (T0 * T1);
+        const bool traced = j < e1 && k < e2 && i <= P.n[0];
+        const long long c = traced ? P.soff + lcell(P, i, lo1 + j, lo2 + k) : 0;
+        R pl[NV], ml[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { pl[q] = R(0); ml[q] = R(0); }
+        if (traced) {
+            R vs[5][NV];
+#pragma unroll
+            for (int m = 0; m < 5; ++m)
+#pragma unroll
+                for (int q = 0; q < NV; ++q) vs[m][q] = Vs[q * a.sstride + c + (m - 2)];
+            char_predict<R, PPM>(vs, gam, ch, dtdx, a.upwind, a.limiter, R(0), pl, ml);
+        }
+        // face between cells i and i + 1 (every lane takes part in the shuffles)
+        R Rr[NV], F[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            Rr[q] = __shfl_down_sync(0xffffffffu, ml[q], 1, t.xw);
+            F[q] = R(0);
+        }
+        if (traced && tx < t.xw - 1 && i <= P.n[0] - 1) riemann_any<PHYS, R>(pl, Rr, gam, ch, F);
+        R Fm[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) Fm[q] = __shfl_up_sync(0xffffffffu, F[q], 1, t.xw);
+        if (traced && tx >= 1 && tx <= t.xw - 2 && i >= 0 && i < P.n[0]) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Ld[q * a.sstride + c] = (Fm[q] - F[q]) * iD;
+        }
+    } else {
+        constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
+        const int SEGL = wh.seg;
+        const int nD = P.n[D];
+        const int eO = a.ndim > O ? P.n[O] + 2 : 1, loO = a.ndim > O ? -1 : 0;
+        const int nseg = (nD + SEGL - 1) / SEGL;
+        const int T0 = (P.n[0] + 2 + t.xw - 1) / t.xw;
+        const int x = (b % T0) * t.xw + t.tx() - 1;
+        const int comb = (b / T0) * t.rows + t.ty();
+        const int o = comb / nseg, seg = comb % nseg;
+        if (x > P.n[0] || o >= eO) return;
+        const int j0 = seg * SEGL, j1 = min(j0 + SEGL, nD);
+        const int st = dstr(P, D);
+        int cc[3];
+        cc[0] = x;
+        cc[O] = loO + o;
+        cc[D] = j0 - 1;
+        long long c = P.soff + lcell(P, cc[0], cc[1], cc[2]);  // traced cell j0 - 1
+        R win[5][NV];
+#pragma unroll
+        for (int m = 0; m < 5; ++m)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) win[m][q] = Vs[gperm<D>(q) * a.sstride + c + (m - 2) * st];
+        R Pprev[NV], Fprev[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { Pprev[q] = R(0); Fprev[q] = R(0); }
+        for (int j = j0 - 1; j <= j1; ++j, c += st) {
+            if (j > j0 - 1) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) win[m][q] = win[m + 1][q];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) win[4][q] = Vs[gperm<D>(q) * a.sstride + c + 2 * st];
+            }
+            R pl[NV], ml[NV];
+            char_predict<R, PPM>(win, gam, ch, dtdx, a.upwind, a.limiter, R(0), pl, ml);
+            if (j >= j0) {  // face between cells j - 1 and j
+                R F[NV];
+                riemann_any<PHYS, R>(Pprev, ml, gam, ch, F);
+                if (j > j0) {  // cell j - 1
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) Ld[gperm<D>(q) * a.sstride + c - st] = (Fprev[q] - F[q]) * iD;
+                }
+#pragma unroll
+                for (int q = 0; q < NV; ++q) Fprev[q] = F[q];
+            }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Pprev[q] = pl[q];
         }
     }
 }

@@ -130,7 +130,26 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     // half-step state needs sum_d L_(H,d)^n there, also in 1-D)
     constexpr bool EXT = recon_par(PPM);
     constexpr bool HY = recon_hybrid(PPM), HC = recon_hllc(PPM);
-    if (a.ndim > 1 || EXT) {
+    if constexpr (recon_mt(PPM)) {
+        // the corner coupling of Mignone & Tzeferacos: the transverse fluxes
+        // from the normal predictor states
+        if (a.ndim > 1) {
+            CTU_MARK("pred1");
+            n += over_groups(
+                li, [&](const Group &G) { return Tiles::pred_x(G.n, a.ndim, G.xw); },
+                [&](const GroupTable &gt, unsigned nb) { k_pred<PHYS, R, PPM, 0><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+            n += over_groups(
+                li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 1, G.xw, G.seg); },
+                [&](const GroupTable &gt, unsigned nb) { k_pred<PHYS, R, PPM, 1><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+            if (a.ndim > 2)
+                n += over_groups(
+                    li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 2, G.xw, G.seg); },
+                    [&](const GroupTable &gt, unsigned nb) {
+                        k_pred<PHYS, R, PPM, 2><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1);
+                    });
+            CTU_MARK(nullptr);
+        }
+    } else if (a.ndim > 1 || EXT) {
         CTU_MARK("flux1");
         n += over_groups(
             li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 0, G.xw, G.seg, EXT); },
@@ -239,6 +258,14 @@ template <class R, int IF64, int G> int launch_step_var(const StepArgs &a, const
     else
         return li.recon == RECON_PPM_REF ? launch_step_t<PH_MHD, R, RECON_PPM_REF, IF64>(a, li, s)
                                          : launch_step_t<PH_MHD, R, RECON_MC_REF, IF64>(a, li, s);
+}
+
+// MHD with the corner coupling of Mignone & Tzeferacos (G = 5: PPM or
+// MC-linear).
+template <class R, int IF64> int launch_step_mt(const StepArgs &a, const LaunchInfo &li, cudaStream_t s)
+{
+    return li.recon == RECON_PPM_MT ? launch_step_t<PH_MHD, R, RECON_PPM_MT, IF64>(a, li, s)
+                                    : launch_step_t<PH_MHD, R, RECON_MC_MT, IF64>(a, li, s);
 }
 
 // SRMHD: MUSCL-Hancock with MC-linear primitive slopes.

@@ -49,5 +49,6 @@ template <class R> int launch_maxspeed(const StepArgs &a, const LaunchInfo &li, 
 template <class R, int IF64> int launch_step_impl(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
 template <class R> int launch_step_sr(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
 template <class R, int IF64, int G> int launch_step_var(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
+template <class R, int IF64> int launch_step_mt(const StepArgs &a, const LaunchInfo &li, cudaStream_t s);
 
 } // namespace ctu

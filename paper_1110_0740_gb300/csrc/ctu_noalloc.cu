@@ -83,7 +83,8 @@ extern "C" ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in
         cfg->riemann != CTU_HLLD || cfg->p_floor != 0.0 || cfg->rho_floor != 0.0 ||
         (cfg->recon > CTU_PPM && cfg->recon <= CTU_WENO3) ||
         (cfg->trace_mode > CTU_TRACE_UPWIND && cfg->trace_mode <= CTU_TRACE_CW84) || cfg->shock_detect != 0 ||
-        cfg->kappa != 0.0 || cfg->kappa_par != 0.0 || cfg->nu != 0.0 || cfg->eta != 0.0 || cfg->tc_phi != 0.0)
+        cfg->kappa != 0.0 || cfg->kappa_par != 0.0 || cfg->nu != 0.0 || cfg->eta != 0.0 || cfg->tc_phi != 0.0 ||
+        cfg->corner != CTU_CORNER_CELL)
         return CTU_EUNSUPPORTED;
     if (!(cfg->gamma > 1.0) || cfg->ndim < 1 || cfg->ndim > 3 || cfg->nghost != 4 ||
         (cfg->recon != CTU_LINEAR_MC && cfg->recon != CTU_PPM) ||

@@ -98,18 +98,25 @@ template <class R> __device__ __forceinline__ R lin_slope(R dm, R dp, int lim)
 // RECON_PPM_PAR and RECON_MC_PAR add the parabolic terms, thermal
 // conduction and viscosity (tracing modes ALL and UPWIND, as RECON_PPM and
 // RECON_MC).
+// RECON_PPM_MT and RECON_MC_MT take the transverse fluxes of the corner
+// coupling from the normal predictor states (Mignone & Tzeferacos 2010).
 enum {
     RECON_MC = 0, RECON_PPM = 1, RECON_LIN = 2, RECON_WENO3 = 3, RECON_PPM_REF = 4, RECON_MC_REF = 5,
     RECON_PPM_HYB = 6, RECON_MC_HYB = 7, RECON_PPM_HLLC = 8, RECON_MC_HLLC = 9, RECON_PPM_PAR = 10,
-    RECON_MC_PAR = 11
+    RECON_MC_PAR = 11, RECON_PPM_MT = 12, RECON_MC_MT = 13
 };
 
 __host__ __device__ constexpr int recon_base(int r)
 {
-    return (r == RECON_PPM_REF || r == RECON_PPM_HYB || r == RECON_PPM_HLLC || r == RECON_PPM_PAR)
+    return (r == RECON_PPM_REF || r == RECON_PPM_HYB || r == RECON_PPM_HLLC || r == RECON_PPM_PAR ||
+            r == RECON_PPM_MT)
                ? RECON_PPM
-               : ((r == RECON_MC_REF || r == RECON_MC_HYB || r == RECON_MC_HLLC || r == RECON_MC_PAR) ? RECON_MC : r);
+               : ((r == RECON_MC_REF || r == RECON_MC_HYB || r == RECON_MC_HLLC || r == RECON_MC_PAR ||
+                   r == RECON_MC_MT)
+                      ? RECON_MC
+                      : r);
 }
+__host__ __device__ constexpr bool recon_mt(int r) { return r == RECON_PPM_MT || r == RECON_MC_MT; }
 
 __host__ __device__ constexpr bool recon_hybrid(int r) { return r == RECON_PPM_HYB || r == RECON_MC_HYB; }
 __host__ __device__ constexpr bool recon_hllc(int r) { return r == RECON_PPM_HLLC || r == RECON_MC_HLLC; }

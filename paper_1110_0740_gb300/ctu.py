@@ -22,6 +22,7 @@ CTU_CHAR_TRACE, CTU_MUSCL_HANCOCK = 0, 1
 CTU_HLLD, CTU_HLL, CTU_HLLC = 0, 1, 2
 CTU_FP64, CTU_MIXED, CTU_MIXED_IFACE64 = 0, 1, 2
 CTU_TRACE_ALL, CTU_TRACE_UPWIND, CTU_TRACE_CENTER, CTU_TRACE_CW84 = 0, 1, 2, 3
+CTU_CORNER_CELL, CTU_CORNER_MT = 0, 1
 CTU_TAG_DENSITY, CTU_TAG_ENERGY, CTU_TAG_B2_OVER_RHO, CTU_TAG_E_OVER_RHO = 0, 1, 2, 3
 
 STATUS = ["CTU_OK", "CTU_EINVAL", "CTU_ENOMEM", "CTU_ECUDA", "CTU_EUNSUPPORTED", "CTU_ENEGATIVE",
@@ -37,7 +38,7 @@ class ctu_config(ctypes.Structure):
                 ("rho_floor", ctypes.c_double), ("shock_detect", ctypes.c_int), ("shock_q", ctypes.c_int),
                 ("shock_eps", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("nu", ctypes.c_double), ("eta", ctypes.c_double), ("kappa_par", ctypes.c_double),
-                ("tc_phi", ctypes.c_double)]
+                ("tc_phi", ctypes.c_double), ("corner", ctypes.c_int)]
 
 
 class ctu_patch(ctypes.Structure):
@@ -201,19 +202,21 @@ def _check(code, where):
 def make_config(ndim=3, gamma=5.0 / 3.0, recon=CTU_PPM, precision=CTU_FP64, cfl=0.3,
                 glm_alpha=0.1, trace_mode=CTU_TRACE_ALL, physics=CTU_MHD, riemann=CTU_HLLD,
                 predictor=CTU_CHAR_TRACE, eos=CTU_EOS_IDEAL, p_floor=0.0, rho_floor=0.0, shock=None,
-                kappa=0.0, nu=0.0, eta=0.0, kappa_par=0.0, tc_phi=0.0):
+                kappa=0.0, nu=0.0, eta=0.0, kappa_par=0.0, tc_phi=0.0, corner=CTU_CORNER_CELL):
     """shock: None (off) or (eps_q, q) for the hybrid integration, q = 0
     thermal or 1 magnetic pressure.  kappa: isotropic thermal conductivity,
     nu: kinematic viscosity, eta: resistivity (0 = off); kappa_par: the
     conductivity along the field, kappa then across it (0 = isotropic);
-    tc_phi: saturation parameter of the heat flux (0 = classical)."""
+    tc_phi: saturation parameter of the heat flux (0 = classical); corner:
+    CTU_CORNER_CELL or CTU_CORNER_MT (transverse fluxes from the normal
+    predictor states)."""
     return ctu_config(physics=physics, eos=eos, gamma=gamma, ndim=ndim, recon=recon,
                       predictor=predictor, riemann=riemann, precision=precision, cfl=cfl,
                       glm_alpha=glm_alpha, nghost=4, trace_mode=trace_mode, p_floor=p_floor,
                       rho_floor=rho_floor, shock_detect=0 if shock is None else 1,
                       shock_q=0 if shock is None else int(shock[1]),
                       shock_eps=0.0 if shock is None else float(shock[0]), kappa=float(kappa), nu=float(nu), eta=float(eta),
-                      kappa_par=float(kappa_par), tc_phi=float(tc_phi))
+                      kappa_par=float(kappa_par), tc_phi=float(tc_phi), corner=int(corner))
 
 
 def make_patches(specs):

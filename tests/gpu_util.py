@@ -43,7 +43,8 @@ def maxrel(got, ref, ch=None):
 
 
 def gpu_run(U0, n, ndim, dx, steps, cfl, precision=0, recon=1, trace_mode=0, glm_alpha=0.1,
-            gamma=5.0 / 3.0, physics=0, eos=0, riemann=0, kappa=0.0, nu=0.0, eta=0.0, kappa_par=0.0, phi=0.0):
+            gamma=5.0 / 3.0, physics=0, eos=0, riemann=0, kappa=0.0, nu=0.0, eta=0.0, kappa_par=0.0, phi=0.0,
+            corner=0):
     """Advance one periodic patch `steps` steps on the GPU; returns
     (U ghosted numpy, list of (dt, ch), status)."""
     import torch
@@ -59,7 +60,7 @@ def gpu_run(U0, n, ndim, dx, steps, cfl, precision=0, recon=1, trace_mode=0, glm
     else:
         cfg = ctu.make_config(ndim=ndim, gamma=gamma, recon=recon, precision=precision, cfl=cfl,
                               glm_alpha=glm_alpha, trace_mode=trace_mode, riemann=riemann, kappa=kappa, nu=nu, eta=eta,
-                              kappa_par=kappa_par, tc_phi=phi)
+                              kappa_par=kappa_par, tc_phi=phi, corner=corner)
     ctx = ctu.Ctx(cfg)
     dx3 = list(dx) + [1.0] * (3 - len(dx))
     patches = ctu.make_patches([(n, dx3, 0)])
@@ -79,8 +80,8 @@ def gpu_run(U0, n, ndim, dx, steps, cfl, precision=0, recon=1, trace_mode=0, glm
 
 
 def oracle_run(U0, n, ndim, dx, steps, cfl, recon=1, trace_mode=0, glm_alpha=0.1,
-               gamma=5.0 / 3.0, riemann=0, kappa=0.0, nu=0.0, eta=0.0, kappa_par=0.0, phi=0.0):
+               gamma=5.0 / 3.0, riemann=0, kappa=0.0, nu=0.0, eta=0.0, kappa_par=0.0, phi=0.0, corner=0):
     U, t, dts = O.mhd_run(U0, n, ndim, list(dx) + [1.0] * (3 - len(dx)), steps, cfl, gamma=gamma,
                           glm_alpha=glm_alpha, recon=recon, upwind=trace_mode, riemann=riemann, kappa=kappa, nu=nu, eta=eta,
-                          kappa_par=kappa_par or None, phi=phi)
+                          kappa_par=kappa_par or None, phi=phi, corner=corner)
     return U, dts
