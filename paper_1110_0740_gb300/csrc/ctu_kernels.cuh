@@ -210,6 +210,16 @@ __host__ __device__ __forceinline__ int tile_xw(int nx)
     return nx >= 24 ? 32 : (nx >= 12 ? 16 : 8);
 }
 
+// Row width of the x sweep's tile: a patch row of up to 32 cells takes one
+// row of n_x + 2 lanes (its traced cells, the rows packed BLOCK / (n_x + 2)
+// to a block), so that small patches leave few lanes idle; wider rows take
+// the group's width w (8, 16 or 32).  The exchange between the lanes of a row
+// goes through shared memory, so a row need not be a power of two wide.
+__host__ __device__ __forceinline__ int sweepx_xw(int nx, int w)
+{
+    return nx <= 32 ? nx + 2 : w;
+}
+
 // Bring the cache line holding *p into L1 ahead of its use (no register is
 // held while the load is in flight).
 __device__ __forceinline__ void prefetch_l1(const void *p)
@@ -720,6 +730,7 @@ struct Tiles {
     }
     static long long sweep_x(const int *n, int w)
     {
+        w = sweepx_xw(n[0], w);
         const int r = BLOCK / w;
         return (long long)((n[0] + w - 3) / (w - 2)) * ((n[1] + r - 1) / r) * n[2];
     }
@@ -1124,7 +1135,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
     const Where wh = locate(gt);
     const int patch = wh.patch;
     const DevPatch P = a.patches[patch];
-    const Tile t(wh.xw);
+    const Tile t(sweepx_xw(P.n[0], wh.xw));
     const int out_x = t.xw - 2;
     const int T0 = (P.n[0] + out_x - 1) / out_x, T1 = (P.n[1] + t.rows - 1) / t.rows;
     const int b = wh.b;
@@ -1132,7 +1143,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
     const int i = (b % T0) * out_x - 1 + tx;  // traced cell, >= -1
     const int j = ((b / T0) % T1) * t.rows + ty;
     const int k = b / (T0 * T1);
-    const bool traced = j < P.n[1] && k < P.n[2] && i <= P.n[0];
+    // threads beyond the block's last full row (BLOCK not a multiple of the
+    // row width) trace nothing
+    const bool traced = ty < t.rows && j < P.n[1] && k < P.n[2] && i <= P.n[0];
     __shared__ R sP[BLOCK][NV], sM[BLOCK][NV], sF[BLOCK][NV];
     // faces of the block with flux-register windows: lane, first and end window
     __shared__ int s_nreg, s_reg[BLOCK][3];
