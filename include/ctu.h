@@ -418,14 +418,22 @@ typedef struct {
     int origin[3];    /* coarse cell holding the fine patch's cell 0: fine cell x lies in
                          coarse cell origin + floor(x / ratio) on every active dimension */
     int ratio;        /* refinement ratio, 1 to 4 */
+    int phys;         /* ctu_prolong: bit 2d (2d + 1) set when the coarse patch's first
+                         (last) interior cell along d touches the physical domain boundary;
+                         such a cell's slope along d is the one-sided difference to its
+                         neighbour inside the domain (0 when it touches both), and no value
+                         beyond the boundary is read.  0 for periodic or interior patches;
+                         bits above 5 are invalid.  Ignored by ctu_restrict. */
 } ctu_level_box;
 
 /* Eq. (prolong) + Eq. (intalpha): every fine cell x of each box takes
  * U* = (1 - alpha) Uc_old + alpha Uc_new of its coarse cell c, plus, along
  * every active dimension d, (((x_d mod r) + 1/2) / r - 1/2) times the
- * monotonised-central (Eq. MClim) central difference of U* at c.  The coarse
- * cell and its neighbours along each active dimension must lie in the
- * coarse patch's ghosted region.  Uc_old and Uc_new may be the same array. */
+ * monotonised-central (Eq. MClim) central difference of U* at c, or, for a
+ * cell touching the domain boundary (the box's phys bits), the one-sided
+ * difference (Section 4).  The coarse cell and its neighbours along each
+ * active dimension must lie in the coarse patch's ghosted region.  Uc_old
+ * and Uc_new may be the same array. */
 ctu_status ctu_prolong(ctu_ctx *ctx, const double *Uc_old, const double *Uc_new, int64_t cstride,
                        double alpha, double *Uf, int64_t fstride, const ctu_level_box *boxes,
                        int nbox, void *stream);

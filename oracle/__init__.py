@@ -124,7 +124,7 @@ def lib():
             L.or_srmhd_mh_predict.argtypes = [P, P, D, D, D, P, P]
         I3 = ctypes.POINTER(ctypes.c_int)
         L.or_prolong.restype = None
-        L.or_prolong.argtypes = [P, P, I3, D, P, I3, I3, I3, I3, I, I]
+        L.or_prolong.argtypes = [P, P, I3, D, P, I3, I3, I3, I3, I, I, I]
         L.or_restrict.restype = None
         L.or_restrict.argtypes = [P, I3, P, I3, I3, I3, I3, I, I]
         L.or_diagnostics.restype = None
@@ -150,16 +150,18 @@ def _i3(v):
 
 # ---------------------------------------------------------------- level operators
 
-def prolong(Uc_old, Uc_new, nc, alpha, Uf, nf, lo, hi, origin, ratio, ndim):
+def prolong(Uc_old, Uc_new, nc, alpha, Uf, nf, lo, hi, origin, ratio, ndim, phys=0):
     """Eq. (prolong) + (intalpha): fill the fine cells [lo, hi) of Uf (in place)
     from the coarse patch at U* = (1 - alpha) Uc_old + alpha Uc_new; fine cell
-    x lies in coarse cell origin + floor(x / ratio)."""
+    x lies in coarse cell origin + floor(x / ratio).  phys: bit 2d (2d + 1)
+    when the coarse patch's first (last) cell along d touches the domain
+    boundary, where the slope is one-sided."""
     Uco = np.ascontiguousarray(Uc_old, dtype=np.float64)
     Ucn = np.ascontiguousarray(Uc_new, dtype=np.float64)
     assert Uco.shape == shape(nc, ndim) and Ucn.shape == Uco.shape and Uf.shape == shape(nf, ndim)
     assert Uf.flags.c_contiguous and Uf.dtype == np.float64
     lib().or_prolong(_dp(Uco), _dp(Ucn), _i3(nc), float(alpha), _dp(Uf), _i3(nf), _i3(lo), _i3(hi),
-                     _i3(origin), int(ratio), int(ndim))
+                     _i3(origin), int(ratio), int(ndim), int(phys))
     return Uf
 
 

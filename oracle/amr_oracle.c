@@ -51,9 +51,16 @@ static int fdiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
  * plus, along each active dimension, (xi_fine - xi_coarse) / (xi_+ - xi_-)
  * times the MC-limited central difference of U* there, with
  * U* = (1 - alpha) Uold + alpha Unew.  For a Cartesian cell of width h the
- * weight is ((x mod r) + 1/2) / r - 1/2. */
+ * weight is ((x mod r) + 1/2) / r - 1/2.
+ * Cells touching the domain boundary take one-sided differences (Section
+ * 4): bit 2d of phys says that the coarse patch's cell 0 along d lies on the
+ * domain's lower boundary, bit 2d + 1 that its cell nc[d] - 1 lies on the
+ * upper one; such a cell's difference along d is the one to its neighbour
+ * inside the domain (the MC limiter of one difference is that difference),
+ * and 0 if it touches both boundaries.  No value beyond the boundary is
+ * read. */
 void or_prolong(const double *Uco, const double *Ucn, const int nc[3], double alpha, double *Uf, const int nf[3],
-                const int lo[3], const int hi[3], const int origin[3], int r, int ndim)
+                const int lo[3], const int hi[3], const int origin[3], int r, int ndim, int phys)
 {
     const long Sc = cells(nc, ndim), Sf = cells(nf, ndim);
     for (int z = lo[2]; z < hi[2]; ++z)
@@ -78,14 +85,28 @@ void or_prolong(const double *Uco, const double *Ucn, const int nc[3], double al
                     const double u0 = (1.0 - alpha) * Uco[q * Sc + c0] + alpha * Ucn[q * Sc + c0];
                     double u = u0;
                     for (int d = 0; d < ndim; ++d) {
+                        const int at_lo = (phys >> (2 * d)) & 1 && c[d] == 0;
+                        const int at_hi = (phys >> (2 * d + 1)) & 1 && c[d] == nc[d] - 1;
                         int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
+                        double slope;
                         cm[d] -= 1;
                         cp[d] += 1;
-                        const long im = cell(nc, ndim, cm[0], cm[1], cm[2]);
-                        const long ip = cell(nc, ndim, cp[0], cp[1], cp[2]);
-                        const double um = (1.0 - alpha) * Uco[q * Sc + im] + alpha * Ucn[q * Sc + im];
-                        const double up = (1.0 - alpha) * Uco[q * Sc + ip] + alpha * Ucn[q * Sc + ip];
-                        u += w[d] * mc(u0 - um, up - u0);
+                        if (at_lo && at_hi) {
+                            slope = 0.0;
+                        } else if (at_lo) {
+                            const long ip = cell(nc, ndim, cp[0], cp[1], cp[2]);
+                            slope = (1.0 - alpha) * Uco[q * Sc + ip] + alpha * Ucn[q * Sc + ip] - u0;
+                        } else if (at_hi) {
+                            const long im = cell(nc, ndim, cm[0], cm[1], cm[2]);
+                            slope = u0 - ((1.0 - alpha) * Uco[q * Sc + im] + alpha * Ucn[q * Sc + im]);
+                        } else {
+                            const long im = cell(nc, ndim, cm[0], cm[1], cm[2]);
+                            const long ip = cell(nc, ndim, cp[0], cp[1], cp[2]);
+                            const double um = (1.0 - alpha) * Uco[q * Sc + im] + alpha * Ucn[q * Sc + im];
+                            const double up = (1.0 - alpha) * Uco[q * Sc + ip] + alpha * Ucn[q * Sc + ip];
+                            slope = mc(u0 - um, up - u0);
+                        }
+                        u += w[d] * slope;
                     }
                     Uf[q * Sf + fi] = u;
                 }

@@ -128,9 +128,22 @@ __global__ void __launch_bounds__(AMR_BLOCK) k_prolong(const ctu_level_box *boxe
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             if (d >= ndim) continue;
-            const double um = ustar(c0 - st[d]);
-            const double up = ustar(c0 + st[d]);
-            s[d] = mc64(u0 - um, up - u0);
+            // a coarse cell touching the domain boundary: the one-sided
+            // difference to its neighbour inside the domain (Section 4)
+            const int cd = B.origin[d] + cr[d];
+            const bool at_lo = ((B.phys >> (2 * d)) & 1) && cd == 0;
+            const bool at_hi = ((B.phys >> (2 * d + 1)) & 1) && cd == B.cn[d] - 1;
+            if (at_lo && at_hi) {
+                s[d] = 0.0;
+            } else if (at_lo) {
+                s[d] = ustar(c0 + st[d]) - u0;
+            } else if (at_hi) {
+                s[d] = u0 - ustar(c0 - st[d]);
+            } else {
+                const double um = ustar(c0 - st[d]);
+                const double up = ustar(c0 + st[d]);
+                s[d] = mc64(u0 - um, up - u0);
+            }
         }
         double *Pf = Uf + q * fs + f00;
         for (int z = 0; z < nz; ++z) {

@@ -888,6 +888,7 @@ static bool box_ok(const ctu_ctx *ctx, const ctu_level_box &B, int64_t cstride, 
 {
     long long cc = 0, fc = 0;
     if (!patch_extent(ctx, B.cn, &cc) || !patch_extent(ctx, B.fn, &fc) || B.ratio < 1 || B.ratio > 4) return false;
+    if (B.phys < 0 || B.phys > 63) return false;
     if (B.cbase < 0 || B.cbase + cc > cstride || B.fbase < 0 || B.fbase + fc > fstride) return false;
     const int *out_n = prolong ? B.fn : B.cn;
     long long cnt = 1;

@@ -74,7 +74,7 @@ def make_copy_boxes(boxes):
 class ctu_level_box(ctypes.Structure):
     _fields_ = [("fn", ctypes.c_int32 * 3), ("cn", ctypes.c_int32 * 3), ("fbase", ctypes.c_int64),
                 ("cbase", ctypes.c_int64), ("lo", ctypes.c_int32 * 3), ("hi", ctypes.c_int32 * 3),
-                ("origin", ctypes.c_int32 * 3), ("ratio", ctypes.c_int32)]
+                ("origin", ctypes.c_int32 * 3), ("ratio", ctypes.c_int32), ("phys", ctypes.c_int32)]
 
 
 class ctu_reflux_set(ctypes.Structure):
@@ -87,12 +87,14 @@ class ctu_reflux_set(ctypes.Structure):
 
 
 def make_level_boxes(boxes):
-    """boxes: iterables of dicts with keys fn, cn, fbase, cbase, lo, hi, origin, ratio."""
+    """boxes: iterables of dicts with keys fn, cn, fbase, cbase, lo, hi, origin, ratio
+    and optionally phys (the physical-boundary bits of ctu_prolong, default 0)."""
     arr = (ctu_level_box * len(boxes))()
     for i, b in enumerate(boxes):
         for k in ("fn", "cn", "lo", "hi", "origin"):
             getattr(arr[i], k)[:] = [int(v) for v in b[k]]
         arr[i].fbase, arr[i].cbase, arr[i].ratio = int(b["fbase"]), int(b["cbase"]), int(b["ratio"])
+        arr[i].phys = int(b.get("phys", 0))
     return arr
 
 

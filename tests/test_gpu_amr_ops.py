@@ -76,6 +76,53 @@ def test_prolong_and_restrict_match_the_oracle(ndim, r):
     assert ctx.status_sync() == 0
 
 
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_prolong_one_sided_at_the_domain_boundary(ndim):
+    """A coarse patch whose cells touch the domain boundary on both sides of
+    every active axis (phys bits), NaN beyond the boundary: the one-sided
+    slopes read no ghost and the fine cells equal the oracle's bit for bit
+    (up to 1e-14); a box with mixed bits (lower x and upper y only) as well;
+    bits above 5 are refused."""
+    import torch
+    from paper_1110_0740_gb300 import ctu
+    rng = np.random.default_rng(40 + ndim)
+    nc = [6 if d < ndim else 1 for d in range(3)]
+    nf = [12 if d < ndim else 1 for d in range(3)]
+    U = rng.standard_normal(O.shape(nc, ndim)) + 3.0
+    g = O.ghosts(ndim)
+    inside = np.zeros(U.shape[1:], dtype=bool)
+    inside[tuple(slice(g[d], g[d] + nc[d]) for d in (2, 1, 0))] = True
+    U[:, ~inside] = np.nan
+    F = np.zeros(O.shape(nf, ndim))
+    (CP, cb), (FP, fb) = _pool([U]), _pool([F])
+    dev = _dev()
+    tC, tF = torch.from_numpy(CP).to(dev), torch.from_numpy(FP).to(dev)
+    ctx = ctu.Ctx(ctu.make_config(ndim=ndim, recon=ctu.CTU_PPM, precision=ctu.CTU_FP64))
+    # every side flagged, NaN beyond the boundary; then only the lower x and
+    # upper y sides flagged, with finite ghosts (the other sides keep the MC
+    # central slope, which needs its ghost)
+    Ufin = U.copy()
+    Ufin[:, ~inside] = rng.standard_normal(int((~inside).sum()))[None, :] + 3.0
+    CPf, _ = _pool([Ufin])
+    for phys, Uc, cpool in ((sum(3 << (2 * d) for d in range(ndim)), U, tC),
+                            (0b1001, Ufin, torch.from_numpy(CPf).to(dev))):
+        box = _box(nf, nc, fb[0], cb[0], [0, 0, 0], nf, [0, 0, 0], 2)
+        box["phys"] = phys
+        tF.zero_()
+        ctx.prolong(cpool, cpool, CP.shape[1], 0.0, tF, FP.shape[1], ctu.make_level_boxes([box]))
+        got = tF.cpu().numpy()[:, fb[0]:fb[0] + F[0].size].reshape(F.shape)
+        ref = F.copy()
+        O.prolong(Uc, Uc, nc, 0.0, ref, nf, [0, 0, 0], nf, [0, 0, 0], 2, ndim, phys=phys)
+        I, R = O.interior(got, nf, ndim), O.interior(ref, nf, ndim)
+        assert np.all(np.isfinite(I)) and np.all(np.isfinite(R))
+        assert np.allclose(I, R, rtol=1e-14, atol=1e-14), np.abs(I - R).max()
+    bad = _box(nf, nc, fb[0], cb[0], [0, 0, 0], nf, [0, 0, 0], 2)
+    bad["phys"] = 64
+    with pytest.raises(ctu.CtuError):
+        ctx.prolong(tC, tC, CP.shape[1], 0.0, tF, FP.shape[1], ctu.make_level_boxes([bad]))
+    assert ctx.status_sync() == 0
+
+
 def test_level_operators_reject_boxes_outside_the_patches():
     import torch
     from paper_1110_0740_gb300 import ctu

@@ -100,6 +100,96 @@ def test_prolongation_adds_no_extrema_along_a_direction(d):
         assert np.all(kids >= nb.min(axis=1)[:, None] - 1e-14)
 
 
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_prolongation_one_sided_at_the_domain_boundary(ndim):
+    """Cells touching the domain boundary take one-sided differences (Section
+    4).  A coarse patch whose first and last cells along every active axis
+    touch the boundary (phys bits set), its ghosts beyond it NaN (no value
+    there may be read): children of a boundary cell take U* + w (u_inside -
+    u_0) (lower boundary) or U* + w (u_0 - u_inside) (upper), in closed form
+    on data quadratic in the cell index (whose central and one-sided
+    differences differ); interior cells keep the MC central slope; linear data
+    are still reproduced exactly, and the children still average to their
+    coarse cell."""
+    r = 2
+    nc = [5 if d < ndim else 1 for d in range(3)]
+    nf = [2 * nc[d] if d < ndim else 1 for d in range(3)]
+    phys = sum(3 << (2 * d) for d in range(ndim))
+    g = O.ghosts(ndim)
+    z, y, x = np.meshgrid(*[np.arange(-g[d], nc[d] + g[d]) for d in (2, 1, 0)], indexing="ij")
+    xs = [x, y, z]
+    U = np.zeros(O.shape(nc, ndim))
+    for q in range(9):
+        U[q] = 1.0 + 0.1 * q + sum((0.3 + 0.1 * d) * xs[d] ** 2 for d in range(ndim))
+    inside = np.ones(U.shape[1:], dtype=bool)
+    for d in range(ndim):
+        inside &= (xs[d] >= 0) & (xs[d] < nc[d])
+    U[:, ~inside] = np.nan
+    Uf = np.zeros(O.shape(nf, ndim))
+    O.prolong(U, U, nc, 0.25, Uf, nf, [0, 0, 0], nf, [0, 0, 0], r, ndim, phys=phys)
+    If = O.interior(Uf, nf, ndim)
+    assert np.all(np.isfinite(If))
+    for kz, ky, kx in itertools.product(*[range(nf[d]) for d in (2, 1, 0)]):
+        f = [kx, ky, kz]
+        c = [f[d] // r for d in range(3)]
+        for q in range(9):
+            u0 = 1.0 + 0.1 * q + sum((0.3 + 0.1 * d) * c[d] ** 2 for d in range(ndim))
+            val = u0
+            for d in range(ndim):
+                a = 0.3 + 0.1 * d
+                w = ((f[d] % r) + 0.5) / r - 0.5
+                if c[d] == 0:
+                    s = a * 1.0                                   # u(1) - u(0)
+                elif c[d] == nc[d] - 1:
+                    s = a * (c[d] ** 2 - (c[d] - 1) ** 2)         # u(n-1) - u(n-2)
+                else:
+                    dm, dp = a * (2 * c[d] - 1), a * (2 * c[d] + 1)
+                    s = min(0.5 * (dm + dp), 2 * dm, 2 * dp)     # MC of two positive differences
+                val += w * s
+            assert If[q, kz, ky, kx] == pytest.approx(val, rel=0, abs=1e-13)
+    # without the boundary bits the boundary cells take the limited central
+    # difference with the (NaN) ghost, which the MC limiter turns into no slope
+    Ug = np.zeros_like(Uf)
+    O.prolong(U, U, nc, 0.25, Ug, nf, [0, 0, 0], nf, [0, 0, 0], r, ndim, phys=0)
+    assert not np.array_equal(O.interior(Ug, nf, ndim), If)
+
+
+def test_prolongation_one_sided_keeps_linear_data_and_averages():
+    rng = np.random.default_rng(21)
+    ndim, r = 3, 2
+    nc, nf = [4, 4, 4], [8, 8, 8]
+    a, b = rng.standard_normal(9), rng.standard_normal((9, 3))
+    Uc = _fill_linear(nc, ndim, a, b)
+    Uf = np.zeros(O.shape(nf, ndim))
+    O.prolong(Uc, Uc, nc, 0.0, Uf, nf, [0, 0, 0], nf, [0, 0, 0], r, ndim, phys=0b010110)
+    z, y, x = np.meshgrid(*[np.arange(8) for _ in range(3)], indexing="ij")
+    If = O.interior(Uf, nf, ndim)
+    for q in range(9):
+        ref = a[q] + sum(b[q, d] * ((xs + 0.5) / r - 0.5) for d, xs in enumerate((x, y, z)))
+        assert np.allclose(If[q], ref, rtol=0, atol=1e-12)
+    Uo = rng.standard_normal(O.shape(nc, ndim))
+    O.prolong(Uo, Uo, nc, 0.0, Uf, nf, [0, 0, 0], nf, [0, 0, 0], r, ndim, phys=0b111111)
+    If = O.interior(Uf, nf, ndim)
+    Ic = O.interior(Uo, nc, ndim)
+    avg = If.reshape(9, 4, 2, 4, 2, 4, 2).mean(axis=(2, 4, 6))
+    assert np.allclose(avg, Ic, rtol=0, atol=1e-14)
+
+
+def test_prolongation_one_cell_domain_has_no_slope():
+    """A domain one coarse cell wide along x (both bits): the children equal
+    their coarse cell's value along x."""
+    nc, nf, ndim = [1, 3, 1], [2, 6, 1], 2
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal(O.shape(nc, ndim))
+    U[:, :, :, :4] = np.nan
+    U[:, :, :, 5:] = np.nan
+    Uf = np.zeros(O.shape(nf, ndim))
+    O.prolong(U, U, nc, 0.0, Uf, nf, [0, 0, 0], nf, [0, 0, 0], 2, ndim, phys=0b11)
+    If = O.interior(Uf, nf, ndim)
+    assert np.all(np.isfinite(If))
+    assert np.array_equal(If[:, :, :, 0], If[:, :, :, 1])
+
+
 def test_prolongation_time_interpolation_is_linear_in_alpha():
     rng = np.random.default_rng(3)
     nc, nf, ndim = [6, 6, 6], [4, 4, 4], 3
