@@ -223,7 +223,7 @@ def run_ours(args):
                                     tc_phi=args.tc_phi, corner=1 if args.corner == "mt" else 0))
         c.flux_registers(reg, windows)
         c.dt(U, stride, patches, dtch)
-        if prec == ctu.CTU_MIXED:  # tile width and segment for the patch shape
+        if prec != ctu.CTU_FP64:  # tile width and segment for the patch shape
             c.autotune(U, Uo, stride, patches, dtch)
             tiles["xw_seg"] = list(c.tile_params([n] * 3))
         return c
@@ -264,8 +264,8 @@ def run_ours(args):
             ms = float(t.item())
         return ms, kern
 
-    primary = ctu.CTU_MIXED if args.precision == "mixed" else ctu.CTU_FP64
-    other = ctu.CTU_FP64 if primary == ctu.CTU_MIXED else ctu.CTU_MIXED
+    primary = {"mixed": ctu.CTU_MIXED, "fp64": ctu.CTU_FP64, "iface64": ctu.CTU_MIXED_IFACE64}[args.precision]
+    other = ctu.CTU_FP64 if primary != ctu.CTU_FP64 else ctu.CTU_MIXED
     cells = n ** 3
     results = {}
     clocks = Clocks(local)
@@ -303,7 +303,7 @@ def run_ours(args):
     top_avg = top_ms / max(1, top_cnt)
     fl = kernel_flops(n, args.recon, args.kappa, args.kappa_par, args.tc_phi, args.nu, args.eta,
                       corner=args.corner)
-    mixed = primary == ctu.CTU_MIXED
+    mixed = primary != ctu.CTU_FP64
     peak_tf = (FP32_PEAK if mixed else FP64_PEAK) / 1e12
     f_top = fl.get(top_name, 0.0)
     achieved = f_top / (top_avg * 1e-3) / 1e12
@@ -382,7 +382,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
                 "steps": res["K"], "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+f64" if primary == ctu.CTU_MIXED else "f64", "data": "synthetic",
+                "dtype": "f32+f64" if primary != ctu.CTU_FP64 else "f64", "data": "synthetic",
                 "config": {"workload": (WORKLOAD if args.recon == "ppm" else
                                         WORKLOAD.replace("PPM", f"{args.recon} reconstruction"))
                            + (f"; hybrid integration (shock flags, eps_q {args.shock})" if args.shock else "")
@@ -1150,7 +1150,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "iface64"])
     ap.add_argument("--n", type=int, default=N_CELLS)
     ap.add_argument("--other-steps", type=int, default=3)
     ap.add_argument("--skip-other", action="store_true")
