@@ -220,6 +220,15 @@ __host__ __device__ __forceinline__ int sweepx_xw(int nx, int w)
     return nx <= 32 ? nx + 2 : w;
 }
 
+// Row width of the marching first-order kernels (k_div1 and k_pred along y
+// and z), whose lanes cover x in [-1, n_x]: the same packing, n_x + 2 lanes
+// per row for rows of up to 32 cells (the lanes of a row do not exchange
+// values, so any width serves).
+__host__ __device__ __forceinline__ int ringx_xw(int nx, int w)
+{
+    return nx <= 32 ? nx + 2 : w;
+}
+
 // Bring the cache line holding *p into L1 ahead of its use (no register is
 // held while the load is in flight).
 __device__ __forceinline__ void prefetch_l1(const void *p)
@@ -706,6 +715,12 @@ struct Tiles {
     {
         return ((long long)N[0] * N[1] * N[2] + BLOCK - 1) / BLOCK;
     }
+    // k_prim<..., TRIM>: the ghosted box without its outermost layer on active
+    // axes (N > 1 there)
+    static long long prim_trim(const int *N)
+    {
+        return ((long long)(N[0] - 2) * (N[1] > 1 ? N[1] - 2 : 1) * (N[2] > 1 ? N[2] - 2 : 1) + BLOCK - 1) / BLOCK;
+    }
     // ext: along D also the ring's layers -1 and n_D (k_div1's EXT)
     static long long div1(const int *n, int ndim, int D, int w, int seg, bool ext = false)
     {
@@ -718,7 +733,8 @@ struct Tiles {
         const int O = D == 1 ? 2 : 1;
         const int eO = ndim > O ? n[O] + 2 : 1;
         const long long nseg = (n[D] + x2 + seg - 1) / seg;
-        return (long long)((n[0] + 2 + w - 1) / w) * ((eO * nseg + r - 1) / r);
+        const int wr = ringx_xw(n[0], w), rr = BLOCK / wr;
+        return (long long)((n[0] + 2 + wr - 1) / wr) * ((eO * nseg + rr - 1) / rr);
     }
     // the corner coupling's transverse fluxes along x (k_pred<0>): traced
     // cells [-1, n_x], rows and planes over the ring [-1, n]
@@ -762,13 +778,25 @@ static __global__ void k_setup(const double *dtch, StepParams *sp)
 // V = V(U) on every ghosted cell (a flat range of the patch region);
 // one block per BLOCK cells of a patch.  LIT64: float64 pressure recovery in
 // the float kernels (CTU_MIXED_IFACE64).
-template <int PHYS, class R, int LIT64 = 0>
+// TRIM: only the cells within three ghost layers of the interior (the
+// stencils of the first-order stage, the predictors and the parabolic face
+// pass reach no further); the hybrid integration's shock flags, which read
+// the fourth layer, take the whole ghosted box.
+template <int PHYS, class R, int LIT64 = 0, bool TRIM = false>
 __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, GroupTable gt, R *Vs)
 {
     const Where w = locate(gt);
     const DevPatch P = a.patches[w.patch];
-    const int c = w.b * BLOCK + threadIdx.x;
-    if (c >= P.N[0] * P.N[1] * P.N[2]) return;
+    int c = w.b * BLOCK + threadIdx.x;
+    if constexpr (TRIM) {
+        // box of the ghosted patch without its outermost layer on active axes
+        const int m0 = P.N[0] - 2, m1 = P.g[1] ? P.N[1] - 2 : 1, m2 = P.g[2] ? P.N[2] - 2 : 1;
+        if (c >= m0 * m1 * m2) return;
+        const int x = c % m0 + 1, y = (c / m0) % m1 + (P.g[1] ? 1 : 0), z = c / (m0 * m1) + (P.g[2] ? 1 : 0);
+        c = (z * P.N[1] + y) * P.N[0] + x;
+    } else {
+        if (c >= P.N[0] * P.N[1] * P.N[2]) return;
+    }
     double U[NV];
     R V[NV];
 #pragma unroll
@@ -912,7 +940,7 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const
 {
     const Where wh = locate(gt);
     const DevPatch P = a.patches[wh.patch];
-    const Tile t(wh.xw);
+    const Tile t(D == 0 ? wh.xw : ringx_xw(P.n[0], wh.xw));
     const int SEGL = wh.seg;
     const R gam = pgam<R>(a), ch = pch<R>(a.sp);
     const R iD = pidx<R>(P, D);
@@ -966,7 +994,8 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const
         const int x = (b % T0) * t.xw + t.tx() - 1;
         const int comb = (b / T0) * t.rows + t.ty();
         const int o = comb / nseg, seg = comb % nseg;
-        if (x > P.n[0] || o >= eO) return;
+        // (threads beyond the block's last full row take no work)
+        if (t.ty() >= t.rows || x > P.n[0] || o >= eO) return;
         const int j0 = seg * SEGL - X, j1 = min(j0 + SEGL, nD + X);
         const int st = dstr(P, D);
         int cc[3];
@@ -1028,7 +1057,7 @@ __global__ void __launch_bounds__(BLOCK) k_pred(StepArgs a, GroupTable gt, const
 {
     const Where wh = locate(gt);
     const DevPatch P = a.patches[wh.patch];
-    const Tile t(wh.xw);
+    const Tile t(D == 0 ? wh.xw : ringx_xw(P.n[0], wh.xw));
     const R gam = pgam<R>(a), ch = pch<R>(a.sp);
     const R dtr = pdt<R>(a.sp);
     const R iD = pidx<R>(P, D);
@@ -1082,7 +1111,7 @@ __global__ void __launch_bounds__(BLOCK) k_pred(StepArgs a, GroupTable gt, const
         const int x = (b % T0) * t.xw + t.tx() - 1;
         const int comb = (b / T0) * t.rows + t.ty();
         const int o = comb / nseg, seg = comb % nseg;
-        if (x > P.n[0] || o >= eO) return;
+        if (t.ty() >= t.rows || x > P.n[0] || o >= eO) return;
         const int j0 = seg * SEGL, j1 = min(j0 + SEGL, nD);
         const int st = dstr(P, D);
         int cc[3];

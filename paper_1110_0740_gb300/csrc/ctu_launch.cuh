@@ -109,9 +109,16 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     CTU_MARK(nullptr);
     ++n;
     CTU_MARK("prim");
-    n += over_groups(
-        li, [&](const Group &G) { return Tiles::prim(G.N); },
-        [&](const GroupTable &gt, unsigned nb) { k_prim<PHYS, R, IF64><<<nb, BLOCK, 0, s>>>(a, gt, Vs); });
+    if constexpr (recon_hybrid(PPM))  // the shock flags read the outermost ghost layer
+        n += over_groups(
+            li, [&](const Group &G) { return Tiles::prim(G.N); },
+            [&](const GroupTable &gt, unsigned nb) { k_prim<PHYS, R, IF64><<<nb, BLOCK, 0, s>>>(a, gt, Vs); });
+    else
+        n += over_groups(
+            li, [&](const Group &G) { return Tiles::prim_trim(G.N); },
+            [&](const GroupTable &gt, unsigned nb) {
+                k_prim<PHYS, R, IF64, true><<<nb, BLOCK, 0, s>>>(a, gt, Vs);
+            });
     CTU_MARK(nullptr);
     if constexpr (recon_hybrid(PPM)) {  // shock flags of the hybrid integration
         CTU_MARK("shock");
