@@ -1082,13 +1082,16 @@ def kernel_flops(n, recon="ppm", kappa=0.0, kappa_par=0.0, tc_phi=0.0, nu=0.0, e
     face = c.get(f"par_mask_{cond}_{1 if nu else 0}_{1 if eta else 0}", 0.0)
     m = 1 + (3 if nu else 0) + (3 if eta else 0)
     swp = sweep + m * c.get("sweep_par_per_component", 0.0)
-    half = (c.get("par_half_per_cell", 0.0) + 3 * face + m * c.get("par_half_per_component", 0.0)
+    # the face passes evaluate every face once (three per cell); the half-step
+    # and update kernels difference them
+    half = (c.get("par_half_per_cell", 0.0) + m * c.get("par_half_per_component", 0.0)
             + (c.get("par_half_visc", 0.0) if nu else 0.0))
-    upd = (3 * face + m * c.get("par_update_per_component", 0.0) + c.get("next_dt", 0.0)
+    upd = (m * c.get("par_update_per_component", 0.0) + c.get("next_dt", 0.0)
            + c.get("par_update_diffusion_number", 0.0))
     return {"prim": c.get("prim", 0.0) * cells, "flux1": 3 * c.get("flux1_per_direction", 0.0) * cells,
-            "par_half": half * cells, "sweep_z": swp * cells, "sweep_y": swp * cells,
-            "sweep_x": (swp + c.get("update", 0.0)) * cells, "par_update": upd * cells}
+            "par_faces_n": 3 * face * cells, "par_half": half * cells, "sweep_z": swp * cells,
+            "sweep_y": swp * cells, "sweep_x": (swp + c.get("update", 0.0)) * cells,
+            "par_faces_h": 3 * face * cells, "par_update": upd * cells}
 
 
 def precision_split_roofline(n, cells_per_s, hbm_gbs):

@@ -229,6 +229,11 @@ __host__ __device__ __forceinline__ int ringx_xw(int nx, int w)
     return nx <= 32 ? nx + 2 : w;
 }
 
+// k_prim's trimmed box (see k_prim) serves patches whose ghosted rows are at
+// most PRIM_TRIM_MAXN cells long.
+constexpr int PRIM_TRIM_MAXN = 72;
+__host__ __device__ __forceinline__ bool prim_trimmed(const int *N) { return N[0] <= PRIM_TRIM_MAXN; }
+
 // Bring the cache line holding *p into L1 ahead of its use (no register is
 // held while the load is in flight).
 __device__ __forceinline__ void prefetch_l1(const void *p)
@@ -715,10 +720,11 @@ struct Tiles {
     {
         return ((long long)N[0] * N[1] * N[2] + BLOCK - 1) / BLOCK;
     }
-    // k_prim<..., TRIM>: the ghosted box without its outermost layer on active
-    // axes (N > 1 there)
+    // k_prim<..., TRIM>: on small patches (prim_trimmed) the ghosted box
+    // without its outermost layer on active axes (N > 1 there)
     static long long prim_trim(const int *N)
     {
+        if (!prim_trimmed(N)) return prim(N);
         return ((long long)(N[0] - 2) * (N[1] > 1 ? N[1] - 2 : 1) * (N[2] > 1 ? N[2] - 2 : 1) + BLOCK - 1) / BLOCK;
     }
     // ext: along D also the ring's layers -1 and n_D (k_div1's EXT)
@@ -778,17 +784,21 @@ static __global__ void k_setup(const double *dtch, StepParams *sp)
 // V = V(U) on every ghosted cell (a flat range of the patch region);
 // one block per BLOCK cells of a patch.  LIT64: float64 pressure recovery in
 // the float kernels (CTU_MIXED_IFACE64).
-// TRIM: only the cells within three ghost layers of the interior (the
-// stencils of the first-order stage, the predictors and the parabolic face
-// pass reach no further); the hybrid integration's shock flags, which read
-// the fourth layer, take the whole ghosted box.
+// TRIM: on patches whose ghosted rows are at most PRIM_TRIM_MAXN cells long,
+// only the cells within three ghost layers of the interior (the stencils of
+// the first-order stage, the predictors and the parabolic face pass reach no
+// further); the layer saved is a large part of a small patch, while on a
+// large one the index arithmetic of the trimmed box would cost more than it
+// saves.  The hybrid integration's shock flags, which read the fourth
+// layer, take the whole ghosted box.
+
 template <int PHYS, class R, int LIT64 = 0, bool TRIM = false>
 __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, GroupTable gt, R *Vs)
 {
     const Where w = locate(gt);
     const DevPatch P = a.patches[w.patch];
     int c = w.b * BLOCK + threadIdx.x;
-    if constexpr (TRIM) {
+    if (TRIM && prim_trimmed(P.N)) {
         // box of the ghosted patch without its outermost layer on active axes
         const int m0 = P.N[0] - 2, m1 = P.g[1] ? P.N[1] - 2 : 1, m2 = P.g[2] ? P.N[2] - 2 : 1;
         if (c >= m0 * m1 * m2) return;

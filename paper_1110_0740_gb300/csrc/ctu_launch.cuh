@@ -172,7 +172,7 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         CTU_MARK(nullptr);
     }
     if constexpr (recon_par(PPM)) {  // parabolic terms: L_P^n and the half-step fields
-        CTU_MARK("par_half");
+        CTU_MARK("par_faces_n");
         auto half = [&](auto tm) {
             constexpr int V = decltype(tm)::value;
             n += over_groups(
@@ -180,6 +180,8 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
                 [&](const GroupTable &gt, unsigned nb) {
                     k_par_faces<R, V, 1><<<nb, BLOCK, 0, s>>>(a, gt, Vs, a.th, (R *)a.pif);
                 });
+            CTU_MARK(nullptr);
+            CTU_MARK("par_half");
             n += over_groups(
                 li, [&](const Group &G) { return ((long long)par_ring_cells(G.n, a.ndim) + BLOCK - 1) / BLOCK; },
                 [&](const GroupTable &gt, unsigned nb) {
@@ -216,7 +218,7 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         });
     CTU_MARK(nullptr);
     if constexpr (recon_par(PPM)) {  // parabolic terms: + dt L_P^(n+1/2)
-        CTU_MARK("par_update");
+        CTU_MARK("par_faces_h");
         with_tm(par_mask(a), [&](auto tm) {
             constexpr int V = decltype(tm)::value;
             n += over_groups(
@@ -224,6 +226,8 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
                 [&](const GroupTable &gt, unsigned nb) {
                     k_par_faces<R, V, 0><<<nb, BLOCK, 0, s>>>(a, gt, Vs, a.th, (R *)a.pif);
                 });
+            CTU_MARK(nullptr);
+            CTU_MARK("par_update");
             n += over_groups(
                 li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
                 [&](const GroupTable &gt, unsigned nb) {
