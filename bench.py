@@ -361,7 +361,8 @@ def run_ours(args):
     e2e = None
     if not args.skip_e2e:
         c = make(primary)
-        e2e = e2e_stream(c, Uh, U, Uo, n, stride, patches, dtch, dtn, max(4, args.steps), dev, world, barrier)
+        e2e = e2e_stream(c, Uh, U, Uo, n, stride, patches, dtch, dtn, max(4, args.steps), dev, world, barrier,
+                         lanes=args.copy_lanes)
         c.close()
 
     fp64_path = None
@@ -407,7 +408,7 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
-def e2e_stream(c, Uh, U, Uo, n, stride, patches, dtch, dtn, E, dev, world, barrier):
+def e2e_stream(c, Uh, U, Uo, n, stride, patches, dtch, dtn, E, dev, world, barrier, lanes=1):
     """End to end through the public API with host buffers, one periodic n^3
     patch: every step copies its input state (the interior, 9 float64 fields
     of n^3 cells, packed) from pinned host memory and reads its result (the
@@ -429,39 +430,52 @@ def e2e_stream(c, Uh, U, Uo, n, stride, patches, dtch, dtn, E, dev, world, barri
     Ibuf = [torch.empty(Ih_pin.shape, dtype=torch.float64, device=dev) for _ in range(2)]
     Pbuf = [torch.empty(Ih_pin.shape, dtype=torch.float64, device=dev) for _ in range(2)]
     Oh = [torch.empty_like(Ih_pin).pin_memory() for _ in range(2)]
-    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    ev_in = [torch.cuda.Event() for _ in range(2)]
+    s_cmp = torch.cuda.Stream()
+    # each direction's copy is split by variable over `lanes` streams, so that
+    # several copy engines share it
+    s_in = [torch.cuda.Stream() for _ in range(lanes)]
+    s_out = [torch.cuda.Stream() for _ in range(lanes)]
+    parts = [list(range(9))[i::lanes] for i in range(lanes)]
+    ev_in = [[torch.cuda.Event() for _ in range(lanes)] for _ in range(2)]
     ev_cmp = [torch.cuda.Event() for _ in range(2)]
-    ev_out = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [[torch.cuda.Event() for _ in range(lanes)] for _ in range(2)]
 
     def pipeline(K):
         for k in range(K):
             b = k % 2
-            if k >= 2:
-                s_in.wait_event(ev_cmp[b])  # step k - 2 has read input buffer b
-            with torch.cuda.stream(s_in):
-                Ibuf[b].copy_(Ih_pin, non_blocking=True)
-                ev_in[b].record(s_in)
-            s_cmp.wait_event(ev_in[b])
-            if k >= 2:
-                s_cmp.wait_event(ev_out[b])  # result buffer b has been read back
+            for i, qs in enumerate(parts):
+                if k >= 2:
+                    s_in[i].wait_event(ev_cmp[b])  # step k - 2 has read input buffer b
+                with torch.cuda.stream(s_in[i]):
+                    for q in qs:
+                        Ibuf[b][q].copy_(Ih_pin[q], non_blocking=True)
+                    ev_in[b][i].record(s_in[i])
+                s_cmp.wait_event(ev_in[b][i])
+                if k >= 2:
+                    s_cmp.wait_event(ev_out[b][i])  # result buffer b has been read back
             c.unpack(Ubuf[b], stride, Ibuf[b], box, stream=s_cmp)
             c.fill_periodic(Ubuf[b], stride, patches, stream=s_cmp)
             c.step_next_dt(Ubuf[b], Obuf[b], stride, patches, dtch, dtn, stream=s_cmp)
             c.pack(Pbuf[b], Obuf[b], stride, box, stream=s_cmp)
             ev_cmp[b].record(s_cmp)
-            s_out.wait_event(ev_cmp[b])
-            with torch.cuda.stream(s_out):
-                Oh[b].copy_(Pbuf[b], non_blocking=True)
-                ev_out[b].record(s_out)
+            for i, qs in enumerate(parts):
+                s_out[i].wait_event(ev_cmp[b])
+                with torch.cuda.stream(s_out[i]):
+                    for q in qs:
+                        Oh[b][q].copy_(Pbuf[b][q], non_blocking=True)
+                    ev_out[b][i].record(s_out[i])
 
     pipeline(2)
     barrier()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(s_in)
+    t0.record(s_in[0])
+    for i in range(1, lanes):
+        s_in[i].wait_event(t0)
     pipeline(E)
-    t1.record(s_out)
+    for i in range(1, lanes):
+        s_out[0].wait_stream(s_out[i])
+    t1.record(s_out[0])
     barrier()
     ems = t0.elapsed_time(t1) / E
     torch.cuda.synchronize()
@@ -471,8 +485,9 @@ def e2e_stream(c, Uh, U, Uo, n, stride, patches, dtch, dtn, E, dev, world, barri
     return {"value": world * n ** 3 / (ems * 1e-3), "unit": "cell-updates/s",
             "h2d_bytes_per_step": int(Ih_pin.numel() * 8), "d2h_bytes_per_step": int(Oh[0].numel() * 8),
             "ms_per_step": ems, "steps": E,
-            "overlap": "two device buffers; packed-interior input copy, unpack + periodic ghost fill + "
-                       "step + pack, and read-back on three streams"}
+            "overlap": f"two device buffers; packed-interior input copy, unpack + periodic ghost fill + "
+                       f"step + pack, and read-back on their own streams, each copy split by variable over "
+                       f"{lanes} stream(s) per direction"}
 
 
 def roofline_alu(kern, flops, mixed, traffic=None):
@@ -907,7 +922,7 @@ def run_srmhd(args):
         def barrier():
             torch.cuda.synchronize()
         e2e = e2e_stream(c, torch.from_numpy(U0.reshape(9, -1)), U, Uo, n, stride, patches, d0, d1,
-                         max(4, args.steps), dev, world, barrier)
+                         max(4, args.steps), dev, world, barrier, lanes=args.copy_lanes)
         c.close()
     line = {"metric": METRIC, "value": world * n ** 3 / (ms * 1e-3), "unit": "cell-updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -1178,6 +1193,8 @@ def main():
                     help="blast: the hybrid integration with this shock threshold (thermal pressure; 0 = off)")
     ap.add_argument("--recon", default="ppm", choices=sorted(RECONS),
                     help="blast: reconstruction of the characteristic variables (the workload uses ppm)")
+    ap.add_argument("--copy-lanes", type=int, default=1,
+                    help="streams per copy direction in the end-to-end leg (each copy split by variable)")
     ap.add_argument("--corner", default="cell", choices=["cell", "mt"],
                     help="transverse fluxes from cell-centred states (Eq. transv) or the normal predictor states")
     ap.add_argument("--config", default="blast", choices=["blast", "amr", "srmhd", "tag"],
