@@ -144,6 +144,8 @@ struct ctu_ctx {
     DevWindow *dwin = nullptr;
     int *dwstart = nullptr;  // npatch * 3 CSR bases, then the plane positions
     int dwin_cap = 0, dws_cap = 0;
+    int dwin_n = 0;      // windows in dwin
+    int dwin_faces = 0;  // most faces of one of them within its patch
     bool win_dirty = false;
     int last_launches = 0;
     EventProf *prof = nullptr;
@@ -186,15 +188,25 @@ static ctu_status validate_patches(const ctu_ctx *ctx, int64_t stride, const ctu
 static ctu_status upload_windows(ctu_ctx *ctx, cudaStream_t s)
 {
     const int np = (int)ctx->hpatch.size();
+    ctx->dwin_n = 0;
+    ctx->dwin_faces = 0;
     if (!ctx->reg || ctx->hwin.empty() || np == 0) {
         ctx->win_dirty = false;
         return CTU_OK;
     }
     struct W { long long key; int n_d; DevWindow w; };
     std::vector<W> v;
+    int faces = 0;
     for (const ctu_flux_window &x : ctx->hwin) {
         if (x.patch >= np) continue;
         if (x.plane > ctx->hpatch[x.patch].n[x.dir]) continue;
+        {  // faces of the window within the patch
+            const int *pn = ctx->hpatch[x.patch].n;
+            const int ea = x.dir == 0 ? 1 : 0, eb = x.dir == 2 ? 1 : 2;
+            const long long fa = std::max(0, std::min(x.a1, pn[ea]) - x.a0);
+            const long long fb = std::max(0, std::min(x.b1, pn[eb]) - x.b0);
+            faces = (int)std::max<long long>(faces, std::min<long long>(fa * fb, 1ll << 30));
+        }
         DevWindow w;
         w.patch = ctx->sorted_of[x.patch];
         w.dir = x.dir; w.plane = x.plane; w.a0 = x.a0; w.a1 = x.a1; w.b0 = x.b0; w.b1 = x.b1; w.pad = 0;
@@ -236,6 +248,8 @@ static ctu_status upload_windows(ctu_ctx *ctx, cudaStream_t s)
     CTU_CUDA(cudaMemcpyAsync(ctx->dwin, dw.data(), sizeof(DevWindow) * dw.size(), cudaMemcpyHostToDevice, s));
     CTU_CUDA(cudaMemcpyAsync(ctx->dwstart, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice, s));
     CTU_CUDA(cudaStreamSynchronize(s));
+    ctx->dwin_n = (int)v.size();
+    ctx->dwin_faces = faces;
     ctx->win_dirty = false;
     return CTU_OK;
 }
@@ -415,6 +429,8 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.status = ctx->dstatus;
     const bool regs = ctx->reg && !ctx->hwin.empty() && !ctx->tuning;
     a.win = regs ? ctx->dwin : nullptr;
+    a.nwin = regs ? ctx->dwin_n : 0;
+    a.wfaces = regs ? ctx->dwin_faces : 0;
     a.wbase = regs ? ctx->dwstart : nullptr;
     a.wpos = regs ? ctx->dwstart + 3 * (int)ctx->hpatch.size() : nullptr;
     a.reg = regs ? ctx->reg : nullptr;

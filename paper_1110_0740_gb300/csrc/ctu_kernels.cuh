@@ -103,6 +103,8 @@ struct StepArgs {
     // wbase[] is -1 or an offset B into wpos[] such that the windows on plane
     // pl are win[wpos[B + pl] .. wpos[B + pl + 1])
     const DevWindow *win;
+    int nwin;              // windows in win (0 without registers)
+    int wfaces;            // most faces of one window within its patch
     const int *wbase;
     const int *wpos;
     double *reg;
@@ -622,10 +624,94 @@ __device__ __forceinline__ void register_face_var(const StepArgs &a, const DevPa
     }
 }
 
+// ---- parabolic terms in the final update (the RECON_*_PAR kernels)
+
+// Entries of L_P and of a face's Pi: 0..2 momentum, 3 energy, 4..6 B
+// (conserved component 1 + q).
+constexpr int NPAR = 7;
+
+// (Gamma - 1) max(kappa_perp, kappa_par), nu and eta in the working precision.
+template <class R> __device__ __forceinline__ R par_gk(const StepArgs &a);
+template <> __device__ __forceinline__ double par_gk<double>(const StepArgs &a)
+{
+    return (a.gam - 1.0) * (a.kpar > a.kappa ? a.kpar : a.kappa);
+}
+template <> __device__ __forceinline__ float par_gk<float>(const StepArgs &a) { return a.gm1f * a.kmaxf; }
+template <class R> __device__ __forceinline__ R par_nu(const StepArgs &a);
+template <> __device__ __forceinline__ double par_nu<double>(const StepArgs &a) { return a.nu; }
+template <> __device__ __forceinline__ float par_nu<float>(const StepArgs &a) { return a.nuf; }
+template <class R> __device__ __forceinline__ R par_eta(const StepArgs &a);
+template <> __device__ __forceinline__ double par_eta<double>(const StepArgs &a) { return a.eta; }
+template <> __device__ __forceinline__ float par_eta<float>(const StepArgs &a) { return a.etaf; }
+
+// Whether the parabolic terms change entry q of L_P: the energy always, the
+// momentum with viscosity, B with resistivity.
+__device__ __forceinline__ bool par_on(const StepArgs &a, int q)
+{
+    return q == 3 || (q < 3 ? a.par_visc != 0 : a.par_res != 0);
+}
+
+// L_P^(n+1/2) of scratch cell c from the face pass's fluxes PiF (3 x NPAR
+// planes; PiF[(d NPAR + q) S + c] is the flux through the cell's lower face
+// along d): sum_d (Pi(c + e_d) - Pi(c)) / dx_d in the order x, y, z, Eq.
+// (incrementop_par); 0 for the entries no term changes.
+template <class R>
+__device__ __forceinline__ void par_lp_cell(const StepArgs &a, const DevPatch &P, long long c, const R *PiF,
+                                            R (&lp)[NPAR])
+{
+    const long long S = a.sstride;
+#pragma unroll
+    for (int q = 0; q < NPAR; ++q) lp[q] = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= a.ndim) continue;
+        const long long st = dstr(P, d);
+        const R ih = pidx<R>(P, d);
+#pragma unroll
+        for (int q = 0; q < NPAR; ++q) {
+            if (!par_on(a, q)) continue;
+            const R *F = PiF + (long long)(d * NPAR + q) * S + c;
+            lp[q] += (F[st] - F[0]) * ih;
+        }
+    }
+}
+
+// par_lp_cell from fluxes staged per thread in shared memory: the lower and
+// upper faces along d at rows 2 d NPAR + q and (2 d + 1) NPAR + q, column t.
+template <class R>
+__device__ __forceinline__ void par_lp_staged(const StepArgs &a, const DevPatch &P, const float (*sPi)[BLOCK], int t,
+                                              R (&lp)[NPAR])
+{
+#pragma unroll
+    for (int q = 0; q < NPAR; ++q) lp[q] = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= a.ndim) continue;
+        const R ih = pidx<R>(P, d);
+#pragma unroll
+        for (int q = 0; q < NPAR; ++q) {
+            if (!par_on(a, q)) continue;
+            lp[q] += (sPi[(2 * d + 1) * NPAR + q][t] - sPi[2 * d * NPAR + q][t]) * ih;
+        }
+    }
+}
+
+// The diffusion term of the CFL rate, Eq. (Ca): 2 D sum_d 1/dx_d^2 with
+// D = max((Gamma - 1) kappa_max / rho, 4/3 nu, eta).
+template <class R> __device__ __forceinline__ R diffusion_rate(const StepArgs &a, const DevPatch &P, R rho)
+{
+    const R D = max(max(par_gk<R>(a) / rho, R(4.0 / 3.0) * par_nu<R>(a)), par_eta<R>(a));
+    R r = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d < a.ndim) r += R(2) * D * (pidx<R>(P, d) * pidx<R>(P, d));
+    return r;
+}
+
 // Final update of one interior cell: U^(n+1) = U^n + dt s, psi source, and
-// the CFL speed of U^(n+1) if requested (returned in R; 0 otherwise).
-// u0: U^n of the cell.
-template <int PHYS, class R, int LIT64 = 0>
+// the CFL speed of U^(n+1) if requested (returned in R; 0 otherwise), with
+// the diffusion term when DIFF.  u0: U^n of the cell.
+template <int PHYS, class R, int LIT64 = 0, bool DIFF = false>
 __device__ __forceinline__ R finish_cell_u(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
                                            const double (&u0)[NV], double dt, double damp, unsigned int &fl)
 {
@@ -638,14 +724,16 @@ __device__ __forceinline__ R finish_cell_u(const StepArgs &a, const DevPatch &P,
     if (!a.nextmax) return R(0);
     R V[NV];
     fl |= prim_any<PHYS, R, LIT64>(u, a, V);
-    return cell_speed<PHYS, R>(V, a, P);
+    R m = cell_speed<PHYS, R>(V, a, P);
+    if constexpr (DIFF) m += diffusion_rate<R>(a, P, V[0]);
+    return m;
 }
 
 // Ideal MHD in float: as finish_cell_u, but the CFL speed of U^(n+1) comes
 // from the primitive state V^n of the cell (global order) and the increment
 // dt s through the exact increment form of the pressure (interface_state),
 // so that U^(n+1) itself is never split or recovered in double-float.
-template <class R>
+template <class R, bool DIFF = false>
 __device__ __forceinline__ R finish_cell_inc(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
                                              const double (&u0)[NV], const R (&Vn)[NV], double dt, R dtr,
                                              double damp, unsigned int &fl)
@@ -661,17 +749,19 @@ __device__ __forceinline__ R finish_cell_inc(const StepArgs &a, const DevPatch &
 #pragma unroll
     for (int q = 0; q < NV; ++q) d[q] = dtr * s[q];
     fl |= interface_state<R, 0>(Vn, d, a, V);
-    return cell_speed<PH_MHD, R>(V, a, P);
+    R m = cell_speed<PH_MHD, R>(V, a, P);
+    if constexpr (DIFF) m += diffusion_rate<R>(a, P, V[0]);
+    return m;
 }
 
-template <int PHYS, class R, int LIT64 = 0>
+template <int PHYS, class R, int LIT64 = 0, bool DIFF = false>
 __device__ __forceinline__ R finish_cell(const StepArgs &a, const DevPatch &P, int cl, const R (&s)[NV],
                                          double dt, double damp, unsigned int &fl)
 {
     double u0[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) u0[q] = a.U[q * a.ustride + P.base + cl];
-    return finish_cell_u<PHYS, R, LIT64>(a, P, cl, s, u0, dt, damp, fl);
+    return finish_cell_u<PHYS, R, LIT64, DIFF>(a, P, cl, s, u0, dt, damp, fl);
 }
 
 // Block maximum of a non-negative value, folded into *out as the bits of a
@@ -1167,7 +1257,9 @@ __global__ void __launch_bounds__(BLOCK) k_pred(StepArgs a, GroupTable gt, const
 // Sweep along x, one thread per traced cell.  A tile covers xw traced cells
 // (xw - 2 updated cells) along x times BLOCK/xw rows along y.  The last sweep
 // of the step: U^(n+1) from U^n, dt (A + L_x) and the psi source, and the
-// next step's CFL speed.
+// next step's CFL speed.  With the parabolic terms the update also adds
+// dt L_P^(n+1/2), differenced from the face pass of the half-step fields,
+// and the CFL rate gains the diffusion term.
 template <int PHYS, class R, int PPM, int IFACE64, int LAST>
 __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k_sweep_x(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *A)
 {
@@ -1198,6 +1290,30 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
     unsigned int fl = 0;
     const long long c = traced ? P.soff + lcell(P, i, j, k) : 0;
     const bool out = traced && tx >= 1 && tx <= t.xw - 2 && i >= 0 && i < P.n[0];
+    // parabolic terms in float: the face fluxes of the updated cell's
+    // L_P^(n+1/2) travel to shared memory by cp.async while the cell is
+    // traced (their loads would otherwise stall the update at the end)
+    constexpr bool PAR = recon_par(PPM);
+    constexpr bool PSTAGE = PAR && LAST && sizeof(R) == 4;
+    __shared__ float sPi[PSTAGE ? 6 * NPAR : 1][BLOCK];
+    if constexpr (PSTAGE) {
+        if (out) {
+            const float *PiF = static_cast<const float *>(a.pif);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d >= a.ndim) continue;
+                const long long st = dstr(P, d);
+#pragma unroll
+                for (int q = 0; q < NPAR; ++q) {
+                    if (!par_on(a, q)) continue;
+                    const float *F = PiF + (long long)(d * NPAR + q) * a.sstride + c;
+                    cp_async(&sPi[2 * d * NPAR + q][me], F);
+                    cp_async(&sPi[(2 * d + 1) * NPAR + q][me], F + st);
+                }
+            }
+        }
+        cp_async_commit();
+    }
     // windows of this lane's face (plane i + 1), read ahead of the solves
     int w0 = 0, w1 = 0;
     if (traced && tx < t.xw - 1 && i <= P.n[0] - 1) {
@@ -1259,6 +1375,17 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
 #pragma unroll
                 for (int q = 0; q < NV; ++q) s[q] = A[q * a.sstride + c] + s[q];
             }
+            if constexpr (PAR) {  // + L_P^(n+1/2) from the face pass of the half-step fields
+                R lp[NPAR];
+                if constexpr (PSTAGE) {
+                    cp_async_wait_all();
+                    par_lp_staged<R>(a, P, sPi, me, lp);
+                } else {
+                    par_lp_cell<R>(a, P, c, static_cast<const R *>(a.pif), lp);
+                }
+#pragma unroll
+                for (int q = 0; q < NPAR; ++q) s[1 + q] += lp[q];
+            }
             if constexpr (PHYS == PH_MHD && sizeof(R) == 4 && !IFACE64) {
                 double u0[NV];
                 R Vn[NV];
@@ -1267,9 +1394,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
                     u0[q] = a.U[q * a.ustride + P.base + cl];
                     Vn[q] = Vs[q * a.sstride + c];
                 }
-                m = finish_cell_inc<R>(a, P, cl, s, u0, Vn, dtd, dtr, damp, fl);
+                m = finish_cell_inc<R, PAR>(a, P, cl, s, u0, Vn, dtd, dtr, damp, fl);
             } else {
-                m = finish_cell<PHYS, R, IFACE64>(a, P, cl, s, dtd, damp, fl);
+                m = finish_cell<PHYS, R, IFACE64, PAR>(a, P, cl, s, dtd, damp, fl);
             }
         }
         if (a.nextmax) block_max_to<R>(m, a.nextmax);

@@ -171,9 +171,11 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
                 [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 2, HY, HC, EXT><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
         CTU_MARK(nullptr);
     }
-    if constexpr (recon_par(PPM)) {  // parabolic terms: L_P^n and the half-step fields
+    if constexpr (recon_par(PPM)) {
+        // parabolic terms: L_P^n, the half-step fields and their face fluxes
+        // (the x sweep differences these into L_P^(n+1/2) for the update)
         CTU_MARK("par_faces_n");
-        auto half = [&](auto tm) {
+        auto par = [&](auto tm) {
             constexpr int V = decltype(tm)::value;
             n += over_groups(
                 li, [&](const Group &G) { return ((long long)par_face_box(G.n, a.ndim, 1) + BLOCK - 1) / BLOCK; },
@@ -187,9 +189,21 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
                 [&](const GroupTable &gt, unsigned nb) {
                     k_par_half<R, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th, (const R *)a.pif);
                 });
+            CTU_MARK(nullptr);
+            CTU_MARK("par_faces_h");
+            n += over_groups(
+                li, [&](const Group &G) { return ((long long)par_face_box(G.n, a.ndim, 0) + BLOCK - 1) / BLOCK; },
+                [&](const GroupTable &gt, unsigned nb) {
+                    k_par_faces<R, V, 0><<<nb, BLOCK, 0, s>>>(a, gt, Vs, a.th, (R *)a.pif);
+                });
+            if (a.reg && a.nwin > 0 && a.wfaces > 0) {
+                const int ny = (a.wfaces + BLOCK - 1) / BLOCK;
+                k_par_register<R, V><<<dim3(a.nwin, ny < 65535 ? ny : 65535), BLOCK, 0, s>>>(a, (const R *)a.pif);
+                ++n;
+            }
         };
         // one kernel per combination of the terms beyond isotropic conduction
-        with_tm(par_mask(a), half);
+        with_tm(par_mask(a), par);
         CTU_MARK(nullptr);
     }
     // sweeps in the order z, y, x: the first writes A = L_D, the middle one
@@ -207,35 +221,13 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
             n += launch_sweep_m<PHYS, R, PPM, IF64, 1, SW_MID>(a, li, Vs, L1, A, s);
         CTU_MARK(nullptr);
     }
-    // with parabolic terms the next step's CFL rate is taken after their update
-    StepArgs ax = a;
-    if constexpr (recon_par(PPM)) ax.nextmax = nullptr;
     CTU_MARK("sweep_x");
     n += over_groups(
         li, [&](const Group &G) { return Tiles::sweep_x(G.n, G.xw); },
         [&](const GroupTable &gt, unsigned nb) {
-            k_sweep_x<PHYS, R, PPM, IF64, 1><<<nb, BLOCK, 0, s>>>(ax, gt, Vs, L1, A);
+            k_sweep_x<PHYS, R, PPM, IF64, 1><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, A);
         });
     CTU_MARK(nullptr);
-    if constexpr (recon_par(PPM)) {  // parabolic terms: + dt L_P^(n+1/2)
-        CTU_MARK("par_faces_h");
-        with_tm(par_mask(a), [&](auto tm) {
-            constexpr int V = decltype(tm)::value;
-            n += over_groups(
-                li, [&](const Group &G) { return ((long long)par_face_box(G.n, a.ndim, 0) + BLOCK - 1) / BLOCK; },
-                [&](const GroupTable &gt, unsigned nb) {
-                    k_par_faces<R, V, 0><<<nb, BLOCK, 0, s>>>(a, gt, Vs, a.th, (R *)a.pif);
-                });
-            CTU_MARK(nullptr);
-            CTU_MARK("par_update");
-            n += over_groups(
-                li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
-                [&](const GroupTable &gt, unsigned nb) {
-                    k_par_update<PHYS, R, V><<<nb, BLOCK, 0, s>>>(a, gt, (const R *)a.pif, a.nextmax);
-                });
-        });
-        CTU_MARK(nullptr);
-    }
     return n;
 }
 

@@ -18,23 +18,24 @@
 // (rho(c) + rho(c + e_d)) and B_f the mean field; L_P = sum_d (Pi_(d,+) -
 // Pi_(d,-)) / dx_d acts on the momentum, the energy and B.
 //
-// Kernels around the hyperbolic step:
-//   k_par_faces  the face pass: every face flux of the ring box (from the
-//                primitive fields of U^n) or of the interior (from the
-//                half-step fields) once, stored per face
-//   k_par_half   after the first-order stage, on the ring box (the interior
-//                and one layer around it): L_P^n from the primitive fields of
-//                U^n (the predictors of every direction add dt/2 L_P^n, Eq.
-//                transv), and the fields (T, rho, v, B) of the cell-centred
-//                U^(n+1/2) = U^n + dt/2 (sum_d L_(H,d)^n + L_P^n), L_(H,d)^n the
-//                first-order stage's divergences, which that stage forms on
-//                the whole ring box for these kernels
-//   k_par_update U^(n+1) += dt L_P^(n+1/2) on the interior (Eq. update), the
-//                flux registers' momentum, energy and B take -dt A Pi, and on
-//                request the CFL rate of the result (with the diffusion
-//                term), in place of the fused reduction of the last sweep
-// The n+1/2 fields and the update are float64 (FP64 path) or double-float
-// with float64 update FMAs (mixed path: no other FP64-pipe instruction).
+// Kernels between the first-order stage and the sweeps:
+//   k_par_faces    the face pass: every face flux of the ring box (from the
+//                  primitive fields of U^n) or of the interior (from the
+//                  half-step fields) once, stored per face
+//   k_par_half     on the ring box (the interior and one layer around it):
+//                  L_P^n from the primitive fields of U^n (the predictors of
+//                  every direction add dt/2 L_P^n, Eq. transv), and the
+//                  fields (T, rho, v, B) of the cell-centred U^(n+1/2) = U^n +
+//                  dt/2 (sum_d L_(H,d)^n + L_P^n), L_(H,d)^n the first-order
+//                  stage's divergences, which that stage forms on the whole
+//                  ring box for these kernels
+//   k_par_register the flux registers' momentum, energy and B take -dt A Pi
+//                  of the half-step face fluxes (Eq. fluxcorr)
+// The x sweep differences the half-step face fluxes into L_P^(n+1/2) and
+// adds it to the update (U^(n+1) = U^n + dt (L_H^(n+1/2) + L_P^(n+1/2)),
+// Eq. update), with the diffusion term in the CFL rate of the result.
+// The n+1/2 fields are float64 (FP64 path) or double-float (mixed path: no
+// FP64-pipe instruction).
 // Each combination of the terms is a kernel of its own (template TM: bit 1
 // viscosity, bit 2 resistivity); conduction alone forms and stores only the
 // temperature.
@@ -49,21 +50,9 @@ namespace ctu {
 // index f: 0 rho, 1..3 v, 4 T, 5..7 B (the order of the primitive state).
 __host__ __device__ __forceinline__ int par_plane(int f) { return f == 4 ? 0 : (f < 4 ? f + 1 : f); }
 
-// Entries of L_P and of a face's Pi: 0..2 momentum, 3 energy, 4..6 B
-// (conserved component 1 + q).
-constexpr int NPAR = 7;
-
-// (Gamma - 1) max(kappa_perp, kappa_par), nu, kappa_perp, kappa_par -
-// kappa_perp and eta in the working precision.
-template <class R> __device__ __forceinline__ R par_gk(const StepArgs &a);
-template <> __device__ __forceinline__ double par_gk<double>(const StepArgs &a)
-{
-    return (a.gam - 1.0) * (a.kpar > a.kappa ? a.kpar : a.kappa);
-}
-template <> __device__ __forceinline__ float par_gk<float>(const StepArgs &a) { return a.gm1f * a.kmaxf; }
-template <class R> __device__ __forceinline__ R par_nu(const StepArgs &a);
-template <> __device__ __forceinline__ double par_nu<double>(const StepArgs &a) { return a.nu; }
-template <> __device__ __forceinline__ float par_nu<float>(const StepArgs &a) { return a.nuf; }
+// kappa_perp, kappa_par - kappa_perp and phi in the working precision (the
+// entries NPAR and par_gk, par_nu, par_eta are in ctu_kernels.cuh, where the
+// x sweep's update uses them).
 template <class R> __device__ __forceinline__ R par_kappa(const StepArgs &a);
 template <> __device__ __forceinline__ double par_kappa<double>(const StepArgs &a) { return a.kappa; }
 template <> __device__ __forceinline__ float par_kappa<float>(const StepArgs &a) { return a.kappaf; }
@@ -73,9 +62,6 @@ template <> __device__ __forceinline__ float par_dkappa<float>(const StepArgs &a
 template <class R> __device__ __forceinline__ R par_phi(const StepArgs &a);
 template <> __device__ __forceinline__ double par_phi<double>(const StepArgs &a) { return a.phi; }
 template <> __device__ __forceinline__ float par_phi<float>(const StepArgs &a) { return a.phif; }
-template <class R> __device__ __forceinline__ R par_eta(const StepArgs &a);
-template <> __device__ __forceinline__ double par_eta<double>(const StepArgs &a) { return a.eta; }
-template <> __device__ __forceinline__ float par_eta<float>(const StepArgs &a) { return a.etaf; }
 
 // Gradient of the fields f0 .. f0 + 2 at the face between c and cp = c + e_d:
 // g[t][i] = d f_(f0 + i) / dx_t.
@@ -258,11 +244,10 @@ __global__ void __launch_bounds__(BLOCK) k_par_faces(StepArgs a, GroupTable gt, 
 }
 
 // L_P at scratch cell c from the face pass: sum_d (Pi(c + e_d, d) -
-// Pi(c, d)) / dx_d in the order x, y, z; Pm, Pp receive each direction's
-// lower and upper face fluxes through faces(d, Pm, Pp).
-template <class R, int TM, class Faces>
+// Pi(c, d)) / dx_d in the order x, y, z, for the entries the terms TM change.
+template <class R, int TM>
 __device__ __forceinline__ void par_lp_faces(const StepArgs &a, const DevPatch &P, long long c, const R *PiF,
-                                             R (&lp)[NPAR], Faces faces)
+                                             R (&lp)[NPAR])
 {
     const long long S = a.sstride;
 #pragma unroll
@@ -272,16 +257,13 @@ __device__ __forceinline__ void par_lp_faces(const StepArgs &a, const DevPatch &
         if (d >= a.ndim) continue;
         const long long st = dstr(P, d);
         const R ih = pidx<R>(P, d);
-        R Pm[NPAR], Pp[NPAR];
 #pragma unroll
         for (int q = 0; q < NPAR; ++q) {
             const bool on = q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0);
+            if (!on) continue;
             const R *F = PiF + (long long)(d * NPAR + q) * S + c;
-            Pm[q] = on ? F[0] : R(0);
-            Pp[q] = on ? F[st] : R(0);
-            lp[q] += (Pp[q] - Pm[q]) * ih;
+            lp[q] += (F[st] - F[0]) * ih;
         }
-        faces(d, Pm, Pp);
     }
 }
 
@@ -310,7 +292,7 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
     const long long c = P.soff + cl;
     // L_P^n from the face pass over the primitive fields of U^n (T = p / rho)
     R lp[NPAR];
-    par_lp_faces<R, TM>(a, P, c, PiF, lp, [](int, const R (&)[NPAR], const R (&)[NPAR]) {});
+    par_lp_faces<R, TM>(a, P, c, PiF, lp);
     LP[3 * S + c] = lp[3];
     // the components each term changes: momentum (viscosity), energy, B
     // (resistivity)
@@ -393,94 +375,38 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
     }
 }
 
-// Flux-register windows of the face of plane `plane` normal to D (transverse
-// coordinates ca, cb in increasing dimension order): the momentum, energy and
-// B fluxes through it gain -Pi^(n+1/2) (Eq. fluxcorr with the parabolic flux).
-template <class R, int TM, int D>
-__device__ __forceinline__ void par_register(const StepArgs &a, const DevPatch &P, int patch, int plane, int ca,
-                                             int cb, const R (&pi)[NPAR], double dt)
-{
-    const int B = window_base(a, patch, D);
-    if (B < 0) return;
-    const int w0 = window_first(a, B, plane), w1 = window_first(a, B, plane + 1);
-    if (w1 <= w0) return;
-#pragma unroll
-    for (int q = 0; q < NPAR; ++q)
-        if (q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0))
-            register_face_var<R, D>(a, P, w0, w1, ca, cb, 1 + q, -pi[q], dt);
-}
-
+// Flux registers of the parabolic fluxes (Eq. fluxcorr with the flux F -
+// Pi): the momentum, energy and B of every window's faces gain -dt A
+// Pi^(n+1/2), Pi from the face pass of the half-step fields (PiF, the lower
+// face of the cell on the window's plane).  Block (w, y) takes window w's
+// faces y BLOCK + t, y BLOCK + t + gridDim.y BLOCK, ... within the patch
+// (as the sweeps' register_face, which skips the window's faces beyond it).
 template <class R, int TM>
-__device__ __forceinline__ void par_register_d(const StepArgs &a, const DevPatch &P, int patch, int d, int plane,
-                                               const int (&x)[3], const R (&pi)[NPAR], double dt)
+__global__ void __launch_bounds__(BLOCK) k_par_register(StepArgs a, const R *PiF)
 {
-    if (d == 0)
-        par_register<R, TM, 0>(a, P, patch, plane, x[1], x[2], pi, dt);
-    else if (d == 1)
-        par_register<R, TM, 1>(a, P, patch, plane, x[0], x[2], pi, dt);
-    else
-        par_register<R, TM, 2>(a, P, patch, plane, x[0], x[1], pi, dt);
-}
-
-// U_out's momentum, energy and B += dt L_P^(n+1/2) on the interior cells (the
-// k_maxspeed tiling), L_P^(n+1/2) from the face pass's fluxes PiF; the flux
-// registers of the cell's lower faces (and of its upper faces on the patch's
-// last plane) gain -dt A Pi; with next != null also the CFL rate of the
-// updated cell, Eq. (Ca) with the diffusion term, folded into *next.
-template <int PHYS, class R, int TM>
-__global__ void __launch_bounds__(BLOCK) k_par_update(StepArgs a, GroupTable gt, const R *PiF,
-                                                      unsigned long long *next)
-{
-    const Where wh = locate(gt);
-    const DevPatch P = a.patches[wh.patch];
-    const Tile t(wh.xw);
-    const int T0 = (P.n[0] + t.xw - 1) / t.xw, T1 = (P.n[1] + t.rows - 1) / t.rows;
-    const int b = wh.b;
-    const int i = (b % T0) * t.xw + t.tx(), j = ((b / T0) % T1) * t.rows + t.ty(), k = b / (T0 * T1);
-    R m = R(0);
-    const bool act = i < P.n[0] && j < P.n[1] && k < P.n[2];
-    const int cl = act ? lcell(P, i, j, k) : 0;
-    const long long c = P.soff + cl;
-    const int x[3] = {i, j, k};
-    const double dt = a.sp->dt;
-    // the flux registers of the cell's lower faces, and of its upper faces on
-    // the patch's last plane
-    auto faces = [&](int d, const R (&Pm)[NPAR], const R (&Pp)[NPAR]) {
-        if (!a.reg) return;
-        par_register_d<R, TM>(a, P, wh.patch, d, x[d], x, Pm, dt);
-        if (x[d] == P.n[d] - 1) par_register_d<R, TM>(a, P, wh.patch, d, x[d] + 1, x, Pp, dt);
-    };
-    R lp[NPAR];
-    if (act) par_lp_faces<R, TM>(a, P, c, PiF, lp, faces);
-    if (act) {
-        double *Uo = a.Uout + P.base + cl;
-        // the conserved components 1 + q the parabolic terms change
-        auto on = [](int q) -> bool { return q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0); };
-        double U[NV];
+    const DevWindow W = a.win[blockIdx.x];
+    const DevPatch P = a.patches[W.patch];
+    const int D = W.dir;
+    // the transverse dimensions ea < eb: (1, 2), (0, 2) or (0, 1)
+    const int na = W.a1 - W.a0, nb = W.b1 - W.b0;
+    const int fa = min(W.a1, D == 0 ? P.n[1] : P.n[0]) - W.a0;  // faces within the patch
+    const int fb = min(W.b1, D == 2 ? P.n[1] : P.n[2]) - W.b0;
+    if (fa <= 0 || fb <= 0) return;
+    // the face area: the cell widths along the two transverse dimensions
+    const double f = W.weight * a.sp->dt * (D == 0 ? P.dx[1] : P.dx[0]) * (D == 2 ? P.dx[1] : P.dx[2]);
+    const long long S = a.sstride;
+    for (int t = blockIdx.y * BLOCK + threadIdx.x; t < fa * fb; t += gridDim.y * BLOCK) {
+        const int ja = t % fa, jb = t / fa;
+        const int ca = W.a0 + ja, cb = W.b0 + jb;  // transverse coordinates, increasing dimension order
+        const int x0 = D == 0 ? W.plane : ca, x1 = D == 1 ? W.plane : (D == 0 ? ca : cb), x2 = D == 2 ? W.plane : cb;
+        const long long c = P.soff + lcell(P, x0, x1, x2);
+        const long long o = W.dst + (long long)jb * na + ja;
 #pragma unroll
         for (int q = 0; q < NPAR; ++q) {
-            if (on(q)) {
-                U[1 + q] = fma(dt, widen<R>(lp[q]), Uo[(1 + q) * a.ustride]);
-                Uo[(1 + q) * a.ustride] = U[1 + q];
-            }
-        }
-        if (next) {
-            U[0] = Uo[0];
-            U[8] = Uo[8 * a.ustride];
-#pragma unroll
-            for (int q = 0; q < NPAR; ++q)
-                if (!on(q)) U[1 + q] = Uo[(1 + q) * a.ustride];
-            R V[NV];
-            const unsigned int f = prim_any<PHYS, R>(U, a, V);
-            if (f) atomicOr(a.status, f);
-            m = cell_speed<PHYS, R>(V, a, P);
-            const R D = max(max(par_gk<R>(a) / V[0], R(4.0 / 3.0) * par_nu<R>(a)), par_eta<R>(a));  // par_gk: max kappa
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                if (d < a.ndim) m += R(2) * D * (pidx<R>(P, d) * pidx<R>(P, d));
+            const bool on = q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0);
+            if (on) a.reg[o + (long long)(1 + q) * nb * na] += f * widen<R>(-PiF[(long long)(D * NPAR + q) * S + c]);
         }
     }
-    if (next) block_max_to<R>(m, next);
 }
 
 } // namespace ctu
