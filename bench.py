@@ -1067,8 +1067,8 @@ def kernel_flops(n, recon="ppm", kappa=0.0, kappa_par=0.0, tc_phi=0.0, nu=0.0, e
     operands not counted) times the cells.  With parabolic terms par_half
     forms L_P^n and the half-step fields, the face passes evaluate every face
     flux once (one face flux is the count of the exact combination of terms
-    on), and the x sweep also differences L_P^(n+1/2) into the update and
-    adds the diffusion term to the next dt."""
+    on), par_lp differences L_P^(n+1/2), and the x sweep adds it to the
+    update and the diffusion term to the next dt."""
     c = {k: float(v) for k, v in _profile_numbers("flops_per_cell.txt").items()}
     cells = float(n) ** 3 if cells is None else float(cells)
     if physics == "srmhd":
@@ -1099,14 +1099,16 @@ def kernel_flops(n, recon="ppm", kappa=0.0, kappa_par=0.0, tc_phi=0.0, nu=0.0, e
     m = 1 + (3 if nu else 0) + (3 if eta else 0)
     swp = sweep + m * c.get("sweep_par_per_component", 0.0)
     # the face passes evaluate every face once (three per cell); the half-step
-    # kernel and the x sweep's update difference them
+    # kernel and par_lp difference them, and the x sweep adds L_P^(n+1/2) to
+    # its update
     half = (c.get("par_half_per_cell", 0.0) + m * c.get("par_half_per_component", 0.0)
             + (c.get("par_half_visc", 0.0) if nu else 0.0))
-    upd = (m * c.get("par_update_per_component", 0.0) + c.get("next_dt", 0.0)
-           + c.get("par_update_diffusion_number", 0.0))
+    upd = m * c.get("par_update_per_component", 0.0)
+    nxt = c.get("next_dt", 0.0) + c.get("par_update_diffusion_number", 0.0)
     return {"prim": c.get("prim", 0.0) * cells, "flux1": 3 * c.get("flux1_per_direction", 0.0) * cells,
             "par_faces_n": 3 * face * cells, "par_half": half * cells, "par_faces_h": 3 * face * cells,
-            "sweep_z": swp * cells, "sweep_y": swp * cells, "sweep_x": (swp + c.get("update", 0.0) + upd) * cells}
+            "par_lp": upd * cells, "sweep_z": swp * cells, "sweep_y": swp * cells,
+            "sweep_x": (swp + c.get("update", 0.0) + nxt) * cells}
 
 
 def precision_split_roofline(n, cells_per_s, hbm_gbs):

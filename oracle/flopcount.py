@@ -27,7 +27,8 @@ one face flux per direction (par_face_* summed over the terms on):
               scalings, two sums) + 16 (three first-order divergences) + m
               + 16 (U^n + dt/2 sum) + 17 (pressure, T) + 3 (v, viscosity)
   par update  3 faces + m x 10 (L_P, dt FMA) + next dt + 13 (diffusion
-              number: D / rho, 3 x (1/dx^2, x D, x 2, +))
+              number: D / rho, 3 x (1/dx^2, x D, x 2, +)); the GPU step
+              splits it over the face pass, par_lp and the x sweep
   sweep (d)   + 2 m (dt/2 L_P in the predictor)
 
     python oracle/flopcount.py [--out profiles/flops_per_cell.txt]

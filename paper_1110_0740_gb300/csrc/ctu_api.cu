@@ -335,9 +335,10 @@ static ctu_status bind_patches(ctu_ctx *ctx, const ctu_patch *p, int np, cudaStr
 // working precision), the half-step fields (one 8-byte plane, T; eight
 // with viscosity, resistivity or anisotropic conduction) and the face fluxes
 // of the parabolic face pass (3 directions x 7 words of the working
-// precision) per scratch cell.
+// precision) per scratch cell, and L_P^(n+1/2) (7 words of the working
+// precision) differenced from them for the x sweep's update.
 struct ScratchOffsets {
-    size_t flags, lp, th, pif, total;
+    size_t flags, lp, th, pif, lph, total;
 };
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 static ScratchOffsets scratch_offsets(const ctu_ctx *ctx)
@@ -352,7 +353,8 @@ static ScratchOffsets scratch_offsets(const ctu_ctx *ctx)
     o.lp = align256(o.flags + (ctx->cfg.shock_detect ? S : 0));
     o.th = align256(o.lp + (par ? 7 * S * elt : 0));
     o.pif = align256(o.th + (par ? (tensor ? 8 : 1) * S * sizeof(double) : 0));
-    o.total = o.pif + (par ? 3 * 7 * S * elt : 0);
+    o.lph = align256(o.pif + (par ? 3 * 7 * S * elt : 0));
+    o.total = o.lph + (par ? 7 * S * elt : 0);
     return o;
 }
 
@@ -411,6 +413,7 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
     a.lp = nullptr;
     a.th = nullptr;
     a.pif = nullptr;
+    a.lph = nullptr;
     if (ctx->scratch) {
         const ScratchOffsets o = scratch_offsets(ctx);
         if (ctx->cfg.shock_detect) a.flags = (unsigned char *)ctx->scratch + o.flags;
@@ -418,6 +421,7 @@ static StepArgs make_args(const ctu_ctx *ctx, const double *Uin, double *Uout, i
             a.lp = (const unsigned char *)ctx->scratch + o.lp;
             a.th = (double *)((unsigned char *)ctx->scratch + o.th);
             a.pif = (unsigned char *)ctx->scratch + o.pif;
+            a.lph = (unsigned char *)ctx->scratch + o.lph;
         }
     }
     a.U = Uin;

@@ -92,6 +92,7 @@ struct StepArgs {
     const void *lp;
     double *th;
     void *pif;             // face fluxes of the parabolic face pass (3 x NPAR planes of R)
+    void *lph;             // L_P^(n+1/2) per scratch cell (NPAR planes of R)
     const double *U;       // pool in
     double *Uout;          // pool out
     long long ustride;     // pool variable stride
@@ -649,51 +650,6 @@ template <> __device__ __forceinline__ float par_eta<float>(const StepArgs &a) {
 __device__ __forceinline__ bool par_on(const StepArgs &a, int q)
 {
     return q == 3 || (q < 3 ? a.par_visc != 0 : a.par_res != 0);
-}
-
-// L_P^(n+1/2) of scratch cell c from the face pass's fluxes PiF (3 x NPAR
-// planes; PiF[(d NPAR + q) S + c] is the flux through the cell's lower face
-// along d): sum_d (Pi(c + e_d) - Pi(c)) / dx_d in the order x, y, z, Eq.
-// (incrementop_par); 0 for the entries no term changes.
-template <class R>
-__device__ __forceinline__ void par_lp_cell(const StepArgs &a, const DevPatch &P, long long c, const R *PiF,
-                                            R (&lp)[NPAR])
-{
-    const long long S = a.sstride;
-#pragma unroll
-    for (int q = 0; q < NPAR; ++q) lp[q] = R(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (d >= a.ndim) continue;
-        const long long st = dstr(P, d);
-        const R ih = pidx<R>(P, d);
-#pragma unroll
-        for (int q = 0; q < NPAR; ++q) {
-            if (!par_on(a, q)) continue;
-            const R *F = PiF + (long long)(d * NPAR + q) * S + c;
-            lp[q] += (F[st] - F[0]) * ih;
-        }
-    }
-}
-
-// par_lp_cell from fluxes staged per thread in shared memory: the lower and
-// upper faces along d at rows 2 d NPAR + q and (2 d + 1) NPAR + q, column t.
-template <class R>
-__device__ __forceinline__ void par_lp_staged(const StepArgs &a, const DevPatch &P, const float (*sPi)[BLOCK], int t,
-                                              R (&lp)[NPAR])
-{
-#pragma unroll
-    for (int q = 0; q < NPAR; ++q) lp[q] = R(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (d >= a.ndim) continue;
-        const R ih = pidx<R>(P, d);
-#pragma unroll
-        for (int q = 0; q < NPAR; ++q) {
-            if (!par_on(a, q)) continue;
-            lp[q] += (sPi[(2 * d + 1) * NPAR + q][t] - sPi[2 * d * NPAR + q][t]) * ih;
-        }
-    }
 }
 
 // The diffusion term of the CFL rate, Eq. (Ca): 2 D sum_d 1/dx_d^2 with
@@ -1258,8 +1214,7 @@ __global__ void __launch_bounds__(BLOCK) k_pred(StepArgs a, GroupTable gt, const
 // (xw - 2 updated cells) along x times BLOCK/xw rows along y.  The last sweep
 // of the step: U^(n+1) from U^n, dt (A + L_x) and the psi source, and the
 // next step's CFL speed.  With the parabolic terms the update also adds
-// dt L_P^(n+1/2), differenced from the face pass of the half-step fields,
-// and the CFL rate gains the diffusion term.
+// dt L_P^(n+1/2) (k_par_lp), and the CFL rate gains the diffusion term.
 template <int PHYS, class R, int PPM, int IFACE64, int LAST>
 __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k_sweep_x(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *A)
 {
@@ -1290,27 +1245,18 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
     unsigned int fl = 0;
     const long long c = traced ? P.soff + lcell(P, i, j, k) : 0;
     const bool out = traced && tx >= 1 && tx <= t.xw - 2 && i >= 0 && i < P.n[0];
-    // parabolic terms in float: the face fluxes of the updated cell's
-    // L_P^(n+1/2) travel to shared memory by cp.async while the cell is
-    // traced (their loads would otherwise stall the update at the end)
+    // parabolic terms in float: the updated cell's L_P^(n+1/2) travels to
+    // shared memory by cp.async while the cell is traced (its loads would
+    // otherwise stall the update at the end)
     constexpr bool PAR = recon_par(PPM);
     constexpr bool PSTAGE = PAR && LAST && sizeof(R) == 4;
-    __shared__ float sPi[PSTAGE ? 6 * NPAR : 1][BLOCK];
+    __shared__ float sLp[PSTAGE ? NPAR : 1][BLOCK];
     if constexpr (PSTAGE) {
         if (out) {
-            const float *PiF = static_cast<const float *>(a.pif);
+            const float *Lh = static_cast<const float *>(a.lph) + c;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (d >= a.ndim) continue;
-                const long long st = dstr(P, d);
-#pragma unroll
-                for (int q = 0; q < NPAR; ++q) {
-                    if (!par_on(a, q)) continue;
-                    const float *F = PiF + (long long)(d * NPAR + q) * a.sstride + c;
-                    cp_async(&sPi[2 * d * NPAR + q][me], F);
-                    cp_async(&sPi[(2 * d + 1) * NPAR + q][me], F + st);
-                }
-            }
+            for (int q = 0; q < NPAR; ++q)
+                if (par_on(a, q)) cp_async(&sLp[q][me], Lh + q * a.sstride);
         }
         cp_async_commit();
     }
@@ -1375,16 +1321,16 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
 #pragma unroll
                 for (int q = 0; q < NV; ++q) s[q] = A[q * a.sstride + c] + s[q];
             }
-            if constexpr (PAR) {  // + L_P^(n+1/2) from the face pass of the half-step fields
-                R lp[NPAR];
-                if constexpr (PSTAGE) {
-                    cp_async_wait_all();
-                    par_lp_staged<R>(a, P, sPi, me, lp);
-                } else {
-                    par_lp_cell<R>(a, P, c, static_cast<const R *>(a.pif), lp);
-                }
+            if constexpr (PSTAGE) {  // + L_P^(n+1/2) of the half-step fields
+                cp_async_wait_all();
 #pragma unroll
-                for (int q = 0; q < NPAR; ++q) s[1 + q] += lp[q];
+                for (int q = 0; q < NPAR; ++q)
+                    if (par_on(a, q)) s[1 + q] += sLp[q][me];
+            } else if constexpr (PAR) {
+                const R *Lh = static_cast<const R *>(a.lph) + c;
+#pragma unroll
+                for (int q = 0; q < NPAR; ++q)
+                    if (par_on(a, q)) s[1 + q] += Lh[q * a.sstride];
             }
             if constexpr (PHYS == PH_MHD && sizeof(R) == 4 && !IFACE64) {
                 double u0[NV];

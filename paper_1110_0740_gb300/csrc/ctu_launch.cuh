@@ -201,6 +201,13 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
                 k_par_register<R, V><<<dim3(a.nwin, ny < 65535 ? ny : 65535), BLOCK, 0, s>>>(a, (const R *)a.pif);
                 ++n;
             }
+            CTU_MARK(nullptr);
+            CTU_MARK("par_lp");
+            n += over_groups(
+                li, [&](const Group &G) { return Tiles::interior(G.n, G.xw); },
+                [&](const GroupTable &gt, unsigned nb) {
+                    k_par_lp<R, V><<<nb, BLOCK, 0, s>>>(a, gt, (const R *)a.pif, (R *)a.lph);
+                });
         };
         // one kernel per combination of the terms beyond isotropic conduction
         with_tm(par_mask(a), par);

@@ -31,9 +31,10 @@
 //                  ring box for these kernels
 //   k_par_register the flux registers' momentum, energy and B take -dt A Pi
 //                  of the half-step face fluxes (Eq. fluxcorr)
-// The x sweep differences the half-step face fluxes into L_P^(n+1/2) and
-// adds it to the update (U^(n+1) = U^n + dt (L_H^(n+1/2) + L_P^(n+1/2)),
-// Eq. update), with the diffusion term in the CFL rate of the result.
+//   k_par_lp       L_P^(n+1/2) of the interior cells from those face fluxes
+// The x sweep adds L_P^(n+1/2) to its update (U^(n+1) = U^n + dt
+// (L_H^(n+1/2) + L_P^(n+1/2)), Eq. update), with the diffusion term in the
+// CFL rate of the result.
 // The n+1/2 fields are float64 (FP64 path) or double-float (mixed path: no
 // FP64-pipe instruction).
 // Each combination of the terms is a kernel of its own (template TM: bit 1
@@ -372,6 +373,29 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
                 for (int q = 0; q < 3; ++q) W2[(5 + q) * S + c] = make_float2(U[5 + q].hi, U[5 + q].lo);
             }
         }
+    }
+}
+
+// L_P^(n+1/2) on the interior cells (the k_maxspeed tiling) from the face
+// pass of the half-step fields, for the x sweep's update: LPh, NPAR planes
+// of R, the entries the terms TM change.
+template <class R, int TM>
+__global__ void __launch_bounds__(BLOCK) k_par_lp(StepArgs a, GroupTable gt, const R *PiF, R *LPh)
+{
+    const Where wh = locate(gt);
+    const DevPatch P = a.patches[wh.patch];
+    const Tile t(wh.xw);
+    const int T0 = (P.n[0] + t.xw - 1) / t.xw, T1 = (P.n[1] + t.rows - 1) / t.rows;
+    const int b = wh.b;
+    const int i = (b % T0) * t.xw + t.tx(), j = ((b / T0) % T1) * t.rows + t.ty(), k = b / (T0 * T1);
+    if (i >= P.n[0] || j >= P.n[1] || k >= P.n[2]) return;
+    const long long c = P.soff + lcell(P, i, j, k);
+    R lp[NPAR];
+    par_lp_faces<R, TM>(a, P, c, PiF, lp);
+#pragma unroll
+    for (int q = 0; q < NPAR; ++q) {
+        const bool on = q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0);
+        if (on) LPh[q * a.sstride + c] = lp[q];
     }
 }
 

@@ -37,7 +37,7 @@ def test_kernel_flops_parabolic(terms):
     c = {k: float(v) for k, v in bench._profile_numbers("flops_per_cell.txt").items()}
     plain = bench.kernel_flops(1, "ppm")
     fl = bench.kernel_flops(1, "ppm", **terms)
-    for k in ("prim", "flux1", "par_faces_n", "par_half", "par_faces_h", "sweep_z", "sweep_y", "sweep_x"):
+    for k in ("prim", "flux1", "par_faces_n", "par_half", "par_faces_h", "par_lp", "sweep_z", "sweep_y", "sweep_x"):
         assert fl[k] > 0, k
     kappa, kp = terms.get("kappa", 0.0), terms.get("kappa_par", 0.0) or terms.get("kappa", 0.0)
     cond = "none"
