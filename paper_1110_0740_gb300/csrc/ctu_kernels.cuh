@@ -494,11 +494,12 @@ __device__ __forceinline__ unsigned int trace_cell_t(const StepArgs &a, const De
     R pl[NV], ml[NV], pg[NV], mg[NV];
     unsigned int f = 0;
     // parabolic terms: dt/2 L_P^n joins the half-step increments of every
-    // direction (Eq. transv with Pi != 0)
+    // direction (Eq. transv with Pi != 0); the sweeps along y and z take it
+    // through the transverse divergence L1_x, to which k_par_half added it
     R Tc[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) Tc[q] = T[q];
-    if constexpr (recon_par(PPM)) {
+    if (recon_par(PPM) && D == 0) {
         const R *lp = static_cast<const R *>(a.lp) + c;
         const R hd = R(0.5) * pdt<R>(a.sp);
         Tc[4] += hd * lp[3 * a.sstride];

@@ -24,7 +24,8 @@
 //                  half-step fields) once, stored per face
 //   k_par_half     on the ring box (the interior and one layer around it):
 //                  L_P^n from the primitive fields of U^n (the predictors of
-//                  every direction add dt/2 L_P^n, Eq. transv), and the
+//                  every direction add dt/2 L_P^n, Eq. transv: those along
+//                  y and z through L1_x, which it adds L_P^n to), and the
 //                  fields (T, rho, v, B) of the cell-centred U^(n+1/2) = U^n +
 //                  dt/2 (sum_d L_(H,d)^n + L_P^n), L_(H,d)^n the first-order
 //                  stage's divergences, which that stage forms on the whole
@@ -46,10 +47,15 @@
 
 namespace ctu {
 
-// Planes of the half-step fields (8 bytes per scratch cell each): T, then
-// with viscosity or resistivity rho, v_x, v_y, v_z, B_x, B_y, B_z.  Field
-// index f: 0 rho, 1..3 v, 4 T, 5..7 B (the order of the primitive state).
+// Planes of the half-step fields: T, then with viscosity or resistivity rho,
+// v_x, v_y, v_z, B_x, B_y, B_z.  Field index f: 0 rho, 1..3 v, 4 T, 5..7 B
+// (the order of the primitive state).  FP64 path: a double plane each.
+// Mixed path: T as double-float pairs (float2, the first 8 bytes per
+// scratch cell), the others as float planes after it (par_fplane; the face
+// pass takes them in float, as coefficients of a small increment).
 __host__ __device__ __forceinline__ int par_plane(int f) { return f == 4 ? 0 : (f < 4 ? f + 1 : f); }
+// float offset, in units of the scratch stride, of field f != 4's plane
+__host__ __device__ __forceinline__ int par_fplane(int f) { return 1 + par_plane(f); }
 
 // kappa_perp, kappa_par - kappa_perp and phi in the working precision (the
 // entries NPAR and par_gk, par_nu, par_eta are in ctu_kernels.cuh, where the
@@ -183,8 +189,7 @@ __host__ __device__ __forceinline__ int par_ring_cells(const int *n, int ndim)
 // through its lower face along each active d whose transverse coordinates
 // lie in [b, n - 1 - b] is stored in PiF[(d NPAR + q) S + c] for the entries
 // q the terms change.  HALF: fields of U^n from the primitive state V (T =
-// p / rho); otherwise the half-step fields Wh (par_plane; double-float pairs
-// in the mixed path).
+// p / rho); otherwise the half-step fields Wh (par_plane, par_fplane).
 __host__ __device__ __forceinline__ int par_face_box(const int *n, int ndim, int half)
 {
     const int w = half ? 3 : 1;
@@ -236,10 +241,14 @@ __global__ void __launch_bounds__(BLOCK) k_par_faces(StepArgs a, GroupTable gt, 
         // temperature differences of the double-float fields, exact to float;
         // those of v and B, coefficients of a small increment, in float
         const float2 *W2 = reinterpret_cast<const float2 *>(Wh);
-        pass([&](int f, long long n) -> float { return W2[par_plane(f) * S + n].x; },
+        const float *Wf = reinterpret_cast<const float *>(Wh);
+        pass([&](int f, long long n) -> float { return f == 4 ? W2[n].x : Wf[par_fplane(f) * S + n]; },
              [&](int f, long long n1, long long n2) -> float {
-                 const float2 u = W2[par_plane(f) * S + n1], v = W2[par_plane(f) * S + n2];
-                 return f == 4 ? df_add(df{u.x, u.y}, df{-v.x, -v.y}).hi : u.x - v.x;
+                 if (f == 4) {
+                     const float2 u = W2[n1], v = W2[n2];
+                     return df_add(df{u.x, u.y}, df{-v.x, -v.y}).hi;
+                 }
+                 return Wf[par_fplane(f) * S + n1] - Wf[par_fplane(f) * S + n2];
              });
     }
 }
@@ -270,13 +279,13 @@ __device__ __forceinline__ void par_lp_faces(const StepArgs &a, const DevPatch &
 
 // One thread per ring-box cell (par_ring_cells), whose first-order
 // divergences the first-order stage formed in every direction (its EXT
-// range).  L1: the first-order divergences (global order); LP: L_P^n per
-// scratch cell, 7 planes of R (momentum, energy, B); Wh: the half-step fields
-// (par_plane), doubles (FP64 path) or double-float pairs (hi, lo) (mixed
-// path).  TM: bit 1 viscosity, bit 2 resistivity, bit 4 anisotropic or
-// saturated conduction (which need the B and rho fields).
+// range).  L1: the first-order divergences (global order), L1_x gains L_P^n
+// in 2-D and 3-D; LP: L_P^n per scratch cell, 7 planes of R (momentum,
+// energy, B); Wh: the half-step fields
+// (par_plane, par_fplane).  TM: bit 1 viscosity, bit 2 resistivity, bit 4
+// anisotropic or saturated conduction (which need the B and rho fields).
 template <class R, int TM>
-__global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *LP,
+__global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, const R *Vs, R *L1, R *LP,
                                                     double *Wh, const R *PiF)
 {
     const Where w = locate(gt);
@@ -294,23 +303,34 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
     // L_P^n from the face pass over the primitive fields of U^n (T = p / rho)
     R lp[NPAR];
     par_lp_faces<R, TM>(a, P, c, PiF, lp);
-    LP[3 * S + c] = lp[3];
     // the components each term changes: momentum (viscosity), energy, B
     // (resistivity)
     auto on = [](int q) -> bool { return q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0); };
 #pragma unroll
     for (int q = 0; q < NPAR; ++q)
-        if (q != 3 && on(q)) LP[q * S + c] = lp[q];
-    // the cell-centred half-step state and its fields
+        if (on(q)) LP[q * S + c] = lp[q];
+    // the cell-centred half-step state and its fields.  dt/2 L_P^n reaches
+    // the predictors of the sweeps along y and z (Eq. transv) through their
+    // transverse terms, which both take L1_x: L1_x gains L_P^n (the x sweep
+    // adds it from LP)
     R s[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) s[q] = R(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         if (d >= a.ndim) continue;
-        const R *Ld = L1 + (long long)d * NV * S + c;
+        R *Ld = L1 + (long long)d * NV * S + c;
+        R l[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) s[q] += Ld[q * S];
+        for (int q = 0; q < 8; ++q) {
+            l[q] = Ld[q * S];
+            s[q] += l[q];
+        }
+        if (d == 0 && a.ndim > 1) {
+#pragma unroll
+            for (int q = 0; q < NPAR; ++q)
+                if (on(q)) Ld[(1 + q) * S] = l[1 + q] + lp[q];
+        }
     }
 #pragma unroll
     for (int q = 0; q < NPAR; ++q)
@@ -342,7 +362,8 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
     } else {
         // double-float (no FP64-pipe instruction): U^(n+1/2) = U^n + (dt/2) s
         // with the product exact, then p, T = p / rho and v = m / rho to
-        // ~2^-44; stored as float pairs (hi, lo)
+        // ~2^-44; T stored as a float pair (hi, lo), the others rounded to
+        // float
         const float hdt = 0.5f * a.sp->dtf;
         df U[8];
 #pragma unroll
@@ -358,19 +379,17 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
         if (!isfinite(U[0].hi) || !isfinite(p.hi)) f |= ST_NAN;
         if (f) atomicOr(a.status, f);
         float2 *W2 = reinterpret_cast<float2 *>(Wh);
+        float *Wf = reinterpret_cast<float *>(Wh);
         W2[c] = make_float2(T.hi, T.lo);
         {
-            if constexpr ((TM & 5) != 0) W2[S + c] = make_float2(U[0].hi, U[0].lo);
+            if constexpr ((TM & 5) != 0) Wf[par_fplane(0) * S + c] = U[0].hi;
             if constexpr ((TM & 1) != 0) {
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const df v = df_div(U[1 + q], U[0]);
-                    W2[(2 + q) * S + c] = make_float2(v.hi, v.lo);
-                }
+                for (int q = 0; q < 3; ++q) Wf[par_fplane(1 + q) * S + c] = df_div(U[1 + q], U[0]).hi;
             }
             if constexpr ((TM & 6) != 0) {
 #pragma unroll
-                for (int q = 0; q < 3; ++q) W2[(5 + q) * S + c] = make_float2(U[5 + q].hi, U[5 + q].lo);
+                for (int q = 0; q < 3; ++q) Wf[par_fplane(5 + q) * S + c] = U[5 + q].hi;
             }
         }
     }
