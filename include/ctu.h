@@ -526,10 +526,9 @@ int ctu_profile_read(ctu_ctx *ctx, int i, const char **name, double *total_ms, l
  * otherwise the call returns CTU_ETOOLARGE and launches nothing.
  *
  * The call allocates nothing (no cudaMalloc/cudaFree, no heap).  Its first
- * call on a device looks up the array's device address (set-up), so make
- * that first call before any stream capture.  The patch table reaches the
- * array in kernel parameters, so no enqueued copy reads host memory after
- * the call returns.  All calls share the one array
+ * call on a device looks up the array's device address (set-up).  The patch
+ * table reaches the array in kernel parameters, so no enqueued copy reads
+ * host memory after the call returns.  All calls share the one array
  * and it keeps the last call's contents (the status word is cleared at the
  * start of every call): calls that overlap on the GPU -- on different
  * streams, or from different threads -- race and corrupt each other.
