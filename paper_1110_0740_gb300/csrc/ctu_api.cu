@@ -98,8 +98,9 @@ static bool grid_fits(const std::vector<Group> &gs, int ndim)
         const long long c = G.count;
         tot[0] += c * Tiles::prim(G.N);
         for (int D = 0; D < 3; ++D) {
-            tot[1 + D] += c * Tiles::div1(G.n, ndim, D, G.xw, G.seg);
-            tot[4 + D] += c * (D == 0 ? Tiles::sweep_x(G.n, G.xw) : Tiles::sweep_m(G.n, D, G.xw, G.seg));
+            // (one row per thread: the most blocks the x kernels launch)
+            tot[1 + D] += c * Tiles::div1(G.n, ndim, D, G.xw, G.seg, true, 1);
+            tot[4 + D] += c * (D == 0 ? Tiles::sweep_x(G.n, G.xw, 1) : Tiles::sweep_m(G.n, D, G.xw, G.seg));
         }
         tot[7] += c * Tiles::interior(G.n, G.xw);
     }

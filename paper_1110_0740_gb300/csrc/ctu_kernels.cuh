@@ -124,6 +124,37 @@ constexpr int BLOCK = 128;
 #ifndef CTU_SWEEPX_MINB
 #define CTU_SWEEPX_MINB 5
 #endif
+#ifndef CTU_DIV1X_ROWS
+#define CTU_DIV1X_ROWS 8
+#endif
+#ifndef CTU_SWEEPX_ROWS
+#define CTU_SWEEPX_ROWS 8
+#endif
+// Rows each thread of the first-order x stage and of the x sweep takes in
+// turn, so that the per-thread set-up (tile decode, patch and window look-up,
+// the block reductions) is shared: up to `most` (per launch: the most that
+// still leaves the launch enough blocks, launch_rows), and within that the x
+// that minimises the patch's row slots ceil(nrows / (tile_rows x))
+// tile_rows x weighted by (1 + 1/(8 x)), the set-up measured at about an
+// eighth of a cell's work, so that small patches are not padded with idle
+// rows (the larger x on a tie).  Chosen on the host per patch group; the
+// kernels read it from the group table.
+constexpr int DIV1X_ROWS = CTU_DIV1X_ROWS, SWEEPX_ROWS = CTU_SWEEPX_ROWS;
+inline int rows_per_thread(int most, int nrows, int tile_rows)
+{
+    int best = 1;
+    long long bc = -1;
+    for (int x = 1; x <= most; ++x) {
+        const long long rr = (long long)tile_rows * x;
+        const long long slots = (nrows + rr - 1) / rr * rr;
+        const long long cost = slots * (8 * x + 1) * (840 / x);  // slots (1 + 1/(8x)), times 8 * 840
+        if (bc < 0 || cost <= bc) {
+            bc = cost;
+            best = x;
+        }
+    }
+    return best;
+}
 constexpr int SEG = CTU_SEG;  // default cells per marching segment
 
 // One launch covers every patch group of a batch (up to MAXG groups): block
@@ -143,6 +174,7 @@ struct GroupTable {
     unsigned char bs1[MAXG], bs2[MAXG];
     int xw[MAXG];
     int seg[MAXG];
+    unsigned char xr[MAXG];  // rows per thread of the x-tiled kernels that take several (rows_per_thread)
 };
 
 // Division of 0 <= x < 2^32 by an invariant divisor d >= 1 with one high
@@ -166,7 +198,7 @@ inline DivMagic divmagic(unsigned d)
 }
 
 struct Where {
-    int patch, b, xw, seg;
+    int patch, b, xw, seg, xr;
 };
 
 __device__ __forceinline__ Where locate(const GroupTable &gt)
@@ -183,6 +215,7 @@ __device__ __forceinline__ Where locate(const GroupTable &gt)
     w.b = (int)rel - q * gt.bpp[g];
     w.xw = gt.xw[g];
     w.seg = gt.seg[g];
+    w.xr = gt.xr[g];
     return w;
 }
 // The marching sweeps are latency bound: they are compiled for at least
@@ -775,13 +808,24 @@ struct Tiles {
         return ((long long)(N[0] - 2) * (N[1] > 1 ? N[1] - 2 : 1) * (N[2] > 1 ? N[2] - 2 : 1) + BLOCK - 1) / BLOCK;
     }
     // ext: along D also the ring's layers -1 and n_D (k_div1's EXT)
-    static long long div1(const int *n, int ndim, int D, int w, int seg, bool ext = false)
+    // rows per thread of k_div1<0> and of k_sweep_x on patches of n cells,
+    // at most `most`
+    static int div1x_rows(const int *n, int ndim, int w, int most)
+    {
+        return rows_per_thread(most, ndim > 1 ? n[1] + 2 : 1, BLOCK / w);
+    }
+    static int sweepx_rows(const int *n, int w, int most)
+    {
+        return rows_per_thread(most, n[1], BLOCK / sweepx_xw(n[0], w));
+    }
+    static long long div1(const int *n, int ndim, int D, int w, int seg, bool ext = false, int most = DIV1X_ROWS)
     {
         const int r = BLOCK / w;
         const int x2 = ext ? 2 : 0;
         if (D == 0) {
             const int e1 = ndim > 1 ? n[1] + 2 : 1, e2 = ndim > 2 ? n[2] + 2 : 1;
-            return (long long)((n[0] + x2 + w - 2) / (w - 1)) * ((e1 + r - 1) / r) * e2;
+            const int rr = r * div1x_rows(n, ndim, w, most);  // rows of a block
+            return (long long)((n[0] + x2 + w - 2) / (w - 1)) * ((e1 + rr - 1) / rr) * e2;
         }
         const int O = D == 1 ? 2 : 1;
         const int eO = ndim > O ? n[O] + 2 : 1;
@@ -797,11 +841,12 @@ struct Tiles {
         const int e1 = ndim > 1 ? n[1] + 2 : 1, e2 = ndim > 2 ? n[2] + 2 : 1;
         return (long long)((n[0] + w - 3) / (w - 2)) * ((e1 + r - 1) / r) * e2;
     }
-    static long long sweep_x(const int *n, int w)
+    static long long sweep_x(const int *n, int w, int most = SWEEPX_ROWS)
     {
+        const int xr = sweepx_rows(n, w, most);
         w = sweepx_xw(n[0], w);
-        const int r = BLOCK / w;
-        return (long long)((n[0] + w - 3) / (w - 2)) * ((n[1] + r - 1) / r) * n[2];
+        const int rr = (BLOCK / w) * xr;  // rows of a block
+        return (long long)((n[0] + w - 3) / (w - 2)) * ((n[1] + rr - 1) / rr) * n[2];
     }
     static long long sweep_m(const int *n, int D, int w, int seg)
     {
@@ -1008,38 +1053,45 @@ __global__ void __launch_bounds__(BLOCK) k_div1(StepArgs a, GroupTable gt, const
         const int e1 = a.ndim > 1 ? P.n[1] + 2 : 1, e2 = a.ndim > 2 ? P.n[2] + 2 : 1;
         const int lo1 = a.ndim > 1 ? -1 : 0, lo2 = a.ndim > 2 ? -1 : 0;
         constexpr int X = EXT ? 1 : 0;
-        const int T0 = (P.n[0] + 2 * X + out - 1) / out, T1 = (e1 + t.rows - 1) / t.rows;
+        const int xr = wh.xr;         // rows of a thread (Tiles::div1x_rows)
+        const int RR = t.rows * xr;  // rows of a block
+        const int T0 = (P.n[0] + 2 * X + out - 1) / out, T1 = (e1 + RR - 1) / RR;
         const int tx = t.tx();
         const int i = (b % T0) * out + tx - X;  // this lane's face lies between cells i - 1 and i
-        const int j = ((b / T0) % T1) * t.rows + t.ty();
+        const int jb = ((b / T0) % T1) * RR + t.ty();
         const int k = b / (T0 * T1);
-        const bool face = j < e1 && k < e2 && i <= P.n[0] + X;
-        const long long c = face ? P.soff + lcell(P, i, lo1 + j, lo2 + k) : 0;  // cell i
-        R F[NV];
-        if (face) {
-            R L[NV], Rr[NV];
+        const long long row = (long long)P.N[0];  // scratch distance of adjacent rows
+        long long c = P.soff + lcell(P, i, lo1 + jb, lo2 + (k < e2 ? k : 0));  // cell i of row jb
+#pragma unroll 1
+        for (int r = 0; r < xr; ++r, c += t.rows * row) {
+            const int j = jb + r * t.rows;
+            const bool face = j < e1 && k < e2 && i <= P.n[0] + X;
+            R F[NV];
+            if (face) {
+                R L[NV], Rr[NV];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                L[q] = Vs[q * a.sstride + c - 1];
-                Rr[q] = Vs[q * a.sstride + c];
+                for (int q = 0; q < NV; ++q) {
+                    L[q] = Vs[q * a.sstride + c - 1];
+                    Rr[q] = Vs[q * a.sstride + c];
+                }
+                if (HYB && PHYS == PH_MHD && ((a.flags[c - 1] | a.flags[c]) & 1))
+                    riemann_hll(L, Rr, gam, ch, F);
+                else if (HLLC && PHYS == PH_MHD)
+                    riemann_hllc(L, Rr, gam, ch, F);
+                else
+                    riemann_any<PHYS, R>(L, Rr, gam, ch, F);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) F[q] = R(0);
             }
-            if (HYB && PHYS == PH_MHD && ((a.flags[c - 1] | a.flags[c]) & 1))
-                riemann_hll(L, Rr, gam, ch, F);
-            else if (HLLC && PHYS == PH_MHD)
-                riemann_hllc(L, Rr, gam, ch, F);
-            else
-                riemann_any<PHYS, R>(L, Rr, gam, ch, F);
-        } else {
+            // every lane of the warp takes part in the exchange
+            R Fm[NV];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) F[q] = R(0);
-        }
-        // every lane of the warp takes part in the exchange
-        R Fm[NV];
+            for (int q = 0; q < NV; ++q) Fm[q] = __shfl_up_sync(0xffffffffu, F[q], 1, t.xw);
+            if (face && tx >= 1) {  // cell i - 1: lower face from lane tx - 1, upper face F
 #pragma unroll
-        for (int q = 0; q < NV; ++q) Fm[q] = __shfl_up_sync(0xffffffffu, F[q], 1, t.xw);
-        if (face && tx >= 1) {  // cell i - 1: lower face from lane tx - 1, upper face F
-#pragma unroll
-            for (int q = 0; q < NV; ++q) Ld[q * a.sstride + c - 1] = (Fm[q] - F[q]) * iD;
+                for (int q = 0; q < NV; ++q) Ld[q * a.sstride + c - 1] = (Fm[q] - F[q]) * iD;
+            }
         }
     } else {
         constexpr int O = D == 1 ? 2 : 1;  // the other transverse dimension
@@ -1211,8 +1263,9 @@ __global__ void __launch_bounds__(BLOCK) k_pred(StepArgs a, GroupTable gt, const
     }
 }
 
-// Sweep along x, one thread per traced cell.  A tile covers xw traced cells
-// (xw - 2 updated cells) along x times BLOCK/xw rows along y.  The last sweep
+// Sweep along x, one thread per traced cell of up to SWEEPX_ROWS rows.  A
+// tile covers xw traced cells (xw - 2 updated cells) along x times BLOCK/xw
+// rows along y, a block that many rows per thread in turn.  The last sweep
 // of the step: U^(n+1) from U^n, dt (A + L_x) and the psi source, and the
 // next step's CFL speed.  With the parabolic terms the update also adds
 // dt L_P^(n+1/2) (k_par_lp), and the CFL rate gains the diffusion term.
@@ -1224,138 +1277,143 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k
     const DevPatch P = a.patches[patch];
     const Tile t(sweepx_xw(P.n[0], wh.xw));
     const int out_x = t.xw - 2;
-    const int T0 = (P.n[0] + out_x - 1) / out_x, T1 = (P.n[1] + t.rows - 1) / t.rows;
+    const int xr = wh.xr;         // rows of a thread (Tiles::sweepx_rows)
+    const int RR = t.rows * xr;  // rows of a block
+    const int T0 = (P.n[0] + out_x - 1) / out_x, T1 = (P.n[1] + RR - 1) / RR;
     const int b = wh.b;
     const int tx = t.tx(), ty = t.ty();
     const int i = (b % T0) * out_x - 1 + tx;  // traced cell, >= -1
-    const int j = ((b / T0) % T1) * t.rows + ty;
+    const int j0 = ((b / T0) % T1) * RR;      // the block's first row
     const int k = b / (T0 * T1);
-    // threads beyond the block's last full row (BLOCK not a multiple of the
-    // row width) trace nothing
-    const bool traced = ty < t.rows && j < P.n[1] && k < P.n[2] && i <= P.n[0];
     __shared__ R sP[BLOCK][NV], sM[BLOCK][NV], sF[BLOCK][NV];
-    // faces of the block with flux-register windows: lane, first and end window
-    __shared__ int s_nreg, s_reg[BLOCK][3];
+    // faces of the block with flux-register windows: lane, first and end
+    // window (the count alternates between two slots from row to row, so
+    // that resetting one never races with reading the other)
+    __shared__ int s_nreg[2], s_reg[BLOCK][3];
     const int me = threadIdx.x;
-    if (me == 0) s_nreg = 0;
     const R gam = pgam<R>(a), ch = pch<R>(a.sp);
     const R dtr = pdt<R>(a.sp);
     const double dtd = a.sp->dt;
     const R dtdx = dtr * pidx<R>(P, 0);
     const R hdt = R(0.5) * dtr;
     unsigned int fl = 0;
-    const long long c = traced ? P.soff + lcell(P, i, j, k) : 0;
-    const bool out = traced && tx >= 1 && tx <= t.xw - 2 && i >= 0 && i < P.n[0];
-    // parabolic terms in float: the updated cell's L_P^(n+1/2) travels to
-    // shared memory by cp.async while the cell is traced (its loads would
-    // otherwise stall the update at the end)
     constexpr bool PAR = recon_par(PPM);
     constexpr bool PSTAGE = PAR && LAST && sizeof(R) == 4;
     __shared__ float sLp[PSTAGE ? NPAR : 1][BLOCK];
-    if constexpr (PSTAGE) {
-        if (out) {
-            const float *Lh = static_cast<const float *>(a.lph) + c;
-#pragma unroll
-            for (int q = 0; q < NPAR; ++q)
-                if (par_on(a, q)) cp_async(&sLp[q][me], Lh + q * a.sstride);
-        }
-        cp_async_commit();
-    }
-    // windows of this lane's face (plane i + 1), read ahead of the solves
-    int w0 = 0, w1 = 0;
-    if (traced && tx < t.xw - 1 && i <= P.n[0] - 1) {
-        const int B = window_base(a, patch, 0);
-        w0 = window_first(a, B, i + 1);
-        w1 = window_first(a, B, i + 2);
-    }
-    if (traced) {
-        R vs[5][NV];
-#pragma unroll
-        for (int m = 0; m < 5; ++m)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) vs[m][q] = Vs[q * a.sstride + c + (m - 2)];
-        R Vp[NV], Vm[NV];
-        fl |= trace_cell<PHYS, R, PPM, IFACE64, 0>(a, P, vs, L1, c, ch, dtdx, hdt, Vp, Vm);
-#pragma unroll
-        for (int q = 0; q < NV; ++q) { sP[me][q] = Vp[q]; sM[me][q] = Vm[q]; }
-    }
-    __syncthreads();
-    if (traced && tx < t.xw - 1 && i <= P.n[0] - 1) {
-        R L[NV], Rr[NV], F[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) { L[q] = sP[me][q]; Rr[q] = sM[me + 1][q]; }
-        face_flux<PHYS, R, 0, recon_hllc(PPM)>(L, Rr, gam, ch, F,
-                                               recon_hybrid(PPM) && ((a.flags[c] | a.flags[c + 1]) & 1));
-#pragma unroll
-        for (int q = 0; q < NV; ++q) sF[me][q] = F[q];
-        // faces on plane i+1; the tile's last face belongs to the next tile
-        if (w1 > w0 && (tx < t.xw - 2 || i + 1 == P.n[0])) {
-            const int slot = atomicAdd(&s_nreg, 1);
-            s_reg[slot][0] = me;
-            s_reg[slot][1] = w0;
-            s_reg[slot][2] = w1;
-        }
-    }
-    // after a block barrier: the listed faces' register sums, one thread per
-    // (face, variable), so that the float64 accumulation of a face is spread
-    // over lanes instead of running on one lane of its warp
-    auto registers = [&]() {
-        const int nr = s_nreg;
-        for (int it = me; it < nr * NV; it += BLOCK) {
-            const int f = it / NV, q = it - f * NV;
-            const int l = s_reg[f][0];
-            const int jl = ((b / T0) % T1) * t.rows + l / t.xw;  // row of lane l; k is the block's
-            register_face_var<R, 0>(a, P, s_reg[f][1], s_reg[f][2], jl, k, q, sF[l][q], dtd);
-        }
-    };
-    if (LAST) {
-        const double damp = patch_damp(a, P);  // includes a block barrier
-        registers();
-        R m = R(0);
-        if (out) {
-            const R ix = pidx<R>(P, 0);
-            R s[NV];
-            const int cl = lcell(P, i, j, k);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) s[q] = (sF[me - 1][q] - sF[me][q]) * ix;
-            if (a.ndim > 1) {  // A = the other directions' L, from the earlier sweeps
-#pragma unroll
-                for (int q = 0; q < NV; ++q) s[q] = A[q * a.sstride + c] + s[q];
-            }
-            if constexpr (PSTAGE) {  // + L_P^(n+1/2) of the half-step fields
-                cp_async_wait_all();
+    const double damp = LAST ? patch_damp(a, P) : 1.0;  // includes a block barrier
+    R m = R(0);
+#pragma unroll 1
+    for (int r = 0; r < xr; ++r) {
+        const int j = j0 + r * t.rows + ty;
+        // threads beyond the block's last full row (BLOCK not a multiple of
+        // the row width) trace nothing
+        const bool traced = ty < t.rows && j < P.n[1] && k < P.n[2] && i <= P.n[0];
+        const long long c = traced ? P.soff + lcell(P, i, j, k) : 0;
+        const bool out = traced && tx >= 1 && tx <= t.xw - 2 && i >= 0 && i < P.n[0];
+        int *nreg = &s_nreg[r & 1];
+        if (me == 0) *nreg = 0;
+        // parabolic terms in float: the updated cell's L_P^(n+1/2) travels to
+        // shared memory by cp.async while the cell is traced (its loads would
+        // otherwise stall the update at the end)
+        if constexpr (PSTAGE) {
+            if (out) {
+                const float *Lh = static_cast<const float *>(a.lph) + c;
 #pragma unroll
                 for (int q = 0; q < NPAR; ++q)
-                    if (par_on(a, q)) s[1 + q] += sLp[q][me];
-            } else if constexpr (PAR) {
-                const R *Lh = static_cast<const R *>(a.lph) + c;
-#pragma unroll
-                for (int q = 0; q < NPAR; ++q)
-                    if (par_on(a, q)) s[1 + q] += Lh[q * a.sstride];
+                    if (par_on(a, q)) cp_async(&sLp[q][me], Lh + q * a.sstride);
             }
-            if constexpr (PHYS == PH_MHD && sizeof(R) == 4 && !IFACE64) {
-                double u0[NV];
-                R Vn[NV];
-#pragma unroll
-                for (int q = 0; q < NV; ++q) {
-                    u0[q] = a.U[q * a.ustride + P.base + cl];
-                    Vn[q] = Vs[q * a.sstride + c];
-                }
-                m = finish_cell_inc<R, PAR>(a, P, cl, s, u0, Vn, dtd, dtr, damp, fl);
-            } else {
-                m = finish_cell<PHYS, R, IFACE64, PAR>(a, P, cl, s, dtd, damp, fl);
-            }
+            cp_async_commit();
         }
-        if (a.nextmax) block_max_to<R>(m, a.nextmax);
-    } else {
+        // windows of this lane's face (plane i + 1), read ahead of the solves
+        int w0 = 0, w1 = 0;
+        if (traced && tx < t.xw - 1 && i <= P.n[0] - 1) {
+            const int B = window_base(a, patch, 0);
+            w0 = window_first(a, B, i + 1);
+            w1 = window_first(a, B, i + 2);
+        }
+        if (traced) {
+            R vs[5][NV];
+#pragma unroll
+            for (int mm = 0; mm < 5; ++mm)
+#pragma unroll
+                for (int q = 0; q < NV; ++q) vs[mm][q] = Vs[q * a.sstride + c + (mm - 2)];
+            R Vp[NV], Vm[NV];
+            fl |= trace_cell<PHYS, R, PPM, IFACE64, 0>(a, P, vs, L1, c, ch, dtdx, hdt, Vp, Vm);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) { sP[me][q] = Vp[q]; sM[me][q] = Vm[q]; }
+        }
         __syncthreads();
-        registers();
-        if (out) {
+        if (traced && tx < t.xw - 1 && i <= P.n[0] - 1) {
+            R L[NV], Rr[NV], F[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) { L[q] = sP[me][q]; Rr[q] = sM[me + 1][q]; }
+            face_flux<PHYS, R, 0, recon_hllc(PPM)>(L, Rr, gam, ch, F,
+                                                   recon_hybrid(PPM) && ((a.flags[c] | a.flags[c + 1]) & 1));
+#pragma unroll
+            for (int q = 0; q < NV; ++q) sF[me][q] = F[q];
+            // faces on plane i+1; the tile's last face belongs to the next tile
+            if (w1 > w0 && (tx < t.xw - 2 || i + 1 == P.n[0])) {
+                const int slot = atomicAdd(nreg, 1);
+                s_reg[slot][0] = me;
+                s_reg[slot][1] = w0;
+                s_reg[slot][2] = w1;
+            }
+        }
+        __syncthreads();
+        // the listed faces' register sums, one thread per (face, variable),
+        // so that the float64 accumulation of a face is spread over lanes
+        // instead of running on one lane of its warp
+        {
+            const int nr = *nreg;
+            for (int it = me; it < nr * NV; it += BLOCK) {
+                const int f = it / NV, q = it - f * NV;
+                const int l = s_reg[f][0];
+                const int jl = j0 + r * t.rows + l / t.xw;  // row of lane l; k is the block's
+                register_face_var<R, 0>(a, P, s_reg[f][1], s_reg[f][2], jl, k, q, sF[l][q], dtd);
+            }
+        }
+        if (LAST) {
+            if (out) {
+                const R ix = pidx<R>(P, 0);
+                R s[NV];
+                const int cl = lcell(P, i, j, k);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) s[q] = (sF[me - 1][q] - sF[me][q]) * ix;
+                if (a.ndim > 1) {  // A = the other directions' L, from the earlier sweeps
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) s[q] = A[q * a.sstride + c] + s[q];
+                }
+                if constexpr (PSTAGE) {  // + L_P^(n+1/2) of the half-step fields
+                    cp_async_wait_all();
+#pragma unroll
+                    for (int q = 0; q < NPAR; ++q)
+                        if (par_on(a, q)) s[1 + q] += sLp[q][me];
+                } else if constexpr (PAR) {
+                    const R *Lh = static_cast<const R *>(a.lph) + c;
+#pragma unroll
+                    for (int q = 0; q < NPAR; ++q)
+                        if (par_on(a, q)) s[1 + q] += Lh[q * a.sstride];
+                }
+                if constexpr (PHYS == PH_MHD && sizeof(R) == 4 && !IFACE64) {
+                    double u0[NV];
+                    R Vn[NV];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        u0[q] = a.U[q * a.ustride + P.base + cl];
+                        Vn[q] = Vs[q * a.sstride + c];
+                    }
+                    m = fmax(m, finish_cell_inc<R, PAR>(a, P, cl, s, u0, Vn, dtd, dtr, damp, fl));
+                } else {
+                    m = fmax(m, finish_cell<PHYS, R, IFACE64, PAR>(a, P, cl, s, dtd, damp, fl));
+                }
+            }
+        } else if (out) {
             const R ix = pidx<R>(P, 0);
 #pragma unroll
             for (int q = 0; q < NV; ++q) A[q * a.sstride + c] = (sF[me - 1][q] - sF[me][q]) * ix;
         }
     }
+    if (LAST && a.nextmax) block_max_to<R>(m, a.nextmax);
     if (fl) atomicOr(a.status, fl);
 }
 

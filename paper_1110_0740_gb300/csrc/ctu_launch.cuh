@@ -15,10 +15,14 @@ namespace ctu {
 
 // Launch a kernel once over every patch group of the batch (MAXG groups per
 // launch), in the order of li.groups (largest patches first).  bpp(G): blocks
-// per patch of group G; go(table, blocks) launches.  Returns the number of
-// launches.
-template <class BPP, class GO>
-static int over_groups(const LaunchInfo &li, BPP bpp, GO go)
+// per patch of group G; go(table, blocks) launches; xr(G): rows per thread
+// of the x-tiled kernels that take several (1 for the others).  Returns the
+// number of launches.
+struct OneRow {
+    int operator()(const Group &) const { return 1; }
+};
+template <class BPP, class GO, class XR = OneRow>
+static int over_groups(const LaunchInfo &li, BPP bpp, GO go, XR xr = XR())
 {
     int launches = 0;
     for (int c0 = 0; c0 < li.ngroups; c0 += MAXG) {
@@ -36,6 +40,7 @@ static int over_groups(const LaunchInfo &li, BPP bpp, GO go)
             gt.bs2[k] = dm.s2;
             gt.xw[k] = G.xw;
             gt.seg[k] = G.seg;
+            gt.xr[k] = (unsigned char)xr(G);
             tot += (long long)G.count * gt.bpp[k];
         }
         gt.start[gt.n] = (int)tot;
@@ -45,6 +50,21 @@ static int over_groups(const LaunchInfo &li, BPP bpp, GO go)
         }
     }
     return launches;
+}
+
+// Rows per thread of an x-tiled kernel for a launch (Tiles::div1x_rows,
+// sweepx_rows): the largest power of two up to `most` at which the launch
+// still has at least 8 waves of blocks (152 SMs x 5), so that the longer
+// blocks leave no long tail on a small batch.  blocks(G, x): blocks of one
+// patch of group G at x rows per thread.
+template <class BLK> static int launch_rows(const LaunchInfo &li, int most, BLK blocks)
+{
+    for (int x = most; x > 1; x /= 2) {
+        long long tot = 0;
+        for (int g = 0; g < li.ngroups; ++g) tot += (long long)li.groups[g].count * blocks(li.groups[g], x);
+        if (tot >= 8LL * 152 * 5) return x;
+    }
+    return 1;
 }
 
 // The parabolic kernels' term mask (bit 1 viscosity, bit 2 resistivity, bit
@@ -158,9 +178,13 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         }
     } else if (a.ndim > 1 || EXT) {
         CTU_MARK("flux1");
+        const int xr1 = launch_rows(li, DIV1X_ROWS, [&](const Group &G, int x) {
+            return Tiles::div1(G.n, a.ndim, 0, G.xw, G.seg, EXT, x);
+        });
         n += over_groups(
-            li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 0, G.xw, G.seg, EXT); },
-            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 0, HY, HC, EXT><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); });
+            li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 0, G.xw, G.seg, EXT, xr1); },
+            [&](const GroupTable &gt, unsigned nb) { k_div1<PHYS, R, 0, HY, HC, EXT><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1); },
+            [&](const Group &G) { return Tiles::div1x_rows(G.n, a.ndim, G.xw, xr1); });
         if (a.ndim > 1)
             n += over_groups(
                 li, [&](const Group &G) { return Tiles::div1(G.n, a.ndim, 1, G.xw, G.seg, EXT); },
@@ -178,21 +202,21 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         auto par = [&](auto tm) {
             constexpr int V = decltype(tm)::value;
             n += over_groups(
-                li, [&](const Group &G) { return ((long long)par_face_box(G.n, a.ndim, 1) + BLOCK - 1) / BLOCK; },
+                li, [&](const Group &G) { return ((long long)par_face_threads(G.n, a.ndim, 1) + BLOCK - 1) / BLOCK; },
                 [&](const GroupTable &gt, unsigned nb) {
                     k_par_faces<R, V, 1><<<nb, BLOCK, 0, s>>>(a, gt, Vs, a.th, (R *)a.pif);
                 });
             CTU_MARK(nullptr);
             CTU_MARK("par_half");
             n += over_groups(
-                li, [&](const Group &G) { return ((long long)par_ring_cells(G.n, a.ndim) + BLOCK - 1) / BLOCK; },
+                li, [&](const Group &G) { return ((long long)par_ring_threads(G.n, a.ndim) + BLOCK - 1) / BLOCK; },
                 [&](const GroupTable &gt, unsigned nb) {
-                    k_par_half<R, V><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, (R *)a.lp, a.th, (const R *)a.pif);
+                    k_par_half<R, V><<<nb, BLOCK, 0, s>>>(a, gt, L1, (R *)a.lp, a.th, (const R *)a.pif);
                 });
             CTU_MARK(nullptr);
             CTU_MARK("par_faces_h");
             n += over_groups(
-                li, [&](const Group &G) { return ((long long)par_face_box(G.n, a.ndim, 0) + BLOCK - 1) / BLOCK; },
+                li, [&](const Group &G) { return ((long long)par_face_threads(G.n, a.ndim, 0) + BLOCK - 1) / BLOCK; },
                 [&](const GroupTable &gt, unsigned nb) {
                     k_par_faces<R, V, 0><<<nb, BLOCK, 0, s>>>(a, gt, Vs, a.th, (R *)a.pif);
                 });
@@ -229,11 +253,13 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
         CTU_MARK(nullptr);
     }
     CTU_MARK("sweep_x");
+    const int xrs = launch_rows(li, SWEEPX_ROWS, [&](const Group &G, int x) { return Tiles::sweep_x(G.n, G.xw, x); });
     n += over_groups(
-        li, [&](const Group &G) { return Tiles::sweep_x(G.n, G.xw); },
+        li, [&](const Group &G) { return Tiles::sweep_x(G.n, G.xw, xrs); },
         [&](const GroupTable &gt, unsigned nb) {
             k_sweep_x<PHYS, R, PPM, IF64, 1><<<nb, BLOCK, 0, s>>>(a, gt, Vs, L1, A);
-        });
+        },
+        [&](const Group &G) { return Tiles::sweepx_rows(G.n, G.xw, xrs); });
     CTU_MARK(nullptr);
     return n;
 }

@@ -183,19 +183,33 @@ __host__ __device__ __forceinline__ int par_ring_cells(const int *n, int ndim)
     return (n[0] + 2) * (ndim > 1 ? n[1] + 2 : 1) * (ndim > 2 ? n[2] + 2 : 1);
 }
 
+// Planes along z each thread of the face passes and of k_par_half takes in
+// turn (sharing its set-up), and the threads of a face pass (its box) and of
+// k_par_half (the ring box) with the z extent in groups of PAR_ZR planes.
+#ifndef CTU_PAR_ZR
+#define CTU_PAR_ZR 4
+#endif
+constexpr int PAR_ZR = CTU_PAR_ZR;
+__host__ __device__ __forceinline__ int par_face_threads(const int *n, int ndim, int half)
+{
+    const int w = half ? 3 : 1;
+    const int e2 = ndim > 2 ? n[2] + w : 1;
+    return (n[0] + w) * (ndim > 1 ? n[1] + w : 1) * ((e2 + PAR_ZR - 1) / PAR_ZR);
+}
+__host__ __device__ __forceinline__ int par_ring_threads(const int *n, int ndim)
+{
+    const int e2 = ndim > 2 ? n[2] + 2 : 1;
+    return (n[0] + 2) * (ndim > 1 ? n[1] + 2 : 1) * ((e2 + PAR_ZR - 1) / PAR_ZR);
+}
+
 // Face pass: every face flux once.  For every cell c of the box [b, n - b]
 // on the active axes (b = -1 with HALF, the faces of the ring box, for
 // L_P^n; b = 0, the faces of the interior, for L_P^(n+1/2)), the flux
 // through its lower face along each active d whose transverse coordinates
 // lie in [b, n - 1 - b] is stored in PiF[(d NPAR + q) S + c] for the entries
-// q the terms change.  HALF: fields of U^n from the primitive state V (T =
-// p / rho); otherwise the half-step fields Wh (par_plane, par_fplane).
-__host__ __device__ __forceinline__ int par_face_box(const int *n, int ndim, int half)
-{
-    const int w = half ? 3 : 1;
-    return (n[0] + w) * (ndim > 1 ? n[1] + w : 1) * (ndim > 2 ? n[2] + w : 1);
-}
-
+// q the terms change; a thread takes PAR_ZR cells along z in turn.  HALF:
+// fields of U^n from the primitive state V (T = p / rho); otherwise the
+// half-step fields Wh (par_plane, par_fplane).
 template <class R, int TM, int HALF>
 __global__ void __launch_bounds__(BLOCK) k_par_faces(StepArgs a, GroupTable gt, const R *Vs, const double *Wh,
                                                      R *PiF)
@@ -203,30 +217,36 @@ __global__ void __launch_bounds__(BLOCK) k_par_faces(StepArgs a, GroupTable gt, 
     const Where w = locate(gt);
     const DevPatch P = a.patches[w.patch];
     const int t = w.b * BLOCK + threadIdx.x;
-    if (t >= par_face_box(P.n, a.ndim, HALF)) return;
+    if (t >= par_face_threads(P.n, a.ndim, HALF)) return;
     constexpr int bb = HALF ? -1 : 0;
     const int e0 = P.n[0] + 1 - 2 * bb, e1 = a.ndim > 1 ? P.n[1] + 1 - 2 * bb : 1;
+    const int e2 = a.ndim > 2 ? P.n[2] + 1 - 2 * bb : 1;
     int x[3];
     x[0] = t % e0 + bb;
     x[1] = (t / e0) % e1 + (a.ndim > 1 ? bb : 0);
-    x[2] = t / (e0 * e1) + (a.ndim > 2 ? bb : 0);
+    const int z0 = (t / (e0 * e1)) * PAR_ZR;  // this thread's planes z0 .. z0 + PAR_ZR - 1 of the box
     const long long S = a.sstride;
-    const long long c = P.soff + lcell(P, x[0], x[1], x[2]);
+    long long c = 0;
     auto on = [](int q) -> bool { return q == 3 || (q < 3 ? (TM & 1) != 0 : (TM & 2) != 0); };
     auto pass = [&](auto get, auto dif) {
+#pragma unroll 1
+        for (int r = 0; r < PAR_ZR && z0 + r < e2; ++r) {
+            x[2] = z0 + r + (a.ndim > 2 ? bb : 0);
+            c = P.soff + lcell(P, x[0], x[1], x[2]);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (d >= a.ndim) continue;
-            bool ok = true;
+            for (int d = 0; d < 3; ++d) {
+                if (d >= a.ndim) continue;
+                bool ok = true;
 #pragma unroll
-            for (int e = 0; e < 3; ++e)
-                if (e != d && e < a.ndim) ok &= x[e] <= P.n[e] - 1 - bb;
-            if (!ok) continue;
-            R Pi[NPAR];
-            par_face<R, TM>(a, P, c - dstr(P, d), d, get, dif, Pi);
+                for (int e = 0; e < 3; ++e)
+                    if (e != d && e < a.ndim) ok &= x[e] <= P.n[e] - 1 - bb;
+                if (!ok) continue;
+                R Pi[NPAR];
+                par_face<R, TM>(a, P, c - dstr(P, d), d, get, dif, Pi);
 #pragma unroll
-            for (int q = 0; q < NPAR; ++q)
-                if (on(q)) PiF[(long long)(d * NPAR + q) * S + c] = Pi[q];
+                for (int q = 0; q < NPAR; ++q)
+                    if (on(q)) PiF[(long long)(d * NPAR + q) * S + c] = Pi[q];
+            }
         }
     };
     if constexpr (HALF) {
@@ -277,27 +297,17 @@ __device__ __forceinline__ void par_lp_faces(const StepArgs &a, const DevPatch &
     }
 }
 
-// One thread per ring-box cell (par_ring_cells), whose first-order
-// divergences the first-order stage formed in every direction (its EXT
-// range).  L1: the first-order divergences (global order), L1_x gains L_P^n
-// in 2-D and 3-D; LP: L_P^n per scratch cell, 7 planes of R (momentum,
-// energy, B); Wh: the half-step fields
-// (par_plane, par_fplane).  TM: bit 1 viscosity, bit 2 resistivity, bit 4
-// anisotropic or saturated conduction (which need the B and rho fields).
+// The half step at one ring-box cell (ghosted-box index cl), whose
+// first-order divergences the first-order stage formed in every direction
+// (its EXT range).  L1: the first-order divergences (global order), L1_x
+// gains L_P^n in 2-D and 3-D; LP: L_P^n per scratch cell, 7 planes of R
+// (momentum, energy, B); Wh: the half-step fields (par_plane, par_fplane).
+// TM: bit 1 viscosity, bit 2 resistivity, bit 4 anisotropic or saturated
+// conduction (which need the B and rho fields).
 template <class R, int TM>
-__global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, const R *Vs, R *L1, R *LP,
-                                                    double *Wh, const R *PiF)
+__device__ __forceinline__ void par_half_cell(const StepArgs &a, const DevPatch &P, int cl, R *L1, R *LP, double *Wh,
+                                              const R *PiF)
 {
-    const Where w = locate(gt);
-    const DevPatch P = a.patches[w.patch];
-    const int t = w.b * BLOCK + threadIdx.x;
-    if (t >= par_ring_cells(P.n, a.ndim)) return;
-    const int e0 = P.n[0] + 2, e1 = a.ndim > 1 ? P.n[1] + 2 : 1;
-    int x[3];
-    x[0] = t % e0 - 1;
-    x[1] = (t / e0) % e1 - (a.ndim > 1 ? 1 : 0);
-    x[2] = t / (e0 * e1) - (a.ndim > 2 ? 1 : 0);
-    const int cl = lcell(P, x[0], x[1], x[2]);
     const long long S = a.sstride;
     const long long c = P.soff + cl;
     // L_P^n from the face pass over the primitive fields of U^n (T = p / rho)
@@ -393,6 +403,23 @@ __global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, c
             }
         }
     }
+}
+
+// k_par_half: the ring box (par_ring_cells), a thread PAR_ZR cells along z.
+template <class R, int TM>
+__global__ void __launch_bounds__(BLOCK) k_par_half(StepArgs a, GroupTable gt, R *L1, R *LP, double *Wh,
+                                                    const R *PiF)
+{
+    const Where w = locate(gt);
+    const DevPatch P = a.patches[w.patch];
+    const int t = w.b * BLOCK + threadIdx.x;
+    if (t >= par_ring_threads(P.n, a.ndim)) return;
+    const int e0 = P.n[0] + 2, e1 = a.ndim > 1 ? P.n[1] + 2 : 1, e2 = a.ndim > 2 ? P.n[2] + 2 : 1;
+    const int x0 = t % e0 - 1, x1 = (t / e0) % e1 - (a.ndim > 1 ? 1 : 0);
+    const int z0 = (t / (e0 * e1)) * PAR_ZR;  // this thread's planes z0 .. z0 + PAR_ZR - 1 of the box
+#pragma unroll 1
+    for (int r = 0; r < PAR_ZR && z0 + r < e2; ++r)
+        par_half_cell<R, TM>(a, P, lcell(P, x0, x1, z0 + r - (a.ndim > 2 ? 1 : 0)), L1, LP, Wh, PiF);
 }
 
 // L_P^(n+1/2) on the interior cells (the k_maxspeed tiling) from the face
