@@ -96,7 +96,7 @@ static bool grid_fits(const std::vector<Group> &gs, int ndim)
     long long tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (const Group &G : gs) {
         const long long c = G.count;
-        tot[0] += c * Tiles::prim(G.N);
+        tot[0] += c * Tiles::ghosted(G.N);
         for (int D = 0; D < 3; ++D) {
             // (one row per thread: the most blocks the x kernels launch)
             tot[1 + D] += c * Tiles::div1(G.n, ndim, D, G.xw, G.seg, true, 1);

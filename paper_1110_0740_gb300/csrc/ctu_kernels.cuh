@@ -130,6 +130,11 @@ constexpr int BLOCK = 128;
 #ifndef CTU_SWEEPX_ROWS
 #define CTU_SWEEPX_ROWS 8
 #endif
+#ifndef CTU_PRIM_CELLS
+#define CTU_PRIM_CELLS 4
+#endif
+// cells each thread of k_prim takes in turn, BLOCK apart
+constexpr int PRIM_CELLS = CTU_PRIM_CELLS;
 // Rows each thread of the first-order x stage and of the x sweep takes in
 // turn, so that the per-thread set-up (tile decode, patch and window look-up,
 // the block reductions) is shared: up to `most` (per launch: the most that
@@ -798,14 +803,17 @@ struct Tiles {
     static int xw(int nx) { return tile_xw(nx); }
     static long long prim(const int *N)
     {
-        return ((long long)N[0] * N[1] * N[2] + BLOCK - 1) / BLOCK;
+        return ((long long)N[0] * N[1] * N[2] + BLOCK * PRIM_CELLS - 1) / (BLOCK * PRIM_CELLS);
     }
+    // one thread per ghosted cell (the shock flags)
+    static long long ghosted(const int *N) { return ((long long)N[0] * N[1] * N[2] + BLOCK - 1) / BLOCK; }
     // k_prim<..., TRIM>: on small patches (prim_trimmed) the ghosted box
     // without its outermost layer on active axes (N > 1 there)
     static long long prim_trim(const int *N)
     {
         if (!prim_trimmed(N)) return prim(N);
-        return ((long long)(N[0] - 2) * (N[1] > 1 ? N[1] - 2 : 1) * (N[2] > 1 ? N[2] - 2 : 1) + BLOCK - 1) / BLOCK;
+        return ((long long)(N[0] - 2) * (N[1] > 1 ? N[1] - 2 : 1) * (N[2] > 1 ? N[2] - 2 : 1) + BLOCK * PRIM_CELLS - 1) /
+               (BLOCK * PRIM_CELLS);
     }
     // ext: along D also the ring's layers -1 and n_D (k_div1's EXT)
     // rows per thread of k_div1<0> and of k_sweep_x on patches of n cells,
@@ -889,24 +897,28 @@ __global__ void __launch_bounds__(BLOCK) k_prim(StepArgs a, GroupTable gt, R *Vs
 {
     const Where w = locate(gt);
     const DevPatch P = a.patches[w.patch];
-    int c = w.b * BLOCK + threadIdx.x;
-    if (TRIM && prim_trimmed(P.N)) {
-        // box of the ghosted patch without its outermost layer on active axes
-        const int m0 = P.N[0] - 2, m1 = P.g[1] ? P.N[1] - 2 : 1, m2 = P.g[2] ? P.N[2] - 2 : 1;
-        if (c >= m0 * m1 * m2) return;
-        const int x = c % m0 + 1, y = (c / m0) % m1 + (P.g[1] ? 1 : 0), z = c / (m0 * m1) + (P.g[2] ? 1 : 0);
-        c = (z * P.N[1] + y) * P.N[0] + x;
-    } else {
-        if (c >= P.N[0] * P.N[1] * P.N[2]) return;
+    const bool trim = TRIM && prim_trimmed(P.N);
+    // box of the ghosted patch without its outermost layer on active axes
+    const int m0 = P.N[0] - 2, m1 = P.g[1] ? P.N[1] - 2 : 1, m2 = P.g[2] ? P.N[2] - 2 : 1;
+    const int ncell = trim ? m0 * m1 * m2 : P.N[0] * P.N[1] * P.N[2];
+    unsigned int f = 0;
+#pragma unroll 1
+    for (int r = 0; r < PRIM_CELLS; ++r) {
+        int c = (w.b * PRIM_CELLS + r) * BLOCK + threadIdx.x;
+        if (c >= ncell) break;
+        if (trim) {
+            const int x = c % m0 + 1, y = (c / m0) % m1 + (P.g[1] ? 1 : 0), z = c / (m0 * m1) + (P.g[2] ? 1 : 0);
+            c = (z * P.N[1] + y) * P.N[0] + x;
+        }
+        double U[NV];
+        R V[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) U[q] = a.U[q * a.ustride + P.base + c];
+        f |= prim_any<PHYS, R, LIT64>(U, a, V);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) Vs[q * a.sstride + P.soff + c] = V[q];
     }
-    double U[NV];
-    R V[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) U[q] = a.U[q * a.ustride + P.base + c];
-    const unsigned int f = prim_any<PHYS, R, LIT64>(U, a, V);
     if (f) atomicOr(a.status, f);
-#pragma unroll
-    for (int q = 0; q < NV; ++q) Vs[q * a.sstride + P.soff + c] = V[q];
 }
 
 // ---- hybrid integration: shock flags (appendix on shock detection) ----

@@ -143,10 +143,10 @@ static int launch_step_t(const StepArgs &a, const LaunchInfo &li, cudaStream_t s
     if constexpr (recon_hybrid(PPM)) {  // shock flags of the hybrid integration
         CTU_MARK("shock");
         n += over_groups(
-            li, [&](const Group &G) { return Tiles::prim(G.N); },
+            li, [&](const Group &G) { return Tiles::ghosted(G.N); },
             [&](const GroupTable &gt, unsigned nb) { k_shock<R><<<nb, BLOCK, 0, s>>>(a, gt, Vs); });
         n += over_groups(
-            li, [&](const Group &G) { return Tiles::prim(G.N); },
+            li, [&](const Group &G) { return Tiles::ghosted(G.N); },
             [&](const GroupTable &gt, unsigned nb) {
                 k_minmod<<<nb, BLOCK, 0, s>>>(a, gt, PPM == RECON_PPM_HYB ? 2 : 1);
             });
