@@ -122,13 +122,16 @@ constexpr int BLOCK = 128;
 #define CTU_MARCH_MINB 3
 #endif
 #ifndef CTU_SWEEPX_MINB
-#define CTU_SWEEPX_MINB 5
+#define CTU_SWEEPX_MINB 6
+#endif
+#ifndef CTU_SWEEPX_MINB_PAR
+#define CTU_SWEEPX_MINB_PAR 5
 #endif
 #ifndef CTU_DIV1X_ROWS
-#define CTU_DIV1X_ROWS 8
+#define CTU_DIV1X_ROWS 16
 #endif
 #ifndef CTU_SWEEPX_ROWS
-#define CTU_SWEEPX_ROWS 8
+#define CTU_SWEEPX_ROWS 16
 #endif
 #ifndef CTU_PRIM_CELLS
 #define CTU_PRIM_CELLS 4
@@ -225,7 +228,8 @@ __device__ __forceinline__ Where locate(const GroupTable &gt)
 }
 // The marching sweeps are latency bound: they are compiled for at least
 // CTU_MARCH_MINB resident blocks per SM (register cap 65536 / (BLOCK * MINB)),
-// the float x sweep for CTU_SWEEPX_MINB.
+// the float x sweep for CTU_SWEEPX_MINB (CTU_SWEEPX_MINB_PAR with the
+// parabolic terms, whose staging needs the registers of one block fewer).
 
 // Local component q of a sweep along D reads global component gperm<D>(q).
 template <int D> __host__ __device__ constexpr int gperm(int q)
@@ -1282,7 +1286,8 @@ __global__ void __launch_bounds__(BLOCK) k_pred(StepArgs a, GroupTable gt, const
 // next step's CFL speed.  With the parabolic terms the update also adds
 // dt L_P^(n+1/2) (k_par_lp), and the CFL rate gains the diffusion term.
 template <int PHYS, class R, int PPM, int IFACE64, int LAST>
-__global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? CTU_SWEEPX_MINB : 1) k_sweep_x(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *A)
+__global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? (recon_par(PPM) ? CTU_SWEEPX_MINB_PAR : CTU_SWEEPX_MINB) : 1)
+    k_sweep_x(StepArgs a, GroupTable gt, const R *Vs, const R *L1, R *A)
 {
     const Where wh = locate(gt);
     const int patch = wh.patch;
