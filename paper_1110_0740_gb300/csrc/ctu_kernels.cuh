@@ -361,13 +361,17 @@ __device__ __forceinline__ unsigned int prim_of<double>(const double (&U)[NV], c
 template <>
 __device__ __forceinline__ unsigned int prim_of<float>(const double (&U)[NV], const StepArgs &a, float (&V)[NV])
 {
+    // each component split once: its float value and, for the first 8, the
+    // double-float pressure
+    df u[8];
     float r[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-        const df s = df_split(U[q]);
-        r[q] = s.hi + s.lo;
+        const df sq = df_split(U[q]);
+        if (q < 8) u[q] = sq;
+        r[q] = sq.hi + sq.lo;
     }
-    const float p = df_pressure(U, a.gm1f);
+    const float p = df_pressure_split(u, a.gm1f);
     const float ir = 1.0f / r[0];
     V[0] = r[0]; V[1] = r[1] * ir; V[2] = r[2] * ir; V[3] = r[3] * ir; V[4] = p;
     V[5] = r[5]; V[6] = r[6]; V[7] = r[7]; V[8] = r[8];

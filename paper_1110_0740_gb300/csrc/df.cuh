@@ -142,18 +142,20 @@ __device__ __forceinline__ df df_scale(df x, float s)  // s a power of two or ex
 
 // Pressure of a float64 MHD state, p = (Gamma-1)(E - m^2/(2 rho) - B^2/2),
 // in double-float: ~2^-44 relative to E, i.e. float32-exact p even when E
-// exceeds p by many orders of magnitude.
-__device__ __forceinline__ float df_pressure(const double (&U)[9], float gm1)
+// exceeds p by many orders of magnitude.  u: the state's first 8 components
+// split (df_split).
+__device__ __forceinline__ float df_pressure_split(const df (&u)[8], float gm1)
 {
-    const df rho = df_split(U[0]);
-    const df mx = df_split(U[1]), my = df_split(U[2]), mz = df_split(U[3]);
-    const df E = df_split(U[4]);
-    const df bx = df_split(U[5]), by = df_split(U[6]), bz = df_split(U[7]);
+    const df rho = u[0];
+    const df mx = u[1], my = u[2], mz = u[3];
+    const df E = u[4];
+    const df bx = u[5], by = u[6], bz = u[7];
     const df m2 = df_add(df_add(df_sqr(mx), df_sqr(my)), df_sqr(mz));
     const df b2 = df_add(df_add(df_sqr(bx), df_sqr(by)), df_sqr(bz));
     const df ke = df_scale(df_div(m2, rho), 0.5f);
     const df eint = df_add(df_add(E, df_neg(ke)), df_neg(df_scale(b2, 0.5f)));
     return gm1 * (eint.hi + eint.lo);
 }
+
 
 } // namespace ctu
