@@ -9,8 +9,9 @@
 //   k_div1<D>      first-order Godunov fluxes F^n_D = R(U_c, U_c+e_D) and
 //                  their divergences L1_D (the transverse terms)
 //   k_sweep_x      direction x: normal predictor + transverse correction,
-//                  n+1/2 Riemann problems and L_x, one thread per traced cell,
-//                  interface states exchanged through shared memory
+//                  n+1/2 Riemann problems and L_x, one thread per traced cell
+//                  of several rows in turn, interface states exchanged
+//                  through shared memory
 //   k_sweep_m<D>   directions y, z: the same, one thread per pencil segment
 //                  marching along D with the 5-cell stencil in registers
 // The last sweep of the step adds U^n + dt (L_x + L_y + L_z), applies the
@@ -890,7 +891,8 @@ static __global__ void k_setup(const double *dtch, StepParams *sp)
 }
 
 // V = V(U) on every ghosted cell (a flat range of the patch region);
-// one block per BLOCK cells of a patch.  LIT64: float64 pressure recovery in
+// one block per BLOCK x PRIM_CELLS cells of a patch, a thread PRIM_CELLS
+// cells BLOCK apart.  LIT64: float64 pressure recovery in
 // the float kernels (CTU_MIXED_IFACE64).
 // TRIM: on patches whose ghosted rows are at most PRIM_TRIM_MAXN cells long,
 // only the cells within three ghost layers of the interior (the stencils of
@@ -1053,8 +1055,9 @@ static __global__ void __launch_bounds__(BLOCK) k_minmod(StepArgs a, GroupTable 
 // sweeps of the other directions trace: c_D in [0, n_D), the other active
 // coordinates in [-1, n]; with EXT (the parabolic terms' half-step state)
 // c_D in [-1, n_D] as well, the whole ring box.
-//   D = x: one thread per face; a tile of xw lanes along x yields xw - 1
-//          cells, the lower face of a cell arriving from the previous lane.
+//   D = x: one thread per face of several rows in turn (Tiles::div1x_rows);
+//          a tile of xw lanes along x yields xw - 1 cells, the lower face of
+//          a cell arriving from the previous lane.
 //   D = y, z: one thread per segment of SEG cells marching along D with the
 //          previous face flux and cell state in registers.
 template <int PHYS, class R, int D, bool HYB = false, bool HLLC = false, bool EXT = false>
