@@ -121,6 +121,7 @@ struct ctu_ctx {
     void *optab[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     size_t opcap[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int device = 0;
+    int sms = 152;  // streaming multiprocessors of the device
     // patch list cache (caller order) and its device table (grouped order)
     std::vector<ctu_patch> hpatch;
     std::vector<int> sorted_of;  // caller index -> device-table index
@@ -466,6 +467,7 @@ static LaunchInfo make_info(const ctu_ctx *ctx)
     li.scratch = ctx->scratch;
     li.sp = ctx->dsp;
     li.prof = ctx->prof;
+    li.sms = ctx->sms;
     return li;
 }
 
@@ -576,6 +578,7 @@ ctu_status ctu_init(const ctu_config *cfg, ctu_ctx **out)
     if (!ctx) return CTU_ENOMEM;
     ctx->cfg = *cfg;
     if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess ||
         cudaMalloc(&ctx->dstatus, sizeof(unsigned int)) != cudaSuccess ||
         cudaMalloc(&ctx->dmax, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&ctx->dfloor, sizeof(unsigned long long)) != cudaSuccess ||

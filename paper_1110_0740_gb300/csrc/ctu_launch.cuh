@@ -54,7 +54,8 @@ static int over_groups(const LaunchInfo &li, BPP bpp, GO go, XR xr = XR())
 
 // Rows per thread of an x-tiled kernel for a launch (Tiles::div1x_rows,
 // sweepx_rows): the largest power of two up to `most` at which the launch
-// still has at least CTU_ROW_WAVES (8) waves of blocks (152 SMs x 5), so that the longer
+// still has at least CTU_ROW_WAVES (8) waves of blocks (the device's SMs x 5
+// resident blocks), so that the longer
 // blocks leave no long tail on a small batch.  blocks(G, x): blocks of one
 // patch of group G at x rows per thread.
 #ifndef CTU_ROW_WAVES
@@ -65,7 +66,7 @@ template <class BLK> static int launch_rows(const LaunchInfo &li, int most, BLK 
     for (int x = most; x > 1; x /= 2) {
         long long tot = 0;
         for (int g = 0; g < li.ngroups; ++g) tot += (long long)li.groups[g].count * blocks(li.groups[g], x);
-        if (tot >= (long long)CTU_ROW_WAVES * 152 * 5) return x;
+        if (tot >= (long long)CTU_ROW_WAVES * (li.sms > 0 ? li.sms : 152) * 5) return x;
     }
     return 1;
 }

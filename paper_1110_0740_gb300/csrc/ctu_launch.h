@@ -36,6 +36,7 @@ struct LaunchInfo {
     void *scratch;         // SCRATCH_ARRAYS * sstride elements of R
     StepParams *sp;        // device per-step parameters
     ProfHook *prof;        // may be null
+    int sms;               // streaming multiprocessors of the device (launch_rows)
 };
 
 // Enqueue one CTU step; returns the number of kernel launches.

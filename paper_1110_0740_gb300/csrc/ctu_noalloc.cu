@@ -194,6 +194,13 @@ extern "C" ctu_status ctu_step_noalloc(const ctu_config *cfg, const double *U_in
     li.scratch = scratch;
     li.sp = sp;
     li.prof = nullptr;
+    li.sms = 0;  // launch_rows takes 152
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            li.sms = sms;
+    }
     if (cfg->precision == CTU_FP64)
         launch_step<double>(a, li, s);
     else
