@@ -465,7 +465,12 @@ typedef struct {
  * total / volume.  With the registers bound as stated (coarse -1, fine +1)
  * the total is dt (the space-time average fine flux minus the coarse flux)
  * times the face area.  A cell beside several interfaces gets every
- * correction (atomic float64 adds, so their order is not fixed). */
+ * correction, in a fixed order: the sets run by class, direction 0..ndim-1
+ * and within it side -1 then +1 (one launch each), so the result is
+ * reproducible bit for bit and does not depend on the order of `sets`.  The
+ * sets of one class reach disjoint cells when the fine patches are disjoint;
+ * sets that do share a cell within a class still all land (atomic float64
+ * adds), in an order that is then not fixed. */
 ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *reg,
                       const ctu_reflux_set *sets, int nset, void *stream);
 

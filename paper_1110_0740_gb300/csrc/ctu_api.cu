@@ -951,13 +951,15 @@ ctu_status ctu_prolong(ctu_ctx *ctx, const double *Uc_old, const double *Uc_new,
     for (int i = 0; i < nbox; ++i) {
         long long c = 0;
         if (!box_ok(ctx, boxes[i], cstride, fstride, true, &c)) return CTU_EINVAL;
-        // one thread per coarse cell under the box
+        // one thread per variable and coarse cell under the box, indexed in
+        // 32 bits
         long long cc = c > 0 ? 1 : 0;
         for (int d = 0; d < ctx->cfg.ndim && cc; ++d) {
             const ctu_level_box &B = boxes[i];
             cc *= floordiv_h(B.hi[d] - 1, B.ratio) + 1 - floordiv_h(B.lo[d], B.ratio);
         }
-        blocks[i] = (cc + AMR_BLOCK - 1) / AMR_BLOCK;
+        if (9 * cc >= (1LL << 31)) return CTU_EINVAL;
+        blocks[i] = (9 * cc + AMR_BLOCK - 1) / AMR_BLOCK;
     }
     cudaStream_t s = (cudaStream_t)stream;
     OpTable T;
@@ -985,6 +987,8 @@ ctu_status ctu_restrict(ctu_ctx *ctx, double *Uc, int64_t cstride, const double 
     for (int i = 0; i < nbox; ++i) {
         long long c = 0;
         if (!box_ok(ctx, boxes[i], cstride, fstride, false, &c)) return CTU_EINVAL;
+        // one thread per coarse cell, indexed in 32 bits
+        if (c >= (1LL << 31)) return CTU_EINVAL;
         blocks[i] = (c + AMR_BLOCK - 1) / AMR_BLOCK;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -1005,9 +1009,15 @@ ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *r
 {
     if (!ctx || !Uc || !reg || !sets || nset <= 0 || nset > 65535) return CTU_EINVAL;
     const int ndim = ctx->cfg.ndim;
+    // sets ordered by class (direction, then side), one launch per class
+    auto cls = [](const ctu_reflux_set &S) { return 2 * S.dir + (S.side > 0 ? 1 : 0); };
+    std::vector<ctu_reflux_set> ord(sets, sets + nset);
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](const ctu_reflux_set &x, const ctu_reflux_set &y) { return cls(x) < cls(y); });
     std::vector<long long> blocks(nset);
+    long long cblk[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int i = 0; i < nset; ++i) {
-        const ctu_reflux_set &S = sets[i];
+        const ctu_reflux_set &S = ord[i];
         long long cc = 0;
         if (!patch_extent(ctx, S.cn, &cc) || S.cbase < 0 || S.cbase + cc > cstride) return CTU_EINVAL;
         if (S.dir < 0 || S.dir >= ndim || (S.side != 1 && S.side != -1) || S.ratio < 1) return CTU_EINVAL;
@@ -1022,15 +1032,25 @@ ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *r
             return CTU_EINVAL;
         for (int d = 0; d < ndim; ++d)
             if (!(S.dx[d] > 0.0)) return CTU_EINVAL;
-        blocks[i] = ((long long)(S.a1 - S.a0) * (S.b1 - S.b0) + AMR_BLOCK - 1) / AMR_BLOCK;
+        // one thread per variable and coarse face, indexed in 32 bits
+        const long long nf = 9LL * (S.a1 - S.a0) * (S.b1 - S.b0);
+        if (nf >= (1LL << 31)) return CTU_EINVAL;
+        blocks[i] = (nf + AMR_BLOCK - 1) / AMR_BLOCK;
+        cblk[cls(S) + 1] += blocks[i];
     }
     cudaStream_t s = (cudaStream_t)stream;
     OpTable T;
-    ctu_status st = op_table(ctx, 2, sets, sizeof(ctu_reflux_set) * nset, nset, blocks.data(), s, &T);
+    ctu_status st = op_table(ctx, 2, ord.data(), sizeof(ctu_reflux_set) * nset, nset, blocks.data(), s, &T);
     if (st != CTU_OK) return st;
     if (T.nblocks == 0) return CTU_OK;
     if (ctx->prof) ctx->prof->mark("reflux", s);
-    k_reflux<<<T.nblocks, AMR_BLOCK, 0, s>>>((const ctu_reflux_set *)T.desc, T.map, ndim, Uc, cstride, reg);
+    long long b0 = 0;
+    for (int c = 0; c < 6; ++c) {
+        if (cblk[c + 1] > 0)
+            k_reflux<<<(unsigned)cblk[c + 1], AMR_BLOCK, 0, s>>>((const ctu_reflux_set *)T.desc, T.map, (unsigned)b0,
+                                                               ndim, Uc, cstride, reg);
+        b0 += cblk[c + 1];
+    }
     if (ctx->prof) ctx->prof->mark(nullptr, s);
     CTU_CUDA(cudaGetLastError());
     return CTU_OK;
