@@ -516,8 +516,9 @@ def run_amr(args):
     calls captured in one CUDA graph; flux-register windows on both sides of
     every coarse-fine interface; on one GPU, before every level step the
     ghosts are filled (prolongation from the parent level in time, then the
-    same-level exchange from siblings) and at every synchronisation the
-    parent is refluxed and restricted.  dt_0 is fixed before timing from ctu_dt on
+    same-level exchange from siblings), so is every new state that a finer
+    level prolongs from, and at every synchronisation the parent is
+    refluxed and restricted.  dt_0 is fixed before timing from ctu_dt on
     every level (dt_0 = min_l 2^l dt_l).  With N > 1 ranks every rank builds
     the same hierarchy and advances its shard of each level (patches split by
     cell count, Section 4); the ranks agree on dt_0 (one scalar reduction) and
@@ -670,15 +671,23 @@ def run_amr(args):
         exchange(lev, fine)
 
     def coarse_step():
-        # recursive subcycling: l0, then for each l1 substep its two l2 substeps
+        # recursive subcycling: l0, then for each l1 substep its two l2
+        # substeps.  A level's new state gets its ghosts at the new time
+        # before the next finer level prolongs from it in time (the
+        # prolongation's slopes reach into the parent's ghost cells), so that
+        # no ghost cell read in a coarse step is left over from the previous one
         if ops:
             exchange(0, A[0])
         lstep(0, A[0], B[0])
+        if ops:
+            exchange(0, B[0])
         for k in range(2):
             s1, d1 = (A[1], B[1]) if k == 0 else (B[1], A[1])
             if ops:
                 ghosts(1, A[0], B[0], k / 2, s1)
             lstep(1, s1, d1)
+            if ops:
+                ghosts(1, A[0], B[0], (k + 1) / 2, d1)
             for m in range(2):
                 s2, d2 = (A[2], B[2]) if m == 0 else (B[2], A[2])
                 if ops:
@@ -775,40 +784,83 @@ def run_amr(args):
                "seconds": el}
     # end to end through the public API with host buffers: every coarse step
     # copies every level's ghosted pool from pinned host memory, replays the
-    # captured coarse step and reads every level's result pool back
+    # captured coarse step and reads every level's result pool back.  The
+    # captured step works on fixed pools (its outputs land in some of its
+    # input pools), so each step's host copies go through two device staging
+    # sets on their own streams: the input of step k + 1 arrives while step k
+    # computes, and the result of step k - 1 leaves meanwhile; the compute
+    # stream moves staging -> pools before the replay and pools -> staging
+    # after it (device copies)
     e2e = None
     if world == 1 and not args.skip_e2e:
         Hin = [torch.from_numpy(lv["pool"]).pin_memory() for lv in L]
         outs = [B[0], A[1], A[2]]  # where the coarse step leaves each level
-        Hout = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+        Hout = [[torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs] for _ in range(2)]
+        Ist = [[torch.empty_like(A[lev]) for lev in range(len(L))] for _ in range(2)]
+        Ost = [[torch.empty_like(o) for o in outs] for _ in range(2)]
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_used = [torch.cuda.Event() for _ in range(2)]
+        ev_cmp = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
 
-        def e2e_step():
+        def pipeline(K):
+            for k in range(K):
+                b = k % 2
+                if k >= 2:
+                    s_in.wait_event(ev_used[b])  # step k - 2 has taken staging input b
+                with torch.cuda.stream(s_in):
+                    for lev in range(len(L)):
+                        Ist[b][lev].copy_(Hin[lev], non_blocking=True)
+                    ev_in[b].record(s_in)
+                stream.wait_event(ev_in[b])
+                with torch.cuda.stream(stream):
+                    for lev in range(len(L)):
+                        A[lev].copy_(Ist[b][lev], non_blocking=True)
+                    ev_used[b].record(stream)
+                    g.replay()
+                    if k >= 2:
+                        stream.wait_event(ev_out[b])  # staging result b has been read back
+                    for lev in range(len(L)):
+                        Ost[b][lev].copy_(outs[lev], non_blocking=True)
+                    ev_cmp[b].record(stream)
+                s_out.wait_event(ev_cmp[b])
+                with torch.cuda.stream(s_out):
+                    for lev in range(len(L)):
+                        Hout[b][lev].copy_(Ost[b][lev], non_blocking=True)
+                    ev_out[b].record(s_out)
+
+        pipeline(2)
+        barrier()
+        E = max(4, args.steps)
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record(s_in)
+        pipeline(E)
+        t1e.record(s_out)
+        barrier()
+        ems = t0e.elapsed_time(t1e) / E
+        # the streamed result is the device step's, bit for bit: one more
+        # replay from the same input, in place (the coarse step reads no state
+        # left by an earlier one, and the reflux sums in a fixed order)
+        with torch.cuda.stream(stream):
             for lev in range(len(L)):
                 A[lev].copy_(Hin[lev], non_blocking=True)
             g.replay()
-            for lev in range(len(L)):
-                Hout[lev].copy_(outs[lev], non_blocking=True)
-
-        with torch.cuda.stream(stream):
-            e2e_step()
-        barrier()
-        E = max(3, args.steps)
-        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            t0e.record(stream)
-            for _ in range(E):
-                e2e_step()
-            t1e.record(stream)
-        barrier()
-        ems = t0e.elapsed_time(t1e) / E
+        torch.cuda.synchronize()
+        for lev in range(len(L)):
+            assert torch.equal(Hout[(E - 1) % 2][lev], outs[lev].cpu()), f"level {lev}"
         e2e = {"value": upd / (ems * 1e-3), "unit": "cell-updates/s",
                "h2d_bytes_per_step": int(sum(h.numel() * 8 for h in Hin)),
-               "d2h_bytes_per_step": int(sum(h.numel() * 8 for h in Hout)),
+               "d2h_bytes_per_step": int(sum(h.numel() * 8 for h in Hout[0])),
                "ms_per_step": ems, "steps": E,
-               "overlap": "none: pools in, captured coarse step, pools out, in order on one stream"}
+               "overlap": "two device staging sets; every level's pool in, and the previous step's pools "
+                          "out, on their own streams while the captured coarse step runs; staging <-> pools "
+                          "by device copies on the compute stream"}
     launches = sum(c.launches() for c in ctxs[:1]) + 2 * ctxs[1].launches() + 4 * ctxs[2].launches()
-    if ops:  # prolongations 2 + 4, refluxes and restrictions 2 + 1 each, exchanges 1 + 2 + 4
-        launches += 6 + 3 + 3 + sum(2 ** lev for lev in xch)
+    if ops:  # prolongations 4 + 4, restrictions 2 + 1, exchanges 2 + 4 + 4 (levels 0, 1, 2),
+        # refluxes 2 + 1 (one launch per class of sets: direction and side)
+        ncls = {lev: len({(S.dir, S.side) for S in ops[lev][2]}) for lev in ops}
+        launches += 8 + 3 + 2 * ncls[2] + ncls[1] + sum((2, 4, 4)[lev] for lev in xch)
     if rank == 0:
         line = {"metric": METRIC, "value": upd / (ms * 1e-3), "unit": "cell-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
