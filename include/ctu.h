@@ -407,7 +407,9 @@ ctu_status ctu_tile_params(ctu_ctx *ctx, const int n[3], int *xw, int *seg);
  * contents (that call synchronises the stream: make it before any capture;
  * later calls with identical descriptors enqueue kernels only).  Returns
  * CTU_EINVAL, on the host, for a descriptor that would reach outside a
- * patch's ghosted region. */
+ * patch's ghosted region, and for a box whose kernel threads reach 2^31
+ * (ctu_prolong: 9 per coarse cell under the box; ctu_restrict: one per
+ * coarse cell). */
 typedef struct {
     int fn[3];        /* interior cells of the fine patch (1 on inactive dimensions) */
     int cn[3];        /* interior cells of the coarse patch */
@@ -470,7 +472,8 @@ typedef struct {
  * reproducible bit for bit and does not depend on the order of `sets`.  The
  * sets of one class reach disjoint cells when the fine patches are disjoint;
  * sets that do share a cell within a class still all land (atomic float64
- * adds), in an order that is then not fixed. */
+ * adds), in an order that is then not fixed.  CTU_EINVAL for a set whose
+ * 9 x faces reach 2^31. */
 ctu_status ctu_reflux(ctu_ctx *ctx, double *Uc, int64_t cstride, const double *reg,
                       const ctu_reflux_set *sets, int nset, void *stream);
 
