@@ -542,60 +542,18 @@ def run_amr(args):
     for lv in L:
         cells_l = [n[0] * n[1] * n[2] for (n, _, _, _) in lv["patches"]]
         mine.append(shard.partition(cells_l, world)[rank])
-    loc = [{g: i for i, g in enumerate(m)} for m in mine]
-    # flux-register windows, per level context (local patch indices); a
-    # coarse window is kept by the rank that owns its parent patch
-    wins = [[] for _ in L]
-    off = 0
-    fine_dst = [dict() for _ in L]      # (patch, dir, plane) -> register offset of a fine window
-    coarse_dst = [dict() for _ in L]    # (fine patch, dir, side) -> offset of its coarse window
-    reg_range = [None for _ in L]       # registers of the interface (lev - 1, lev)
-    for lev in range(1, len(L)):
-        r0 = off
-        for gi in mine[lev]:
-            n = L[lev]["patches"][gi][0]
-            for d in range(3):
-                a_, b_ = [e for e in range(3) if e != d]
-                for plane in (0, n[d]):
-                    wins[lev].append((loc[lev][gi], d, plane, 0, n[a_], 0, n[b_], 1.0, off))
-                    fine_dst[lev][(gi, d, plane)] = off
-                    off += 9 * n[a_] * n[b_]
-        for fi, (parent, o_zyx, sz) in enumerate(L[lev]["footprints"]):
-            if parent not in loc[lev - 1]:
-                continue
-            o = [o_zyx[2], o_zyx[1], o_zyx[0]]
-            for d in range(3):
-                a_, b_ = [e for e in range(3) if e != d]
-                for side, plane in ((-1, o[d]), (+1, o[d] + sz)):
-                    wins[lev - 1].append((loc[lev - 1][parent], d, plane, o[a_], o[a_] + sz, o[b_],
-                                          o[b_] + sz, -1.0, off))
-                    coarse_dst[lev][(fi, d, side)] = off
-                    off += 9 * sz * sz
-        reg_range[lev] = (r0, off)
-    reg = torch.zeros(max(off, 1), dtype=torch.float64, device=dev)
-    ctxs, A, B, P, D = [], [], [], [], []
-    for lev, lv in enumerate(L):
-        c = ctu.Ctx(ctu.make_config(ndim=3, recon=ctu.CTU_PPM, precision=prec, cfl=0.3, kappa=args.kappa,
-                                    nu=args.nu, eta=args.eta, kappa_par=args.kappa_par, tc_phi=args.tc_phi))
-        pool = torch.from_numpy(lv["pool"]).to(dev)
-        A.append(pool)
-        B.append(pool.clone())
-        P.append(ctu.make_patches([lv["patches"][gi][:3] for gi in mine[lev]]) if mine[lev] else None)
-        if wins[lev]:
-            c.flux_registers(reg, wins[lev])
-        ctxs.append(c)
-    h = []
-    for lev, c in enumerate(ctxs):
-        if P[lev] is None:
-            continue
-        hd = torch.zeros(2, dtype=torch.float64, device=dev)
-        c.dt(A[lev], A[lev].shape[1], P[lev], hd)
-        h.append(hd.cpu().tolist()[0] * 2 ** lev)
+    # the hierarchy's coarse step: pools, flux-register windows, level-operator
+    # tables and the subcycled launch sequence (paper_1110_0740_gb300.amr_advance);
+    # the level operators run on one rank (the cross-rank exchange is host-tested)
+    from paper_1110_0740_gb300.amr_advance import LevelAdvance
     dx0 = L[0]["patches"][0][1][0]
-    dt0, ch = shard.agree_dt((min(h) if h else float("inf"), 0.0), 0.3, dx0,
-                             group=None if pg is None else pg.group.WORLD)
-    for lev in range(len(L)):
-        D.append(torch.tensor([dt0 / 2 ** lev, ch], dtype=torch.float64, device=dev))
+    adv = LevelAdvance(L, int(round(1.0 / dx0)), precision=prec, cfl=0.3, mine=mine,
+                       level_ops=world == 1 and not args.no_level_ops, device=dev, kappa=args.kappa,
+                       kappa_par=args.kappa_par, tc_phi=args.tc_phi, nu=args.nu, eta=args.eta)
+    ctxs, A, B, P, D = adv.ctxs, adv.A, adv.B, adv.P, adv.D
+    ops, xch, wins = adv.ops, adv.xch, adv.windows
+    dt0, ch = shard.agree_dt((adv.local_dt(), 0.0), 0.3, dx0, group=None if pg is None else pg.group.WORLD)
+    adv.set_dt(dt0, ch)
     stream = torch.cuda.Stream(device=dev)
     # tile width and marching segment per patch shape of each level
     tiles = {}
@@ -606,97 +564,8 @@ def run_amr(args):
                 tiles[f"l{lev}_{n[0]}^3"] = list(ctxs[lev].tile_params(n))
     torch.cuda.synchronize()
 
-    def lstep(lev, src, dst):
-        if P[lev] is not None:
-            ctxs[lev].step(src, dst, src.shape[1], P[lev], D[lev], stream=stream)
-
-    # level operators (Section 4), single rank: ghosts of every fine patch
-    # prolonged from its parent (time-interpolated) before each fine substep;
-    # at each synchronisation the parent level is refluxed, then restricted
-    # (reflux first, so that a correction landing on a covered coarse cell is
-    # overwritten by the restriction), and the interface registers zeroed
-    ops = None
-    xch, xunc = {}, {}
-    if world == 1 and not args.no_level_ops:
-        from paper_1110_0740_gb300 import exchange as X
-        # same-level ghost exchange: ghosts over a sibling's interior (or a
-        # periodic image of one) are copied from it, after the prolongation
-        for lev, lv in enumerate(L):
-            specs = [((o[2], o[1], o[0]), (sz_, sz_, sz_), p_[2]) for (o, sz_), p_ in zip(lv["origins"], lv["patches"])]
-            xb = X.plan(specs, [128 * 2 ** lev] * 3, [True] * 3, 3)
-            xunc[lev] = X.uncovered(xb, len(specs), [sp[1] for sp in specs], 3)
-            if xb:
-                xch[lev] = ctu.make_copy_boxes(xb)
-        ops = {}
-        for lev in range(1, len(L)):
-            pb, rb, fs = [], [], []
-            for fi, (n, dx, base, _) in enumerate(L[lev]["patches"]):
-                parent, o_zyx, sz = L[lev]["footprints"][fi]
-                cn, cdx, cbase, _ = L[lev - 1]["patches"][parent]
-                o = [o_zyx[2], o_zyx[1], o_zyx[0]]
-                # the ghost cells no sibling covers: the coarse-fine boundary
-                for lo_, hi_ in xunc[lev][fi]:
-                    pb.append(dict(fn=n, cn=cn, fbase=base, cbase=cbase, lo=lo_, hi=hi_, origin=o, ratio=2))
-                rb.append(dict(fn=n, cn=cn, fbase=base, cbase=cbase, lo=o, hi=[o[e] + sz for e in range(3)],
-                               origin=o, ratio=2))
-                for d in range(3):
-                    a_, b_ = [e for e in range(3) if e != d]
-                    for side, fplane in ((-1, 0), (+1, n[d])):
-                        cell = o[d] - 1 if side < 0 else o[d] + sz
-                        if not 0 <= cell < cn[d]:
-                            continue  # the coarse neighbour lies in another coarse patch
-                        fs.append(dict(cn=cn, dir=d, plane=o[d] if side < 0 else o[d] + sz, side=side,
-                                       cbase=cbase, dx=cdx, a0=o[a_], a1=o[a_] + sz, b0=o[b_], b1=o[b_] + sz,
-                                       creg=coarse_dst[lev][(fi, d, side)],
-                                       freg=fine_dst[lev][(fi, d, fplane)], fa0=0, fb0=0, fna=n[a_],
-                                       fnb=n[b_], ratio=2))
-            ops[lev] = (ctu.make_level_boxes(pb), ctu.make_level_boxes(rb), ctu.make_reflux_sets(fs))
-
-    def sync(lev, coarse_new, fine_latest):
-        """Reflux level lev - 1, restrict level lev into it, clear the registers."""
-        pb, rb, fs = ops[lev]
-        ctxs[lev - 1].reflux(coarse_new, coarse_new.shape[1], reg, fs, stream=stream)
-        ctxs[lev - 1].restrict(coarse_new, coarse_new.shape[1], fine_latest, fine_latest.shape[1], rb,
-                               stream=stream)
-        r0, r1 = reg_range[lev]
-        reg[r0:r1].zero_()
-
-    def exchange(lev, U):
-        if lev in xch:
-            ctxs[lev].copy(U, U.shape[1], U, U.shape[1], xch[lev], stream=stream)
-
-    def ghosts(lev, coarse_old, coarse_new, alpha, fine):
-        ctxs[lev].prolong(coarse_old, coarse_new, coarse_old.shape[1], alpha, fine, fine.shape[1], ops[lev][0],
-                          stream=stream)
-        exchange(lev, fine)
-
     def coarse_step():
-        # recursive subcycling: l0, then for each l1 substep its two l2
-        # substeps.  A level's new state gets its ghosts at the new time
-        # before the next finer level prolongs from it in time (the
-        # prolongation's slopes reach into the parent's ghost cells), so that
-        # no ghost cell read in a coarse step is left over from the previous one
-        if ops:
-            exchange(0, A[0])
-        lstep(0, A[0], B[0])
-        if ops:
-            exchange(0, B[0])
-        for k in range(2):
-            s1, d1 = (A[1], B[1]) if k == 0 else (B[1], A[1])
-            if ops:
-                ghosts(1, A[0], B[0], k / 2, s1)
-            lstep(1, s1, d1)
-            if ops:
-                ghosts(1, A[0], B[0], (k + 1) / 2, d1)
-            for m in range(2):
-                s2, d2 = (A[2], B[2]) if m == 0 else (B[2], A[2])
-                if ops:
-                    ghosts(2, s1, d1, m / 2, s2)
-                lstep(2, s2, d2)
-            if ops:
-                sync(2, d1, A[2])
-        if ops:
-            sync(1, B[0], A[1])
+        adv.coarse_step(stream)
 
     def barrier():
         if pg is not None:
@@ -794,7 +663,7 @@ def run_amr(args):
     e2e = None
     if world == 1 and not args.skip_e2e:
         Hin = [torch.from_numpy(lv["pool"]).pin_memory() for lv in L]
-        outs = [B[0], A[1], A[2]]  # where the coarse step leaves each level
+        outs = adv.outputs()  # where the coarse step leaves each level
         Hout = [[torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs] for _ in range(2)]
         Ist = [[torch.empty_like(A[lev]) for lev in range(len(L))] for _ in range(2)]
         Ost = [[torch.empty_like(o) for o in outs] for _ in range(2)]
@@ -856,11 +725,7 @@ def run_amr(args):
                "overlap": "two device staging sets; every level's pool in, and the previous step's pools "
                           "out, on their own streams while the captured coarse step runs; staging <-> pools "
                           "by device copies on the compute stream"}
-    launches = sum(c.launches() for c in ctxs[:1]) + 2 * ctxs[1].launches() + 4 * ctxs[2].launches()
-    if ops:  # prolongations 4 + 4, restrictions 2 + 1, exchanges 2 + 4 + 4 (levels 0, 1, 2),
-        # refluxes 2 + 1 (one launch per class of sets: direction and side)
-        ncls = {lev: len({(S.dir, S.side) for S in ops[lev][2]}) for lev in ops}
-        launches += 8 + 3 + 2 * ncls[2] + ncls[1] + sum((2, 4, 4)[lev] for lev in xch)
+    launches = adv.launches()
     if rank == 0:
         line = {"metric": METRIC, "value": upd / (ms * 1e-3), "unit": "cell-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,

@@ -310,6 +310,32 @@ def amr_hierarchy(seed=0, base=128, target=600, gamma=5.0 / 3.0):
         if best is None or abs(tot - target) < abs(best[0] - target):
             best = (tot, levels, parents)
     tot, levels, parents = best
+    return amr_levels(levels, parents, base, c, r0, gamma)
+
+
+def _smooth_prim(xc, yc, zc):
+    """A smooth state periodic on the unit cube: density 0.6 to 1.4, pressure
+    0.8 to 1.2, velocity of amplitude 0.4 and a solenoidal field of amplitude
+    0.3 (B_x(z), B_y(x), B_z(y)), psi = 0."""
+    t = 2.0 * np.pi
+    rho = 1.0 + 0.25 * np.sin(t * xc) * np.cos(t * yc) + 0.15 * np.sin(t * zc)
+    p = 1.0 + 0.2 * np.cos(t * (xc + yc))
+    z = np.zeros_like(rho)
+    return [rho, 0.4 * np.sin(t * yc), 0.4 * np.sin(t * zc), 0.4 * np.sin(t * xc), p,
+            0.3 * np.cos(t * zc), 0.3 * np.cos(t * xc), 0.3 * np.cos(t * yc), z]
+
+
+def amr_levels(levels, parents, base, center, radius, gamma=5.0 / 3.0, smooth=False):
+    """The level dicts of a hierarchy given its patches: levels[l] lists the
+    (origin (z, y, x), size) cubes of level l in its own cells (level l: base
+    x 2^l cells per side of the unit cube), parents[l][i] the index of patch
+    i's parent on level l - 1 (parents[0] empty).  Every patch is filled,
+    ghosts included, at its cell centres with the expanding spherical shock
+    of amr_hierarchy (centre `center`, radius `radius`), or with the smooth
+    periodic state of _smooth_prim when `smooth`.  Returns {"levels":
+    [{"patches", "pool", "origins", "footprints"}], "center", "radius"} as
+    amr_hierarchy does."""
+    c, r0 = center, radius
     out = {"levels": [], "center": c, "radius": r0}
     for lev, plist in enumerate(levels):
         h = 1.0 / (base * 2 ** lev)
@@ -320,7 +346,7 @@ def amr_hierarchy(seed=0, base=128, target=600, gamma=5.0 / 3.0):
             yc = (o[1] + g) * h
             zc = (o[0] + g) * h
             Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
-            U = ideal_cons(_shock_prim(X, Y, Z, c, r0, gamma), gamma)
+            U = ideal_cons(_smooth_prim(X, Y, Z) if smooth else _shock_prim(X, Y, Z, c, r0, gamma), gamma)
             specs.append(([s, s, s], [h, h, h], off, lev))
             chunks.append(U.reshape(9, -1))
             off += U[0].size
