@@ -48,8 +48,9 @@ class LevelPlan:
 
     levels, domain, mine: as for LevelAdvance.  After construction:
     windows[l] (the windows bound to level l's context, local patch indices),
-    fine_dst[l][(patch, dir, plane)] and coarse_dst[l][(fine patch, dir,
-    side)] (window offsets), reg_range[l] (the registers of interface
+    fine_dst[l][(patch, dir, plane)] (a fine window's offset),
+    coarse_dst[l][(fine patch, dir, side)] (the pieces of a coarse window,
+    see _windows), unmatched_faces, reg_range[l] (the registers of interface
     (l - 1, l)), nreg; with level_ops, xch[l] (exchange boxes) and ops[l] =
     (prolongation boxes, restriction boxes, reflux sets) for l >= 1."""
 
@@ -59,6 +60,8 @@ class LevelPlan:
         if mine is None:
             mine = [list(range(len(lv["patches"]))) for lv in levels]
         self.mine = mine
+        if level_ops and any(sorted(m) != list(range(len(lv["patches"]))) for m, lv in zip(mine, levels)):
+            raise ValueError("the level operators run on one rank: mine must hold every patch of every level")
         self._windows([{g: i for i, g in enumerate(m)} for m in mine], domain)
         self.ops = None
         self.xch = {}

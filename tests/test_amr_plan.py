@@ -137,6 +137,8 @@ def test_shards_keep_every_window_once(plan, levels):
                 parent = levels[lev]["footprints"][fi][0]
                 assert parent in m[lev - 1]  # kept by the rank that owns the parent
                 coarse_all.append((lev, fi, d, side))
+    with pytest.raises(ValueError):  # the level operators need every patch on one rank
+        LevelPlan(levels, BASE, mine=[mine[lev][0] for lev in range(len(levels))], level_ops=True)
     full_fine = [(lev, gi, d, pl) for lev in range(1, len(levels)) for (gi, d, pl) in plan.fine_dst[lev]]
     full_coarse = [(lev, fi, d, s) for lev in range(1, len(levels)) for (fi, d, s) in plan.coarse_dst[lev]]
     assert sorted(fine_all) == sorted(full_fine)
