@@ -346,3 +346,152 @@ def test_the_check_rejects_a_coarse_state_without_its_ghost_fill(plan):
     adv, _ = _mock(plan, NoNewStateFill)
     with pytest.raises(AssertionError, match="stale ghosts of B1"):
         adv.coarse_step(None)
+
+
+# ---------------------------------------------------------------- the coarse
+# step in the oracle: LevelAdvance's plan and launch sequence, every launch
+# carried out by the oracle's operators on float64 host pools
+
+
+class _RegArray:
+    """The flux registers as a host array, with the slice zeroing the
+    coarse step uses."""
+
+    def __init__(self, n):
+        self.arr = np.zeros(max(n, 1))
+
+    def __getitem__(self, sl):
+        arr = self.arr
+
+        class _Slice:
+            def zero_(self):
+                arr[sl] = 0.0
+        return _Slice()
+
+
+def _block(pool, base, n):
+    N = [v + 8 for v in n]
+    return pool[:, base:base + N[0] * N[1] * N[2]].reshape(9, N[2], N[1], N[0])
+
+
+class _OracleCtx:
+    """One level's context: ctu_step, ctu_prolong, ctu_copy, ctu_reflux and
+    ctu_restrict on host pools, each by the oracle's function of the same
+    equation, patch by patch and box by box."""
+
+    def __init__(self, windows, reg, par):
+        import oracle as O
+        self.O, self.reg, self.par = O, reg, par
+        self.win = {}
+        for (p, d, plane, a0, a1, b0, b1, wgt, off) in windows:
+            self.win.setdefault(p, []).append((d, plane, a0, a1, b0, b1, off, wgt))
+
+    def step(self, src, dst, stride, P, D, stream=None):
+        dt, ch = D
+        for i, p in enumerate(P):
+            n = list(p.n)
+            U = np.ascontiguousarray(_block(src, p.base, n))
+            R, bad = self.O.mhd_step(U, n, 3, list(p.dx), dt, ch, recon=1, windows=self.win.get(i, []),
+                                     reg=self.reg.arr, **self.par)
+            assert bad == 0
+            _block(dst, p.base, n)[:, 4:-4, 4:-4, 4:-4] = R[:, 4:-4, 4:-4, 4:-4]
+
+    def prolong(self, po, pn, cs, alpha, U, fs, boxes, stream=None):
+        for b in boxes:
+            cn, fn = list(b.cn), list(b.fn)
+            F = np.ascontiguousarray(_block(U, b.fbase, fn))
+            self.O.prolong(np.ascontiguousarray(_block(po, b.cbase, cn)), np.ascontiguousarray(_block(pn, b.cbase, cn)),
+                           cn, alpha, F, fn, list(b.lo), list(b.hi), list(b.origin), b.ratio, 3, b.phys)
+            _block(U, b.fbase, fn)[...] = F
+
+    def copy(self, d, ds, s, ss, boxes, stream=None):
+        self.O.copy_boxes(d, s, [dict(dn=list(b.dn), sn=list(b.sn), lo=list(b.lo), hi=list(b.hi),
+                                      shift=list(b.shift), dbase=b.dbase, sbase=b.sbase) for b in boxes], 3)
+
+    def reflux(self, U, cs, reg, sets, stream=None):
+        for S in sorted(sets, key=lambda S: (S.dir, S.side)):
+            cn = list(S.cn)
+            C = np.ascontiguousarray(_block(U, S.cbase, cn))
+            self.O.reflux(C, cn, list(S.dx), reg.arr, S.dir, S.plane, S.side, S.a0, S.a1, S.b0, S.b1, S.creg,
+                          S.freg, S.fa0, S.fb0, S.fna, S.fnb, S.ratio, 3)
+            _block(U, S.cbase, cn)[...] = C
+
+    def restrict(self, U, cs, F, fs, boxes, stream=None):
+        for b in boxes:
+            cn, fn = list(b.cn), list(b.fn)
+            C = np.ascontiguousarray(_block(U, b.cbase, cn))
+            self.O.restrict(C, cn, np.ascontiguousarray(_block(F, b.fbase, fn)), fn, list(b.lo), list(b.hi),
+                            list(b.origin), b.ratio, 3)
+            _block(U, b.cbase, cn)[...] = C
+
+
+def _oracle_coarse_step(levels, base, plan, par):
+    """Restrict the hierarchy (every covered coarse cell the mean of its
+    children), then take one coarse step; returns level 0's totals of
+    U_q x cell volume before and after, and the totals of |U_q| x volume."""
+    import oracle as O
+    from paper_1110_0740_gb300 import ctu
+    adv = LevelAdvance.__new__(LevelAdvance)
+    adv.nlev = len(levels)
+    adv.A = [lv["pool"].copy() for lv in levels]
+    adv.B = [a.copy() for a in adv.A]
+    adv.reg = _RegArray(plan.nreg)
+    adv.ctxs = [_OracleCtx(plan.windows[lev], adv.reg, par) for lev in range(len(levels))]
+    adv.P = [ctu.make_patches([p[:3] for p in lv["patches"]]) for lv in levels]
+    adv.ops, adv.xch, adv.reg_range = plan.ops, plan.xch, plan.reg_range
+    # dt_0 from Eq. Ca on every level, dt_l = dt_0 / 2^l, one c_h
+    dt0 = np.inf
+    for lev, lv in enumerate(levels):
+        for n, dx, b in (p[:3] for p in lv["patches"]):
+            U = np.ascontiguousarray(_block(lv["pool"], b, n))
+            rate = O.mhd_max_rate(U, n, 3, dx, **par) if par else O.mhd_max_speed(U, n, 3, dx)
+            dt0 = min(dt0, O.dt_ch(rate, dx, 3, 0.3)[0] * 2 ** lev)
+    ch = 0.3 * levels[0]["patches"][0][1][0] / dt0
+    adv.D = [(dt0 / 2 ** lev, ch) for lev in range(len(levels))]
+    for lev in (2, 1):
+        adv.ctxs[lev - 1].restrict(adv.A[lev - 1], 0, adv.A[lev], 0, plan.ops[lev][1])
+
+    def totals(pool):
+        tot, mag = np.zeros(9), np.zeros(9)
+        for n, dx, b in (p[:3] for p in levels[0]["patches"]):
+            U = _block(pool, b, n)[:, 4:-4, 4:-4, 4:-4]
+            tot += U.sum(axis=(1, 2, 3)) * dx[0] * dx[1] * dx[2]
+            mag += np.abs(U).sum(axis=(1, 2, 3)) * dx[0] * dx[1] * dx[2]
+        return tot, mag
+    tot0, mag = totals(adv.A[0])
+    adv.coarse_step(None)
+    tot1, _ = totals(adv.outputs()[0])
+    return tot0, tot1, mag
+
+
+@pytest.mark.parametrize("par", [{}, dict(kappa=0.002, nu=0.001, eta=0.001)])
+def test_the_oracle_conserves_through_the_plan(par):
+    """Eq. fluxcorr, Eq. addreflux, Eq. avgdown: the plan's registers, reflux
+    sets (the pieces across a parent boundary included) and launch sequence
+    keep the composite totals of a properly nested hierarchy to round-off,
+    the operators being the oracle's."""
+    levels = nested_levels()
+    tot0, tot1, mag = _oracle_coarse_step(levels, 32, LevelPlan(levels, 32), par)
+    assert np.all(np.abs(tot1 - tot0)[:8] <= 1e-13 * mag[:8]), (tot1 - tot0) / mag
+
+
+def test_without_the_pieces_across_a_parent_boundary_the_totals_drift():
+    """The same step with the reflux sets of the faces on a parent's boundary
+    left out (the former plan): the flux there stays uncorrected."""
+    from paper_1110_0740_gb300 import ctu
+    levels = nested_levels()
+    plan = LevelPlan(levels, 32)
+    for lev in (1, 2):
+        pb, rb, fs = plan.ops[lev]
+        inside = set()
+        for fi, d, side, fplane, parent, ga, gb, sz, layer in _faces(levels, lev):
+            po = _zyx(levels[lev - 1]["origins"][parent][0])
+            cn = levels[lev - 1]["patches"][parent][0]
+            if 0 <= layer - po[d] < cn[d]:
+                inside.update(off for off, *_ in plan.coarse_dst[lev][(fi, d, side)])
+        keep = [S for S in fs if S.creg in inside]
+        assert 0 < len(keep) < len(fs)
+        sets = (ctu.ctu_reflux_set * len(keep))(*keep)
+        plan.ops[lev] = (pb, rb, sets)
+    tot0, tot1, mag = _oracle_coarse_step(levels, 32, plan, {})
+    assert np.any(np.abs(tot1 - tot0)[:8] > 1e-10 * mag[:8])
