@@ -425,10 +425,11 @@ class _OracleCtx:
             _block(U, b.cbase, cn)[...] = C
 
 
-def _oracle_coarse_step(levels, base, plan, par):
+def _oracle_coarse_step(levels, base, plan, par, result=None):
     """Restrict the hierarchy (every covered coarse cell the mean of its
     children), then take one coarse step; returns level 0's totals of
-    U_q x cell volume before and after, and the totals of |U_q| x volume."""
+    U_q x cell volume before and after, and the totals of |U_q| x volume.
+    `result`, a dict, receives dt_0, c_h and every level's output pool."""
     import oracle as O
     from paper_1110_0740_gb300 import ctu
     adv = LevelAdvance.__new__(LevelAdvance)
@@ -461,6 +462,8 @@ def _oracle_coarse_step(levels, base, plan, par):
     tot0, mag = totals(adv.A[0])
     adv.coarse_step(None)
     tot1, _ = totals(adv.outputs()[0])
+    if result is not None:
+        result.update(dt0=dt0, ch=ch, outputs=adv.outputs())
     return tot0, tot1, mag
 
 
