@@ -263,18 +263,43 @@ def _shock_prim(xc, yc, zc, c, r0, gamma):
     return [rho, vr * dx_ / r, vr * dy_ / r, vr * dz_ / r, p, z + 0.3, z + 0.4, z, z]
 
 
-def amr_hierarchy(seed=0, base=128, target=600, gamma=5.0 / 3.0):
+def _nest(cubes, parents, region, smallest=8):
+    """Proper nesting: keep the level-(l+1) cubes [(origin (z, y, x), size)]
+    whose footprint on level l, grown by one level-l cell on every side,
+    lies inside `region` (level l's cells covered by its patches, periodic);
+    a cube that does not is replaced by its eight children, down to the
+    smallest size, below which it is dropped.  Returns (cubes, parents)."""
+    dom = region.shape[0]
+    out, par = [], []
+    todo = list(zip(cubes, parents))
+    while todo:
+        (o, s), pi = todo.pop()
+        idx = [np.arange(v // 2 - 1, (v + s) // 2 + 1) % dom for v in o]
+        if region[np.ix_(*idx)].all():
+            out.append((o, s))
+            par.append(pi)
+        elif s > smallest:
+            h = s // 2
+            todo += [(((o[0] + a * h, o[1] + b * h, o[2] + c * h), h), pi)
+                     for a in (0, 1) for b in (0, 1) for c in (0, 1)]
+    return out, par
+
+
+def amr_hierarchy(seed=0, base=128, target=600, gamma=5.0 / 3.0, nested=False, smooth=False):
     """Seeded 3-level hierarchy (refinement ratio 2, base `base`^3 cells on the
     unit cube as 8 patches of (base/2)^3) around an expanding spherical shock.
     Level l+1 tags the cells of level l within a shell around the shock
     radius and covers them with aligned cubes from {64, 32, 16, 8} (in level
-    l+1 cells), largest first, each inside one level-l patch (proper
-    nesting).  The shell width is tuned by bisection so that the hierarchy
-    has about `target` patches.  Returns a dict with, per level, the patch
-    list [(n(3), dx(3), base offset)], the float64 pool (9, stride) with
-    ghosts filled from the analytic state, and the footprints of every
-    level-(l+1) patch in its parent (parent index, origin in parent cells,
-    size in parent cells)."""
+    l+1 cells), largest first, each inside one level-l patch.  A level-2
+    patch may then touch the edge of level 1's region; with `nested`, every
+    level-(l+1) patch keeps one level-l cell of level l around it (proper
+    nesting, see _nest).  The shell width is tuned by bisection so that the
+    hierarchy has about `target` patches.  Returns a dict with, per level,
+    the patch list [(n(3), dx(3), base offset)], the float64 pool (9,
+    stride) with ghosts filled from the analytic state (or the smooth state
+    of _smooth_prim with `smooth`), and the footprints of every level-(l+1)
+    patch in its parent (parent index, origin in parent cells, size in
+    parent cells)."""
     rng = np.random.default_rng(seed)
     c = rng.uniform(0.4, 0.6, size=3)
     r0 = rng.uniform(0.18, 0.25)
@@ -299,6 +324,11 @@ def amr_hierarchy(seed=0, base=128, target=600, gamma=5.0 / 3.0):
                 for (lo, sz) in _cover(tags):
                     plist.append(((lo[0] + oz, lo[1] + oy, lo[2] + ox), sz))
                     par.append(pi)
+            if nested and lev > 1:
+                region = np.zeros((base * 2 ** (lev - 1),) * 3, dtype=bool)
+                for (o, s) in levels[-1]:
+                    region[o[0]:o[0] + s, o[1]:o[1] + s, o[2]:o[2] + s] = True
+                plist, par = _nest(plist, par, region)
             levels.append(plist)
             parents.append(par)
         return levels, parents
@@ -306,11 +336,13 @@ def amr_hierarchy(seed=0, base=128, target=600, gamma=5.0 / 3.0):
     best = None
     for width in np.geomspace(0.004, 0.12, 16):
         levels, parents = build(width)
+        if not all(levels):
+            continue  # a level left empty (nesting can drop a thin level whole)
         tot = sum(len(L) for L in levels)
         if best is None or abs(tot - target) < abs(best[0] - target):
             best = (tot, levels, parents)
     tot, levels, parents = best
-    return amr_levels(levels, parents, base, c, r0, gamma)
+    return amr_levels(levels, parents, base, c, r0, gamma, smooth=smooth)
 
 
 def _smooth_prim(xc, yc, zc):

@@ -498,3 +498,16 @@ def test_without_the_pieces_across_a_parent_boundary_the_totals_drift():
         plan.ops[lev] = (pb, rb, sets)
     tot0, tot1, mag = _oracle_coarse_step(levels, 32, plan, {})
     assert np.any(np.abs(tot1 - tot0)[:8] > 1e-10 * mag[:8])
+
+
+def test_a_nested_seeded_hierarchy_conserves():
+    """amr_hierarchy(nested=True) keeps one level-l cell of level l around
+    every level-(l+1) patch, so every coarse face beside a fine patch has a
+    patch to reflux (none unmatched), and the oracle-driven coarse step of
+    the seeded hierarchy (smooth state, 61 patches) conserves to round-off."""
+    levels = W.amr_hierarchy(seed=5, base=32, target=40, nested=True, smooth=True)["levels"]
+    assert all(len(lv["patches"]) for lv in levels)
+    plan = LevelPlan(levels, 32)
+    assert plan.unmatched_faces == 0
+    tot0, tot1, mag = _oracle_coarse_step(levels, 32, plan, {})
+    assert np.all(np.abs(tot1 - tot0)[:8] <= 1e-13 * mag[:8]), (tot1 - tot0) / mag
