@@ -534,7 +534,7 @@ def run_amr(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    H = W.amr_hierarchy(seed=0)
+    H = W.amr_hierarchy(seed=0, nested=args.amr_nested)
     L = H["levels"]
     prec = ctu.CTU_MIXED if args.precision == "mixed" else ctu.CTU_FP64
     # this rank's patches per level (indices into the level's patch list)
@@ -734,6 +734,8 @@ def run_amr(args):
                 "config": {"workload": "batched AMR level advance: 3-level hierarchy, ratio 2, base "
                                        "128^3, PPM+HLLD+GLM, subcycled 1/2/4 in one CUDA graph, "
                                        "coarse-fine flux registers"
+                                       + ("; properly nested (one coarse cell around every fine patch)"
+                                          if args.amr_nested else "")
                                        + (f"; parabolic terms kappa {args.kappa} (along the field "
                                           f"{args.kappa_par or args.kappa}, phi {args.tc_phi}), nu {args.nu}, "
                                           f"eta {args.eta}"
@@ -1095,6 +1097,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-level-ops", action="store_true",
                     help="amr: advance the levels without prolongation, restriction and reflux")
+    ap.add_argument("--amr-nested", action="store_true",
+                    help="amr: the seeded hierarchy with proper nesting (every coarse face beside a fine "
+                         "patch refluxed)")
     ap.add_argument("--riemann", default="hlld", choices=["hlld", "hllc"],
                     help="blast: the Riemann solver (the workload uses HLLD)")
     ap.add_argument("--kappa", type=float, default=0.0,
