@@ -263,6 +263,7 @@ class _Ghosts:
     def __init__(self):
         self.done = {}  # buffer -> set of fills since its last write
         self.log = []
+        self.launches = 0
 
     def written(self, U):
         self.done[U.name] = set()
@@ -296,6 +297,10 @@ class _Ctx:
     def reflux(self, U, cs, reg, sets, stream=None):
         self.g.written(U)
         self.g.log.append(("reflux", U.name))
+        self.g.launches += len({(S.dir, S.side) for S in sets})  # one launch per class
+
+    def launches(self):
+        return 7 + self.lev  # a step's kernel launches, any per-level count
 
     def restrict(self, U, cs, F, fs, boxes, stream=None):
         self.g.written(U)
@@ -329,6 +334,12 @@ def test_coarse_step_reads_no_stale_ghosts(plan):
         ("reflux", "B1"), ("restrict", "B1", "A2"), ("reflux", "A1"), ("restrict", "A1", "A2"),
         ("reflux", "B0"), ("restrict", "B0", "A1")]
     assert [b.name for b in adv.outputs()] == ["B0", "A1", "A2"]
+    # the launch count the bench reports: every step's launches, one per
+    # prolongation, exchange and restriction, one per reflux class
+    lev_of = {"A0": 0, "B0": 0, "A1": 1, "B1": 1, "A2": 2, "B2": 2}
+    issued = g.launches + sum(7 + lev_of[e[2]] for e in g.log if e[0] == "step")
+    issued += sum(1 for e in g.log if e[0] in ("prolong", "exchange", "restrict"))
+    assert adv.launches() == issued
 
 
 def test_the_check_rejects_a_coarse_state_without_its_ghost_fill(plan):
